@@ -1,0 +1,362 @@
+"""Benchmark: V-cycle throughput of the GB300 multigrid solve (DOFs per second per V-cycle).
+
+Workload (default): 3D Poisson on the unit cube, conforming Q1 on a 128^3 hex mesh
+(2,048,383 interior DOFs, 27-point stencil), f from u = sin(pi x) sin(pi y) sin(pi z),
+FP64, 6 levels (coarsest 4^3 cells, dense LU), V(2,2) with one degree-2 Chebyshev
+polynomial per smoothing phase. A step is one defect-correction iteration: FP64 outer
+residual and its norm, one V-cycle, x += c.
+
+Prints one JSON line (rank 0). Besides the throughput it reports
+  * roofline: the dominant kernel (finest-level smoother sweep) timed with CUDA events
+    around each launch inside the timed region, its algorithmic bytes per launch, and
+    the fraction of the measured HBM copy bandwidth;
+  * e2e: full solves to 1e-10 through mg_solve_host from pinned host memory;
+  * time_to_solution: FP64 and mixed (FP32 V-cycle in FP64 defect correction) solves;
+  * cpu_baseline: the FP64 CPU oracle on a bounded sample of the same workload.
+--impl reference times the oracle alone (the reference arm) on host cores.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "V-cycle DOFs/s"
+UNIT = "DOF/s"
+WORKLOADS = {
+    "q1_3d_128_cheb": "3D Poisson, Q1, 128^3 cells (2,048,383 DOFs), 6 levels, V(2,2) Chebyshev deg 2, FP64",
+    "q1_2d_64": "2D Poisson, Q1, 64^2 cells (3,969 DOFs), 5 levels, V(2,2) Jacobi 0.8, FP64",
+    "rq1_3d_96": "3D Poisson, rotated Q1, 96^3 cells (2,626,560 DOFs), 6 levels, V(2,2) Jacobi 0.7, FP64",
+}
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.lines:
+            return None
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _traffic_from_profile(kernel_tag):
+    """DRAM bytes per launch from the committed ncu summary, if it matches the current kernels."""
+    src = os.path.join(ROOT, "paper_1609_04809_gb300", "csrc", "kernels.cuh")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        parts = line.split()
+        if len(parts) >= 3 and parts[0] == kernel_tag and parts[1] == sha:
+            return float(parts[2])
+    return None
+
+
+def _config_args(name):
+    from paper_1609_04809_gb300 import workloads as W
+    c = dict(W.CONFIGS[name])
+    return c
+
+
+def _problem_rhs(c):
+    from paper_1609_04809_gb300 import mg, workloads as W
+    modes = W.manufactured_modes(c["dim"]) if c["rhs"] == "manufactured" else None
+    return mg.mg_load_vector(c["dim"], c["element"], c["n_cells"], modes=modes, f_const=1.0), modes
+
+
+def _oracle_workload(name):
+    import oracle
+    from paper_1609_04809_gb300 import workloads as W
+    c = _config_args(name)
+    O = oracle.Hierarchy(c["dim"], c["element"], c["n_cells"], c["n_levels"],
+                         opts=oracle.Options(smoother=c["smoother"], omega=c["omega"], cheb_degree=c["cheb_degree"],
+                                             nu_pre=c["nu_pre"], nu_post=c["nu_post"]))
+    modes = W.manufactured_modes(c["dim"]) if c["rhs"] == "manufactured" else None
+    b = oracle.load_vector(c["dim"], c["element"], c["n_cells"], modes=modes)
+    return O, O.A(c["n_levels"] - 1), b
+
+
+def _oracle_step(O, A, b, x):
+    """One defect-correction iteration of the oracle: r = b - A x, c = V(r), x + c."""
+    import oracle
+    r = b - oracle.spmv(A, x)
+    return x + O.vcycle(r)
+
+
+def cpu_baseline(name, cycles):
+    """The oracle (single-threaded C, FP64) on the same workload: setup, then `cycles` timed iterations."""
+    O, A, b = _oracle_workload(name)
+    x = np.zeros(O.n)
+    t0 = time.perf_counter()
+    for _ in range(cycles):
+        x = _oracle_step(O, A, b, x)
+    dt = time.perf_counter() - t0
+    return O.n * cycles / dt, dt
+
+
+def run_reference(args):
+    rank = _env_int("RANK", 0)
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    name = args.config
+    O, A, b = _oracle_workload(name)
+    x = np.zeros(O.n)
+    for _ in range(args.warmup):
+        x = _oracle_step(O, A, b, x)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        x = _oracle_step(O, A, b, x)
+    dt = time.perf_counter() - t0
+    val = O.n * args.steps / dt
+    sample = ("%d defect-correction iterations (FP64 residual + V-cycle + update) of the %s workload, "
+              "oracle setup excluded" % (args.steps, name))
+    out = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": name, "description": WORKLOADS.get(name, name)},
+           "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    from paper_1609_04809_gb300 import mg, workloads as W
+    import __graft_entry__
+
+    world = _env_int("WORLD_SIZE", 1)
+    rank = _env_int("RANK", 0)
+    local = _env_int("LOCAL_RANK", 0)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    if rank == 0 or world == 1:
+        __graft_entry__.build_library()
+    if dist:
+        dist.barrier()
+
+    name = args.config
+    c = _config_args(name)
+    b_host, modes = _problem_rhs(c)
+    n = b_host.size
+    H = mg.Hierarchy(c["dim"], c["element"], c["n_cells"], c["n_levels"], smoother=c["smoother"],
+                     omega=c["omega"], cheb_degree=c["cheb_degree"], nu_pre=c["nu_pre"], nu_post=c["nu_post"],
+                     precision=mg.MG_FP64)
+    info = H.info()
+    Lf = c["n_levels"] - 1
+    bd = torch.from_numpy(b_host).cuda()
+    xd = torch.zeros_like(bd)
+    stream = torch.cuda.current_stream()
+
+    # warm-up steps
+    H.cycle(bd, xd, args.warmup)
+    torch.cuda.synchronize()
+    mg.mg_profile_enable(H.h, True)
+    xd.zero_()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        H.cycle(bd, xd, args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    t = torch.tensor([ms], device="cuda")
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * n * args.steps / (ms_max * 1e-3)
+
+    # dominant kernel: finest-level smoother sweep
+    k_ms, k_cnt, k_bytes = mg.mg_profile_read(H.h, mg.MG_K_SMOOTH, Lf)
+    per_kernel = {}
+    for kc in range(mg.MG_K_COUNT):
+        tot = 0.0
+        for l in range(c["n_levels"]):
+            tot += mg.mg_profile_read(H.h, kc, l)[0]
+        per_kernel[mg.KCLASS_NAMES[kc]] = round(tot / args.steps, 4)
+    mg.mg_profile_enable(H.h, False)
+    peak, peak_kind = _peaks()
+    achieved = k_bytes / (k_ms / k_cnt * 1e-3) / 1e9 if k_cnt else None
+
+    out = None
+    if rank == 0:
+        # end to end through the public host API: full solves from pinned host memory
+        bh = torch.from_numpy(b_host).pin_memory()
+        xh = torch.zeros(n, dtype=torch.float64).pin_memory()
+        tol = c["tol"]
+        mg.mg_solve_host(H.h, bh.numpy(), xh.numpy(), tol)  # warm
+        e2e_runs, e2e_iters = [], 0
+        for _ in range(args.e2e_solves):
+            xh.zero_()
+            t0 = time.perf_counter()
+            st, it, hist = mg.mg_solve_host(H.h, bh.numpy(), xh.numpy(), tol)
+            e2e_runs.append(time.perf_counter() - t0)
+            e2e_iters = it
+        e2e_t = float(np.median(e2e_runs))
+        e2e = {"value": n * e2e_iters / e2e_t, "unit": UNIT, "h2d_bytes_per_step": 16 * n, "d2h_bytes_per_step": 8 * n,
+               "step": "one mg_solve_host call to rel. residual %g (%d V-cycles, %.3f ms)" % (tol, e2e_iters, 1e3 * e2e_t)}
+
+        # time to solution, FP64 vs mixed
+        tts = None
+        if not args.no_mixed:
+            def solve_time(h):
+                x = torch.zeros_like(bd)
+                mg.mg_solve(h.h, bd, x, tol, 100)
+                ts = []
+                for _ in range(3):
+                    x.zero_()
+                    torch.cuda.synchronize()
+                    s0 = time.perf_counter()
+                    st, it, hist = mg.mg_solve(h.h, bd, x, tol, 100)
+                    ts.append(time.perf_counter() - s0)
+                return float(np.median(ts)), it, hist[-1]
+            t64, it64, r64 = solve_time(H)
+            Hm = mg.Hierarchy(c["dim"], c["element"], c["n_cells"], c["n_levels"], smoother=c["smoother"],
+                              omega=c["omega"], cheb_degree=c["cheb_degree"], nu_pre=c["nu_pre"],
+                              nu_post=c["nu_post"], precision=mg.MG_MIXED)
+            t32, it32, r32 = solve_time(Hm)
+            tts = {"tol": tol, "fp64_ms": 1e3 * t64, "fp64_iters": it64, "mixed_ms": 1e3 * t32, "mixed_iters": it32,
+                   "mixed_final_rel_residual": r32, "speedup_mixed_vs_fp64": t64 / t32}
+            Hm.close()
+
+        cpu = None
+        if world == 1 and not args.no_cpu:
+            cv, cdt = cpu_baseline(name, args.cpu_cycles)
+            cpu = {"value": cv, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": "%d defect-correction iterations of the %s workload by the single-threaded FP64 "
+                             "C oracle (setup excluded, %.1f s)" % (args.cpu_cycles, name, cdt)}
+
+        clocks = clk.summary()
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+               "config": {"workload": name, "description": WORKLOADS.get(name, name), "n_dofs": n,
+                          "parallelism": "replicas" if world > 1 else "single-gpu",
+                          "l2": "inputs larger than L2 (finest FP64 matrix %.0f MB > 129 MB L2)"
+                                % (info["nnz"][Lf] * 8 / 1e6),
+                          "storage": ["csr", "ell", "dia"][info["storage"][Lf] - 1]},
+               "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                            "frac": achieved / peak if achieved else None,
+                            "traffic": _traffic_from_profile("smooth_fp64_%s" % name),
+                            "kernel": "finest-level smoother sweep (fused residual + Chebyshev update)",
+                            "bytes_per_launch": k_bytes, "launches": k_cnt,
+                            "us_per_launch": 1e3 * k_ms / k_cnt if k_cnt else None,
+                            "peak_kind": "%s HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" % peak_kind},
+               "kernel_ms_per_step": per_kernel,
+               "e2e": e2e, "time_to_solution": tts, "cpu_baseline": cpu,
+               "gpu_launches": info["kernels_per_cycle"] * args.steps + 1,
+               "clocks": clocks}
+        print(json.dumps(out))
+    H.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="q1_3d_128_cheb", choices=sorted(WORKLOADS))
+    ap.add_argument("--e2e-solves", type=int, default=3)
+    ap.add_argument("--cpu-cycles", type=int, default=8)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

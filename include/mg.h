@@ -1,0 +1,212 @@
+/*
+ * mg.h -- C ABI of libmg.so, a GB300 (sm_103a) geometric multigrid solver for the
+ * sparse finite element systems of conforming Q1 and nonconforming rotated-Q1
+ * (Rannacher-Turek) elements on uniformly refined grids of the unit square / cube.
+ *
+ * The operation is the multigrid solve of the paper "An object oriented parallel
+ * finite element scheme for computations of PDEs: Design and implementation"
+ * (Ganesan et al.): V-cycles (Sec. 5.3, Algorithm "Parallel Multigrid Solver
+ * (V-Cycle)") of smoothing sweeps, restriction of the residual, an exact solve on the
+ * coarsest level, prolongation with correction, on a hierarchy of meshes obtained by
+ * uniform refinement (Sec. 5.1), with grid transfers between the levels (Sec. 5.4).
+ * The V-cycle is applied to the defect inside a defect-correction loop that stops at
+ * a relative residual.
+ *
+ * Conventions for every entry point:
+ *   - Return value: MG_OK (0) or a negative MG_E* code; mg_last_error() then returns a
+ *     thread-local message. No C++ exception crosses this interface.
+ *   - "device pointer": memory of the CUDA device current when mg_setup was called.
+ *     "host pointer": ordinary (pageable or pinned) CPU memory.
+ *   - The library owns hierarchies and servers; the caller owns every array it passes.
+ *   - DOF order: interior DOFs only (homogeneous Dirichlet boundary eliminated).
+ *     Q1: vertices (ix, iy[, iz]) in [1, N-1]^d, index (ix-1) + (N-1)*((iy-1) +
+ *     (N-1)*(iz-1)). Rotated Q1: faces normal to x, then y, then z; a face normal to x
+ *     at x = i/N over cell (j, k) has index (i-1) + (N-1)*(j + N*k), normal to y at
+ *     y = j/N over cell (i, k): (N-1)N^2 + i + N*((j-1) + (N-1)*k), normal to z at
+ *     z = k/N over cell (i, j): 2(N-1)N^2 + i + N*(j + N*(k-1)).
+ *   - Thread safety: calls on different hierarchies may run concurrently; calls on one
+ *     hierarchy must not overlap.
+ */
+#ifndef MG_H
+#define MG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int mg_status;
+#define MG_OK 0
+#define MG_PENDING 1      /* mg_serve_poll: the request is not finished yet */
+#define MG_EINVAL (-1)    /* invalid argument (sizes, enum values, NULL where required) */
+#define MG_ENOMEM (-2)    /* host or device allocation failed */
+#define MG_ENOCONV (-3)   /* max_iters reached before the tolerance; x holds the last iterate */
+#define MG_ECUDA (-4)     /* a CUDA runtime call failed */
+#define MG_ETIMEOUT (-5)  /* a bounded wait ran out */
+#define MG_EBUDGET (-6)   /* a serving request can never fit the device-memory budget */
+#define MG_ENOTFOUND (-7) /* unknown serving ticket */
+
+/* element */
+#define MG_Q1 0  /* conforming bi/trilinear, vertex DOFs, 2D or 3D */
+#define MG_RQ1 1 /* nonconforming rotated Q1 with face-mean DOFs, 3D */
+/* smoother */
+#define MG_JACOBI 0    /* damped Jacobi x <- x + omega D^-1 (b - A x) */
+#define MG_CHEBYSHEV 1 /* Chebyshev polynomial in D^-1 A of degree cheb_degree */
+/* precision */
+#define MG_FP64 0  /* every step in FP64 */
+#define MG_MIXED 1 /* FP32 V-cycle (matrices, smoother, transfers) inside FP64 defect correction */
+/* device storage of the level matrices */
+#define MG_STORAGE_AUTO 0 /* chosen by timing the candidates on the device at setup */
+#define MG_STORAGE_CSR 1  /* compressed sparse rows, one thread per row */
+#define MG_STORAGE_ELL 2  /* column-major ELLPACK with explicit 32-bit column indices */
+#define MG_STORAGE_DIA 3  /* column-major ELLPACK whose columns are row + fixed offsets (Q1 only) */
+
+#define MG_MAX_LEVELS 16
+
+/* The problem: a uniform grid of n_cells^dim cells on the unit square / cube, refined
+ * n_levels-1 times from the coarsest grid of n_cells / 2^(n_levels-1) cells per axis
+ * (which must be an integer >= 2). k_cell: host pointer to the per-cell diffusion
+ * coefficient of the finest grid (n_cells^dim values, x fastest), or NULL for k = 1. */
+typedef struct {
+    int dim;
+    int element;
+    int n_cells;
+    int n_levels;
+    const double *k_cell;
+} mg_problem;
+
+/* Solver options. mg_options_default() fills in damped Jacobi (omega 0.8), V(2,2),
+ * FP64, automatic storage, 100 iterations, CUDA graphs on. nu_pre / nu_post count
+ * smoother applications; a Chebyshev application performs cheb_degree matrix-vector
+ * products. Chebyshev targets [lambda_u / cheb_ratio, lambda_u] with lambda_u =
+ * cheb_hi * lambda_hat and lambda_hat from power_iters steps of the power method on
+ * D^-1 A (start vector from SplitMix64(power_seed)). */
+typedef struct {
+    int smoother;
+    double omega;
+    int cheb_degree;
+    int nu_pre, nu_post;
+    double cheb_hi, cheb_ratio;
+    int power_iters;
+    uint64_t power_seed;
+    int precision;
+    int storage;
+    int max_iters;
+    int use_graph;
+} mg_options;
+
+/* Right-hand side f of -div(k grad u) = f: the constant f_const if n_modes == 0, else
+ * f = -Laplace(u) of the manufactured u = sum_m amp[m] prod_d sin(freq[3m+d] pi x_d).
+ * amp: host, n_modes values; freq: host, 3*n_modes integers (third ignored in 2D). */
+typedef struct {
+    int n_modes;
+    const double *amp;
+    const int *freq;
+    double f_const;
+} mg_rhs;
+
+/* Device memory and ordering. alloc/free: the only source of device memory (NULL:
+ * cudaMalloc/cudaFree); alloc returns NULL on failure and must return 256-byte aligned
+ * memory. stream: the cudaStream_t the caller orders its work on (NULL: the legacy
+ * default stream); the library runs on a private stream joined to it by events. */
+typedef struct {
+    void *(*alloc)(size_t bytes, void *ctx);
+    void (*free)(void *ptr, size_t bytes, void *ctx);
+    void *ctx;
+    void *stream;
+} mg_device;
+
+typedef struct mg_hierarchy mg_hierarchy;
+
+/* Description of a built hierarchy (level 0 = coarsest). */
+typedef struct {
+    int n_levels;
+    int precision;
+    int64_t n[MG_MAX_LEVELS];       /* DOFs per level */
+    int64_t nnz[MG_MAX_LEVELS];     /* stored structural nonzeros per level matrix */
+    int storage[MG_MAX_LEVELS];     /* MG_STORAGE_* chosen per level */
+    int galerkin[MG_MAX_LEVELS];    /* 1 if the level matrix is R A P of the finer level */
+    double lambda[MG_MAX_LEVELS];   /* power-method estimate of lambda_max(D^-1 A), 0 if unused */
+    size_t device_bytes;            /* device memory held by the hierarchy */
+    int kernels_per_cycle;          /* kernel launches in one defect-correction iteration */
+} mg_info;
+
+void mg_options_default(mg_options *o);
+
+/* Number of interior DOFs; -1 for an invalid combination. */
+int64_t mg_ndofs(int dim, int element, int n_cells);
+
+/* Load vector b_i = integral of f phi_i over the finest grid, 3-point Gauss rule per
+ * axis per cell (host computation). b_host: n DOFs, caller-owned. */
+mg_status mg_load_vector(const mg_problem *p, const mg_rhs *f, double *b_host);
+
+/* The hierarchy's level operators as assembled on the host, without a GPU: which = 0:
+ * A_level, 1: P_level (rows: level, columns: level-1), 2: R_level = P_level^T, in CSR
+ * with ascending columns and FP64 values (the same matrices mg_setup stores). Call with
+ * rowptr = NULL to get *nrows and *nnz only; then rowptr holds nrows+1 entries and
+ * col/val nnz entries (caller-owned host arrays). */
+mg_status mg_assemble_operator(const mg_problem *p, int level, int which, int64_t *nrows, int64_t *nnz,
+                               int64_t *rowptr, int32_t *col, double *val);
+
+/* Build the level hierarchy: per-level stiffness matrices (rediscretised; R A P of the
+ * finer level where the coefficient is not resolved by the coarse cells), transfer
+ * operators P (Q1 nodal interpolation, rotated-Q1 face averaging) and R = P^T, device
+ * storage, the coarsest-level LU factorisation (FP64, on the device), smoother
+ * parameters and the CUDA graphs of one iteration. dev may be NULL. */
+mg_status mg_setup(const mg_problem *p, const mg_options *o, const mg_device *dev, mg_hierarchy **out);
+mg_status mg_hierarchy_free(mg_hierarchy *h);
+mg_status mg_get_info(const mg_hierarchy *h, mg_info *info);
+
+/* Defect correction with V-cycles until ||b - A x||_2 <= rel_tol * ||b||_2:
+ *   r_k = b - A x_k (FP64), stop test, c = V(r_k), x_{k+1} = x_k + c.
+ * b_dev, x_dev: device pointers to n doubles; x_dev holds the initial guess on entry
+ * and the result on exit. iters (may be NULL): V-cycles performed. res_hist (host, may
+ * be NULL, max_iters + 1 doubles): ||r_k|| / ||b|| for k = 0..iters. Returns MG_ENOCONV
+ * if max_iters cycles do not reach the tolerance. Synchronises with the caller's
+ * stream on return. */
+mg_status mg_solve(mg_hierarchy *h, const double *b_dev, double *x_dev, double rel_tol, int *iters,
+                   double *res_hist);
+
+/* mg_solve with host arrays: copies b to the device, solves, copies x back (x_host
+ * also supplies the initial guess). */
+mg_status mg_solve_host(mg_hierarchy *h, const double *b_host, double *x_host, double rel_tol, int *iters,
+                        double *res_hist);
+
+/* Exactly n_cycles defect-correction iterations without a stop test (no host
+ * synchronisation between them). rel_res (may be NULL): ||r|| / ||b|| of the last
+ * residual computed, i.e. before the last correction. */
+mg_status mg_cycle(mg_hierarchy *h, const double *b_dev, double *x_dev, int n_cycles, double *rel_res);
+
+/* Copy a level operator to the host as CSR (FP64 values, structural pattern):
+ * which = 0: A_level (precision MG_FP64 or MG_MIXED selects the stored copy),
+ * 1: P_level (rows: level, columns: level-1), 2: R_level = P_level^T.
+ * Call with rowptr = NULL to get *nnz only; otherwise rowptr holds nrows+1, col/val nnz. */
+mg_status mg_export_operator(const mg_hierarchy *h, int level, int which, int precision, int64_t *nrows,
+                             int64_t *nnz, int64_t *rowptr, int32_t *col, double *val);
+
+/* Per-kernel timing with CUDA events recorded around every launch (kernel classes
+ * below); off by default. mg_profile_read returns the accumulated device time and
+ * launch count of one (class, level) since the last enable, and the algorithmic
+ * bytes one such launch moves. */
+#define MG_K_SMOOTH 0   /* smoother sweep (fused residual + update) */
+#define MG_K_RESID 1    /* residual before restriction */
+#define MG_K_RESTRICT 2 /* b_{l-1} = R r */
+#define MG_K_PROLONG 3  /* x_l += P x_{l-1} */
+#define MG_K_COARSE 4   /* coarsest-level LU solve */
+#define MG_K_OUTER 5    /* FP64 outer residual and its norm */
+#define MG_K_UPDATE 6   /* x += c */
+#define MG_K_SMOOTH0 7  /* first smoother step from x = 0 (diagonal only, no matrix-vector product) */
+#define MG_K_COUNT 8
+mg_status mg_profile_enable(mg_hierarchy *h, int enable);
+mg_status mg_profile_read(const mg_hierarchy *h, int kclass, int level, double *ms_total, int64_t *launches,
+                          double *bytes_per_launch);
+
+/* Thread-local description of the last error on this thread. */
+const char *mg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MG_H */

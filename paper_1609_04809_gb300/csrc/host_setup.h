@@ -1,0 +1,75 @@
+// host_setup.h -- host-side construction of the multigrid hierarchy (internal).
+//
+// Mesh numbering, element matrices, grid transfers, Galerkin products, the load vector
+// and the power-method eigenvalue estimate, all in FP64 on the host. The results feed
+// the device formats built in solver.cu.
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include "mg.h"
+
+namespace mgh {
+
+struct Csr {
+    int64_t nrows = 0, ncols = 0;
+    std::vector<int64_t> rowptr;  // nrows + 1
+    std::vector<int32_t> col;     // ascending within a row
+    std::vector<double> val;
+    int64_t nnz() const { return (int64_t)col.size(); }
+};
+
+int64_t ndofs(int dim, int elem, int N);
+
+// Stiffness matrix of the level with N cells per axis; k: per-cell coefficient on that
+// grid (lexicographic, x fastest) or nullptr for k = 1.
+void assemble(int dim, int elem, int N, const double *k, Csr &A);
+
+// Prolongation from Nc to 2 Nc cells per axis (rows: fine DOFs, columns: coarse DOFs).
+void prolongation(int dim, int elem, int Nc, Csr &P);
+
+void transpose(const Csr &M, Csr &T);
+
+// Ac = R A P with entries summed as (r_Ii a_ij) p_jJ, i, j, J ascending.
+void galerkin(const Csr &R, const Csr &A, const Csr &P, Csr &Ac);
+
+// Per-cell coefficient of the level with Nl cells if each of its cells covers fine
+// cells of one value; false otherwise.
+bool coarse_coefficient(int dim, int NL, const double *kL, int Nl, std::vector<double> &kl);
+
+void load_vector(int dim, int elem, int N, const mg_rhs *f, double *b);
+
+double power_lambda(const Csr &A, const std::vector<double> &dinv, int iters, uint64_t seed);
+
+// Row-sum-preserving FP32 copy: off-diagonals rounded to nearest, the diagonal set so
+// that the FP32 row sum matches the FP64 one (the Dirichlet part of the row).
+void round_fp32(const Csr &A, std::vector<float> &val32);
+
+// The host hierarchy: levels 0 (coarsest) .. n_levels-1 (finest, N_finest cells per
+// axis). Level l is rediscretised with the coefficient of its cells when every cell
+// covers fine cells of one value, else (and on every coarser level) it is R A P of the
+// next finer level. P[l], R[l] (l >= 1) map between levels l-1 and l. Levels below
+// `stop` are not built.
+struct HostHierarchy {
+    std::vector<int> N;
+    std::vector<int> galerkin;
+    std::vector<Csr> A, P, R;
+};
+void build_hierarchy(int dim, int elem, int N_finest, int n_levels, const double *k_finest, int stop,
+                     HostHierarchy &H);
+
+// Power-method estimate of lambda_max(D^-1 A) (the start vector is 1 + 0.2 (u - 1/2),
+// u from SplitMix64(seed), normalised).
+double level_lambda(const Csr &A, int iters, uint64_t seed);
+
+// Lexicographic coordinates of a Q1 vertex DOF (1-based grid indices).
+inline void q1_coords(int dim, int N, int64_t i, int *v)
+{
+    int64_t n1 = N - 1;
+    v[0] = (int)(i % n1) + 1;
+    v[1] = (int)((i / n1) % n1) + 1;
+    v[2] = dim == 3 ? (int)(i / (n1 * n1)) + 1 : 0;
+}
+
+}  // namespace mgh

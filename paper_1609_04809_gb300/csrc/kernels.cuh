@@ -1,0 +1,369 @@
+// kernels.cuh -- sm_103a device kernels of the multigrid V-cycle (internal).
+//
+// All level operators are memory-bound sparse passes (about 0.17 flop per byte), so
+// the kernels are built for HBM streaming, not tensor cores:
+//   * matrices are stored column-major by slot (ELLPACK order, leading dimension ld),
+//     so the 32 rows of a warp read one contiguous 128/256-byte segment per slot;
+//   * matrix values are read with the streaming cache hint (ld.global.cs): each value
+//     is used once per pass and must not evict the x vector from L2;
+//   * x is gathered through the read-only path and stays L2-resident across slots;
+//   * one thread per row, sum over the row's slots in ascending column order.
+//
+// FP64 arithmetic uses explicitly rounded products and sums (__dmul_rn, __dadd_rn),
+// never fused multiply-adds: together with the fixed slot order this makes every FP64
+// result the same bit pattern as a sequential CPU evaluation of the same formula.
+// FP32 arithmetic (the inner V-cycle of the mixed-precision solve) uses fused
+// multiply-adds.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mgk {
+
+template <typename T>
+struct Ar;
+template <>
+struct Ar<double> {
+    static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+    static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+    static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+    static __device__ __forceinline__ double mac(double s, double a, double b) { return __dadd_rn(s, __dmul_rn(a, b)); }
+    static __device__ __forceinline__ double rcp(double a) { return __ddiv_rn(1.0, a); }
+};
+template <>
+struct Ar<float> {
+    static __device__ __forceinline__ float mul(float a, float b) { return a * b; }
+    static __device__ __forceinline__ float add(float a, float b) { return a + b; }
+    static __device__ __forceinline__ float sub(float a, float b) { return a - b; }
+    static __device__ __forceinline__ float mac(float s, float a, float b) { return fmaf(a, b, s); }
+    static __device__ __forceinline__ float rcp(float a) { return __fdiv_rn(1.0f, a); }
+};
+
+// Sweep modes: what a pass does with s = (A x)_i.
+enum SweepMode {
+    SW_RESID = 0,    // out = b - s
+    SW_JACOBI = 1,   // out = x + c1*(dinv*(b - s))                 (c1 = omega)
+    SW_CHEBF = 2,    // d = c1*(dinv*(b - s)); out = x + d           (first Chebyshev step)
+    SW_CHEB = 3,     // d = c1*d + c2*(dinv*(b - s)); out = x + d    (later steps)
+    SW_JACOBI_Z = 4, // x = 0: out = c1*(dinv*b)
+    SW_CHEBF_Z = 5,  // x = 0: d = c1*(dinv*b); out = d
+};
+
+struct DiaOffs {
+    int32_t o[27];
+};
+
+// Matrix view for the kernels (values of type T).
+template <typename T>
+struct MatView {
+    const T *val;         // DIA/ELL: K*ld (slot-major); CSR: nnz
+    const int32_t *col;   // ELL: K*ld; CSR: nnz
+    const int64_t *rowptr;// CSR
+    int64_t ld;
+    int K;
+    DiaOffs offs;         // DIA: column = row + offs.o[k]
+};
+
+template <typename T, int MODE>
+__device__ __forceinline__ void sweep_out(int i, T s, T diag, T xi, const T *__restrict__ b, T *__restrict__ out,
+                                          T *__restrict__ d, T c1, T c2)
+{
+    using A = Ar<T>;
+    T bi = b[i];
+    if (MODE == SW_RESID) {
+        out[i] = A::sub(bi, s);
+    } else if (MODE == SW_JACOBI) {
+        T r = A::sub(bi, s);
+        out[i] = A::add(xi, A::mul(c1, A::mul(A::rcp(diag), r)));
+    } else if (MODE == SW_CHEBF) {
+        T r = A::sub(bi, s);
+        T dd = A::mul(c1, A::mul(A::rcp(diag), r));
+        d[i] = dd;
+        out[i] = A::add(xi, dd);
+    } else if (MODE == SW_CHEB) {
+        T r = A::sub(bi, s);
+        T dd = A::add(A::mul(c1, d[i]), A::mul(c2, A::mul(A::rcp(diag), r)));
+        d[i] = dd;
+        out[i] = A::add(xi, dd);
+    } else if (MODE == SW_JACOBI_Z) {
+        out[i] = A::mul(c1, A::mul(A::rcp(diag), bi));
+    } else {  // SW_CHEBF_Z
+        T dd = A::mul(c1, A::mul(A::rcp(diag), bi));
+        d[i] = dd;
+        out[i] = dd;
+    }
+}
+
+// DIA: column of slot k is i + offs.o[k]; slot K/2 is the diagonal. x points at element
+// 0 of a buffer padded on both sides by at least max|offs|, so no bounds test is needed
+// (slots of missing neighbours hold 0 and read a finite padded or interior value).
+template <typename T, int K, int MODE>
+__global__ void __launch_bounds__(256) k_dia_sweep(MatView<T> A, int n, const T *__restrict__ x,
+                                                   const T *__restrict__ b, T *__restrict__ out,
+                                                   T *__restrict__ d, T c1, T c2)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    constexpr int C = K / 2;
+    if (MODE == SW_JACOBI_Z || MODE == SW_CHEBF_Z) {
+        T diag = __ldcs(A.val + (int64_t)C * A.ld + i);
+        sweep_out<T, MODE>(i, T(0), diag, T(0), b, out, d, c1, c2);
+        return;
+    }
+    T a[K], xv[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) a[k] = __ldcs(A.val + (int64_t)k * A.ld + i);
+#pragma unroll
+    for (int k = 0; k < K; k++) xv[k] = __ldg(x + i + A.offs.o[k]);
+    T s = T(0);
+#pragma unroll
+    for (int k = 0; k < K; k++) s = Ar<T>::mac(s, a[k], xv[k]);
+    sweep_out<T, MODE>(i, s, a[C], xv[C], b, out, d, c1, c2);
+}
+
+// ELL with explicit columns; padded slots hold column i and value 0.
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256) k_ell_sweep(MatView<T> A, int n, const T *__restrict__ x,
+                                                   const T *__restrict__ b, T *__restrict__ out,
+                                                   T *__restrict__ d, T c1, T c2)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    T s = T(0), diag = T(0);
+    if (MODE == SW_JACOBI_Z || MODE == SW_CHEBF_Z) {
+        for (int k = 0; k < A.K; k++) {
+            int c = __ldcs(A.col + (int64_t)k * A.ld + i);
+            T v = __ldcs(A.val + (int64_t)k * A.ld + i);
+            if (c == i && diag == T(0)) diag = v;
+        }
+        sweep_out<T, MODE>(i, T(0), diag, T(0), b, out, d, c1, c2);
+        return;
+    }
+    for (int k = 0; k < A.K; k++) {
+        int c = __ldcs(A.col + (int64_t)k * A.ld + i);
+        T v = __ldcs(A.val + (int64_t)k * A.ld + i);
+        if (c == i && diag == T(0)) diag = v;
+        s = Ar<T>::mac(s, v, __ldg(x + c));
+    }
+    sweep_out<T, MODE>(i, s, diag, x[i], b, out, d, c1, c2);
+}
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256) k_csr_sweep(MatView<T> A, int n, const T *__restrict__ x,
+                                                   const T *__restrict__ b, T *__restrict__ out,
+                                                   T *__restrict__ d, T c1, T c2)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    T s = T(0), diag = T(0);
+    int64_t k0 = A.rowptr[i], k1 = A.rowptr[i + 1];
+    for (int64_t k = k0; k < k1; k++) {
+        int c = A.col[k];
+        T v = A.val[k];
+        if (c == i) diag = v;
+        if (MODE != SW_JACOBI_Z && MODE != SW_CHEBF_Z) s = Ar<T>::mac(s, v, __ldg(x + c));
+    }
+    sweep_out<T, MODE>(i, s, diag, (MODE == SW_JACOBI_Z || MODE == SW_CHEBF_Z) ? T(0) : x[i], b, out, d, c1, c2);
+}
+
+// ------------------------------------------------------------------------------------
+// Q1 grid transfers on the structured grid (no stored matrix)
+// ------------------------------------------------------------------------------------
+// Restriction b_c = P^T r: coarse vertex (X,Y[,Z]) gathers the 3^d fine vertices around
+// (2X,2Y[,2Z]) in ascending fine index, weight prod_d (1 if on the line, 1/2 otherwise).
+template <typename T, int DIM>
+__global__ void __launch_bounds__(256) k_restrict_q1(const T *__restrict__ r, T *__restrict__ bc, int Nc)
+{
+    int nc1 = Nc - 1, nf1 = 2 * Nc - 1;
+    int nc = DIM == 2 ? nc1 * nc1 : nc1 * nc1 * nc1;
+    int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= nc) return;
+    int X = I % nc1 + 1, Y = (I / nc1) % nc1 + 1, Z = DIM == 3 ? I / (nc1 * nc1) + 1 : 0;
+    T s = T(0);
+    const int zlo = DIM == 3 ? -1 : 0, zhi = DIM == 3 ? 1 : 0;
+#pragma unroll
+    for (int dz = zlo; dz <= zhi; dz++)
+#pragma unroll
+        for (int dy = -1; dy <= 1; dy++)
+#pragma unroll
+            for (int dx = -1; dx <= 1; dx++) {
+                T w = (dx ? T(0.5) : T(1)) * (dy ? T(0.5) : T(1)) * (dz ? T(0.5) : T(1));
+                int64_t j = (2 * X + dx - 1) + (int64_t)nf1 * ((2 * Y + dy - 1) + (DIM == 3 ? (int64_t)nf1 * (2 * Z + dz - 1) : 0));
+                s = Ar<T>::mac(s, w, __ldg(r + j));
+            }
+    bc[I] = s;
+}
+
+// Prolongation and correction x_f += P x_c: fine vertex v takes the coarse vertices V
+// with |v - 2V| <= 1 per axis (boundary ones are zero and skipped), ascending coarse index.
+template <typename T, int DIM>
+__global__ void __launch_bounds__(256) k_prolong_q1(const T *__restrict__ xc, T *__restrict__ xf, int Nc)
+{
+    int Nf = 2 * Nc, nf1 = Nf - 1, nc1 = Nc - 1;
+    int nf = DIM == 2 ? nf1 * nf1 : nf1 * nf1 * nf1;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nf) return;
+    int v0 = i % nf1 + 1, v1 = (i / nf1) % nf1 + 1, v2 = DIM == 3 ? i / (nf1 * nf1) + 1 : 0;
+    T t = T(0);
+    int zlo = DIM == 3 ? v2 / 2 : 0, zhi = DIM == 3 ? (v2 + 1) / 2 : 0;
+    for (int Z = zlo; Z <= zhi; Z++) {
+        if (DIM == 3 && (Z <= 0 || Z >= Nc)) continue;
+        T wz = DIM == 3 ? (v2 == 2 * Z ? T(1) : T(0.5)) : T(1);
+        for (int Y = v1 / 2; Y <= (v1 + 1) / 2; Y++) {
+            if (Y <= 0 || Y >= Nc) continue;
+            T wy = v1 == 2 * Y ? T(1) : T(0.5);
+            for (int X = v0 / 2; X <= (v0 + 1) / 2; X++) {
+                if (X <= 0 || X >= Nc) continue;
+                T wx = v0 == 2 * X ? T(1) : T(0.5);
+                int64_t J = (X - 1) + (int64_t)nc1 * ((Y - 1) + (DIM == 3 ? (int64_t)nc1 * (Z - 1) : 0));
+                t = Ar<T>::mac(t, (wx * wy) * wz, __ldg(xc + J));
+            }
+        }
+    }
+    xf[i] = Ar<T>::add(xf[i], t);
+}
+
+// Explicit CSR transfer (rotated Q1): y_i = sum_k v_k x_col  (ADD: y_i += that sum).
+template <typename T, bool ADD>
+__global__ void __launch_bounds__(256) k_csr_apply(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+                                                   const T *__restrict__ val, int n, const T *__restrict__ x,
+                                                   T *__restrict__ y)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    T s = T(0);
+    for (int64_t k = rowptr[i]; k < rowptr[i + 1]; k++) s = Ar<T>::mac(s, val[k], __ldg(x + col[k]));
+    y[i] = ADD ? Ar<T>::add(y[i], s) : s;
+}
+
+// ------------------------------------------------------------------------------------
+// Coarsest level: dense LU in FP64 (one CTA, n <= 1024)
+// ------------------------------------------------------------------------------------
+// Right-looking LU with partial pivoting; the first row of maximal |a| is the pivot.
+__global__ void k_lu_factor(double *a, int n, int *piv, int *info);
+
+// Solve with the factors: row swaps in factorisation order, then column-oriented
+// substitutions so every thread owns one row and its running sum: forward in ascending
+// column order, backward in descending column order. Input and output in T.
+template <typename T>
+__global__ void k_coarse_solve(const double *__restrict__ lu, const int *__restrict__ piv, int n,
+                               const T *__restrict__ b, T *__restrict__ x)
+{
+    extern __shared__ double xs[];
+    int t = threadIdx.x;
+    if (t < n) xs[t] = (double)b[t];
+    __syncthreads();
+    if (t == 0)
+        for (int k = 0; k < n; k++) {
+            int p = piv[k];
+            if (p != k) {
+                double tmp = xs[k];
+                xs[k] = xs[p];
+                xs[p] = tmp;
+            }
+        }
+    __syncthreads();
+    double s = 0.0;
+    for (int j = 0; j < n; j++) {
+        if (t == j) xs[j] = __dsub_rn(xs[j], s);
+        __syncthreads();
+        if (t > j && t < n) s = __dadd_rn(s, __dmul_rn(lu[(int64_t)t * n + j], xs[j]));
+    }
+    __syncthreads();
+    s = 0.0;
+    for (int j = n - 1; j >= 0; j--) {
+        if (t == j) xs[j] = __ddiv_rn(__dsub_rn(xs[j], s), lu[(int64_t)j * n + j]);
+        __syncthreads();
+        if (t < j) s = __dadd_rn(s, __dmul_rn(lu[(int64_t)t * n + j], xs[j]));
+    }
+    __syncthreads();
+    if (t < n) x[t] = (T)xs[t];
+}
+
+// ------------------------------------------------------------------------------------
+// FP64 outer residual r = b - A64 x64 with ||r||^2, and helpers
+// ------------------------------------------------------------------------------------
+// Block sums of r^2 in a fixed tree order; the last block to finish (ticket) adds the
+// block sums in a fixed order and writes the total, so the result does not depend on
+// block scheduling.
+__device__ __forceinline__ double block_sum(double v, double *sh)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x < 32) {
+        s = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    }
+    __syncthreads();
+    return s;  // valid in thread 0
+}
+
+__device__ __forceinline__ void finish_norm(double part, double *partial, unsigned *ticket, double *out)
+{
+    __shared__ double sh[32];
+    __shared__ bool last;
+    double s = block_sum(part, sh);
+    if (threadIdx.x == 0) {
+        partial[blockIdx.x] = s;
+        __threadfence();
+        unsigned t = atomicAdd(ticket, 1u);
+        last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double acc = 0.0;
+    for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x) acc += ((volatile double *)partial)[k];
+    double tot = block_sum(acc, sh);
+    if (threadIdx.x == 0) {
+        *out = tot;
+        *ticket = 0u;
+    }
+}
+
+template <typename Tin, int FMT, int K>
+__global__ void __launch_bounds__(256) k_outer_resid(MatView<double> A, int n, const double *__restrict__ x,
+                                                     const double *__restrict__ b, Tin *__restrict__ r,
+                                                     double *partial, unsigned *ticket, double *norm2)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double sq = 0.0;
+    if (i < n) {
+        double s = 0.0;
+        if (FMT == 3) {  // DIA
+            double a[K], xv[K];
+#pragma unroll
+            for (int k = 0; k < K; k++) a[k] = __ldcs(A.val + (int64_t)k * A.ld + i);
+#pragma unroll
+            for (int k = 0; k < K; k++) xv[k] = __ldg(x + i + A.offs.o[k]);
+#pragma unroll
+            for (int k = 0; k < K; k++) s = __dadd_rn(s, __dmul_rn(a[k], xv[k]));
+        } else if (FMT == 2) {  // ELL
+            for (int k = 0; k < A.K; k++) {
+                int c = __ldcs(A.col + (int64_t)k * A.ld + i);
+                s = __dadd_rn(s, __dmul_rn(__ldcs(A.val + (int64_t)k * A.ld + i), __ldg(x + c)));
+            }
+        } else {  // CSR
+            for (int64_t k = A.rowptr[i]; k < A.rowptr[i + 1]; k++) s = __dadd_rn(s, __dmul_rn(A.val[k], __ldg(x + A.col[k])));
+        }
+        double ri = __dsub_rn(b[i], s);
+        r[i] = (Tin)ri;
+        sq = ri * ri;
+    }
+    finish_norm(sq, partial, ticket, norm2);
+}
+
+__global__ void k_norm2(const double *__restrict__ v, int n, double *partial, unsigned *ticket, double *norm2);
+
+template <typename Tin>
+__global__ void __launch_bounds__(256) k_update(double *__restrict__ x, const Tin *__restrict__ c, int n)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) x[i] = __dadd_rn(x[i], (double)c[i]);
+}
+
+}  // namespace mgk

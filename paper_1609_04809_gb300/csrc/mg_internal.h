@@ -1,0 +1,83 @@
+// mg_internal.h -- data structures shared by the library's translation units (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+#include "mg.h"
+
+namespace mgi {
+
+struct Error {
+    mg_status st;
+    std::string msg;
+    Error(mg_status s, std::string m) : st(s), msg(std::move(m)) {}
+};
+
+void set_error(const std::string &m);
+
+// One device allocation per hierarchy, carved into 256-byte aligned pieces. A first
+// pass only reserves (counts) so that the total is known before the allocation.
+struct Slab {
+    char *base = nullptr;
+    size_t size = 0, used = 0;
+    void reserve(size_t bytes);
+    void *take(size_t bytes);
+};
+
+// A level operator in one device format (values of elem_size bytes).
+struct DevMat {
+    int fmt = 0;  // MG_STORAGE_*
+    int64_t n = 0, ld = 0, nnz = 0;
+    int K = 0;
+    int elem_size = 8;
+    mgk::DiaOffs offs{};
+    void *val = nullptr;
+    int32_t *col = nullptr;
+    int64_t *rowptr = nullptr;
+};
+
+struct LevelD {
+    int N = 0;        // cells per axis
+    int64_t n = 0;    // DOFs
+    int64_t nnz = 0;  // structural nonzeros of A
+    int fmt = 0;
+    int64_t pad = 0;  // zero elements on each side of the x buffers (DIA gathers)
+    int galerkin = 0;
+    DevMat A;         // inner precision
+    void *x[2] = {nullptr, nullptr};
+    void *b = nullptr, *t = nullptr, *d = nullptr;
+    bool structured = false;  // Q1 transfers computed from the grid
+    DevMat P, R;              // explicit transfers to level-1 (CSR)
+    double omega = 0.8, lambda = 0.0, cheb_c0 = 0.0;
+    std::vector<double> cheb_c1, cheb_c2;
+};
+
+struct Prof {
+    struct Rec {
+        int kclass, level;
+        double bytes;
+        cudaEvent_t e0, e1;
+    };
+    double ms_total[MG_K_COUNT * MG_MAX_LEVELS] = {};
+    int64_t launches[MG_K_COUNT * MG_MAX_LEVELS] = {};
+    double bytes_total[MG_K_COUNT * MG_MAX_LEVELS] = {};
+    void begin(cudaStream_t s, int kclass, int level, double bytes, std::vector<Rec> *sink, bool capturing);
+    void end(cudaStream_t s, std::vector<Rec> *sink, bool capturing);
+    void collect(std::vector<Rec> &recs);
+    void release(std::vector<Rec> &recs);
+    void reset()
+    {
+        for (int k = 0; k < MG_K_COUNT * MG_MAX_LEVELS; k++) {
+            ms_total[k] = 0.0;
+            launches[k] = 0;
+            bytes_total[k] = 0.0;
+        }
+    }
+};
+
+}  // namespace mgi

@@ -1,0 +1,1269 @@
+// solver.cu -- device hierarchy, V-cycle schedule, CUDA graphs and the C ABI of libmg.so.
+//
+// One defect-correction iteration is two CUDA graphs replayed on a private stream:
+//   G_r: FP64 outer residual r = b - A64 x64 (written in the inner precision into the
+//        finest level's right-hand side) and ||r||^2;
+//   G_v: one V-cycle on that right-hand side (Sec. 5.3: pre-smoothing, restriction of
+//        the residual level by level, exact coarsest solve, prolongation with
+//        correction and post-smoothing on the way up), then x64 += c.
+// The host reads ||r||^2 after G_r (one 8-byte copy) for the stopping test.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "host_setup.h"
+#include "kernels.cuh"
+#include "mg.h"
+#include "mg_internal.h"
+
+using namespace mgk;
+
+// ------------------------------------------------------------------------------------
+// Errors
+// ------------------------------------------------------------------------------------
+static thread_local std::string g_err;
+
+namespace mgi {
+void set_error(const std::string &m) { g_err = m; }
+}  // namespace mgi
+
+extern "C" const char *mg_last_error(void) { return g_err.c_str(); }
+
+#define CK(call)                                                                                    \
+    do {                                                                                            \
+        cudaError_t e_ = (call);                                                                    \
+        if (e_ != cudaSuccess) throw mgi::Error(MG_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+#define CKL()                                                                                       \
+    do {                                                                                            \
+        cudaError_t e_ = cudaGetLastError();                                                        \
+        if (e_ != cudaSuccess) throw mgi::Error(MG_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e_)); \
+    } while (0)
+
+// ------------------------------------------------------------------------------------
+// Non-template kernels
+// ------------------------------------------------------------------------------------
+namespace mgk {
+__global__ void k_lu_factor(double *a, int n, int *piv, int *info)
+{
+    __shared__ int p_sh;
+    int t = threadIdx.x;
+    for (int k = 0; k < n; k++) {
+        if (t == 0) {
+            int p = k;
+            double best = fabs(a[(int64_t)k * n + k]);
+            for (int i = k + 1; i < n; i++) {
+                double v = fabs(a[(int64_t)i * n + k]);
+                if (v > best) {
+                    best = v;
+                    p = i;
+                }
+            }
+            piv[k] = p;
+            p_sh = p;
+            if (best == 0.0) *info = 1;
+        }
+        __syncthreads();
+        int p = p_sh;
+        if (p != k)
+            for (int j = t; j < n; j += blockDim.x) {
+                double tmp = a[(int64_t)k * n + j];
+                a[(int64_t)k * n + j] = a[(int64_t)p * n + j];
+                a[(int64_t)p * n + j] = tmp;
+            }
+        __syncthreads();
+        for (int i = k + 1 + t; i < n; i += blockDim.x) {
+            double l = __ddiv_rn(a[(int64_t)i * n + k], a[(int64_t)k * n + k]);
+            a[(int64_t)i * n + k] = l;
+            for (int j = k + 1; j < n; j++)
+                a[(int64_t)i * n + j] = __dsub_rn(a[(int64_t)i * n + j], __dmul_rn(l, a[(int64_t)k * n + j]));
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(256) k_norm2(const double *__restrict__ v, int n, double *partial, unsigned *ticket,
+                                               double *norm2)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double sq = 0.0;
+    if (i < n) sq = v[i] * v[i];
+    finish_norm(sq, partial, ticket, norm2);
+}
+}  // namespace mgk
+
+// ------------------------------------------------------------------------------------
+// Helpers
+// ------------------------------------------------------------------------------------
+using mgi::DevMat;
+using mgi::Error;
+using mgi::LevelD;
+
+static inline int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+static inline unsigned grid_for(int64_t n) { return (unsigned)((n + 255) / 256); }
+
+void mgi::Slab::reserve(size_t bytes)
+{
+    used = round_up((int64_t)used, 256) + bytes;
+}
+
+void *mgi::Slab::take(size_t bytes)
+{
+    size_t off = (size_t)round_up((int64_t)used, 256);
+    if (off + bytes > size) throw Error(MG_ENOMEM, "device slab overflow");
+    used = off + bytes;
+    return base + off;
+}
+
+template <typename T>
+static MatView<T> view(const DevMat &m)
+{
+    MatView<T> v;
+    v.val = (const T *)m.val;
+    v.col = m.col;
+    v.rowptr = m.rowptr;
+    v.ld = m.ld;
+    v.K = m.K;
+    v.offs = m.offs;
+    return v;
+}
+
+// ------------------------------------------------------------------------------------
+// Profiling: CUDA events around launches
+// ------------------------------------------------------------------------------------
+void mgi::Prof::begin(cudaStream_t s, int kclass, int level, double bytes, std::vector<Rec> *sink, bool capturing)
+{
+    Rec r;
+    r.kclass = kclass;
+    r.level = level;
+    r.bytes = bytes;
+    CK(cudaEventCreate(&r.e0));
+    CK(cudaEventCreate(&r.e1));
+    if (capturing)
+        CK(cudaEventRecordWithFlags(r.e0, s, cudaEventRecordExternal));
+    else
+        CK(cudaEventRecord(r.e0, s));
+    sink->push_back(r);
+}
+
+void mgi::Prof::end(cudaStream_t s, std::vector<Rec> *sink, bool capturing)
+{
+    Rec &r = sink->back();
+    if (capturing)
+        CK(cudaEventRecordWithFlags(r.e1, s, cudaEventRecordExternal));
+    else
+        CK(cudaEventRecord(r.e1, s));
+}
+
+void mgi::Prof::collect(std::vector<Rec> &recs)
+{
+    for (auto &r : recs) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, r.e0, r.e1));
+        int k = r.kclass * MG_MAX_LEVELS + r.level;
+        ms_total[k] += ms;
+        launches[k] += 1;
+        bytes_total[k] += r.bytes;
+    }
+}
+
+void mgi::Prof::release(std::vector<Rec> &recs)
+{
+    for (auto &r : recs) {
+        cudaEventDestroy(r.e0);
+        cudaEventDestroy(r.e1);
+    }
+    recs.clear();
+}
+
+// ------------------------------------------------------------------------------------
+// The hierarchy
+// ------------------------------------------------------------------------------------
+struct mg_hierarchy {
+    mg_problem prob{};
+    mg_options opt{};
+    int dim = 0, elem = 0, nlev = 0, Lf = 0;
+    bool mixed = false;
+    int inner_size = 8;  // bytes per inner-precision value
+    mg_device dev{};
+    bool own_alloc = false;
+    cudaStream_t caller = nullptr, s = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    int device = 0;
+    mgi::Slab slab;
+    std::vector<LevelD> lev;
+    DevMat A64;                 // finest FP64 operator for the outer residual
+    double *x64 = nullptr;      // interior pointer of the padded FP64 iterate
+    double *b64 = nullptr;
+    int64_t pad64 = 0;
+    double *lu = nullptr;
+    int *piv = nullptr;
+    int *d_info = nullptr;
+    int n0 = 0;
+    double *partial = nullptr;
+    unsigned *ticket = nullptr;
+    double *norm2 = nullptr;
+    double *h_norm2 = nullptr;  // pinned
+    cudaGraphExec_t g_r = nullptr, g_v = nullptr;
+    bool capturing = false;
+    // profiling
+    bool profiling = false;
+    mgi::Prof prof;
+    std::vector<mgi::Prof::Rec> rec_r, rec_v, rec_eager;
+    std::vector<mgi::Prof::Rec> *sink = nullptr;
+    int kernels_per_cycle = 0;
+    int counting = 0;  // counts launches while > 0
+    std::mutex mu;
+
+    ~mg_hierarchy();
+};
+
+static void destroy_graphs(mg_hierarchy *h)
+{
+    if (h->g_r) cudaGraphExecDestroy(h->g_r);
+    if (h->g_v) cudaGraphExecDestroy(h->g_v);
+    h->g_r = h->g_v = nullptr;
+    h->prof.release(h->rec_r);
+    h->prof.release(h->rec_v);
+}
+
+mg_hierarchy::~mg_hierarchy()
+{
+    destroy_graphs(this);
+    prof.release(rec_eager);
+    if (s) cudaStreamSynchronize(s);
+    if (slab.base) {
+        if (own_alloc)
+            cudaFree(slab.base);
+        else if (dev.free)
+            dev.free(slab.base, slab.size, dev.ctx);
+    }
+    if (h_norm2) cudaFreeHost(h_norm2);
+    if (ev_in) cudaEventDestroy(ev_in);
+    if (ev_out) cudaEventDestroy(ev_out);
+    if (s) cudaStreamDestroy(s);
+}
+
+// launch bookkeeping: profiling events and launch counting
+struct LaunchScope {
+    mg_hierarchy *h;
+    cudaStream_t s;
+    LaunchScope(mg_hierarchy *h_, cudaStream_t s_, int kclass, int level, double bytes) : h(h_), s(s_)
+    {
+        if (h->counting) h->kernels_per_cycle++;
+        if (h->profiling) h->prof.begin(s, kclass, level, bytes, h->sink, h->capturing);
+    }
+    ~LaunchScope() noexcept(false)
+    {
+        if (h->profiling) h->prof.end(s, h->sink, h->capturing);
+    }
+};
+
+static double mat_bytes(const DevMat &m, int sv)
+{
+    switch (m.fmt) {
+    case MG_STORAGE_DIA: return (double)m.K * (double)m.n * sv;
+    case MG_STORAGE_ELL: return (double)m.K * (double)m.n * (sv + 4);
+    default: return (double)m.nnz * (sv + 4) + 8.0 * (double)(m.n + 1);
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// Kernel dispatch
+// ------------------------------------------------------------------------------------
+template <typename T, int MODE>
+static void sweep_fmt(const DevMat &A, int n, const T *x, const T *b, T *out, T *d, T c1, T c2, cudaStream_t s)
+{
+    MatView<T> v = view<T>(A);
+    unsigned g = grid_for(n);
+    if (A.fmt == MG_STORAGE_DIA) {
+        if (A.K == 27)
+            k_dia_sweep<T, 27, MODE><<<g, 256, 0, s>>>(v, n, x, b, out, d, c1, c2);
+        else
+            k_dia_sweep<T, 9, MODE><<<g, 256, 0, s>>>(v, n, x, b, out, d, c1, c2);
+    } else if (A.fmt == MG_STORAGE_ELL) {
+        k_ell_sweep<T, MODE><<<g, 256, 0, s>>>(v, n, x, b, out, d, c1, c2);
+    } else {
+        k_csr_sweep<T, MODE><<<g, 256, 0, s>>>(v, n, x, b, out, d, c1, c2);
+    }
+    CKL();
+}
+
+template <typename T>
+static void sweep(mg_hierarchy *h, int l, int mode, const T *x, const T *b, T *out, T *d, double c1, double c2,
+                  cudaStream_t s)
+{
+    LevelD &L = h->lev[l];
+    int sv = sizeof(T);
+    double n = (double)L.n;
+    double bytes;
+    int kclass;
+    bool zero = mode == SW_JACOBI_Z || mode == SW_CHEBF_Z;
+    if (zero) {
+        kclass = MG_K_SMOOTH0;
+        double diag = L.A.fmt == MG_STORAGE_DIA ? n * sv : mat_bytes(L.A, sv);
+        bytes = diag + 2 * n * sv + (mode == SW_CHEBF_Z ? n * sv : 0);
+    } else {
+        kclass = mode == SW_RESID ? MG_K_RESID : MG_K_SMOOTH;
+        bytes = mat_bytes(L.A, sv) + 3 * n * sv;
+        if (mode == SW_CHEBF) bytes += n * sv;
+        if (mode == SW_CHEB) bytes += 2 * n * sv;
+    }
+    LaunchScope ls(h, s, kclass, l, bytes);
+    int nn = (int)L.n;
+    T a = (T)c1, bb = (T)c2;
+    switch (mode) {
+    case SW_RESID: sweep_fmt<T, SW_RESID>(L.A, nn, x, b, out, d, a, bb, s); break;
+    case SW_JACOBI: sweep_fmt<T, SW_JACOBI>(L.A, nn, x, b, out, d, a, bb, s); break;
+    case SW_CHEBF: sweep_fmt<T, SW_CHEBF>(L.A, nn, x, b, out, d, a, bb, s); break;
+    case SW_CHEB: sweep_fmt<T, SW_CHEB>(L.A, nn, x, b, out, d, a, bb, s); break;
+    case SW_JACOBI_Z: sweep_fmt<T, SW_JACOBI_Z>(L.A, nn, x, b, out, d, a, bb, s); break;
+    default: sweep_fmt<T, SW_CHEBF_Z>(L.A, nn, x, b, out, d, a, bb, s); break;
+    }
+}
+
+// one smoother application on level l; c: buffer holding x (-1: x = 0); returns new buffer
+template <typename T>
+static int smooth(mg_hierarchy *h, int l, int c, cudaStream_t s)
+{
+    LevelD &L = h->lev[l];
+    T *b = (T *)L.b, *d = (T *)L.d;
+    if (h->opt.smoother == MG_JACOBI) {
+        if (c < 0) {
+            sweep<T>(h, l, SW_JACOBI_Z, nullptr, b, (T *)L.x[0], d, L.omega, 0.0, s);
+            return 0;
+        }
+        sweep<T>(h, l, SW_JACOBI, (T *)L.x[c], b, (T *)L.x[1 - c], d, L.omega, 0.0, s);
+        return 1 - c;
+    }
+    if (c < 0) {
+        sweep<T>(h, l, SW_CHEBF_Z, nullptr, b, (T *)L.x[0], d, L.cheb_c0, 0.0, s);
+        c = 0;
+    } else {
+        sweep<T>(h, l, SW_CHEBF, (T *)L.x[c], b, (T *)L.x[1 - c], d, L.cheb_c0, 0.0, s);
+        c = 1 - c;
+    }
+    for (int j = 1; j < h->opt.cheb_degree; j++) {
+        sweep<T>(h, l, SW_CHEB, (T *)L.x[c], b, (T *)L.x[1 - c], d, L.cheb_c1[j], L.cheb_c2[j], s);
+        c = 1 - c;
+    }
+    return c;
+}
+
+template <typename T>
+static void restrict_to(mg_hierarchy *h, int l, const T *r, cudaStream_t s)
+{
+    LevelD &F = h->lev[l], &C = h->lev[l - 1];
+    int sv = sizeof(T);
+    double bytes = (double)F.n * sv + (double)C.n * sv;
+    if (!F.structured) bytes += mat_bytes(F.R, sv);
+    LaunchScope ls(h, s, MG_K_RESTRICT, l, bytes);
+    if (F.structured) {
+        if (h->dim == 3)
+            k_restrict_q1<T, 3><<<grid_for(C.n), 256, 0, s>>>(r, (T *)C.b, C.N);
+        else
+            k_restrict_q1<T, 2><<<grid_for(C.n), 256, 0, s>>>(r, (T *)C.b, C.N);
+    } else {
+        k_csr_apply<T, false><<<grid_for(C.n), 256, 0, s>>>(F.R.rowptr, F.R.col, (const T *)F.R.val, (int)C.n, r,
+                                                             (T *)C.b);
+    }
+    CKL();
+}
+
+template <typename T>
+static void prolong_add(mg_hierarchy *h, int l, const T *xc, T *xf, cudaStream_t s)
+{
+    LevelD &F = h->lev[l], &C = h->lev[l - 1];
+    int sv = sizeof(T);
+    double bytes = 2.0 * F.n * sv + (double)C.n * sv;
+    if (!F.structured) bytes += mat_bytes(F.P, sv);
+    LaunchScope ls(h, s, MG_K_PROLONG, l, bytes);
+    if (F.structured) {
+        if (h->dim == 3)
+            k_prolong_q1<T, 3><<<grid_for(F.n), 256, 0, s>>>(xc, xf, C.N);
+        else
+            k_prolong_q1<T, 2><<<grid_for(F.n), 256, 0, s>>>(xc, xf, C.N);
+    } else {
+        k_csr_apply<T, true><<<grid_for(F.n), 256, 0, s>>>(F.P.rowptr, F.P.col, (const T *)F.P.val, (int)F.n, xc, xf);
+    }
+    CKL();
+}
+
+// V-cycle on the finest level's right-hand side (the defect); returns the buffer of the
+// finest level holding the correction
+template <typename T>
+static int enqueue_vcycle(mg_hierarchy *h, cudaStream_t s)
+{
+    int Lf = h->Lf;
+    std::vector<int> cur((size_t)h->nlev, -1);
+    for (int l = Lf; l >= 1; l--) {  // pre-smoothing and restriction of the residual
+        LevelD &L = h->lev[l];
+        int c = -1;
+        for (int a = 0; a < h->opt.nu_pre; a++) c = smooth<T>(h, l, c, s);
+        const T *r;
+        if (c < 0) {
+            r = (const T *)L.b;  // b - A 0 = b
+        } else {
+            sweep<T>(h, l, SW_RESID, (T *)L.x[c], (T *)L.b, (T *)L.t, nullptr, 0.0, 0.0, s);
+            r = (const T *)L.t;
+        }
+        restrict_to<T>(h, l, r, s);
+        cur[l] = c;
+    }
+    {  // exact solve on the coarsest level
+        LevelD &C = h->lev[0];
+        LaunchScope ls(h, s, MG_K_COARSE, 0, (double)h->n0 * h->n0 * 8 + 2.0 * h->n0 * sizeof(T));
+        int thr = (int)round_up(h->n0, 32);
+        k_coarse_solve<T><<<1, thr, (size_t)h->n0 * sizeof(double), s>>>(h->lu, h->piv, h->n0, (const T *)C.b,
+                                                                           (T *)C.x[0]);
+        CKL();
+        cur[0] = 0;
+    }
+    for (int l = 1; l <= Lf; l++) {  // prolongation, correction and post-smoothing
+        LevelD &L = h->lev[l];
+        if (cur[l] < 0) {
+            CK(cudaMemsetAsync(L.x[0], 0, (size_t)L.n * sizeof(T), s));
+            cur[l] = 0;
+        }
+        prolong_add<T>(h, l, (const T *)h->lev[l - 1].x[cur[l - 1]], (T *)L.x[cur[l]], s);
+        for (int a = 0; a < h->opt.nu_post; a++) cur[l] = smooth<T>(h, l, cur[l], s);
+    }
+    return cur[Lf];
+}
+
+template <typename T>
+static void enqueue_outer(mg_hierarchy *h, cudaStream_t s)
+{
+    LevelD &F = h->lev[h->Lf];
+    const DevMat &A = h->A64;
+    int n = (int)F.n;
+    double bytes = mat_bytes(A, 8) + 16.0 * n + (double)n * sizeof(T);
+    LaunchScope ls(h, s, MG_K_OUTER, h->Lf, bytes);
+    MatView<double> v = view<double>(A);
+    unsigned g = grid_for(n);
+    T *r = (T *)F.b;
+    if (A.fmt == MG_STORAGE_DIA) {
+        if (A.K == 27)
+            k_outer_resid<T, 3, 27><<<g, 256, 0, s>>>(v, n, h->x64, h->b64, r, h->partial, h->ticket, h->norm2);
+        else
+            k_outer_resid<T, 3, 9><<<g, 256, 0, s>>>(v, n, h->x64, h->b64, r, h->partial, h->ticket, h->norm2);
+    } else if (A.fmt == MG_STORAGE_ELL) {
+        k_outer_resid<T, 2, 1><<<g, 256, 0, s>>>(v, n, h->x64, h->b64, r, h->partial, h->ticket, h->norm2);
+    } else {
+        k_outer_resid<T, 1, 1><<<g, 256, 0, s>>>(v, n, h->x64, h->b64, r, h->partial, h->ticket, h->norm2);
+    }
+    CKL();
+}
+
+template <typename T>
+static void enqueue_update(mg_hierarchy *h, int cur, cudaStream_t s)
+{
+    LevelD &F = h->lev[h->Lf];
+    int n = (int)F.n;
+    LaunchScope ls(h, s, MG_K_UPDATE, h->Lf, 16.0 * n + (double)n * sizeof(T));
+    k_update<T><<<grid_for(n), 256, 0, s>>>(h->x64, (const T *)F.x[cur], n);
+    CKL();
+}
+
+static void enqueue_r(mg_hierarchy *h, cudaStream_t s)
+{
+    if (h->mixed)
+        enqueue_outer<float>(h, s);
+    else
+        enqueue_outer<double>(h, s);
+}
+
+static void enqueue_v(mg_hierarchy *h, cudaStream_t s)
+{
+    if (h->mixed) {
+        int c = enqueue_vcycle<float>(h, s);
+        enqueue_update<float>(h, c, s);
+    } else {
+        int c = enqueue_vcycle<double>(h, s);
+        enqueue_update<double>(h, c, s);
+    }
+}
+
+static cudaGraphExec_t capture(mg_hierarchy *h, void (*fn)(mg_hierarchy *, cudaStream_t), std::vector<mgi::Prof::Rec> *sink)
+{
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    h->sink = sink;
+    h->capturing = true;
+    CK(cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal));
+    try {
+        fn(h, h->s);
+    } catch (...) {
+        cudaStreamEndCapture(h->s, &g);
+        if (g) cudaGraphDestroy(g);
+        h->capturing = false;
+        throw;
+    }
+    CK(cudaStreamEndCapture(h->s, &g));
+    h->capturing = false;
+    cudaError_t e = cudaGraphInstantiate(&ge, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) throw Error(MG_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+    return ge;
+}
+
+static void ensure_graphs(mg_hierarchy *h)
+{
+    if (!h->opt.use_graph || (h->g_r && h->g_v)) return;
+    destroy_graphs(h);
+    h->g_r = capture(h, enqueue_r, &h->rec_r);
+    h->g_v = capture(h, enqueue_v, &h->rec_v);
+}
+
+static void run_r(mg_hierarchy *h)
+{
+    if (h->opt.use_graph) {
+        CK(cudaGraphLaunch(h->g_r, h->s));
+    } else {
+        h->sink = &h->rec_eager;
+        enqueue_r(h, h->s);
+    }
+}
+
+static void run_v(mg_hierarchy *h)
+{
+    if (h->opt.use_graph) {
+        CK(cudaGraphLaunch(h->g_v, h->s));
+    } else {
+        h->sink = &h->rec_eager;
+        enqueue_v(h, h->s);
+    }
+}
+
+// after a synchronisation of h->s: fold the finished launches into the profile
+static void prof_collect(mg_hierarchy *h, bool r_ran, bool v_ran)
+{
+    if (!h->profiling) return;
+    if (h->opt.use_graph) {
+        if (r_ran) h->prof.collect(h->rec_r);
+        if (v_ran) h->prof.collect(h->rec_v);
+    } else {
+        h->prof.collect(h->rec_eager);
+        h->prof.release(h->rec_eager);
+    }
+}
+
+static double read_norm2(mg_hierarchy *h)
+{
+    CK(cudaMemcpyAsync(h->h_norm2, h->norm2, sizeof(double), cudaMemcpyDeviceToHost, h->s));
+    CK(cudaStreamSynchronize(h->s));
+    return *h->h_norm2;
+}
+
+static double norm_b(mg_hierarchy *h)
+{
+    int n = (int)h->lev[h->Lf].n;
+    k_norm2<<<grid_for(n), 256, 0, h->s>>>(h->b64, n, h->partial, h->ticket, h->norm2);
+    CKL();
+    return std::sqrt(read_norm2(h));
+}
+
+// ------------------------------------------------------------------------------------
+// Setup
+// ------------------------------------------------------------------------------------
+extern "C" void mg_options_default(mg_options *o)
+{
+    std::memset(o, 0, sizeof(*o));
+    o->smoother = MG_JACOBI;
+    o->omega = 0.8;
+    o->cheb_degree = 2;
+    o->nu_pre = 2;
+    o->nu_post = 2;
+    o->cheb_hi = 1.1;
+    o->cheb_ratio = 4.0;
+    o->power_iters = 20;
+    o->power_seed = 1609;
+    o->precision = MG_FP64;
+    o->storage = MG_STORAGE_AUTO;
+    o->max_iters = 100;
+    o->use_graph = 1;
+}
+
+extern "C" int64_t mg_ndofs(int dim, int element, int n_cells)
+{
+    if (n_cells < 1 || !((element == MG_Q1 && (dim == 2 || dim == 3)) || (element == MG_RQ1 && dim == 3))) return -1;
+    return mgh::ndofs(dim, element, n_cells);
+}
+
+static void validate_problem(const mg_problem *p)
+{
+    if (!p) throw Error(MG_EINVAL, "problem is NULL");
+    if (mg_ndofs(p->dim, p->element, p->n_cells) < 0) throw Error(MG_EINVAL, "invalid dim/element/n_cells");
+    if (p->n_levels < 1 || p->n_levels > MG_MAX_LEVELS) throw Error(MG_EINVAL, "n_levels out of range");
+    int Nc = p->n_cells >> (p->n_levels - 1);
+    if (Nc < 2 || (Nc << (p->n_levels - 1)) != p->n_cells)
+        throw Error(MG_EINVAL, "n_cells must be the coarsest size (>= 2) times 2^(n_levels-1)");
+    int64_t n = mgh::ndofs(p->dim, p->element, p->n_cells);
+    if (n > (int64_t)INT32_MAX / 32) throw Error(MG_EINVAL, "problem too large for 32-bit row indices");
+}
+
+extern "C" mg_status mg_load_vector(const mg_problem *p, const mg_rhs *f, double *b_host)
+{
+    try {
+        validate_problem(p);
+        if (!f || !b_host) throw Error(MG_EINVAL, "rhs or output is NULL");
+        if (f->n_modes < 0 || (f->n_modes > 0 && (!f->amp || !f->freq))) throw Error(MG_EINVAL, "bad rhs modes");
+        mgh::load_vector(p->dim, p->element, p->n_cells, f, b_host);
+        return MG_OK;
+    } catch (const Error &e) {
+        g_err = e.msg;
+        return e.st;
+    } catch (const std::bad_alloc &) {
+        g_err = "host allocation failed";
+        return MG_ENOMEM;
+    }
+}
+
+// device format of a level operator
+static void plan_matrix(DevMat &m, const mgh::Csr &A, int fmt, int dim, int N, int sv, mgi::Slab &slab, bool take)
+{
+    m.fmt = fmt;
+    m.n = A.nrows;
+    m.nnz = A.nnz();
+    m.ld = round_up(std::max<int64_t>(m.n, 1), 64);
+    m.elem_size = sv;
+    if (fmt == MG_STORAGE_DIA) {
+        m.K = dim == 3 ? 27 : 9;
+        int64_t n1 = N - 1;
+        int k = 0;
+        for (int dz = (dim == 3 ? -1 : 0); dz <= (dim == 3 ? 1 : 0); dz++)
+            for (int dy = -1; dy <= 1; dy++)
+                for (int dx = -1; dx <= 1; dx++) m.offs.o[k++] = (int32_t)(dx + n1 * dy + n1 * n1 * dz);
+        size_t bytes = (size_t)m.K * m.ld * sv;
+        if (take)
+            m.val = slab.take(bytes);
+        else
+            slab.reserve(bytes);
+    } else if (fmt == MG_STORAGE_ELL) {
+        int K = 0;
+        for (int64_t i = 0; i < A.nrows; i++) K = std::max<int>(K, (int)(A.rowptr[i + 1] - A.rowptr[i]));
+        m.K = std::max(K, 1);
+        size_t vb = (size_t)m.K * m.ld * sv, cb = (size_t)m.K * m.ld * 4;
+        if (take) {
+            m.val = slab.take(vb);
+            m.col = (int32_t *)slab.take(cb);
+        } else {
+            slab.reserve(vb);
+            slab.reserve(cb);
+        }
+    } else {
+        m.K = 0;
+        size_t vb = (size_t)std::max<int64_t>(m.nnz, 1) * sv, cb = (size_t)std::max<int64_t>(m.nnz, 1) * 4,
+               rb = (size_t)(m.n + 1) * 8;
+        if (take) {
+            m.val = slab.take(vb);
+            m.col = (int32_t *)slab.take(cb);
+            m.rowptr = (int64_t *)slab.take(rb);
+        } else {
+            slab.reserve(vb);
+            slab.reserve(cb);
+            slab.reserve(rb);
+        }
+    }
+}
+
+template <typename T>
+static void upload_matrix(const DevMat &m, const mgh::Csr &A, const std::vector<T> &vals, int dim, int N,
+                          cudaStream_t s)
+{
+    if (m.fmt == MG_STORAGE_DIA) {
+        std::vector<T> v((size_t)m.K * m.ld, T(0));
+        int k3 = dim == 3 ? 9 : 0;
+#pragma omp parallel for schedule(static)
+        for (int64_t i = 0; i < A.nrows; i++) {
+            int ci[3], cj[3];
+            mgh::q1_coords(dim, N, i, ci);
+            for (int64_t k = A.rowptr[i]; k < A.rowptr[i + 1]; k++) {
+                mgh::q1_coords(dim, N, A.col[k], cj);
+                int slot = (cj[0] - ci[0] + 1) + 3 * (cj[1] - ci[1] + 1) + k3 * (cj[2] - ci[2] + 1);
+                v[(size_t)slot * m.ld + i] = vals[k];
+            }
+        }
+        CK(cudaMemcpyAsync(m.val, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+        CK(cudaStreamSynchronize(s));
+    } else if (m.fmt == MG_STORAGE_ELL) {
+        std::vector<T> v((size_t)m.K * m.ld, T(0));
+        std::vector<int32_t> c((size_t)m.K * m.ld, 0);
+#pragma omp parallel for schedule(static)
+        for (int64_t i = 0; i < m.ld; i++) {
+            int64_t len = i < A.nrows ? A.rowptr[i + 1] - A.rowptr[i] : 0;
+            for (int k = 0; k < m.K; k++) {
+                if (k < len) {
+                    c[(size_t)k * m.ld + i] = A.col[A.rowptr[i] + k];
+                    v[(size_t)k * m.ld + i] = vals[A.rowptr[i] + k];
+                } else {
+                    c[(size_t)k * m.ld + i] = (int32_t)std::min<int64_t>(i, std::max<int64_t>(A.nrows - 1, 0));
+                }
+            }
+        }
+        CK(cudaMemcpyAsync(m.val, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(m.col, c.data(), c.size() * 4, cudaMemcpyHostToDevice, s));
+        CK(cudaStreamSynchronize(s));
+    } else {
+        CK(cudaMemcpyAsync(m.val, vals.data(), vals.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(m.col, A.col.data(), A.col.size() * 4, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(m.rowptr, A.rowptr.data(), A.rowptr.size() * 8, cudaMemcpyHostToDevice, s));
+        CK(cudaStreamSynchronize(s));
+    }
+}
+
+static std::vector<float> to_f32(const std::vector<double> &v)
+{
+    std::vector<float> o(v.size());
+    for (size_t i = 0; i < v.size(); i++) o[i] = (float)v[i];
+    return o;
+}
+
+// Chebyshev coefficients of level l (the same recurrence as the smoother's definition)
+static void cheb_coeffs(LevelD &L, const mg_options &o)
+{
+    double hi = o.cheb_hi * L.lambda;
+    double lo = hi / o.cheb_ratio;
+    double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo);
+    double sigma = theta / delta;
+    double rho0 = 1.0 / sigma;
+    L.cheb_c0 = 1.0 / theta;
+    L.cheb_c1.assign((size_t)std::max(o.cheb_degree, 1), 0.0);
+    L.cheb_c2.assign((size_t)std::max(o.cheb_degree, 1), 0.0);
+    for (int j = 1; j < o.cheb_degree; j++) {
+        double rho1 = 1.0 / (2.0 * sigma - rho0);
+        L.cheb_c1[j] = rho1 * rho0;
+        L.cheb_c2[j] = (2.0 * rho1) / delta;
+        rho0 = rho1;
+    }
+}
+
+static int pick_storage(const mg_options &o, int elem)
+{
+    if (o.storage == MG_STORAGE_DIA && elem != MG_Q1) throw Error(MG_EINVAL, "DIA storage needs Q1 (fixed stencil offsets)");
+    if (o.storage != MG_STORAGE_AUTO) return o.storage;
+    return elem == MG_Q1 ? MG_STORAGE_DIA : MG_STORAGE_ELL;
+}
+
+static void build(mg_hierarchy *h, const mg_problem *p, const mg_options *o, const mg_device *dev)
+{
+    validate_problem(p);
+    if (o->smoother != MG_JACOBI && o->smoother != MG_CHEBYSHEV) throw Error(MG_EINVAL, "bad smoother");
+    if (o->smoother == MG_CHEBYSHEV && (o->cheb_degree < 1 || !(o->cheb_ratio > 1.0) || !(o->cheb_hi > 0.0) || o->power_iters < 1))
+        throw Error(MG_EINVAL, "bad Chebyshev parameters");
+    if (o->nu_pre < 0 || o->nu_post < 0 || o->max_iters < 0) throw Error(MG_EINVAL, "negative counts");
+    if (o->precision != MG_FP64 && o->precision != MG_MIXED) throw Error(MG_EINVAL, "bad precision");
+    if (o->storage < MG_STORAGE_AUTO || o->storage > MG_STORAGE_DIA) throw Error(MG_EINVAL, "bad storage");
+    h->prob = *p;
+    h->prob.k_cell = nullptr;
+    h->opt = *o;
+    h->dim = p->dim;
+    h->elem = p->element;
+    h->nlev = p->n_levels;
+    h->Lf = p->n_levels - 1;
+    h->mixed = o->precision == MG_MIXED;
+    h->inner_size = h->mixed ? 4 : 8;
+    if (dev) h->dev = *dev;
+    h->own_alloc = !h->dev.alloc;
+    CK(cudaGetDevice(&h->device));
+    h->caller = (cudaStream_t)h->dev.stream;
+    CK(cudaStreamCreateWithFlags(&h->s, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming));
+    CK(cudaMallocHost(&h->h_norm2, sizeof(double)));
+
+    int dim = h->dim, elem = h->elem, nlev = h->nlev, Lf = h->Lf;
+    h->lev.resize((size_t)nlev);
+    // ---- host hierarchy, finest to coarsest ----
+    mgh::HostHierarchy HH;
+    mgh::build_hierarchy(dim, elem, p->n_cells, nlev, p->k_cell, 0, HH);
+    std::vector<mgh::Csr> &A = HH.A, &P = HH.P, &R = HH.R;
+    for (int l = Lf; l >= 0; l--) {
+        LevelD &L = h->lev[l];
+        L.N = HH.N[l];
+        L.n = A[l].nrows;
+        L.galerkin = HH.galerkin[l];
+        L.nnz = A[l].nnz();
+    }
+    // ---- smoother parameters ----
+    for (int l = 0; l <= Lf; l++) {
+        LevelD &L = h->lev[l];
+        L.omega = o->omega;
+        if (l >= 1 && o->smoother == MG_CHEBYSHEV) {
+            L.lambda = mgh::level_lambda(A[l], o->power_iters, o->power_seed);
+            cheb_coeffs(L, *o);
+        }
+    }
+    h->n0 = (int)h->lev[0].n;
+    if (h->n0 > 1024) throw Error(MG_EINVAL, "coarsest level has more than 1024 DOFs; add levels");
+
+    // ---- device memory plan (pass 0: count, pass 1: assign) ----
+    int fmt = pick_storage(*o, elem);
+    int sv = h->inner_size;
+    for (int pass = 0; pass < 2; pass++) {
+        bool take = pass == 1;
+        mgi::Slab &S = h->slab;
+        if (take) {
+            size_t bytes = S.used + 256;
+            S.used = 0;
+            S.size = bytes;
+            if (h->own_alloc) {
+                cudaError_t e = cudaMalloc(&S.base, bytes);
+                if (e != cudaSuccess) {
+                    S.base = nullptr;
+                    cudaGetLastError();
+                    throw Error(MG_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+                }
+            } else {
+                S.base = (char *)h->dev.alloc(bytes, h->dev.ctx);
+                if (!S.base) throw Error(MG_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+            }
+        }
+        auto vec = [&](size_t bytes) -> void * {
+            if (take) return S.take(bytes);
+            S.reserve(bytes);
+            return nullptr;
+        };
+        for (int l = 0; l <= Lf; l++) {
+            LevelD &L = h->lev[l];
+            int lf = (l == 0 && fmt == MG_STORAGE_DIA) ? MG_STORAGE_DIA : fmt;
+            L.fmt = lf;
+            plan_matrix(L.A, A[l], lf, dim, L.N, sv, S, take);
+            int64_t n1 = L.N - 1;
+            L.pad = lf == MG_STORAGE_DIA ? round_up(dim == 3 ? n1 * n1 + n1 + 1 : n1 + 1, 64) : 0;
+            int64_t ld = L.A.ld;
+            for (int c = 0; c < 2; c++) {
+                char *base = (char *)vec((size_t)(ld + 2 * L.pad) * sv);
+                L.x[c] = take ? base + (size_t)L.pad * sv : nullptr;
+            }
+            L.b = vec((size_t)ld * sv);
+            L.t = vec((size_t)ld * sv);
+            L.d = vec((size_t)ld * sv);
+            if (l >= 1) {
+                L.structured = elem == MG_Q1;
+                if (!L.structured) {
+                    plan_matrix(L.P, P[l], MG_STORAGE_CSR, dim, L.N, sv, S, take);
+                    plan_matrix(L.R, R[l], MG_STORAGE_CSR, dim, L.N, sv, S, take);
+                }
+            }
+        }
+        LevelD &F = h->lev[Lf];
+        if (h->mixed) {
+            plan_matrix(h->A64, A[Lf], F.fmt, dim, F.N, 8, S, take);
+        } else if (take) {
+            h->A64 = F.A;
+        }
+        h->pad64 = F.pad;
+        {
+            char *base = (char *)vec((size_t)(F.A.ld + 2 * h->pad64) * 8);
+            h->x64 = take ? (double *)(base + (size_t)h->pad64 * 8) : nullptr;
+        }
+        h->b64 = (double *)vec((size_t)F.A.ld * 8);
+        h->lu = (double *)vec((size_t)h->n0 * h->n0 * 8);
+        h->piv = (int *)vec((size_t)h->n0 * 4);
+        h->d_info = (int *)vec(64);
+        h->partial = (double *)vec((size_t)grid_for(F.A.ld) * 8);
+        h->ticket = (unsigned *)vec(64);
+        h->norm2 = (double *)vec(64);
+    }
+    // ---- upload ----
+    CK(cudaMemsetAsync(h->slab.base, 0, h->slab.size, h->s));
+    for (int l = 0; l <= Lf; l++) {
+        LevelD &L = h->lev[l];
+        if (h->mixed) {
+            std::vector<float> v32;
+            mgh::round_fp32(A[l], v32);
+            upload_matrix<float>(L.A, A[l], v32, dim, L.N, h->s);
+            if (l >= 1 && !L.structured) {
+                upload_matrix<float>(L.P, P[l], to_f32(P[l].val), dim, L.N, h->s);
+                upload_matrix<float>(L.R, R[l], to_f32(R[l].val), dim, L.N, h->s);
+            }
+        } else {
+            upload_matrix<double>(L.A, A[l], A[l].val, dim, L.N, h->s);
+            if (l >= 1 && !L.structured) {
+                upload_matrix<double>(L.P, P[l], P[l].val, dim, L.N, h->s);
+                upload_matrix<double>(L.R, R[l], R[l].val, dim, L.N, h->s);
+            }
+        }
+    }
+    if (h->mixed) upload_matrix<double>(h->A64, A[Lf], A[Lf].val, dim, h->lev[Lf].N, h->s);
+    // ---- coarsest LU on the device ----
+    {
+        std::vector<double> dense((size_t)h->n0 * h->n0, 0.0);
+        for (int i = 0; i < h->n0; i++)
+            for (int64_t k = A[0].rowptr[i]; k < A[0].rowptr[i + 1]; k++) dense[(size_t)i * h->n0 + A[0].col[k]] = A[0].val[k];
+        CK(cudaMemcpyAsync(h->lu, dense.data(), dense.size() * 8, cudaMemcpyHostToDevice, h->s));
+        k_lu_factor<<<1, 256, 0, h->s>>>(h->lu, h->n0, h->piv, h->d_info);
+        CKL();
+        int info = 0;
+        CK(cudaMemcpyAsync(&info, h->d_info, 4, cudaMemcpyDeviceToHost, h->s));
+        CK(cudaStreamSynchronize(h->s));
+        if (info) throw Error(MG_EINVAL, "coarsest matrix is singular");
+    }
+    // ---- launch count of one iteration, graphs ----
+    h->counting = 1;
+    h->kernels_per_cycle = 0;
+    {
+        // count by a dry enqueue on a capture that is discarded
+        cudaGraph_t g = nullptr;
+        h->capturing = true;
+        CK(cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal));
+        enqueue_r(h, h->s);
+        enqueue_v(h, h->s);
+        CK(cudaStreamEndCapture(h->s, &g));
+        h->capturing = false;
+        if (g) cudaGraphDestroy(g);
+    }
+    h->counting = 0;
+    ensure_graphs(h);
+    CK(cudaStreamSynchronize(h->s));
+}
+
+extern "C" mg_status mg_setup(const mg_problem *p, const mg_options *o, const mg_device *dev, mg_hierarchy **out)
+{
+    if (!out) {
+        g_err = "out is NULL";
+        return MG_EINVAL;
+    }
+    *out = nullptr;
+    mg_options def;
+    if (!o) {
+        mg_options_default(&def);
+        o = &def;
+    }
+    std::unique_ptr<mg_hierarchy> h(new (std::nothrow) mg_hierarchy());
+    if (!h) {
+        g_err = "host allocation failed";
+        return MG_ENOMEM;
+    }
+    try {
+        build(h.get(), p, o, dev);
+    } catch (const Error &e) {
+        g_err = e.msg;
+        return e.st;
+    } catch (const std::bad_alloc &) {
+        g_err = "host allocation failed";
+        return MG_ENOMEM;
+    }
+    *out = h.release();
+    return MG_OK;
+}
+
+extern "C" mg_status mg_hierarchy_free(mg_hierarchy *h)
+{
+    delete h;
+    return MG_OK;
+}
+
+extern "C" mg_status mg_get_info(const mg_hierarchy *h, mg_info *info)
+{
+    if (!h || !info) {
+        g_err = "NULL argument";
+        return MG_EINVAL;
+    }
+    std::memset(info, 0, sizeof(*info));
+    info->n_levels = h->nlev;
+    info->precision = h->opt.precision;
+    for (int l = 0; l < h->nlev; l++) {
+        info->n[l] = h->lev[l].n;
+        info->nnz[l] = h->lev[l].nnz;
+        info->storage[l] = h->lev[l].fmt;
+        info->galerkin[l] = h->lev[l].galerkin;
+        info->lambda[l] = h->lev[l].lambda;
+    }
+    info->device_bytes = h->slab.size;
+    info->kernels_per_cycle = h->kernels_per_cycle;
+    return MG_OK;
+}
+
+// ------------------------------------------------------------------------------------
+// Solve
+// ------------------------------------------------------------------------------------
+static void join_in(mg_hierarchy *h)
+{
+    CK(cudaEventRecord(h->ev_in, h->caller));
+    CK(cudaStreamWaitEvent(h->s, h->ev_in, 0));
+}
+
+static void join_out(mg_hierarchy *h)
+{
+    CK(cudaEventRecord(h->ev_out, h->s));
+    CK(cudaStreamWaitEvent(h->caller, h->ev_out, 0));
+    CK(cudaStreamSynchronize(h->s));
+}
+
+static mg_status solve_internal(mg_hierarchy *h, double tol, int *iters, double *hist)
+{
+    ensure_graphs(h);
+    double nb = norm_b(h);
+    int k = 0;
+    mg_status st = MG_ENOCONV;
+    run_r(h);
+    double nr = std::sqrt(read_norm2(h));
+    prof_collect(h, true, false);
+    for (;;) {
+        double rel = nb > 0.0 ? nr / nb : nr;
+        if (hist) hist[k] = rel;
+        if (rel <= tol) {  // a NaN residual runs on to max_iters
+            st = MG_OK;
+            break;
+        }
+        if (k == h->opt.max_iters) break;
+        run_v(h);
+        run_r(h);
+        nr = std::sqrt(read_norm2(h));
+        prof_collect(h, true, true);
+        k++;
+    }
+    if (iters) *iters = k;
+    if (st == MG_ENOCONV) g_err = "max_iters reached before the tolerance";
+    return st;
+}
+
+template <typename F>
+static mg_status guarded(mg_hierarchy *h, F &&fn)
+{
+    if (!h) {
+        g_err = "hierarchy is NULL";
+        return MG_EINVAL;
+    }
+    std::lock_guard<std::mutex> lk(h->mu);
+    int prev = 0;
+    cudaGetDevice(&prev);
+    if (prev != h->device) cudaSetDevice(h->device);
+    mg_status st;
+    try {
+        st = fn();
+    } catch (const Error &e) {
+        g_err = e.msg;
+        st = e.st;
+    } catch (const std::bad_alloc &) {
+        g_err = "host allocation failed";
+        st = MG_ENOMEM;
+    }
+    if (prev != h->device) cudaSetDevice(prev);
+    return st;
+}
+
+extern "C" mg_status mg_solve(mg_hierarchy *h, const double *b_dev, double *x_dev, double rel_tol, int *iters,
+                              double *res_hist)
+{
+    return guarded(h, [&]() -> mg_status {
+        if (!b_dev || !x_dev) throw Error(MG_EINVAL, "b or x is NULL");
+        size_t bytes = (size_t)h->lev[h->Lf].n * 8;
+        join_in(h);
+        CK(cudaMemcpyAsync(h->b64, b_dev, bytes, cudaMemcpyDeviceToDevice, h->s));
+        CK(cudaMemcpyAsync(h->x64, x_dev, bytes, cudaMemcpyDeviceToDevice, h->s));
+        mg_status st = solve_internal(h, rel_tol, iters, res_hist);
+        CK(cudaMemcpyAsync(x_dev, h->x64, bytes, cudaMemcpyDeviceToDevice, h->s));
+        join_out(h);
+        return st;
+    });
+}
+
+extern "C" mg_status mg_solve_host(mg_hierarchy *h, const double *b_host, double *x_host, double rel_tol, int *iters,
+                                   double *res_hist)
+{
+    return guarded(h, [&]() -> mg_status {
+        if (!b_host || !x_host) throw Error(MG_EINVAL, "b or x is NULL");
+        size_t bytes = (size_t)h->lev[h->Lf].n * 8;
+        join_in(h);
+        CK(cudaMemcpyAsync(h->b64, b_host, bytes, cudaMemcpyHostToDevice, h->s));
+        CK(cudaMemcpyAsync(h->x64, x_host, bytes, cudaMemcpyHostToDevice, h->s));
+        mg_status st = solve_internal(h, rel_tol, iters, res_hist);
+        CK(cudaMemcpyAsync(x_host, h->x64, bytes, cudaMemcpyDeviceToHost, h->s));
+        join_out(h);
+        return st;
+    });
+}
+
+extern "C" mg_status mg_cycle(mg_hierarchy *h, const double *b_dev, double *x_dev, int n_cycles, double *rel_res)
+{
+    return guarded(h, [&]() -> mg_status {
+        if (!b_dev || !x_dev || n_cycles < 0) throw Error(MG_EINVAL, "bad arguments");
+        size_t bytes = (size_t)h->lev[h->Lf].n * 8;
+        ensure_graphs(h);
+        join_in(h);
+        CK(cudaMemcpyAsync(h->b64, b_dev, bytes, cudaMemcpyDeviceToDevice, h->s));
+        CK(cudaMemcpyAsync(h->x64, x_dev, bytes, cudaMemcpyDeviceToDevice, h->s));
+        double nb = norm_b(h);
+        for (int c = 0; c < n_cycles; c++) {
+            run_r(h);
+            run_v(h);
+            if (h->profiling) {
+                CK(cudaStreamSynchronize(h->s));
+                prof_collect(h, true, true);
+            }
+        }
+        double nr = 0.0;
+        if (n_cycles > 0) nr = std::sqrt(read_norm2(h));
+        if (rel_res) *rel_res = nb > 0.0 ? nr / nb : nr;
+        CK(cudaMemcpyAsync(x_dev, h->x64, bytes, cudaMemcpyDeviceToDevice, h->s));
+        join_out(h);
+        return MG_OK;
+    });
+}
+
+// ------------------------------------------------------------------------------------
+// Host-only assembly export
+// ------------------------------------------------------------------------------------
+extern "C" mg_status mg_assemble_operator(const mg_problem *p, int level, int which, int64_t *nrows, int64_t *nnz,
+                                          int64_t *rowptr, int32_t *col, double *val)
+{
+    try {
+        validate_problem(p);
+        int Lf = p->n_levels - 1;
+        if (level < 0 || level > Lf || which < 0 || which > 2 || (which > 0 && level < 1))
+            throw Error(MG_EINVAL, "bad level/which");
+        mgh::HostHierarchy HH;
+        mgh::build_hierarchy(p->dim, p->element, p->n_cells, p->n_levels, p->k_cell, which == 0 ? level : level - 1, HH);
+        const mgh::Csr &m = which == 0 ? HH.A[level] : (which == 1 ? HH.P[level] : HH.R[level]);
+        if (nrows) *nrows = m.nrows;
+        if (nnz) *nnz = m.nnz();
+        if (rowptr) {
+            std::memcpy(rowptr, m.rowptr.data(), m.rowptr.size() * 8);
+            if (col) std::memcpy(col, m.col.data(), m.col.size() * 4);
+            if (val) std::memcpy(val, m.val.data(), m.val.size() * 8);
+        }
+        return MG_OK;
+    } catch (const Error &e) {
+        g_err = e.msg;
+        return e.st;
+    } catch (const std::bad_alloc &) {
+        g_err = "host allocation failed";
+        return MG_ENOMEM;
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// Export and profiling
+// ------------------------------------------------------------------------------------
+template <typename T>
+static std::vector<double> download_vals(const DevMat &m, size_t count)
+{
+    std::vector<T> v(count);
+    CK(cudaMemcpy(v.data(), m.val, count * sizeof(T), cudaMemcpyDeviceToHost));
+    return std::vector<double>(v.begin(), v.end());
+}
+
+static void export_dev(const DevMat &m, int dim, int N, int sv, mgh::Csr &out)
+{
+    out.nrows = m.n;
+    out.rowptr.assign((size_t)m.n + 1, 0);
+    out.col.clear();
+    out.val.clear();
+    if (m.fmt == MG_STORAGE_CSR) {
+        out.rowptr.resize((size_t)m.n + 1);
+        CK(cudaMemcpy(out.rowptr.data(), m.rowptr, (m.n + 1) * 8, cudaMemcpyDeviceToHost));
+        out.col.resize((size_t)m.nnz);
+        CK(cudaMemcpy(out.col.data(), m.col, m.nnz * 4, cudaMemcpyDeviceToHost));
+        out.val = sv == 8 ? download_vals<double>(m, (size_t)m.nnz) : download_vals<float>(m, (size_t)m.nnz);
+        return;
+    }
+    size_t cnt = (size_t)m.K * m.ld;
+    std::vector<double> v = sv == 8 ? download_vals<double>(m, cnt) : download_vals<float>(m, cnt);
+    std::vector<int32_t> c;
+    if (m.fmt == MG_STORAGE_ELL) {
+        c.resize(cnt);
+        CK(cudaMemcpy(c.data(), m.col, cnt * 4, cudaMemcpyDeviceToHost));
+    }
+    for (int64_t i = 0; i < m.n; i++) {
+        int ci[3] = {0, 0, 0};
+        if (m.fmt == MG_STORAGE_DIA) mgh::q1_coords(dim, N, i, ci);
+        int32_t prev = -1;
+        for (int k = 0; k < m.K; k++) {
+            int32_t j;
+            if (m.fmt == MG_STORAGE_DIA) {
+                int d[3] = {k % 3 - 1, (k / 3) % 3 - 1, dim == 3 ? k / 9 - 1 : 0};
+                bool inside = true;
+                for (int a = 0; a < dim; a++)
+                    if (ci[a] + d[a] < 1 || ci[a] + d[a] > N - 1) inside = false;
+                if (!inside) continue;
+                j = (int32_t)(i + m.offs.o[k]);
+            } else {
+                j = c[(size_t)k * m.ld + i];
+                if (j <= prev) break;  // padding (column i after larger columns)
+                prev = j;
+            }
+            out.col.push_back(j);
+            out.val.push_back(v[(size_t)k * m.ld + i]);
+        }
+        out.rowptr[i + 1] = (int64_t)out.col.size();
+    }
+}
+
+extern "C" mg_status mg_export_operator(const mg_hierarchy *hc, int level, int which, int precision, int64_t *nrows,
+                                        int64_t *nnz, int64_t *rowptr, int32_t *col, double *val)
+{
+    mg_hierarchy *h = const_cast<mg_hierarchy *>(hc);
+    return guarded(h, [&]() -> mg_status {
+        if (level < 0 || level > h->Lf || which < 0 || which > 2 || (which > 0 && level < 1))
+            throw Error(MG_EINVAL, "bad level/which");
+        mgh::Csr m;
+        const LevelD &L = h->lev[level];
+        if (which == 0) {
+            if (precision == MG_FP64 && h->mixed) {
+                if (level != h->Lf) throw Error(MG_EINVAL, "FP64 copy exists on the finest level only");
+                export_dev(h->A64, h->dim, L.N, 8, m);
+            } else if (precision == MG_MIXED && !h->mixed) {
+                throw Error(MG_EINVAL, "no FP32 copy in an FP64 hierarchy");
+            } else {
+                export_dev(L.A, h->dim, L.N, h->inner_size, m);
+            }
+        } else if (L.structured) {
+            mgh::Csr P;
+            mgh::prolongation(h->dim, h->elem, h->lev[level - 1].N, P);
+            if (which == 1)
+                m = P;
+            else
+                mgh::transpose(P, m);
+        } else {
+            export_dev(which == 1 ? L.P : L.R, h->dim, L.N, h->inner_size, m);
+            if (which == 2) m.nrows = h->lev[level - 1].n;
+        }
+        if (which == 2 && L.structured) m.nrows = h->lev[level - 1].n;
+        if (nrows) *nrows = m.nrows;
+        if (nnz) *nnz = m.nnz();
+        if (rowptr) {
+            std::memcpy(rowptr, m.rowptr.data(), m.rowptr.size() * 8);
+            if (col) std::memcpy(col, m.col.data(), m.col.size() * 4);
+            if (val) std::memcpy(val, m.val.data(), m.val.size() * 8);
+        }
+        return MG_OK;
+    });
+}
+
+extern "C" mg_status mg_profile_enable(mg_hierarchy *h, int enable)
+{
+    return guarded(h, [&]() -> mg_status {
+        CK(cudaStreamSynchronize(h->s));
+        destroy_graphs(h);
+        h->prof.release(h->rec_eager);
+        h->prof.reset();
+        h->profiling = enable != 0;
+        ensure_graphs(h);
+        return MG_OK;
+    });
+}
+
+extern "C" mg_status mg_profile_read(const mg_hierarchy *h, int kclass, int level, double *ms_total, int64_t *launches,
+                                     double *bytes_per_launch)
+{
+    if (!h || kclass < 0 || kclass >= MG_K_COUNT || level < 0 || level >= MG_MAX_LEVELS) {
+        g_err = "bad arguments";
+        return MG_EINVAL;
+    }
+    int k = kclass * MG_MAX_LEVELS + level;
+    if (ms_total) *ms_total = h->prof.ms_total[k];
+    if (launches) *launches = h->prof.launches[k];
+    if (bytes_per_launch) *bytes_per_launch = h->prof.launches[k] ? h->prof.bytes_total[k] / h->prof.launches[k] : 0.0;
+    return MG_OK;
+}
