@@ -18,12 +18,14 @@
  * sum, on x86 and on Arm alike.)
  *
  * Floating-point conventions (the reading of every step, in the order evaluated):
- *   y_i = sum_j a_ij x_j           column-ascending, starting from 0.0
+ *   y_i = sum_j a_ij x_j           column-ascending, starting from 0.0, each term
+ *                                  added by a fused multiply-add s <- fma(a_ij, x_j, s)
+ *                                  (IEEE 754 fusedMultiplyAdd: one rounding per term)
  *   residual r_i = b_i - y_i
  *   damped Jacobi x_i <- x_i + omega*(dinv_i*r_i),    dinv_i = 1.0/a_ii
  *   Chebyshev step  d_i <- c1*d_i + c2*(dinv_i*r_i),  x_i <- x_i + d_i
  *   restriction b_c = R r with R = P^T stored by rows (fine index ascending)
- *   prolongation x_i <- x_i + t_i,  t_i = sum_J p_iJ c_J   (coarse index ascending)
+ *   prolongation x_i <- x_i + t_i,  t_i = sum_J p_iJ c_J   (coarse index ascending, fused)
  *   coarsest solve: LU with partial pivoting; forward substitution sums column-
  *   ascending, back substitution sums column-descending.
  */
@@ -658,7 +660,7 @@ void orc_spmv(const orc_csr *A, const double *x, double *y)
     for (int64_t i = 0; i < A->nrows; i++) {
         double s = 0.0;
         for (int64_t k = A->rowptr[i]; k < A->rowptr[i + 1]; k++)
-            s = s + A->val[k] * x[A->col[k]];
+            s = fma(A->val[k], x[A->col[k]], s);
         y[i] = s;
     }
 }
@@ -668,7 +670,7 @@ static void residual(const orc_csr *A, const double *b, const double *x, double 
     for (int64_t i = 0; i < A->nrows; i++) {
         double s = 0.0;
         for (int64_t k = A->rowptr[i]; k < A->rowptr[i + 1]; k++)
-            s = s + A->val[k] * x[A->col[k]];
+            s = fma(A->val[k], x[A->col[k]], s);
         r[i] = b[i] - s;
     }
 }
@@ -993,7 +995,7 @@ static void vcycle(orc_hier *H, const orc_opts *o, int l, const double *b, doubl
     for (int64_t i = 0; i < n; i++) {    /* prolongation and correction */
         double t = 0.0;
         for (int64_t k = H->P[l].rowptr[i]; k < H->P[l].rowptr[i + 1]; k++)
-            t = t + H->P[l].val[k] * xc[H->P[l].col[k]];
+            t = fma(H->P[l].val[k], xc[H->P[l].col[k]], t);
         x[i] = x[i] + t;
     }
     for (int s = 0; s < o->nu_post; s++) /* post-smoothing */
