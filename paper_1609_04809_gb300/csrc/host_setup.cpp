@@ -565,7 +565,7 @@ double power_lambda(const Csr &A, const std::vector<double> &dinv, int iters, ui
 #pragma omp parallel for schedule(static)
         for (int64_t i = 0; i < n; i++) {
             double s = 0.0;
-            for (int64_t k = A.rowptr[i]; k < A.rowptr[i + 1]; k++) s = s + A.val[k] * v[A.col[k]];
+            for (int64_t k = A.rowptr[i]; k < A.rowptr[i + 1]; k++) s = std::fma(A.val[k], v[A.col[k]], s);
             w[i] = dinv[i] * s;
         }
         lam = seq_norm(w);

@@ -1,19 +1,23 @@
 // kernels.cuh -- sm_103a device kernels of the multigrid V-cycle (internal).
 //
-// All level operators are memory-bound sparse passes (about 0.17 flop per byte), so
-// the kernels are built for HBM streaming, not tensor cores:
+// Every level operator is a sparse pass of about one multiply-add per 8 bytes, so the
+// kernels are built for streaming, not tensor cores:
 //   * matrices are stored column-major by slot (ELLPACK order, leading dimension ld),
 //     so the 32 rows of a warp read one contiguous 128/256-byte segment per slot;
+//   * DIA keeps only the diagonals that hold a nonzero (21 of the 27 for the 3D Q1
+//     stiffness, whose face-neighbour couplings vanish) and needs no column indices;
 //   * matrix values are read with the streaming cache hint (ld.global.cs): each value
-//     is used once per pass and must not evict the x vector from L2;
+//     is used once per pass and must not evict the gathered vector from L2;
 //   * x is gathered through the read-only path and stays L2-resident across slots;
 //   * one thread per row, sum over the row's slots in ascending column order.
 //
-// FP64 arithmetic uses explicitly rounded products and sums (__dmul_rn, __dadd_rn),
-// never fused multiply-adds: together with the fixed slot order this makes every FP64
-// result the same bit pattern as a sequential CPU evaluation of the same formula.
-// FP32 arithmetic (the inner V-cycle of the mixed-precision solve) uses fused
-// multiply-adds.
+// GB300 issues FP64 at a small fraction of its FP32 rate, so FP64 passes are bounded by
+// the FP64 pipe before HBM: they use one fused multiply-add per stored entry and read a
+// precomputed D^-1 instead of dividing. Every FP64 operation is an explicitly rounded
+// intrinsic (__fma_rn, __dmul_rn, __dadd_rn) evaluated in the same order as the
+// sequential definition, so FP64 results are bit-for-bit those of a CPU evaluation of
+// the same formula. The FP32 inner V-cycle of the mixed-precision solve is HBM-bound
+// and computes D^-1 on the fly.
 #pragma once
 
 #include <cstdint>
@@ -25,14 +29,16 @@ template <typename T>
 struct Ar;
 template <>
 struct Ar<double> {
+    static constexpr bool kStoredDinv = true;
     static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
     static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
     static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
-    static __device__ __forceinline__ double mac(double s, double a, double b) { return __dadd_rn(s, __dmul_rn(a, b)); }
+    static __device__ __forceinline__ double mac(double s, double a, double b) { return __fma_rn(a, b, s); }
     static __device__ __forceinline__ double rcp(double a) { return __ddiv_rn(1.0, a); }
 };
 template <>
 struct Ar<float> {
+    static constexpr bool kStoredDinv = false;
     static __device__ __forceinline__ float mul(float a, float b) { return a * b; }
     static __device__ __forceinline__ float add(float a, float b) { return a + b; }
     static __device__ __forceinline__ float sub(float a, float b) { return a - b; }
@@ -40,7 +46,7 @@ struct Ar<float> {
     static __device__ __forceinline__ float rcp(float a) { return __fdiv_rn(1.0f, a); }
 };
 
-// Sweep modes: what a pass does with s = (A x)_i.
+// Sweep modes: what a pass does with s = (A x)_i and dinv = 1 / a_ii.
 enum SweepMode {
     SW_RESID = 0,    // out = b - s
     SW_JACOBI = 1,   // out = x + c1*(dinv*(b - s))                 (c1 = omega)
@@ -50,6 +56,11 @@ enum SweepMode {
     SW_CHEBF_Z = 5,  // x = 0: d = c1*(dinv*b); out = d
 };
 
+template <int MODE>
+struct IsZero {
+    static constexpr bool value = MODE == SW_JACOBI_Z || MODE == SW_CHEBF_Z;
+};
+
 struct DiaOffs {
     int32_t o[27];
 };
@@ -57,16 +68,18 @@ struct DiaOffs {
 // Matrix view for the kernels (values of type T).
 template <typename T>
 struct MatView {
-    const T *val;         // DIA/ELL: K*ld (slot-major); CSR: nnz
-    const int32_t *col;   // ELL: K*ld; CSR: nnz
-    const int64_t *rowptr;// CSR
+    const T *val;          // DIA/ELL: K*ld (slot-major); CSR: nnz
+    const int32_t *col;    // ELL: K*ld; CSR: nnz
+    const int64_t *rowptr; // CSR
+    const T *dinv;         // 1 / a_ii (FP64 levels)
     int64_t ld;
     int K;
-    DiaOffs offs;         // DIA: column = row + offs.o[k]
+    int center;            // DIA: slot of the diagonal
+    DiaOffs offs;          // DIA: column = row + offs.o[k]
 };
 
 template <typename T, int MODE>
-__device__ __forceinline__ void sweep_out(int i, T s, T diag, T xi, const T *__restrict__ b, T *__restrict__ out,
+__device__ __forceinline__ void sweep_out(int i, T s, T dinv, T xi, const T *__restrict__ b, T *__restrict__ out,
                                           T *__restrict__ d, T c1, T c2)
 {
     using A = Ar<T>;
@@ -75,29 +88,29 @@ __device__ __forceinline__ void sweep_out(int i, T s, T diag, T xi, const T *__r
         out[i] = A::sub(bi, s);
     } else if (MODE == SW_JACOBI) {
         T r = A::sub(bi, s);
-        out[i] = A::add(xi, A::mul(c1, A::mul(A::rcp(diag), r)));
+        out[i] = A::add(xi, A::mul(c1, A::mul(dinv, r)));
     } else if (MODE == SW_CHEBF) {
         T r = A::sub(bi, s);
-        T dd = A::mul(c1, A::mul(A::rcp(diag), r));
+        T dd = A::mul(c1, A::mul(dinv, r));
         d[i] = dd;
         out[i] = A::add(xi, dd);
     } else if (MODE == SW_CHEB) {
         T r = A::sub(bi, s);
-        T dd = A::add(A::mul(c1, d[i]), A::mul(c2, A::mul(A::rcp(diag), r)));
+        T dd = A::add(A::mul(c1, d[i]), A::mul(c2, A::mul(dinv, r)));
         d[i] = dd;
         out[i] = A::add(xi, dd);
     } else if (MODE == SW_JACOBI_Z) {
-        out[i] = A::mul(c1, A::mul(A::rcp(diag), bi));
+        out[i] = A::mul(c1, A::mul(dinv, bi));
     } else {  // SW_CHEBF_Z
-        T dd = A::mul(c1, A::mul(A::rcp(diag), bi));
+        T dd = A::mul(c1, A::mul(dinv, bi));
         d[i] = dd;
         out[i] = dd;
     }
 }
 
-// DIA: column of slot k is i + offs.o[k]; slot K/2 is the diagonal. x points at element
-// 0 of a buffer padded on both sides by at least max|offs|, so no bounds test is needed
-// (slots of missing neighbours hold 0 and read a finite padded or interior value).
+// DIA: column of slot k is i + offs.o[k]. x points at element 0 of a buffer padded on
+// both sides by at least max|offs|, so no bounds test is needed (slots of missing
+// neighbours hold 0 and read a finite padded or interior value).
 template <typename T, int K, int MODE>
 __global__ void __launch_bounds__(256) k_dia_sweep(MatView<T> A, int n, const T *__restrict__ x,
                                                    const T *__restrict__ b, T *__restrict__ out,
@@ -105,10 +118,10 @@ __global__ void __launch_bounds__(256) k_dia_sweep(MatView<T> A, int n, const T 
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    constexpr int C = K / 2;
-    if (MODE == SW_JACOBI_Z || MODE == SW_CHEBF_Z) {
-        T diag = __ldcs(A.val + (int64_t)C * A.ld + i);
-        sweep_out<T, MODE>(i, T(0), diag, T(0), b, out, d, c1, c2);
+    constexpr int C = K / 2;  // the stored diagonals are symmetric about the main one
+    if (IsZero<MODE>::value) {
+        T dinv = Ar<T>::kStoredDinv ? __ldcs(A.dinv + i) : Ar<T>::rcp(__ldcs(A.val + (int64_t)C * A.ld + i));
+        sweep_out<T, MODE>(i, T(0), dinv, T(0), b, out, d, c1, c2);
         return;
     }
     T a[K], xv[K];
@@ -119,7 +132,8 @@ __global__ void __launch_bounds__(256) k_dia_sweep(MatView<T> A, int n, const T 
     T s = T(0);
 #pragma unroll
     for (int k = 0; k < K; k++) s = Ar<T>::mac(s, a[k], xv[k]);
-    sweep_out<T, MODE>(i, s, a[C], xv[C], b, out, d, c1, c2);
+    T dinv = Ar<T>::kStoredDinv ? __ldcs(A.dinv + i) : Ar<T>::rcp(a[C]);
+    sweep_out<T, MODE>(i, s, dinv, xv[C], b, out, d, c1, c2);
 }
 
 // ELL with explicit columns; padded slots hold column i and value 0.
@@ -131,22 +145,16 @@ __global__ void __launch_bounds__(256) k_ell_sweep(MatView<T> A, int n, const T 
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     T s = T(0), diag = T(0);
-    if (MODE == SW_JACOBI_Z || MODE == SW_CHEBF_Z) {
+    if (!IsZero<MODE>::value || !Ar<T>::kStoredDinv) {
         for (int k = 0; k < A.K; k++) {
             int c = __ldcs(A.col + (int64_t)k * A.ld + i);
             T v = __ldcs(A.val + (int64_t)k * A.ld + i);
             if (c == i && diag == T(0)) diag = v;
+            if (!IsZero<MODE>::value) s = Ar<T>::mac(s, v, __ldg(x + c));
         }
-        sweep_out<T, MODE>(i, T(0), diag, T(0), b, out, d, c1, c2);
-        return;
     }
-    for (int k = 0; k < A.K; k++) {
-        int c = __ldcs(A.col + (int64_t)k * A.ld + i);
-        T v = __ldcs(A.val + (int64_t)k * A.ld + i);
-        if (c == i && diag == T(0)) diag = v;
-        s = Ar<T>::mac(s, v, __ldg(x + c));
-    }
-    sweep_out<T, MODE>(i, s, diag, x[i], b, out, d, c1, c2);
+    T dinv = Ar<T>::kStoredDinv ? __ldcs(A.dinv + i) : Ar<T>::rcp(diag);
+    sweep_out<T, MODE>(i, s, dinv, IsZero<MODE>::value ? T(0) : x[i], b, out, d, c1, c2);
 }
 
 template <typename T, int MODE>
@@ -157,14 +165,17 @@ __global__ void __launch_bounds__(256) k_csr_sweep(MatView<T> A, int n, const T 
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     T s = T(0), diag = T(0);
-    int64_t k0 = A.rowptr[i], k1 = A.rowptr[i + 1];
-    for (int64_t k = k0; k < k1; k++) {
-        int c = A.col[k];
-        T v = A.val[k];
-        if (c == i) diag = v;
-        if (MODE != SW_JACOBI_Z && MODE != SW_CHEBF_Z) s = Ar<T>::mac(s, v, __ldg(x + c));
+    if (!IsZero<MODE>::value || !Ar<T>::kStoredDinv) {
+        int64_t k0 = A.rowptr[i], k1 = A.rowptr[i + 1];
+        for (int64_t k = k0; k < k1; k++) {
+            int c = A.col[k];
+            T v = A.val[k];
+            if (c == i) diag = v;
+            if (!IsZero<MODE>::value) s = Ar<T>::mac(s, v, __ldg(x + c));
+        }
     }
-    sweep_out<T, MODE>(i, s, diag, (MODE == SW_JACOBI_Z || MODE == SW_CHEBF_Z) ? T(0) : x[i], b, out, d, c1, c2);
+    T dinv = Ar<T>::kStoredDinv ? A.dinv[i] : Ar<T>::rcp(diag);
+    sweep_out<T, MODE>(i, s, dinv, IsZero<MODE>::value ? T(0) : x[i], b, out, d, c1, c2);
 }
 
 // ------------------------------------------------------------------------------------
@@ -341,14 +352,14 @@ __global__ void __launch_bounds__(256) k_outer_resid(MatView<double> A, int n, c
 #pragma unroll
             for (int k = 0; k < K; k++) xv[k] = __ldg(x + i + A.offs.o[k]);
 #pragma unroll
-            for (int k = 0; k < K; k++) s = __dadd_rn(s, __dmul_rn(a[k], xv[k]));
+            for (int k = 0; k < K; k++) s = __fma_rn(a[k], xv[k], s);
         } else if (FMT == 2) {  // ELL
             for (int k = 0; k < A.K; k++) {
                 int c = __ldcs(A.col + (int64_t)k * A.ld + i);
-                s = __dadd_rn(s, __dmul_rn(__ldcs(A.val + (int64_t)k * A.ld + i), __ldg(x + c)));
+                s = __fma_rn(__ldcs(A.val + (int64_t)k * A.ld + i), __ldg(x + c), s);
             }
         } else {  // CSR
-            for (int64_t k = A.rowptr[i]; k < A.rowptr[i + 1]; k++) s = __dadd_rn(s, __dmul_rn(A.val[k], __ldg(x + A.col[k])));
+            for (int64_t k = A.rowptr[i]; k < A.rowptr[i + 1]; k++) s = __fma_rn(A.val[k], __ldg(x + A.col[k]), s);
         }
         double ri = __dsub_rn(b[i], s);
         r[i] = (Tin)ri;

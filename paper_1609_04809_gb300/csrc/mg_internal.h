@@ -36,9 +36,12 @@ struct DevMat {
     int K = 0;
     int elem_size = 8;
     mgk::DiaOffs offs{};
+    int center = 0;      // DIA: stored slot of the diagonal
+    int full_of[27] = {};// DIA: stencil position (dx+1) + 3(dy+1) + 9(dz+1) of each stored slot
     void *val = nullptr;
     int32_t *col = nullptr;
     int64_t *rowptr = nullptr;
+    void *dinv = nullptr;  // 1 / a_ii, FP64 inner levels only
 };
 
 struct LevelD {

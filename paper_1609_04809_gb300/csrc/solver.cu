@@ -130,8 +130,10 @@ static MatView<T> view(const DevMat &m)
     v.val = (const T *)m.val;
     v.col = m.col;
     v.rowptr = m.rowptr;
+    v.dinv = (const T *)m.dinv;
     v.ld = m.ld;
     v.K = m.K;
+    v.center = m.center;
     v.offs = m.offs;
     return v;
 }
@@ -287,6 +289,8 @@ static void sweep_fmt(const DevMat &A, int n, const T *x, const T *b, T *out, T 
     if (A.fmt == MG_STORAGE_DIA) {
         if (A.K == 27)
             k_dia_sweep<T, 27, MODE><<<g, 256, 0, s>>>(v, n, x, b, out, d, c1, c2);
+        else if (A.K == 21)
+            k_dia_sweep<T, 21, MODE><<<g, 256, 0, s>>>(v, n, x, b, out, d, c1, c2);
         else
             k_dia_sweep<T, 9, MODE><<<g, 256, 0, s>>>(v, n, x, b, out, d, c1, c2);
     } else if (A.fmt == MG_STORAGE_ELL) {
@@ -307,13 +311,14 @@ static void sweep(mg_hierarchy *h, int l, int mode, const T *x, const T *b, T *o
     double bytes;
     int kclass;
     bool zero = mode == SW_JACOBI_Z || mode == SW_CHEBF_Z;
-    if (zero) {
+    if (zero) {  // the diagonal (stored D^-1, the DIA diagonal slot, or a row scan), b, out [, d]
         kclass = MG_K_SMOOTH0;
-        double diag = L.A.fmt == MG_STORAGE_DIA ? n * sv : mat_bytes(L.A, sv);
+        double diag = L.A.dinv ? n * sv : (L.A.fmt == MG_STORAGE_DIA ? n * sv : mat_bytes(L.A, sv));
         bytes = diag + 2 * n * sv + (mode == SW_CHEBF_Z ? n * sv : 0);
-    } else {
+    } else {  // the matrix, x, b, out [, D^-1] [, d read and/or write]
         kclass = mode == SW_RESID ? MG_K_RESID : MG_K_SMOOTH;
         bytes = mat_bytes(L.A, sv) + 3 * n * sv;
+        if (mode != SW_RESID && L.A.dinv) bytes += n * sv;
         if (mode == SW_CHEBF) bytes += n * sv;
         if (mode == SW_CHEB) bytes += 2 * n * sv;
     }
@@ -453,6 +458,8 @@ static void enqueue_outer(mg_hierarchy *h, cudaStream_t s)
     if (A.fmt == MG_STORAGE_DIA) {
         if (A.K == 27)
             k_outer_resid<T, 3, 27><<<g, 256, 0, s>>>(v, n, h->x64, h->b64, r, h->partial, h->ticket, h->norm2);
+        else if (A.K == 21)
+            k_outer_resid<T, 3, 21><<<g, 256, 0, s>>>(v, n, h->x64, h->b64, r, h->partial, h->ticket, h->norm2);
         else
             k_outer_resid<T, 3, 9><<<g, 256, 0, s>>>(v, n, h->x64, h->b64, r, h->partial, h->ticket, h->norm2);
     } else if (A.fmt == MG_STORAGE_ELL) {
@@ -636,12 +643,47 @@ static void plan_matrix(DevMat &m, const mgh::Csr &A, int fmt, int dim, int N, i
     m.ld = round_up(std::max<int64_t>(m.n, 1), 64);
     m.elem_size = sv;
     if (fmt == MG_STORAGE_DIA) {
-        m.K = dim == 3 ? 27 : 9;
+        // keep the stencil positions that hold a nonzero anywhere (ascending offset),
+        // padded with unused positions up to an instantiated slot count (9, 21 or 27).
+        // A symmetric matrix uses position p iff it uses npos-1-p, and padding adds such
+        // pairs, so the diagonal is always the middle slot K/2.
+        int npos = dim == 3 ? 27 : 9, cpos = npos / 2;
+        bool used[27] = {};
+        used[cpos] = true;
+        for (int64_t i = 0; i < A.nrows; i++) {
+            int ci[3], cj[3];
+            mgh::q1_coords(dim, N, i, ci);
+            for (int64_t k = A.rowptr[i]; k < A.rowptr[i + 1]; k++) {
+                if (A.val[k] == 0.0) continue;
+                mgh::q1_coords(dim, N, A.col[k], cj);
+                used[(cj[0] - ci[0] + 1) + 3 * (cj[1] - ci[1] + 1) + (dim == 3 ? 9 * (cj[2] - ci[2] + 1) : 0)] = true;
+            }
+        }
+        int cnt = 0;
+        for (int p = 0; p < npos; p++) cnt += used[p];
+        int K = dim == 2 ? 9 : (cnt <= 21 ? 21 : 27);
+        for (int p = 0; p < npos; p++)  // symmetrise (a Galerkin product may round asymmetrically)
+            if (used[p]) used[npos - 1 - p] = true;
+        cnt = 0;
+        for (int p = 0; p < npos; p++) cnt += used[p];
+        if (cnt > K) K = 27;
+        for (int p = 0; p < cpos && cnt < K; p++)
+            if (!used[p]) {
+                used[p] = used[npos - 1 - p] = true;
+                cnt += 2;
+            }
+        m.K = K;
         int64_t n1 = N - 1;
         int k = 0;
-        for (int dz = (dim == 3 ? -1 : 0); dz <= (dim == 3 ? 1 : 0); dz++)
-            for (int dy = -1; dy <= 1; dy++)
-                for (int dx = -1; dx <= 1; dx++) m.offs.o[k++] = (int32_t)(dx + n1 * dy + n1 * n1 * dz);
+        for (int p = 0; p < npos; p++) {
+            if (!used[p]) continue;
+            int dx = p % 3 - 1, dy = (p / 3) % 3 - 1, dz = dim == 3 ? p / 9 - 1 : 0;
+            m.offs.o[k] = (int32_t)(dx + n1 * dy + n1 * n1 * dz);
+            m.full_of[k] = p;
+            if (p == cpos) m.center = k;
+            k++;
+        }
+        if (k != K || m.center != K / 2) throw Error(MG_EINVAL, "DIA slot selection is not symmetric");
         size_t bytes = (size_t)m.K * m.ld * sv;
         if (take)
             m.val = slab.take(bytes);
@@ -682,14 +724,17 @@ static void upload_matrix(const DevMat &m, const mgh::Csr &A, const std::vector<
     if (m.fmt == MG_STORAGE_DIA) {
         std::vector<T> v((size_t)m.K * m.ld, T(0));
         int k3 = dim == 3 ? 9 : 0;
+        int slot_of[27];
+        for (int p = 0; p < 27; p++) slot_of[p] = -1;
+        for (int k = 0; k < m.K; k++) slot_of[m.full_of[k]] = k;
 #pragma omp parallel for schedule(static)
         for (int64_t i = 0; i < A.nrows; i++) {
             int ci[3], cj[3];
             mgh::q1_coords(dim, N, i, ci);
             for (int64_t k = A.rowptr[i]; k < A.rowptr[i + 1]; k++) {
                 mgh::q1_coords(dim, N, A.col[k], cj);
-                int slot = (cj[0] - ci[0] + 1) + 3 * (cj[1] - ci[1] + 1) + k3 * (cj[2] - ci[2] + 1);
-                v[(size_t)slot * m.ld + i] = vals[k];
+                int slot = slot_of[(cj[0] - ci[0] + 1) + 3 * (cj[1] - ci[1] + 1) + k3 * (cj[2] - ci[2] + 1)];
+                if (slot >= 0) v[(size_t)slot * m.ld + i] = vals[k];  // dropped positions hold only zeros
             }
         }
         CK(cudaMemcpyAsync(m.val, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s));
@@ -837,6 +882,7 @@ static void build(mg_hierarchy *h, const mg_problem *p, const mg_options *o, con
             int lf = (l == 0 && fmt == MG_STORAGE_DIA) ? MG_STORAGE_DIA : fmt;
             L.fmt = lf;
             plan_matrix(L.A, A[l], lf, dim, L.N, sv, S, take);
+            if (!h->mixed && l >= 1) L.A.dinv = vec((size_t)L.A.ld * 8);  // FP64 smoothers read D^-1
             int64_t n1 = L.N - 1;
             L.pad = lf == MG_STORAGE_DIA ? round_up(dim == 3 ? n1 * n1 + n1 + 1 : n1 + 1, 64) : 0;
             int64_t ld = L.A.ld;
@@ -888,6 +934,14 @@ static void build(mg_hierarchy *h, const mg_problem *p, const mg_options *o, con
             }
         } else {
             upload_matrix<double>(L.A, A[l], A[l].val, dim, L.N, h->s);
+            if (L.A.dinv) {
+                std::vector<double> dv((size_t)L.A.ld, 0.0);
+                for (int64_t i = 0; i < A[l].nrows; i++)
+                    for (int64_t k = A[l].rowptr[i]; k < A[l].rowptr[i + 1]; k++)
+                        if (A[l].col[k] == i) dv[i] = 1.0 / A[l].val[k];
+                CK(cudaMemcpyAsync(L.A.dinv, dv.data(), dv.size() * 8, cudaMemcpyHostToDevice, h->s));
+                CK(cudaStreamSynchronize(h->s));
+            }
             if (l >= 1 && !L.structured) {
                 upload_matrix<double>(L.P, P[l], P[l].val, dim, L.N, h->s);
                 upload_matrix<double>(L.R, R[l], R[l].val, dim, L.N, h->s);
@@ -1175,26 +1229,34 @@ static void export_dev(const DevMat &m, int dim, int N, int sv, mgh::Csr &out)
         c.resize(cnt);
         CK(cudaMemcpy(c.data(), m.col, cnt * 4, cudaMemcpyDeviceToHost));
     }
+    int slot_of[27];
+    for (int p = 0; p < 27; p++) slot_of[p] = -1;
+    if (m.fmt == MG_STORAGE_DIA)
+        for (int k = 0; k < m.K; k++) slot_of[m.full_of[k]] = k;
+    int64_t n1 = N - 1;
     for (int64_t i = 0; i < m.n; i++) {
-        int ci[3] = {0, 0, 0};
-        if (m.fmt == MG_STORAGE_DIA) mgh::q1_coords(dim, N, i, ci);
-        int32_t prev = -1;
-        for (int k = 0; k < m.K; k++) {
-            int32_t j;
-            if (m.fmt == MG_STORAGE_DIA) {
-                int d[3] = {k % 3 - 1, (k / 3) % 3 - 1, dim == 3 ? k / 9 - 1 : 0};
+        if (m.fmt == MG_STORAGE_DIA) {
+            // every in-grid neighbour is a structural entry; dropped positions are zero
+            int ci[3] = {0, 0, 0};
+            mgh::q1_coords(dim, N, i, ci);
+            for (int p = 0; p < (dim == 3 ? 27 : 9); p++) {
+                int d[3] = {p % 3 - 1, (p / 3) % 3 - 1, dim == 3 ? p / 9 - 1 : 0};
                 bool inside = true;
                 for (int a = 0; a < dim; a++)
                     if (ci[a] + d[a] < 1 || ci[a] + d[a] > N - 1) inside = false;
                 if (!inside) continue;
-                j = (int32_t)(i + m.offs.o[k]);
-            } else {
-                j = c[(size_t)k * m.ld + i];
+                out.col.push_back((int32_t)(i + d[0] + n1 * d[1] + n1 * n1 * d[2]));
+                out.val.push_back(slot_of[p] >= 0 ? v[(size_t)slot_of[p] * m.ld + i] : 0.0);
+            }
+        } else {
+            int32_t prev = -1;
+            for (int k = 0; k < m.K; k++) {
+                int32_t j = c[(size_t)k * m.ld + i];
                 if (j <= prev) break;  // padding (column i after larger columns)
                 prev = j;
+                out.col.push_back(j);
+                out.val.push_back(v[(size_t)k * m.ld + i]);
             }
-            out.col.push_back(j);
-            out.val.push_back(v[(size_t)k * m.ld + i]);
         }
         out.rowptr[i + 1] = (int64_t)out.col.size();
     }

@@ -108,8 +108,8 @@ def test_rq1_storage(orc, storage):
 
 
 def test_variable_coefficient_with_galerkin_levels(orc):
-    dim, elem, N, L = 3, 0, 32, 4  # blocks of 8 cells: the two coarsest levels are Galerkin
-    k = W.k_blocks(N, dim=3, blocks_per_axis=4, seed=20260101)
+    dim, elem, N, L = 3, 0, 32, 4  # blocks of 4 cells: the 4^3-cell level straddles blocks
+    k = W.k_blocks(N, dim=3, blocks_per_axis=8, seed=20260101)
     b = mg.mg_load_vector(dim, elem, N, modes=None, f_const=1.0)
     H, O, g, o = _run_both(orc, dim, elem, N, L, b, smoother=1, nu_pre=1, nu_post=1, k=k)
     assert H.info()["galerkin"] == [1, 0, 0, 0]
