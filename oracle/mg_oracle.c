@@ -689,6 +689,25 @@ static double norm2(const double *v, int64_t n)
     return sqrt(s);
 }
 
+/* ||v||_2 for the residual history and the stopping test: the sum of squares is
+ * accumulated with Neumaier's compensated summation (Neumaier 1974), so the reported
+ * norm is within a few ulps of the exact one for any length, unlike the plain
+ * sequential sum whose relative error grows with n. */
+static double norm2_accurate(const double *v, int64_t n)
+{
+    double s = 0.0, c = 0.0;
+    for (int64_t i = 0; i < n; i++) {
+        double t = v[i] * v[i];
+        double u = s + t;
+        if (fabs(s) >= fabs(t))
+            c = c + ((s - u) + t);
+        else
+            c = c + ((t - u) + s);
+        s = u;
+    }
+    return sqrt(s + c);
+}
+
 /* ------------------------------------------------------------------------------ */
 /* Coarsest level: dense LU with partial pivoting (first row of maximal |a| wins)    */
 /* ------------------------------------------------------------------------------ */
@@ -1024,12 +1043,12 @@ int orc_solve(orc_hier *H, const orc_opts *o, const double *b, double *x, double
     int64_t n = A->nrows;
     double *r = (double *)malloc((size_t)n * sizeof(double));
     double *c = (double *)malloc((size_t)n * sizeof(double));
-    double nb = norm2(b, n);
+    double nb = norm2_accurate(b, n);
     int status = 1;
     int k;
     for (k = 0;; k++) {
         residual(A, b, x, r);
-        double nr = norm2(r, n);
+        double nr = norm2_accurate(r, n);
         double h = nb > 0.0 ? nr / nb : nr;
         if (hist)
             hist[k] = h;

@@ -441,6 +441,19 @@ def test_vcycle_equals_closed_form_operator(orc, dim, elem, N, L, smoother):
     np.testing.assert_allclose(c, Bop @ r, rtol=0, atol=1e-11 * np.max(np.abs(c)))
 
 
+def test_reported_residual_norm_is_accurate(orc):
+    """hist[0] = ||b - A x0|| / ||b|| to a few ulps (checked with an exactly rounded sum)."""
+    import math
+    N, L = 512, 8
+    H = orc.Hierarchy(2, orc.Q1, N, L)
+    b = W.random_vector(H.n, seed=3) * 1e3
+    x0 = W.random_vector(H.n, seed=4)
+    x, hist, it, conv = H.solve(b, 0.0, x0=x0, max_iters=0)
+    r = b - orc.spmv(H.A(L - 1), x0)
+    exact = math.sqrt(math.fsum(r * r)) / math.sqrt(math.fsum(b * b))
+    assert abs(hist[0] - exact) <= 4e-16 * exact
+
+
 def test_power_iteration_bounds(orc):
     N = 16
     opts = orc.Options(smoother=orc.CHEBYSHEV)
