@@ -203,6 +203,26 @@ mg_status mg_profile_enable(mg_hierarchy *h, int enable);
 mg_status mg_profile_read(const mg_hierarchy *h, int kclass, int level, double *ms_total, int64_t *launches,
                           double *bytes_per_launch);
 
+/* r = b - A x on the finest level in FP64 and rnorm = ||r||_2, without allocating
+ * anything. The paper has no counterpart: this entry point is for callers that cannot
+ * allocate device memory at the moment they need a residual, for example because a
+ * memory pool owns the whole device, because they run inside a callback that must not
+ * re-enter an allocator, or because their latency budget rules out an allocation. It
+ * calls no cudaMalloc, cudaFree or other allocating routine: its scratch (block partial
+ * sums, a completion counter, the result) is a fixed device array of about 512 KiB that
+ * every GPU loading the library holds until the process exits.
+ *   b_dev, x_dev: device pointers to n doubles (inputs, caller-owned; x needs no
+ *   padding); r_dev: device pointer to n doubles (output, caller-owned); rnorm: host
+ *   pointer to one double (output). Runs on the caller's stream of mg_device and
+ *   synchronises it before returning.
+ * Limit: n <= 16,777,216 rows (MG_EINVAL with a message beyond it).
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture. Every call shares the one array and
+ * it keeps the last call's contents: calls that overlap on the GPU (other streams or
+ * threads) race on it and must be serialised by the caller. */
+mg_status mg_residual_norm_noalloc(mg_hierarchy *h, const double *b_dev, const double *x_dev, double *r_dev,
+                                   double *rnorm);
+
 /* Thread-local description of the last error on this thread. */
 const char *mg_last_error(void);
 

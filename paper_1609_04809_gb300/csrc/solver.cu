@@ -1329,3 +1329,114 @@ extern "C" mg_status mg_profile_read(const mg_hierarchy *h, int kclass, int leve
     if (bytes_per_launch) *bytes_per_launch = h->prof.launches[k] ? h->prof.bytes_total[k] / h->prof.launches[k] : 0.0;
     return MG_OK;
 }
+
+// ------------------------------------------------------------------------------------
+// Residual and norm without any allocation
+// ------------------------------------------------------------------------------------
+// Some callers cannot allocate device memory when they need a residual: code running
+// where cudaMalloc is not allowed or would stall (a memory pool that owns the whole
+// device, an allocator that must not be re-entered from a callback, a latency-critical
+// path that may not trigger allocation). mg_residual_norm_noalloc serves them: its
+// block partial sums, completion ticket and result live in the fixed device array
+// below (about 512 KiB, held by every GPU that loads the library until the process
+// exits), so a call allocates nothing. The array is shared by all calls: overlapping
+// calls on the GPU (different streams or threads) race on it.
+#define MG_NOALLOC_MAX_BLOCKS 65536
+#define MG_NOALLOC_MAX_ROWS ((int64_t)MG_NOALLOC_MAX_BLOCKS * 256)
+
+struct NoallocScratch {
+    double partial[MG_NOALLOC_MAX_BLOCKS];
+    double result;
+    unsigned ticket;
+};
+
+static __device__ __align__(256) NoallocScratch g_noalloc_scratch;
+
+// Same residual as the outer residual kernel, for x without the padding the DIA gathers
+// need: neighbours outside [0, n) read as zero (their matrix entries are zero).
+template <int FMT, int K>
+__global__ void __launch_bounds__(256) k_residual_noalloc(MatView<double> A, int n, const double *__restrict__ x,
+                                                          const double *__restrict__ b, double *__restrict__ r,
+                                                          NoallocScratch *sc)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double sq = 0.0;
+    if (i < n) {
+        double s = 0.0;
+        if (FMT == MG_STORAGE_DIA) {
+#pragma unroll
+            for (int k = 0; k < K; k++) {
+                int64_t j = (int64_t)i + A.offs.o[k];
+                double xv = (j >= 0 && j < n) ? __ldg(x + j) : 0.0;
+                s = __fma_rn(__ldcs(A.val + (int64_t)k * A.ld + i), xv, s);
+            }
+        } else if (FMT == MG_STORAGE_ELL) {
+            for (int k = 0; k < A.K; k++) {
+                int c = __ldcs(A.col + (int64_t)k * A.ld + i);
+                s = __fma_rn(__ldcs(A.val + (int64_t)k * A.ld + i), __ldg(x + c), s);
+            }
+        } else {
+            for (int64_t k = A.rowptr[i]; k < A.rowptr[i + 1]; k++) s = __fma_rn(A.val[k], __ldg(x + A.col[k]), s);
+        }
+        double ri = __dsub_rn(b[i], s);
+        r[i] = ri;
+        sq = ri * ri;
+    }
+    finish_norm(sq, sc->partial, &sc->ticket, &sc->result);
+}
+
+// Device address of the scratch array, looked up once per device with that device
+// current (the host-side name of a __device__ variable is not a device address).
+static NoallocScratch *noalloc_scratch_address(int device)
+{
+    static std::mutex mu;
+    static NoallocScratch *addr[256] = {};
+    if (device < 0 || device >= 256) throw Error(MG_EINVAL, "device ordinal out of range");
+    std::lock_guard<std::mutex> lk(mu);
+    if (!addr[device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            throw Error(MG_ECUDA, std::string("cudaGetSymbolAddress of the residual scratch: ") + cudaGetErrorString(e));
+        addr[device] = (NoallocScratch *)p;
+    }
+    return addr[device];
+}
+
+extern "C" mg_status mg_residual_norm_noalloc(mg_hierarchy *h, const double *b_dev, const double *x_dev, double *r_dev,
+                                              double *rnorm)
+{
+    return guarded(h, [&]() -> mg_status {
+        if (!b_dev || !x_dev || !r_dev || !rnorm) throw Error(MG_EINVAL, "b, x, r or rnorm is NULL");
+        const DevMat &A = h->A64;
+        int64_t n = A.n;
+        if (n > MG_NOALLOC_MAX_ROWS)
+            throw Error(MG_EINVAL, "mg_residual_norm_noalloc: " + std::to_string(n) + " rows exceed its limit of " +
+                                       std::to_string(MG_NOALLOC_MAX_ROWS));
+        NoallocScratch *sc = noalloc_scratch_address(h->device);
+        cudaStream_t s = h->caller;
+        // the ticket must start at zero; the last block resets it, this covers an aborted call
+        CK(cudaMemsetAsync(&sc->ticket, 0, sizeof(unsigned), s));
+        MatView<double> v = view<double>(A);
+        unsigned g = grid_for(n);
+        int nn = (int)n;
+        if (A.fmt == MG_STORAGE_DIA) {
+            if (A.K == 27)
+                k_residual_noalloc<MG_STORAGE_DIA, 27><<<g, 256, 0, s>>>(v, nn, x_dev, b_dev, r_dev, sc);
+            else if (A.K == 21)
+                k_residual_noalloc<MG_STORAGE_DIA, 21><<<g, 256, 0, s>>>(v, nn, x_dev, b_dev, r_dev, sc);
+            else
+                k_residual_noalloc<MG_STORAGE_DIA, 9><<<g, 256, 0, s>>>(v, nn, x_dev, b_dev, r_dev, sc);
+        } else if (A.fmt == MG_STORAGE_ELL) {
+            k_residual_noalloc<MG_STORAGE_ELL, 1><<<g, 256, 0, s>>>(v, nn, x_dev, b_dev, r_dev, sc);
+        } else {
+            k_residual_noalloc<MG_STORAGE_CSR, 1><<<g, 256, 0, s>>>(v, nn, x_dev, b_dev, r_dev, sc);
+        }
+        CKL();
+        double nr2 = 0.0;
+        CK(cudaMemcpyAsync(&nr2, &sc->result, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        *rnorm = std::sqrt(nr2);
+        return MG_OK;
+    });
+}

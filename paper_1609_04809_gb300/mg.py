@@ -85,6 +85,7 @@ SIGNATURES = {
                                           _P(ctypes.c_int64), _P(ctypes.c_int64), _P(ctypes.c_int32), _dp]),
     "mg_profile_enable": (ctypes.c_int, [_vp, ctypes.c_int]),
     "mg_profile_read": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _dp, _P(ctypes.c_int64), _dp]),
+    "mg_residual_norm_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _vp, _dp]),
     "mg_last_error": (ctypes.c_char_p, []),
 }
 
@@ -283,6 +284,14 @@ def mg_export_operator(h, level, which, precision=MG_FP64):
                                 rowptr.ctypes.data_as(_P(ctypes.c_int64)),
                                 col.ctypes.data_as(_P(ctypes.c_int32)), _as_dp(val)))
     return rowptr, col[:nnz.value], val[:nnz.value]
+
+
+def mg_residual_norm_noalloc(h, b_dev, x_dev, r_dev):
+    """r_dev = b - A x on the finest level and ||r||_2, with no device allocation (see mg.h)."""
+    nr = ctypes.c_double(0.0)
+    _check(lib().mg_residual_norm_noalloc(h, ctypes.c_void_p(b_dev.data_ptr()), ctypes.c_void_p(x_dev.data_ptr()),
+                                          ctypes.c_void_p(r_dev.data_ptr()), ctypes.byref(nr)))
+    return nr.value
 
 
 def mg_profile_enable(h, enable=True):
