@@ -199,7 +199,10 @@ mg_status mg_export_operator(const mg_hierarchy *h, int level, int which, int pr
 #define MG_K_UPDATE 6   /* x += c */
 #define MG_K_SMOOTH0 7  /* first smoother step from x = 0 (diagonal only, no matrix-vector product) */
 #define MG_K_COUNT 8
-mg_status mg_profile_enable(mg_hierarchy *h, int enable);
+/* enable: 0 off, else on for launches whose class bit is set in class_mask and whose
+ * level bit is set in level_mask (~0u: all). Resets the accumulated profile. With
+ * profiling on, mg_cycle synchronises after every iteration to read the events. */
+mg_status mg_profile_enable(mg_hierarchy *h, int enable, unsigned class_mask, unsigned level_mask);
 mg_status mg_profile_read(const mg_hierarchy *h, int kclass, int level, double *ms_total, int64_t *launches,
                           double *bytes_per_launch);
 

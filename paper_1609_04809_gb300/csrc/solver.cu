@@ -218,6 +218,7 @@ struct mg_hierarchy {
     bool capturing = false;
     // profiling
     bool profiling = false;
+    unsigned prof_class_mask = ~0u, prof_level_mask = ~0u;
     mgi::Prof prof;
     std::vector<mgi::Prof::Rec> rec_r, rec_v, rec_eager;
     std::vector<mgi::Prof::Rec> *sink = nullptr;
@@ -258,14 +259,16 @@ mg_hierarchy::~mg_hierarchy()
 struct LaunchScope {
     mg_hierarchy *h;
     cudaStream_t s;
+    bool on;
     LaunchScope(mg_hierarchy *h_, cudaStream_t s_, int kclass, int level, double bytes) : h(h_), s(s_)
     {
         if (h->counting) h->kernels_per_cycle++;
-        if (h->profiling) h->prof.begin(s, kclass, level, bytes, h->sink, h->capturing);
+        on = h->profiling && ((h->prof_class_mask >> kclass) & 1) && ((h->prof_level_mask >> level) & 1);
+        if (on) h->prof.begin(s, kclass, level, bytes, h->sink, h->capturing);
     }
     ~LaunchScope() noexcept(false)
     {
-        if (h->profiling) h->prof.end(s, h->sink, h->capturing);
+        if (on) h->prof.end(s, h->sink, h->capturing);
     }
 };
 
@@ -1303,7 +1306,7 @@ extern "C" mg_status mg_export_operator(const mg_hierarchy *hc, int level, int w
     });
 }
 
-extern "C" mg_status mg_profile_enable(mg_hierarchy *h, int enable)
+extern "C" mg_status mg_profile_enable(mg_hierarchy *h, int enable, unsigned class_mask, unsigned level_mask)
 {
     return guarded(h, [&]() -> mg_status {
         CK(cudaStreamSynchronize(h->s));
@@ -1311,6 +1314,8 @@ extern "C" mg_status mg_profile_enable(mg_hierarchy *h, int enable)
         h->prof.release(h->rec_eager);
         h->prof.reset();
         h->profiling = enable != 0;
+        h->prof_class_mask = class_mask;
+        h->prof_level_mask = level_mask;
         ensure_graphs(h);
         return MG_OK;
     });

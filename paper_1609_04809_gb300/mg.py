@@ -83,7 +83,7 @@ SIGNATURES = {
     "mg_cycle": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _dp]),
     "mg_export_operator": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P(ctypes.c_int64),
                                           _P(ctypes.c_int64), _P(ctypes.c_int64), _P(ctypes.c_int32), _dp]),
-    "mg_profile_enable": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "mg_profile_enable": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_uint, ctypes.c_uint]),
     "mg_profile_read": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _dp, _P(ctypes.c_int64), _dp]),
     "mg_residual_norm_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _vp, _dp]),
     "mg_last_error": (ctypes.c_char_p, []),
@@ -294,8 +294,11 @@ def mg_residual_norm_noalloc(h, b_dev, x_dev, r_dev):
     return nr.value
 
 
-def mg_profile_enable(h, enable=True):
-    return _check(lib().mg_profile_enable(h, int(bool(enable))))
+def mg_profile_enable(h, enable=True, classes=None, levels=None):
+    """Time launches with CUDA events; classes / levels: iterables of MG_K_* / level indices (None: all)."""
+    cm = 0xFFFFFFFF if classes is None else sum(1 << c for c in classes)
+    lm = 0xFFFFFFFF if levels is None else sum(1 << l for l in levels)
+    return _check(lib().mg_profile_enable(h, int(bool(enable)), cm, lm))
 
 
 def mg_profile_read(h, kclass, level):

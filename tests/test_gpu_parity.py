@@ -179,7 +179,7 @@ def test_profiled_launch_counts(orc):
     dim, elem, N, L = 3, 0, 16, 3
     b = torch.from_numpy(W.random_vector(mg.mg_ndofs(dim, elem, N), seed=2)).cuda()
     H = mg.Hierarchy(dim, elem, N, L, smoother=1, nu_pre=1, nu_post=1)
-    mg.mg_profile_enable(H.h, True)
+    mg.mg_profile_enable(H.h, True)  # every class and level
     x = torch.zeros_like(b)
     H.cycle(b, x, 3)
     total = sum(mg.mg_profile_read(H.h, k, l)[1] for k in range(mg.MG_K_COUNT) for l in range(L))
