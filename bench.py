@@ -30,6 +30,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "V-cycle DOFs/s"
+# FP64 issue rate of GB300: 2 DFMA per clock per SM (the recipe's nominal 1.25 TFLOP/s)
+FP64_PEAK_TFLOPS = 152 * 2.07e9 * 2 * 2 / 1e12
 UNIT = "DOF/s"
 WORKLOADS = {
     "q1_3d_128_cheb": "3D Poisson, Q1, 128^3 cells (2,048,383 DOFs), 6 levels, V(2,2) Chebyshev deg 2, FP64",
@@ -113,7 +115,7 @@ class ClockSampler:
 
 def _traffic_from_profile(kernel_tag):
     """DRAM bytes per launch from the committed ncu summary, if it matches the current kernels."""
-    src = os.path.join(ROOT, "paper_1609_04809_gb300", "csrc", "kernels.cuh")
+    src = os.path.join(ROOT, "paper_1609_04809_gb300", "csrc", "sweep.cuh")
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
@@ -252,7 +254,7 @@ def run_ours(args):
     value = world * n * args.steps / (ms_max * 1e-3)
 
     # dominant kernel: finest-level smoother sweep
-    k_ms, k_cnt, k_bytes = mg.mg_profile_read(H.h, mg.MG_K_SMOOTH, Lf)
+    k_ms, k_cnt, k_bytes, k_flops = mg.mg_profile_read(H.h, mg.MG_K_SMOOTH, Lf)
     mg.mg_profile_enable(H.h, False)
     # per-class device time of one step, from a separate profiled pass over every launch
     mg.mg_profile_enable(H.h, True)
@@ -264,7 +266,9 @@ def run_ours(args):
         per_kernel[mg.KCLASS_NAMES[kc]] = round(tot / 5, 4)
     mg.mg_profile_enable(H.h, False)
     peak, peak_kind = _peaks()
-    achieved = k_bytes / (k_ms / k_cnt * 1e-3) / 1e9 if k_cnt else None
+    k_s = k_ms / k_cnt * 1e-3 if k_cnt else None
+    achieved = k_bytes / k_s / 1e9 if k_cnt else None
+    fp64_tflops = k_flops / k_s / 1e12 if k_cnt else None
 
     out = None
     if rank == 0:
@@ -324,13 +328,16 @@ def run_ours(args):
                           "l2": "inputs larger than L2 (finest FP64 matrix %.0f MB > 129 MB L2)"
                                 % (info["nnz"][Lf] * 8 / 1e6),
                           "storage": ["csr", "ell", "dia"][info["storage"][Lf] - 1]},
-               "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                            "frac": achieved / peak if achieved else None,
+               "roofline": {"bound": "alu", "achieved": fp64_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                            "frac": fp64_tflops / FP64_PEAK_TFLOPS if fp64_tflops else None,
                             "traffic": _traffic_from_profile("smooth_fp64_%s" % name),
-                            "kernel": "finest-level smoother sweep (fused residual + Chebyshev update)",
-                            "bytes_per_launch": k_bytes, "launches": k_cnt,
-                            "us_per_launch": 1e3 * k_ms / k_cnt if k_cnt else None,
-                            "peak_kind": "%s HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" % peak_kind},
+                            "kernel": "finest-level smoother sweep (fused residual + Chebyshev update), FP64",
+                            "peak_kind": "FP64 pipe: 152 SMs x 2.07 GHz x 2 DFMA/clk/SM x 2 flop (recipe nominal)",
+                            "flops_per_launch": k_flops, "bytes_per_launch": k_bytes, "launches": k_cnt,
+                            "us_per_launch": 1e6 * k_s if k_cnt else None,
+                            "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s",
+                                    "frac": achieved / peak if achieved else None,
+                                    "peak_kind": "%s HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" % peak_kind}},
                "kernel_ms_per_step": per_kernel,
                "e2e": e2e, "time_to_solution": tts, "cpu_baseline": cpu,
                "gpu_launches": info["kernels_per_cycle"] * args.steps + 1,

@@ -204,7 +204,7 @@ mg_status mg_export_operator(const mg_hierarchy *h, int level, int which, int pr
  * profiling on, mg_cycle synchronises after every iteration to read the events. */
 mg_status mg_profile_enable(mg_hierarchy *h, int enable, unsigned class_mask, unsigned level_mask);
 mg_status mg_profile_read(const mg_hierarchy *h, int kclass, int level, double *ms_total, int64_t *launches,
-                          double *bytes_per_launch);
+                          double *bytes_per_launch, double *flops_per_launch);
 
 /* r = b - A x on the finest level in FP64 and rnorm = ||r||_2, without allocating
  * anything. The paper has no counterpart: this entry point is for callers that cannot

@@ -23,160 +23,9 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "sweep.cuh"
+
 namespace mgk {
-
-template <typename T>
-struct Ar;
-template <>
-struct Ar<double> {
-    static constexpr bool kStoredDinv = true;
-    static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
-    static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
-    static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
-    static __device__ __forceinline__ double mac(double s, double a, double b) { return __fma_rn(a, b, s); }
-    static __device__ __forceinline__ double rcp(double a) { return __ddiv_rn(1.0, a); }
-};
-template <>
-struct Ar<float> {
-    static constexpr bool kStoredDinv = false;
-    static __device__ __forceinline__ float mul(float a, float b) { return a * b; }
-    static __device__ __forceinline__ float add(float a, float b) { return a + b; }
-    static __device__ __forceinline__ float sub(float a, float b) { return a - b; }
-    static __device__ __forceinline__ float mac(float s, float a, float b) { return fmaf(a, b, s); }
-    static __device__ __forceinline__ float rcp(float a) { return __fdiv_rn(1.0f, a); }
-};
-
-// Sweep modes: what a pass does with s = (A x)_i and dinv = 1 / a_ii.
-enum SweepMode {
-    SW_RESID = 0,    // out = b - s
-    SW_JACOBI = 1,   // out = x + c1*(dinv*(b - s))                 (c1 = omega)
-    SW_CHEBF = 2,    // d = c1*(dinv*(b - s)); out = x + d           (first Chebyshev step)
-    SW_CHEB = 3,     // d = c1*d + c2*(dinv*(b - s)); out = x + d    (later steps)
-    SW_JACOBI_Z = 4, // x = 0: out = c1*(dinv*b)
-    SW_CHEBF_Z = 5,  // x = 0: d = c1*(dinv*b); out = d
-};
-
-template <int MODE>
-struct IsZero {
-    static constexpr bool value = MODE == SW_JACOBI_Z || MODE == SW_CHEBF_Z;
-};
-
-struct DiaOffs {
-    int32_t o[27];
-};
-
-// Matrix view for the kernels (values of type T).
-template <typename T>
-struct MatView {
-    const T *val;          // DIA/ELL: K*ld (slot-major); CSR: nnz
-    const int32_t *col;    // ELL: K*ld; CSR: nnz
-    const int64_t *rowptr; // CSR
-    const T *dinv;         // 1 / a_ii (FP64 levels)
-    int64_t ld;
-    int K;
-    int center;            // DIA: slot of the diagonal
-    DiaOffs offs;          // DIA: column = row + offs.o[k]
-};
-
-template <typename T, int MODE>
-__device__ __forceinline__ void sweep_out(int i, T s, T dinv, T xi, const T *__restrict__ b, T *__restrict__ out,
-                                          T *__restrict__ d, T c1, T c2)
-{
-    using A = Ar<T>;
-    T bi = b[i];
-    if (MODE == SW_RESID) {
-        out[i] = A::sub(bi, s);
-    } else if (MODE == SW_JACOBI) {
-        T r = A::sub(bi, s);
-        out[i] = A::add(xi, A::mul(c1, A::mul(dinv, r)));
-    } else if (MODE == SW_CHEBF) {
-        T r = A::sub(bi, s);
-        T dd = A::mul(c1, A::mul(dinv, r));
-        d[i] = dd;
-        out[i] = A::add(xi, dd);
-    } else if (MODE == SW_CHEB) {
-        T r = A::sub(bi, s);
-        T dd = A::add(A::mul(c1, d[i]), A::mul(c2, A::mul(dinv, r)));
-        d[i] = dd;
-        out[i] = A::add(xi, dd);
-    } else if (MODE == SW_JACOBI_Z) {
-        out[i] = A::mul(c1, A::mul(dinv, bi));
-    } else {  // SW_CHEBF_Z
-        T dd = A::mul(c1, A::mul(dinv, bi));
-        d[i] = dd;
-        out[i] = dd;
-    }
-}
-
-// DIA: column of slot k is i + offs.o[k]. x points at element 0 of a buffer padded on
-// both sides by at least max|offs|, so no bounds test is needed (slots of missing
-// neighbours hold 0 and read a finite padded or interior value).
-template <typename T, int K, int MODE>
-__global__ void __launch_bounds__(256) k_dia_sweep(MatView<T> A, int n, const T *__restrict__ x,
-                                                   const T *__restrict__ b, T *__restrict__ out,
-                                                   T *__restrict__ d, T c1, T c2)
-{
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    constexpr int C = K / 2;  // the stored diagonals are symmetric about the main one
-    if (IsZero<MODE>::value) {
-        T dinv = Ar<T>::kStoredDinv ? __ldcs(A.dinv + i) : Ar<T>::rcp(__ldcs(A.val + (int64_t)C * A.ld + i));
-        sweep_out<T, MODE>(i, T(0), dinv, T(0), b, out, d, c1, c2);
-        return;
-    }
-    T a[K], xv[K];
-#pragma unroll
-    for (int k = 0; k < K; k++) a[k] = __ldcs(A.val + (int64_t)k * A.ld + i);
-#pragma unroll
-    for (int k = 0; k < K; k++) xv[k] = __ldg(x + i + A.offs.o[k]);
-    T s = T(0);
-#pragma unroll
-    for (int k = 0; k < K; k++) s = Ar<T>::mac(s, a[k], xv[k]);
-    T dinv = Ar<T>::kStoredDinv ? __ldcs(A.dinv + i) : Ar<T>::rcp(a[C]);
-    sweep_out<T, MODE>(i, s, dinv, xv[C], b, out, d, c1, c2);
-}
-
-// ELL with explicit columns; padded slots hold column i and value 0.
-template <typename T, int MODE>
-__global__ void __launch_bounds__(256) k_ell_sweep(MatView<T> A, int n, const T *__restrict__ x,
-                                                   const T *__restrict__ b, T *__restrict__ out,
-                                                   T *__restrict__ d, T c1, T c2)
-{
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    T s = T(0), diag = T(0);
-    if (!IsZero<MODE>::value || !Ar<T>::kStoredDinv) {
-        for (int k = 0; k < A.K; k++) {
-            int c = __ldcs(A.col + (int64_t)k * A.ld + i);
-            T v = __ldcs(A.val + (int64_t)k * A.ld + i);
-            if (c == i && diag == T(0)) diag = v;
-            if (!IsZero<MODE>::value) s = Ar<T>::mac(s, v, __ldg(x + c));
-        }
-    }
-    T dinv = Ar<T>::kStoredDinv ? __ldcs(A.dinv + i) : Ar<T>::rcp(diag);
-    sweep_out<T, MODE>(i, s, dinv, IsZero<MODE>::value ? T(0) : x[i], b, out, d, c1, c2);
-}
-
-template <typename T, int MODE>
-__global__ void __launch_bounds__(256) k_csr_sweep(MatView<T> A, int n, const T *__restrict__ x,
-                                                   const T *__restrict__ b, T *__restrict__ out,
-                                                   T *__restrict__ d, T c1, T c2)
-{
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    T s = T(0), diag = T(0);
-    if (!IsZero<MODE>::value || !Ar<T>::kStoredDinv) {
-        int64_t k0 = A.rowptr[i], k1 = A.rowptr[i + 1];
-        for (int64_t k = k0; k < k1; k++) {
-            int c = A.col[k];
-            T v = A.val[k];
-            if (c == i) diag = v;
-            if (!IsZero<MODE>::value) s = Ar<T>::mac(s, v, __ldg(x + c));
-        }
-    }
-    T dinv = Ar<T>::kStoredDinv ? A.dinv[i] : Ar<T>::rcp(diag);
-    sweep_out<T, MODE>(i, s, dinv, IsZero<MODE>::value ? T(0) : x[i], b, out, d, c1, c2);
-}
 
 // ------------------------------------------------------------------------------------
 // Q1 grid transfers on the structured grid (no stored matrix)
@@ -208,6 +57,8 @@ __global__ void __launch_bounds__(256) k_restrict_q1(const T *__restrict__ r, T 
 
 // Prolongation and correction x_f += P x_c: fine vertex v takes the coarse vertices V
 // with |v - 2V| <= 1 per axis (boundary ones are zero and skipped), ascending coarse index.
+// Every such V carries the same weight prod_d (1 or 1/2) = 2^-(number of odd coordinates
+// of v), taken from a table: no floating-point work beyond one multiply-add per term.
 template <typename T, int DIM>
 __global__ void __launch_bounds__(256) k_prolong_q1(const T *__restrict__ xc, T *__restrict__ xf, int Nc)
 {
@@ -215,23 +66,18 @@ __global__ void __launch_bounds__(256) k_prolong_q1(const T *__restrict__ xc, T 
     int nf = DIM == 2 ? nf1 * nf1 : nf1 * nf1 * nf1;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nf) return;
-    int v0 = i % nf1 + 1, v1 = (i / nf1) % nf1 + 1, v2 = DIM == 3 ? i / (nf1 * nf1) + 1 : 0;
+    int v0 = i % nf1 + 1, v1 = (i / nf1) % nf1 + 1, v2 = DIM == 3 ? i / (nf1 * nf1) + 1 : 2;
+    int odd = (v0 & 1) + (v1 & 1) + (DIM == 3 ? (v2 & 1) : 0);
+    const T w = odd == 0 ? T(1) : (odd == 1 ? T(0.5) : (odd == 2 ? T(0.25) : T(0.125)));
+    int x0 = max(v0 >> 1, 1), x1 = min((v0 + 1) >> 1, Nc - 1);
+    int y0 = max(v1 >> 1, 1), y1 = min((v1 + 1) >> 1, Nc - 1);
+    int z0 = DIM == 3 ? max(v2 >> 1, 1) : 1, z1 = DIM == 3 ? min((v2 + 1) >> 1, Nc - 1) : 1;
     T t = T(0);
-    int zlo = DIM == 3 ? v2 / 2 : 0, zhi = DIM == 3 ? (v2 + 1) / 2 : 0;
-    for (int Z = zlo; Z <= zhi; Z++) {
-        if (DIM == 3 && (Z <= 0 || Z >= Nc)) continue;
-        T wz = DIM == 3 ? (v2 == 2 * Z ? T(1) : T(0.5)) : T(1);
-        for (int Y = v1 / 2; Y <= (v1 + 1) / 2; Y++) {
-            if (Y <= 0 || Y >= Nc) continue;
-            T wy = v1 == 2 * Y ? T(1) : T(0.5);
-            for (int X = v0 / 2; X <= (v0 + 1) / 2; X++) {
-                if (X <= 0 || X >= Nc) continue;
-                T wx = v0 == 2 * X ? T(1) : T(0.5);
-                int64_t J = (X - 1) + (int64_t)nc1 * ((Y - 1) + (DIM == 3 ? (int64_t)nc1 * (Z - 1) : 0));
-                t = Ar<T>::mac(t, (wx * wy) * wz, __ldg(xc + J));
-            }
+    for (int Z = z0; Z <= z1; Z++)
+        for (int Y = y0; Y <= y1; Y++) {
+            int64_t row = (int64_t)nc1 * ((Y - 1) + (DIM == 3 ? (int64_t)nc1 * (Z - 1) : 0)) - 1;
+            for (int X = x0; X <= x1; X++) t = Ar<T>::mac(t, w, __ldg(xc + row + X));
         }
-    }
     xf[i] = Ar<T>::add(xf[i], t);
 }
 
@@ -290,6 +136,52 @@ __global__ void k_coarse_solve(const double *__restrict__ lu, const int *__restr
     }
     __syncthreads();
     if (t < n) x[t] = (T)xs[t];
+}
+
+// The same solve for n <= 64 by one warp with the factors in shared memory: lane l owns
+// rows l and l + 32 and their running sums; one __syncwarp per column.
+template <typename T>
+__global__ void __launch_bounds__(32) k_coarse_solve_warp(const double *__restrict__ lu, const int *__restrict__ piv,
+                                                          int n, const T *__restrict__ b, T *__restrict__ x)
+{
+    __shared__ double L[64 * 64];
+    __shared__ double xs[64];
+    int l = threadIdx.x;
+    for (int k = l; k < n * n; k += 32) L[k] = lu[k];
+    for (int k = l; k < n; k += 32) xs[k] = (double)b[k];
+    __syncwarp();
+    if (l == 0)
+        for (int k = 0; k < n; k++) {
+            int p = piv[k];
+            if (p != k) {
+                double tmp = xs[k];
+                xs[k] = xs[p];
+                xs[p] = tmp;
+            }
+        }
+    __syncwarp();
+    int r0 = l, r1 = l + 32;
+    double s0 = 0.0, s1 = 0.0;
+    for (int j = 0; j < n; j++) {  // forward: x_i -= sum_{j<i} l_ij x_j, ascending j
+        if (j == r0) xs[j] = __dsub_rn(xs[j], s0);
+        if (j == r1) xs[j] = __dsub_rn(xs[j], s1);
+        __syncwarp();
+        double xj = xs[j];
+        if (r0 > j && r0 < n) s0 = __dadd_rn(s0, __dmul_rn(L[r0 * n + j], xj));
+        if (r1 > j && r1 < n) s1 = __dadd_rn(s1, __dmul_rn(L[r1 * n + j], xj));
+        __syncwarp();
+    }
+    s0 = s1 = 0.0;
+    for (int j = n - 1; j >= 0; j--) {  // backward: descending j
+        if (j == r0) xs[j] = __ddiv_rn(__dsub_rn(xs[j], s0), L[j * n + j]);
+        if (j == r1) xs[j] = __ddiv_rn(__dsub_rn(xs[j], s1), L[j * n + j]);
+        __syncwarp();
+        double xj = xs[j];
+        if (r0 < j) s0 = __dadd_rn(s0, __dmul_rn(L[r0 * n + j], xj));
+        if (r1 < j) s1 = __dadd_rn(s1, __dmul_rn(L[r1 * n + j], xj));
+        __syncwarp();
+    }
+    for (int k = l; k < n; k += 32) x[k] = (T)xs[k];
 }
 
 // ------------------------------------------------------------------------------------

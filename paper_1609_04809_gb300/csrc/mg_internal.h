@@ -63,13 +63,15 @@ struct LevelD {
 struct Prof {
     struct Rec {
         int kclass, level;
-        double bytes;
+        double bytes, flops;
         cudaEvent_t e0, e1;
     };
     double ms_total[MG_K_COUNT * MG_MAX_LEVELS] = {};
     int64_t launches[MG_K_COUNT * MG_MAX_LEVELS] = {};
     double bytes_total[MG_K_COUNT * MG_MAX_LEVELS] = {};
-    void begin(cudaStream_t s, int kclass, int level, double bytes, std::vector<Rec> *sink, bool capturing);
+    double flops_total[MG_K_COUNT * MG_MAX_LEVELS] = {};
+    void begin(cudaStream_t s, int kclass, int level, double bytes, double flops, std::vector<Rec> *sink,
+               bool capturing);
     void end(cudaStream_t s, std::vector<Rec> *sink, bool capturing);
     void collect(std::vector<Rec> &recs);
     void release(std::vector<Rec> &recs);
@@ -79,6 +81,7 @@ struct Prof {
             ms_total[k] = 0.0;
             launches[k] = 0;
             bytes_total[k] = 0.0;
+            flops_total[k] = 0.0;
         }
     }
 };

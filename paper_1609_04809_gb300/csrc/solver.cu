@@ -141,12 +141,14 @@ static MatView<T> view(const DevMat &m)
 // ------------------------------------------------------------------------------------
 // Profiling: CUDA events around launches
 // ------------------------------------------------------------------------------------
-void mgi::Prof::begin(cudaStream_t s, int kclass, int level, double bytes, std::vector<Rec> *sink, bool capturing)
+void mgi::Prof::begin(cudaStream_t s, int kclass, int level, double bytes, double flops, std::vector<Rec> *sink,
+                      bool capturing)
 {
     Rec r;
     r.kclass = kclass;
     r.level = level;
     r.bytes = bytes;
+    r.flops = flops;
     CK(cudaEventCreate(&r.e0));
     CK(cudaEventCreate(&r.e1));
     if (capturing)
@@ -174,6 +176,7 @@ void mgi::Prof::collect(std::vector<Rec> &recs)
         ms_total[k] += ms;
         launches[k] += 1;
         bytes_total[k] += r.bytes;
+        flops_total[k] += r.flops;
     }
 }
 
@@ -260,11 +263,12 @@ struct LaunchScope {
     mg_hierarchy *h;
     cudaStream_t s;
     bool on;
-    LaunchScope(mg_hierarchy *h_, cudaStream_t s_, int kclass, int level, double bytes) : h(h_), s(s_)
+    LaunchScope(mg_hierarchy *h_, cudaStream_t s_, int kclass, int level, double bytes, double flops = 0.0)
+        : h(h_), s(s_)
     {
         if (h->counting) h->kernels_per_cycle++;
         on = h->profiling && ((h->prof_class_mask >> kclass) & 1) && ((h->prof_level_mask >> level) & 1);
-        if (on) h->prof.begin(s, kclass, level, bytes, h->sink, h->capturing);
+        if (on) h->prof.begin(s, kclass, level, bytes, flops, h->sink, h->capturing);
     }
     ~LaunchScope() noexcept(false)
     {
@@ -325,7 +329,11 @@ static void sweep(mg_hierarchy *h, int l, int mode, const T *x, const T *b, T *o
         if (mode == SW_CHEBF) bytes += n * sv;
         if (mode == SW_CHEB) bytes += 2 * n * sv;
     }
-    LaunchScope ls(h, s, kclass, l, bytes);
+    // algorithmic flops: two per stored entry (a multiply-add) plus the update's operations
+    static const int kUpdateOps[6] = {1, 4, 4, 6, 2, 2};
+    double entries = L.A.fmt == MG_STORAGE_CSR ? (double)L.A.nnz : (double)L.A.K * n;
+    double flops = (zero ? 0.0 : 2.0 * entries) + kUpdateOps[mode] * n;
+    LaunchScope ls(h, s, kclass, l, bytes, flops);
     int nn = (int)L.n;
     T a = (T)c1, bb = (T)c2;
     switch (mode) {
@@ -429,9 +437,13 @@ static int enqueue_vcycle(mg_hierarchy *h, cudaStream_t s)
     {  // exact solve on the coarsest level
         LevelD &C = h->lev[0];
         LaunchScope ls(h, s, MG_K_COARSE, 0, (double)h->n0 * h->n0 * 8 + 2.0 * h->n0 * sizeof(T));
-        int thr = (int)round_up(h->n0, 32);
-        k_coarse_solve<T><<<1, thr, (size_t)h->n0 * sizeof(double), s>>>(h->lu, h->piv, h->n0, (const T *)C.b,
-                                                                           (T *)C.x[0]);
+        if (h->n0 <= 64) {
+            k_coarse_solve_warp<T><<<1, 32, 0, s>>>(h->lu, h->piv, h->n0, (const T *)C.b, (T *)C.x[0]);
+        } else {
+            int thr = (int)round_up(h->n0, 32);
+            k_coarse_solve<T><<<1, thr, (size_t)h->n0 * sizeof(double), s>>>(h->lu, h->piv, h->n0, (const T *)C.b,
+                                                                               (T *)C.x[0]);
+        }
         CKL();
         cur[0] = 0;
     }
@@ -454,7 +466,8 @@ static void enqueue_outer(mg_hierarchy *h, cudaStream_t s)
     const DevMat &A = h->A64;
     int n = (int)F.n;
     double bytes = mat_bytes(A, 8) + 16.0 * n + (double)n * sizeof(T);
-    LaunchScope ls(h, s, MG_K_OUTER, h->Lf, bytes);
+    double entries = A.fmt == MG_STORAGE_CSR ? (double)A.nnz : (double)A.K * n;
+    LaunchScope ls(h, s, MG_K_OUTER, h->Lf, bytes, 2.0 * entries + 3.0 * n);
     MatView<double> v = view<double>(A);
     unsigned g = grid_for(n);
     T *r = (T *)F.b;
@@ -1322,7 +1335,7 @@ extern "C" mg_status mg_profile_enable(mg_hierarchy *h, int enable, unsigned cla
 }
 
 extern "C" mg_status mg_profile_read(const mg_hierarchy *h, int kclass, int level, double *ms_total, int64_t *launches,
-                                     double *bytes_per_launch)
+                                     double *bytes_per_launch, double *flops_per_launch)
 {
     if (!h || kclass < 0 || kclass >= MG_K_COUNT || level < 0 || level >= MG_MAX_LEVELS) {
         g_err = "bad arguments";
@@ -1332,6 +1345,7 @@ extern "C" mg_status mg_profile_read(const mg_hierarchy *h, int kclass, int leve
     if (ms_total) *ms_total = h->prof.ms_total[k];
     if (launches) *launches = h->prof.launches[k];
     if (bytes_per_launch) *bytes_per_launch = h->prof.launches[k] ? h->prof.bytes_total[k] / h->prof.launches[k] : 0.0;
+    if (flops_per_launch) *flops_per_launch = h->prof.launches[k] ? h->prof.flops_total[k] / h->prof.launches[k] : 0.0;
     return MG_OK;
 }
 

@@ -1,0 +1,166 @@
+// sweep.cuh -- the level-operator sweeps of the multigrid V-cycle (internal).
+//
+// One thread per row; the row's stored entries are summed in ascending column order
+// (one rounded fused multiply-add each in FP64) and the smoother update is applied in
+// the same pass. See kernels.cuh for the storage formats and the FP64 rounding rules.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mgk {
+
+template <typename T>
+struct Ar;
+template <>
+struct Ar<double> {
+    static constexpr bool kStoredDinv = true;
+    static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+    static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+    static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+    static __device__ __forceinline__ double mac(double s, double a, double b) { return __fma_rn(a, b, s); }
+    static __device__ __forceinline__ double rcp(double a) { return __ddiv_rn(1.0, a); }
+};
+template <>
+struct Ar<float> {
+    static constexpr bool kStoredDinv = false;
+    static __device__ __forceinline__ float mul(float a, float b) { return a * b; }
+    static __device__ __forceinline__ float add(float a, float b) { return a + b; }
+    static __device__ __forceinline__ float sub(float a, float b) { return a - b; }
+    static __device__ __forceinline__ float mac(float s, float a, float b) { return fmaf(a, b, s); }
+    static __device__ __forceinline__ float rcp(float a) { return __fdiv_rn(1.0f, a); }
+};
+
+// Sweep modes: what a pass does with s = (A x)_i and dinv = 1 / a_ii.
+enum SweepMode {
+    SW_RESID = 0,    // out = b - s
+    SW_JACOBI = 1,   // out = x + c1*(dinv*(b - s))                 (c1 = omega)
+    SW_CHEBF = 2,    // d = c1*(dinv*(b - s)); out = x + d           (first Chebyshev step)
+    SW_CHEB = 3,     // d = c1*d + c2*(dinv*(b - s)); out = x + d    (later steps)
+    SW_JACOBI_Z = 4, // x = 0: out = c1*(dinv*b)
+    SW_CHEBF_Z = 5,  // x = 0: d = c1*(dinv*b); out = d
+};
+
+template <int MODE>
+struct IsZero {
+    static constexpr bool value = MODE == SW_JACOBI_Z || MODE == SW_CHEBF_Z;
+};
+
+struct DiaOffs {
+    int32_t o[27];
+};
+
+// Matrix view for the kernels (values of type T).
+template <typename T>
+struct MatView {
+    const T *val;          // DIA/ELL: K*ld (slot-major); CSR: nnz
+    const int32_t *col;    // ELL: K*ld; CSR: nnz
+    const int64_t *rowptr; // CSR
+    const T *dinv;         // 1 / a_ii (FP64 levels)
+    int64_t ld;
+    int K;
+    int center;            // DIA: slot of the diagonal
+    DiaOffs offs;          // DIA: column = row + offs.o[k]
+};
+
+template <typename T, int MODE>
+__device__ __forceinline__ void sweep_out(int i, T s, T dinv, T xi, const T *__restrict__ b, T *__restrict__ out,
+                                          T *__restrict__ d, T c1, T c2)
+{
+    using A = Ar<T>;
+    T bi = b[i];
+    if (MODE == SW_RESID) {
+        out[i] = A::sub(bi, s);
+    } else if (MODE == SW_JACOBI) {
+        T r = A::sub(bi, s);
+        out[i] = A::add(xi, A::mul(c1, A::mul(dinv, r)));
+    } else if (MODE == SW_CHEBF) {
+        T r = A::sub(bi, s);
+        T dd = A::mul(c1, A::mul(dinv, r));
+        d[i] = dd;
+        out[i] = A::add(xi, dd);
+    } else if (MODE == SW_CHEB) {
+        T r = A::sub(bi, s);
+        T dd = A::add(A::mul(c1, d[i]), A::mul(c2, A::mul(dinv, r)));
+        d[i] = dd;
+        out[i] = A::add(xi, dd);
+    } else if (MODE == SW_JACOBI_Z) {
+        out[i] = A::mul(c1, A::mul(dinv, bi));
+    } else {  // SW_CHEBF_Z
+        T dd = A::mul(c1, A::mul(dinv, bi));
+        d[i] = dd;
+        out[i] = dd;
+    }
+}
+
+// DIA: column of slot k is i + offs.o[k]. x points at element 0 of a buffer padded on
+// both sides by at least max|offs|, so no bounds test is needed (slots of missing
+// neighbours hold 0 and read a finite padded or interior value).
+template <typename T, int K, int MODE>
+__global__ void __launch_bounds__(256) k_dia_sweep(MatView<T> A, int n, const T *__restrict__ x,
+                                                   const T *__restrict__ b, T *__restrict__ out,
+                                                   T *__restrict__ d, T c1, T c2)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    constexpr int C = K / 2;  // the stored diagonals are symmetric about the main one
+    if (IsZero<MODE>::value) {
+        T dinv = Ar<T>::kStoredDinv ? __ldcs(A.dinv + i) : Ar<T>::rcp(__ldcs(A.val + (int64_t)C * A.ld + i));
+        sweep_out<T, MODE>(i, T(0), dinv, T(0), b, out, d, c1, c2);
+        return;
+    }
+    T a[K], xv[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) a[k] = __ldcs(A.val + (int64_t)k * A.ld + i);
+#pragma unroll
+    for (int k = 0; k < K; k++) xv[k] = __ldg(x + i + A.offs.o[k]);
+    T s = T(0);
+#pragma unroll
+    for (int k = 0; k < K; k++) s = Ar<T>::mac(s, a[k], xv[k]);
+    T dinv = Ar<T>::kStoredDinv ? __ldcs(A.dinv + i) : Ar<T>::rcp(a[C]);
+    sweep_out<T, MODE>(i, s, dinv, xv[C], b, out, d, c1, c2);
+}
+
+// ELL with explicit columns; padded slots hold column i and value 0.
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256) k_ell_sweep(MatView<T> A, int n, const T *__restrict__ x,
+                                                   const T *__restrict__ b, T *__restrict__ out,
+                                                   T *__restrict__ d, T c1, T c2)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    T s = T(0), diag = T(0);
+    if (!IsZero<MODE>::value || !Ar<T>::kStoredDinv) {
+        for (int k = 0; k < A.K; k++) {
+            int c = __ldcs(A.col + (int64_t)k * A.ld + i);
+            T v = __ldcs(A.val + (int64_t)k * A.ld + i);
+            if (c == i && diag == T(0)) diag = v;
+            if (!IsZero<MODE>::value) s = Ar<T>::mac(s, v, __ldg(x + c));
+        }
+    }
+    T dinv = Ar<T>::kStoredDinv ? __ldcs(A.dinv + i) : Ar<T>::rcp(diag);
+    sweep_out<T, MODE>(i, s, dinv, IsZero<MODE>::value ? T(0) : x[i], b, out, d, c1, c2);
+}
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256) k_csr_sweep(MatView<T> A, int n, const T *__restrict__ x,
+                                                   const T *__restrict__ b, T *__restrict__ out,
+                                                   T *__restrict__ d, T c1, T c2)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    T s = T(0), diag = T(0);
+    if (!IsZero<MODE>::value || !Ar<T>::kStoredDinv) {
+        int64_t k0 = A.rowptr[i], k1 = A.rowptr[i + 1];
+        for (int64_t k = k0; k < k1; k++) {
+            int c = A.col[k];
+            T v = A.val[k];
+            if (c == i) diag = v;
+            if (!IsZero<MODE>::value) s = Ar<T>::mac(s, v, __ldg(x + c));
+        }
+    }
+    T dinv = Ar<T>::kStoredDinv ? A.dinv[i] : Ar<T>::rcp(diag);
+    sweep_out<T, MODE>(i, s, dinv, IsZero<MODE>::value ? T(0) : x[i], b, out, d, c1, c2);
+}
+
+}  // namespace mgk

@@ -84,7 +84,7 @@ SIGNATURES = {
     "mg_export_operator": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P(ctypes.c_int64),
                                           _P(ctypes.c_int64), _P(ctypes.c_int64), _P(ctypes.c_int32), _dp]),
     "mg_profile_enable": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_uint, ctypes.c_uint]),
-    "mg_profile_read": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _dp, _P(ctypes.c_int64), _dp]),
+    "mg_profile_read": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _dp, _P(ctypes.c_int64), _dp, _dp]),
     "mg_residual_norm_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _vp, _dp]),
     "mg_last_error": (ctypes.c_char_p, []),
 }
@@ -302,9 +302,11 @@ def mg_profile_enable(h, enable=True, classes=None, levels=None):
 
 
 def mg_profile_read(h, kclass, level):
-    ms, n, b = ctypes.c_double(0), ctypes.c_int64(0), ctypes.c_double(0)
-    _check(lib().mg_profile_read(h, kclass, level, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(b)))
-    return ms.value, n.value, b.value
+    """(total ms, launches, algorithmic bytes per launch, algorithmic flops per launch)."""
+    ms, n, b, f = ctypes.c_double(0), ctypes.c_int64(0), ctypes.c_double(0), ctypes.c_double(0)
+    _check(lib().mg_profile_read(h, kclass, level, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(b),
+                                 ctypes.byref(f)))
+    return ms.value, n.value, b.value, f.value
 
 
 # ---------------------------------------------------------------------------------

@@ -184,10 +184,11 @@ def test_profiled_launch_counts(orc):
     H.cycle(b, x, 3)
     total = sum(mg.mg_profile_read(H.h, k, l)[1] for k in range(mg.MG_K_COUNT) for l in range(L))
     assert total == 3 * H.info()["kernels_per_cycle"]
-    ms, cnt, byts = mg.mg_profile_read(H.h, mg.MG_K_SMOOTH, L - 1)
+    ms, cnt, byts, flops = mg.mg_profile_read(H.h, mg.MG_K_SMOOTH, L - 1)
     # 21 stored diagonals (the face-neighbour couplings of 3D Q1 vanish) plus vectors
     assert H.info()["storage"][L - 1] == mg.MG_STORAGE_DIA
     assert cnt == 3 * 3 and ms > 0 and byts >= 21 * 15 ** 3 * 8 + 3 * 15 ** 3 * 8
+    assert flops >= 2 * 21 * 15 ** 3
 
 
 @pytest.mark.parametrize("dim,elem,N,L,sm", [(3, 0, 32, 4, 1), (3, 1, 16, 4, 0), (2, 0, 128, 6, 0)])
