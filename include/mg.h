@@ -226,6 +226,71 @@ mg_status mg_profile_read(const mg_hierarchy *h, int kclass, int level, double *
 mg_status mg_residual_norm_noalloc(mg_hierarchy *h, const double *b_dev, const double *x_dev, double *r_dev,
                                    double *rnorm);
 
+/* ---------------------------------------------------------------------------------
+ * Serving: a request loop that solves many Q1 Poisson problems (k = 1) of different
+ * sizes and dimensions with continuous batching, in mixed precision (FP32 V-cycle
+ * inside FP64 defect correction).
+ *
+ * The server reserves hbm_budget_bytes of device memory once (through dev, as for
+ * mg_setup) and keeps everything inside it: one operator set per problem shape
+ * (dim, n_cells, n_levels), shared by all requests of that shape and cached while
+ * memory allows, and one workspace per admitted request. A submitted request waits
+ * until a slot (max_active) and its memory are free, is then admitted at the next
+ * iteration boundary, and leaves as soon as it converges; requests in flight share
+ * every kernel launch: one launch per V-cycle phase covers that phase of all admitted
+ * requests (tiles of 256 * rows_per_thread rows, blocks_per_sm persistent blocks per
+ * SM), replayed as a CUDA graph. A request's result does not depend on the other
+ * requests in flight (its arithmetic and reduction order are its own).
+ * Requirements: element MG_Q1, k_cell NULL, n_levels >= 2, coarsest level <= 64 DOFs,
+ * options.nu_pre >= 1, Chebyshev degree <= 4. The options are the server's; every
+ * request uses them with options.precision forced to MG_MIXED.
+ * Threads: one scheduler thread and one setup thread (host assembly of new shapes and
+ * of right-hand sides given as mg_rhs) per server. Entry points are thread safe.
+ * --------------------------------------------------------------------------------- */
+typedef struct mg_server mg_server;
+
+typedef struct {
+    size_t hbm_budget_bytes; /* device memory reserved at creation and never exceeded */
+    int max_active;          /* requests resident at once (1..4096) */
+    int rows_per_thread;     /* tile shape: 1, 2, 4 or 8 rows per thread (256 threads) */
+    int blocks_per_sm;       /* persistent blocks per SM of each phase launch (1..8) */
+    mg_options options;      /* smoother, nu_pre/nu_post, max_iters, ... */
+} mg_serve_config;
+
+typedef struct {
+    uint64_t completed;          /* requests finished (converged or max_iters) */
+    uint64_t cycles;             /* batched iterations run */
+    int active;                  /* admitted now */
+    int queued;                  /* submitted, not admitted */
+    int operator_sets;           /* cached problem shapes */
+    double mean_batch;           /* mean admitted requests per iteration */
+    double p50_ms, p99_ms, max_ms; /* latency submit -> completion of finished requests */
+    double solves_per_s;         /* completed / (last completion - first submission) */
+    size_t device_bytes_in_use, device_bytes_peak;
+} mg_serve_stats;
+
+/* Defaults: 4 GiB budget, 256 slots, 4 rows per thread, 4 blocks per SM, Chebyshev
+ * degree 2 with one application before and after the coarse correction. */
+void mg_serve_config_default(mg_serve_config *cfg);
+mg_status mg_serve_create(const mg_serve_config *cfg, const mg_device *dev, mg_server **out);
+/* Submit A x = b with b copied from b_host (n doubles, host) before returning; the
+ * ticket identifies the request. Relative tolerance on ||b - A x||_2 / ||b||_2. */
+mg_status mg_serve_submit(mg_server *s, const mg_problem *p, const double *b_host, double rel_tol, uint64_t *ticket);
+/* Submit with the right-hand side given by f; the load vector is assembled on the
+ * server's setup thread. */
+mg_status mg_serve_submit_rhs(mg_server *s, const mg_problem *p, const mg_rhs *f, double rel_tol, uint64_t *ticket);
+/* MG_PENDING while the request runs; otherwise its final status (MG_OK, MG_ENOCONV,
+ * MG_EBUDGET, ...), with x copied to x_host (n doubles, may be NULL) and the V-cycle
+ * count in iters. A finished request is forgotten after it has been returned once. */
+mg_status mg_serve_poll(mg_server *s, uint64_t ticket, double *x_host, int *iters);
+/* Blocking form of mg_serve_poll; MG_ETIMEOUT after timeout_s seconds. res_hist (may be
+ * NULL) receives up to hist_len relative residuals, one per iteration. */
+mg_status mg_serve_wait(mg_server *s, uint64_t ticket, double timeout_s, double *x_host, int *iters,
+                        double *res_hist, int hist_len);
+mg_status mg_serve_get_stats(mg_server *s, mg_serve_stats *out);
+/* Stops the threads (requests in flight are dropped) and releases the budget. */
+mg_status mg_serve_destroy(mg_server *s);
+
 /* Thread-local description of the last error on this thread. */
 const char *mg_last_error(void);
 

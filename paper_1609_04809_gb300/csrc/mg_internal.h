@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -87,3 +88,53 @@ struct Prof {
 };
 
 }  // namespace mgi
+
+// A level hierarchy: device operators of every level, the coarsest LU factors, and
+// (unless with_vectors is false) the vectors and CUDA graphs of the single-solve path.
+struct mg_hierarchy {
+    mg_problem prob{};
+    mg_options opt{};
+    int dim = 0, elem = 0, nlev = 0, Lf = 0;
+    bool mixed = false;
+    int inner_size = 8;  // bytes per inner-precision value
+    mg_device dev{};
+    bool own_alloc = false;
+    cudaStream_t caller = nullptr, s = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    int device = 0;
+    mgi::Slab slab;
+    std::vector<mgi::LevelD> lev;
+    mgi::DevMat A64;               // finest FP64 operator for the outer residual
+    double *x64 = nullptr;      // interior pointer of the padded FP64 iterate
+    double *b64 = nullptr;
+    int64_t pad64 = 0;
+    double *lu = nullptr;
+    int *piv = nullptr;
+    int *d_info = nullptr;
+    int n0 = 0;
+    double *partial = nullptr;
+    unsigned *ticket = nullptr;
+    double *norm2 = nullptr;
+    double *h_norm2 = nullptr;  // pinned
+    cudaGraphExec_t g_r = nullptr, g_v = nullptr;
+    bool capturing = false;
+    // profiling
+    bool profiling = false;
+    unsigned prof_class_mask = ~0u, prof_level_mask = ~0u;
+    mgi::Prof prof;
+    std::vector<mgi::Prof::Rec> rec_r, rec_v, rec_eager;
+    std::vector<mgi::Prof::Rec> *sink = nullptr;
+    int kernels_per_cycle = 0;
+    int counting = 0;  // counts launches while > 0
+    bool with_vectors = true;  // false: operators only (serving keeps vectors per request)
+    std::mutex mu;
+
+    ~mg_hierarchy();
+};
+
+namespace mgi {
+// Build h from the problem on the current device (host assembly, device formats, LU).
+void build_hierarchy(mg_hierarchy *h, const mg_problem *p, const mg_options *o, const mg_device *dev,
+                     bool with_vectors);
+}  // namespace mgi
+

@@ -192,46 +192,6 @@ void mgi::Prof::release(std::vector<Rec> &recs)
 // ------------------------------------------------------------------------------------
 // The hierarchy
 // ------------------------------------------------------------------------------------
-struct mg_hierarchy {
-    mg_problem prob{};
-    mg_options opt{};
-    int dim = 0, elem = 0, nlev = 0, Lf = 0;
-    bool mixed = false;
-    int inner_size = 8;  // bytes per inner-precision value
-    mg_device dev{};
-    bool own_alloc = false;
-    cudaStream_t caller = nullptr, s = nullptr;
-    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
-    int device = 0;
-    mgi::Slab slab;
-    std::vector<LevelD> lev;
-    DevMat A64;                 // finest FP64 operator for the outer residual
-    double *x64 = nullptr;      // interior pointer of the padded FP64 iterate
-    double *b64 = nullptr;
-    int64_t pad64 = 0;
-    double *lu = nullptr;
-    int *piv = nullptr;
-    int *d_info = nullptr;
-    int n0 = 0;
-    double *partial = nullptr;
-    unsigned *ticket = nullptr;
-    double *norm2 = nullptr;
-    double *h_norm2 = nullptr;  // pinned
-    cudaGraphExec_t g_r = nullptr, g_v = nullptr;
-    bool capturing = false;
-    // profiling
-    bool profiling = false;
-    unsigned prof_class_mask = ~0u, prof_level_mask = ~0u;
-    mgi::Prof prof;
-    std::vector<mgi::Prof::Rec> rec_r, rec_v, rec_eager;
-    std::vector<mgi::Prof::Rec> *sink = nullptr;
-    int kernels_per_cycle = 0;
-    int counting = 0;  // counts launches while > 0
-    std::mutex mu;
-
-    ~mg_hierarchy();
-};
-
 static void destroy_graphs(mg_hierarchy *h)
 {
     if (h->g_r) cudaGraphExecDestroy(h->g_r);
@@ -814,9 +774,11 @@ static int pick_storage(const mg_options &o, int elem)
     return elem == MG_Q1 ? MG_STORAGE_DIA : MG_STORAGE_ELL;
 }
 
-static void build(mg_hierarchy *h, const mg_problem *p, const mg_options *o, const mg_device *dev)
+void mgi::build_hierarchy(mg_hierarchy *h, const mg_problem *p, const mg_options *o, const mg_device *dev,
+                          bool with_vectors)
 {
     validate_problem(p);
+    h->with_vectors = with_vectors;
     if (o->smoother != MG_JACOBI && o->smoother != MG_CHEBYSHEV) throw Error(MG_EINVAL, "bad smoother");
     if (o->smoother == MG_CHEBYSHEV && (o->cheb_degree < 1 || !(o->cheb_ratio > 1.0) || !(o->cheb_hi > 0.0) || o->power_iters < 1))
         throw Error(MG_EINVAL, "bad Chebyshev parameters");
@@ -902,13 +864,15 @@ static void build(mg_hierarchy *h, const mg_problem *p, const mg_options *o, con
             int64_t n1 = L.N - 1;
             L.pad = lf == MG_STORAGE_DIA ? round_up(dim == 3 ? n1 * n1 + n1 + 1 : n1 + 1, 64) : 0;
             int64_t ld = L.A.ld;
-            for (int c = 0; c < 2; c++) {
-                char *base = (char *)vec((size_t)(ld + 2 * L.pad) * sv);
-                L.x[c] = take ? base + (size_t)L.pad * sv : nullptr;
+            if (with_vectors) {
+                for (int c = 0; c < 2; c++) {
+                    char *base = (char *)vec((size_t)(ld + 2 * L.pad) * sv);
+                    L.x[c] = take ? base + (size_t)L.pad * sv : nullptr;
+                }
+                L.b = vec((size_t)ld * sv);
+                L.t = vec((size_t)ld * sv);
+                L.d = vec((size_t)ld * sv);
             }
-            L.b = vec((size_t)ld * sv);
-            L.t = vec((size_t)ld * sv);
-            L.d = vec((size_t)ld * sv);
             if (l >= 1) {
                 L.structured = elem == MG_Q1;
                 if (!L.structured) {
@@ -924,11 +888,11 @@ static void build(mg_hierarchy *h, const mg_problem *p, const mg_options *o, con
             h->A64 = F.A;
         }
         h->pad64 = F.pad;
-        {
+        if (with_vectors) {
             char *base = (char *)vec((size_t)(F.A.ld + 2 * h->pad64) * 8);
             h->x64 = take ? (double *)(base + (size_t)h->pad64 * 8) : nullptr;
+            h->b64 = (double *)vec((size_t)F.A.ld * 8);
         }
-        h->b64 = (double *)vec((size_t)F.A.ld * 8);
         h->lu = (double *)vec((size_t)h->n0 * h->n0 * 8);
         h->piv = (int *)vec((size_t)h->n0 * 4);
         h->d_info = (int *)vec(64);
@@ -979,6 +943,10 @@ static void build(mg_hierarchy *h, const mg_problem *p, const mg_options *o, con
         if (info) throw Error(MG_EINVAL, "coarsest matrix is singular");
     }
     // ---- launch count of one iteration, graphs ----
+    if (!with_vectors) {
+        CK(cudaStreamSynchronize(h->s));
+        return;
+    }
     h->counting = 1;
     h->kernels_per_cycle = 0;
     {
@@ -1015,7 +983,7 @@ extern "C" mg_status mg_setup(const mg_problem *p, const mg_options *o, const mg
         return MG_ENOMEM;
     }
     try {
-        build(h.get(), p, o, dev);
+        mgi::build_hierarchy(h.get(), p, o, dev, true);
     } catch (const Error &e) {
         g_err = e.msg;
         return e.st;

@@ -65,6 +65,19 @@ class mg_info(ctypes.Structure):
                 ("kernels_per_cycle", ctypes.c_int)]
 
 
+class mg_serve_config(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_active", ctypes.c_int),
+                ("rows_per_thread", ctypes.c_int), ("blocks_per_sm", ctypes.c_int), ("options", mg_options)]
+
+
+class mg_serve_stats(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_uint64), ("cycles", ctypes.c_uint64), ("active", ctypes.c_int),
+                ("queued", ctypes.c_int), ("operator_sets", ctypes.c_int), ("mean_batch", ctypes.c_double),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
+                ("solves_per_s", ctypes.c_double), ("device_bytes_in_use", ctypes.c_size_t),
+                ("device_bytes_peak", ctypes.c_size_t)]
+
+
 # every entry point declared in include/mg.h, with its ctypes signature
 _P = ctypes.POINTER
 _vp = ctypes.c_void_p
@@ -86,6 +99,16 @@ SIGNATURES = {
     "mg_profile_enable": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_uint, ctypes.c_uint]),
     "mg_profile_read": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _dp, _P(ctypes.c_int64), _dp, _dp]),
     "mg_residual_norm_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _vp, _dp]),
+    "mg_serve_config_default": (None, [_P(mg_serve_config)]),
+    "mg_serve_create": (ctypes.c_int, [_P(mg_serve_config), _P(mg_device), _P(_vp)]),
+    "mg_serve_submit": (ctypes.c_int, [_vp, _P(mg_problem), _dp, ctypes.c_double, _P(ctypes.c_uint64)]),
+    "mg_serve_submit_rhs": (ctypes.c_int, [_vp, _P(mg_problem), _P(mg_rhs), ctypes.c_double,
+                                           _P(ctypes.c_uint64)]),
+    "mg_serve_poll": (ctypes.c_int, [_vp, ctypes.c_uint64, _dp, _P(ctypes.c_int)]),
+    "mg_serve_wait": (ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.c_double, _dp, _P(ctypes.c_int), _dp,
+                                     ctypes.c_int]),
+    "mg_serve_get_stats": (ctypes.c_int, [_vp, _P(mg_serve_stats)]),
+    "mg_serve_destroy": (ctypes.c_int, [_vp]),
     "mg_last_error": (ctypes.c_char_p, []),
 }
 
@@ -347,3 +370,83 @@ class Hierarchy:
 
     def export(self, level, which=0, precision=MG_FP64):
         return mg_export_operator(self.h, level, which, precision)
+
+
+# ---------------------------------------------------------------------------------
+# Serving (mg_serve_*)
+# ---------------------------------------------------------------------------------
+def mg_serve_config_default(**overrides):
+    c = mg_serve_config()
+    lib().mg_serve_config_default(ctypes.byref(c))
+    for k, v in overrides.items():
+        if hasattr(c, k):
+            setattr(c, k, v)
+        else:
+            setattr(c.options, k, v)
+    return c
+
+
+class Server:
+    """A continuous-batching multigrid server (one mg_server); torch supplies the budget memory."""
+
+    def __init__(self, hbm_budget_bytes, device=None, **overrides):
+        self.config = mg_serve_config_default(hbm_budget_bytes=int(hbm_budget_bytes), **overrides)
+        self.device = device if device is not None else TorchDevice()
+        h = _vp()
+        _check(lib().mg_serve_create(ctypes.byref(self.config), ctypes.byref(self.device.struct), ctypes.byref(h)))
+        self.h = h.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().mg_serve_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, dim, n_cells, n_levels, b_host, rel_tol):
+        """Copy b_host (float64, n DOFs) into a new request; returns its ticket."""
+        p, _k = _problem(dim, MG_Q1, n_cells, n_levels)
+        b = np.ascontiguousarray(b_host, dtype=np.float64)
+        t = ctypes.c_uint64(0)
+        _check(lib().mg_serve_submit(self.h, ctypes.byref(p), _as_dp(b), float(rel_tol), ctypes.byref(t)))
+        return t.value
+
+    def submit_rhs(self, dim, n_cells, n_levels, modes, rel_tol, f_const=1.0):
+        """Request whose load vector the server assembles from sine modes (or f = f_const)."""
+        p, _k = _problem(dim, MG_Q1, n_cells, n_levels)
+        f, _keep = _rhs(modes, f_const)
+        t = ctypes.c_uint64(0)
+        _check(lib().mg_serve_submit_rhs(self.h, ctypes.byref(p), ctypes.byref(f), float(rel_tol), ctypes.byref(t)))
+        return t.value
+
+    def poll(self, ticket, n=None):
+        """None while pending, else (status, x or None, iters)."""
+        x = np.zeros(n) if n else None
+        it = ctypes.c_int(0)
+        st = lib().mg_serve_poll(self.h, ctypes.c_uint64(ticket), _as_dp(x) if x is not None else None,
+                                 ctypes.byref(it))
+        if st == MG_PENDING:
+            return None
+        if st in (MG_EINVAL, MG_ENOTFOUND, MG_ECUDA):
+            raise MgError(st, last_error())
+        return st, x, it.value
+
+    def wait(self, ticket, n, timeout_s=600.0, hist_len=0):
+        """Block until the request finishes: (status, x, iters, hist)."""
+        x = np.zeros(n)
+        it = ctypes.c_int(0)
+        hist = np.zeros(max(hist_len, 1))
+        st = lib().mg_serve_wait(self.h, ctypes.c_uint64(ticket), float(timeout_s), _as_dp(x), ctypes.byref(it),
+                                 _as_dp(hist), int(hist_len))
+        if st in (MG_EINVAL, MG_ENOTFOUND, MG_ECUDA, MG_ETIMEOUT):
+            raise MgError(st, last_error())
+        return st, x, it.value, hist[:min(hist_len, it.value + 1)].copy()
+
+    def stats(self):
+        s = mg_serve_stats()
+        _check(lib().mg_serve_get_stats(self.h, ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in mg_serve_stats._fields_}
