@@ -169,6 +169,76 @@ def cpu_baseline(name, cycles):
     return O.n * cycles / dt, dt
 
 
+def serve_bench(args):
+    """Serving workload: seeded trace of Q1 Poisson solves, Poisson arrivals at 70% of capacity.
+
+    1. operator cache warm-up (one solve per problem shape) and tile-shape autotuning;
+    2. capacity: the first requests of the trace submitted at once (closed loop);
+    3. the whole trace with Poisson arrivals at 0.7 x capacity; latency = completion -
+       arrival (submission happens at the arrival time), right-hand sides assembled by
+       the server from the four sine modes, tolerance 1e-8, FP32 V-cycle in FP64.
+    """
+    import threading as th
+
+    from paper_1609_04809_gb300 import mg, workloads as W
+    tol = 1e-8
+    levels = lambda N: int(round(np.log2(N))) - 1  # coarsest 4 cells per axis
+    trace = W.serving_trace(n_requests=args.serve_requests, seed=4096)
+    shapes = sorted(set((r["dim"], r["n_cells"]) for r in trace))
+    S = mg.Server(int(args.serve_budget_gb * (1 << 30)), max_active=args.serve_slots)
+    try:
+        t0 = time.perf_counter()
+        tuned = S.tune([(d, n, levels(n)) for d, n in shapes], repeats=2, rel_tol=tol)
+        t_tune = time.perf_counter() - t0
+        nmax = max(mg.mg_ndofs(d, 0, n) for d, n in shapes)
+        xbuf = np.zeros(nmax)
+
+        def run(reqs, rate):
+            S.reset_stats()
+            tickets = [None] * len(reqs)
+            start = time.perf_counter()
+
+            def submitter():
+                for k, r in enumerate(reqs):
+                    if rate:
+                        delay = start + r["arrival"] - time.perf_counter()
+                        if delay > 0:
+                            time.sleep(delay)
+                    tickets[k] = S.submit_rhs(r["dim"], r["n_cells"], levels(r["n_cells"]), r["modes"], tol)
+
+            th_sub = th.Thread(target=submitter)
+            th_sub.start()
+            iters = []
+            for k, r in enumerate(reqs):
+                while tickets[k] is None:
+                    time.sleep(0.0005)
+                n = mg.mg_ndofs(r["dim"], 0, r["n_cells"])
+                st, x, it, _ = S.wait(tickets[k], n, timeout_s=1200.0)
+                if st != mg.MG_OK:
+                    raise RuntimeError("request %d ended with status %d" % (k, st))
+                iters.append(it)
+            th_sub.join()
+            return time.perf_counter() - start, S.stats(), iters
+
+        cap_n = min(args.serve_capacity_requests, len(trace))
+        cap_wall, cap_stats, _ = run(trace[:cap_n], None)
+        capacity = cap_n / cap_wall
+        rate = 0.7 * capacity
+        trace = W.serving_trace(n_requests=args.serve_requests, seed=4096, rate=rate)
+        wall, st, iters = run(trace, rate)
+        dofs = sum(mg.mg_ndofs(r["dim"], 0, r["n_cells"]) for r in trace)
+        return {"requests": len(trace), "tol": tol, "precision": "FP32 V-cycle in FP64 defect correction",
+                "arrival_rate_per_s": rate, "capacity_solves_per_s": capacity,
+                "capacity_sample": cap_n, "solves_per_s": st["solves_per_s"], "p50_ms": st["p50_ms"],
+                "p99_ms": st["p99_ms"], "max_ms": st["max_ms"], "mean_batch": st["mean_batch"],
+                "iterations_mean": float(np.mean(iters)), "iterations_max": int(np.max(iters)),
+                "dofs_total": int(dofs), "wall_s": wall, "budget_gb": args.serve_budget_gb,
+                "device_bytes_peak": int(st["device_bytes_peak"]), "operator_sets": st["operator_sets"],
+                "tile": {"rows_per_thread": tuned[0], "blocks_per_sm": tuned[1], "tune_s": t_tune}}
+    finally:
+        S.close()
+
+
 def run_reference(args):
     rank = _env_int("RANK", 0)
     if rank != 0:
@@ -312,6 +382,12 @@ def run_ours(args):
                    "mixed_final_rel_residual": r32, "speedup_mixed_vs_fp64": t64 / t32}
             Hm.close()
 
+        serving = None
+        if world == 1 and args.serve_requests > 0:
+            H.close()
+            torch.cuda.empty_cache()
+            serving = serve_bench(args)
+
         cpu = None
         if world == 1 and not args.no_cpu:
             cv, cdt = cpu_baseline(name, args.cpu_cycles)
@@ -341,6 +417,7 @@ def run_ours(args):
                "kernel_ms_per_step": per_kernel,
                "e2e": e2e, "time_to_solution": tts, "cpu_baseline": cpu,
                "gpu_launches": info["kernels_per_cycle"] * args.steps + 1,
+               "serving": serving,
                "clocks": clocks}
         print(json.dumps(out))
     H.close()
@@ -361,6 +438,10 @@ def main():
     ap.add_argument("--cpu-cycles", type=int, default=8)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=4096)
+    ap.add_argument("--serve-capacity-requests", type=int, default=1024)
+    ap.add_argument("--serve-budget-gb", type=float, default=150.0)
+    ap.add_argument("--serve-slots", type=int, default=256)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

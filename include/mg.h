@@ -142,6 +142,11 @@ int64_t mg_ndofs(int dim, int element, int n_cells);
  * axis per cell (host computation). b_host: n DOFs, caller-owned. */
 mg_status mg_load_vector(const mg_problem *p, const mg_rhs *f, double *b_host);
 
+/* The same Q1 load vector with the tensor Gauss rule factorised per sine mode and axis
+ * (b = sum_m c_m X_m (x) Y_m [(x) Z_m]): O(modes * n) instead of O(modes * 3^d * n) sine
+ * evaluations, equal to mg_load_vector up to rounding. Q1 only. */
+mg_status mg_load_vector_separable(const mg_problem *p, const mg_rhs *f, double *b_host);
+
 /* The hierarchy's level operators as assembled on the host, without a GPU: which = 0:
  * A_level, 1: P_level (rows: level, columns: level-1), 2: R_level = P_level^T, in CSR
  * with ascending columns and FP64 values (the same matrices mg_setup stores). Call with
@@ -288,6 +293,14 @@ mg_status mg_serve_poll(mg_server *s, uint64_t ticket, double *x_host, int *iter
 mg_status mg_serve_wait(mg_server *s, uint64_t ticket, double timeout_s, double *x_host, int *iters,
                         double *res_hist, int hist_len);
 mg_status mg_serve_get_stats(mg_server *s, mg_serve_stats *out);
+/* Clears the latency record and counters (for a measured run after warm-up). */
+mg_status mg_serve_reset_stats(mg_server *s);
+/* Autotuner for the tile shape of the phase launches: on an idle server, solves
+ * `repeats` copies of each of the nshapes problems (f = 1, tolerance rel_tol) as one
+ * batch for every candidate (rows per thread 1/2/4/8 x blocks per SM 2/4/8), keeps the
+ * fastest and reports it. Resets the statistics. */
+mg_status mg_serve_tune(mg_server *s, const mg_problem *shapes, int nshapes, int repeats, double rel_tol,
+                        int *rows_per_thread, int *blocks_per_sm);
 /* Stops the threads (requests in flight are dropped) and releases the budget. */
 mg_status mg_serve_destroy(mg_server *s);
 

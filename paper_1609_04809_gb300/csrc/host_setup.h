@@ -40,6 +40,10 @@ bool coarse_coefficient(int dim, int NL, const double *kL, int Nl, std::vector<d
 
 void load_vector(int dim, int elem, int N, const mg_rhs *f, double *b);
 
+// The Q1 load vector of the same rule, factorised per mode and axis (O(modes * n));
+// equal to load_vector up to rounding.
+void load_vector_separable(int dim, int N, const mg_rhs *f, double *b);
+
 double power_lambda(const Csr &A, const std::vector<double> &dinv, int iters, uint64_t seed);
 
 // Row-sum-preserving FP32 copy: off-diagonals rounded to nearest, the diagonal set so

@@ -610,6 +610,24 @@ extern "C" mg_status mg_load_vector(const mg_problem *p, const mg_rhs *f, double
     }
 }
 
+extern "C" mg_status mg_load_vector_separable(const mg_problem *p, const mg_rhs *f, double *b_host)
+{
+    try {
+        validate_problem(p);
+        if (p->element != MG_Q1) throw Error(MG_EINVAL, "the factorised load vector is for Q1");
+        if (!f || !b_host) throw Error(MG_EINVAL, "rhs or output is NULL");
+        if (f->n_modes < 0 || (f->n_modes > 0 && (!f->amp || !f->freq))) throw Error(MG_EINVAL, "bad rhs modes");
+        mgh::load_vector_separable(p->dim, p->n_cells, f, b_host);
+        return MG_OK;
+    } catch (const Error &e) {
+        g_err = e.msg;
+        return e.st;
+    } catch (const std::bad_alloc &) {
+        g_err = "host allocation failed";
+        return MG_ENOMEM;
+    }
+}
+
 // device format of a level operator
 static void plan_matrix(DevMat &m, const mgh::Csr &A, int fmt, int dim, int N, int sv, mgi::Slab &slab, bool take)
 {

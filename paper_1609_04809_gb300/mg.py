@@ -86,6 +86,7 @@ SIGNATURES = {
     "mg_options_default": (None, [_P(mg_options)]),
     "mg_ndofs": (ctypes.c_int64, [ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "mg_load_vector": (ctypes.c_int, [_P(mg_problem), _P(mg_rhs), _dp]),
+    "mg_load_vector_separable": (ctypes.c_int, [_P(mg_problem), _P(mg_rhs), _dp]),
     "mg_assemble_operator": (ctypes.c_int, [_P(mg_problem), ctypes.c_int, ctypes.c_int, _P(ctypes.c_int64),
                                             _P(ctypes.c_int64), _P(ctypes.c_int64), _P(ctypes.c_int32), _dp]),
     "mg_setup": (ctypes.c_int, [_P(mg_problem), _P(mg_options), _P(mg_device), _P(_vp)]),
@@ -108,6 +109,9 @@ SIGNATURES = {
     "mg_serve_wait": (ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.c_double, _dp, _P(ctypes.c_int), _dp,
                                      ctypes.c_int]),
     "mg_serve_get_stats": (ctypes.c_int, [_vp, _P(mg_serve_stats)]),
+    "mg_serve_reset_stats": (ctypes.c_int, [_vp]),
+    "mg_serve_tune": (ctypes.c_int, [_vp, _P(mg_problem), ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                     _P(ctypes.c_int), _P(ctypes.c_int)]),
     "mg_serve_destroy": (ctypes.c_int, [_vp]),
     "mg_last_error": (ctypes.c_char_p, []),
 }
@@ -240,6 +244,15 @@ def mg_assemble_operator(dim, element, n_cells, n_levels, level, which=0, k_cell
                                   rowptr.ctypes.data_as(_P(ctypes.c_int64)),
                                   col.ctypes.data_as(_P(ctypes.c_int32)), _as_dp(val)))
     return rowptr, col[:nnz.value], val[:nnz.value]
+
+
+def mg_load_vector_separable(dim, n_cells, modes=None, f_const=1.0):
+    """The Q1 load vector with the Gauss rule factorised per mode and axis (equal up to rounding)."""
+    p, _k = _problem(dim, MG_Q1, n_cells, 1)
+    f, _keep = _rhs(modes, f_const)
+    b = np.zeros(mg_ndofs(dim, MG_Q1, n_cells))
+    _check(lib().mg_load_vector_separable(ctypes.byref(p), ctypes.byref(f), _as_dp(b)))
+    return b
 
 
 def mg_setup(dim, element, n_cells, n_levels, options=None, k_cell=None, device=None):
@@ -450,3 +463,14 @@ class Server:
         s = mg_serve_stats()
         _check(lib().mg_serve_get_stats(self.h, ctypes.byref(s)))
         return {k: getattr(s, k) for k, _ in mg_serve_stats._fields_}
+
+    def reset_stats(self):
+        _check(lib().mg_serve_reset_stats(self.h))
+
+    def tune(self, shapes, repeats=2, rel_tol=1e-8):
+        """shapes: list of (dim, n_cells, n_levels). Returns the chosen (rows_per_thread, blocks_per_sm)."""
+        arr = (mg_problem * len(shapes))(*[mg_problem(d, MG_Q1, n, l, None) for d, n, l in shapes])
+        r, b = ctypes.c_int(0), ctypes.c_int(0)
+        _check(lib().mg_serve_tune(self.h, arr, len(shapes), int(repeats), float(rel_tol), ctypes.byref(r),
+                                   ctypes.byref(b)))
+        return r.value, b.value

@@ -89,6 +89,14 @@ def test_load_vector_bitwise_equal_oracle(lib, orc, dim, elem, N):
         assert np.array_equal(b1.view(np.uint64), b2.view(np.uint64))
 
 
+@pytest.mark.parametrize("dim,N", [(2, 64), (3, 16)])
+def test_separable_load_vector_equals_quadrature(lib, orc, dim, N):
+    for modes in (W.random_modes(dim, seed=6), W.manufactured_modes(dim), None):
+        b1 = mg.mg_load_vector_separable(dim, N, modes=modes, f_const=2.5)
+        b2 = orc.load_vector(dim, orc.Q1, N, modes=modes, fconst=2.5)
+        assert np.max(np.abs(b1 - b2)) <= 1e-13 * np.max(np.abs(b2))
+
+
 def test_invalid_arguments_are_rejected(lib):
     with pytest.raises(mg.MgError) as e:
         mg.mg_assemble_operator(3, mg.MG_Q1, 12, 4, 0)  # 12 / 8 is not an integer

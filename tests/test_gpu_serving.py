@@ -160,7 +160,10 @@ def test_server_side_right_hand_side():
         b = mg.mg_load_vector(2, mg.MG_Q1, 128, modes=modes)
         r1 = S.wait(S.submit(2, 128, 6, b, TOL), b.size)
         r2 = S.wait(S.submit_rhs(2, 128, 6, modes, TOL), b.size)
-        assert r1[0] == r2[0] == mg.MG_OK and r1[2] == r2[2] and np.array_equal(r1[1], r2[1])
+        # the server factorises the same quadrature rule: equal up to rounding
+        assert r1[0] == r2[0] == mg.MG_OK
+        assert np.linalg.norm(r1[1] - r2[1]) <= 1e-9 * np.linalg.norm(r1[1])
+        assert _true_rel_residual(2, 128, 6, b, r2[1]) <= TOL * (1 + 1e-6)
     finally:
         S.close()
 
@@ -174,6 +177,8 @@ def test_invalid_requests():
             S.submit(2, 64, 2, np.zeros(63 * 63), TOL)  # coarsest 32^2 cells: too many DOFs for the LU
         with pytest.raises(mg.MgError):
             S.submit(2, 64, 5, np.zeros(63 * 63), 0.0)  # tolerance must be positive
-        assert S.poll(123456) is None or True
+        with pytest.raises(mg.MgError) as e:
+            S.poll(123456)
+        assert e.value.status == mg.MG_ENOTFOUND
     finally:
         S.close()
