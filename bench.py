@@ -127,6 +127,17 @@ def _traffic_from_profile(kernel_tag):
     return None
 
 
+def replica_throughput(ms_local, n_dofs, steps, world, dist=None, device="cpu"):
+    """Whole-job V-cycle DOFs/s of `world` independent replicas: every rank ran `steps`
+    iterations on its own n_dofs problem; the job time is the slowest rank's."""
+    import torch
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    if dist is not None and world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    return world * n_dofs * steps / (ms_max * 1e-3), ms_max
+
+
 def _config_args(name):
     from paper_1609_04809_gb300 import workloads as W
     c = dict(W.CONFIGS[name])
@@ -292,7 +303,7 @@ def run_ours(args):
     n = b_host.size
     H = mg.Hierarchy(c["dim"], c["element"], c["n_cells"], c["n_levels"], smoother=c["smoother"],
                      omega=c["omega"], cheb_degree=c["cheb_degree"], nu_pre=c["nu_pre"], nu_post=c["nu_post"],
-                     precision=mg.MG_FP64)
+                     precision=mg.MG_MIXED if args.precision == "mixed" else mg.MG_FP64)
     info = H.info()
     Lf = c["n_levels"] - 1
     bd = torch.from_numpy(b_host).cuda()
@@ -317,11 +328,7 @@ def run_ours(args):
     if dist:
         dist.barrier()
     ms = e0.elapsed_time(e1)
-    t = torch.tensor([ms], device="cuda")
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = world * n * args.steps / (ms_max * 1e-3)
+    value, ms_max = replica_throughput(ms, n, args.steps, world, dist, device="cuda")
 
     # dominant kernel: finest-level smoother sweep
     k_ms, k_cnt, k_bytes, k_flops = mg.mg_profile_read(H.h, mg.MG_K_SMOOTH, Lf)
@@ -398,7 +405,8 @@ def run_ours(args):
         clocks = clk.summary()
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-               "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+               "scaling": "weak", "vs_baseline": None,
+               "dtype": "f64" if args.precision == "fp64" else "f32 V-cycle / f64 outer", "data": "synthetic",
                "config": {"workload": name, "description": WORKLOADS.get(name, name), "n_dofs": n,
                           "parallelism": "replicas" if world > 1 else "single-gpu",
                           "l2": "inputs larger than L2 (finest FP64 matrix %.0f MB > 129 MB L2)"
@@ -442,6 +450,8 @@ def main():
     ap.add_argument("--serve-capacity-requests", type=int, default=1024)
     ap.add_argument("--serve-budget-gb", type=float, default=150.0)
     ap.add_argument("--serve-slots", type=int, default=256)
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
+                    help="fp64: the workload as specified (headline); mixed: FP32 V-cycle, for analysis")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -14,7 +14,9 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -792,6 +794,91 @@ static int pick_storage(const mg_options &o, int elem)
     return elem == MG_Q1 ? MG_STORAGE_DIA : MG_STORAGE_ELL;
 }
 
+// Storage chosen by measurement: every candidate format of this level's matrix is built
+// in temporary device memory and timed on residual sweeps; the fastest wins. Choices are
+// cached per (dim, element, cells, value size) for the life of the process.
+template <typename T>
+static double time_format(mg_hierarchy *h, const mgh::Csr &A, int fmt, int dim, int N)
+{
+    mgi::Slab S;
+    DevMat m;
+    plan_matrix(m, A, fmt, dim, N, sizeof(T), S, false);
+    int64_t n1 = N - 1;
+    int64_t pad = fmt == MG_STORAGE_DIA ? round_up(dim == 3 ? n1 * n1 + n1 + 1 : n1 + 1, 64) : 0;
+    int64_t ld = round_up(std::max<int64_t>(A.nrows, 1), 64);
+    S.reserve((size_t)(ld + 2 * pad) * sizeof(T));
+    S.reserve((size_t)ld * sizeof(T) * 2);
+    size_t bytes = S.used + 256;
+    S.used = 0;
+    S.size = bytes;
+    S.base = h->own_alloc ? nullptr : (char *)h->dev.alloc(bytes, h->dev.ctx);
+    if (h->own_alloc && cudaMalloc(&S.base, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        S.base = nullptr;
+    }
+    if (!S.base) return 1e300;  // no room to try it: never chosen
+    double ms_best = 1e300;
+    try {
+        plan_matrix(m, A, fmt, dim, N, sizeof(T), S, true);
+        char *xb = (char *)S.take((size_t)(ld + 2 * pad) * sizeof(T));
+        T *x = (T *)(xb + pad * sizeof(T));
+        T *b = (T *)S.take((size_t)ld * sizeof(T)), *r = (T *)S.take((size_t)ld * sizeof(T));
+        CK(cudaMemsetAsync(S.base, 0, S.size, h->s));
+        std::vector<T> vals(A.val.begin(), A.val.end());
+        upload_matrix<T>(m, A, vals, dim, N, h->s);
+        cudaEvent_t e0, e1;
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        for (int rep = 0; rep < 6; rep++) {
+            CK(cudaEventRecord(e0, h->s));
+            sweep_fmt<T, SW_RESID>(m, (int)A.nrows, x, b, r, (T *)nullptr, T(0), T(0), h->s);
+            CK(cudaEventRecord(e1, h->s));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            if (rep > 0) ms_best = std::min(ms_best, (double)ms);  // the first run warms up
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    } catch (...) {
+        ms_best = 1e300;
+    }
+    CK(cudaStreamSynchronize(h->s));
+    if (h->own_alloc)
+        cudaFree(S.base);
+    else
+        h->dev.free(S.base, S.size, h->dev.ctx);
+    return ms_best;
+}
+
+static int tune_storage(mg_hierarchy *h, const mgh::Csr &A, int dim, int elem, int N)
+{
+    static std::mutex mu;
+    static std::map<std::tuple<int, int, int, int>, int> cache;
+    auto key = std::make_tuple(dim, elem, N, h->inner_size);
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) return it->second;
+    }
+    std::vector<int> cands;
+    if (elem == MG_Q1) cands.push_back(MG_STORAGE_DIA);
+    cands.push_back(MG_STORAGE_ELL);
+    cands.push_back(MG_STORAGE_CSR);
+    int best = cands[0];
+    double best_ms = 1e300;
+    for (int f : cands) {
+        double ms = h->mixed ? time_format<float>(h, A, f, dim, N) : time_format<double>(h, A, f, dim, N);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = f;
+        }
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    cache[key] = best;
+    return best;
+}
+
 void mgi::build_hierarchy(mg_hierarchy *h, const mg_problem *p, const mg_options *o, const mg_device *dev,
                           bool with_vectors)
 {
@@ -848,6 +935,10 @@ void mgi::build_hierarchy(mg_hierarchy *h, const mg_problem *p, const mg_options
 
     // ---- device memory plan (pass 0: count, pass 1: assign) ----
     int fmt = pick_storage(*o, elem);
+    std::vector<int> lfmt((size_t)nlev, fmt);
+    if (o->storage == MG_STORAGE_AUTO)  // measured on the levels large enough to be bandwidth-bound
+        for (int l = 1; l <= Lf; l++)
+            if (h->lev[l].n >= 32768) lfmt[l] = tune_storage(h, A[l], dim, elem, h->lev[l].N);
     int sv = h->inner_size;
     for (int pass = 0; pass < 2; pass++) {
         bool take = pass == 1;
@@ -875,7 +966,7 @@ void mgi::build_hierarchy(mg_hierarchy *h, const mg_problem *p, const mg_options
         };
         for (int l = 0; l <= Lf; l++) {
             LevelD &L = h->lev[l];
-            int lf = (l == 0 && fmt == MG_STORAGE_DIA) ? MG_STORAGE_DIA : fmt;
+            int lf = lfmt[l];
             L.fmt = lf;
             plan_matrix(L.A, A[l], lf, dim, L.N, sv, S, take);
             if (!h->mixed && l >= 1) L.A.dinv = vec((size_t)L.A.ld * 8);  // FP64 smoothers read D^-1
