@@ -127,6 +127,28 @@ def _traffic_from_profile(kernel_tag):
     return None
 
 
+def roofline_block(precision, name, tflops, gbs, peak_gbs, peak_kind, flops, nbytes, launches, sec):
+    """The dominant kernel against the roofline that binds it: the FP64 pipe for the FP64
+    sweep (GB300 issues about 2 DFMA per clock per SM), HBM bandwidth for the FP32 one."""
+    hbm = {"achieved": gbs, "peak": peak_gbs, "unit": "GB/s", "frac": gbs / peak_gbs if gbs else None,
+           "peak_kind": "%s HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" % peak_kind}
+    common = {"flops_per_launch": flops, "bytes_per_launch": nbytes, "launches": launches,
+              "us_per_launch": 1e6 * sec if launches else None}
+    if precision == "fp64":
+        out = {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+               "frac": tflops / FP64_PEAK_TFLOPS if tflops else None,
+               "traffic": _traffic_from_profile("smooth_fp64_%s" % name),
+               "kernel": "finest-level smoother sweep (fused residual + Chebyshev update), FP64",
+               "peak_kind": "FP64 pipe: 152 SMs x 2.07 GHz x 2 DFMA/clk/SM x 2 flop (recipe nominal)",
+               "hbm": hbm}
+    else:
+        out = dict(hbm)
+        out.update({"bound": "hbm", "traffic": _traffic_from_profile("smooth_fp32_%s" % name),
+                    "kernel": "finest-level smoother sweep (fused residual + Chebyshev update), FP32"})
+    out.update(common)
+    return out
+
+
 def replica_throughput(ms_local, n_dofs, steps, world, dist=None, device="cpu"):
     """Whole-job V-cycle DOFs/s of `world` independent replicas: every rank ran `steps`
     iterations on its own n_dofs problem; the job time is the slowest rank's."""
@@ -412,16 +434,8 @@ def run_ours(args):
                           "l2": "inputs larger than L2 (finest FP64 matrix %.0f MB > 129 MB L2)"
                                 % (info["nnz"][Lf] * 8 / 1e6),
                           "storage": ["csr", "ell", "dia"][info["storage"][Lf] - 1]},
-               "roofline": {"bound": "alu", "achieved": fp64_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                            "frac": fp64_tflops / FP64_PEAK_TFLOPS if fp64_tflops else None,
-                            "traffic": _traffic_from_profile("smooth_fp64_%s" % name),
-                            "kernel": "finest-level smoother sweep (fused residual + Chebyshev update), FP64",
-                            "peak_kind": "FP64 pipe: 152 SMs x 2.07 GHz x 2 DFMA/clk/SM x 2 flop (recipe nominal)",
-                            "flops_per_launch": k_flops, "bytes_per_launch": k_bytes, "launches": k_cnt,
-                            "us_per_launch": 1e6 * k_s if k_cnt else None,
-                            "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s",
-                                    "frac": achieved / peak if achieved else None,
-                                    "peak_kind": "%s HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" % peak_kind}},
+               "roofline": roofline_block(args.precision, name, fp64_tflops, achieved, peak, peak_kind, k_flops,
+                                          k_bytes, k_cnt, k_s),
                "kernel_ms_per_step": per_kernel,
                "e2e": e2e, "time_to_solution": tts, "cpu_baseline": cpu,
                "gpu_launches": info["kernels_per_cycle"] * args.steps + 1,

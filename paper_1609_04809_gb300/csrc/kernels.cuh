@@ -32,14 +32,15 @@ namespace mgk {
 // ------------------------------------------------------------------------------------
 // Restriction b_c = P^T r: coarse vertex (X,Y[,Z]) gathers the 3^d fine vertices around
 // (2X,2Y[,2Z]) in ascending fine index, weight prod_d (1 if on the line, 1/2 otherwise).
+// Launch: x-lines of the coarse grid, grid (ceil(nc1/blockDim), nc1, DIM == 3 ? nc1 : 1).
 template <typename T, int DIM>
-__global__ void __launch_bounds__(256) k_restrict_q1(const T *__restrict__ r, T *__restrict__ bc, int Nc)
+__global__ void __launch_bounds__(128) k_restrict_q1(const T *__restrict__ r, T *__restrict__ bc, int Nc)
 {
     int nc1 = Nc - 1, nf1 = 2 * Nc - 1;
-    int nc = DIM == 2 ? nc1 * nc1 : nc1 * nc1 * nc1;
-    int I = blockIdx.x * blockDim.x + threadIdx.x;
-    if (I >= nc) return;
-    int X = I % nc1 + 1, Y = (I / nc1) % nc1 + 1, Z = DIM == 3 ? I / (nc1 * nc1) + 1 : 0;
+    int X = blockIdx.x * blockDim.x + threadIdx.x + 1;
+    if (X > nc1) return;
+    int Y = blockIdx.y + 1, Z = DIM == 3 ? blockIdx.z + 1 : 0;
+    int64_t I = (X - 1) + (int64_t)nc1 * ((Y - 1) + (DIM == 3 ? (int64_t)nc1 * (Z - 1) : 0));
     T s = T(0);
     const int zlo = DIM == 3 ? -1 : 0, zhi = DIM == 3 ? 1 : 0;
 #pragma unroll
@@ -59,14 +60,15 @@ __global__ void __launch_bounds__(256) k_restrict_q1(const T *__restrict__ r, T 
 // with |v - 2V| <= 1 per axis (boundary ones are zero and skipped), ascending coarse index.
 // Every such V carries the same weight prod_d (1 or 1/2) = 2^-(number of odd coordinates
 // of v), taken from a table: no floating-point work beyond one multiply-add per term.
+// Launch: x-lines of the fine grid, grid (ceil(nf1/blockDim), nf1, DIM == 3 ? nf1 : 1).
 template <typename T, int DIM>
-__global__ void __launch_bounds__(256) k_prolong_q1(const T *__restrict__ xc, T *__restrict__ xf, int Nc)
+__global__ void __launch_bounds__(128) k_prolong_q1(const T *__restrict__ xc, T *__restrict__ xf, int Nc)
 {
     int Nf = 2 * Nc, nf1 = Nf - 1, nc1 = Nc - 1;
-    int nf = DIM == 2 ? nf1 * nf1 : nf1 * nf1 * nf1;
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nf) return;
-    int v0 = i % nf1 + 1, v1 = (i / nf1) % nf1 + 1, v2 = DIM == 3 ? i / (nf1 * nf1) + 1 : 2;
+    int v0 = blockIdx.x * blockDim.x + threadIdx.x + 1;
+    if (v0 > nf1) return;
+    int v1 = blockIdx.y + 1, v2 = DIM == 3 ? blockIdx.z + 1 : 2;
+    int64_t i = (v0 - 1) + (int64_t)nf1 * ((v1 - 1) + (DIM == 3 ? (int64_t)nf1 * (v2 - 1) : 0));
     int odd = (v0 & 1) + (v1 & 1) + (DIM == 3 ? (v2 & 1) : 0);
     const T w = odd == 0 ? T(1) : (odd == 1 ? T(0.5) : (odd == 2 ? T(0.25) : T(0.125)));
     int x0 = max(v0 >> 1, 1), x1 = min((v0 + 1) >> 1, Nc - 1);
@@ -139,20 +141,29 @@ __global__ void k_coarse_solve(const double *__restrict__ lu, const int *__restr
 }
 
 // The same solve for n <= 64 by one warp with the factors in shared memory: lane l owns
-// rows l and l + 32 and their running sums; one __syncwarp per column.
+// rows l and l + 32 and their running sums; one __syncwarp per column. All 256 threads
+// of the block stage the factors, pivots and right-hand side first (independent loads in
+// flight together), then warp 0 alone solves.
 template <typename T>
-__global__ void __launch_bounds__(32) k_coarse_solve_warp(const double *__restrict__ lu, const int *__restrict__ piv,
-                                                          int n, const T *__restrict__ b, T *__restrict__ x)
+__global__ void __launch_bounds__(256) k_coarse_solve_warp(const double *__restrict__ lu, const int *__restrict__ piv,
+                                                           int n, const T *__restrict__ b, T *__restrict__ x)
 {
     __shared__ double L[64 * 64];
     __shared__ double xs[64];
-    int l = threadIdx.x;
-    for (int k = l; k < n * n; k += 32) L[k] = lu[k];
-    for (int k = l; k < n; k += 32) xs[k] = (double)b[k];
-    __syncwarp();
+    __shared__ int ps[64];
+    int tid = threadIdx.x;
+#pragma unroll 4
+    for (int k = tid; k < n * n; k += 256) L[k] = lu[k];
+    if (tid < n) {
+        xs[tid] = (double)b[tid];
+        ps[tid] = piv[tid];
+    }
+    __syncthreads();
+    if (tid >= 32) return;
+    int l = tid;
     if (l == 0)
         for (int k = 0; k < n; k++) {
-            int p = piv[k];
+            int p = ps[k];
             if (p != k) {
                 double tmp = xs[k];
                 xs[k] = xs[p];

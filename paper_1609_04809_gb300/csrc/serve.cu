@@ -327,6 +327,7 @@ __global__ void __launch_bounds__(32) k_sv_coarse(Plan P, int p)
     SvPhase ph = P.phases[p];
     __shared__ double Ls[64 * 64];
     __shared__ double xs[64];
+    __shared__ int ps[64];
     for (int it_i = blockIdx.x; it_i < ph.nitems; it_i += gridDim.x) {
         int4 it = P.items[ph.item_off + it_i];
         const SvReq &R = P.reqs[it.x];
@@ -334,12 +335,17 @@ __global__ void __launch_bounds__(32) k_sv_coarse(Plan P, int p)
         if (slot_done(P, it.x)) continue;
         int n = R.n0, l = threadIdx.x;
         __syncwarp();
+        // stage the factors, pivots and right-hand side with independent loads in flight
+        int pv0 = l < n ? R.piv[l] : 0, pv1 = l + 32 < n ? R.piv[l + 32] : 0;
+#pragma unroll 8
         for (int k = l; k < n * n; k += 32) Ls[k] = R.lu[k];
         for (int k = l; k < n; k += 32) xs[k] = (double)C.b[k];
+        if (l < n) ps[l] = pv0;
+        if (l + 32 < n) ps[l + 32] = pv1;
         __syncwarp();
         if (l == 0)
             for (int k = 0; k < n; k++) {
-                int q = R.piv[k];
+                int q = ps[k];
                 if (q != k) {
                     double tmp = xs[k];
                     xs[k] = xs[q];
