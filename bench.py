@@ -325,7 +325,8 @@ def run_ours(args):
     n = b_host.size
     H = mg.Hierarchy(c["dim"], c["element"], c["n_cells"], c["n_levels"], smoother=c["smoother"],
                      omega=c["omega"], cheb_degree=c["cheb_degree"], nu_pre=c["nu_pre"], nu_post=c["nu_post"],
-                     precision=mg.MG_MIXED if args.precision == "mixed" else mg.MG_FP64)
+                     precision=mg.MG_MIXED if args.precision == "mixed" else mg.MG_FP64,
+                     use_pdl=0 if args.no_pdl else 1)
     info = H.info()
     Lf = c["n_levels"] - 1
     bd = torch.from_numpy(b_host).cuda()
@@ -464,6 +465,7 @@ def main():
     ap.add_argument("--serve-capacity-requests", type=int, default=1024)
     ap.add_argument("--serve-budget-gb", type=float, default=150.0)
     ap.add_argument("--serve-slots", type=int, default=256)
+    ap.add_argument("--no-pdl", action="store_true", help="launch without programmatic dependent launch")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                     help="fp64: the workload as specified (headline); mixed: FP32 V-cycle, for analysis")
     args = ap.parse_args()

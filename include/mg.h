@@ -95,6 +95,7 @@ typedef struct {
     int storage;
     int max_iters;
     int use_graph;
+    int use_pdl; /* launch V-cycle kernels with programmatic dependent launch (default 1) */
 } mg_options;
 
 /* Right-hand side f of -div(k grad u) = f: the constant f_const if n_modes == 0, else

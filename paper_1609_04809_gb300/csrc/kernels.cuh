@@ -36,6 +36,7 @@ namespace mgk {
 template <typename T, int DIM>
 __global__ void __launch_bounds__(128) k_restrict_q1(const T *__restrict__ r, T *__restrict__ bc, int Nc)
 {
+    pdl_enter();
     int nc1 = Nc - 1, nf1 = 2 * Nc - 1;
     int X = blockIdx.x * blockDim.x + threadIdx.x + 1;
     if (X > nc1) return;
@@ -64,6 +65,7 @@ __global__ void __launch_bounds__(128) k_restrict_q1(const T *__restrict__ r, T 
 template <typename T, int DIM>
 __global__ void __launch_bounds__(128) k_prolong_q1(const T *__restrict__ xc, T *__restrict__ xf, int Nc)
 {
+    pdl_enter();
     int Nf = 2 * Nc, nf1 = Nf - 1, nc1 = Nc - 1;
     int v0 = blockIdx.x * blockDim.x + threadIdx.x + 1;
     if (v0 > nf1) return;
@@ -89,6 +91,7 @@ __global__ void __launch_bounds__(256) k_csr_apply(const int64_t *__restrict__ r
                                                    const T *__restrict__ val, int n, const T *__restrict__ x,
                                                    T *__restrict__ y)
 {
+    pdl_enter();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     T s = T(0);
@@ -110,6 +113,7 @@ __global__ void k_coarse_solve(const double *__restrict__ lu, const int *__restr
                                const T *__restrict__ b, T *__restrict__ x)
 {
     extern __shared__ double xs[];
+    pdl_enter();
     int t = threadIdx.x;
     if (t < n) xs[t] = (double)b[t];
     __syncthreads();
@@ -151,6 +155,7 @@ __global__ void __launch_bounds__(256) k_coarse_solve_warp(const double *__restr
     __shared__ double L[64 * 64];
     __shared__ double xs[64];
     __shared__ int ps[64];
+    pdl_enter();
     int tid = threadIdx.x;
 #pragma unroll 4
     for (int k = tid; k < n * n; k += 256) L[k] = lu[k];
@@ -244,6 +249,7 @@ __global__ void __launch_bounds__(256) k_outer_resid(MatView<double> A, int n, c
                                                      const double *__restrict__ b, Tin *__restrict__ r,
                                                      double *partial, unsigned *ticket, double *norm2)
 {
+    pdl_enter();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     double sq = 0.0;
     if (i < n) {
@@ -276,6 +282,7 @@ __global__ void k_norm2(const double *__restrict__ v, int n, double *partial, un
 template <typename Tin>
 __global__ void __launch_bounds__(256) k_update(double *__restrict__ x, const Tin *__restrict__ c, int n)
 {
+    pdl_enter();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) x[i] = __dadd_rn(x[i], (double)c[i]);
 }

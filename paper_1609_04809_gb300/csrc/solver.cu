@@ -250,24 +250,44 @@ static double mat_bytes(const DevMat &m, int sv)
 // ------------------------------------------------------------------------------------
 // Kernel dispatch
 // ------------------------------------------------------------------------------------
+// Launch with programmatic dependent launch when pdl is set: the kernel may be scheduled
+// while the previous one in the stream finishes; it waits for it in pdl_enter().
+template <typename... KArgs, typename... Args>
+static void klaunch(bool pdl, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                    Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl ? 1 : 0;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+    if (e != cudaSuccess) throw Error(MG_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+}
+
 template <typename T, int MODE>
-static void sweep_fmt(const DevMat &A, int n, const T *x, const T *b, T *out, T *d, T c1, T c2, cudaStream_t s)
+static void sweep_fmt(const DevMat &A, int n, const T *x, const T *b, T *out, T *d, T c1, T c2, cudaStream_t s,
+                      bool pdl = false)
 {
     MatView<T> v = view<T>(A);
-    unsigned g = grid_for(n);
+    dim3 g(grid_for(n)), blk(256);
     if (A.fmt == MG_STORAGE_DIA) {
         if (A.K == 27)
-            k_dia_sweep<T, 27, MODE><<<g, 256, 0, s>>>(v, n, x, b, out, d, c1, c2);
+            klaunch(pdl, k_dia_sweep<T, 27, MODE>, g, blk, 0, s, v, n, x, b, out, d, c1, c2);
         else if (A.K == 21)
-            k_dia_sweep<T, 21, MODE><<<g, 256, 0, s>>>(v, n, x, b, out, d, c1, c2);
+            klaunch(pdl, k_dia_sweep<T, 21, MODE>, g, blk, 0, s, v, n, x, b, out, d, c1, c2);
         else
-            k_dia_sweep<T, 9, MODE><<<g, 256, 0, s>>>(v, n, x, b, out, d, c1, c2);
+            klaunch(pdl, k_dia_sweep<T, 9, MODE>, g, blk, 0, s, v, n, x, b, out, d, c1, c2);
     } else if (A.fmt == MG_STORAGE_ELL) {
-        k_ell_sweep<T, MODE><<<g, 256, 0, s>>>(v, n, x, b, out, d, c1, c2);
+        klaunch(pdl, k_ell_sweep<T, MODE>, g, blk, 0, s, v, n, x, b, out, d, c1, c2);
     } else {
-        k_csr_sweep<T, MODE><<<g, 256, 0, s>>>(v, n, x, b, out, d, c1, c2);
+        klaunch(pdl, k_csr_sweep<T, MODE>, g, blk, 0, s, v, n, x, b, out, d, c1, c2);
     }
-    CKL();
 }
 
 template <typename T>
@@ -299,12 +319,12 @@ static void sweep(mg_hierarchy *h, int l, int mode, const T *x, const T *b, T *o
     int nn = (int)L.n;
     T a = (T)c1, bb = (T)c2;
     switch (mode) {
-    case SW_RESID: sweep_fmt<T, SW_RESID>(L.A, nn, x, b, out, d, a, bb, s); break;
-    case SW_JACOBI: sweep_fmt<T, SW_JACOBI>(L.A, nn, x, b, out, d, a, bb, s); break;
-    case SW_CHEBF: sweep_fmt<T, SW_CHEBF>(L.A, nn, x, b, out, d, a, bb, s); break;
-    case SW_CHEB: sweep_fmt<T, SW_CHEB>(L.A, nn, x, b, out, d, a, bb, s); break;
-    case SW_JACOBI_Z: sweep_fmt<T, SW_JACOBI_Z>(L.A, nn, x, b, out, d, a, bb, s); break;
-    default: sweep_fmt<T, SW_CHEBF_Z>(L.A, nn, x, b, out, d, a, bb, s); break;
+    case SW_RESID: sweep_fmt<T, SW_RESID>(L.A, nn, x, b, out, d, a, bb, s, h->opt.use_pdl != 0); break;
+    case SW_JACOBI: sweep_fmt<T, SW_JACOBI>(L.A, nn, x, b, out, d, a, bb, s, h->opt.use_pdl != 0); break;
+    case SW_CHEBF: sweep_fmt<T, SW_CHEBF>(L.A, nn, x, b, out, d, a, bb, s, h->opt.use_pdl != 0); break;
+    case SW_CHEB: sweep_fmt<T, SW_CHEB>(L.A, nn, x, b, out, d, a, bb, s, h->opt.use_pdl != 0); break;
+    case SW_JACOBI_Z: sweep_fmt<T, SW_JACOBI_Z>(L.A, nn, x, b, out, d, a, bb, s, h->opt.use_pdl != 0); break;
+    default: sweep_fmt<T, SW_CHEBF_Z>(L.A, nn, x, b, out, d, a, bb, s, h->opt.use_pdl != 0); break;
     }
 }
 
@@ -347,15 +367,15 @@ static void restrict_to(mg_hierarchy *h, int l, const T *r, cudaStream_t s)
     if (F.structured) {
         unsigned l1 = (unsigned)(C.N - 1);
         dim3 g((l1 + 127) / 128, l1, h->dim == 3 ? l1 : 1);
+        bool pdl = h->opt.use_pdl != 0;
         if (h->dim == 3)
-            k_restrict_q1<T, 3><<<g, 128, 0, s>>>(r, (T *)C.b, C.N);
+            klaunch(pdl, k_restrict_q1<T, 3>, g, dim3(128), 0, s, r, (T *)C.b, C.N);
         else
-            k_restrict_q1<T, 2><<<g, 128, 0, s>>>(r, (T *)C.b, C.N);
+            klaunch(pdl, k_restrict_q1<T, 2>, g, dim3(128), 0, s, r, (T *)C.b, C.N);
     } else {
-        k_csr_apply<T, false><<<grid_for(C.n), 256, 0, s>>>(F.R.rowptr, F.R.col, (const T *)F.R.val, (int)C.n, r,
-                                                             (T *)C.b);
+        klaunch(h->opt.use_pdl != 0, k_csr_apply<T, false>, dim3(grid_for(C.n)), dim3(256), 0, s,
+                (const int64_t *)F.R.rowptr, (const int32_t *)F.R.col, (const T *)F.R.val, (int)C.n, r, (T *)C.b);
     }
-    CKL();
 }
 
 template <typename T>
@@ -369,14 +389,15 @@ static void prolong_add(mg_hierarchy *h, int l, const T *xc, T *xf, cudaStream_t
     if (F.structured) {
         unsigned l1 = (unsigned)(F.N - 1);
         dim3 g((l1 + 127) / 128, l1, h->dim == 3 ? l1 : 1);
+        bool pdl = h->opt.use_pdl != 0;
         if (h->dim == 3)
-            k_prolong_q1<T, 3><<<g, 128, 0, s>>>(xc, xf, C.N);
+            klaunch(pdl, k_prolong_q1<T, 3>, g, dim3(128), 0, s, xc, xf, C.N);
         else
-            k_prolong_q1<T, 2><<<g, 128, 0, s>>>(xc, xf, C.N);
+            klaunch(pdl, k_prolong_q1<T, 2>, g, dim3(128), 0, s, xc, xf, C.N);
     } else {
-        k_csr_apply<T, true><<<grid_for(F.n), 256, 0, s>>>(F.P.rowptr, F.P.col, (const T *)F.P.val, (int)F.n, xc, xf);
+        klaunch(h->opt.use_pdl != 0, k_csr_apply<T, true>, dim3(grid_for(F.n)), dim3(256), 0, s,
+                (const int64_t *)F.P.rowptr, (const int32_t *)F.P.col, (const T *)F.P.val, (int)F.n, xc, xf);
     }
-    CKL();
 }
 
 // V-cycle on the finest level's right-hand side (the defect); returns the buffer of the
@@ -403,14 +424,17 @@ static int enqueue_vcycle(mg_hierarchy *h, cudaStream_t s)
     {  // exact solve on the coarsest level
         LevelD &C = h->lev[0];
         LaunchScope ls(h, s, MG_K_COARSE, 0, (double)h->n0 * h->n0 * 8 + 2.0 * h->n0 * sizeof(T));
+        bool pdl = h->opt.use_pdl != 0;
+        const double *lu = h->lu;
+        const int *piv = h->piv;
         if (h->n0 <= 64) {
-            k_coarse_solve_warp<T><<<1, 256, 0, s>>>(h->lu, h->piv, h->n0, (const T *)C.b, (T *)C.x[0]);
+            klaunch(pdl, k_coarse_solve_warp<T>, dim3(1), dim3(256), 0, s, lu, piv, h->n0, (const T *)C.b,
+                    (T *)C.x[0]);
         } else {
             int thr = (int)round_up(h->n0, 32);
-            k_coarse_solve<T><<<1, thr, (size_t)h->n0 * sizeof(double), s>>>(h->lu, h->piv, h->n0, (const T *)C.b,
-                                                                               (T *)C.x[0]);
+            klaunch(pdl, k_coarse_solve<T>, dim3(1), dim3(thr), (size_t)h->n0 * sizeof(double), s, lu, piv, h->n0,
+                    (const T *)C.b, (T *)C.x[0]);
         }
-        CKL();
         cur[0] = 0;
     }
     for (int l = 1; l <= Lf; l++) {  // prolongation, correction and post-smoothing
@@ -435,21 +459,22 @@ static void enqueue_outer(mg_hierarchy *h, cudaStream_t s)
     double entries = A.fmt == MG_STORAGE_CSR ? (double)A.nnz : (double)A.K * n;
     LaunchScope ls(h, s, MG_K_OUTER, h->Lf, bytes, 2.0 * entries + 3.0 * n);
     MatView<double> v = view<double>(A);
-    unsigned g = grid_for(n);
+    dim3 g(grid_for(n)), blk(256);
     T *r = (T *)F.b;
+    bool pdl = h->opt.use_pdl != 0;
+    const double *x = h->x64, *b = h->b64;
     if (A.fmt == MG_STORAGE_DIA) {
         if (A.K == 27)
-            k_outer_resid<T, 3, 27><<<g, 256, 0, s>>>(v, n, h->x64, h->b64, r, h->partial, h->ticket, h->norm2);
+            klaunch(pdl, k_outer_resid<T, 3, 27>, g, blk, 0, s, v, n, x, b, r, h->partial, h->ticket, h->norm2);
         else if (A.K == 21)
-            k_outer_resid<T, 3, 21><<<g, 256, 0, s>>>(v, n, h->x64, h->b64, r, h->partial, h->ticket, h->norm2);
+            klaunch(pdl, k_outer_resid<T, 3, 21>, g, blk, 0, s, v, n, x, b, r, h->partial, h->ticket, h->norm2);
         else
-            k_outer_resid<T, 3, 9><<<g, 256, 0, s>>>(v, n, h->x64, h->b64, r, h->partial, h->ticket, h->norm2);
+            klaunch(pdl, k_outer_resid<T, 3, 9>, g, blk, 0, s, v, n, x, b, r, h->partial, h->ticket, h->norm2);
     } else if (A.fmt == MG_STORAGE_ELL) {
-        k_outer_resid<T, 2, 1><<<g, 256, 0, s>>>(v, n, h->x64, h->b64, r, h->partial, h->ticket, h->norm2);
+        klaunch(pdl, k_outer_resid<T, 2, 1>, g, blk, 0, s, v, n, x, b, r, h->partial, h->ticket, h->norm2);
     } else {
-        k_outer_resid<T, 1, 1><<<g, 256, 0, s>>>(v, n, h->x64, h->b64, r, h->partial, h->ticket, h->norm2);
+        klaunch(pdl, k_outer_resid<T, 1, 1>, g, blk, 0, s, v, n, x, b, r, h->partial, h->ticket, h->norm2);
     }
-    CKL();
 }
 
 template <typename T>
@@ -458,8 +483,7 @@ static void enqueue_update(mg_hierarchy *h, int cur, cudaStream_t s)
     LevelD &F = h->lev[h->Lf];
     int n = (int)F.n;
     LaunchScope ls(h, s, MG_K_UPDATE, h->Lf, 16.0 * n + (double)n * sizeof(T));
-    k_update<T><<<grid_for(n), 256, 0, s>>>(h->x64, (const T *)F.x[cur], n);
-    CKL();
+    klaunch(h->opt.use_pdl != 0, k_update<T>, dim3(grid_for(n)), dim3(256), 0, s, h->x64, (const T *)F.x[cur], n);
 }
 
 static void enqueue_r(mg_hierarchy *h, cudaStream_t s)
@@ -579,6 +603,7 @@ extern "C" void mg_options_default(mg_options *o)
     o->storage = MG_STORAGE_AUTO;
     o->max_iters = 100;
     o->use_graph = 1;
+    o->use_pdl = 1;
 }
 
 extern "C" int64_t mg_ndofs(int dim, int element, int n_cells)

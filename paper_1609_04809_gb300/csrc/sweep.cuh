@@ -10,6 +10,15 @@
 
 namespace mgk {
 
+// Programmatic dependent launch: wait until the preceding kernel of the stream has
+// finished and its writes are visible, then let the next kernel start its launch while
+// this one runs. Both are no-ops for a kernel launched without the PDL attribute.
+__device__ __forceinline__ void pdl_enter()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 template <typename T>
 struct Ar;
 template <>
@@ -101,6 +110,7 @@ __global__ void __launch_bounds__(256) k_dia_sweep(MatView<T> A, int n, const T 
                                                    const T *__restrict__ b, T *__restrict__ out,
                                                    T *__restrict__ d, T c1, T c2)
 {
+    pdl_enter();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     constexpr int C = K / 2;  // the stored diagonals are symmetric about the main one
@@ -127,6 +137,7 @@ __global__ void __launch_bounds__(256) k_ell_sweep(MatView<T> A, int n, const T 
                                                    const T *__restrict__ b, T *__restrict__ out,
                                                    T *__restrict__ d, T c1, T c2)
 {
+    pdl_enter();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     T s = T(0), diag = T(0);
@@ -147,6 +158,7 @@ __global__ void __launch_bounds__(256) k_csr_sweep(MatView<T> A, int n, const T 
                                                    const T *__restrict__ b, T *__restrict__ out,
                                                    T *__restrict__ d, T c1, T c2)
 {
+    pdl_enter();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     T s = T(0), diag = T(0);

@@ -99,6 +99,19 @@ def test_fp64_every_storage_and_graph_mode(orc, storage, graph):
     _assert_fp64_parity(g, o)
 
 
+@pytest.mark.parametrize("precision", [mg.MG_FP64, mg.MG_MIXED])
+def test_programmatic_dependent_launch_changes_no_bit(precision):
+    dim, elem, N, L = 3, 0, 32, 4
+    b = torch.from_numpy(W.random_vector(mg.mg_ndofs(dim, elem, N), seed=13)).cuda()
+    xs = []
+    for pdl in (0, 1):
+        H = mg.Hierarchy(dim, elem, N, L, smoother=1, nu_pre=1, nu_post=1, precision=precision, use_pdl=pdl)
+        x = torch.zeros_like(b)
+        H.solve(b, x, 1e-10)
+        xs.append(x.cpu().numpy())
+    assert np.array_equal(xs[0], xs[1])
+
+
 @pytest.mark.parametrize("storage", [mg.MG_STORAGE_ELL, mg.MG_STORAGE_CSR])
 def test_rq1_storage(orc, storage):
     dim, elem, N, L = 3, 1, 8, 3
