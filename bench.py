@@ -272,6 +272,67 @@ def serve_bench(args):
         S.close()
 
 
+def config_report(name, steps=20, warmup=5):
+    """One workload in both precisions: V-cycle throughput, the finest sweep against its
+    roofline, and time to 1e-10 (median of 3 solves)."""
+    import torch
+
+    from paper_1609_04809_gb300 import mg, workloads as W
+    c = _config_args(name)
+    k = W.k_blocks(c["n_cells"], dim=3, blocks_per_axis=16, seed=20260101) if c.get("k") == "blocks16" else None
+    modes = W.manufactured_modes(c["dim"]) if c["rhs"] == "manufactured" else None
+    b = mg.mg_load_vector(c["dim"], c["element"], c["n_cells"], modes=modes, f_const=1.0)
+    bd = torch.from_numpy(b).cuda()
+    out = {"workload": name, "n_dofs": int(b.size)}
+    peak, _ = _peaks()
+    for prec, tag in ((mg.MG_FP64, "fp64"), (mg.MG_MIXED, "mixed")):
+        t0 = time.perf_counter()
+        H = mg.Hierarchy(c["dim"], c["element"], c["n_cells"], c["n_levels"], k_cell=k, smoother=c["smoother"],
+                         omega=c["omega"], cheb_degree=c["cheb_degree"], nu_pre=c["nu_pre"], nu_post=c["nu_post"],
+                         precision=prec)
+        setup_s = time.perf_counter() - t0
+        info = H.info()
+        Lf = c["n_levels"] - 1
+        x = torch.zeros_like(bd)
+        H.cycle(bd, x, warmup)
+        mg.mg_profile_enable(H.h, True, classes=[mg.MG_K_SMOOTH], levels=[Lf])
+        x.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        H.cycle(bd, x, steps)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        k_ms, k_cnt, k_bytes, k_flops = mg.mg_profile_read(H.h, mg.MG_K_SMOOTH, Lf)
+        mg.mg_profile_enable(H.h, False)
+        ts, its, rel = [], 0, None
+        for _ in range(4):
+            x.zero_()
+            torch.cuda.synchronize()
+            s0 = time.perf_counter()
+            st, it, hist = H.solve(bd, x, c["tol"])
+            ts.append(time.perf_counter() - s0)
+            its, rel = it, hist[-1]
+        rd = torch.empty_like(bd)
+        true_rel = mg.mg_residual_norm_noalloc(H.h, bd, x, rd) / float(np.linalg.norm(b))
+        ks = k_ms / k_cnt * 1e-3 if k_cnt else None
+        out[tag] = {"dofs_per_s_per_vcycle": b.size / (ms * 1e-3), "ms_per_iteration": ms,
+                    "finest_sweep_us": 1e6 * ks if ks else None,
+                    "finest_sweep_gbs": k_bytes / ks / 1e9 if ks else None,
+                    "finest_sweep_hbm_frac": k_bytes / ks / 1e9 / peak if ks else None,
+                    "finest_sweep_fp64_tflops": k_flops / ks / 1e12 if (ks and tag == "fp64") else None,
+                    "time_to_tol_ms": 1e3 * float(np.median(ts[1:])), "iterations": its,
+                    "final_rel_residual": rel, "true_fp64_rel_residual": true_rel,
+                    "storage": ["csr", "ell", "dia"][info["storage"][Lf] - 1], "setup_s": setup_s,
+                    "device_gb": info["device_bytes"] / 1e9}
+        H.close()
+        del H
+        torch.cuda.empty_cache()
+    out["speedup_mixed_vs_fp64"] = out["fp64"]["time_to_tol_ms"] / out["mixed"]["time_to_tol_ms"]
+    return out
+
+
 def run_reference(args):
     rank = _env_int("RANK", 0)
     if rank != 0:
@@ -466,6 +527,8 @@ def main():
     ap.add_argument("--serve-budget-gb", type=float, default=150.0)
     ap.add_argument("--serve-slots", type=int, default=256)
     ap.add_argument("--no-pdl", action="store_true", help="launch without programmatic dependent launch")
+    ap.add_argument("--all-configs", action="store_true",
+                    help="report every solve workload (FP64 and mixed) instead of the bench line")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                     help="fp64: the workload as specified (headline); mixed: FP32 V-cycle, for analysis")
     args = ap.parse_args()
@@ -473,6 +536,16 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.all_configs:
+        import torch
+
+        import __graft_entry__
+        __graft_entry__.build_library()
+        torch.cuda.set_device(0)
+        from paper_1609_04809_gb300 import workloads as W
+        for name in W.CONFIGS:
+            print(json.dumps(config_report(name)), flush=True)
+        return 0
     return run_ours(args)
 
 
