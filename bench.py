@@ -387,7 +387,7 @@ def run_ours(args):
     H = mg.Hierarchy(c["dim"], c["element"], c["n_cells"], c["n_levels"], smoother=c["smoother"],
                      omega=c["omega"], cheb_degree=c["cheb_degree"], nu_pre=c["nu_pre"], nu_post=c["nu_post"],
                      precision=mg.MG_MIXED if args.precision == "mixed" else mg.MG_FP64,
-                     use_pdl=0 if args.no_pdl else 1)
+                     use_pdl=0 if args.no_pdl else 1, coarse_tail=0 if args.no_tail else 1)
     info = H.info()
     Lf = c["n_levels"] - 1
     bd = torch.from_numpy(b_host).cuda()
@@ -527,6 +527,7 @@ def main():
     ap.add_argument("--serve-budget-gb", type=float, default=150.0)
     ap.add_argument("--serve-slots", type=int, default=256)
     ap.add_argument("--no-pdl", action="store_true", help="launch without programmatic dependent launch")
+    ap.add_argument("--no-tail", action="store_true", help="run the small levels as separate kernels")
     ap.add_argument("--all-configs", action="store_true",
                     help="report every solve workload (FP64 and mixed) instead of the bench line")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],

@@ -96,6 +96,7 @@ typedef struct {
     int max_iters;
     int use_graph;
     int use_pdl; /* launch V-cycle kernels with programmatic dependent launch (default 1) */
+    int coarse_tail; /* run the levels of at most 4096 rows as one thread-block-cluster launch (default 1) */
 } mg_options;
 
 /* Right-hand side f of -div(k grad u) = f: the constant f_const if n_modes == 0, else

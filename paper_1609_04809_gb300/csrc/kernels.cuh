@@ -201,6 +201,207 @@ __global__ void __launch_bounds__(256) k_coarse_solve_warp(const double *__restr
 }
 
 // ------------------------------------------------------------------------------------
+// Coarse-level tail: the V-cycle below a small level in one thread-block-cluster launch
+// ------------------------------------------------------------------------------------
+// The levels with at most a few thousand rows each cost one latency-bound kernel per
+// operation. The host records those operations in V-cycle order (TailOp) and one launch
+// of a cluster of CTAs replays them: rows are spread over all threads of the cluster and
+// a cluster barrier (release/acquire at cluster scope) separates consecutive operations.
+// Each row is computed by the same arithmetic as the single-operation kernels.
+enum TailOpKind { TAIL_SWEEP = 0, TAIL_RESTRICT, TAIL_COARSE, TAIL_PROLONG, TAIL_ZERO };
+constexpr int TAIL_MAX_LEVELS = 8;
+constexpr int TAIL_MAX_OPS = 96;
+
+struct TailOp {
+    int kind, level, mode;
+    int in, out;  // x buffers 0/1; out 2 = the residual vector t
+    int aux;      // RESTRICT: 1 = restrict b itself; PROLONG: coarse buffer
+    double c1, c2;
+};
+
+template <typename T>
+struct TailLevel {
+    MatView<T> A;
+    int n, N;
+    T *x[2];
+    T *b, *t, *d;
+};
+
+template <typename T>
+struct TailProg {
+    TailLevel<T> lev[TAIL_MAX_LEVELS];
+    TailOp ops[TAIL_MAX_OPS];
+    int nops, dim, K;
+    const double *lu;
+    const int *piv;
+    int n0;
+};
+
+template <typename T, int K, int MODE>
+__device__ __forceinline__ void tail_sweep_row(const TailLevel<T> &L, int i, const TailOp &op)
+{
+    constexpr int C = K / 2;
+    T c1 = (T)op.c1, c2 = (T)op.c2;
+    T *o = op.out == 2 ? L.t : L.x[op.out];
+    if (IsZero<MODE>::value) {
+        T dinv = Ar<T>::kStoredDinv ? L.A.dinv[i] : Ar<T>::rcp(L.A.val[(int64_t)C * L.A.ld + i]);
+        sweep_out<T, MODE>(i, T(0), dinv, T(0), L.b, o, L.d, c1, c2);
+        return;
+    }
+    const T *x = L.x[op.in];
+    T a[K], xv[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) a[k] = L.A.val[(int64_t)k * L.A.ld + i];
+#pragma unroll
+    for (int k = 0; k < K; k++) xv[k] = x[i + L.A.offs.o[k]];
+    T s = T(0);
+#pragma unroll
+    for (int k = 0; k < K; k++) s = Ar<T>::mac(s, a[k], xv[k]);
+    T dinv = Ar<T>::kStoredDinv ? L.A.dinv[i] : Ar<T>::rcp(a[C]);
+    sweep_out<T, MODE>(i, s, dinv, xv[C], L.b, o, L.d, c1, c2);
+}
+
+template <typename T, int K>
+__device__ __forceinline__ void tail_sweep(const TailLevel<T> &L, const TailOp &op, int g, int G)
+{
+    for (int i = g; i < L.n; i += G) {
+        switch (op.mode) {
+        case SW_RESID: tail_sweep_row<T, K, SW_RESID>(L, i, op); break;
+        case SW_JACOBI: tail_sweep_row<T, K, SW_JACOBI>(L, i, op); break;
+        case SW_CHEBF: tail_sweep_row<T, K, SW_CHEBF>(L, i, op); break;
+        case SW_CHEB: tail_sweep_row<T, K, SW_CHEB>(L, i, op); break;
+        case SW_JACOBI_Z: tail_sweep_row<T, K, SW_JACOBI_Z>(L, i, op); break;
+        default: tail_sweep_row<T, K, SW_CHEBF_Z>(L, i, op); break;
+        }
+    }
+}
+
+template <typename T, int DIM>
+__device__ __forceinline__ void tail_restrict(const TailLevel<T> &F, const TailLevel<T> &C, const TailOp &op, int g, int G)
+{
+    const T *r = op.aux ? F.b : F.t;
+    int nc1 = C.N - 1, nf1 = F.N - 1;
+    for (int I = g; I < C.n; I += G) {
+        int X = I % nc1 + 1, Y = (I / nc1) % nc1 + 1, Z = DIM == 3 ? I / (nc1 * nc1) + 1 : 0;
+        T s = T(0);
+        const int zlo = DIM == 3 ? -1 : 0, zhi = DIM == 3 ? 1 : 0;
+#pragma unroll
+        for (int dz = zlo; dz <= zhi; dz++)
+#pragma unroll
+            for (int dy = -1; dy <= 1; dy++)
+#pragma unroll
+                for (int dx = -1; dx <= 1; dx++) {
+                    T w = (dx ? T(0.5) : T(1)) * (dy ? T(0.5) : T(1)) * (dz ? T(0.5) : T(1));
+                    int64_t j = (2 * X + dx - 1) + (int64_t)nf1 * ((2 * Y + dy - 1) + (DIM == 3 ? (int64_t)nf1 * (2 * Z + dz - 1) : 0));
+                    s = Ar<T>::mac(s, w, r[j]);
+                }
+        C.b[I] = s;
+    }
+}
+
+template <typename T, int DIM>
+__device__ __forceinline__ void tail_prolong(const TailLevel<T> &F, const TailLevel<T> &C, const TailOp &op, int g, int G)
+{
+    const T *xc = C.x[op.aux];
+    T *xf = F.x[op.out];
+    int Nc = C.N, nf1 = F.N - 1, nc1 = Nc - 1;
+    for (int i = g; i < F.n; i += G) {
+        int v0 = i % nf1 + 1, v1 = (i / nf1) % nf1 + 1, v2 = DIM == 3 ? i / (nf1 * nf1) + 1 : 2;
+        int odd = (v0 & 1) + (v1 & 1) + (DIM == 3 ? (v2 & 1) : 0);
+        const T w = odd == 0 ? T(1) : (odd == 1 ? T(0.5) : (odd == 2 ? T(0.25) : T(0.125)));
+        int x0 = max(v0 >> 1, 1), x1 = min((v0 + 1) >> 1, Nc - 1);
+        int y0 = max(v1 >> 1, 1), y1 = min((v1 + 1) >> 1, Nc - 1);
+        int z0 = DIM == 3 ? max(v2 >> 1, 1) : 1, z1 = DIM == 3 ? min((v2 + 1) >> 1, Nc - 1) : 1;
+        T t = T(0);
+        for (int Z = z0; Z <= z1; Z++)
+            for (int Y = y0; Y <= y1; Y++) {
+                int64_t row = (int64_t)nc1 * ((Y - 1) + (DIM == 3 ? (int64_t)nc1 * (Z - 1) : 0)) - 1;
+                for (int X = x0; X <= x1; X++) t = Ar<T>::mac(t, w, xc[row + X]);
+            }
+        xf[i] = Ar<T>::add(xf[i], t);
+    }
+}
+
+// Launched as one cluster (grid = cluster size) of 512 threads per CTA.
+template <typename T>
+__global__ void __launch_bounds__(512) k_tail(TailProg<T> P)
+{
+    __shared__ double Ls[64 * 64];
+    __shared__ double xs[64];
+    __shared__ int ps[64];
+    pdl_enter();
+    int g = blockIdx.x * blockDim.x + threadIdx.x, G = gridDim.x * blockDim.x;
+    for (int o = 0; o < P.nops; o++) {
+        const TailOp op = P.ops[o];
+        const TailLevel<T> &L = P.lev[op.level];
+        if (op.kind == TAIL_SWEEP) {
+            if (L.A.K == 21)
+                tail_sweep<T, 21>(L, op, g, G);
+            else if (L.A.K == 27)
+                tail_sweep<T, 27>(L, op, g, G);
+            else
+                tail_sweep<T, 9>(L, op, g, G);
+        } else if (op.kind == TAIL_RESTRICT) {
+            if (P.dim == 3)
+                tail_restrict<T, 3>(L, P.lev[op.level - 1], op, g, G);
+            else
+                tail_restrict<T, 2>(L, P.lev[op.level - 1], op, g, G);
+        } else if (op.kind == TAIL_PROLONG) {
+            if (P.dim == 3)
+                tail_prolong<T, 3>(L, P.lev[op.level - 1], op, g, G);
+            else
+                tail_prolong<T, 2>(L, P.lev[op.level - 1], op, g, G);
+        } else if (op.kind == TAIL_ZERO) {
+            for (int i = g; i < L.n; i += G) L.x[op.out][i] = T(0);
+        } else if (blockIdx.x == 0) {  // TAIL_COARSE: the LU solve by the first CTA
+            int n = P.n0, tid = threadIdx.x;
+            for (int k = tid; k < n * n; k += blockDim.x) Ls[k] = P.lu[k];
+            if (tid < n) {
+                xs[tid] = (double)L.b[tid];
+                ps[tid] = P.piv[tid];
+            }
+            __syncthreads();
+            if (tid < 32) {
+                if (tid == 0)
+                    for (int k = 0; k < n; k++) {
+                        int q = ps[k];
+                        if (q != k) {
+                            double tmp = xs[k];
+                            xs[k] = xs[q];
+                            xs[q] = tmp;
+                        }
+                    }
+                __syncwarp();
+                int r0 = tid, r1 = tid + 32;
+                double s0 = 0.0, s1 = 0.0;
+                for (int j = 0; j < n; j++) {
+                    if (j == r0) xs[j] = __dsub_rn(xs[j], s0);
+                    if (j == r1) xs[j] = __dsub_rn(xs[j], s1);
+                    __syncwarp();
+                    double xj = xs[j];
+                    if (r0 > j && r0 < n) s0 = __dadd_rn(s0, __dmul_rn(Ls[r0 * n + j], xj));
+                    if (r1 > j && r1 < n) s1 = __dadd_rn(s1, __dmul_rn(Ls[r1 * n + j], xj));
+                    __syncwarp();
+                }
+                s0 = s1 = 0.0;
+                for (int j = n - 1; j >= 0; j--) {
+                    if (j == r0) xs[j] = __ddiv_rn(__dsub_rn(xs[j], s0), Ls[j * n + j]);
+                    if (j == r1) xs[j] = __ddiv_rn(__dsub_rn(xs[j], s1), Ls[j * n + j]);
+                    __syncwarp();
+                    double xj = xs[j];
+                    if (r0 < j) s0 = __dadd_rn(s0, __dmul_rn(Ls[r0 * n + j], xj));
+                    if (r1 < j) s1 = __dadd_rn(s1, __dmul_rn(Ls[r1 * n + j], xj));
+                    __syncwarp();
+                }
+                for (int k = tid; k < n; k += 32) L.x[0][k] = (T)xs[k];
+            }
+        }
+        // every thread of the cluster finishes op o before any starts op o + 1
+        asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+    }
+}
+
+// ------------------------------------------------------------------------------------
 // FP64 outer residual r = b - A64 x64 with ||r||^2, and helpers
 // ------------------------------------------------------------------------------------
 // Block sums of r^2 in a fixed tree order; the last block to finish (ticket) adds the

@@ -127,6 +127,11 @@ struct mg_hierarchy {
     int kernels_per_cycle = 0;
     int counting = 0;  // counts launches while > 0
     bool with_vectors = true;  // false: operators only (serving keeps vectors per request)
+    // coarse-level tail: levels 0..tail_level run as one cluster launch (-1: none)
+    int tail_level = -1;
+    int tail_cluster = 8;
+    bool tail_rec = false;
+    std::vector<mgk::TailOp> tail_ops;
     std::mutex mu;
 
     ~mg_hierarchy();

@@ -295,6 +295,18 @@ static void sweep(mg_hierarchy *h, int l, int mode, const T *x, const T *b, T *o
                   cudaStream_t s)
 {
     LevelD &L = h->lev[l];
+    if (h->tail_rec && l <= h->tail_level) {  // part of the coarse-level tail launch
+        TailOp op{};
+        op.kind = TAIL_SWEEP;
+        op.level = l;
+        op.mode = mode;
+        op.in = x == (const T *)L.x[1] ? 1 : 0;
+        op.out = out == (T *)L.t ? 2 : (out == (T *)L.x[1] ? 1 : 0);
+        op.c1 = c1;
+        op.c2 = c2;
+        h->tail_ops.push_back(op);
+        return;
+    }
     int sv = sizeof(T);
     double n = (double)L.n;
     double bytes;
@@ -360,6 +372,14 @@ template <typename T>
 static void restrict_to(mg_hierarchy *h, int l, const T *r, cudaStream_t s)
 {
     LevelD &F = h->lev[l], &C = h->lev[l - 1];
+    if (h->tail_rec && l <= h->tail_level) {
+        TailOp op{};
+        op.kind = TAIL_RESTRICT;
+        op.level = l;
+        op.aux = r == (const T *)F.b ? 1 : 0;
+        h->tail_ops.push_back(op);
+        return;
+    }
     int sv = sizeof(T);
     double bytes = (double)F.n * sv + (double)C.n * sv;
     if (!F.structured) bytes += mat_bytes(F.R, sv);
@@ -382,6 +402,15 @@ template <typename T>
 static void prolong_add(mg_hierarchy *h, int l, const T *xc, T *xf, cudaStream_t s)
 {
     LevelD &F = h->lev[l], &C = h->lev[l - 1];
+    if (h->tail_rec && l <= h->tail_level) {
+        TailOp op{};
+        op.kind = TAIL_PROLONG;
+        op.level = l;
+        op.out = xf == (T *)F.x[1] ? 1 : 0;
+        op.aux = xc == (const T *)C.x[1] ? 1 : 0;
+        h->tail_ops.push_back(op);
+        return;
+    }
     int sv = sizeof(T);
     double bytes = 2.0 * F.n * sv + (double)C.n * sv;
     if (!F.structured) bytes += mat_bytes(F.P, sv);
@@ -403,10 +432,54 @@ static void prolong_add(mg_hierarchy *h, int l, const T *xc, T *xf, cudaStream_t
 // V-cycle on the finest level's right-hand side (the defect); returns the buffer of the
 // finest level holding the correction
 template <typename T>
+static void launch_tail(mg_hierarchy *h, cudaStream_t s)
+{
+    TailProg<T> P{};
+    if ((int)h->tail_ops.size() > TAIL_MAX_OPS) throw Error(MG_EINVAL, "coarse-level tail has too many operations");
+    for (int l = 0; l <= h->tail_level; l++) {
+        LevelD &L = h->lev[l];
+        P.lev[l].A = view<T>(L.A);
+        P.lev[l].n = (int)L.n;
+        P.lev[l].N = L.N;
+        P.lev[l].x[0] = (T *)L.x[0];
+        P.lev[l].x[1] = (T *)L.x[1];
+        P.lev[l].b = (T *)L.b;
+        P.lev[l].t = (T *)L.t;
+        P.lev[l].d = (T *)L.d;
+    }
+    for (size_t k = 0; k < h->tail_ops.size(); k++) P.ops[k] = h->tail_ops[k];
+    P.nops = (int)h->tail_ops.size();
+    P.dim = h->dim;
+    P.K = h->lev[h->tail_level].A.K;
+    P.lu = h->lu;
+    P.piv = h->piv;
+    P.n0 = h->n0;
+    LaunchScope ls(h, s, MG_K_COARSE, 0, 0.0);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(h->tail_cluster);
+    cfg.blockDim = dim3(512);
+    cfg.stream = s;
+    cudaLaunchAttribute at[2];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = h->tail_cluster;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[1].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = h->opt.use_pdl ? 2 : 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k_tail<T>, P);
+    if (e != cudaSuccess) throw Error(MG_ECUDA, std::string("coarse-level tail launch: ") + cudaGetErrorString(e));
+    h->tail_ops.clear();
+}
+
+template <typename T>
 static int enqueue_vcycle(mg_hierarchy *h, cudaStream_t s)
 {
     int Lf = h->Lf;
     std::vector<int> cur((size_t)h->nlev, -1);
+    h->tail_ops.clear();
+    h->tail_rec = h->tail_level >= 1;
     for (int l = Lf; l >= 1; l--) {  // pre-smoothing and restriction of the residual
         LevelD &L = h->lev[l];
         int c = -1;
@@ -421,7 +494,13 @@ static int enqueue_vcycle(mg_hierarchy *h, cudaStream_t s)
         restrict_to<T>(h, l, r, s);
         cur[l] = c;
     }
-    {  // exact solve on the coarsest level
+    if (h->tail_rec) {  // the coarsest solve belongs to the tail launch
+        TailOp op{};
+        op.kind = TAIL_COARSE;
+        op.level = 0;
+        h->tail_ops.push_back(op);
+        cur[0] = 0;
+    } else {  // exact solve on the coarsest level
         LevelD &C = h->lev[0];
         LaunchScope ls(h, s, MG_K_COARSE, 0, (double)h->n0 * h->n0 * 8 + 2.0 * h->n0 * sizeof(T));
         bool pdl = h->opt.use_pdl != 0;
@@ -439,12 +518,28 @@ static int enqueue_vcycle(mg_hierarchy *h, cudaStream_t s)
     }
     for (int l = 1; l <= Lf; l++) {  // prolongation, correction and post-smoothing
         LevelD &L = h->lev[l];
+        if (h->tail_rec && l == h->tail_level + 1) {  // leaving the tail: replay it in one launch
+            launch_tail<T>(h, s);
+            h->tail_rec = false;
+        }
         if (cur[l] < 0) {
-            CK(cudaMemsetAsync(L.x[0], 0, (size_t)L.n * sizeof(T), s));
+            if (h->tail_rec && l <= h->tail_level) {
+                TailOp op{};
+                op.kind = TAIL_ZERO;
+                op.level = l;
+                op.out = 0;
+                h->tail_ops.push_back(op);
+            } else {
+                CK(cudaMemsetAsync(L.x[0], 0, (size_t)L.n * sizeof(T), s));
+            }
             cur[l] = 0;
         }
         prolong_add<T>(h, l, (const T *)h->lev[l - 1].x[cur[l - 1]], (T *)L.x[cur[l]], s);
         for (int a = 0; a < h->opt.nu_post; a++) cur[l] = smooth<T>(h, l, cur[l], s);
+    }
+    if (h->tail_rec) {  // the whole hierarchy was the tail
+        launch_tail<T>(h, s);
+        h->tail_rec = false;
     }
     return cur[Lf];
 }
@@ -604,6 +699,7 @@ extern "C" void mg_options_default(mg_options *o)
     o->max_iters = 100;
     o->use_graph = 1;
     o->use_pdl = 1;
+    o->coarse_tail = 1;
 }
 
 extern "C" int64_t mg_ndofs(int dim, int element, int n_cells)
@@ -1081,6 +1177,36 @@ void mgi::build_hierarchy(mg_hierarchy *h, const mg_problem *p, const mg_options
         CK(cudaMemcpyAsync(&info, h->d_info, 4, cudaMemcpyDeviceToHost, h->s));
         CK(cudaStreamSynchronize(h->s));
         if (info) throw Error(MG_EINVAL, "coarsest matrix is singular");
+    }
+    // ---- coarse-level tail: the levels of at most 4096 rows in one cluster launch ----
+    h->tail_level = -1;
+    if (o->coarse_tail && h->n0 <= 64) {
+        int t = -1;
+        for (int l = 0; l <= Lf; l++) {
+            const LevelD &L = h->lev[l];
+            bool ok = L.n <= 4096 && L.fmt == MG_STORAGE_DIA && (l == 0 || L.structured);
+            if (!ok) break;
+            t = l;
+        }
+        if (t >= 1 && t < TAIL_MAX_LEVELS) {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(h->tail_cluster);
+            cfg.blockDim = dim3(512);
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = h->tail_cluster;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            int nclusters = 0;
+            cudaError_t e = h->mixed ? cudaOccupancyMaxActiveClusters(&nclusters, k_tail<float>, &cfg)
+                                     : cudaOccupancyMaxActiveClusters(&nclusters, k_tail<double>, &cfg);
+            if (e == cudaSuccess && nclusters > 0)
+                h->tail_level = t;
+            else
+                cudaGetLastError();
+        }
     }
     // ---- launch count of one iteration, graphs ----
     if (!with_vectors) {

@@ -99,6 +99,28 @@ def test_fp64_every_storage_and_graph_mode(orc, storage, graph):
     _assert_fp64_parity(g, o)
 
 
+@pytest.mark.parametrize("dim,N,L,sm", [(3, 32, 4, 1), (2, 64, 5, 0), (3, 16, 3, 0)])
+@pytest.mark.parametrize("precision", [mg.MG_FP64, mg.MG_MIXED])
+def test_coarse_level_tail_changes_no_bit(orc, dim, N, L, sm, precision):
+    """Levels of at most 4096 rows run as one cluster launch; results are identical."""
+    b = W.random_vector(mg.mg_ndofs(dim, 0, N), seed=14)
+    bd = torch.from_numpy(b).cuda()
+    xs, its = [], []
+    for tail in (0, 1):
+        H = mg.Hierarchy(dim, 0, N, L, smoother=sm, nu_pre=1 if sm else 2, nu_post=1 if sm else 2,
+                         precision=precision, coarse_tail=tail)
+        x = torch.zeros_like(bd)
+        st, it, hist = H.solve(bd, x, 1e-10)
+        assert st == mg.MG_OK
+        xs.append(x.cpu().numpy())
+        its.append(it)
+    assert its[0] == its[1] and np.array_equal(xs[0], xs[1])
+    if precision == mg.MG_FP64:  # and both equal the oracle
+        O = orc.Hierarchy(dim, 0, N, L, opts=_orc_opts(orc, sm, 0.8, 1 if sm else 2, 1 if sm else 2))
+        xo, ho, ito, conv = O.solve(b, 1e-10)
+        assert np.array_equal(xs[1], xo)
+
+
 @pytest.mark.parametrize("precision", [mg.MG_FP64, mg.MG_MIXED])
 def test_programmatic_dependent_launch_changes_no_bit(precision):
     dim, elem, N, L = 3, 0, 32, 4
