@@ -1188,6 +1188,11 @@ void mgi::build_hierarchy(mg_hierarchy *h, const mg_problem *p, const mg_options
             if (!ok) break;
             t = l;
         }
+        // operations one V-cycle records per tail level: the sweeps of pre- and post-smoothing,
+        // the residual, the restriction, the zeroing of the correction and the prolongation
+        int64_t spc = o->smoother == MG_JACOBI ? 1 : o->cheb_degree;
+        int64_t per_level = ((int64_t)o->nu_pre + o->nu_post) * spc + 4;
+        while (t >= 1 && 1 + t * per_level > TAIL_MAX_OPS) t--;
         if (t >= 1 && t < TAIL_MAX_LEVELS) {
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3(h->tail_cluster);

@@ -121,6 +121,19 @@ def test_coarse_level_tail_changes_no_bit(orc, dim, N, L, sm, precision):
         assert np.array_equal(xs[1], xo)
 
 
+def test_coarse_level_tail_with_long_smoothing_fits_its_operation_list():
+    """Chebyshev of degree 8 with 3+3 steps records 52 operations per level: fewer levels join the tail."""
+    b = torch.from_numpy(W.random_vector(mg.mg_ndofs(3, 0, 32), seed=15)).cuda()
+    xs = []
+    for tail in (0, 1):
+        H = mg.Hierarchy(3, 0, 32, 4, smoother=1, cheb_degree=8, nu_pre=3, nu_post=3, coarse_tail=tail)
+        x = torch.zeros_like(b)
+        st, it, hist = H.solve(b, x, 1e-10)
+        assert st == mg.MG_OK
+        xs.append(x.cpu().numpy())
+    assert np.array_equal(xs[0], xs[1])
+
+
 @pytest.mark.parametrize("precision", [mg.MG_FP64, mg.MG_MIXED])
 def test_programmatic_dependent_launch_changes_no_bit(precision):
     dim, elem, N, L = 3, 0, 32, 4
