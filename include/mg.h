@@ -96,7 +96,10 @@ typedef struct {
     int max_iters;
     int use_graph;
     int use_pdl; /* launch V-cycle kernels with programmatic dependent launch (default 1) */
-    int coarse_tail; /* run the levels of at most 4096 rows as one thread-block-cluster launch (default 1) */
+    int coarse_tail; /* the levels of at most 4096 rows as one thread-block-cluster launch:
+                        0 never, 1 whenever it applies, 2 (default) where setup measures the
+                        captured V-cycle faster with it than without (always when use_graph
+                        is 0); every choice computes the same bits */
 } mg_options;
 
 /* Right-hand side f of -div(k grad u) = f: the constant f_const if n_modes == 0, else
@@ -133,6 +136,7 @@ typedef struct {
     double lambda[MG_MAX_LEVELS];   /* power-method estimate of lambda_max(D^-1 A), 0 if unused */
     size_t device_bytes;            /* device memory held by the hierarchy */
     int kernels_per_cycle;          /* kernel launches in one defect-correction iteration */
+    int tail_levels;                /* levels replayed by the coarse-level tail launch (0: none) */
 } mg_info;
 
 void mg_options_default(mg_options *o);

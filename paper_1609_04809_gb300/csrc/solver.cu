@@ -631,6 +631,31 @@ static void ensure_graphs(mg_hierarchy *h)
     h->g_v = capture(h, enqueue_v, &h->rec_v);
 }
 
+// median device time of the captured V-cycle (with the update), from the hierarchy's own
+// vectors; used at setup to choose between launch plans that compute the same bits
+static double time_vcycle_graph(mg_hierarchy *h)
+{
+    cudaGraphExec_t ge = capture(h, enqueue_v, nullptr);
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    std::vector<float> ms;
+    for (int r = 0; r < 25; r++) {
+        CK(cudaEventRecord(e0, h->s));
+        CK(cudaGraphLaunch(ge, h->s));
+        CK(cudaEventRecord(e1, h->s));
+        CK(cudaEventSynchronize(e1));
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, e0, e1));
+        if (r >= 5) ms.push_back(t);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaGraphExecDestroy(ge);
+    std::sort(ms.begin(), ms.end());
+    return ms[ms.size() / 2];
+}
+
 static void run_r(mg_hierarchy *h)
 {
     if (h->opt.use_graph) {
@@ -699,7 +724,7 @@ extern "C" void mg_options_default(mg_options *o)
     o->max_iters = 100;
     o->use_graph = 1;
     o->use_pdl = 1;
-    o->coarse_tail = 1;
+    o->coarse_tail = 2;
 }
 
 extern "C" int64_t mg_ndofs(int dim, int element, int n_cells)
@@ -1218,6 +1243,16 @@ void mgi::build_hierarchy(mg_hierarchy *h, const mg_problem *p, const mg_options
         CK(cudaStreamSynchronize(h->s));
         return;
     }
+    if (o->coarse_tail == 2 && h->tail_level >= 1 && h->opt.use_graph) {
+        // keep the tail only where the captured V-cycle is measurably faster with it
+        double with_tail = time_vcycle_graph(h);
+        int t = h->tail_level;
+        h->tail_level = -1;
+        destroy_graphs(h);
+        double without = time_vcycle_graph(h);
+        destroy_graphs(h);
+        if (with_tail < 0.98 * without) h->tail_level = t;
+    }
     h->counting = 1;
     h->kernels_per_cycle = 0;
     {
@@ -1290,6 +1325,7 @@ extern "C" mg_status mg_get_info(const mg_hierarchy *h, mg_info *info)
     }
     info->device_bytes = h->slab.size;
     info->kernels_per_cycle = h->kernels_per_cycle;
+    info->tail_levels = h->tail_level + 1;
     return MG_OK;
 }
 

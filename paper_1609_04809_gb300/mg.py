@@ -63,7 +63,7 @@ class mg_info(ctypes.Structure):
                 ("n", ctypes.c_int64 * MG_MAX_LEVELS), ("nnz", ctypes.c_int64 * MG_MAX_LEVELS),
                 ("storage", ctypes.c_int * MG_MAX_LEVELS), ("galerkin", ctypes.c_int * MG_MAX_LEVELS),
                 ("lambda_", ctypes.c_double * MG_MAX_LEVELS), ("device_bytes", ctypes.c_size_t),
-                ("kernels_per_cycle", ctypes.c_int)]
+                ("kernels_per_cycle", ctypes.c_int), ("tail_levels", ctypes.c_int)]
 
 
 class mg_serve_config(ctypes.Structure):
@@ -277,7 +277,7 @@ def mg_get_info(h):
     return dict(n_levels=L, precision=info.precision, n=list(info.n[:L]), nnz=list(info.nnz[:L]),
                 storage=list(info.storage[:L]), galerkin=list(info.galerkin[:L]),
                 lambda_=list(info.lambda_[:L]), device_bytes=int(info.device_bytes),
-                kernels_per_cycle=info.kernels_per_cycle)
+                kernels_per_cycle=info.kernels_per_cycle, tail_levels=info.tail_levels)
 
 
 def mg_solve(h, b_dev, x_dev, rel_tol, max_iters=100):

@@ -109,12 +109,19 @@ def test_coarse_level_tail_changes_no_bit(orc, dim, N, L, sm, precision):
     for tail in (0, 1):
         H = mg.Hierarchy(dim, 0, N, L, smoother=sm, nu_pre=1 if sm else 2, nu_post=1 if sm else 2,
                          precision=precision, coarse_tail=tail)
+        assert (H.info()["tail_levels"] > 0) == bool(tail)
         x = torch.zeros_like(bd)
         st, it, hist = H.solve(bd, x, 1e-10)
         assert st == mg.MG_OK
         xs.append(x.cpu().numpy())
         its.append(it)
     assert its[0] == its[1] and np.array_equal(xs[0], xs[1])
+    # the default measures both launch plans at setup and keeps the faster; same bits again
+    H = mg.Hierarchy(dim, 0, N, L, smoother=sm, nu_pre=1 if sm else 2, nu_post=1 if sm else 2,
+                     precision=precision)
+    x = torch.zeros_like(bd)
+    H.solve(bd, x, 1e-10)
+    assert np.array_equal(x.cpu().numpy(), xs[0])
     if precision == mg.MG_FP64:  # and both equal the oracle
         O = orc.Hierarchy(dim, 0, N, L, opts=_orc_opts(orc, sm, 0.8, 1 if sm else 2, 1 if sm else 2))
         xo, ho, ito, conv = O.solve(b, 1e-10)
@@ -226,7 +233,8 @@ def test_host_entry_point_and_fixed_cycles(orc):
 def test_profiled_launch_counts(orc):
     dim, elem, N, L = 3, 0, 16, 3
     b = torch.from_numpy(W.random_vector(mg.mg_ndofs(dim, elem, N), seed=2)).cuda()
-    H = mg.Hierarchy(dim, elem, N, L, smoother=1, nu_pre=1, nu_post=1)
+    # one launch per operation (at 16^3 every level would otherwise join the tail launch)
+    H = mg.Hierarchy(dim, elem, N, L, smoother=1, nu_pre=1, nu_post=1, coarse_tail=0)
     mg.mg_profile_enable(H.h, True)  # every class and level
     x = torch.zeros_like(b)
     H.cycle(b, x, 3)
@@ -237,6 +245,14 @@ def test_profiled_launch_counts(orc):
     assert H.info()["storage"][L - 1] == mg.MG_STORAGE_DIA
     assert cnt == 3 * 3 and ms > 0 and byts >= 21 * 15 ** 3 * 8 + 3 * 15 ** 3 * 8
     assert flops >= 2 * 21 * 15 ** 3
+    # with the tail the whole V-cycle is one cluster launch, profiled as the coarse solve
+    T = mg.Hierarchy(dim, elem, N, L, smoother=1, nu_pre=1, nu_post=1, coarse_tail=1)
+    mg.mg_profile_enable(T.h, True)
+    T.cycle(b, torch.zeros_like(b), 3)
+    total = sum(mg.mg_profile_read(T.h, k, l)[1] for k in range(mg.MG_K_COUNT) for l in range(L))
+    assert total == 3 * T.info()["kernels_per_cycle"] < 3 * H.info()["kernels_per_cycle"]
+    assert mg.mg_profile_read(T.h, mg.MG_K_COARSE, 0)[1] == 3
+    assert all(mg.mg_profile_read(T.h, mg.MG_K_SMOOTH, l)[1] == 0 for l in range(L))
 
 
 @pytest.mark.parametrize("dim,elem,N,L,sm", [(3, 0, 32, 4, 1), (3, 1, 16, 4, 0), (2, 0, 128, 6, 0)])
