@@ -16,6 +16,8 @@ Which parts of the paper each function follows:
   * ``Hierarchy.solve``: V-cycles of the paper's V-cycle algorithm (Sec. 5.3) inside a
     defect-correction loop that stops at a relative residual.
   * ``load_vector``: the load vector of the sparse FE system.
+  * ``colours`` / ``gs_sweep``: the multicolour Gauss-Seidel smoother (the paper's
+    Gauss-Seidel step, Eq. GS, on DOFs numbered colour-wise, Sec. 4 "DOF Reordering").
 """
 import ctypes
 import os
@@ -31,7 +33,7 @@ _LIB_DIR = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_LIB_DIR, "liboracle.so")
 
 Q1, RQ1 = 0, 1
-JACOBI, CHEBYSHEV = 0, 1
+JACOBI, CHEBYSHEV, GAUSS_SEIDEL = 0, 1, 2
 
 _lib = None
 
@@ -97,6 +99,11 @@ def lib():
         L.orc_lu_factor.restype = ctypes.c_int
         L.orc_lu_factor.argtypes = [dp, ctypes.c_int, ip]
         L.orc_lu_solve.argtypes = [dp, ctypes.c_int, ip, dp, dp]
+        L.orc_n_colours.restype = ctypes.c_int
+        L.orc_n_colours.argtypes = [ctypes.c_int] * 2
+        L.orc_colour.restype = ctypes.c_int
+        L.orc_colour.argtypes = [ctypes.c_int] * 3 + [ctypes.c_int64]
+        L.orc_gs_sweep.argtypes = [P(_CSR), dp, ip, ctypes.c_int, ctypes.c_int, dp, dp]
         L.orc_power_lambda.restype = ctypes.c_double
         L.orc_power_lambda.argtypes = [P(_CSR), dp, ctypes.c_int, ctypes.c_uint64]
         _lib = L
@@ -215,11 +222,37 @@ def l2_error(dim, elem, N, modes, x):
     return float(L.orc_l2_error(dim, elem, N, nm, _dp(amp), _ip(kf), _dp(_rq1_basis()), _dp(x)))
 
 
+def _c_csr(A):
+    return _CSR(A.shape[0], A.shape[1], len(A.val),
+                A.rowptr.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                A.col.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _dp(A.val))
+
+
+def n_colours(dim, elem):
+    return int(lib().orc_n_colours(dim, elem))
+
+
+def colours(dim, elem, N):
+    """Gauss-Seidel colour of every DOF (parity colouring, see mg_oracle.c)."""
+    n = ndofs(dim, elem, N)
+    L = lib()
+    return np.array([L.orc_colour(dim, elem, N, i) for i in range(n)], dtype=np.intc)
+
+
+def gs_sweep(A, colour, ncol, b, x, backward=False):
+    """One multicolour Gauss-Seidel sweep (returns the new x; x is not modified)."""
+    c = _c_csr(A)
+    d = A.to_scipy().diagonal()
+    dinv = np.array([1.0 / v for v in d])
+    x = np.array(x, dtype=np.float64)
+    colour = np.ascontiguousarray(colour, dtype=np.intc)
+    lib().orc_gs_sweep(ctypes.byref(c), _dp(dinv), _ip(colour), ncol, int(backward), _dp(_f64(b)), _dp(x))
+    return x
+
+
 def spmv(A, x):
     """y = A x with the oracle's sequential row sums."""
-    c = _CSR(A.shape[0], A.shape[1], len(A.val),
-             A.rowptr.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
-             A.col.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _dp(A.val))
+    c = _c_csr(A)
     x = _f64(x)
     y = np.zeros(A.shape[0])
     lib().orc_spmv(ctypes.byref(c), _dp(x), _dp(y))

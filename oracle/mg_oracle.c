@@ -23,6 +23,8 @@
  *                                  (IEEE 754 fusedMultiplyAdd: one rounding per term)
  *   residual r_i = b_i - y_i
  *   damped Jacobi x_i <- x_i + omega*(dinv_i*r_i),    dinv_i = 1.0/a_ii
+ *   Gauss-Seidel  x_i <- x_i + dinv_i*(b_i - sum_j a_ij x_j), rows one at a time in
+ *                 colour order (the latest value of every x_j is used)
  *   Chebyshev step  d_i <- c1*d_i + c2*(dinv_i*r_i),  x_i <- x_i + d_i
  *   restriction b_c = R r with R = P^T stored by rows (fine index ascending)
  *   prolongation x_i <- x_i + t_i,  t_i = sum_J p_iJ c_J   (coarse index ascending, fused)
@@ -62,6 +64,9 @@ void orc_csr_free(orc_csr *m)
 /*        (i-1) + (N-1)*(j + N*k); family y: i + N*((j-1) + (N-1)*k);                */
 /*        family z: i + N*(j + N*(k-1)); families stored x, then y, then z.          */
 /* ------------------------------------------------------------------------------ */
+
+int orc_colour(int dim, int elem, int N, int64_t i);
+int orc_n_colours(int dim, int elem);
 
 int64_t orc_ndofs(int dim, int elem, int N)
 {
@@ -783,10 +788,11 @@ typedef struct {
     int *piv;
     int n0;
     double *b[ORC_MAXLEV], *x[ORC_MAXLEV], *r[ORC_MAXLEV], *t[ORC_MAXLEV], *d[ORC_MAXLEV];
+    int *colour[ORC_MAXLEV];    /* Gauss-Seidel colour of every DOF */
 } orc_hier;
 
 typedef struct {
-    int smoother;       /* 0: damped Jacobi, 1: Chebyshev */
+    int smoother;       /* 0: damped Jacobi, 1: Chebyshev, 2: multicolour Gauss-Seidel */
     double omega;       /* Jacobi damping */
     int cheb_degree;    /* matrix-vector products per Chebyshev application */
     int nu_pre, nu_post;/* smoother applications before / after the coarse correction */
@@ -847,6 +853,7 @@ void orc_free(orc_hier *H)
         free(H->r[l]);
         free(H->t[l]);
         free(H->d[l]);
+        free(H->colour[l]);
     }
     free(H->lu);
     free(H->piv);
@@ -939,6 +946,9 @@ orc_hier *orc_setup(int dim, int elem, int N_finest, int n_levels, const double 
         H->r[l] = (double *)calloc((size_t)n, sizeof(double));
         H->t[l] = (double *)calloc((size_t)n, sizeof(double));
         H->d[l] = (double *)calloc((size_t)n, sizeof(double));
+        H->colour[l] = (int *)malloc((size_t)n * sizeof(int));
+        for (int64_t i = 0; i < n; i++)
+            H->colour[l][i] = orc_colour(dim, elem, H->N[l], i);
         H->lam[l] = (l > 0 && power_iters > 0) ? orc_power_lambda(&H->A[l], H->dinv[l], power_iters, power_seed) : 0.0;
     }
     /* coarsest: dense copy and LU factorisation */
@@ -956,14 +966,75 @@ orc_hier *orc_setup(int dim, int elem, int N_finest, int n_levels, const double 
     return H;
 }
 
-/* one application of the smoother on level l: damped Jacobi sweeps or one Chebyshev
- * polynomial (the paper's smoothing step, Sec. 5.3: "a few iterations" of a simple
- * iterative method) */
-static void smooth(orc_hier *H, const orc_opts *o, int l, const double *b, double *x)
+/*
+ * Colour of DOF i for the multicolour Gauss-Seidel smoother. The paper colours the DOFs
+ * of its hybrid computations and numbers them colour-wise (Sec. 4, "DOF Reordering");
+ * the colouring is the natural one of each element, such that two DOFs of one colour
+ * never share a cell, hence are never coupled by A:
+ *   Q1:  parity of each vertex coordinate, colour = (vx&1) + 2(vy&1) [+ 4(vz&1)]
+ *        (two vertices of one cell differ by 1 in some coordinate);
+ *   RQ1: face family and parity of the normal position, colour = 2f + (p&1)
+ *        (the two faces of one family in a cell sit at p and p+1).
+ */
+int orc_n_colours(int dim, int elem) { return elem == ORC_Q1 ? (1 << dim) : 6; }
+
+int orc_colour(int dim, int elem, int N, int64_t i)
+{
+    int64_t n1 = N - 1, NN = N;
+    if (elem == ORC_Q1) {
+        int vx = (int)(i % n1) + 1;
+        int vy = (int)((i / n1) % n1) + 1;
+        int c = (vx & 1) + 2 * (vy & 1);
+        if (dim == 3)
+            c += 4 * (((int)(i / (n1 * n1)) + 1) & 1);
+        return c;
+    }
+    int64_t fam = n1 * NN * NN;
+    int f = (int)(i / fam);
+    int64_t r = i % fam;
+    int p;
+    if (f == 0)
+        p = (int)(r % n1) + 1;
+    else if (f == 1)
+        p = (int)((r / NN) % n1) + 1;
+    else
+        p = (int)(r / (NN * NN)) + 1;
+    return 2 * f + (p & 1);
+}
+
+/* one Gauss-Seidel sweep over the colours in increasing order (forward) or decreasing
+ * order (backward): within a colour the rows are independent, so visiting them in
+ * index order is the same as updating them all at once from the current x */
+void orc_gs_sweep(const orc_csr *A, const double *dinv, const int *colour, int ncol, int backward,
+                  const double *b, double *x)
+{
+    int64_t n = A->nrows;
+    for (int cc = 0; cc < ncol; cc++) {
+        int c = backward ? ncol - 1 - cc : cc;
+        for (int64_t i = 0; i < n; i++) {
+            if (colour[i] != c)
+                continue;
+            double s = 0.0;
+            for (int64_t k = A->rowptr[i]; k < A->rowptr[i + 1]; k++)
+                s = fma(A->val[k], x[A->col[k]], s);
+            x[i] = x[i] + dinv[i] * (b[i] - s);
+        }
+    }
+}
+
+/* one application of the smoother on level l: damped Jacobi sweeps, one Chebyshev
+ * polynomial, or one multicolour Gauss-Seidel sweep, backward in post-smoothing so that
+ * the V-cycle is a symmetric operator (the paper's smoothing step, Sec. 5.3: "a few
+ * iterations" of Jacobi or Gauss-Seidel) */
+static void smooth(orc_hier *H, const orc_opts *o, int l, const double *b, double *x, int post)
 {
     const orc_csr *A = &H->A[l];
     int64_t n = A->nrows;
     double *r = H->r[l], *dinv = H->dinv[l], *t = H->t[l], *d = H->d[l];
+    if (o->smoother == 2) {
+        orc_gs_sweep(A, dinv, H->colour[l], orc_n_colours(H->dim, H->elem), post, b, x);
+        return;
+    }
     if (o->smoother == 0) {
         residual(A, b, x, r);
         for (int64_t i = 0; i < n; i++)
@@ -1005,7 +1076,7 @@ static void vcycle(orc_hier *H, const orc_opts *o, int l, const double *b, doubl
     const orc_csr *A = &H->A[l];
     int64_t n = A->nrows;
     for (int s = 0; s < o->nu_pre; s++) /* pre-smoothing */
-        smooth(H, o, l, b, x);
+        smooth(H, o, l, b, x, 0);
     residual(A, b, x, H->r[l]);          /* restriction of the residual */
     double *bc = H->b[l - 1], *xc = H->x[l - 1];
     orc_spmv(&H->R[l], H->r[l], bc);
@@ -1018,7 +1089,7 @@ static void vcycle(orc_hier *H, const orc_opts *o, int l, const double *b, doubl
         x[i] = x[i] + t;
     }
     for (int s = 0; s < o->nu_post; s++) /* post-smoothing */
-        smooth(H, o, l, b, x);
+        smooth(H, o, l, b, x, 1);
 }
 
 /* one V-cycle applied to the defect: c = V(r), c starting from zero */

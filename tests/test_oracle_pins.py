@@ -384,7 +384,8 @@ def test_mg_matches_dst_exact_solution(orc, dim, N, L):
 
 @pytest.mark.parametrize("dim,elem,N,L,smoother", [(2, 0, 16, 3, 0), (3, 0, 8, 3, 0),
                                                     (3, 1, 4, 2, 0), (3, 0, 8, 3, 1),
-                                                    (3, 1, 8, 3, 1)])
+                                                    (3, 1, 8, 3, 1), (2, 0, 16, 3, 2),
+                                                    (3, 0, 8, 3, 2), (3, 1, 8, 3, 2)])
 def test_mg_matches_dense_solve(orc, dim, elem, N, L, smoother):
     opts = orc.Options(smoother=smoother, omega=0.7 if elem else 0.8,
                        nu_pre=1 if smoother else 2, nu_post=1 if smoother else 2)
@@ -394,6 +395,20 @@ def test_mg_matches_dense_solve(orc, dim, elem, N, L, smoother):
     assert conv and np.all(np.diff(hist) < 0)
     xd = np.linalg.solve(H.A(L - 1).dense(), b)
     assert np.linalg.norm(x - xd) <= 1e-9 * np.linalg.norm(xd)
+
+
+def _level_colours(H, l):
+    from oracle import colours
+    return colours(H.dim, H.elem, H.level_N(l))
+
+
+def _colour_triangles(A, col):
+    """Strictly lower / upper parts of dense A in the order (colour, index)."""
+    n = A.shape[0]
+    key = col.astype(np.int64) * n + np.arange(n)
+    before = key[None, :] < key[:, None]  # column j is visited before row i
+    after = key[None, :] > key[:, None]
+    return np.where(before, A, 0.0), np.where(after, A, 0.0)
 
 
 def _vcycle_operator(H, opts, l):
@@ -407,6 +422,11 @@ def _vcycle_operator(H, opts, l):
     if opts.smoother == 0:
         S = np.linalg.matrix_power(I - opts.omega * Dinv @ A, opts.nu_pre)
         T = np.linalg.matrix_power(I - opts.omega * Dinv @ A, opts.nu_post)
+    elif opts.smoother == 2:  # Gauss-Seidel in colour order: forward before, backward after
+        Lo, Up = _colour_triangles(A, _level_colours(H, l))
+        D = np.diag(np.diag(A))
+        S = np.linalg.matrix_power(I - np.linalg.solve(D + Lo, A), opts.nu_pre)
+        T = np.linalg.matrix_power(I - np.linalg.solve(D + Up, A), opts.nu_post)
     else:  # Chebyshev: error polynomial T_k((theta - t)/delta) / T_k(theta/delta)
         hi = opts.cheb_hi * H.lam(l)
         lo = hi / opts.cheb_ratio
@@ -430,7 +450,8 @@ def _vcycle_operator(H, opts, l):
 
 
 @pytest.mark.parametrize("dim,elem,N,L,smoother", [(2, 0, 16, 3, 0), (2, 0, 16, 3, 1),
-                                                    (3, 1, 4, 2, 0), (3, 1, 4, 2, 1)])
+                                                    (3, 1, 4, 2, 0), (3, 1, 4, 2, 1),
+                                                    (2, 0, 16, 3, 2), (3, 0, 8, 3, 2), (3, 1, 4, 2, 2)])
 def test_vcycle_equals_closed_form_operator(orc, dim, elem, N, L, smoother):
     opts = orc.Options(smoother=smoother, omega=0.7, nu_pre=2 if not smoother else 1,
                        nu_post=1 if not smoother else 2, cheb_degree=3 if smoother else 2)
@@ -498,3 +519,100 @@ def test_contraction_is_h_independent(orc):
         rates.append((hist[-1] / hist[1]) ** (1.0 / (len(hist) - 2)))
     rates = np.array(rates)
     assert np.all(rates < 0.2) and rates.max() / rates.min() < 1.2, rates
+
+
+# ---------------------------------------------------------------------------------
+# Multicolour Gauss-Seidel (the paper's smoother, Eq. GS, on colour-wise numbered DOFs)
+# ---------------------------------------------------------------------------------
+@pytest.mark.parametrize("dim,elem,N", [(2, 0, 8), (2, 0, 9), (3, 0, 8), (3, 1, 6), (3, 1, 5)])
+def test_gs_colouring_is_valid_and_counts_parity_classes(orc, dim, elem, N):
+    A = orc.assemble(dim, elem, N).to_scipy().tocoo()
+    col = orc.colours(dim, elem, N)
+    off = A.row != A.col
+    assert not np.any(col[A.row[off]] == col[A.col[off]])  # no coupling inside a colour
+    n1 = N - 1
+    odd, even = (n1 + 1) // 2, n1 // 2  # positions 1..N-1 with parity 1 / 0
+    cnt = np.bincount(col, minlength=orc.n_colours(dim, elem))
+    if elem == orc.Q1:
+        for c in range(1 << dim):
+            want = 1
+            for d in range(dim):
+                want *= odd if (c >> d) & 1 else even
+            assert cnt[c] == want
+    else:
+        assert list(cnt) == [even * N * N, odd * N * N] * 3
+
+
+def test_gs_colouring_valid_on_galerkin_levels(orc):
+    k = W.k_blocks(16, dim=3, blocks_per_axis=16, seed=20260101)  # one value per cell
+    H = orc.Hierarchy(3, orc.Q1, 16, 3, k_cell=k, opts=orc.Options(smoother=orc.GAUSS_SEIDEL))
+    assert H.galerkin(0) and H.galerkin(1)
+    for l in range(3):
+        A = H.A(l).to_scipy().tocoo()
+        col = orc.colours(3, orc.Q1, H.level_N(l))
+        off = (A.row != A.col) & (A.data != 0)
+        assert not np.any(col[A.row[off]] == col[A.col[off]])
+
+
+@pytest.mark.parametrize("dim,elem,N", [(2, 0, 12), (3, 0, 6), (3, 1, 4)])
+@pytest.mark.parametrize("backward", [False, True])
+def test_gs_sweep_is_a_triangular_solve(orc, dim, elem, N, backward):
+    """x' = x + (D + L)^-1 (b - A x), L the couplings to earlier colours (later ones backward)."""
+    import scipy.sparse.linalg as sla
+    Ao = orc.assemble(dim, elem, N)
+    A = Ao.to_scipy().tocsr()
+    col = orc.colours(dim, elem, N)
+    n = A.shape[0]
+    order = np.lexsort((np.arange(n), col))  # colour-wise numbering, index order inside
+    Ap = A[order][:, order]
+    T = sp.triu(Ap, format="csr") if backward else sp.tril(Ap, format="csr")
+    b = W.random_vector(n, seed=21)
+    x = W.random_vector(n, seed=22)
+    r = (b - A @ x)[order]
+    dx = np.empty(n)
+    dx[order] = sla.spsolve_triangular(T, r, lower=not backward)
+    want = x + dx
+    got = orc.gs_sweep(Ao, col, orc.n_colours(dim, elem), b, x, backward=backward)
+    assert np.linalg.norm(got - want) <= 1e-13 * np.linalg.norm(want)
+
+
+@pytest.mark.parametrize("dim,elem,N", [(2, 0, 12), (3, 0, 6), (3, 1, 4)])
+def test_gs_sweep_contracts_the_energy_error(orc, dim, elem, N):
+    Ao = orc.assemble(dim, elem, N)
+    A = Ao.dense()
+    col = orc.colours(dim, elem, N)
+    b = W.random_vector(A.shape[0], seed=23)
+    xs = np.linalg.solve(A, b)
+    x = W.random_vector(A.shape[0], seed=24)
+    en = lambda e: float(np.sqrt(e @ A @ e))
+    for backward in (False, True, False):
+        x1 = orc.gs_sweep(Ao, col, orc.n_colours(dim, elem), b, x, backward=backward)
+        assert en(x1 - xs) < en(x - xs)
+        x = x1
+    # the exact solution is a fixed point
+    x2 = orc.gs_sweep(Ao, col, orc.n_colours(dim, elem), b, xs)
+    assert np.linalg.norm(x2 - xs) <= 1e-12 * np.linalg.norm(xs)
+
+
+@pytest.mark.parametrize("dim,elem,N,L", [(2, 0, 16, 3), (3, 0, 8, 3), (3, 1, 4, 2)])
+def test_gs_vcycle_is_symmetric(orc, dim, elem, N, L):
+    """Forward sweeps before and backward sweeps after the correction: V = V^T."""
+    H = orc.Hierarchy(dim, elem, N, L, opts=orc.Options(smoother=orc.GAUSS_SEIDEL, nu_pre=2, nu_post=2))
+    u = W.random_vector(H.n, seed=25)
+    w = W.random_vector(H.n, seed=26)
+    a, c = u @ H.vcycle(w), w @ H.vcycle(u)
+    assert abs(a - c) <= 1e-12 * max(abs(a), abs(c))
+    # and positive definite on these vectors
+    assert u @ H.vcycle(u) > 0 and w @ H.vcycle(w) > 0
+
+
+def test_gs_converges_faster_per_cycle_than_jacobi(orc):
+    N, L = 32, 4
+    b = orc.load_vector(3, orc.Q1, N, modes=W.manufactured_modes(3))
+    its = []
+    for sm in (orc.JACOBI, orc.GAUSS_SEIDEL):
+        H = orc.Hierarchy(3, orc.Q1, N, L, opts=orc.Options(smoother=sm, omega=0.8))
+        x, hist, it, conv = H.solve(b, 1e-10)
+        assert conv
+        its.append(it)
+    assert its[1] < its[0]
