@@ -127,7 +127,7 @@ def _traffic_from_profile(kernel_tag):
     return None
 
 
-def roofline_block(precision, name, tflops, gbs, peak_gbs, peak_kind, flops, nbytes, launches, sec):
+def roofline_block(precision, name, tflops, gbs, peak_gbs, peak_kind, flops, nbytes, launches, sec, smoother=1):
     """The dominant kernel against the roofline that binds it: the FP64 pipe for the FP64
     sweep (GB300 issues about 2 DFMA per clock per SM), HBM bandwidth for the FP32 one."""
     hbm = {"achieved": gbs, "peak": peak_gbs, "unit": "GB/s", "frac": gbs / peak_gbs if gbs else None,
@@ -137,14 +137,15 @@ def roofline_block(precision, name, tflops, gbs, peak_gbs, peak_kind, flops, nby
     if precision == "fp64":
         out = {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                "frac": tflops / FP64_PEAK_TFLOPS if tflops else None,
-               "traffic": _traffic_from_profile("smooth_fp64_%s" % name),
-               "kernel": "finest-level smoother sweep (fused residual + Chebyshev update), FP64",
+               "traffic": _traffic_from_profile("smooth_fp64_%s" % name) if smoother != 2 else None,
+               "kernel": "finest-level smoother sweep (%s), FP64" % SWEEP_TEXT[smoother],
                "peak_kind": "FP64 pipe: 152 SMs x 2.07 GHz x 2 DFMA/clk/SM x 2 flop (recipe nominal)",
                "hbm": hbm}
     else:
         out = dict(hbm)
-        out.update({"bound": "hbm", "traffic": _traffic_from_profile("smooth_fp32_%s" % name),
-                    "kernel": "finest-level smoother sweep (fused residual + Chebyshev update), FP32"})
+        out.update({"bound": "hbm",
+                    "traffic": _traffic_from_profile("smooth_fp32_%s" % name) if smoother != 2 else None,
+                    "kernel": "finest-level smoother sweep (%s), FP32" % SWEEP_TEXT[smoother]})
     out.update(common)
     return out
 
@@ -160,9 +161,17 @@ def replica_throughput(ms_local, n_dofs, steps, world, dist=None, device="cpu"):
     return world * n_dofs * steps / (ms_max * 1e-3), ms_max
 
 
-def _config_args(name):
+SMOOTHERS = {"jacobi": 0, "chebyshev": 1, "gauss-seidel": 2}
+SWEEP_TEXT = {0: "fused residual + damped Jacobi update", 1: "fused residual + Chebyshev update",
+              2: "one colour of a multicolour Gauss-Seidel sweep, in place"}
+
+
+def _config_args(name, smoother="workload"):
+    """The workload's parameters; `smoother` other than "workload" replaces its smoother."""
     from paper_1609_04809_gb300 import workloads as W
     c = dict(W.CONFIGS[name])
+    if smoother != "workload":
+        c["smoother"] = SMOOTHERS[smoother]
     return c
 
 
@@ -172,10 +181,10 @@ def _problem_rhs(c):
     return mg.mg_load_vector(c["dim"], c["element"], c["n_cells"], modes=modes, f_const=1.0), modes
 
 
-def _oracle_workload(name):
+def _oracle_workload(name, smoother="workload"):
     import oracle
     from paper_1609_04809_gb300 import workloads as W
-    c = _config_args(name)
+    c = _config_args(name, smoother)
     O = oracle.Hierarchy(c["dim"], c["element"], c["n_cells"], c["n_levels"],
                          opts=oracle.Options(smoother=c["smoother"], omega=c["omega"], cheb_degree=c["cheb_degree"],
                                              nu_pre=c["nu_pre"], nu_post=c["nu_post"]))
@@ -191,9 +200,9 @@ def _oracle_step(O, A, b, x):
     return x + O.vcycle(r)
 
 
-def cpu_baseline(name, cycles):
+def cpu_baseline(name, cycles, smoother="workload"):
     """The oracle (single-threaded C, FP64) on the same workload: setup, then `cycles` timed iterations."""
-    O, A, b = _oracle_workload(name)
+    O, A, b = _oracle_workload(name, smoother)
     x = np.zeros(O.n)
     t0 = time.perf_counter()
     for _ in range(cycles):
@@ -272,18 +281,19 @@ def serve_bench(args):
         S.close()
 
 
-def config_report(name, steps=20, warmup=5):
+def config_report(name, steps=20, warmup=5, smoother="workload"):
     """One workload in both precisions: V-cycle throughput, the finest sweep against its
     roofline, and time to 1e-10 (median of 3 solves)."""
     import torch
 
     from paper_1609_04809_gb300 import mg, workloads as W
-    c = _config_args(name)
+    c = _config_args(name, smoother)
     k = W.k_blocks(c["n_cells"], dim=3, blocks_per_axis=16, seed=20260101) if c.get("k") == "blocks16" else None
     modes = W.manufactured_modes(c["dim"]) if c["rhs"] == "manufactured" else None
     b = mg.mg_load_vector(c["dim"], c["element"], c["n_cells"], modes=modes, f_const=1.0)
     bd = torch.from_numpy(b).cuda()
-    out = {"workload": name, "n_dofs": int(b.size)}
+    out = {"workload": name, "smoother": [k for k, v in SMOOTHERS.items() if v == c["smoother"]][0],
+           "n_dofs": int(b.size)}
     peak, _ = _peaks()
     for prec, tag in ((mg.MG_FP64, "fp64"), (mg.MG_MIXED, "mixed")):
         t0 = time.perf_counter()
@@ -340,7 +350,7 @@ def run_reference(args):
     import oracle
     oracle.build()
     name = args.config
-    O, A, b = _oracle_workload(name)
+    O, A, b = _oracle_workload(name, args.smoother)
     x = np.zeros(O.n)
     for _ in range(args.warmup):
         x = _oracle_step(O, A, b, x)
@@ -381,13 +391,13 @@ def run_ours(args):
         dist.barrier()
 
     name = args.config
-    c = _config_args(name)
+    c = _config_args(name, args.smoother)
     b_host, modes = _problem_rhs(c)
     n = b_host.size
     H = mg.Hierarchy(c["dim"], c["element"], c["n_cells"], c["n_levels"], smoother=c["smoother"],
                      omega=c["omega"], cheb_degree=c["cheb_degree"], nu_pre=c["nu_pre"], nu_post=c["nu_post"],
                      precision=mg.MG_MIXED if args.precision == "mixed" else mg.MG_FP64,
-                     use_pdl=0 if args.no_pdl else 1, coarse_tail=0 if args.no_tail else 1)
+                     use_pdl=0 if args.no_pdl else 1, coarse_tail=0 if args.no_tail else 2)
     info = H.info()
     Lf = c["n_levels"] - 1
     bd = torch.from_numpy(b_host).cuda()
@@ -481,7 +491,7 @@ def run_ours(args):
 
         cpu = None
         if world == 1 and not args.no_cpu:
-            cv, cdt = cpu_baseline(name, args.cpu_cycles)
+            cv, cdt = cpu_baseline(name, args.cpu_cycles, args.smoother)
             cpu = {"value": cv, "unit": UNIT, "cores": 1, "kind": "oracle",
                    "sample": "%d defect-correction iterations of the %s workload by the single-threaded FP64 "
                              "C oracle (setup excluded, %.1f s)" % (args.cpu_cycles, name, cdt)}
@@ -495,9 +505,10 @@ def run_ours(args):
                           "parallelism": "replicas" if world > 1 else "single-gpu",
                           "l2": "inputs larger than L2 (finest FP64 matrix %.0f MB > 129 MB L2)"
                                 % (info["nnz"][Lf] * 8 / 1e6),
-                          "storage": ["csr", "ell", "dia"][info["storage"][Lf] - 1]},
+                          "storage": ["csr", "ell", "dia"][info["storage"][Lf] - 1],
+                          "smoother": [k for k, v in SMOOTHERS.items() if v == c["smoother"]][0]},
                "roofline": roofline_block(args.precision, name, fp64_tflops, achieved, peak, peak_kind, k_flops,
-                                          k_bytes, k_cnt, k_s),
+                                          k_bytes, k_cnt, k_s, c["smoother"]),
                "kernel_ms_per_step": per_kernel,
                "e2e": e2e, "time_to_solution": tts, "cpu_baseline": cpu,
                "gpu_launches": info["kernels_per_cycle"] * args.steps + 1,
@@ -528,6 +539,8 @@ def main():
     ap.add_argument("--serve-slots", type=int, default=256)
     ap.add_argument("--no-pdl", action="store_true", help="launch without programmatic dependent launch")
     ap.add_argument("--no-tail", action="store_true", help="run the small levels as separate kernels")
+    ap.add_argument("--smoother", default="workload", choices=["workload"] + sorted(SMOOTHERS),
+                    help="replace the workload's smoother (the headline uses the workload's own)")
     ap.add_argument("--all-configs", action="store_true",
                     help="report every solve workload (FP64 and mixed) instead of the bench line")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
@@ -545,7 +558,7 @@ def main():
         torch.cuda.set_device(0)
         from paper_1609_04809_gb300 import workloads as W
         for name in W.CONFIGS:
-            print(json.dumps(config_report(name)), flush=True)
+            print(json.dumps(config_report(name, smoother=args.smoother)), flush=True)
         return 0
     return run_ours(args)
 

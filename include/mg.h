@@ -54,6 +54,14 @@ typedef int mg_status;
 /* smoother */
 #define MG_JACOBI 0    /* damped Jacobi x <- x + omega D^-1 (b - A x) */
 #define MG_CHEBYSHEV 1 /* Chebyshev polynomial in D^-1 A of degree cheb_degree */
+#define MG_GAUSS_SEIDEL 2 /* multicolour Gauss-Seidel (the paper's Eq. GS on DOFs numbered
+                             colour-wise, Sec. 4 "DOF Reordering"): one application visits
+                             every colour once, x_i <- x_i + (b_i - (A x)_i) / a_ii for all
+                             DOFs of a colour at once; colours ascending before the coarse
+                             correction, descending after it, so the V-cycle is symmetric.
+                             Q1 colours: parity classes of the vertex coordinates (2^dim);
+                             rotated Q1: face family x parity of the normal position (6).
+                             Not available to the serving API. */
 /* precision */
 #define MG_FP64 0  /* every step in FP64 */
 #define MG_MIXED 1 /* FP32 V-cycle (matrices, smoother, transfers) inside FP64 defect correction */
@@ -80,7 +88,7 @@ typedef struct {
 /* Solver options. mg_options_default() fills in damped Jacobi (omega 0.8), V(2,2),
  * FP64, automatic storage, 100 iterations, CUDA graphs on. nu_pre / nu_post count
  * smoother applications; a Chebyshev application performs cheb_degree matrix-vector
- * products. Chebyshev targets [lambda_u / cheb_ratio, lambda_u] with lambda_u =
+ * products, a Gauss-Seidel application one sweep over all colours. Chebyshev targets [lambda_u / cheb_ratio, lambda_u] with lambda_u =
  * cheb_hi * lambda_hat and lambda_hat from power_iters steps of the power method on
  * D^-1 A (start vector from SplitMix64(power_seed)). */
 typedef struct {

@@ -694,4 +694,48 @@ void round_fp32(const Csr &A, std::vector<float> &val32)
     }
 }
 
+
+// ------------------------------------------------------------------------------------
+// Multicolour Gauss-Seidel ordering (DOFs numbered colour-wise, Sec. 4 "DOF Reordering")
+// ------------------------------------------------------------------------------------
+int n_colours(int dim, int elem) { return elem == MG_Q1 ? 1 << dim : 6; }
+
+int dof_colour(int dim, int elem, int N, int64_t i)
+{
+    if (elem == MG_Q1) {
+        int v[3];
+        q1_coords(dim, N, i, v);
+        return (v[0] & 1) | (v[1] & 1) << 1 | (dim == 3 ? (v[2] & 1) << 2 : 0);
+    }
+    int f, p, q1, q2;
+    rq1_decode(N, i, f, p, q1, q2);
+    return 2 * f + (p & 1);
+}
+
+void colour_order(int dim, int elem, int N, std::vector<int32_t> &perm, std::vector<int64_t> &coff)
+{
+    int64_t n = ndofs(dim, elem, N);
+    int nc = n_colours(dim, elem);
+    coff.assign((size_t)nc + 1, 0);
+    std::vector<uint8_t> col((size_t)n);
+    for (int64_t i = 0; i < n; i++) {
+        col[i] = (uint8_t)dof_colour(dim, elem, N, i);
+        coff[col[i] + 1]++;
+    }
+    for (int c = 0; c < nc; c++) coff[c + 1] += coff[c];
+    std::vector<int64_t> next(coff.begin(), coff.end() - 1);
+    perm.resize((size_t)n);
+    for (int64_t i = 0; i < n; i++) perm[next[col[i]]++] = (int32_t)i;
+}
+
+bool colouring_valid(const Csr &A, int dim, int elem, int N)
+{
+    for (int64_t i = 0; i < A.nrows; i++) {
+        int ci = dof_colour(dim, elem, N, i);
+        for (int64_t k = A.rowptr[i]; k < A.rowptr[i + 1]; k++)
+            if (A.col[k] != i && dof_colour(dim, elem, N, A.col[k]) == ci) return false;
+    }
+    return true;
+}
+
 }  // namespace mgh

@@ -63,6 +63,17 @@ struct HostHierarchy {
 void build_hierarchy(int dim, int elem, int N_finest, int n_levels, const double *k_finest, int stop,
                      HostHierarchy &H);
 
+// Multicolour Gauss-Seidel ordering. Q1: the parity class of the vertex coordinates,
+// colour (vx&1) + 2(vy&1) [+ 4(vz&1)]; rotated Q1: face family f and parity of the normal
+// position p, colour 2f + (p&1). DOFs of one colour never share a cell.
+int n_colours(int dim, int elem);
+int dof_colour(int dim, int elem, int N, int64_t i);
+// DOFs sorted by colour (index order within a colour): perm[coff[c] .. coff[c+1]) are
+// the DOFs of colour c.
+void colour_order(int dim, int elem, int N, std::vector<int32_t> &perm, std::vector<int64_t> &coff);
+// true iff no stored entry (zero or not) couples two distinct DOFs of one colour
+bool colouring_valid(const Csr &A, int dim, int elem, int N);
+
 // Power-method estimate of lambda_max(D^-1 A) (the start vector is 1 + 0.2 (u - 1/2),
 // u from SplitMix64(seed), normalised).
 double level_lambda(const Csr &A, int iters, uint64_t seed);

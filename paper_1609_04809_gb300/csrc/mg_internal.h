@@ -57,6 +57,11 @@ struct LevelD {
     void *b = nullptr, *t = nullptr, *d = nullptr;
     bool structured = false;  // Q1 transfers computed from the grid
     DevMat P, R;              // explicit transfers to level-1 (CSR)
+    // multicolour Gauss-Seidel: a copy of A with its rows stored colour by colour (row r
+    // of G is DOF perm[r]; colour c owns rows coff[c] .. coff[c+1]); D^-1 in G.dinv
+    DevMat G;
+    int32_t *perm = nullptr;
+    std::vector<int64_t> coff;
     double omega = 0.8, lambda = 0.0, cheb_c0 = 0.0;
     std::vector<double> cheb_c1, cheb_c2;
 };

@@ -1162,6 +1162,8 @@ extern "C" mg_status mg_serve_create(const mg_serve_config *cfg, const mg_device
     std::unique_ptr<mg_server> S(new mg_server());
     try {
         const mg_options &o = cfg->options;
+        if (o.smoother == MG_GAUSS_SEIDEL)
+            throw Error(MG_EINVAL, "the Gauss-Seidel smoother is not available to the serving API");
         if (o.smoother != MG_JACOBI && o.smoother != MG_CHEBYSHEV) throw Error(MG_EINVAL, "bad smoother");
         if (o.smoother == MG_CHEBYSHEV && (o.cheb_degree < 1 || o.cheb_degree > SV_MAXDEG))
             throw Error(MG_EINVAL, "serving supports Chebyshev degree 1..4");

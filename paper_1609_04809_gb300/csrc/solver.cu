@@ -22,6 +22,7 @@
 
 #include "host_setup.h"
 #include "kernels.cuh"
+#include "gs.cuh"
 #include "mg.h"
 #include "mg_internal.h"
 
@@ -341,11 +342,60 @@ static void sweep(mg_hierarchy *h, int l, int mode, const T *x, const T *b, T *o
 }
 
 // one smoother application on level l; c: buffer holding x (-1: x = 0); returns new buffer
+// one multicolour Gauss-Seidel sweep of level l on x in place: one launch per colour,
+// colours ascending (descending in post-smoothing)
 template <typename T>
-static int smooth(mg_hierarchy *h, int l, int c, cudaStream_t s)
+static void gs_sweep(mg_hierarchy *h, int l, T *x, bool post, cudaStream_t s)
+{
+    LevelD &L = h->lev[l];
+    const DevMat &G = L.G;
+    MatView<T> v = view<T>(G);
+    int nc = (int)L.coff.size() - 1, sv = sizeof(T);
+    bool pdl = h->opt.use_pdl != 0;
+    const T *b = (const T *)L.b;
+    for (int cc = 0; cc < nc; cc++) {
+        int c = post ? nc - 1 - cc : cc;
+        int64_t r0 = L.coff[c];
+        int nr = (int)(L.coff[c + 1] - r0);
+        if (nr == 0) continue;
+        // the colour's slice of the matrix (values, columns), perm, D^-1, b, and x read
+        // and written at its rows; gathers of x at other rows count as cache hits
+        double per_row = G.fmt == MG_STORAGE_CSR ? 0.0 : (double)G.K * (sv + (G.fmt == MG_STORAGE_ELL ? 4 : 0));
+        double slice = G.fmt == MG_STORAGE_CSR
+                           ? (double)(L.nnz) * (sv + 4) * nr / std::max<int64_t>(L.n, 1) + 8.0 * nr
+                           : per_row * nr;
+        double bytes = slice + nr * (4.0 + 3.0 * sv + (G.dinv ? sv : 0));
+        double entries = G.fmt == MG_STORAGE_CSR ? (double)L.nnz * nr / std::max<int64_t>(L.n, 1) : (double)G.K * nr;
+        LaunchScope ls(h, s, MG_K_SMOOTH, l, bytes, 2.0 * entries + 4.0 * nr);
+        dim3 g((unsigned)((nr + 255) / 256)), blk(256);
+        if (G.fmt == MG_STORAGE_DIA) {
+            if (G.K == 21)
+                klaunch(pdl, k_gs_dia<T, 21>, g, blk, 0, s, v, (const int32_t *)L.perm, r0, nr, x, b);
+            else if (G.K == 27)
+                klaunch(pdl, k_gs_dia<T, 27>, g, blk, 0, s, v, (const int32_t *)L.perm, r0, nr, x, b);
+            else
+                klaunch(pdl, k_gs_dia<T, 9>, g, blk, 0, s, v, (const int32_t *)L.perm, r0, nr, x, b);
+        } else if (G.fmt == MG_STORAGE_ELL) {
+            klaunch(pdl, k_gs_ell<T>, g, blk, 0, s, v, (const int32_t *)L.perm, r0, nr, x, b);
+        } else {
+            klaunch(pdl, k_gs_csr<T>, g, blk, 0, s, v, (const int32_t *)L.perm, r0, nr, x, b);
+        }
+    }
+}
+
+template <typename T>
+static int smooth(mg_hierarchy *h, int l, int c, bool post, cudaStream_t s)
 {
     LevelD &L = h->lev[l];
     T *b = (T *)L.b, *d = (T *)L.d;
+    if (h->opt.smoother == MG_GAUSS_SEIDEL) {  // in place: the buffer does not change
+        if (c < 0) {
+            CK(cudaMemsetAsync(L.x[0], 0, (size_t)L.n * sizeof(T), s));
+            c = 0;
+        }
+        gs_sweep<T>(h, l, (T *)L.x[c], post, s);
+        return c;
+    }
     if (h->opt.smoother == MG_JACOBI) {
         if (c < 0) {
             sweep<T>(h, l, SW_JACOBI_Z, nullptr, b, (T *)L.x[0], d, L.omega, 0.0, s);
@@ -483,7 +533,7 @@ static int enqueue_vcycle(mg_hierarchy *h, cudaStream_t s)
     for (int l = Lf; l >= 1; l--) {  // pre-smoothing and restriction of the residual
         LevelD &L = h->lev[l];
         int c = -1;
-        for (int a = 0; a < h->opt.nu_pre; a++) c = smooth<T>(h, l, c, s);
+        for (int a = 0; a < h->opt.nu_pre; a++) c = smooth<T>(h, l, c, false, s);
         const T *r;
         if (c < 0) {
             r = (const T *)L.b;  // b - A 0 = b
@@ -535,7 +585,7 @@ static int enqueue_vcycle(mg_hierarchy *h, cudaStream_t s)
             cur[l] = 0;
         }
         prolong_add<T>(h, l, (const T *)h->lev[l - 1].x[cur[l - 1]], (T *)L.x[cur[l]], s);
-        for (int a = 0; a < h->opt.nu_post; a++) cur[l] = smooth<T>(h, l, cur[l], s);
+        for (int a = 0; a < h->opt.nu_post; a++) cur[l] = smooth<T>(h, l, cur[l], true, s);
     }
     if (h->tail_rec) {  // the whole hierarchy was the tail
         launch_tail<T>(h, s);
@@ -911,6 +961,59 @@ static void upload_matrix(const DevMat &m, const mgh::Csr &A, const std::vector<
     }
 }
 
+// The colour-major copy G of level l's matrix: DIA / ELL slots and D^-1 gathered on the
+// device from the level's own arrays (so both hold the same values in either precision),
+// CSR rows reordered on the host.
+static void upload_gs_copy(mg_hierarchy *h, int l, const mgh::Csr &A, const std::vector<int32_t> &perm)
+{
+    LevelD &L = h->lev[l];
+    DevMat &G = L.G;
+    int64_t n = L.n;
+    if (n == 0) return;
+    CK(cudaMemcpyAsync(L.perm, perm.data(), perm.size() * 4, cudaMemcpyHostToDevice, h->s));
+    auto gather = [&](void *dst, const void *src, int K, int esz) {
+        int64_t tot = n * K;
+        unsigned grid = (unsigned)((tot + 255) / 256);
+        if (esz == 8)
+            k_gather_rows<double><<<grid, 256, 0, h->s>>>((double *)dst, (const double *)src, L.perm, n, G.ld, K);
+        else if (esz == 4)
+            k_gather_rows<float><<<grid, 256, 0, h->s>>>((float *)dst, (const float *)src, L.perm, n, G.ld, K);
+        else
+            k_gather_rows<int32_t><<<grid, 256, 0, h->s>>>((int32_t *)dst, (const int32_t *)src, L.perm, n, G.ld, K);
+        CKL();
+    };
+    if (G.fmt == MG_STORAGE_DIA || G.fmt == MG_STORAGE_ELL) {
+        gather(G.val, L.A.val, G.K, h->inner_size);
+        if (G.fmt == MG_STORAGE_ELL) gather(G.col, L.A.col, G.K, -4);  // column indices
+    } else {
+        std::vector<int64_t> rp((size_t)n + 1, 0);
+        for (int64_t r = 0; r < n; r++) rp[r + 1] = rp[r] + (A.rowptr[perm[r] + 1] - A.rowptr[perm[r]]);
+        std::vector<int32_t> cols((size_t)A.nnz());
+        std::vector<float> v32;
+        if (h->mixed) mgh::round_fp32(A, v32);
+        std::vector<double> vd(h->mixed ? 0 : (size_t)A.nnz());
+        std::vector<float> vf(h->mixed ? (size_t)A.nnz() : 0);
+        for (int64_t r = 0; r < n; r++) {
+            int64_t src = A.rowptr[perm[r]], len = rp[r + 1] - rp[r];
+            for (int64_t k = 0; k < len; k++) {
+                cols[rp[r] + k] = A.col[src + k];
+                if (h->mixed)
+                    vf[rp[r] + k] = v32[src + k];
+                else
+                    vd[rp[r] + k] = A.val[src + k];
+            }
+        }
+        if (h->mixed)
+            CK(cudaMemcpyAsync(G.val, vf.data(), vf.size() * 4, cudaMemcpyHostToDevice, h->s));
+        else
+            CK(cudaMemcpyAsync(G.val, vd.data(), vd.size() * 8, cudaMemcpyHostToDevice, h->s));
+        CK(cudaMemcpyAsync(G.col, cols.data(), cols.size() * 4, cudaMemcpyHostToDevice, h->s));
+        CK(cudaMemcpyAsync(G.rowptr, rp.data(), rp.size() * 8, cudaMemcpyHostToDevice, h->s));
+    }
+    if (G.dinv) gather(G.dinv, L.A.dinv, 1, 8);
+    CK(cudaStreamSynchronize(h->s));
+}
+
 static std::vector<float> to_f32(const std::vector<double> &v)
 {
     std::vector<float> o(v.size());
@@ -1036,7 +1139,8 @@ void mgi::build_hierarchy(mg_hierarchy *h, const mg_problem *p, const mg_options
 {
     validate_problem(p);
     h->with_vectors = with_vectors;
-    if (o->smoother != MG_JACOBI && o->smoother != MG_CHEBYSHEV) throw Error(MG_EINVAL, "bad smoother");
+    if (o->smoother != MG_JACOBI && o->smoother != MG_CHEBYSHEV && o->smoother != MG_GAUSS_SEIDEL)
+        throw Error(MG_EINVAL, "bad smoother");
     if (o->smoother == MG_CHEBYSHEV && (o->cheb_degree < 1 || !(o->cheb_ratio > 1.0) || !(o->cheb_hi > 0.0) || o->power_iters < 1))
         throw Error(MG_EINVAL, "bad Chebyshev parameters");
     if (o->nu_pre < 0 || o->nu_post < 0 || o->max_iters < 0) throw Error(MG_EINVAL, "negative counts");
@@ -1092,6 +1196,15 @@ void mgi::build_hierarchy(mg_hierarchy *h, const mg_problem *p, const mg_options
         for (int l = 1; l <= Lf; l++)
             if (h->lev[l].n >= 32768) lfmt[l] = tune_storage(h, A[l], dim, elem, h->lev[l].N);
     int sv = h->inner_size;
+    // ---- multicolour Gauss-Seidel: colour order of every smoothed level ----
+    const bool gs = o->smoother == MG_GAUSS_SEIDEL;
+    std::vector<std::vector<int32_t>> gs_perm((size_t)nlev);
+    if (gs)
+        for (int l = 1; l <= Lf; l++) {
+            if (!mgh::colouring_valid(A[l], dim, elem, h->lev[l].N))
+                throw Error(MG_EINVAL, "level " + std::to_string(l) + " couples two DOFs of one colour");
+            mgh::colour_order(dim, elem, h->lev[l].N, gs_perm[l], h->lev[l].coff);
+        }
     for (int pass = 0; pass < 2; pass++) {
         bool take = pass == 1;
         mgi::Slab &S = h->slab;
@@ -1122,6 +1235,11 @@ void mgi::build_hierarchy(mg_hierarchy *h, const mg_problem *p, const mg_options
             L.fmt = lf;
             plan_matrix(L.A, A[l], lf, dim, L.N, sv, S, take);
             if (!h->mixed && l >= 1) L.A.dinv = vec((size_t)L.A.ld * 8);  // FP64 smoothers read D^-1
+            if (gs && l >= 1) {  // the colour-major copy of A for the Gauss-Seidel sweeps
+                plan_matrix(L.G, A[l], lf, dim, L.N, sv, S, take);
+                if (!h->mixed) L.G.dinv = vec((size_t)L.G.ld * 8);
+                L.perm = (int32_t *)vec((size_t)std::max<int64_t>(L.G.n, 1) * 4);
+            }
             int64_t n1 = L.N - 1;
             L.pad = lf == MG_STORAGE_DIA ? round_up(dim == 3 ? n1 * n1 + n1 + 1 : n1 + 1, 64) : 0;
             int64_t ld = L.A.ld;
@@ -1190,6 +1308,8 @@ void mgi::build_hierarchy(mg_hierarchy *h, const mg_problem *p, const mg_options
         }
     }
     if (h->mixed) upload_matrix<double>(h->A64, A[Lf], A[Lf].val, dim, h->lev[Lf].N, h->s);
+    if (gs)
+        for (int l = 1; l <= Lf; l++) upload_gs_copy(h, l, A[l], gs_perm[l]);
     // ---- coarsest LU on the device ----
     {
         std::vector<double> dense((size_t)h->n0 * h->n0, 0.0);
@@ -1205,7 +1325,7 @@ void mgi::build_hierarchy(mg_hierarchy *h, const mg_problem *p, const mg_options
     }
     // ---- coarse-level tail: the levels of at most 4096 rows in one cluster launch ----
     h->tail_level = -1;
-    if (o->coarse_tail && h->n0 <= 64) {
+    if (o->coarse_tail && h->n0 <= 64 && o->smoother != MG_GAUSS_SEIDEL) {
         int t = -1;
         for (int l = 0; l <= Lf; l++) {
             const LevelD &L = h->lev[l];
