@@ -15,6 +15,8 @@ Which parts of the paper each function follows:
     R = P^T (Sec. 5.4).
   * ``Hierarchy.solve``: V-cycles of the paper's V-cycle algorithm (Sec. 5.3) inside a
     defect-correction loop that stops at a relative residual.
+  * ``Hierarchy.pcg``: conjugate gradients preconditioned by one V-cycle (Sec. 1: multigrid
+    as a preconditioner of a Krylov method), Saad's Alg. 9.1.
   * ``load_vector``: the load vector of the sparse FE system.
   * ``colours`` / ``gs_sweep``: the multicolour Gauss-Seidel smoother (the paper's
     Gauss-Seidel step, Eq. GS, on DOFs numbered colour-wise, Sec. 4 "DOF Reordering").
@@ -87,6 +89,8 @@ def lib():
         L.orc_solve.restype = ctypes.c_int
         L.orc_solve.argtypes = [vp, P(_Opts), dp, dp, ctypes.c_double, dp, ip]
         L.orc_vcycle.argtypes = [vp, P(_Opts), dp, dp]
+        L.orc_pcg.restype = ctypes.c_int
+        L.orc_pcg.argtypes = [vp, P(_Opts), dp, dp, ctypes.c_double, dp, ip]
         L.orc_n_levels.argtypes = [vp]
         L.orc_level_N.argtypes = [vp, ctypes.c_int]
         L.orc_level_galerkin.argtypes = [vp, ctypes.c_int]
@@ -343,4 +347,16 @@ class Hierarchy:
         it = ctypes.c_int(0)
         st = lib().orc_solve(self._h, ctypes.byref(o), _dp(b), _dp(x), float(tol), _dp(hist),
                              ctypes.byref(it))
+        return x, hist[:it.value + 1].copy(), it.value, st == 0
+
+    def pcg(self, b, tol, x0=None, max_iters=None):
+        """CG preconditioned by one V-cycle. Returns (x, hist, iters, converged)."""
+        o = self.opts._c()
+        if max_iters is not None:
+            o.max_iters = max_iters
+        b = _f64(b)
+        x = np.zeros(self.n) if x0 is None else np.array(x0, dtype=np.float64)
+        hist = np.zeros(o.max_iters + 1)
+        it = ctypes.c_int(0)
+        st = lib().orc_pcg(self._h, ctypes.byref(o), _dp(b), _dp(x), float(tol), _dp(hist), ctypes.byref(it))
         return x, hist[:it.value + 1].copy(), it.value, st == 0

@@ -1139,6 +1139,87 @@ int orc_solve(orc_hier *H, const orc_opts *o, const double *b, double *x, double
     return status;
 }
 
+/* Euclidean inner product u.v: each product rounded, the sum by Neumaier's
+ * compensated summation (as the residual norm) */
+static double dot_accurate(const double *u, const double *v, int64_t n)
+{
+    double s = 0.0, c = 0.0;
+    for (int64_t i = 0; i < n; i++) {
+        double t = u[i] * v[i];
+        double y = s + t;
+        if (fabs(s) >= fabs(t))
+            c += (s - y) + t;
+        else
+            c += (t - y) + s;
+        s = y;
+    }
+    return s + c;
+}
+
+/*
+ * Conjugate gradients preconditioned by one V-cycle (the paper's introduction, Sec. 1:
+ * multigrid is often used as a preconditioner of a Krylov method such as CG or GMRES).
+ * The preconditioned CG iteration (Saad, Iterative Methods for Sparse Linear Systems,
+ * Alg. 9.1) with M^-1 r = V(r), the V-cycle applied to r from a zero start:
+ *   r_0 = b - A x_0; hist[0] = ||r_0|| / ||b||
+ *   for j = 0, 1, ...: stop if hist[j] <= tol;
+ *     z_j = V(r_j); rz_j = (r_j, z_j)
+ *     p_j = z_j (j = 0), p_j = z_j + (rz_j / rz_{j-1}) p_{j-1} (j > 0)
+ *     q_j = A p_j; alpha_j = rz_j / (p_j, q_j)
+ *     x_{j+1} = x_j + alpha_j p_j; r_{j+1} = r_j - alpha_j q_j
+ *     hist[j+1] = ||r_{j+1}|| / ||b||   (the recursively updated residual)
+ * The V-cycle is symmetric when nu_pre = nu_post (Gauss-Seidel: forward before the
+ * correction, backward after). Returns 0 on convergence, 1 after max_iters iterations.
+ */
+int orc_pcg(orc_hier *H, const orc_opts *o, const double *b, double *x, double tol, double *hist, int *iters)
+{
+    int L = H->n_levels - 1;
+    const orc_csr *A = &H->A[L];
+    int64_t n = A->nrows;
+    double *r = (double *)malloc((size_t)n * sizeof(double));
+    double *z = (double *)malloc((size_t)n * sizeof(double));
+    double *p = (double *)malloc((size_t)n * sizeof(double));
+    double *q = (double *)malloc((size_t)n * sizeof(double));
+    double nb = norm2_accurate(b, n);
+    residual(A, b, x, r);
+    double rz_old = 0.0;
+    int status = 1, j;
+    for (j = 0;; j++) {
+        double h = norm2_accurate(r, n);
+        h = nb > 0.0 ? h / nb : h;
+        if (hist)
+            hist[j] = h;
+        if (h <= tol) {
+            status = 0;
+            break;
+        }
+        if (j == o->max_iters)
+            break;
+        orc_vcycle(H, o, r, z);
+        double rz = dot_accurate(r, z, n);
+        if (j == 0) {
+            memcpy(p, z, (size_t)n * sizeof(double));
+        } else {
+            double beta = rz / rz_old;
+            for (int64_t i = 0; i < n; i++)
+                p[i] = z[i] + beta * p[i];
+        }
+        orc_spmv(A, p, q);
+        double alpha = rz / dot_accurate(p, q, n);
+        for (int64_t i = 0; i < n; i++) {
+            x[i] = x[i] + alpha * p[i];
+            r[i] = r[i] - alpha * q[i];
+        }
+        rz_old = rz;
+    }
+    *iters = j;
+    free(r);
+    free(z);
+    free(p);
+    free(q);
+    return status;
+}
+
 /* accessors for the test harness */
 int orc_n_levels(const orc_hier *H) { return H->n_levels; }
 int orc_level_N(const orc_hier *H, int l) { return H->N[l]; }

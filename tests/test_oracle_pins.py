@@ -616,3 +616,65 @@ def test_gs_converges_faster_per_cycle_than_jacobi(orc):
         assert conv
         its.append(it)
     assert its[1] < its[0]
+
+
+# ---------------------------------------------------------------------------------
+# Conjugate gradients preconditioned by one V-cycle (Sec. 1: MG as a preconditioner)
+# ---------------------------------------------------------------------------------
+def _textbook_pcg(A, Minv, b, tol, maxit=100):
+    """Preconditioned CG written from the textbook with dense numpy operators."""
+    x = np.zeros_like(b)
+    r = b - A @ x
+    nb = np.linalg.norm(b)
+    hist = [np.linalg.norm(r) / nb]
+    p = None
+    rz_old = None
+    for _ in range(maxit):
+        if hist[-1] <= tol:
+            break
+        z = Minv @ r
+        rz = r @ z
+        p = z if p is None else z + (rz / rz_old) * p
+        q = A @ p
+        alpha = rz / (p @ q)
+        x = x + alpha * p
+        r = r - alpha * q
+        rz_old = rz
+        hist.append(np.linalg.norm(r) / nb)
+    return x, np.array(hist)
+
+
+@pytest.mark.parametrize("dim,elem,N,L,smoother", [(2, 0, 16, 3, 0), (2, 0, 16, 3, 1), (3, 0, 8, 3, 2),
+                                                    (3, 1, 4, 2, 0), (3, 1, 4, 2, 2)])
+def test_pcg_matches_textbook_pcg_with_closed_form_vcycle(orc, dim, elem, N, L, smoother):
+    opts = orc.Options(smoother=smoother, omega=0.7, nu_pre=2, nu_post=2)
+    H = orc.Hierarchy(dim, elem, N, L, opts=opts)
+    b = W.random_vector(H.n, seed=41)
+    x, hist, it, conv = H.pcg(b, 1e-11)
+    A = H.A(L - 1).dense()
+    xt, ht = _textbook_pcg(A, _vcycle_operator(H, opts, L - 1), b, 1e-11)
+    assert conv and it == len(ht) - 1
+    np.testing.assert_allclose(hist, ht, rtol=1e-8, atol=0)
+    assert np.linalg.norm(x - xt) <= 1e-10 * np.linalg.norm(xt)
+    xd = np.linalg.solve(A, b)
+    assert np.linalg.norm(x - xd) <= 1e-9 * np.linalg.norm(xd)
+
+
+def test_pcg_with_exact_preconditioner_converges_in_one_step(orc):
+    """One level: the V-cycle is the LU solve, M^-1 = A^-1, so x_1 is the solution."""
+    H = orc.Hierarchy(3, orc.Q1, 8, 1)
+    b = W.random_vector(H.n, seed=42)
+    x, hist, it, conv = H.pcg(b, 1e-13)
+    assert conv and it == 1 and hist[1] <= 1e-14
+
+
+@pytest.mark.parametrize("smoother", [0, 1, 2])
+def test_pcg_needs_no_more_cycles_than_defect_correction(orc, smoother):
+    N, L = 32, 4
+    b = orc.load_vector(3, orc.Q1, N, modes=W.manufactured_modes(3))
+    H = orc.Hierarchy(3, orc.Q1, N, L, opts=orc.Options(smoother=smoother, omega=0.8, nu_pre=1, nu_post=1))
+    x1, h1, it1, c1 = H.solve(b, 1e-10)
+    x2, h2, it2, c2 = H.pcg(b, 1e-10)
+    assert c1 and c2 and it2 <= it1
+    r = b - orc.spmv(H.A(L - 1), x2)  # the recursive residual tracks the true one
+    assert abs(np.linalg.norm(r) / np.linalg.norm(b) - h2[-1]) <= 1e-3 * h2[-1]
