@@ -326,6 +326,24 @@ def config_report(name, steps=20, warmup=5, smoother="workload"):
             its, rel = it, hist[-1]
         rd = torch.empty_like(bd)
         true_rel = mg.mg_residual_norm_noalloc(H.h, bd, x, rd) / float(np.linalg.norm(b))
+        pcg = None
+        if c["nu_pre"] == c["nu_post"]:
+            pts, pits = [], 0
+            for rep_i in range(4):
+                x.zero_()
+                if rep_i == 3:
+                    mg.mg_profile_enable(H.h, True, classes=[mg.MG_K_KRYLOV], levels=[Lf])
+                torch.cuda.synchronize()
+                s0 = time.perf_counter()
+                st, pits, ph = H.pcg(bd, x, c["tol"])
+                pts.append(time.perf_counter() - s0)
+            kk_ms, kk_cnt, kk_bytes, _ = mg.mg_profile_read(H.h, mg.MG_K_KRYLOV, Lf)
+            mg.mg_profile_enable(H.h, False)
+            ptrue = mg.mg_residual_norm_noalloc(H.h, bd, x, rd) / float(np.linalg.norm(b))
+            pcg = {"time_to_tol_ms": 1e3 * float(np.median(pts[1:3])), "iterations": pits,
+                   "true_fp64_rel_residual": ptrue,
+                   "krylov_kernels_gbs": kk_bytes * kk_cnt / (kk_ms * 1e-3) / 1e9 if kk_cnt else None,
+                   "krylov_kernels_us_per_iteration": 1e3 * kk_ms / max(pits, 1) if kk_cnt else None}
         ks = k_ms / k_cnt * 1e-3 if k_cnt else None
         out[tag] = {"dofs_per_s_per_vcycle": b.size / (ms * 1e-3), "ms_per_iteration": ms,
                     "finest_sweep_us": 1e6 * ks if ks else None,
@@ -335,7 +353,7 @@ def config_report(name, steps=20, warmup=5, smoother="workload"):
                     "time_to_tol_ms": 1e3 * float(np.median(ts[1:])), "iterations": its,
                     "final_rel_residual": rel, "true_fp64_rel_residual": true_rel,
                     "storage": ["csr", "ell", "dia"][info["storage"][Lf] - 1], "setup_s": setup_s,
-                    "device_gb": info["device_bytes"] / 1e9}
+                    "device_gb": info["device_bytes"] / 1e9, "pcg": pcg}
         H.close()
         del H
         torch.cuda.empty_cache()
@@ -463,24 +481,28 @@ def run_ours(args):
         # time to solution, FP64 vs mixed
         tts = None
         if not args.no_mixed:
-            def solve_time(h):
+            def solve_time(h, fn=mg.mg_solve):
                 x = torch.zeros_like(bd)
-                mg.mg_solve(h.h, bd, x, tol, 100)
+                fn(h.h, bd, x, tol, 100)
                 ts = []
                 for _ in range(3):
                     x.zero_()
                     torch.cuda.synchronize()
                     s0 = time.perf_counter()
-                    st, it, hist = mg.mg_solve(h.h, bd, x, tol, 100)
+                    st, it, hist = fn(h.h, bd, x, tol, 100)
                     ts.append(time.perf_counter() - s0)
                 return float(np.median(ts)), it, hist[-1]
             t64, it64, r64 = solve_time(H)
+            p64, pit64, _ = solve_time(H, mg.mg_pcg)
             Hm = mg.Hierarchy(c["dim"], c["element"], c["n_cells"], c["n_levels"], smoother=c["smoother"],
                               omega=c["omega"], cheb_degree=c["cheb_degree"], nu_pre=c["nu_pre"],
                               nu_post=c["nu_post"], precision=mg.MG_MIXED)
             t32, it32, r32 = solve_time(Hm)
+            p32, pit32, _ = solve_time(Hm, mg.mg_pcg)
             tts = {"tol": tol, "fp64_ms": 1e3 * t64, "fp64_iters": it64, "mixed_ms": 1e3 * t32, "mixed_iters": it32,
-                   "mixed_final_rel_residual": r32, "speedup_mixed_vs_fp64": t64 / t32}
+                   "mixed_final_rel_residual": r32, "speedup_mixed_vs_fp64": t64 / t32,
+                   "pcg": {"fp64_ms": 1e3 * p64, "fp64_iters": pit64, "mixed_ms": 1e3 * p32, "mixed_iters": pit32,
+                           "method": "CG preconditioned by one V-cycle (mg_pcg)"}}
             Hm.close()
 
         serving = None

@@ -193,6 +193,24 @@ mg_status mg_solve(mg_hierarchy *h, const double *b_dev, double *x_dev, double r
 mg_status mg_solve_host(mg_hierarchy *h, const double *b_host, double *x_host, double rel_tol, int *iters,
                         double *res_hist);
 
+/* Conjugate gradients preconditioned by one V-cycle (the paper, Sec. 1: multigrid is
+ * most often used as the preconditioner of a Krylov method such as CG or GMRES; for
+ * these symmetric positive definite systems that is CG, Saad Alg. 9.1, M^-1 r = V(r)):
+ *   r_0 = b - A x_0; per iteration z = V(r), rz = (r, z), p = z + (rz / rz_old) p
+ *   (p = z first), q = A p, alpha = rz / (p, q), x += alpha p, r -= alpha q,
+ * in FP64 on the finest operator (the V-cycle in the hierarchy's precision). Stops when
+ * ||r|| <= rel_tol ||b|| for the recursively updated r; iters counts V-cycles and
+ * res_hist (host, may be NULL, max_iters + 1 doubles) holds ||r_k|| / ||b||. The
+ * V-cycle must be symmetric: MG_EINVAL unless nu_pre == nu_post (Gauss-Seidel runs
+ * its colours backward after the correction). MG_ENOCONV after max_iters iterations,
+ * x holding the last iterate. Arguments, ownership and synchronisation as mg_solve. */
+mg_status mg_pcg(mg_hierarchy *h, const double *b_dev, double *x_dev, double rel_tol, int *iters,
+                 double *res_hist);
+
+/* mg_pcg with host arrays (x_host also supplies the initial guess). */
+mg_status mg_pcg_host(mg_hierarchy *h, const double *b_host, double *x_host, double rel_tol, int *iters,
+                      double *res_hist);
+
 /* Exactly n_cycles defect-correction iterations without a stop test (no host
  * synchronisation between them). rel_res (may be NULL): ||r|| / ||b|| of the last
  * residual computed, i.e. before the last correction. */
@@ -217,7 +235,8 @@ mg_status mg_export_operator(const mg_hierarchy *h, int level, int which, int pr
 #define MG_K_OUTER 5    /* FP64 outer residual and its norm */
 #define MG_K_UPDATE 6   /* x += c */
 #define MG_K_SMOOTH0 7  /* first smoother step from x = 0 (diagonal only, no matrix-vector product) */
-#define MG_K_COUNT 8
+#define MG_K_KRYLOV 8   /* conjugate gradients: inner products, search direction, A p, x and r update */
+#define MG_K_COUNT 9
 /* enable: 0 off, else on for launches whose class bit is set in class_mask and whose
  * level bit is set in level_mask (~0u: all). Resets the accumulated profile. With
  * profiling on, mg_cycle synchronises after every iteration to read the events. */

@@ -422,7 +422,9 @@ __device__ __forceinline__ double block_sum(double v, double *sh)
     return s;  // valid in thread 0
 }
 
-__device__ __forceinline__ void finish_norm(double part, double *partial, unsigned *ticket, double *out)
+// Sum of `part` over the grid in a fixed order: block sums to partial[], the last block
+// to finish (ticket) adds them up. Returns true in the thread that wrote *out.
+__device__ __forceinline__ bool finish_norm(double part, double *partial, unsigned *ticket, double *out)
 {
     __shared__ double sh[32];
     __shared__ bool last;
@@ -434,7 +436,7 @@ __device__ __forceinline__ void finish_norm(double part, double *partial, unsign
         last = (t == gridDim.x - 1);
     }
     __syncthreads();
-    if (!last) return;
+    if (!last) return false;
     __threadfence();
     double acc = 0.0;
     for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x) acc += ((volatile double *)partial)[k];
@@ -442,7 +444,9 @@ __device__ __forceinline__ void finish_norm(double part, double *partial, unsign
     if (threadIdx.x == 0) {
         *out = tot;
         *ticket = 0u;
+        return true;
     }
+    return false;
 }
 
 template <typename Tin, int FMT, int K>

@@ -1,0 +1,126 @@
+// krylov.cuh -- conjugate gradients preconditioned by one V-cycle (internal).
+//
+// The paper notes that multigrid is most often used as the preconditioner of a Krylov
+// method (Sec. 1). For the symmetric positive definite Q1 / rotated-Q1 systems that is
+// preconditioned CG (Saad, Alg. 9.1) with M^-1 r = V(r). One iteration is one V-cycle on
+// the FP64 residual (in the inner precision) followed by four FP64 kernels:
+//   k_pcg_rz      rz = (r, z)                          z: the V-cycle's correction
+//   k_pcg_dir     p = z + (rz / rz_old) p              (p = z in the first iteration)
+//   k_pcg_apply   q = A p, pq = (p, q)                 A: the FP64 finest operator
+//   k_pcg_update  x += alpha p, r -= alpha q, ||r||^2, alpha = rz / pq; rz_old = rz
+// The scalars live in device memory (scal[]), so the iteration needs no host round trip
+// except for the residual norm of the stopping test. Inner products are reduced in a
+// fixed order (block sums, then the last block), so a solve is deterministic.
+#pragma once
+
+#include "kernels.cuh"
+
+namespace mgk {
+
+enum PcgScalar { PCG_RZ = 0, PCG_RZ_OLD = 1, PCG_PQ = 2, PCG_NSCAL = 4 };
+
+// row i of the FP64 operator applied to the padded vector v
+template <int FMT, int K>
+__device__ __forceinline__ double pcg_row(const MatView<double> &A, int i, const double *__restrict__ v)
+{
+    double s = 0.0;
+    if (FMT == 3) {  // DIA
+        double a[K], xv[K];
+#pragma unroll
+        for (int k = 0; k < K; k++) a[k] = __ldcs(A.val + (int64_t)k * A.ld + i);
+#pragma unroll
+        for (int k = 0; k < K; k++) xv[k] = __ldg(v + i + A.offs.o[k]);
+#pragma unroll
+        for (int k = 0; k < K; k++) s = __fma_rn(a[k], xv[k], s);
+    } else if (FMT == 2) {  // ELL
+        for (int k = 0; k < A.K; k++) {
+            int c = __ldcs(A.col + (int64_t)k * A.ld + i);
+            s = __fma_rn(__ldcs(A.val + (int64_t)k * A.ld + i), __ldg(v + c), s);
+        }
+    } else {  // CSR
+        for (int64_t k = A.rowptr[i]; k < A.rowptr[i + 1]; k++) s = __fma_rn(A.val[k], __ldg(v + A.col[k]), s);
+    }
+    return s;
+}
+
+// r = b - A x in FP64 (kept in r64 and, in the inner precision, in rin: the V-cycle's
+// right-hand side); p = 0, rz_old = 0; ||r||^2 -> norm2
+template <typename Tin, int FMT, int K>
+__global__ void __launch_bounds__(256) k_pcg_init(MatView<double> A, int n, const double *__restrict__ x,
+                                                  const double *__restrict__ b, double *__restrict__ r64,
+                                                  Tin *__restrict__ rin, double *__restrict__ p, double *scal,
+                                                  double *partial, unsigned *ticket, double *norm2)
+{
+    pdl_enter();
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double sq = 0.0;
+    if (i < n) {
+        double ri = __dsub_rn(b[i], pcg_row<FMT, K>(A, i, x));
+        r64[i] = ri;
+        rin[i] = (Tin)ri;
+        p[i] = 0.0;
+        sq = __dmul_rn(ri, ri);
+    }
+    if (i == 0) scal[PCG_RZ_OLD] = 0.0;
+    finish_norm(sq, partial, ticket, norm2);
+}
+
+template <typename Tin>
+__global__ void __launch_bounds__(256) k_pcg_rz(const double *__restrict__ r, const Tin *__restrict__ z, int n,
+                                                double *partial, unsigned *ticket, double *scal)
+{
+    pdl_enter();
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double part = i < n ? __dmul_rn(r[i], (double)z[i]) : 0.0;
+    finish_norm(part, partial, ticket, scal + PCG_RZ);
+}
+
+template <typename Tin>
+__global__ void __launch_bounds__(256) k_pcg_dir(const Tin *__restrict__ z, double *__restrict__ p, int n,
+                                                 const double *__restrict__ scal)
+{
+    pdl_enter();
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double ro = scal[PCG_RZ_OLD];
+    double beta = ro == 0.0 ? 0.0 : __ddiv_rn(scal[PCG_RZ], ro);
+    p[i] = __dadd_rn((double)z[i], __dmul_rn(beta, p[i]));
+}
+
+template <int FMT, int K>
+__global__ void __launch_bounds__(256) k_pcg_apply(MatView<double> A, int n, const double *__restrict__ p,
+                                                   double *__restrict__ q, double *partial, unsigned *ticket,
+                                                   double *scal)
+{
+    pdl_enter();
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double part = 0.0;
+    if (i < n) {
+        double s = pcg_row<FMT, K>(A, i, p);
+        q[i] = s;
+        part = __dmul_rn(p[i], s);
+    }
+    finish_norm(part, partial, ticket, scal + PCG_PQ);
+}
+
+template <typename Tin>
+__global__ void __launch_bounds__(256) k_pcg_update(double *__restrict__ x, double *__restrict__ r,
+                                                    Tin *__restrict__ rin, const double *__restrict__ p,
+                                                    const double *__restrict__ q, int n, double *scal,
+                                                    double *partial, unsigned *ticket, double *norm2)
+{
+    pdl_enter();
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double alpha = __ddiv_rn(scal[PCG_RZ], scal[PCG_PQ]);
+    double sq = 0.0;
+    if (i < n) {
+        x[i] = __dadd_rn(x[i], __dmul_rn(alpha, p[i]));
+        double ri = __dsub_rn(r[i], __dmul_rn(alpha, q[i]));
+        r[i] = ri;
+        rin[i] = (Tin)ri;
+        sq = __dmul_rn(ri, ri);
+    }
+    if (finish_norm(sq, partial, ticket, norm2)) scal[PCG_RZ_OLD] = scal[PCG_RZ];
+}
+
+}  // namespace mgk

@@ -122,12 +122,16 @@ struct mg_hierarchy {
     double *norm2 = nullptr;
     double *h_norm2 = nullptr;  // pinned
     cudaGraphExec_t g_r = nullptr, g_v = nullptr;
+    // preconditioned CG (mg_pcg): FP64 residual, search direction (padded like x64), A p,
+    // the recurrence scalars; one graph for r_0, one per iteration
+    double *pcg_r = nullptr, *pcg_p = nullptr, *pcg_q = nullptr, *pcg_scal = nullptr;
+    cudaGraphExec_t g_pi = nullptr, g_pc = nullptr;
     bool capturing = false;
     // profiling
     bool profiling = false;
     unsigned prof_class_mask = ~0u, prof_level_mask = ~0u;
     mgi::Prof prof;
-    std::vector<mgi::Prof::Rec> rec_r, rec_v, rec_eager;
+    std::vector<mgi::Prof::Rec> rec_r, rec_v, rec_pi, rec_pc, rec_eager;
     std::vector<mgi::Prof::Rec> *sink = nullptr;
     int kernels_per_cycle = 0;
     int counting = 0;  // counts launches while > 0

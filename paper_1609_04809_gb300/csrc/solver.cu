@@ -17,12 +17,14 @@
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <type_traits>
 #include <string>
 #include <vector>
 
 #include "host_setup.h"
 #include "kernels.cuh"
 #include "gs.cuh"
+#include "krylov.cuh"
 #include "mg.h"
 #include "mg_internal.h"
 
@@ -199,9 +201,13 @@ static void destroy_graphs(mg_hierarchy *h)
 {
     if (h->g_r) cudaGraphExecDestroy(h->g_r);
     if (h->g_v) cudaGraphExecDestroy(h->g_v);
-    h->g_r = h->g_v = nullptr;
+    if (h->g_pi) cudaGraphExecDestroy(h->g_pi);
+    if (h->g_pc) cudaGraphExecDestroy(h->g_pc);
+    h->g_r = h->g_v = h->g_pi = h->g_pc = nullptr;
     h->prof.release(h->rec_r);
     h->prof.release(h->rec_v);
+    h->prof.release(h->rec_pi);
+    h->prof.release(h->rec_pc);
 }
 
 mg_hierarchy::~mg_hierarchy()
@@ -650,6 +656,96 @@ static void enqueue_v(mg_hierarchy *h, cudaStream_t s)
     }
 }
 
+// ---- preconditioned CG ----
+template <typename MK>
+static void launch_fp64_rows(mg_hierarchy *h, const DevMat &A, MK &&mk)
+{
+    if (A.fmt == MG_STORAGE_DIA) {
+        if (A.K == 27)
+            mk(std::integral_constant<int, 3>(), std::integral_constant<int, 27>());
+        else if (A.K == 21)
+            mk(std::integral_constant<int, 3>(), std::integral_constant<int, 21>());
+        else
+            mk(std::integral_constant<int, 3>(), std::integral_constant<int, 9>());
+    } else if (A.fmt == MG_STORAGE_ELL) {
+        mk(std::integral_constant<int, 2>(), std::integral_constant<int, 1>());
+    } else {
+        mk(std::integral_constant<int, 1>(), std::integral_constant<int, 1>());
+    }
+}
+
+// r_0 = b - A x_0 (FP64, and in the inner precision as the V-cycle's right-hand side)
+template <typename T>
+static void enqueue_pcg_init(mg_hierarchy *h, cudaStream_t s)
+{
+    LevelD &F = h->lev[h->Lf];
+    const DevMat &A = h->A64;
+    int n = (int)F.n;
+    double entries = A.fmt == MG_STORAGE_CSR ? (double)A.nnz : (double)A.K * n;
+    LaunchScope ls(h, s, MG_K_OUTER, h->Lf, mat_bytes(A, 8) + 32.0 * n + (double)n * sizeof(T),
+                   2.0 * entries + 3.0 * n);
+    MatView<double> v = view<double>(A);
+    bool pdl = h->opt.use_pdl != 0;
+    dim3 g(grid_for(n)), blk(256);
+    launch_fp64_rows(h, A, [&](auto fmt, auto k) {
+        klaunch(pdl, k_pcg_init<T, decltype(fmt)::value, decltype(k)::value>, g, blk, 0, s, v, n,
+                (const double *)h->x64, (const double *)h->b64, h->pcg_r, (T *)F.b, h->pcg_p, h->pcg_scal,
+                h->partial, h->ticket, h->norm2);
+    });
+}
+
+// one CG iteration: z = V(r), rz, p, q = A p, x and r
+template <typename T>
+static void enqueue_pcg_iter(mg_hierarchy *h, cudaStream_t s)
+{
+    LevelD &F = h->lev[h->Lf];
+    const DevMat &A = h->A64;
+    int n = (int)F.n, sv = sizeof(T);
+    bool pdl = h->opt.use_pdl != 0;
+    dim3 g(grid_for(n)), blk(256);
+    int c = enqueue_vcycle<T>(h, s);
+    const T *z = (const T *)F.x[c];
+    {
+        LaunchScope ls(h, s, MG_K_KRYLOV, h->Lf, 8.0 * n + (double)n * sv, 2.0 * n);
+        klaunch(pdl, k_pcg_rz<T>, g, blk, 0, s, (const double *)h->pcg_r, z, n, h->partial, h->ticket,
+                h->pcg_scal);
+    }
+    {
+        LaunchScope ls(h, s, MG_K_KRYLOV, h->Lf, 16.0 * n + (double)n * sv, 2.0 * n);
+        klaunch(pdl, k_pcg_dir<T>, g, blk, 0, s, z, h->pcg_p, n, (const double *)h->pcg_scal);
+    }
+    {
+        double entries = A.fmt == MG_STORAGE_CSR ? (double)A.nnz : (double)A.K * n;
+        LaunchScope ls(h, s, MG_K_KRYLOV, h->Lf, mat_bytes(A, 8) + 16.0 * n, 2.0 * entries + 2.0 * n);
+        MatView<double> v = view<double>(A);
+        launch_fp64_rows(h, A, [&](auto fmt, auto k) {
+            klaunch(pdl, k_pcg_apply<decltype(fmt)::value, decltype(k)::value>, g, blk, 0, s, v, n,
+                    (const double *)h->pcg_p, h->pcg_q, h->partial, h->ticket, h->pcg_scal);
+        });
+    }
+    {
+        LaunchScope ls(h, s, MG_K_KRYLOV, h->Lf, 48.0 * n + (double)n * sv, 6.0 * n);
+        klaunch(pdl, k_pcg_update<T>, g, blk, 0, s, h->x64, h->pcg_r, (T *)F.b, (const double *)h->pcg_p,
+                (const double *)h->pcg_q, n, h->pcg_scal, h->partial, h->ticket, h->norm2);
+    }
+}
+
+static void enqueue_pi(mg_hierarchy *h, cudaStream_t s)
+{
+    if (h->mixed)
+        enqueue_pcg_init<float>(h, s);
+    else
+        enqueue_pcg_init<double>(h, s);
+}
+
+static void enqueue_pc(mg_hierarchy *h, cudaStream_t s)
+{
+    if (h->mixed)
+        enqueue_pcg_iter<float>(h, s);
+    else
+        enqueue_pcg_iter<double>(h, s);
+}
+
 static cudaGraphExec_t capture(mg_hierarchy *h, void (*fn)(mg_hierarchy *, cudaStream_t), std::vector<mgi::Prof::Rec> *sink)
 {
     cudaGraph_t g = nullptr;
@@ -706,6 +802,23 @@ static double time_vcycle_graph(mg_hierarchy *h)
     return ms[ms.size() / 2];
 }
 
+static void ensure_pcg_graphs(mg_hierarchy *h)
+{
+    if (!h->opt.use_graph || (h->g_pi && h->g_pc)) return;
+    h->g_pi = capture(h, enqueue_pi, &h->rec_pi);
+    h->g_pc = capture(h, enqueue_pc, &h->rec_pc);
+}
+
+static void run_graph_or_eager(mg_hierarchy *h, cudaGraphExec_t g, void (*fn)(mg_hierarchy *, cudaStream_t))
+{
+    if (h->opt.use_graph) {
+        CK(cudaGraphLaunch(g, h->s));
+    } else {
+        h->sink = &h->rec_eager;
+        fn(h, h->s);
+    }
+}
+
 static void run_r(mg_hierarchy *h)
 {
     if (h->opt.use_graph) {
@@ -733,6 +846,18 @@ static void prof_collect(mg_hierarchy *h, bool r_ran, bool v_ran)
     if (h->opt.use_graph) {
         if (r_ran) h->prof.collect(h->rec_r);
         if (v_ran) h->prof.collect(h->rec_v);
+    } else {
+        h->prof.collect(h->rec_eager);
+        h->prof.release(h->rec_eager);
+    }
+}
+
+static void prof_collect_pcg(mg_hierarchy *h, bool init_ran, bool iter_ran)
+{
+    if (!h->profiling) return;
+    if (h->opt.use_graph) {
+        if (init_ran) h->prof.collect(h->rec_pi);
+        if (iter_ran) h->prof.collect(h->rec_pc);
     } else {
         h->prof.collect(h->rec_eager);
         h->prof.release(h->rec_eager);
@@ -1271,6 +1396,11 @@ void mgi::build_hierarchy(mg_hierarchy *h, const mg_problem *p, const mg_options
             char *base = (char *)vec((size_t)(F.A.ld + 2 * h->pad64) * 8);
             h->x64 = take ? (double *)(base + (size_t)h->pad64 * 8) : nullptr;
             h->b64 = (double *)vec((size_t)F.A.ld * 8);
+            char *pb = (char *)vec((size_t)(F.A.ld + 2 * h->pad64) * 8);  // CG search direction
+            h->pcg_p = take ? (double *)(pb + (size_t)h->pad64 * 8) : nullptr;
+            h->pcg_r = (double *)vec((size_t)F.A.ld * 8);
+            h->pcg_q = (double *)vec((size_t)F.A.ld * 8);
+            h->pcg_scal = (double *)vec(PCG_NSCAL * 8);
         }
         h->lu = (double *)vec((size_t)h->n0 * h->n0 * 8);
         h->piv = (int *)vec((size_t)h->n0 * 4);
@@ -1493,6 +1623,37 @@ static mg_status solve_internal(mg_hierarchy *h, double tol, int *iters, double 
     return st;
 }
 
+// CG preconditioned by one V-cycle; hist[k] = ||r_k|| / ||b|| of the recursively updated
+// residual, the same stopping rule as the defect correction
+static mg_status pcg_internal(mg_hierarchy *h, double tol, int *iters, double *hist)
+{
+    if (h->opt.nu_pre != h->opt.nu_post)
+        throw Error(MG_EINVAL, "conjugate gradients need a symmetric V-cycle (nu_pre == nu_post)");
+    ensure_pcg_graphs(h);
+    double nb = norm_b(h);
+    int k = 0;
+    mg_status st = MG_ENOCONV;
+    run_graph_or_eager(h, h->g_pi, enqueue_pi);
+    double nr = std::sqrt(read_norm2(h));
+    prof_collect_pcg(h, true, false);
+    for (;;) {
+        double rel = nb > 0.0 ? nr / nb : nr;
+        if (hist) hist[k] = rel;
+        if (rel <= tol) {
+            st = MG_OK;
+            break;
+        }
+        if (k == h->opt.max_iters) break;
+        run_graph_or_eager(h, h->g_pc, enqueue_pc);
+        nr = std::sqrt(read_norm2(h));
+        prof_collect_pcg(h, false, true);
+        k++;
+    }
+    if (iters) *iters = k;
+    if (st == MG_ENOCONV) g_err = "max_iters reached before the tolerance";
+    return st;
+}
+
 template <typename F>
 static mg_status guarded(mg_hierarchy *h, F &&fn)
 {
@@ -1544,6 +1705,40 @@ extern "C" mg_status mg_solve_host(mg_hierarchy *h, const double *b_host, double
         CK(cudaMemcpyAsync(h->b64, b_host, bytes, cudaMemcpyHostToDevice, h->s));
         CK(cudaMemcpyAsync(h->x64, x_host, bytes, cudaMemcpyHostToDevice, h->s));
         mg_status st = solve_internal(h, rel_tol, iters, res_hist);
+        CK(cudaMemcpyAsync(x_host, h->x64, bytes, cudaMemcpyDeviceToHost, h->s));
+        join_out(h);
+        return st;
+    });
+}
+
+extern "C" mg_status mg_pcg(mg_hierarchy *h, const double *b_dev, double *x_dev, double rel_tol, int *iters,
+                            double *res_hist)
+{
+    return guarded(h, [&]() -> mg_status {
+        if (!b_dev || !x_dev) throw Error(MG_EINVAL, "b or x is NULL");
+        if (!h->with_vectors) throw Error(MG_EINVAL, "hierarchy has no vectors");
+        size_t bytes = (size_t)h->lev[h->Lf].n * 8;
+        join_in(h);
+        CK(cudaMemcpyAsync(h->b64, b_dev, bytes, cudaMemcpyDeviceToDevice, h->s));
+        CK(cudaMemcpyAsync(h->x64, x_dev, bytes, cudaMemcpyDeviceToDevice, h->s));
+        mg_status st = pcg_internal(h, rel_tol, iters, res_hist);
+        CK(cudaMemcpyAsync(x_dev, h->x64, bytes, cudaMemcpyDeviceToDevice, h->s));
+        join_out(h);
+        return st;
+    });
+}
+
+extern "C" mg_status mg_pcg_host(mg_hierarchy *h, const double *b_host, double *x_host, double rel_tol, int *iters,
+                                 double *res_hist)
+{
+    return guarded(h, [&]() -> mg_status {
+        if (!b_host || !x_host) throw Error(MG_EINVAL, "b or x is NULL");
+        if (!h->with_vectors) throw Error(MG_EINVAL, "hierarchy has no vectors");
+        size_t bytes = (size_t)h->lev[h->Lf].n * 8;
+        join_in(h);
+        CK(cudaMemcpyAsync(h->b64, b_host, bytes, cudaMemcpyHostToDevice, h->s));
+        CK(cudaMemcpyAsync(h->x64, x_host, bytes, cudaMemcpyHostToDevice, h->s));
+        mg_status st = pcg_internal(h, rel_tol, iters, res_hist);
         CK(cudaMemcpyAsync(x_host, h->x64, bytes, cudaMemcpyDeviceToHost, h->s));
         join_out(h);
         return st;

@@ -20,9 +20,9 @@ MG_FP64, MG_MIXED = 0, 1
 MG_STORAGE_AUTO, MG_STORAGE_CSR, MG_STORAGE_ELL, MG_STORAGE_DIA = 0, 1, 2, 3
 MG_MAX_LEVELS = 16
 (MG_K_SMOOTH, MG_K_RESID, MG_K_RESTRICT, MG_K_PROLONG, MG_K_COARSE, MG_K_OUTER, MG_K_UPDATE,
- MG_K_SMOOTH0) = range(8)
-MG_K_COUNT = 8
-KCLASS_NAMES = ["smooth", "resid", "restrict", "prolong", "coarse", "outer", "update", "smooth0"]
+ MG_K_SMOOTH0, MG_K_KRYLOV) = range(9)
+MG_K_COUNT = 9
+KCLASS_NAMES = ["smooth", "resid", "restrict", "prolong", "coarse", "outer", "update", "smooth0", "krylov"]
 
 
 class MgError(RuntimeError):
@@ -95,6 +95,8 @@ SIGNATURES = {
     "mg_get_info": (ctypes.c_int, [_vp, _P(mg_info)]),
     "mg_solve": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, _P(ctypes.c_int), _dp]),
     "mg_solve_host": (ctypes.c_int, [_vp, _dp, _dp, ctypes.c_double, _P(ctypes.c_int), _dp]),
+    "mg_pcg": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, _P(ctypes.c_int), _dp]),
+    "mg_pcg_host": (ctypes.c_int, [_vp, _dp, _dp, ctypes.c_double, _P(ctypes.c_int), _dp]),
     "mg_cycle": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _dp]),
     "mg_export_operator": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P(ctypes.c_int64),
                                           _P(ctypes.c_int64), _P(ctypes.c_int64), _P(ctypes.c_int32), _dp]),
@@ -301,6 +303,27 @@ def mg_solve_host(h, b_host, x_host, rel_tol, max_iters=100):
     return st, it.value, hist[:it.value + 1].copy()
 
 
+def mg_pcg(h, b_dev, x_dev, rel_tol, max_iters=100):
+    """CG preconditioned by one V-cycle; arguments and result as mg_solve."""
+    it = ctypes.c_int(0)
+    hist = np.zeros(max_iters + 1)
+    st = lib().mg_pcg(h, ctypes.c_void_p(b_dev.data_ptr()), ctypes.c_void_p(x_dev.data_ptr()),
+                      float(rel_tol), ctypes.byref(it), _as_dp(hist))
+    _check(st, (MG_OK, MG_ENOCONV))
+    return st, it.value, hist[:it.value + 1].copy()
+
+
+def mg_pcg_host(h, b_host, x_host, rel_tol, max_iters=100):
+    """mg_pcg with float64 numpy arrays (x_host updated in place)."""
+    assert b_host.dtype == np.float64 and x_host.dtype == np.float64
+    assert b_host.flags.c_contiguous and x_host.flags.c_contiguous
+    it = ctypes.c_int(0)
+    hist = np.zeros(max_iters + 1)
+    st = lib().mg_pcg_host(h, _as_dp(b_host), _as_dp(x_host), float(rel_tol), ctypes.byref(it), _as_dp(hist))
+    _check(st, (MG_OK, MG_ENOCONV))
+    return st, it.value, hist[:it.value + 1].copy()
+
+
 def mg_cycle(h, b_dev, x_dev, n_cycles):
     rel = ctypes.c_double(0.0)
     _check(lib().mg_cycle(h, ctypes.c_void_p(b_dev.data_ptr()), ctypes.c_void_p(x_dev.data_ptr()),
@@ -378,6 +401,12 @@ class Hierarchy:
 
     def solve_host(self, b_host, x_host, rel_tol):
         return mg_solve_host(self.h, b_host, x_host, rel_tol, self.options.max_iters)
+
+    def pcg(self, b_dev, x_dev, rel_tol):
+        return mg_pcg(self.h, b_dev, x_dev, rel_tol, self.options.max_iters)
+
+    def pcg_host(self, b_host, x_host, rel_tol):
+        return mg_pcg_host(self.h, b_host, x_host, rel_tol, self.options.max_iters)
 
     def cycle(self, b_dev, x_dev, n_cycles):
         return mg_cycle(self.h, b_dev, x_dev, n_cycles)
