@@ -4,12 +4,13 @@
 // method (Sec. 1). For the symmetric positive definite Q1 / rotated-Q1 systems that is
 // preconditioned CG (Saad, Alg. 9.1) with M^-1 r = V(r). One iteration is one V-cycle on
 // the FP64 residual (in the inner precision) followed by four FP64 kernels:
-//   k_pcg_rz      rz = (r, z)                          z: the V-cycle's correction
-//   k_pcg_dir     p = z + (rz / rz_old) p              (p = z in the first iteration)
-//   k_pcg_apply   q = A p, pq = (p, q)                 A: the FP64 finest operator
-//   k_pcg_update  x += alpha p, r -= alpha q, ||r||^2, alpha = rz / pq; rz_old = rz
+//   k_pcg_rz      rz = (r, z), beta = rz / rz_old      z: the V-cycle's correction
+//   k_pcg_dir     p = z + beta p                       (beta = 0 in the first iteration)
+//   k_pcg_apply   q = A p, pq = (p, q), alpha = rz / pq   A: the FP64 finest operator
+//   k_pcg_update  x += alpha p, r -= alpha q, ||r||^2; rz_old = rz
 // The scalars live in device memory (scal[]), so the iteration needs no host round trip
-// except for the residual norm of the stopping test. Inner products are reduced in a
+// except for the residual norm of the stopping test. Each division is done once, by the
+// thread that finishes the reduction it needs. Inner products are reduced in a
 // fixed order (block sums, then the last block), so a solve is deterministic.
 #pragma once
 
@@ -17,7 +18,7 @@
 
 namespace mgk {
 
-enum PcgScalar { PCG_RZ = 0, PCG_RZ_OLD = 1, PCG_PQ = 2, PCG_NSCAL = 4 };
+enum PcgScalar { PCG_RZ = 0, PCG_RZ_OLD = 1, PCG_PQ = 2, PCG_ALPHA = 3, PCG_BETA = 4, PCG_NSCAL = 8 };
 
 // row i of the FP64 operator applied to the padded vector v
 template <int FMT, int K>
@@ -72,7 +73,10 @@ __global__ void __launch_bounds__(256) k_pcg_rz(const double *__restrict__ r, co
     pdl_enter();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     double part = i < n ? __dmul_rn(r[i], (double)z[i]) : 0.0;
-    finish_norm(part, partial, ticket, scal + PCG_RZ);
+    if (finish_norm(part, partial, ticket, scal + PCG_RZ)) {
+        double ro = scal[PCG_RZ_OLD];
+        scal[PCG_BETA] = ro == 0.0 ? 0.0 : __ddiv_rn(scal[PCG_RZ], ro);
+    }
 }
 
 template <typename Tin>
@@ -82,9 +86,7 @@ __global__ void __launch_bounds__(256) k_pcg_dir(const Tin *__restrict__ z, doub
     pdl_enter();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    double ro = scal[PCG_RZ_OLD];
-    double beta = ro == 0.0 ? 0.0 : __ddiv_rn(scal[PCG_RZ], ro);
-    p[i] = __dadd_rn((double)z[i], __dmul_rn(beta, p[i]));
+    p[i] = __dadd_rn((double)z[i], __dmul_rn(scal[PCG_BETA], p[i]));
 }
 
 template <int FMT, int K>
@@ -100,7 +102,7 @@ __global__ void __launch_bounds__(256) k_pcg_apply(MatView<double> A, int n, con
         q[i] = s;
         part = __dmul_rn(p[i], s);
     }
-    finish_norm(part, partial, ticket, scal + PCG_PQ);
+    if (finish_norm(part, partial, ticket, scal + PCG_PQ)) scal[PCG_ALPHA] = __ddiv_rn(scal[PCG_RZ], scal[PCG_PQ]);
 }
 
 template <typename Tin>
@@ -111,7 +113,7 @@ __global__ void __launch_bounds__(256) k_pcg_update(double *__restrict__ x, doub
 {
     pdl_enter();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    double alpha = __ddiv_rn(scal[PCG_RZ], scal[PCG_PQ]);
+    double alpha = scal[PCG_ALPHA];
     double sq = 0.0;
     if (i < n) {
         x[i] = __dadd_rn(x[i], __dmul_rn(alpha, p[i]));
