@@ -18,6 +18,8 @@ Which parts of the paper each function follows:
   * ``Hierarchy.pcg``: conjugate gradients preconditioned by one V-cycle (Sec. 1: multigrid
     as a preconditioner of a Krylov method), Saad's Alg. 9.1.
   * ``load_vector``: the load vector of the sparse FE system.
+  * ``assemble_mass``, ``heat_B``, ``heat_rhs``, ``heat``: Crank-Nicolson time stepping of
+    the heat equation (Sec. 6 "Model Problem") on the shifted operator A + (2/dt) M.
   * ``colours`` / ``gs_sweep``: the multicolour Gauss-Seidel smoother (the paper's
     Gauss-Seidel step, Eq. GS, on DOFs numbered colour-wise, Sec. 4 "DOF Reordering").
 """
@@ -84,7 +86,9 @@ def lib():
         L.orc_l2_error.restype = ctypes.c_double
         L.orc_l2_error.argtypes = [ctypes.c_int] * 4 + [dp, ip, dp, dp]
         L.orc_setup.restype = vp
-        L.orc_setup.argtypes = [ctypes.c_int] * 4 + [dp, dp, dp, ctypes.c_int, ctypes.c_uint64]
+        L.orc_setup.argtypes = [ctypes.c_int] * 4 + [dp, dp, dp, ctypes.c_int, ctypes.c_uint64, dp, ctypes.c_double]
+        L.orc_assemble_mass.argtypes = [ctypes.c_int] * 3 + [dp, P(_CSR)]
+        L.orc_heat_rhs.argtypes = [P(_CSR), dp, dp, ctypes.c_double, dp]
         L.orc_free.argtypes = [vp]
         L.orc_solve.restype = ctypes.c_int
         L.orc_solve.argtypes = [vp, P(_Opts), dp, dp, ctypes.c_double, dp, ip]
@@ -180,6 +184,56 @@ def assemble(dim, elem, N, k_cell=None):
         return CSR._from_c(c)
     finally:
         L.orc_csr_free(ctypes.byref(c))
+
+
+def mref(dim, elem):
+    """Unit-cell element mass matrix as nearest doubles (Q1 only)."""
+    if elem != Q1:
+        raise ValueError("the mass matrix is built for Q1")
+    return np.array(elements.q1_mass(dim), dtype=np.float64)
+
+
+def assemble_mass(dim, elem, N):
+    """Consistent mass matrix on N^dim cells, Dirichlet DOFs eliminated (CSR copy)."""
+    L = lib()
+    c = _CSR()
+    Mr = mref(dim, elem)
+    if L.orc_assemble_mass(dim, elem, N, _dp(Mr), ctypes.byref(c)) != 0:
+        raise MemoryError("oracle assembly failed")
+    try:
+        return CSR._from_c(c)
+    finally:
+        L.orc_csr_free(ctypes.byref(c))
+
+
+def heat_B(dim, elem, N, sigma, k_cell=None):
+    """B = sigma M - A of the scaled Crank-Nicolson step (entrywise, same pattern)."""
+    A = assemble(dim, elem, N, k_cell)
+    M = assemble_mass(dim, elem, N)
+    assert np.array_equal(A.rowptr, M.rowptr) and np.array_equal(A.col, M.col)
+    return CSR(A.rowptr, A.col, sigma * M.val - A.val, A.shape)
+
+
+def heat_rhs(B, u, bF, t):
+    """rhs = B u + t bF (one Crank-Nicolson right-hand side, see mg_oracle.c)."""
+    rhs = np.zeros(B.shape[0])
+    lib().orc_heat_rhs(ctypes.byref(_c_csr(B)), _dp(_f64(u)), _dp(_f64(bF)), float(t), _dp(rhs))
+    return rhs
+
+
+def heat(H, B, bF, g, u0, tol, method="dc"):
+    """Crank-Nicolson steps n = 0 .. len(g)-2 of (A + sigma M) u^{n+1} = B u^n + (g_n + g_{n+1}) bF,
+    each solved from u^n by defect correction ("dc") or V-cycle CG ("pcg"). Returns (u, iters)."""
+    u = np.array(u0, dtype=np.float64)
+    its = []
+    for k in range(len(g) - 1):
+        rhs = heat_rhs(B, u, bF, g[k] + g[k + 1])
+        solve = H.solve if method == "dc" else H.pcg
+        u, hist, it, conv = solve(rhs, tol, x0=u)
+        if not conv:
+            raise RuntimeError("oracle heat step %d did not converge" % k)
+        its.append(it)
+    return u, its
 
 
 def prolongation(dim, elem, Nc):
@@ -294,15 +348,17 @@ class Options:
 class Hierarchy:
     """Levels 0 (coarsest) .. L (finest, N cells per axis) of the oracle's multigrid."""
 
-    def __init__(self, dim, elem, N, n_levels, k_cell=None, opts=None):
+    def __init__(self, dim, elem, N, n_levels, k_cell=None, opts=None, mass=0.0):
+        """mass: sigma of the shifted operator A + sigma M on every level (0: A alone)."""
         self.opts = opts or Options()
         L = lib()
         self.dim, self.elem, self.N, self.n_levels = dim, elem, N, n_levels
         self.n = ndofs(dim, elem, N)
         K, W, kc = kref(dim, elem), _rq1_w(), _f64(k_cell)
         piters = self.opts.power_iters if self.opts.smoother == CHEBYSHEV else 0
+        Mr = mref(dim, elem) if mass else None
         self._h = L.orc_setup(dim, elem, N, n_levels, _dp(K), _dp(W), _dp(kc), piters,
-                              self.opts.power_seed)
+                              self.opts.power_seed, _dp(Mr), float(mass))
         if not self._h:
             raise ValueError("oracle setup failed (bad sizes or out of memory)")
 

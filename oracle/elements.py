@@ -128,6 +128,23 @@ def q1_stiffness_exact(dim):
     return K
 
 
+def q1_mass_exact(dim):
+    """M[a][b] = int_{unit cell} phi_a phi_b, exact rationals (dim = 2 or 3)."""
+    basis = q1_basis(dim)
+    box = [(0, 1)] * dim + [(0, 0)] * (3 - dim)
+    nl = len(basis)
+    M = [[Fr(0)] * nl for _ in range(nl)]
+    for a in range(nl):
+        for b in range(nl):
+            g = _pmul(basis[a], basis[b])
+            if dim == 2:
+                M[a][b] = sum((v * _mono_int(k[0], 0, 1) * _mono_int(k[1], 0, 1)
+                               for k, v in g.items()), Fr(0))
+            else:
+                M[a][b] = _pint_box(g, box)
+    return M
+
+
 # ---------------------------------------------------------------------------------
 # Rotated Q1 (Rannacher-Turek, face means), 3D only
 # ---------------------------------------------------------------------------------
@@ -220,6 +237,11 @@ def rq1_fine_face_weights_exact():
 def q1_stiffness(dim):
     """Row-major flat list of the unit-cell Q1 stiffness, nearest doubles."""
     return [float(v) for row in q1_stiffness_exact(dim) for v in row]
+
+
+def q1_mass(dim):
+    """Row-major flat list of the unit-cell Q1 mass matrix, nearest doubles."""
+    return [float(v) for row in q1_mass_exact(dim) for v in row]
 
 
 def rq1_stiffness():

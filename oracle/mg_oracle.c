@@ -198,12 +198,34 @@ static int64_t find_col(const orc_csr *A, int64_t row, int64_t col)
  * to a_ij in increasing lexicographic cell order, starting from 0.0.
  * k_cell: per-cell coefficient on this grid (lexicographic, x fastest) or NULL (k=1).
  */
+static int assemble_ref(int dim, int elem, int N, const double *kref, const double *k_cell, double hfac,
+                        orc_csr *A);
+
 int orc_assemble(int dim, int elem, int N, const double *kref, const double *k_cell, orc_csr *A)
+{
+    double h = 1.0 / (double)N;
+    return assemble_ref(dim, elem, N, kref, k_cell, dim == 2 ? 1.0 : h, A);
+}
+
+/*
+ * Consistent mass matrix m_ij = sum_e int_e phi_i phi_j (the time derivative of the heat
+ * equation, Sec. 6 "Model Problem"): the element matrix of a cell of side h is h^d mref
+ * (mref on the unit cell), added in increasing lexicographic cell order like the
+ * stiffness; same pattern as orc_assemble.
+ */
+int orc_assemble_mass(int dim, int elem, int N, const double *mref, orc_csr *M)
+{
+    double h = 1.0 / (double)N;
+    return assemble_ref(dim, elem, N, mref, NULL, dim == 2 ? h * h : (h * h) * h, M);
+}
+
+/* element loop shared by the stiffness and the mass matrix: element matrix
+ * (k_e * hfac) * kref[a][b] */
+static int assemble_ref(int dim, int elem, int N, const double *kref, const double *k_cell, double hfac,
+                        orc_csr *A)
 {
     int64_t n = orc_ndofs(dim, elem, N);
     int64_t NN = N, ncells = dim == 2 ? NN * NN : NN * NN * NN;
-    double h = 1.0 / (double)N;
-    double hfac = dim == 2 ? 1.0 : h;
     memset(A, 0, sizeof(*A));
     A->nrows = A->ncols = n;
     A->rowptr = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
@@ -890,7 +912,8 @@ static int coarse_k(int dim, int NL, const double *kL, int Nl, double *kl)
  * product R A P of the next finer level instead.
  */
 orc_hier *orc_setup(int dim, int elem, int N_finest, int n_levels, const double *kref,
-                    const double *rq1_w, const double *k_cell, int power_iters, uint64_t power_seed)
+                    const double *rq1_w, const double *k_cell, int power_iters, uint64_t power_seed,
+                    const double *mref, double mass)
 {
     if (n_levels < 1 || n_levels > ORC_MAXLEV)
         return NULL;
@@ -929,6 +952,14 @@ orc_hier *orc_setup(int dim, int elem, int N_finest, int n_levels, const double 
             H->galerkin[l] = 1;
         } else {
             rc = orc_assemble(dim, elem, Nl, kref, kl, &H->A[l]);
+            if (rc == 0 && mass != 0.0) { /* the shifted operator A + mass * M */
+                orc_csr M;
+                rc = orc_assemble_mass(dim, elem, Nl, mref, &M);
+                if (rc == 0)
+                    for (int64_t k = 0; k < M.nnz; k++)
+                        H->A[l].val[k] = H->A[l].val[k] + mass * M.val[k];
+                orc_csr_free(&M);
+            }
         }
         free(kl);
         if (rc) {
@@ -1137,6 +1168,25 @@ int orc_solve(orc_hier *H, const orc_opts *o, const double *b, double *x, double
     free(r);
     free(c);
     return status;
+}
+
+/*
+ * Right-hand side of one Crank-Nicolson step of the heat equation (Sec. 6, "Model
+ * Problem": Galerkin FE in space, Crank-Nicolson in time). Multiplying the step
+ *   (M + dt/2 A) u^{n+1} = (M - dt/2 A) u^n + dt/2 (b^{n+1} + b^n)
+ * by sigma = 2/dt gives (A + sigma M) u^{n+1} = B u^n + (b^{n+1} + b^n) with
+ * B = sigma M - A. For a separable source f(t, x) = g(t) F(x), b^n = g(t_n) b_F, so
+ *   rhs_i = sum_j B_ij u_j + t * bF_i,   t = g(t_n) + g(t_{n+1}),
+ * the row sum column-ascending by fused multiply-adds, then a rounded product and sum.
+ */
+void orc_heat_rhs(const orc_csr *B, const double *u, const double *bF, double t, double *rhs)
+{
+    for (int64_t i = 0; i < B->nrows; i++) {
+        double s = 0.0;
+        for (int64_t k = B->rowptr[i]; k < B->rowptr[i + 1]; k++)
+            s = fma(B->val[k], u[B->col[k]], s);
+        rhs[i] = s + t * bF[i];
+    }
 }
 
 /* Euclidean inner product u.v: each product rounded, the sum by Neumaier's

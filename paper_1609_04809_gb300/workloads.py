@@ -60,6 +60,34 @@ def manufactured_modes(dim):
     return [(1.0, (1,) * dim)]
 
 
+def q1_nodal_sine(dim, n_cells, freqs=None, amp=1.0):
+    """amp * prod_d sin(k_d pi x_d) at the interior Q1 vertices (lexicographic, x fastest)."""
+    freqs = freqs or (1,) * dim
+    x = np.arange(1, n_cells) / n_cells
+    v = amp * np.ones(1)
+    for d in reversed(range(dim)):  # x fastest: the last axis outermost
+        v = np.multiply.outer(v, np.sin(freqs[d] * np.pi * x))
+    return v.reshape(-1).copy()
+
+
+def heat_workload(dim=3, n_cells=128, n_levels=6, dt=0.01, t_end=5.0, decay=0.1):
+    """The heat-equation workload (the paper's model problem, Sec. 6, on hexahedra with
+    homogeneous Dirichlet data): u = exp(-decay t) prod_d sin(pi x_d) solves
+    u_t - Lap u = f with f = (d pi^2 - decay) exp(-decay t) prod_d sin(pi x_d), i.e.
+    f(t, x) = g(t) F(x) with g(t) = exp(-decay t).
+
+    Returns a dict: sigma = 2 / dt (the operator A + sigma M of the scaled Crank-Nicolson
+    step), n_steps, g (g(t_k), k = 0..n_steps), the sine mode of F for the load-vector
+    routines (amplitude (d pi^2 - decay) / (d pi^2): they build f = amp pi^2 |k|^2 sin),
+    u0 (nodal values of u at t = 0) and the exact solution's amplitude at t_end."""
+    n_steps = int(round(t_end / dt))
+    g = np.exp(-decay * dt * np.arange(n_steps + 1))
+    dpi2 = dim * np.pi ** 2
+    return dict(dim=dim, n_cells=n_cells, n_levels=n_levels, dt=dt, sigma=2.0 / dt, n_steps=n_steps, g=g,
+                source_modes=[((dpi2 - decay) / dpi2, (1,) * dim)], u0=q1_nodal_sine(dim, n_cells),
+                exact_amp=float(np.exp(-decay * dt * n_steps)))
+
+
 def random_modes(dim, n_modes=4, kmax=8, seed=0):
     """n_modes sine modes with integer frequencies U{1..kmax} per axis and N(0,1) amplitudes."""
     rng = np.random.Generator(np.random.PCG64(seed))

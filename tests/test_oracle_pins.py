@@ -678,3 +678,99 @@ def test_pcg_needs_no_more_cycles_than_defect_correction(orc, smoother):
     assert c1 and c2 and it2 <= it1
     r = b - orc.spmv(H.A(L - 1), x2)  # the recursive residual tracks the true one
     assert abs(np.linalg.norm(r) / np.linalg.norm(b) - h2[-1]) <= 1e-3 * h2[-1]
+
+
+# ---------------------------------------------------------------------------------
+# Crank-Nicolson heat equation (Sec. 6 "Model Problem"): mass matrix, shifted operator
+# ---------------------------------------------------------------------------------
+def test_q1_mass_element_textbook_values(orc):
+    from fractions import Fraction as Fr
+
+    from oracle import elements
+    for dim in (2, 3):
+        M = elements.q1_mass_exact(dim)
+        for a in range(2 ** dim):
+            for b in range(2 ** dim):
+                want = Fr(1)
+                for d in range(dim):
+                    want *= Fr(1, 3) if ((a >> d) & 1) == ((b >> d) & 1) else Fr(1, 6)
+                assert M[a][b] == want
+        assert sum(sum(r) for r in M) == 1  # the unit cell's volume
+
+
+@pytest.mark.parametrize("dim,N", [(2, 8), (2, 12), (3, 6)])
+def test_q1_mass_is_kronecker_product(orc, dim, N):
+    h = 1.0 / N
+    n1 = N - 1
+    M1 = (h / 6) * (4 * np.eye(n1) + np.eye(n1, k=1) + np.eye(n1, k=-1))
+    want = M1
+    for _ in range(dim - 1):
+        want = np.kron(want, M1)
+    M = orc.assemble_mass(dim, orc.Q1, N).dense()
+    assert np.max(np.abs(M - want)) <= 1e-15 * np.max(np.abs(want))
+
+
+def _mode_vector(dim, N, ks):
+    x = np.arange(1, N) / N
+    v = np.ones(1)
+    for d in reversed(range(dim)):
+        v = np.multiply.outer(v, np.sin(ks[d] * np.pi * x))
+    return v.reshape(-1)
+
+
+@pytest.mark.parametrize("dim,N,L,ks", [(2, 16, 3, (1, 2)), (2, 16, 3, (5, 3)), (3, 8, 2, (1, 2, 3))])
+def test_cn_step_damps_a_discrete_mode_by_the_closed_form_factor(orc, dim, N, L, ks):
+    """With f = 0 a DST mode is an eigenvector of A and M: u^n = rho^n u^0 with
+    rho = (sigma - lam) / (sigma + lam), lam = sum_d kappa_k / mu_k (1D eigenvalues)."""
+    h = 1.0 / N
+    sigma = 2.0 / 0.01
+    lam = 0.0
+    for k in ks:
+        kap = (2.0 / h) * (1 - np.cos(k * np.pi / N))
+        mu = (h / 6.0) * (4 + 2 * np.cos(k * np.pi / N))
+        lam += kap / mu
+    rho = (sigma - lam) / (sigma + lam)
+    H = orc.Hierarchy(dim, orc.Q1, N, L, opts=orc.Options(omega=0.8), mass=sigma)
+    B = orc.heat_B(dim, orc.Q1, N, sigma)
+    u0 = _mode_vector(dim, N, ks)
+    n_steps = 5
+    u, its = orc.heat(H, B, np.zeros_like(u0), np.zeros(n_steps + 1), u0, 1e-14)
+    assert np.linalg.norm(u - rho ** n_steps * u0) <= 1e-11 * np.linalg.norm(u0)
+
+
+def test_cn_matches_dense_direct_time_stepping(orc):
+    dim, N, L = 2, 12, 2
+    wl = W.heat_workload(dim=dim, n_cells=N, n_levels=L, dt=0.02, t_end=0.2)
+    sigma = wl["sigma"]
+    H = orc.Hierarchy(dim, orc.Q1, N, L, opts=orc.Options(omega=0.8), mass=sigma)
+    B = orc.heat_B(dim, orc.Q1, N, sigma)
+    bF = orc.load_vector(dim, orc.Q1, N, modes=wl["source_modes"])
+    u, its = orc.heat(H, B, bF, wl["g"], wl["u0"], 1e-13)
+    A = orc.assemble(dim, orc.Q1, N).dense()
+    M = orc.assemble_mass(dim, orc.Q1, N).dense()
+    dt = wl["dt"]
+    ud = wl["u0"].copy()
+    for k in range(wl["n_steps"]):  # the unscaled textbook step
+        rhs = (M - dt / 2 * A) @ ud + dt / 2 * (wl["g"][k] + wl["g"][k + 1]) * bF
+        ud = np.linalg.solve(M + dt / 2 * A, rhs)
+    assert np.linalg.norm(u - ud) <= 1e-10 * np.linalg.norm(ud)
+    # and the shifted operator of every level is A_l + sigma M_l
+    for l in range(L):
+        Nl = H.level_N(l)
+        want = orc.assemble(dim, orc.Q1, Nl).dense() + sigma * orc.assemble_mass(dim, orc.Q1, Nl).dense()
+        assert np.max(np.abs(H.A(l).dense() - want)) <= 1e-15 * np.max(np.abs(want))
+
+
+@pytest.mark.slow
+def test_heat_manufactured_solution_is_second_order(orc):
+    """dt proportional to h: the L2 error at t_end falls by about 4 per refinement."""
+    errs = []
+    for N in (8, 16, 32):
+        wl = W.heat_workload(dim=3, n_cells=N, n_levels=2, dt=0.5 / N, t_end=0.5)
+        H = orc.Hierarchy(3, orc.Q1, N, 2 if N == 8 else 3, opts=orc.Options(omega=0.8), mass=wl["sigma"])
+        B = orc.heat_B(3, orc.Q1, N, wl["sigma"])
+        bF = orc.load_vector(3, orc.Q1, N, modes=wl["source_modes"])
+        u, its = orc.heat(H, B, bF, wl["g"], wl["u0"], 1e-12)
+        errs.append(orc.l2_error(3, orc.Q1, N, [(wl["exact_amp"], (1, 1, 1))], u))
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all((rates > 1.8) & (rates < 2.2)), (errs, rates)
