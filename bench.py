@@ -281,6 +281,55 @@ def serve_bench(args):
         S.close()
 
 
+def heat_report(n_cells=128, n_levels=6, dt=0.01, t_end=5.0, smoother=1, nu=1, tol=1e-10, methods=("dc", "pcg"),
+                precisions=("fp64", "mixed")):
+    """The heat-equation workload (Crank-Nicolson, the paper's model problem on Q1
+    hexahedra): the whole time loop with u resident on the device (mg_heat), per method
+    and precision, and once through the host API (mg_heat_host, host arrays in and out)."""
+    import torch
+
+    from paper_1609_04809_gb300 import mg, workloads as W
+    wl = W.heat_workload(dim=3, n_cells=n_cells, n_levels=n_levels, dt=dt, t_end=t_end)
+    bF = mg.mg_load_vector(3, 0, n_cells, modes=wl["source_modes"])
+    bFd = torch.from_numpy(bF).cuda()
+    exact = W.q1_nodal_sine(3, n_cells, amp=wl["exact_amp"])
+    n = bF.size
+    out = {"workload": "heat_q1_3d_%d" % n_cells, "n_dofs": int(n), "dt": dt, "t_end": t_end,
+           "n_steps": wl["n_steps"], "tol_per_step": tol,
+           "smoother": [k for k, v in SMOOTHERS.items() if v == smoother][0], "nu": nu}
+    meth = {"dc": mg.MG_METHOD_DC, "pcg": mg.MG_METHOD_PCG}
+    for prec in precisions:
+        H = mg.Hierarchy(3, 0, n_cells, n_levels, mass=wl["sigma"], smoother=smoother, nu_pre=nu, nu_post=nu,
+                         precision=mg.MG_MIXED if prec == "mixed" else mg.MG_FP64)
+        for m in methods:
+            u = torch.from_numpy(wl["u0"].copy()).cuda()
+            H.heat(bFd, wl["g"][:4], u, tol, meth[m])  # warm-up: graphs, clocks
+            u.copy_(torch.from_numpy(wl["u0"]))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st, its = H.heat(bFd, wl["g"], u, tol, meth[m])
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+            err = float(np.max(np.abs(u.cpu().numpy() - exact)) / np.max(np.abs(exact)))
+            out["%s_%s" % (m, prec)] = {"status": int(st), "wall_s": wall, "ms_per_step": 1e3 * wall / wl["n_steps"],
+                                        "dof_steps_per_s": n * wl["n_steps"] / wall,
+                                        "vcycles_per_step_mean": float(np.mean(its)),
+                                        "vcycles_per_step_max": int(np.max(its)),
+                                        "rel_max_error_vs_exact": err}
+        if prec == "fp64":  # end to end through the host API
+            uh = torch.from_numpy(wl["u0"].copy()).pin_memory()
+            bh = torch.from_numpy(bF).pin_memory()
+            t0 = time.perf_counter()
+            st, its = H.heat_host(bh.numpy(), wl["g"], uh.numpy(), tol, mg.MG_METHOD_DC)
+            wall = time.perf_counter() - t0
+            out["dc_fp64_host_api"] = {"wall_s": wall, "ms_per_step": 1e3 * wall / wl["n_steps"],
+                                       "h2d_bytes": 16 * n, "d2h_bytes": 8 * n}
+        H.close()
+        del H
+        torch.cuda.empty_cache()
+    return out
+
+
 def config_report(name, steps=20, warmup=5, smoother="workload"):
     """One workload in both precisions: V-cycle throughput, the finest sweep against its
     roofline, and time to 1e-10 (median of 3 solves)."""
@@ -505,6 +554,12 @@ def run_ours(args):
                            "method": "CG preconditioned by one V-cycle (mg_pcg)"}}
             Hm.close()
 
+        heat = None
+        if world == 1 and not args.no_heat:
+            H.close()
+            torch.cuda.empty_cache()
+            heat = heat_report(methods=("dc", "pcg"), precisions=("fp64", "mixed"))
+
         serving = None
         if world == 1 and args.serve_requests > 0:
             H.close()
@@ -534,6 +589,7 @@ def run_ours(args):
                "kernel_ms_per_step": per_kernel,
                "e2e": e2e, "time_to_solution": tts, "cpu_baseline": cpu,
                "gpu_launches": info["kernels_per_cycle"] * args.steps + 1,
+               "heat": heat,
                "serving": serving,
                "clocks": clocks}
         print(json.dumps(out))
@@ -555,6 +611,7 @@ def main():
     ap.add_argument("--cpu-cycles", type=int, default=8)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-heat", action="store_true", help="skip the Crank-Nicolson heat workload")
     ap.add_argument("--serve-requests", type=int, default=4096)
     ap.add_argument("--serve-capacity-requests", type=int, default=1024)
     ap.add_argument("--serve-budget-gb", type=float, default=150.0)
@@ -581,6 +638,8 @@ def main():
         from paper_1609_04809_gb300 import workloads as W
         for name in W.CONFIGS:
             print(json.dumps(config_report(name, smoother=args.smoother)), flush=True)
+        if not args.no_heat:
+            print(json.dumps(heat_report()), flush=True)
         return 0
     return run_ours(args)
 

@@ -76,13 +76,17 @@ typedef int mg_status;
 /* The problem: a uniform grid of n_cells^dim cells on the unit square / cube, refined
  * n_levels-1 times from the coarsest grid of n_cells / 2^(n_levels-1) cells per axis
  * (which must be an integer >= 2). k_cell: host pointer to the per-cell diffusion
- * coefficient of the finest grid (n_cells^dim values, x fastest), or NULL for k = 1. */
+ * coefficient of the finest grid (n_cells^dim values, x fastest), or NULL for k = 1.
+ * mass: sigma >= 0; the operator of every level is A + sigma M with M the consistent
+ * mass matrix (Q1 only), the system of a Crank-Nicolson step scaled by sigma = 2/dt
+ * (mg_heat); 0 for the stiffness matrix alone. Zero-initialise unused fields. */
 typedef struct {
     int dim;
     int element;
     int n_cells;
     int n_levels;
     const double *k_cell;
+    double mass;
 } mg_problem;
 
 /* Solver options. mg_options_default() fills in damped Jacobi (omega 0.8), V(2,2),
@@ -210,6 +214,28 @@ mg_status mg_pcg(mg_hierarchy *h, const double *b_dev, double *x_dev, double rel
 /* mg_pcg with host arrays (x_host also supplies the initial guess). */
 mg_status mg_pcg_host(mg_hierarchy *h, const double *b_host, double *x_host, double rel_tol, int *iters,
                       double *res_hist);
+
+/* Crank-Nicolson time stepping of the heat equation u_t - div(k grad u) = f with
+ * homogeneous Dirichlet data (the paper's model problem, Sec. 6: Galerkin FE in space,
+ * Crank-Nicolson in time; here on Q1 hexahedra). The hierarchy must be set up with
+ * problem.mass = sigma = 2/dt. For a source f(t, x) = g(t) F(x) with load vector bF of
+ * F, step k = 0..n_steps-1 solves
+ *     (A + sigma M) u_{k+1} = (sigma M - A) u_k + (g_k + g_{k+1}) bF
+ * (the step (M + dt/2 A) u' = (M - dt/2 A) u + dt/2 (b' + b) times 2/dt; the right-hand
+ * side row sums column-ascending by fused multiply-adds, then + t*bF_i), starting from
+ * u_k, by defect correction (method MG_METHOD_DC) or V-cycle CG (MG_METHOD_PCG) to
+ * ||r|| <= rel_tol ||rhs||. bF_dev, u_dev: device arrays of n doubles (u: u_0 in, u_n
+ * out); g_host: n_steps + 1 values g(t_k); iters (host, n_steps ints, may be NULL):
+ * V-cycles of each step. MG_ENOCONV if a step does not converge (u holds its last
+ * iterate, later steps are not taken); MG_EINVAL if the hierarchy has no mass shift. */
+#define MG_METHOD_DC 0
+#define MG_METHOD_PCG 1
+mg_status mg_heat(mg_hierarchy *h, const double *bF_dev, const double *g_host, int n_steps, double *u_dev,
+                  double rel_tol, int method, int *iters);
+
+/* mg_heat with host arrays bF_host, u_host (copied in, u copied back). */
+mg_status mg_heat_host(mg_hierarchy *h, const double *bF_host, const double *g_host, int n_steps, double *u_host,
+                       double rel_tol, int method, int *iters);
 
 /* Exactly n_cycles defect-correction iterations without a stop test (no host
  * synchronisation between them). rel_res (may be NULL): ||r|| / ||b|| of the last

@@ -49,6 +49,21 @@ static void q1_kref(int dim, double *K)
         }
 }
 
+// Q1 mass on the unit cell: M_ref = prod_d M1(a_d, b_d), the integer numerator over 6^d
+// rounded by one division.
+static void q1_mref(int dim, double *M)
+{
+    static const int M1[2][2] = {{2, 1}, {1, 2}};
+    int nl = 1 << dim;
+    double den = dim == 2 ? 36.0 : 216.0;
+    for (int a = 0; a < nl; a++)
+        for (int b = 0; b < nl; b++) {
+            int num = 1;
+            for (int d = 0; d < dim; d++) num *= M1[(a >> d) & 1][(b >> d) & 1];
+            M[a * nl + b] = (double)num / den;
+        }
+}
+
 // Rotated Q1 on the unit cube, faces x0,x1,y0,y1,z0,z1: 3 on the diagonal, 1 for the
 // opposite face, -1 for the four other faces.
 static void rq1_kref(double *K)
@@ -220,6 +235,8 @@ static void assemble_row(int dim, int elem, int N, const double *k, const double
     acc.sort();
 }
 
+static void assemble_with(int dim, int elem, int N, const double *k, const double *kref, double hfac, Csr &A);
+
 void assemble(int dim, int elem, int N, const double *k, Csr &A)
 {
     double kref[64];
@@ -228,7 +245,20 @@ void assemble(int dim, int elem, int N, const double *k, Csr &A)
     else
         rq1_kref(kref);
     double h = 1.0 / (double)N;
-    double hfac = dim == 2 ? 1.0 : h;
+    assemble_with(dim, elem, N, k, kref, dim == 2 ? 1.0 : h, A);
+}
+
+void assemble_mass(int dim, int N, Csr &M)
+{
+    double mref[64];
+    q1_mref(dim, mref);
+    double h = 1.0 / (double)N;
+    assemble_with(dim, MG_Q1, N, nullptr, mref, dim == 2 ? h * h : (h * h) * h, M);
+}
+
+// element matrices (k_e * hfac) * kref, added row by row in increasing cell order
+static void assemble_with(int dim, int elem, int N, const double *k, const double *kref, double hfac, Csr &A)
+{
     int64_t n = ndofs(dim, elem, N);
     A.nrows = A.ncols = n;
     A.rowptr.assign((size_t)n + 1, 0);
@@ -627,7 +657,7 @@ double power_lambda(const Csr &A, const std::vector<double> &dinv, int iters, ui
 }
 
 void build_hierarchy(int dim, int elem, int N_finest, int n_levels, const double *k_finest, int stop,
-                     HostHierarchy &H)
+                     HostHierarchy &H, double mass)
 {
     int Lf = n_levels - 1;
     H.N.assign((size_t)n_levels, 0);
@@ -658,6 +688,11 @@ void build_hierarchy(int dim, int elem, int N_finest, int n_levels, const double
             H.galerkin[l] = 1;
         } else {
             assemble(dim, elem, Nl, kp, H.A[l]);
+            if (mass != 0.0) {  // the shifted operator A + mass * M (same pattern)
+                Csr M;
+                assemble_mass(dim, Nl, M);
+                for (size_t q = 0; q < M.val.size(); q++) H.A[l].val[q] = H.A[l].val[q] + mass * M.val[q];
+            }
         }
     }
 }

@@ -26,6 +26,10 @@ int64_t ndofs(int dim, int elem, int N);
 // grid (lexicographic, x fastest) or nullptr for k = 1.
 void assemble(int dim, int elem, int N, const double *k, Csr &A);
 
+// Consistent Q1 mass matrix m_ij = sum_e int_e phi_i phi_j (element matrix h^d M_ref,
+// added in increasing cell order); same pattern as the Q1 stiffness matrix.
+void assemble_mass(int dim, int N, Csr &M);
+
 // Prolongation from Nc to 2 Nc cells per axis (rows: fine DOFs, columns: coarse DOFs).
 void prolongation(int dim, int elem, int Nc, Csr &P);
 
@@ -54,14 +58,15 @@ void round_fp32(const Csr &A, std::vector<float> &val32);
 // axis). Level l is rediscretised with the coefficient of its cells when every cell
 // covers fine cells of one value, else (and on every coarser level) it is R A P of the
 // next finer level. P[l], R[l] (l >= 1) map between levels l-1 and l. Levels below
-// `stop` are not built.
+// `stop` are not built. mass != 0: every rediscretised level holds A_l + mass * M_l
+// (Q1), the operator of a scaled Crank-Nicolson step; Galerkin levels take R S P.
 struct HostHierarchy {
     std::vector<int> N;
     std::vector<int> galerkin;
     std::vector<Csr> A, P, R;
 };
 void build_hierarchy(int dim, int elem, int N_finest, int n_levels, const double *k_finest, int stop,
-                     HostHierarchy &H);
+                     HostHierarchy &H, double mass = 0.0);
 
 // Multicolour Gauss-Seidel ordering. Q1: the parity class of the vertex coordinates,
 // colour (vx&1) + 2(vy&1) [+ 4(vz&1)]; rotated Q1: face family f and parity of the normal

@@ -126,6 +126,10 @@ struct mg_hierarchy {
     // the recurrence scalars; one graph for r_0, one per iteration
     double *pcg_r = nullptr, *pcg_p = nullptr, *pcg_q = nullptr, *pcg_scal = nullptr;
     cudaGraphExec_t g_pi = nullptr, g_pc = nullptr;
+    // Crank-Nicolson (mg_heat): sigma, B = sigma M - A on the finest level (FP64), bF
+    double mass = 0.0;
+    mgi::DevMat B64;
+    double *bF64 = nullptr;
     bool capturing = false;
     // profiling
     bool profiling = false;

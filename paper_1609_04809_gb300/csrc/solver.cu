@@ -25,6 +25,7 @@
 #include "kernels.cuh"
 #include "gs.cuh"
 #include "krylov.cuh"
+#include "heat.cuh"
 #include "mg.h"
 #include "mg_internal.h"
 
@@ -918,6 +919,8 @@ static void validate_problem(const mg_problem *p)
         throw Error(MG_EINVAL, "n_cells must be the coarsest size (>= 2) times 2^(n_levels-1)");
     int64_t n = mgh::ndofs(p->dim, p->element, p->n_cells);
     if (n > (int64_t)INT32_MAX / 32) throw Error(MG_EINVAL, "problem too large for 32-bit row indices");
+    if (!(p->mass >= 0.0) || !std::isfinite(p->mass)) throw Error(MG_EINVAL, "mass must be finite and >= 0");
+    if (p->mass != 0.0 && p->element != MG_Q1) throw Error(MG_EINVAL, "the mass shift is built for Q1");
 }
 
 extern "C" mg_status mg_load_vector(const mg_problem *p, const mg_rhs *f, double *b_host)
@@ -1293,7 +1296,16 @@ void mgi::build_hierarchy(mg_hierarchy *h, const mg_problem *p, const mg_options
     h->lev.resize((size_t)nlev);
     // ---- host hierarchy, finest to coarsest ----
     mgh::HostHierarchy HH;
-    mgh::build_hierarchy(dim, elem, p->n_cells, nlev, p->k_cell, 0, HH);
+    mgh::build_hierarchy(dim, elem, p->n_cells, nlev, p->k_cell, 0, HH, p->mass);
+    h->mass = p->mass;
+    // Crank-Nicolson: B = sigma M - A of the finest level, entrywise on the common pattern
+    mgh::Csr Bh;
+    if (p->mass != 0.0 && with_vectors) {
+        mgh::Csr Mf;
+        mgh::assemble(dim, elem, p->n_cells, p->k_cell, Bh);
+        mgh::assemble_mass(dim, p->n_cells, Mf);
+        for (size_t q = 0; q < Bh.val.size(); q++) Bh.val[q] = p->mass * Mf.val[q] - Bh.val[q];
+    }
     std::vector<mgh::Csr> &A = HH.A, &P = HH.P, &R = HH.R;
     for (int l = Lf; l >= 0; l--) {
         LevelD &L = h->lev[l];
@@ -1401,6 +1413,10 @@ void mgi::build_hierarchy(mg_hierarchy *h, const mg_problem *p, const mg_options
             h->pcg_r = (double *)vec((size_t)F.A.ld * 8);
             h->pcg_q = (double *)vec((size_t)F.A.ld * 8);
             h->pcg_scal = (double *)vec(PCG_NSCAL * 8);
+            if (h->mass != 0.0) {
+                plan_matrix(h->B64, Bh, F.fmt, dim, F.N, 8, S, take);
+                h->bF64 = (double *)vec((size_t)F.A.ld * 8);
+            }
         }
         h->lu = (double *)vec((size_t)h->n0 * h->n0 * 8);
         h->piv = (int *)vec((size_t)h->n0 * 4);
@@ -1440,6 +1456,7 @@ void mgi::build_hierarchy(mg_hierarchy *h, const mg_problem *p, const mg_options
     if (h->mixed) upload_matrix<double>(h->A64, A[Lf], A[Lf].val, dim, h->lev[Lf].N, h->s);
     if (gs)
         for (int l = 1; l <= Lf; l++) upload_gs_copy(h, l, A[l], gs_perm[l]);
+    if (h->B64.val) upload_matrix<double>(h->B64, Bh, Bh.val, dim, h->lev[Lf].N, h->s);
     // ---- coarsest LU on the device ----
     {
         std::vector<double> dense((size_t)h->n0 * h->n0, 0.0);
@@ -1745,6 +1762,74 @@ extern "C" mg_status mg_pcg_host(mg_hierarchy *h, const double *b_host, double *
     });
 }
 
+// Crank-Nicolson steps on the hierarchy's iterate x64 (u_k in, u_n out) with bF in bF64
+static mg_status heat_internal(mg_hierarchy *h, const double *g, int n_steps, double tol, int method, int *iters)
+{
+    int n = (int)h->lev[h->Lf].n;
+    MatView<double> v = view<double>(h->B64);
+    bool pdl = h->opt.use_pdl != 0;
+    for (int k = 0; k < n_steps; k++) {
+        double t = g[k] + g[k + 1];
+        {
+            const DevMat &B = h->B64;
+            double entries = B.fmt == MG_STORAGE_CSR ? (double)B.nnz : (double)B.K * n;
+            LaunchScope ls(h, h->s, MG_K_OUTER, h->Lf, mat_bytes(B, 8) + 24.0 * n, 2.0 * entries + 2.0 * n);
+            launch_fp64_rows(h, B, [&](auto fmt, auto kk) {
+                klaunch(pdl, k_heat_rhs<decltype(fmt)::value, decltype(kk)::value>, dim3(grid_for(n)), dim3(256), 0,
+                        h->s, v, n, (const double *)h->x64, (const double *)h->bF64, t, h->b64);
+            });
+        }
+        int it = 0;
+        mg_status st = method == MG_METHOD_PCG ? pcg_internal(h, tol, &it, nullptr) : solve_internal(h, tol, &it, nullptr);
+        if (iters) iters[k] = it;
+        if (st != MG_OK) return st;
+    }
+    return MG_OK;
+}
+
+static void heat_check(mg_hierarchy *h, const double *g, int n_steps, int method)
+{
+    if (h->mass == 0.0 || !h->B64.val) throw Error(MG_EINVAL, "the hierarchy has no mass shift (problem.mass)");
+    if (!g || n_steps < 0) throw Error(MG_EINVAL, "bad g or n_steps");
+    if (method != MG_METHOD_DC && method != MG_METHOD_PCG) throw Error(MG_EINVAL, "bad method");
+}
+
+extern "C" mg_status mg_heat(mg_hierarchy *h, const double *bF_dev, const double *g_host, int n_steps, double *u_dev,
+                             double rel_tol, int method, int *iters)
+{
+    return guarded(h, [&]() -> mg_status {
+        heat_check(h, g_host, n_steps, method);
+        if (!bF_dev || !u_dev) throw Error(MG_EINVAL, "bF or u is NULL");
+        size_t bytes = (size_t)h->lev[h->Lf].n * 8;
+        ensure_graphs(h);
+        join_in(h);
+        CK(cudaMemcpyAsync(h->bF64, bF_dev, bytes, cudaMemcpyDeviceToDevice, h->s));
+        CK(cudaMemcpyAsync(h->x64, u_dev, bytes, cudaMemcpyDeviceToDevice, h->s));
+        mg_status st = heat_internal(h, g_host, n_steps, rel_tol, method, iters);
+        CK(cudaMemcpyAsync(u_dev, h->x64, bytes, cudaMemcpyDeviceToDevice, h->s));
+        join_out(h);
+        return st;
+    });
+}
+
+extern "C" mg_status mg_heat_host(mg_hierarchy *h, const double *bF_host, const double *g_host, int n_steps,
+                                  double *u_host, double rel_tol, int method, int *iters)
+{
+    return guarded(h, [&]() -> mg_status {
+        heat_check(h, g_host, n_steps, method);
+        if (!bF_host || !u_host) throw Error(MG_EINVAL, "bF or u is NULL");
+        size_t bytes = (size_t)h->lev[h->Lf].n * 8;
+        ensure_graphs(h);
+        join_in(h);
+        CK(cudaMemcpyAsync(h->bF64, bF_host, bytes, cudaMemcpyHostToDevice, h->s));
+        CK(cudaMemcpyAsync(h->x64, u_host, bytes, cudaMemcpyHostToDevice, h->s));
+        mg_status st = heat_internal(h, g_host, n_steps, rel_tol, method, iters);
+        CK(cudaMemcpyAsync(u_host, h->x64, bytes, cudaMemcpyDeviceToHost, h->s));
+        join_out(h);
+        return st;
+    });
+}
+
 extern "C" mg_status mg_cycle(mg_hierarchy *h, const double *b_dev, double *x_dev, int n_cycles, double *rel_res)
 {
     return guarded(h, [&]() -> mg_status {
@@ -1784,7 +1869,8 @@ extern "C" mg_status mg_assemble_operator(const mg_problem *p, int level, int wh
         if (level < 0 || level > Lf || which < 0 || which > 2 || (which > 0 && level < 1))
             throw Error(MG_EINVAL, "bad level/which");
         mgh::HostHierarchy HH;
-        mgh::build_hierarchy(p->dim, p->element, p->n_cells, p->n_levels, p->k_cell, which == 0 ? level : level - 1, HH);
+        mgh::build_hierarchy(p->dim, p->element, p->n_cells, p->n_levels, p->k_cell, which == 0 ? level : level - 1, HH,
+                             p->mass);
         const mgh::Csr &m = which == 0 ? HH.A[level] : (which == 1 ? HH.P[level] : HH.R[level]);
         if (nrows) *nrows = m.nrows;
         if (nnz) *nnz = m.nnz();

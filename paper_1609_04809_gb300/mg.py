@@ -33,7 +33,8 @@ class MgError(RuntimeError):
 
 class mg_problem(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("element", ctypes.c_int), ("n_cells", ctypes.c_int),
-                ("n_levels", ctypes.c_int), ("k_cell", ctypes.POINTER(ctypes.c_double))]
+                ("n_levels", ctypes.c_int), ("k_cell", ctypes.POINTER(ctypes.c_double)),
+                ("mass", ctypes.c_double)]
 
 
 class mg_options(ctypes.Structure):
@@ -97,6 +98,9 @@ SIGNATURES = {
     "mg_solve_host": (ctypes.c_int, [_vp, _dp, _dp, ctypes.c_double, _P(ctypes.c_int), _dp]),
     "mg_pcg": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, _P(ctypes.c_int), _dp]),
     "mg_pcg_host": (ctypes.c_int, [_vp, _dp, _dp, ctypes.c_double, _P(ctypes.c_int), _dp]),
+    "mg_heat": (ctypes.c_int, [_vp, _vp, _dp, ctypes.c_int, _vp, ctypes.c_double, ctypes.c_int, _P(ctypes.c_int)]),
+    "mg_heat_host": (ctypes.c_int, [_vp, _dp, _dp, ctypes.c_int, _dp, ctypes.c_double, ctypes.c_int,
+                                    _P(ctypes.c_int)]),
     "mg_cycle": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _dp]),
     "mg_export_operator": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P(ctypes.c_int64),
                                           _P(ctypes.c_int64), _P(ctypes.c_int64), _P(ctypes.c_int32), _dp]),
@@ -204,9 +208,9 @@ def mg_ndofs(dim, element, n_cells):
     return int(lib().mg_ndofs(dim, element, n_cells))
 
 
-def _problem(dim, element, n_cells, n_levels, k_cell=None):
+def _problem(dim, element, n_cells, n_levels, k_cell=None, mass=0.0):
     keep = None
-    p = mg_problem(dim, element, n_cells, n_levels, None)
+    p = mg_problem(dim, element, n_cells, n_levels, None, float(mass))
     if k_cell is not None:
         keep = np.ascontiguousarray(k_cell, dtype=np.float64)
         p.k_cell = _as_dp(keep)
@@ -233,10 +237,10 @@ def mg_load_vector(dim, element, n_cells, modes=None, f_const=1.0, n_levels=1):
     return b
 
 
-def mg_assemble_operator(dim, element, n_cells, n_levels, level, which=0, k_cell=None):
-    """Host-assembled level operator (no GPU) as (rowptr, col, val): which 0 = A, 1 = P, 2 = R."""
+def mg_assemble_operator(dim, element, n_cells, n_levels, level, which=0, k_cell=None, mass=0.0):
+    """Host-assembled level operator (no GPU) as (rowptr, col, val): which 0 = A (+ mass M), 1 = P, 2 = R."""
     L = lib()
-    p, _k = _problem(dim, element, n_cells, n_levels, k_cell)
+    p, _k = _problem(dim, element, n_cells, n_levels, k_cell, mass)
     nrows, nnz = ctypes.c_int64(0), ctypes.c_int64(0)
     _check(L.mg_assemble_operator(ctypes.byref(p), level, which, ctypes.byref(nrows), ctypes.byref(nnz),
                                   None, None, None))
@@ -258,9 +262,10 @@ def mg_load_vector_separable(dim, n_cells, modes=None, f_const=1.0):
     return b
 
 
-def mg_setup(dim, element, n_cells, n_levels, options=None, k_cell=None, device=None):
-    """Build a hierarchy; returns the opaque handle (int). device: TorchDevice or None (cudaMalloc)."""
-    p, _k = _problem(dim, element, n_cells, n_levels, k_cell)
+def mg_setup(dim, element, n_cells, n_levels, options=None, k_cell=None, device=None, mass=0.0):
+    """Build a hierarchy; returns the opaque handle (int). device: TorchDevice or None (cudaMalloc).
+    mass: sigma of the operator A + sigma M (Crank-Nicolson, sigma = 2/dt)."""
+    p, _k = _problem(dim, element, n_cells, n_levels, k_cell, mass)
     o = options if options is not None else mg_options_default()
     h = _vp()
     dptr = ctypes.byref(device.struct) if device is not None else None
@@ -324,6 +329,34 @@ def mg_pcg_host(h, b_host, x_host, rel_tol, max_iters=100):
     return st, it.value, hist[:it.value + 1].copy()
 
 
+MG_METHOD_DC, MG_METHOD_PCG = 0, 1
+
+
+def mg_heat(h, bF_dev, g, u_dev, rel_tol, method=MG_METHOD_DC):
+    """Crank-Nicolson steps k = 0..len(g)-2 on a hierarchy set up with mass = 2/dt.
+    bF_dev, u_dev: CUDA float64 tensors (u updated in place). Returns (status, iters per step)."""
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    n_steps = len(g) - 1
+    its = np.zeros(max(n_steps, 1), dtype=np.intc)
+    st = lib().mg_heat(h, ctypes.c_void_p(bF_dev.data_ptr()), _as_dp(g), n_steps, ctypes.c_void_p(u_dev.data_ptr()),
+                       float(rel_tol), int(method), its.ctypes.data_as(_P(ctypes.c_int)))
+    _check(st, (MG_OK, MG_ENOCONV))
+    return st, its[:n_steps].copy()
+
+
+def mg_heat_host(h, bF_host, g, u_host, rel_tol, method=MG_METHOD_DC):
+    """mg_heat with float64 numpy arrays (u_host updated in place)."""
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    assert bF_host.dtype == np.float64 and u_host.dtype == np.float64 and u_host.flags.c_contiguous
+    bF_host = np.ascontiguousarray(bF_host)
+    n_steps = len(g) - 1
+    its = np.zeros(max(n_steps, 1), dtype=np.intc)
+    st = lib().mg_heat_host(h, _as_dp(bF_host), _as_dp(g), n_steps, _as_dp(u_host), float(rel_tol), int(method),
+                            its.ctypes.data_as(_P(ctypes.c_int)))
+    _check(st, (MG_OK, MG_ENOCONV))
+    return st, its[:n_steps].copy()
+
+
 def mg_cycle(h, b_dev, x_dev, n_cycles):
     rel = ctypes.c_double(0.0)
     _check(lib().mg_cycle(h, ctypes.c_void_p(b_dev.data_ptr()), ctypes.c_void_p(x_dev.data_ptr()),
@@ -375,12 +408,12 @@ def mg_profile_read(h, kclass, level):
 class Hierarchy:
     """Owns an mg_hierarchy built on torch device memory."""
 
-    def __init__(self, dim, element, n_cells, n_levels, k_cell=None, device=None, **opts):
+    def __init__(self, dim, element, n_cells, n_levels, k_cell=None, device=None, mass=0.0, **opts):
         self.options = mg_options_default(**opts)
         self.device = device if device is not None else TorchDevice()
         self.dim, self.element, self.n_cells, self.n_levels = dim, element, n_cells, n_levels
         self.n = mg_ndofs(dim, element, n_cells)
-        self.h = mg_setup(dim, element, n_cells, n_levels, self.options, k_cell, self.device)
+        self.h = mg_setup(dim, element, n_cells, n_levels, self.options, k_cell, self.device, mass)
 
     def close(self):
         if getattr(self, "h", None):
@@ -401,6 +434,12 @@ class Hierarchy:
 
     def solve_host(self, b_host, x_host, rel_tol):
         return mg_solve_host(self.h, b_host, x_host, rel_tol, self.options.max_iters)
+
+    def heat(self, bF_dev, g, u_dev, rel_tol, method=MG_METHOD_DC):
+        return mg_heat(self.h, bF_dev, g, u_dev, rel_tol, method)
+
+    def heat_host(self, bF_host, g, u_host, rel_tol, method=MG_METHOD_DC):
+        return mg_heat_host(self.h, bF_host, g, u_host, rel_tol, method)
 
     def pcg(self, b_dev, x_dev, rel_tol):
         return mg_pcg(self.h, b_dev, x_dev, rel_tol, self.options.max_iters)
@@ -499,7 +538,7 @@ class Server:
 
     def tune(self, shapes, repeats=2, rel_tol=1e-8):
         """shapes: list of (dim, n_cells, n_levels). Returns the chosen (rows_per_thread, blocks_per_sm)."""
-        arr = (mg_problem * len(shapes))(*[mg_problem(d, MG_Q1, n, l, None) for d, n, l in shapes])
+        arr = (mg_problem * len(shapes))(*[mg_problem(d, MG_Q1, n, l, None, 0.0) for d, n, l in shapes])
         r, b = ctypes.c_int(0), ctypes.c_int(0)
         _check(lib().mg_serve_tune(self.h, arr, len(shapes), int(repeats), float(rel_tol), ctypes.byref(r),
                                    ctypes.byref(b)))
