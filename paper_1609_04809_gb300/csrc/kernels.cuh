@@ -438,8 +438,17 @@ __device__ __forceinline__ bool finish_norm(double part, double *partial, unsign
     __syncthreads();
     if (!last) return false;
     __threadfence();
+    // the block partials, read from L2 eight at a time per thread (independent loads,
+    // then a fixed-order sum) so that the last block does not wait for one round trip
+    // per partial
+    const int G = (int)gridDim.x, B = (int)blockDim.x;
     double acc = 0.0;
-    for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x) acc += ((volatile double *)partial)[k];
+    for (int k0 = threadIdx.x; k0 < G; k0 += 8 * B) {
+        double v[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++) v[u] = k0 + u * B < G ? __ldcg(partial + k0 + u * B) : 0.0;
+        acc += ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
+    }
     double tot = block_sum(acc, sh);
     if (threadIdx.x == 0) {
         *out = tot;
