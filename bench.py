@@ -162,6 +162,7 @@ def replica_throughput(ms_local, n_dofs, steps, world, dist=None, device="cpu"):
 
 
 SMOOTHERS = {"jacobi": 0, "chebyshev": 1, "gauss-seidel": 2}
+STORAGES = {"auto": 0, "csr": 1, "ell": 2, "dia": 3}
 SWEEP_TEXT = {0: "fused residual + damped Jacobi update", 1: "fused residual + Chebyshev update",
               2: "one colour of a multicolour Gauss-Seidel sweep, in place"}
 
@@ -464,7 +465,8 @@ def run_ours(args):
     H = mg.Hierarchy(c["dim"], c["element"], c["n_cells"], c["n_levels"], smoother=c["smoother"],
                      omega=c["omega"], cheb_degree=c["cheb_degree"], nu_pre=c["nu_pre"], nu_post=c["nu_post"],
                      precision=mg.MG_MIXED if args.precision == "mixed" else mg.MG_FP64,
-                     use_pdl=0 if args.no_pdl else 1, coarse_tail=0 if args.no_tail else 2)
+                     use_pdl=0 if args.no_pdl else 1, coarse_tail=0 if args.no_tail else 2,
+                     storage=STORAGES[args.storage])
     info = H.info()
     Lf = c["n_levels"] - 1
     bd = torch.from_numpy(b_host).cuda()
@@ -618,6 +620,9 @@ def main():
     ap.add_argument("--serve-slots", type=int, default=256)
     ap.add_argument("--no-pdl", action="store_true", help="launch without programmatic dependent launch")
     ap.add_argument("--no-tail", action="store_true", help="run the small levels as separate kernels")
+    ap.add_argument("--storage", default="auto", choices=sorted(STORAGES),
+                    help="level-matrix storage; auto times the candidates at setup (pin it under a profiler, "
+                         "whose serialisation would skew that timing)")
     ap.add_argument("--smoother", default="workload", choices=["workload"] + sorted(SMOOTHERS),
                     help="replace the workload's smoother (the headline uses the workload's own)")
     ap.add_argument("--all-configs", action="store_true",

@@ -422,6 +422,12 @@ __device__ __forceinline__ double block_sum(double v, double *sh)
     return s;  // valid in thread 0
 }
 
+// Grid of the kernels that end in a reduction: a fixed number of blocks (8 per SM of
+// GB300's 152) stepping through the rows, so that the per-block ticket of finish_norm
+// is taken 1216 times instead of once per 256 rows; a constant keeps the summation
+// order, hence the bits, independent of the device.
+constexpr int kReduceBlocks = 1216;
+
 // Sum of `part` over the grid in a fixed order: block sums to partial[], the last block
 // to finish (ticket) adds them up. Returns true in the thread that wrote *out.
 __device__ __forceinline__ bool finish_norm(double part, double *partial, unsigned *ticket, double *out)
@@ -464,9 +470,8 @@ __global__ void __launch_bounds__(256) k_outer_resid(MatView<double> A, int n, c
                                                      double *partial, unsigned *ticket, double *norm2)
 {
     pdl_enter();
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
     double sq = 0.0;
-    if (i < n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         double s = 0.0;
         if (FMT == 3) {  // DIA
             double a[K], xv[K];
@@ -486,7 +491,7 @@ __global__ void __launch_bounds__(256) k_outer_resid(MatView<double> A, int n, c
         }
         double ri = __dsub_rn(b[i], s);
         r[i] = (Tin)ri;
-        sq = ri * ri;
+        sq = __fma_rn(ri, ri, sq);
     }
     finish_norm(sq, partial, ticket, norm2);
 }

@@ -53,16 +53,15 @@ __global__ void __launch_bounds__(256) k_pcg_init(MatView<double> A, int n, cons
                                                   double *partial, unsigned *ticket, double *norm2)
 {
     pdl_enter();
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
     double sq = 0.0;
-    if (i < n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         double ri = __dsub_rn(b[i], pcg_row<FMT, K>(A, i, x));
         r64[i] = ri;
         rin[i] = (Tin)ri;
         p[i] = 0.0;
-        sq = __dmul_rn(ri, ri);
+        sq = __fma_rn(ri, ri, sq);
     }
-    if (i == 0) scal[PCG_RZ_OLD] = 0.0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) scal[PCG_RZ_OLD] = 0.0;
     finish_norm(sq, partial, ticket, norm2);
 }
 
@@ -71,8 +70,9 @@ __global__ void __launch_bounds__(256) k_pcg_rz(const double *__restrict__ r, co
                                                 double *partial, unsigned *ticket, double *scal)
 {
     pdl_enter();
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    double part = i < n ? __dmul_rn(r[i], (double)z[i]) : 0.0;
+    double part = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        part = __fma_rn(r[i], (double)z[i], part);
     if (finish_norm(part, partial, ticket, scal + PCG_RZ)) {
         double ro = scal[PCG_RZ_OLD];
         scal[PCG_BETA] = ro == 0.0 ? 0.0 : __ddiv_rn(scal[PCG_RZ], ro);
@@ -95,12 +95,11 @@ __global__ void __launch_bounds__(256) k_pcg_apply(MatView<double> A, int n, con
                                                    double *scal)
 {
     pdl_enter();
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
     double part = 0.0;
-    if (i < n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         double s = pcg_row<FMT, K>(A, i, p);
         q[i] = s;
-        part = __dmul_rn(p[i], s);
+        part = __fma_rn(p[i], s, part);
     }
     if (finish_norm(part, partial, ticket, scal + PCG_PQ)) scal[PCG_ALPHA] = __ddiv_rn(scal[PCG_RZ], scal[PCG_PQ]);
 }
@@ -112,15 +111,14 @@ __global__ void __launch_bounds__(256) k_pcg_update(double *__restrict__ x, doub
                                                     double *partial, unsigned *ticket, double *norm2)
 {
     pdl_enter();
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
     double alpha = scal[PCG_ALPHA];
     double sq = 0.0;
-    if (i < n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         x[i] = __dadd_rn(x[i], __dmul_rn(alpha, p[i]));
         double ri = __dsub_rn(r[i], __dmul_rn(alpha, q[i]));
         r[i] = ri;
         rin[i] = (Tin)ri;
-        sq = __dmul_rn(ri, ri);
+        sq = __fma_rn(ri, ri, sq);
     }
     if (finish_norm(sq, partial, ticket, norm2)) scal[PCG_RZ_OLD] = scal[PCG_RZ];
 }

@@ -99,9 +99,8 @@ __global__ void k_lu_factor(double *a, int n, int *piv, int *info)
 __global__ void __launch_bounds__(256) k_norm2(const double *__restrict__ v, int n, double *partial, unsigned *ticket,
                                                double *norm2)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
     double sq = 0.0;
-    if (i < n) sq = v[i] * v[i];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) sq = __fma_rn(v[i], v[i], sq);
     finish_norm(sq, partial, ticket, norm2);
 }
 }  // namespace mgk
@@ -115,6 +114,8 @@ using mgi::LevelD;
 
 static inline int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 static inline unsigned grid_for(int64_t n) { return (unsigned)((n + 255) / 256); }
+// grid of a kernel that ends in a block-partial reduction (finish_norm)
+static inline unsigned reduce_grid(int64_t n) { return std::min<unsigned>(std::max<unsigned>(grid_for(n), 1u), kReduceBlocks); }
 
 void mgi::Slab::reserve(size_t bytes)
 {
@@ -611,7 +612,7 @@ static void enqueue_outer(mg_hierarchy *h, cudaStream_t s)
     double entries = A.fmt == MG_STORAGE_CSR ? (double)A.nnz : (double)A.K * n;
     LaunchScope ls(h, s, MG_K_OUTER, h->Lf, bytes, 2.0 * entries + 3.0 * n);
     MatView<double> v = view<double>(A);
-    dim3 g(grid_for(n)), blk(256);
+    dim3 g(reduce_grid(n)), blk(256);
     T *r = (T *)F.b;
     bool pdl = h->opt.use_pdl != 0;
     const double *x = h->x64, *b = h->b64;
@@ -687,7 +688,7 @@ static void enqueue_pcg_init(mg_hierarchy *h, cudaStream_t s)
                    2.0 * entries + 3.0 * n);
     MatView<double> v = view<double>(A);
     bool pdl = h->opt.use_pdl != 0;
-    dim3 g(grid_for(n)), blk(256);
+    dim3 g(reduce_grid(n)), blk(256);
     launch_fp64_rows(h, A, [&](auto fmt, auto k) {
         klaunch(pdl, k_pcg_init<T, decltype(fmt)::value, decltype(k)::value>, g, blk, 0, s, v, n,
                 (const double *)h->x64, (const double *)h->b64, h->pcg_r, (T *)F.b, h->pcg_p, h->pcg_scal,
@@ -706,9 +707,10 @@ static void enqueue_pcg_iter(mg_hierarchy *h, cudaStream_t s)
     dim3 g(grid_for(n)), blk(256);
     int c = enqueue_vcycle<T>(h, s);
     const T *z = (const T *)F.x[c];
+    dim3 gr(reduce_grid(n));  // the kernels that end in an inner product
     {
         LaunchScope ls(h, s, MG_K_KRYLOV, h->Lf, 8.0 * n + (double)n * sv, 2.0 * n);
-        klaunch(pdl, k_pcg_rz<T>, g, blk, 0, s, (const double *)h->pcg_r, z, n, h->partial, h->ticket,
+        klaunch(pdl, k_pcg_rz<T>, gr, blk, 0, s, (const double *)h->pcg_r, z, n, h->partial, h->ticket,
                 h->pcg_scal);
     }
     {
@@ -720,13 +722,13 @@ static void enqueue_pcg_iter(mg_hierarchy *h, cudaStream_t s)
         LaunchScope ls(h, s, MG_K_KRYLOV, h->Lf, mat_bytes(A, 8) + 16.0 * n, 2.0 * entries + 2.0 * n);
         MatView<double> v = view<double>(A);
         launch_fp64_rows(h, A, [&](auto fmt, auto k) {
-            klaunch(pdl, k_pcg_apply<decltype(fmt)::value, decltype(k)::value>, g, blk, 0, s, v, n,
+            klaunch(pdl, k_pcg_apply<decltype(fmt)::value, decltype(k)::value>, gr, blk, 0, s, v, n,
                     (const double *)h->pcg_p, h->pcg_q, h->partial, h->ticket, h->pcg_scal);
         });
     }
     {
         LaunchScope ls(h, s, MG_K_KRYLOV, h->Lf, 48.0 * n + (double)n * sv, 6.0 * n);
-        klaunch(pdl, k_pcg_update<T>, g, blk, 0, s, h->x64, h->pcg_r, (T *)F.b, (const double *)h->pcg_p,
+        klaunch(pdl, k_pcg_update<T>, gr, blk, 0, s, h->x64, h->pcg_r, (T *)F.b, (const double *)h->pcg_p,
                 (const double *)h->pcg_q, n, h->pcg_scal, h->partial, h->ticket, h->norm2);
     }
 }
@@ -875,7 +877,7 @@ static double read_norm2(mg_hierarchy *h)
 static double norm_b(mg_hierarchy *h)
 {
     int n = (int)h->lev[h->Lf].n;
-    k_norm2<<<grid_for(n), 256, 0, h->s>>>(h->b64, n, h->partial, h->ticket, h->norm2);
+    k_norm2<<<reduce_grid(n), 256, 0, h->s>>>(h->b64, n, h->partial, h->ticket, h->norm2);
     CKL();
     return std::sqrt(read_norm2(h));
 }
