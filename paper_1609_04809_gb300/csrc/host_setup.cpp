@@ -763,6 +763,29 @@ void colour_order(int dim, int elem, int N, std::vector<int32_t> &perm, std::vec
     for (int64_t i = 0; i < n; i++) perm[next[col[i]]++] = (int32_t)i;
 }
 
+std::vector<std::pair<int64_t, int64_t>> colour_launch_groups(const Csr &A, int dim, int elem, int N,
+                                                              const std::vector<int64_t> &coff)
+{
+    int nc = (int)coff.size() - 1;
+    std::vector<bool> coupled((size_t)nc * nc, false);
+    for (int64_t i = 0; i < A.nrows; i++) {
+        int ci = dof_colour(dim, elem, N, i);
+        for (int64_t k = A.rowptr[i]; k < A.rowptr[i + 1]; k++)
+            if (A.val[k] != 0.0) coupled[(size_t)ci * nc + dof_colour(dim, elem, N, A.col[k])] = true;
+    }
+    std::vector<std::pair<int64_t, int64_t>> g;
+    for (int c = 0; c < nc;) {
+        if (c + 1 < nc && !coupled[(size_t)c * nc + c + 1] && !coupled[(size_t)(c + 1) * nc + c]) {
+            g.push_back({coff[c], coff[c + 2]});
+            c += 2;
+        } else {
+            g.push_back({coff[c], coff[c + 1]});
+            c += 1;
+        }
+    }
+    return g;
+}
+
 bool colouring_valid(const Csr &A, int dim, int elem, int N)
 {
     for (int64_t i = 0; i < A.nrows; i++) {

@@ -6,6 +6,7 @@
 #pragma once
 
 #include <cstdint>
+#include <utility>
 #include <vector>
 
 #include "mg.h"
@@ -78,6 +79,11 @@ int dof_colour(int dim, int elem, int N, int64_t i);
 void colour_order(int dim, int elem, int N, std::vector<int32_t> &perm, std::vector<int64_t> &coff);
 // true iff no stored entry (zero or not) couples two distinct DOFs of one colour
 bool colouring_valid(const Csr &A, int dim, int elem, int N);
+// Launch groups of a sweep: consecutive colours 2g, 2g+1 share a launch when A holds no
+// nonzero between them (then updating them together gives the sequential sweep's bits;
+// 3D Q1 couples no face neighbours). Returns the row ranges [start, end) in colour order.
+std::vector<std::pair<int64_t, int64_t>> colour_launch_groups(const Csr &A, int dim, int elem, int N,
+                                                              const std::vector<int64_t> &coff);
 
 // Power-method estimate of lambda_max(D^-1 A) (the start vector is 1 + 0.2 (u - 1/2),
 // u from SplitMix64(seed), normalised).

@@ -62,6 +62,7 @@ struct LevelD {
     DevMat G;
     int32_t *perm = nullptr;
     std::vector<int64_t> coff;
+    std::vector<std::pair<int64_t, int64_t>> gs_groups;  // row ranges of one sweep's launches
     double omega = 0.8, lambda = 0.0, cheb_c0 = 0.0;
     std::vector<double> cheb_c1, cheb_c2;
 };

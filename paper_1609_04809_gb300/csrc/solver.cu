@@ -350,21 +350,22 @@ static void sweep(mg_hierarchy *h, int l, int mode, const T *x, const T *b, T *o
 }
 
 // one smoother application on level l; c: buffer holding x (-1: x = 0); returns new buffer
-// one multicolour Gauss-Seidel sweep of level l on x in place: one launch per colour,
-// colours ascending (descending in post-smoothing)
+// one multicolour Gauss-Seidel sweep of level l on x in place: one launch per colour
+// (or per pair of mutually uncoupled colours), colours ascending (descending in
+// post-smoothing)
 template <typename T>
 static void gs_sweep(mg_hierarchy *h, int l, T *x, bool post, cudaStream_t s)
 {
     LevelD &L = h->lev[l];
     const DevMat &G = L.G;
     MatView<T> v = view<T>(G);
-    int nc = (int)L.coff.size() - 1, sv = sizeof(T);
+    int ng = (int)L.gs_groups.size(), sv = sizeof(T);
     bool pdl = h->opt.use_pdl != 0;
     const T *b = (const T *)L.b;
-    for (int cc = 0; cc < nc; cc++) {
-        int c = post ? nc - 1 - cc : cc;
-        int64_t r0 = L.coff[c];
-        int nr = (int)(L.coff[c + 1] - r0);
+    for (int gg = 0; gg < ng; gg++) {
+        const auto &grp = L.gs_groups[post ? ng - 1 - gg : gg];
+        int64_t r0 = grp.first;
+        int nr = (int)(grp.second - r0);
         if (nr == 0) continue;
         // the colour's slice of the matrix (values, columns), perm, D^-1, b, and x read
         // and written at its rows; gathers of x at other rows count as cache hits
@@ -1343,6 +1344,7 @@ void mgi::build_hierarchy(mg_hierarchy *h, const mg_problem *p, const mg_options
             if (!mgh::colouring_valid(A[l], dim, elem, h->lev[l].N))
                 throw Error(MG_EINVAL, "level " + std::to_string(l) + " couples two DOFs of one colour");
             mgh::colour_order(dim, elem, h->lev[l].N, gs_perm[l], h->lev[l].coff);
+            h->lev[l].gs_groups = mgh::colour_launch_groups(A[l], dim, elem, h->lev[l].N, h->lev[l].coff);
         }
     for (int pass = 0; pass < 2; pass++) {
         bool take = pass == 1;
