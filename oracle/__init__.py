@@ -36,7 +36,7 @@ _SRC = os.path.join(_HERE, "mg_oracle.c")
 _LIB_DIR = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_LIB_DIR, "liboracle.so")
 
-Q1, RQ1 = 0, 1
+Q1, RQ1, P1, P2 = 0, 1, 2, 3
 JACOBI, CHEBYSHEV, GAUSS_SEIDEL = 0, 1, 2
 
 _lib = None
@@ -89,6 +89,7 @@ def lib():
         L.orc_setup.argtypes = [ctypes.c_int] * 4 + [dp, dp, dp, ctypes.c_int, ctypes.c_uint64, dp, ctypes.c_double]
         L.orc_assemble_mass.argtypes = [ctypes.c_int] * 3 + [dp, P(_CSR)]
         L.orc_heat_rhs.argtypes = [P(_CSR), dp, dp, ctypes.c_double, dp]
+        L.orc_load_vector_tet.argtypes = [ctypes.c_int] * 3 + [dp, ip, ctypes.c_double, dp, dp]
         L.orc_free.argtypes = [vp]
         L.orc_solve.restype = ctypes.c_int
         L.orc_solve.argtypes = [vp, P(_Opts), dp, dp, ctypes.c_double, dp, ip]
@@ -157,9 +158,12 @@ def ndofs(dim, elem, N):
 
 
 def kref(dim, elem):
-    """Unit-cell element stiffness as nearest doubles (row-major)."""
+    """Unit-cell element stiffness as nearest doubles (row-major); P1/P2: one Kuhn tetrahedron."""
     if elem == Q1:
         return np.array(elements.q1_stiffness(dim), dtype=np.float64)
+    if elem in (P1, P2):
+        assert dim == 3
+        return np.array(elements.tet_stiffness(1 if elem == P1 else 2), dtype=np.float64)
     assert dim == 3
     return np.array(elements.rq1_stiffness(), dtype=np.float64)
 
@@ -187,10 +191,21 @@ def assemble(dim, elem, N, k_cell=None):
 
 
 def mref(dim, elem):
-    """Unit-cell element mass matrix as nearest doubles (Q1 only)."""
+    """Unit-cell element mass matrix as nearest doubles (Q1, or a Kuhn tetrahedron for P1/P2)."""
+    if elem in (P1, P2):
+        return np.array(elements.tet_mass(1 if elem == P1 else 2), dtype=np.float64)
     if elem != Q1:
-        raise ValueError("the mass matrix is built for Q1")
+        raise ValueError("the mass matrix is built for Q1, P1 and P2")
     return np.array(elements.q1_mass(dim), dtype=np.float64)
+
+
+def node_coords(elem, N):
+    """Coordinates (n x 3) of the DOFs of a tetrahedral element (P1: vertices; P2: points of
+    the grid of 2N cells), lexicographic with x fastest."""
+    M = N if elem == P1 else 2 * N
+    w = np.arange(1, M) / M
+    z, y, x = np.meshgrid(w, w, w, indexing="ij")
+    return np.stack([x.ravel(), y.ravel(), z.ravel()], axis=1)
 
 
 def assemble_mass(dim, elem, N):
@@ -269,6 +284,9 @@ def load_vector(dim, elem, N, modes=None, fconst=1.0):
     L = lib()
     nm, amp, kf = _modes(modes)
     b = np.zeros(ndofs(dim, elem, N))
+    if elem in (P1, P2):  # b = M f_I (see mg_oracle.c)
+        L.orc_load_vector_tet(elem, N, nm, _dp(amp), _ip(kf), float(fconst), _dp(mref(dim, elem)), _dp(b))
+        return b
     L.orc_load_vector(dim, elem, N, nm, _dp(amp), _ip(kf), float(fconst), _dp(_rq1_basis()), _dp(b))
     return b
 

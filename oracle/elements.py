@@ -230,6 +230,105 @@ def rq1_fine_face_weights_exact():
 
 
 # ---------------------------------------------------------------------------------
+# P1 / P2 on tetrahedra: the Kuhn (Freudenthal) triangulation of the cube grid
+# ---------------------------------------------------------------------------------
+# A cell is split into 6 tetrahedra, one per permutation pi of the axes: the path
+# 0 -> e_pi0 -> e_pi0 + e_pi1 -> (1,1,1) through the unit cell. Its barycentric
+# coordinates are lambda_0 = 1 - s_pi0, lambda_1 = s_pi0 - s_pi1, lambda_2 = s_pi1 - s_pi2,
+# lambda_3 = s_pi2 (s the local coordinate), with constant gradients g_0 = -e_pi0,
+# g_1 = e_pi0 - e_pi1, g_2 = e_pi1 - e_pi2, g_3 = e_pi2. Halving the grid splits each of
+# these tetrahedra into 8 of the finer grid's, so the P1 and P2 spaces are nested.
+
+KUHN_PERMS = [(0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)]
+P2_EDGES = [(0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3)]  # local nodes 4..9
+
+
+def kuhn_grads(perm):
+    """Gradients of the barycentric coordinates of the Kuhn tetrahedron `perm` (unit cell)."""
+    e = [[1 if d == a else 0 for d in range(3)] for a in range(3)]
+    g0 = [-v for v in e[perm[0]]]
+    g1 = [e[perm[0]][d] - e[perm[1]][d] for d in range(3)]
+    g2 = [e[perm[1]][d] - e[perm[2]][d] for d in range(3)]
+    g3 = list(e[perm[2]])
+    return [g0, g1, g2, g3]
+
+
+def _bmul(p, q):
+    """Product of polynomials in the barycentric coordinates {(a0,a1,a2,a3): coeff}."""
+    r = {}
+    for k1, v1 in p.items():
+        for k2, v2 in q.items():
+            k = tuple(a + b for a, b in zip(k1, k2))
+            r[k] = r.get(k, Fr(0)) + v1 * v2
+    return r
+
+
+def _bint(p):
+    """Integral over the unit cell's Kuhn tetrahedron (volume 1/6):
+    int lambda^alpha = alpha! 3! |T| / (|alpha| + 3)!."""
+    from math import factorial
+    tot = Fr(0)
+    for k, v in p.items():
+        num = 1
+        for a in k:
+            num *= factorial(a)
+        tot += v * Fr(num * factorial(3), factorial(sum(k) + 3)) * Fr(1, 6)
+    return tot
+
+
+def _lam(a, c=Fr(1)):
+    k = [0, 0, 0, 0]
+    k[a] = 1
+    return {tuple(k): c}
+
+
+def tet_basis(order):
+    """P1 or P2 basis on a tetrahedron as polynomials in lambda, and their gradients as
+    lists of (polynomial coefficient of g_a) for a = 0..3."""
+    one = {(0, 0, 0, 0): Fr(1)}
+    if order == 1:
+        basis = [_lam(a) for a in range(4)]
+        grads = [[one if b == a else {} for b in range(4)] for a in range(4)]
+        return basis, grads
+    basis, grads = [], []
+    for a in range(4):  # vertex: lambda_a (2 lambda_a - 1), gradient (4 lambda_a - 1) g_a
+        basis.append(_bmul(_lam(a), {**_lam(a, Fr(2)), (0, 0, 0, 0): Fr(-1)}))
+        grads.append([{**_lam(a, Fr(4)), (0, 0, 0, 0): Fr(-1)} if b == a else {} for b in range(4)])
+    for a, b in P2_EDGES:  # edge: 4 lambda_a lambda_b, gradient 4 (lambda_b g_a + lambda_a g_b)
+        basis.append(_bmul(_lam(a, Fr(4)), _lam(b)))
+        grads.append([_lam(b, Fr(4)) if c == a else (_lam(a, Fr(4)) if c == b else {}) for c in range(4)])
+    return basis, grads
+
+
+def tet_stiffness_exact(order, perm=(0, 1, 2)):
+    """K[i][j] = int_T grad N_i . grad N_j on the unit cell's Kuhn tetrahedron `perm`."""
+    basis, grads = tet_basis(order)
+    g = kuhn_grads(perm)
+    G = [[sum(g[a][d] * g[b][d] for d in range(3)) for b in range(4)] for a in range(4)]
+    n = len(basis)
+    K = [[Fr(0)] * n for _ in range(n)]
+    for i in range(n):
+        for j in range(n):
+            acc = {}
+            for a in range(4):
+                for b in range(4):
+                    if G[a][b] == 0 or not grads[i][a] or not grads[j][b]:
+                        continue
+                    t = _bmul(grads[i][a], grads[j][b])
+                    for k, v in t.items():
+                        acc[k] = acc.get(k, Fr(0)) + v * G[a][b]
+            K[i][j] = _bint(acc)
+    return K
+
+
+def tet_mass_exact(order):
+    """M[i][j] = int_T N_i N_j on a Kuhn tetrahedron of the unit cell (volume 1/6)."""
+    basis, _ = tet_basis(order)
+    n = len(basis)
+    return [[_bint(_bmul(basis[i], basis[j])) for j in range(n)] for i in range(n)]
+
+
+# ---------------------------------------------------------------------------------
 # Double-precision tables handed to the C oracle (nearest double of each rational)
 # ---------------------------------------------------------------------------------
 
@@ -242,6 +341,15 @@ def q1_stiffness(dim):
 def q1_mass(dim):
     """Row-major flat list of the unit-cell Q1 mass matrix, nearest doubles."""
     return [float(v) for row in q1_mass_exact(dim) for v in row]
+
+
+def tet_stiffness(order):
+    """Row-major flat P1 (4x4) or P2 (10x10) Kuhn-tetrahedron stiffness, nearest doubles."""
+    return [float(v) for row in tet_stiffness_exact(order) for v in row]
+
+
+def tet_mass(order):
+    return [float(v) for row in tet_mass_exact(order) for v in row]
 
 
 def rq1_stiffness():

@@ -38,6 +38,8 @@
 
 #define ORC_Q1 0
 #define ORC_RQ1 1
+#define ORC_P1 2 /* conforming P1 on the Kuhn tetrahedra of the cube grid (3D) */
+#define ORC_P2 3 /* conforming P2 on the same tetrahedra (3D) */
 #define ORC_PI 3.14159265358979323846 /* nearest double to pi */
 
 typedef struct {
@@ -67,12 +69,17 @@ void orc_csr_free(orc_csr *m)
 
 int orc_colour(int dim, int elem, int N, int64_t i);
 int orc_n_colours(int dim, int elem);
+void orc_tet_node_coords(int elem, int N, int64_t i, double *x);
 
 int64_t orc_ndofs(int dim, int elem, int N)
 {
     int64_t n1 = N - 1;
     if (elem == ORC_Q1)
         return dim == 2 ? n1 * n1 : n1 * n1 * n1;
+    if (elem == ORC_P1)
+        return n1 * n1 * n1;
+    if (elem == ORC_P2)
+        return (int64_t)(2 * N - 1) * (2 * N - 1) * (2 * N - 1);
     return 3 * n1 * (int64_t)N * N;
 }
 
@@ -221,9 +228,13 @@ int orc_assemble_mass(int dim, int elem, int N, const double *mref, orc_csr *M)
 
 /* element loop shared by the stiffness and the mass matrix: element matrix
  * (k_e * hfac) * kref[a][b] */
+static int assemble_tet(int elem, int N, const double *kref, const double *k_cell, double hfac, orc_csr *A);
+
 static int assemble_ref(int dim, int elem, int N, const double *kref, const double *k_cell, double hfac,
                         orc_csr *A)
 {
+    if (elem == ORC_P1 || elem == ORC_P2)
+        return assemble_tet(elem, N, kref, k_cell, hfac, A);
     int64_t n = orc_ndofs(dim, elem, N);
     int64_t NN = N, ncells = dim == 2 ? NN * NN : NN * NN * NN;
     memset(A, 0, sizeof(*A));
@@ -396,8 +407,12 @@ static int prolong_row(int dim, int elem, int Nc, int64_t i, const double *rq1_w
 }
 
 /* rq1_w: W[axis][v][s1][s2][a] mean of coarse basis a over the fine face (elements.py) */
+static int prolong_tet(int elem, int Nc, orc_csr *P);
+
 int orc_prolongation(int dim, int elem, int Nc, const double *rq1_w, orc_csr *P)
 {
+    if (elem == ORC_P1 || elem == ORC_P2)
+        return prolong_tet(elem, Nc, P);
     int Nf = 2 * Nc;
     int64_t nf = orc_ndofs(dim, elem, Nf), nc = orc_ndofs(dim, elem, Nc);
     orc_entry ent[16];
@@ -793,6 +808,281 @@ void orc_lu_solve(const double *lu, int n, const int *piv, const double *b, doub
     }
 }
 
+
+/* ------------------------------------------------------------------------------ */
+/* P1 / P2 on tetrahedra (3D): the Kuhn (Freudenthal) triangulation of the grid.     */
+/* Cell (cx,cy,cz) holds one tetrahedron per permutation pi of the axes, in the      */
+/* order (012) (021) (102) (120) (201) (210): vertices v0 = (cx,cy,cz), v1 = v0 +    */
+/* e_pi0, v2 = v1 + e_pi1, v3 = v0 + (1,1,1). Refinement by halving splits each into */
+/* 8 tetrahedra of the finer grid (Freudenthal), so the spaces are nested.           */
+/*   P1 DOFs: interior vertices, numbered like Q1.                                   */
+/*   P2 DOFs: vertices and edge midpoints = the interior points of the grid of 2N    */
+/*   cells per axis, numbered like Q1 there; local nodes 0..3 are the vertices,      */
+/*   4..9 the midpoints of edges (01) (02) (03) (12) (13) (23).                      */
+/* The element matrix of a tetrahedron of a cell of side h is (k_e * hfac) * kref    */
+/* (the same table for all six: they are congruent with the same local order).       */
+/* ------------------------------------------------------------------------------ */
+static const int KUHN[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+static const int TET_EDGE[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
+
+/* global DOFs of tetrahedron t of cell (cx,cy,cz) (-1: Dirichlet); returns the count */
+static int tet_dofs(int elem, int N, int cx, int cy, int cz, int t, int64_t *g)
+{
+    int v[4][3];
+    v[0][0] = cx;
+    v[0][1] = cy;
+    v[0][2] = cz;
+    for (int a = 1; a < 4; a++) {
+        for (int d = 0; d < 3; d++)
+            v[a][d] = v[a - 1][d];
+        if (a < 3)
+            v[a][KUHN[t][a - 1]] += 1;
+        else
+            v[a][KUHN[t][2]] += 1;
+    }
+    if (elem == ORC_P1) {
+        for (int a = 0; a < 4; a++)
+            g[a] = q1_vertex(3, N, v[a][0], v[a][1], v[a][2]);
+        return 4;
+    }
+    for (int a = 0; a < 4; a++)
+        g[a] = q1_vertex(3, 2 * N, 2 * v[a][0], 2 * v[a][1], 2 * v[a][2]);
+    for (int e = 0; e < 6; e++) {
+        int a = TET_EDGE[e][0], b = TET_EDGE[e][1];
+        g[4 + e] = q1_vertex(3, 2 * N, v[a][0] + v[b][0], v[a][1] + v[b][1], v[a][2] + v[b][2]);
+    }
+    return 10;
+}
+
+/* the tetrahedra containing DOF i, as cell * 6 + t in increasing order */
+static int node_tets(int elem, int N, int64_t i, int64_t *out)
+{
+    int M = elem == ORC_P1 ? N : 2 * N; /* grid of the DOFs */
+    int64_t m1 = M - 1, NN = N;
+    int w[3] = {(int)(i % m1) + 1, (int)((i / m1) % m1) + 1, (int)(i / (m1 * m1)) + 1};
+    int lo[3], hi[3];
+    for (int d = 0; d < 3; d++) {
+        if (elem == ORC_P1) {
+            lo[d] = w[d] - 1;
+            hi[d] = w[d];
+        } else {
+            lo[d] = (w[d] - 1) >> 1;
+            hi[d] = w[d] >> 1;
+        }
+        if (lo[d] < 0)
+            lo[d] = 0;
+        if (hi[d] > N - 1)
+            hi[d] = N - 1;
+    }
+    int m = 0;
+    int64_t g[10];
+    for (int cz = lo[2]; cz <= hi[2]; cz++)
+        for (int cy = lo[1]; cy <= hi[1]; cy++)
+            for (int cx = lo[0]; cx <= hi[0]; cx++)
+                for (int t = 0; t < 6; t++) {
+                    int nl = tet_dofs(elem, N, cx, cy, cz, t, g);
+                    for (int a = 0; a < nl; a++)
+                        if (g[a] == i) {
+                            out[m++] = (cx + NN * (cy + NN * (int64_t)cz)) * 6 + t;
+                            break;
+                        }
+                }
+    return m;
+}
+
+static int assemble_tet(int elem, int N, const double *kref, const double *k_cell, double hfac, orc_csr *A)
+{
+    int64_t n = orc_ndofs(3, elem, N), NN = N;
+    int nl = elem == ORC_P1 ? 4 : 10;
+    memset(A, 0, sizeof(*A));
+    A->nrows = A->ncols = n;
+    A->rowptr = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+    if (!A->rowptr)
+        return -1;
+    int64_t tets[256], g[10], cand[2560];
+    for (int pass = 0; pass < 2; pass++) {
+        for (int64_t i = 0; i < n; i++) {
+            int mt = node_tets(elem, N, i, tets);
+            int m = 0;
+            for (int q = 0; q < mt; q++) {
+                int64_t c = tets[q] / 6;
+                int t = (int)(tets[q] % 6);
+                tet_dofs(elem, N, (int)(c % NN), (int)((c / NN) % NN), (int)(c / (NN * NN)), t, g);
+                for (int a = 0; a < nl; a++)
+                    if (g[a] >= 0)
+                        cand[m++] = g[a];
+            }
+            qsort(cand, (size_t)m, sizeof(int64_t), cmp_i64);
+            int u = 0;
+            for (int a = 0; a < m; a++)
+                if (u == 0 || cand[a] != cand[u - 1])
+                    cand[u++] = cand[a];
+            if (pass == 0) {
+                A->rowptr[i + 1] = u;
+            } else {
+                int64_t p = A->rowptr[i];
+                for (int a = 0; a < u; a++)
+                    A->col[p + a] = (int32_t)cand[a];
+            }
+        }
+        if (pass == 0) {
+            for (int64_t i = 0; i < n; i++)
+                A->rowptr[i + 1] += A->rowptr[i];
+            A->nnz = A->rowptr[n];
+            A->col = (int32_t *)malloc((size_t)A->nnz * sizeof(int32_t));
+            A->val = (double *)calloc((size_t)A->nnz, sizeof(double));
+            if (!A->col || !A->val)
+                return -1;
+        }
+    }
+    /* values: element loop, cells in lexicographic order, tetrahedra in KUHN order */
+    int64_t ncells = NN * NN * NN;
+    for (int64_t e = 0; e < ncells; e++) {
+        int cx = (int)(e % NN), cy = (int)((e / NN) % NN), cz = (int)(e / (NN * NN));
+        double ke = k_cell ? k_cell[e] : 1.0;
+        double sc = ke * hfac;
+        for (int t = 0; t < 6; t++) {
+            tet_dofs(elem, N, cx, cy, cz, t, g);
+            for (int a = 0; a < nl; a++) {
+                if (g[a] < 0)
+                    continue;
+                for (int b = 0; b < nl; b++) {
+                    if (g[b] < 0)
+                        continue;
+                    int64_t p = find_col(A, g[a], g[b]);
+                    A->val[p] = A->val[p] + sc * kref[a * nl + b];
+                }
+            }
+        }
+    }
+    return 0;
+}
+
+/*
+ * Prolongation = interpolation of the coarse function at the fine nodes (the spaces
+ * are nested; the paper's general transfer of Sec. 5.4 reduces to this for conforming
+ * elements). A fine node at coarse-cell coordinates c + s, s in [0,1]^3 (c the cell
+ * of the node, the last cell on the upper boundary), lies in the Kuhn tetrahedron
+ * whose permutation sorts s in decreasing order (ties by axis); there
+ * lambda = (1 - s_pi0, s_pi0 - s_pi1, s_pi1 - s_pi2, s_pi2) and the weights are the
+ * coarse basis values (P1: lambda_a; P2: lambda_a (2 lambda_a - 1), 4 lambda_a lambda_b).
+ * All are dyadic, so exact. Zero weights and Dirichlet coarse DOFs are dropped.
+ */
+static int prolong_tet(int elem, int Nc, orc_csr *P)
+{
+    int Nf = 2 * Nc;
+    int64_t nf = orc_ndofs(3, elem, Nf), nc = orc_ndofs(3, elem, Nc);
+    int Mf = elem == ORC_P1 ? Nf : 2 * Nf; /* fine node grid */
+    int r = elem == ORC_P1 ? 2 : 4;        /* fine node spacings per coarse cell */
+    int64_t m1 = Mf - 1;
+    memset(P, 0, sizeof(*P));
+    P->nrows = nf;
+    P->ncols = nc;
+    P->rowptr = (int64_t *)calloc((size_t)nf + 1, sizeof(int64_t));
+    if (!P->rowptr)
+        return -1;
+    orc_entry ent[10];
+    for (int pass = 0; pass < 2; pass++) {
+        for (int64_t i = 0; i < nf; i++) {
+            int w[3] = {(int)(i % m1) + 1, (int)((i / m1) % m1) + 1, (int)(i / (m1 * m1)) + 1};
+            int c[3];
+            double sv[3];
+            for (int d = 0; d < 3; d++) {
+                c[d] = w[d] / r;
+                if (c[d] > Nc - 1)
+                    c[d] = Nc - 1;
+                sv[d] = (double)(w[d] - r * c[d]) / (double)r;
+            }
+            int pi[3] = {0, 1, 2};
+            for (int a = 1; a < 3; a++) /* stable insertion sort, decreasing s */
+                for (int b = a; b > 0 && sv[pi[b]] > sv[pi[b - 1]]; b--) {
+                    int tmp = pi[b];
+                    pi[b] = pi[b - 1];
+                    pi[b - 1] = tmp;
+                }
+            int t = 0;
+            while (!(KUHN[t][0] == pi[0] && KUHN[t][1] == pi[1] && KUHN[t][2] == pi[2]))
+                t++;
+            double lam[4] = {1.0 - sv[pi[0]], sv[pi[0]] - sv[pi[1]], sv[pi[1]] - sv[pi[2]], sv[pi[2]]};
+            int64_t g[10];
+            int nl = tet_dofs(elem, Nc, c[0], c[1], c[2], t, g);
+            double wt[10];
+            if (elem == ORC_P1) {
+                for (int a = 0; a < 4; a++)
+                    wt[a] = lam[a];
+            } else {
+                for (int a = 0; a < 4; a++)
+                    wt[a] = lam[a] * (2.0 * lam[a] - 1.0);
+                for (int e = 0; e < 6; e++)
+                    wt[4 + e] = (4.0 * lam[TET_EDGE[e][0]]) * lam[TET_EDGE[e][1]];
+            }
+            int m = 0;
+            for (int a = 0; a < nl; a++)
+                if (g[a] >= 0 && wt[a] != 0.0) {
+                    ent[m].col = g[a];
+                    ent[m].w = wt[a];
+                    m++;
+                }
+            qsort(ent, (size_t)m, sizeof(orc_entry), cmp_entry);
+            if (pass == 0) {
+                P->rowptr[i + 1] = m;
+            } else {
+                int64_t p = P->rowptr[i];
+                for (int a = 0; a < m; a++) {
+                    P->col[p + a] = (int32_t)ent[a].col;
+                    P->val[p + a] = ent[a].w;
+                }
+            }
+        }
+        if (pass == 0) {
+            for (int64_t i = 0; i < nf; i++)
+                P->rowptr[i + 1] += P->rowptr[i];
+            P->nnz = P->rowptr[nf];
+            P->col = (int32_t *)malloc((size_t)(P->nnz ? P->nnz : 1) * sizeof(int32_t));
+            P->val = (double *)malloc((size_t)(P->nnz ? P->nnz : 1) * sizeof(double));
+            if (!P->col || !P->val)
+                return -1;
+        }
+    }
+    return 0;
+}
+
+/*
+ * Load vector of the tetrahedral elements: b = M f_I, the consistent mass matrix times
+ * the nodal values of f (the quadrature is not given by the paper; interpolating f
+ * keeps the order of the element, 2 for P1 and 3 for P2). mref: the element mass table;
+ * the row sums are column-ascending fused multiply-adds as in orc_spmv.
+ */
+int orc_load_vector_tet(int elem, int N, int nmodes, const double *amp, const int *kf, double fconst,
+                        const double *mref, double *b)
+{
+    orc_csr M;
+    double h = 1.0 / (double)N;
+    if (assemble_tet(elem, N, mref, NULL, (h * h) * h, &M))
+        return -1;
+    int64_t n = M.nrows;
+    double *f = (double *)malloc((size_t)n * sizeof(double));
+    for (int64_t i = 0; i < n; i++) {
+        double x[3];
+        orc_tet_node_coords(elem, N, i, x);
+        f[i] = eval_f(3, nmodes, amp, kf, fconst, x);
+    }
+    orc_spmv(&M, f, b);
+    free(f);
+    orc_csr_free(&M);
+    return 0;
+}
+
+/* coordinate of DOF i of a tetrahedral element on N cells (node grid: N for P1, 2N for P2) */
+void orc_tet_node_coords(int elem, int N, int64_t i, double *x)
+{
+    int M = elem == ORC_P1 ? N : 2 * N;
+    int64_t m1 = M - 1;
+    int w[3] = {(int)(i % m1) + 1, (int)((i / m1) % m1) + 1, (int)(i / (m1 * m1)) + 1};
+    for (int d = 0; d < 3; d++)
+        x[d] = (double)w[d] / (double)M;
+}
+
 /* ------------------------------------------------------------------------------ */
 /* Hierarchy and V-cycle                                                             */
 /* ------------------------------------------------------------------------------ */
@@ -1007,12 +1297,17 @@ orc_hier *orc_setup(int dim, int elem, int N_finest, int n_levels, const double 
  *   RQ1: face family and parity of the normal position, colour = 2f + (p&1)
  *        (the two faces of one family in a cell sit at p and p+1).
  */
-int orc_n_colours(int dim, int elem) { return elem == ORC_Q1 ? (1 << dim) : 6; }
+int orc_n_colours(int dim, int elem)
+{
+    if (elem == ORC_Q1 || elem == ORC_P1) /* P1: Kuhn edges change the parity of a coordinate */
+        return 1 << dim;
+    return elem == ORC_RQ1 ? 6 : 0;       /* P2: no colouring */
+}
 
 int orc_colour(int dim, int elem, int N, int64_t i)
 {
     int64_t n1 = N - 1, NN = N;
-    if (elem == ORC_Q1) {
+    if (elem == ORC_Q1 || elem == ORC_P1) {
         int vx = (int)(i % n1) + 1;
         int vy = (int)((i / n1) % n1) + 1;
         int c = (vx & 1) + 2 * (vy & 1);

@@ -774,3 +774,144 @@ def test_heat_manufactured_solution_is_second_order(orc):
         errs.append(orc.l2_error(3, orc.Q1, N, [(wl["exact_amp"], (1, 1, 1))], u))
     rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
     assert np.all((rates > 1.8) & (rates < 2.2)), (errs, rates)
+
+
+# ---------------------------------------------------------------------------------
+# P1 / P2 on the Kuhn tetrahedra of the cube grid (the paper's elements, Sec. 6)
+# ---------------------------------------------------------------------------------
+def _kuhn_vertices(perm):
+    v = [np.zeros(3)]
+    for d in perm:
+        w = v[-1].copy()
+        w[d] += 1
+        v.append(w)
+    return np.array(v)
+
+
+def _tet_quadrature(V, order=6):
+    """Conical-product Gauss rule on the tetrahedron with vertices V (Stroud): points, weights."""
+    from scipy.special import roots_jacobi
+    from numpy.polynomial.legendre import leggauss
+    x1, w1 = roots_jacobi(order, 2, 0)   # (1-t)^2 weight
+    x2, w2 = roots_jacobi(order, 1, 0)   # (1-t) weight
+    x3, w3 = leggauss(order)
+    pts, wts = [], []
+    for a, wa in zip(x1, w1):
+        for b, wb in zip(x2, w2):
+            for c, wc in zip(x3, w3):
+                u, v, w = (1 + a) / 2, (1 + b) / 2, (1 + c) / 2
+                # collapsed coordinates: barycentric (l1, l2, l3) of the tetrahedron
+                l1 = u
+                l2 = (1 - u) * v
+                l3 = (1 - u) * (1 - v) * w
+                lam = np.array([1 - l1 - l2 - l3, l1, l2, l3])
+                pts.append(lam @ V)
+                wts.append(wa * wb * wc / 8.0 / 8.0 * 6.0)
+    vol = abs(np.linalg.det((V[1:] - V[0]).T)) / 6.0
+    w = np.array(wts)
+    return np.array(pts), w * vol / w.sum()
+
+
+def _p2_basis_numeric(V, x):
+    """P2 basis values and gradients at x on the tetrahedron V, from the affine barycentric map."""
+    T = np.vstack([V.T, np.ones(4)])
+    Ti = np.linalg.inv(T)
+    lam = Ti @ np.append(x, 1.0)
+    g = Ti[:, :3]  # gradients of lambda_a
+    vals, grads = [], []
+    for a in range(4):
+        vals.append(lam[a] * (2 * lam[a] - 1))
+        grads.append((4 * lam[a] - 1) * g[a])
+    for a, b in [(0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3)]:
+        vals.append(4 * lam[a] * lam[b])
+        grads.append(4 * (lam[b] * g[a] + lam[a] * g[b]))
+    return np.array(vals), np.array(grads)
+
+
+def test_tet_elements_match_numeric_quadrature(orc):
+    from oracle import elements as E
+    for perm in E.KUHN_PERMS:
+        V = _kuhn_vertices(perm)
+        X, Wq = _tet_quadrature(V)
+        K = np.zeros((10, 10))
+        M = np.zeros((10, 10))
+        for x, w in zip(X, Wq):
+            v, g = _p2_basis_numeric(V, x)
+            K += w * g @ g.T
+            M += w * np.outer(v, v)
+        assert np.max(np.abs(np.array(E.tet_stiffness_exact(2, perm), dtype=float) - K)) <= 1e-13
+        assert np.max(np.abs(np.array(E.tet_mass_exact(2), dtype=float) - M)) <= 1e-14
+    # P1: the path-graph Laplacian over 6 and the textbook mass |T| (1 + delta_ab) / 20
+    G = np.array([[1, -1, 0, 0], [-1, 2, -1, 0], [0, -1, 2, -1], [0, 0, -1, 1]]) / 6
+    assert np.array_equal(np.array(E.tet_stiffness_exact(1), dtype=float), G)
+    assert np.array_equal(np.array(E.tet_mass_exact(1), dtype=float), (np.ones((4, 4)) + np.eye(4)) / 120)
+
+
+@pytest.mark.parametrize("N", [4, 7])
+def test_p1_stiffness_is_the_seven_point_laplacian(orc, N):
+    """P1 on the Kuhn triangulation gives h (T x I x I + I x T x I + I x I x T), T = tridiag(-1, 2, -1)."""
+    h = 1.0 / N
+    n1 = N - 1
+    T = 2 * np.eye(n1) - np.eye(n1, k=1) - np.eye(n1, k=-1)
+    I = np.eye(n1)
+    want = h * (np.kron(np.kron(I, I), T) + np.kron(np.kron(I, T), I) + np.kron(np.kron(T, I), I))
+    A = orc.assemble(3, orc.P1, N).dense()
+    assert np.max(np.abs(A - want)) <= 1e-15 * np.max(np.abs(want))
+
+
+@pytest.mark.parametrize("elem,Nc", [(2, 4), (3, 3), (3, 4)])
+def test_tet_prolongation_interpolates_the_element_exactly(orc, elem, Nc):
+    """Away from the boundary a row of P applied to the coarse nodal values of a linear (P1)
+    or quadratic (P2) function gives its value at the fine node."""
+    P = orc.prolongation(3, elem, Nc).dense()
+    xc, xf = orc.node_coords(elem, Nc), orc.node_coords(elem, 2 * Nc)
+    rng = np.random.Generator(np.random.PCG64(5))
+    c = rng.standard_normal(10)
+
+    def q(x):
+        x0, x1, x2 = x[:, 0], x[:, 1], x[:, 2]
+        v = c[0] + c[1] * x0 + c[2] * x1 + c[3] * x2
+        if elem == orc.P2:
+            v = v + c[4] * x0 * x0 + c[5] * x1 * x1 + c[6] * x2 * x2 + c[7] * x0 * x1 + c[8] * x1 * x2 + c[9] * x0 * x2
+        return v
+    y = P @ q(xc)
+    hc = 1.0 / Nc
+    inner = np.all((xf >= hc - 1e-12) & (xf <= 1 - hc + 1e-12), axis=1)  # no Dirichlet node in its cell
+    assert inner.any()
+    assert np.max(np.abs(y[inner] - q(xf)[inner])) <= 1e-13
+    # and every row's weights sum to one there (partition of unity)
+    assert np.allclose(P[inner].sum(axis=1), 1.0, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("elem,N,L,sm", [(2, 8, 3, 0), (2, 8, 3, 2), (3, 4, 2, 0), (3, 4, 2, 1)])
+def test_tet_mg_matches_dense_solve(orc, elem, N, L, sm):
+    H = orc.Hierarchy(3, elem, N, L, opts=orc.Options(smoother=sm, omega=0.7, nu_pre=2, nu_post=2))
+    b = W.random_vector(H.n, seed=61)
+    x, hist, it, conv = H.solve(b, 1e-12)
+    assert conv
+    xd = np.linalg.solve(H.A(L - 1).dense(), b)
+    assert np.linalg.norm(x - xd) <= 1e-9 * np.linalg.norm(xd)
+
+
+def test_p1_gs_colouring_is_valid(orc):
+    A = orc.assemble(3, orc.P1, 6).to_scipy().tocoo()
+    col = orc.colours(3, orc.P1, 6)
+    off = A.row != A.col
+    assert not np.any(col[A.row[off]] == col[A.col[off]])
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("elem,Ns,order", [(2, (8, 16, 32), 2), (3, (4, 8, 16), 3)])
+def test_tet_nodal_error_has_the_element_order(orc, elem, Ns, order):
+    """Manufactured u = prod sin(pi x_d): the nodal error falls at least as h^order."""
+    errs = []
+    for N in Ns:
+        L = 2 if N <= 8 else 3
+        H = orc.Hierarchy(3, elem, N, L, opts=orc.Options(omega=0.7))
+        b = orc.load_vector(3, elem, N, modes=W.manufactured_modes(3))
+        x, hist, it, conv = H.solve(b, 1e-13)
+        X = orc.node_coords(elem, N)
+        u = np.prod(np.sin(np.pi * X), axis=1)
+        errs.append(np.max(np.abs(x - u)))
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(rates > order - 0.1), (errs, rates)
