@@ -37,6 +37,8 @@ WORKLOADS = {
     "q1_3d_128_cheb": "3D Poisson, Q1, 128^3 cells (2,048,383 DOFs), 6 levels, V(2,2) Chebyshev deg 2, FP64",
     "q1_2d_64": "2D Poisson, Q1, 64^2 cells (3,969 DOFs), 5 levels, V(2,2) Jacobi 0.8, FP64",
     "rq1_3d_96": "3D Poisson, rotated Q1, 96^3 cells (2,626,560 DOFs), 6 levels, V(2,2) Jacobi 0.7, FP64",
+    "p1_3d_128_cheb": "3D Poisson, P1 on Kuhn tetrahedra, 128^3 cells (2,048,383 DOFs), 6 levels, Chebyshev deg 2, FP64",
+    "p2_3d_64_cheb": "3D Poisson, P2 on Kuhn tetrahedra, 64^3 cells (2,048,383 DOFs), 5 levels, Chebyshev deg 2, FP64",
 }
 
 
@@ -170,7 +172,7 @@ SWEEP_TEXT = {0: "fused residual + damped Jacobi update", 1: "fused residual + C
 def _config_args(name, smoother="workload"):
     """The workload's parameters; `smoother` other than "workload" replaces its smoother."""
     from paper_1609_04809_gb300 import workloads as W
-    c = dict(W.CONFIGS[name])
+    c = dict({**W.CONFIGS, **W.TET_CONFIGS}[name])
     if smoother != "workload":
         c["smoother"] = SMOOTHERS[smoother]
     return c
@@ -641,7 +643,7 @@ def main():
         __graft_entry__.build_library()
         torch.cuda.set_device(0)
         from paper_1609_04809_gb300 import workloads as W
-        for name in W.CONFIGS:
+        for name in list(W.CONFIGS) + list(W.TET_CONFIGS):
             print(json.dumps(config_report(name, smoother=args.smoother)), flush=True)
         if not args.no_heat:
             print(json.dumps(heat_report()), flush=True)

@@ -51,6 +51,16 @@ typedef int mg_status;
 /* element */
 #define MG_Q1 0  /* conforming bi/trilinear, vertex DOFs, 2D or 3D */
 #define MG_RQ1 1 /* nonconforming rotated Q1 with face-mean DOFs, 3D */
+/* Conforming P1 / P2 on tetrahedra (the paper's elements, Sec. 6), 3D: every cell of the
+ * grid is split into the six Kuhn tetrahedra along its main diagonal (cell (c), axis
+ * permutation pi: vertices c, c + e_pi0, c + e_pi0 + e_pi1, c + (1,1,1)); halving the grid
+ * splits each into eight of the finer grid's, so the spaces are nested and P is
+ * interpolation. P1 DOFs: the interior vertices (numbered like Q1; storage DIA, ELL or
+ * CSR). P2 DOFs: vertices and edge midpoints, i.e. the interior points of the grid of
+ * 2 n_cells cells, numbered like Q1 there (ELL or CSR). Load vector: b = M f_I (the mass
+ * matrix times f at the nodes). Gauss-Seidel: P1 only (vertex parity colours). */
+#define MG_P1 2
+#define MG_P2 3
 /* smoother */
 #define MG_JACOBI 0    /* damped Jacobi x <- x + omega D^-1 (b - A x) */
 #define MG_CHEBYSHEV 1 /* Chebyshev polynomial in D^-1 A of degree cheb_degree */

@@ -21,6 +21,8 @@ int64_t ndofs(int dim, int elem, int N)
 {
     int64_t n1 = N - 1, NN = N;
     if (elem == MG_Q1) return dim == 2 ? n1 * n1 : n1 * n1 * n1;
+    if (elem == MG_P1) return n1 * n1 * n1;
+    if (elem == MG_P2) return (2 * NN - 1) * (2 * NN - 1) * (2 * NN - 1);
     return 3 * n1 * NN * NN;
 }
 
@@ -184,8 +186,8 @@ static inline int dof_cells(int dim, int elem, int N, int64_t i, int (*c)[3], in
 // ---------------------------------------------------------------------------------
 struct RowAcc {
     int m = 0;
-    int64_t col[32];
-    double val[32];
+    int64_t col[96];  // P2 rows hold up to 65 entries
+    double val[96];
     void add(int64_t j, double v)
     {
         for (int k = 0; k < m; k++)
@@ -235,11 +237,266 @@ static void assemble_row(int dim, int elem, int N, const double *k, const double
     acc.sort();
 }
 
+// ---------------------------------------------------------------------------------
+// P1 / P2 on the Kuhn tetrahedra of the cube grid (3D)
+// ---------------------------------------------------------------------------------
+// Cell (cx,cy,cz) holds six tetrahedra, one per permutation pi of the axes (in the order
+// of kKuhn): the path v0 = (cx,cy,cz), v1 = v0 + e_pi0, v2 = v1 + e_pi1, v3 = v0 + (1,1,1).
+// Their barycentric coordinates at local point s are 1 - s_pi0, s_pi0 - s_pi1,
+// s_pi1 - s_pi2, s_pi2. Halving the grid splits each into 8 tetrahedra of the finer one.
+// P1 DOFs are the interior vertices (numbered like Q1); P2 DOFs are the interior points
+// of the grid of 2N cells (vertices and edge midpoints), local nodes 0..3 the vertices
+// and 4..9 the midpoints of edges (01) (02) (03) (12) (13) (23).
+static const int kKuhn[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+static const int kTetEdge[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
+
+static inline int64_t grid_point(int M, const int *w)  // interior point of the M-cell grid, or -1
+{
+    for (int d = 0; d < 3; d++)
+        if (w[d] <= 0 || w[d] >= M) return -1;
+    int64_t m1 = M - 1;
+    return (w[0] - 1) + m1 * ((w[1] - 1) + m1 * (int64_t)(w[2] - 1));
+}
+
+static int tet_nodes(int elem, int N, int cx, int cy, int cz, int t, int64_t *g)
+{
+    int v[4][3] = {{cx, cy, cz}};
+    for (int a = 1; a < 4; a++) {
+        for (int d = 0; d < 3; d++) v[a][d] = v[a - 1][d];
+        v[a][kKuhn[t][a - 1]] += 1;
+    }
+    if (elem == MG_P1) {
+        for (int a = 0; a < 4; a++) g[a] = grid_point(N, v[a]);
+        return 4;
+    }
+    for (int a = 0; a < 4; a++) {
+        int w[3] = {2 * v[a][0], 2 * v[a][1], 2 * v[a][2]};
+        g[a] = grid_point(2 * N, w);
+    }
+    for (int e = 0; e < 6; e++) {
+        const int *A = v[kTetEdge[e][0]], *B = v[kTetEdge[e][1]];
+        int w[3] = {A[0] + B[0], A[1] + B[1], A[2] + B[2]};
+        g[4 + e] = grid_point(2 * N, w);
+    }
+    return 10;
+}
+
+// exact rationals for the element tables
+struct Rat {
+    int64_t p = 0, q = 1;
+};
+static int64_t gcd64(int64_t a, int64_t b)
+{
+    if (a < 0) a = -a;
+    while (b) {
+        int64_t t = a % b;
+        a = b;
+        b = t;
+    }
+    return a ? a : 1;
+}
+static Rat rat(int64_t p, int64_t q)
+{
+    int64_t g = gcd64(p, q);
+    return Rat{p / g, q / g};
+}
+static Rat radd(Rat a, Rat b) { return rat(a.p * b.q + b.p * a.q, a.q * b.q); }
+static Rat rmul(Rat a, Rat b) { return rat(a.p * b.p, a.q * b.q); }
+
+// polynomial in the four barycentric coordinates: terms (exponents, coefficient)
+struct Term {
+    int e[4];
+    Rat c;
+};
+using Poly = std::vector<Term>;
+static Poly pmul(const Poly &a, const Poly &b)
+{
+    Poly r;
+    for (const Term &x : a)
+        for (const Term &y : b) {
+            Term t;
+            for (int k = 0; k < 4; k++) t.e[k] = x.e[k] + y.e[k];
+            t.c = rmul(x.c, y.c);
+            r.push_back(t);
+        }
+    return r;
+}
+// integral over a Kuhn tetrahedron of the unit cell (volume 1/6):
+// int lambda^alpha = alpha! 3! |T| / (|alpha| + 3)! = alpha! / (|alpha| + 3)!
+static Rat pint(const Poly &a)
+{
+    static const int64_t fact[12] = {1, 1, 2, 6, 24, 120, 720, 5040, 40320, 362880, 3628800, 39916800};
+    Rat s;
+    for (const Term &t : a) {
+        int64_t num = 1;
+        int deg = 0;
+        for (int k = 0; k < 4; k++) {
+            num *= fact[t.e[k]];
+            deg += t.e[k];
+        }
+        s = radd(s, rmul(t.c, rat(num, fact[deg + 3])));
+    }
+    return s;
+}
+static Poly lam(int a, int64_t c = 1)
+{
+    Term t{{0, 0, 0, 0}, rat(c, 1)};
+    t.e[a] = 1;
+    return Poly{t};
+}
+static Poly konst(int64_t c) { return Poly{Term{{0, 0, 0, 0}, rat(c, 1)}}; }
+static Poly padd(Poly a, const Poly &b)
+{
+    a.insert(a.end(), b.begin(), b.end());
+    return a;
+}
+
+// unit-cell element stiffness and mass of P1 (4 x 4) or P2 (10 x 10), nearest doubles of
+// the exact rationals (the same for all six tetrahedra: congruent with the same order)
+static void tet_tables(int elem, double *K, double *M)
+{
+    int nl = elem == MG_P1 ? 4 : 10;
+    // gradients of lambda for the path (0,1,2): -e0, e0 - e1, e1 - e2, e2
+    static const int g[4][3] = {{-1, 0, 0}, {1, -1, 0}, {0, 1, -1}, {0, 0, 1}};
+    int G[4][4];
+    for (int a = 0; a < 4; a++)
+        for (int b = 0; b < 4; b++) G[a][b] = g[a][0] * g[b][0] + g[a][1] * g[b][1] + g[a][2] * g[b][2];
+    std::vector<Poly> N((size_t)nl);
+    std::vector<std::vector<Poly>> dN((size_t)nl, std::vector<Poly>(4));  // grad N_i = sum_a dN[i][a] g_a
+    if (elem == MG_P1) {
+        for (int a = 0; a < 4; a++) {
+            N[a] = lam(a);
+            dN[a][a] = konst(1);
+        }
+    } else {
+        for (int a = 0; a < 4; a++) {  // lambda_a (2 lambda_a - 1)
+            N[a] = pmul(lam(a), padd(lam(a, 2), konst(-1)));
+            dN[a][a] = padd(lam(a, 4), konst(-1));
+        }
+        for (int e = 0; e < 6; e++) {  // 4 lambda_a lambda_b
+            int a = kTetEdge[e][0], b = kTetEdge[e][1];
+            N[4 + e] = pmul(lam(a, 4), lam(b));
+            dN[4 + e][a] = lam(b, 4);
+            dN[4 + e][b] = lam(a, 4);
+        }
+    }
+    for (int i = 0; i < nl; i++)
+        for (int j = 0; j < nl; j++) {
+            Rat k;
+            for (int a = 0; a < 4; a++)
+                for (int b = 0; b < 4; b++)
+                    if (G[a][b] && !dN[i][a].empty() && !dN[j][b].empty())
+                        k = radd(k, rmul(rat(G[a][b], 1), pint(pmul(dN[i][a], dN[j][b]))));
+            Rat m = pint(pmul(N[i], N[j]));
+            K[i * nl + j] = (double)k.p / (double)k.q;
+            M[i * nl + j] = (double)m.p / (double)m.q;
+        }
+}
+
+// the tetrahedra (cell * 6 + t, increasing) that contain DOF i, and i's local index
+static int node_tets(int elem, int N, int64_t i, int64_t *et, int *loc)
+{
+    int M = elem == MG_P1 ? N : 2 * N;
+    int64_t m1 = M - 1, NN = N;
+    int w[3] = {(int)(i % m1) + 1, (int)((i / m1) % m1) + 1, (int)(i / (m1 * m1)) + 1};
+    int lo[3], hi[3];
+    for (int d = 0; d < 3; d++) {
+        lo[d] = elem == MG_P1 ? w[d] - 1 : (w[d] - 1) >> 1;
+        hi[d] = elem == MG_P1 ? w[d] : w[d] >> 1;
+        lo[d] = std::max(lo[d], 0);
+        hi[d] = std::min(hi[d], N - 1);
+    }
+    int m = 0;
+    int64_t g[10];
+    for (int cz = lo[2]; cz <= hi[2]; cz++)
+        for (int cy = lo[1]; cy <= hi[1]; cy++)
+            for (int cx = lo[0]; cx <= hi[0]; cx++)
+                for (int t = 0; t < 6; t++) {
+                    int nl = tet_nodes(elem, N, cx, cy, cz, t, g);
+                    for (int a = 0; a < nl; a++)
+                        if (g[a] == i) {
+                            et[m] = (cx + NN * (cy + NN * (int64_t)cz)) * 6 + t;
+                            loc[m] = a;
+                            m++;
+                            break;
+                        }
+                }
+    return m;
+}
+
+static void assemble_row_tet(int elem, int N, const double *k, const double *kref, double hfac, int64_t i,
+                             RowAcc &acc)
+{
+    int64_t et[64], g[10], NN = N;
+    int loc[64];
+    int nl = elem == MG_P1 ? 4 : 10;
+    int mt = node_tets(elem, N, i, et, loc);
+    acc.m = 0;
+    for (int q = 0; q < mt; q++) {
+        int64_t c = et[q] / 6;
+        double s = (k ? k[c] : 1.0) * hfac;
+        tet_nodes(elem, N, (int)(c % NN), (int)((c / NN) % NN), (int)(c / (NN * NN)), (int)(et[q] % 6), g);
+        for (int b = 0; b < nl; b++)
+            if (g[b] >= 0) acc.add(g[b], s * kref[loc[q] * nl + b]);
+    }
+    acc.sort();
+}
+
+// Interpolation of the coarse function at the fine nodes (nested spaces): a fine node at
+// coarse-cell coordinates c + s lies in the tetrahedron whose permutation sorts s
+// decreasing (ties by axis); the weights are the coarse basis values there (dyadic).
+static int prolong_row_tet(int elem, int Nc, int64_t i, int64_t *cols, double *vals)
+{
+    int Nf = 2 * Nc;
+    int Mf = elem == MG_P1 ? Nf : 2 * Nf, r = elem == MG_P1 ? 2 : 4;
+    int64_t m1 = Mf - 1;
+    int w[3] = {(int)(i % m1) + 1, (int)((i / m1) % m1) + 1, (int)(i / (m1 * m1)) + 1};
+    int c[3];
+    double sv[3];
+    for (int d = 0; d < 3; d++) {
+        c[d] = std::min(w[d] / r, Nc - 1);
+        sv[d] = (double)(w[d] - r * c[d]) / (double)r;
+    }
+    int pi[3] = {0, 1, 2};
+    for (int a = 1; a < 3; a++)
+        for (int b = a; b > 0 && sv[pi[b]] > sv[pi[b - 1]]; b--) std::swap(pi[b], pi[b - 1]);
+    int t = 0;
+    while (kKuhn[t][0] != pi[0] || kKuhn[t][1] != pi[1] || kKuhn[t][2] != pi[2]) t++;
+    double l[4] = {1.0 - sv[pi[0]], sv[pi[0]] - sv[pi[1]], sv[pi[1]] - sv[pi[2]], sv[pi[2]]};
+    int64_t g[10];
+    int nl = tet_nodes(elem, Nc, c[0], c[1], c[2], t, g);
+    double wt[10];
+    if (elem == MG_P1) {
+        for (int a = 0; a < 4; a++) wt[a] = l[a];
+    } else {
+        for (int a = 0; a < 4; a++) wt[a] = l[a] * (2.0 * l[a] - 1.0);
+        for (int e = 0; e < 6; e++) wt[4 + e] = (4.0 * l[kTetEdge[e][0]]) * l[kTetEdge[e][1]];
+    }
+    int m = 0;
+    for (int a = 0; a < nl; a++)
+        if (g[a] >= 0 && wt[a] != 0.0) {
+            cols[m] = g[a];
+            vals[m] = wt[a];
+            m++;
+        }
+    for (int a = 1; a < m; a++)  // columns ascending
+        for (int b = a; b > 0 && cols[b] < cols[b - 1]; b--) {
+            std::swap(cols[b], cols[b - 1]);
+            std::swap(vals[b], vals[b - 1]);
+        }
+    return m;
+}
+
 static void assemble_with(int dim, int elem, int N, const double *k, const double *kref, double hfac, Csr &A);
 
 void assemble(int dim, int elem, int N, const double *k, Csr &A)
 {
-    double kref[64];
+    double kref[100], mref[100];
+    if (elem == MG_P1 || elem == MG_P2) {
+        tet_tables(elem, kref, mref);
+        assemble_with(3, elem, N, k, kref, 1.0 / (double)N, A);
+        return;
+    }
     if (elem == MG_Q1)
         q1_kref(dim, kref);
     else
@@ -248,12 +505,15 @@ void assemble(int dim, int elem, int N, const double *k, Csr &A)
     assemble_with(dim, elem, N, k, kref, dim == 2 ? 1.0 : h, A);
 }
 
-void assemble_mass(int dim, int N, Csr &M)
+void assemble_mass(int dim, int elem, int N, Csr &M)
 {
-    double mref[64];
-    q1_mref(dim, mref);
+    double kref[100], mref[100];
+    if (elem == MG_P1 || elem == MG_P2)
+        tet_tables(elem, kref, mref);
+    else
+        q1_mref(dim, mref);
     double h = 1.0 / (double)N;
-    assemble_with(dim, MG_Q1, N, nullptr, mref, dim == 2 ? h * h : (h * h) * h, M);
+    assemble_with(dim, elem, N, nullptr, mref, dim == 2 ? h * h : (h * h) * h, M);
 }
 
 // element matrices (k_e * hfac) * kref, added row by row in increasing cell order
@@ -262,10 +522,14 @@ static void assemble_with(int dim, int elem, int N, const double *k, const doubl
     int64_t n = ndofs(dim, elem, N);
     A.nrows = A.ncols = n;
     A.rowptr.assign((size_t)n + 1, 0);
+    const bool tet = elem == MG_P1 || elem == MG_P2;
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; i++) {
         RowAcc acc;
-        assemble_row(dim, elem, N, k, kref, hfac, i, acc);
+        if (tet)
+            assemble_row_tet(elem, N, k, kref, hfac, i, acc);
+        else
+            assemble_row(dim, elem, N, k, kref, hfac, i, acc);
         A.rowptr[i + 1] = acc.m;
     }
     for (int64_t i = 0; i < n; i++) A.rowptr[i + 1] += A.rowptr[i];
@@ -274,7 +538,10 @@ static void assemble_with(int dim, int elem, int N, const double *k, const doubl
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; i++) {
         RowAcc acc;
-        assemble_row(dim, elem, N, k, kref, hfac, i, acc);
+        if (tet)
+            assemble_row_tet(elem, N, k, kref, hfac, i, acc);
+        else
+            assemble_row(dim, elem, N, k, kref, hfac, i, acc);
         int64_t p = A.rowptr[i];
         for (int q = 0; q < acc.m; q++) {
             A.col[p + q] = (int32_t)acc.col[q];
@@ -370,11 +637,12 @@ void prolongation(int dim, int elem, int Nc, Csr &P)
     P.nrows = nf;
     P.ncols = nc;
     P.rowptr.assign((size_t)nf + 1, 0);
+    const bool tet = elem == MG_P1 || elem == MG_P2;
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < nf; i++) {
         int64_t cols[16];
         double vals[16];
-        P.rowptr[i + 1] = prolong_row(dim, elem, Nc, i, cols, vals);
+        P.rowptr[i + 1] = tet ? prolong_row_tet(elem, Nc, i, cols, vals) : prolong_row(dim, elem, Nc, i, cols, vals);
     }
     for (int64_t i = 0; i < nf; i++) P.rowptr[i + 1] += P.rowptr[i];
     P.col.resize((size_t)P.rowptr[nf]);
@@ -383,7 +651,7 @@ void prolongation(int dim, int elem, int Nc, Csr &P)
     for (int64_t i = 0; i < nf; i++) {
         int64_t cols[16];
         double vals[16];
-        int m = prolong_row(dim, elem, Nc, i, cols, vals);
+        int m = tet ? prolong_row_tet(elem, Nc, i, cols, vals) : prolong_row(dim, elem, Nc, i, cols, vals);
         for (int q = 0; q < m; q++) {
             P.col[P.rowptr[i] + q] = (int32_t)cols[q];
             P.val[P.rowptr[i] + q] = vals[q];
@@ -513,6 +781,25 @@ static inline double basis_value(int dim, int elem, int a, const double *xi)
 
 void load_vector(int dim, int elem, int N, const mg_rhs *f, double *b)
 {
+    if (elem == MG_P1 || elem == MG_P2) {
+        // b = M f_I: the mass matrix times f at the nodes (column-ascending fused sums)
+        Csr M;
+        assemble_mass(3, elem, N, M);
+        int Mg = elem == MG_P1 ? N : 2 * N;
+        int64_t m1 = Mg - 1;
+        std::vector<double> fi((size_t)M.nrows);
+        for (int64_t i = 0; i < M.nrows; i++) {
+            double x[3] = {(double)((int)(i % m1) + 1) / (double)Mg, (double)((int)((i / m1) % m1) + 1) / (double)Mg,
+                           (double)((int)(i / (m1 * m1)) + 1) / (double)Mg};
+            fi[i] = eval_f(3, f, x);
+        }
+        for (int64_t i = 0; i < M.nrows; i++) {
+            double acc = 0.0;
+            for (int64_t k = M.rowptr[i]; k < M.rowptr[i + 1]; k++) acc = std::fma(M.val[k], fi[M.col[k]], acc);
+            b[i] = acc;
+        }
+        return;
+    }
     int64_t n = ndofs(dim, elem, N), NN = N;
     int64_t ncells = dim == 2 ? NN * NN : NN * NN * NN;
     int nl = elem == MG_Q1 ? (1 << dim) : 6;
@@ -690,7 +977,7 @@ void build_hierarchy(int dim, int elem, int N_finest, int n_levels, const double
             assemble(dim, elem, Nl, kp, H.A[l]);
             if (mass != 0.0) {  // the shifted operator A + mass * M (same pattern)
                 Csr M;
-                assemble_mass(dim, Nl, M);
+                assemble_mass(dim, elem, Nl, M);
                 for (size_t q = 0; q < M.val.size(); q++) H.A[l].val[q] = H.A[l].val[q] + mass * M.val[q];
             }
         }
@@ -733,11 +1020,15 @@ void round_fp32(const Csr &A, std::vector<float> &val32)
 // ------------------------------------------------------------------------------------
 // Multicolour Gauss-Seidel ordering (DOFs numbered colour-wise, Sec. 4 "DOF Reordering")
 // ------------------------------------------------------------------------------------
-int n_colours(int dim, int elem) { return elem == MG_Q1 ? 1 << dim : 6; }
+int n_colours(int dim, int elem)
+{
+    if (elem == MG_Q1 || elem == MG_P1) return 1 << dim;  // P1: Kuhn edges change a coordinate's parity
+    return elem == MG_RQ1 ? 6 : 0;                        // P2: no colouring
+}
 
 int dof_colour(int dim, int elem, int N, int64_t i)
 {
-    if (elem == MG_Q1) {
+    if (elem == MG_Q1 || elem == MG_P1) {
         int v[3];
         q1_coords(dim, N, i, v);
         return (v[0] & 1) | (v[1] & 1) << 1 | (dim == 3 ? (v[2] & 1) << 2 : 0);

@@ -27,9 +27,9 @@ int64_t ndofs(int dim, int elem, int N);
 // grid (lexicographic, x fastest) or nullptr for k = 1.
 void assemble(int dim, int elem, int N, const double *k, Csr &A);
 
-// Consistent Q1 mass matrix m_ij = sum_e int_e phi_i phi_j (element matrix h^d M_ref,
-// added in increasing cell order); same pattern as the Q1 stiffness matrix.
-void assemble_mass(int dim, int N, Csr &M);
+// Consistent mass matrix m_ij = sum_e int_e phi_i phi_j (element matrix h^d M_ref, added
+// in increasing cell order; Q1, P1, P2); same pattern as the stiffness matrix.
+void assemble_mass(int dim, int elem, int N, Csr &M);
 
 // Prolongation from Nc to 2 Nc cells per axis (rows: fine DOFs, columns: coarse DOFs).
 void prolongation(int dim, int elem, int Nc, Csr &P);

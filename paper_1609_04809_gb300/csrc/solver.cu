@@ -117,6 +117,21 @@ static inline unsigned grid_for(int64_t n) { return (unsigned)((n + 255) / 256);
 // grid of a kernel that ends in a block-partial reduction (finish_norm)
 static inline unsigned reduce_grid(int64_t n) { return std::min<unsigned>(std::max<unsigned>(grid_for(n), 1u), kReduceBlocks); }
 
+// f(std::integral_constant<int, K>()) for the stored slot count K of a DIA matrix: the
+// instantiated counts are 7 and 15 (P1, P1 + mass), 9 (2D Q1), 21 and 27 (3D Q1).
+template <typename F>
+static void with_dia_k(int K, F &&f)
+{
+    switch (K) {
+    case 7: f(std::integral_constant<int, 7>()); break;
+    case 9: f(std::integral_constant<int, 9>()); break;
+    case 15: f(std::integral_constant<int, 15>()); break;
+    case 21: f(std::integral_constant<int, 21>()); break;
+    case 27: f(std::integral_constant<int, 27>()); break;
+    default: throw mgi::Error(MG_EINVAL, "no DIA kernel for " + std::to_string(K) + " stored diagonals");
+    }
+}
+
 void mgi::Slab::reserve(size_t bytes)
 {
     used = round_up((int64_t)used, 256) + bytes;
@@ -286,12 +301,9 @@ static void sweep_fmt(const DevMat &A, int n, const T *x, const T *b, T *out, T 
     MatView<T> v = view<T>(A);
     dim3 g(grid_for(n)), blk(256);
     if (A.fmt == MG_STORAGE_DIA) {
-        if (A.K == 27)
-            klaunch(pdl, k_dia_sweep<T, 27, MODE>, g, blk, 0, s, v, n, x, b, out, d, c1, c2);
-        else if (A.K == 21)
-            klaunch(pdl, k_dia_sweep<T, 21, MODE>, g, blk, 0, s, v, n, x, b, out, d, c1, c2);
-        else
-            klaunch(pdl, k_dia_sweep<T, 9, MODE>, g, blk, 0, s, v, n, x, b, out, d, c1, c2);
+        with_dia_k(A.K, [&](auto k) {
+            klaunch(pdl, k_dia_sweep<T, decltype(k)::value, MODE>, g, blk, 0, s, v, n, x, b, out, d, c1, c2);
+        });
     } else if (A.fmt == MG_STORAGE_ELL) {
         klaunch(pdl, k_ell_sweep<T, MODE>, g, blk, 0, s, v, n, x, b, out, d, c1, c2);
     } else {
@@ -378,12 +390,9 @@ static void gs_sweep(mg_hierarchy *h, int l, T *x, bool post, cudaStream_t s)
         LaunchScope ls(h, s, MG_K_SMOOTH, l, bytes, 2.0 * entries + 4.0 * nr);
         dim3 g((unsigned)((nr + 255) / 256)), blk(256);
         if (G.fmt == MG_STORAGE_DIA) {
-            if (G.K == 21)
-                klaunch(pdl, k_gs_dia<T, 21>, g, blk, 0, s, v, (const int32_t *)L.perm, r0, nr, x, b);
-            else if (G.K == 27)
-                klaunch(pdl, k_gs_dia<T, 27>, g, blk, 0, s, v, (const int32_t *)L.perm, r0, nr, x, b);
-            else
-                klaunch(pdl, k_gs_dia<T, 9>, g, blk, 0, s, v, (const int32_t *)L.perm, r0, nr, x, b);
+            with_dia_k(G.K, [&](auto k) {
+                klaunch(pdl, k_gs_dia<T, decltype(k)::value>, g, blk, 0, s, v, (const int32_t *)L.perm, r0, nr, x, b);
+            });
         } else if (G.fmt == MG_STORAGE_ELL) {
             klaunch(pdl, k_gs_ell<T>, g, blk, 0, s, v, (const int32_t *)L.perm, r0, nr, x, b);
         } else {
@@ -618,12 +627,10 @@ static void enqueue_outer(mg_hierarchy *h, cudaStream_t s)
     bool pdl = h->opt.use_pdl != 0;
     const double *x = h->x64, *b = h->b64;
     if (A.fmt == MG_STORAGE_DIA) {
-        if (A.K == 27)
-            klaunch(pdl, k_outer_resid<T, 3, 27>, g, blk, 0, s, v, n, x, b, r, h->partial, h->ticket, h->norm2);
-        else if (A.K == 21)
-            klaunch(pdl, k_outer_resid<T, 3, 21>, g, blk, 0, s, v, n, x, b, r, h->partial, h->ticket, h->norm2);
-        else
-            klaunch(pdl, k_outer_resid<T, 3, 9>, g, blk, 0, s, v, n, x, b, r, h->partial, h->ticket, h->norm2);
+        with_dia_k(A.K, [&](auto k) {
+            klaunch(pdl, k_outer_resid<T, 3, decltype(k)::value>, g, blk, 0, s, v, n, x, b, r, h->partial, h->ticket,
+                    h->norm2);
+        });
     } else if (A.fmt == MG_STORAGE_ELL) {
         klaunch(pdl, k_outer_resid<T, 2, 1>, g, blk, 0, s, v, n, x, b, r, h->partial, h->ticket, h->norm2);
     } else {
@@ -664,12 +671,7 @@ template <typename MK>
 static void launch_fp64_rows(mg_hierarchy *h, const DevMat &A, MK &&mk)
 {
     if (A.fmt == MG_STORAGE_DIA) {
-        if (A.K == 27)
-            mk(std::integral_constant<int, 3>(), std::integral_constant<int, 27>());
-        else if (A.K == 21)
-            mk(std::integral_constant<int, 3>(), std::integral_constant<int, 21>());
-        else
-            mk(std::integral_constant<int, 3>(), std::integral_constant<int, 9>());
+        with_dia_k(A.K, [&](auto k) { mk(std::integral_constant<int, 3>(), k); });
     } else if (A.fmt == MG_STORAGE_ELL) {
         mk(std::integral_constant<int, 2>(), std::integral_constant<int, 1>());
     } else {
@@ -908,7 +910,9 @@ extern "C" void mg_options_default(mg_options *o)
 
 extern "C" int64_t mg_ndofs(int dim, int element, int n_cells)
 {
-    if (n_cells < 1 || !((element == MG_Q1 && (dim == 2 || dim == 3)) || (element == MG_RQ1 && dim == 3))) return -1;
+    if (n_cells < 1 || !((element == MG_Q1 && (dim == 2 || dim == 3)) ||
+                         ((element == MG_RQ1 || element == MG_P1 || element == MG_P2) && dim == 3)))
+        return -1;
     return mgh::ndofs(dim, element, n_cells);
 }
 
@@ -923,7 +927,7 @@ static void validate_problem(const mg_problem *p)
     int64_t n = mgh::ndofs(p->dim, p->element, p->n_cells);
     if (n > (int64_t)INT32_MAX / 32) throw Error(MG_EINVAL, "problem too large for 32-bit row indices");
     if (!(p->mass >= 0.0) || !std::isfinite(p->mass)) throw Error(MG_EINVAL, "mass must be finite and >= 0");
-    if (p->mass != 0.0 && p->element != MG_Q1) throw Error(MG_EINVAL, "the mass shift is built for Q1");
+    if (p->mass != 0.0 && p->element == MG_RQ1) throw Error(MG_EINVAL, "the mass shift is built for Q1, P1 and P2");
 }
 
 extern "C" mg_status mg_load_vector(const mg_problem *p, const mg_rhs *f, double *b_host)
@@ -986,14 +990,13 @@ static void plan_matrix(DevMat &m, const mgh::Csr &A, int fmt, int dim, int N, i
                 used[(cj[0] - ci[0] + 1) + 3 * (cj[1] - ci[1] + 1) + (dim == 3 ? 9 * (cj[2] - ci[2] + 1) : 0)] = true;
             }
         }
-        int cnt = 0;
-        for (int p = 0; p < npos; p++) cnt += used[p];
-        int K = dim == 2 ? 9 : (cnt <= 21 ? 21 : 27);
         for (int p = 0; p < npos; p++)  // symmetrise (a Galerkin product may round asymmetrically)
             if (used[p]) used[npos - 1 - p] = true;
-        cnt = 0;
+        int cnt = 0;
         for (int p = 0; p < npos; p++) cnt += used[p];
-        if (cnt > K) K = 27;
+        // the smallest instantiated slot count that holds them: 9 in 2D; 7, 15, 21, 27 in 3D
+        int K = 9;
+        if (dim == 3) K = cnt <= 7 ? 7 : (cnt <= 15 ? 15 : (cnt <= 21 ? 21 : 27));
         for (int p = 0; p < cpos && cnt < K; p++)
             if (!used[p]) {
                 used[p] = used[npos - 1 - p] = true;
@@ -1173,9 +1176,11 @@ static void cheb_coeffs(LevelD &L, const mg_options &o)
 
 static int pick_storage(const mg_options &o, int elem)
 {
-    if (o.storage == MG_STORAGE_DIA && elem != MG_Q1) throw Error(MG_EINVAL, "DIA storage needs Q1 (fixed stencil offsets)");
+    bool vertex_grid = elem == MG_Q1 || elem == MG_P1;  // DOFs on the grid vertices, stencil in the 27-point box
+    if (o.storage == MG_STORAGE_DIA && !vertex_grid)
+        throw Error(MG_EINVAL, "DIA storage needs Q1 or P1 (fixed stencil offsets)");
     if (o.storage != MG_STORAGE_AUTO) return o.storage;
-    return elem == MG_Q1 ? MG_STORAGE_DIA : MG_STORAGE_ELL;
+    return vertex_grid ? MG_STORAGE_DIA : MG_STORAGE_ELL;
 }
 
 // Storage chosen by measurement: every candidate format of this level's matrix is built
@@ -1240,15 +1245,15 @@ static double time_format(mg_hierarchy *h, const mgh::Csr &A, int fmt, int dim, 
 static int tune_storage(mg_hierarchy *h, const mgh::Csr &A, int dim, int elem, int N)
 {
     static std::mutex mu;
-    static std::map<std::tuple<int, int, int, int>, int> cache;
-    auto key = std::make_tuple(dim, elem, N, h->inner_size);
+    static std::map<std::tuple<int, int, int, int, bool>, int> cache;
+    auto key = std::make_tuple(dim, elem, N, h->inner_size, h->mass != 0.0);
     {
         std::lock_guard<std::mutex> lk(mu);
         auto it = cache.find(key);
         if (it != cache.end()) return it->second;
     }
     std::vector<int> cands;
-    if (elem == MG_Q1) cands.push_back(MG_STORAGE_DIA);
+    if (elem == MG_Q1 || elem == MG_P1) cands.push_back(MG_STORAGE_DIA);
     cands.push_back(MG_STORAGE_ELL);
     cands.push_back(MG_STORAGE_CSR);
     int best = cands[0];
@@ -1306,7 +1311,7 @@ void mgi::build_hierarchy(mg_hierarchy *h, const mg_problem *p, const mg_options
     if (p->mass != 0.0 && with_vectors) {
         mgh::Csr Mf;
         mgh::assemble(dim, elem, p->n_cells, p->k_cell, Bh);
-        mgh::assemble_mass(dim, p->n_cells, Mf);
+        mgh::assemble_mass(dim, elem, p->n_cells, Mf);
         for (size_t q = 0; q < Bh.val.size(); q++) Bh.val[q] = p->mass * Mf.val[q] - Bh.val[q];
     }
     std::vector<mgh::Csr> &A = HH.A, &P = HH.P, &R = HH.R;
@@ -1339,6 +1344,8 @@ void mgi::build_hierarchy(mg_hierarchy *h, const mg_problem *p, const mg_options
     // ---- multicolour Gauss-Seidel: colour order of every smoothed level ----
     const bool gs = o->smoother == MG_GAUSS_SEIDEL;
     std::vector<std::vector<int32_t>> gs_perm((size_t)nlev);
+    if (gs && mgh::n_colours(dim, elem) == 0)
+        throw Error(MG_EINVAL, "the Gauss-Seidel smoother needs a colouring of the DOFs; P2 has none");
     if (gs)
         for (int l = 1; l <= Lf; l++) {
             if (!mgh::colouring_valid(A[l], dim, elem, h->lev[l].N))
@@ -2120,12 +2127,9 @@ extern "C" mg_status mg_residual_norm_noalloc(mg_hierarchy *h, const double *b_d
         unsigned g = grid_for(n);
         int nn = (int)n;
         if (A.fmt == MG_STORAGE_DIA) {
-            if (A.K == 27)
-                k_residual_noalloc<MG_STORAGE_DIA, 27><<<g, 256, 0, s>>>(v, nn, x_dev, b_dev, r_dev, sc);
-            else if (A.K == 21)
-                k_residual_noalloc<MG_STORAGE_DIA, 21><<<g, 256, 0, s>>>(v, nn, x_dev, b_dev, r_dev, sc);
-            else
-                k_residual_noalloc<MG_STORAGE_DIA, 9><<<g, 256, 0, s>>>(v, nn, x_dev, b_dev, r_dev, sc);
+            with_dia_k(A.K, [&](auto k) {
+                k_residual_noalloc<MG_STORAGE_DIA, decltype(k)::value><<<g, 256, 0, s>>>(v, nn, x_dev, b_dev, r_dev, sc);
+            });
         } else if (A.fmt == MG_STORAGE_ELL) {
             k_residual_noalloc<MG_STORAGE_ELL, 1><<<g, 256, 0, s>>>(v, nn, x_dev, b_dev, r_dev, sc);
         } else {

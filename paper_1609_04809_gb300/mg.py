@@ -14,7 +14,7 @@ from . import _build
 
 MG_OK, MG_PENDING = 0, 1
 MG_EINVAL, MG_ENOMEM, MG_ENOCONV, MG_ECUDA, MG_ETIMEOUT, MG_EBUDGET, MG_ENOTFOUND = -1, -2, -3, -4, -5, -6, -7
-MG_Q1, MG_RQ1 = 0, 1
+MG_Q1, MG_RQ1, MG_P1, MG_P2 = 0, 1, 2, 3
 MG_JACOBI, MG_CHEBYSHEV, MG_GAUSS_SEIDEL = 0, 1, 2
 MG_FP64, MG_MIXED = 0, 1
 MG_STORAGE_AUTO, MG_STORAGE_CSR, MG_STORAGE_ELL, MG_STORAGE_DIA = 0, 1, 2, 3

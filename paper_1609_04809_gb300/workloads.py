@@ -102,10 +102,13 @@ def random_vector(n, seed=0):
 
 
 def ndofs(dim, element, n_cells):
-    """Interior DOF count: Q1 (element 0) vertices, rotated Q1 (element 1) faces."""
+    """Interior DOF count: Q1 (element 0) and P1 (2) vertices, rotated Q1 (1) faces, P2 (3)
+    the points of the grid of 2 n_cells cells."""
     n1 = n_cells - 1
-    if element == 0:
+    if element in (0, 2):
         return n1 ** dim
+    if element == 3:
+        return (2 * n_cells - 1) ** dim
     return 3 * n1 * n_cells * n_cells
 
 
@@ -126,6 +129,18 @@ CONFIGS = {
     "q1_3d_256_vark": dict(dim=3, element=0, n_cells=256, n_levels=7, smoother=1, omega=0.8,
                            cheb_degree=2, nu_pre=1, nu_post=1, tol=1e-10, rhs="const",
                            precision="mixed", k="blocks16"),
+}
+
+
+# The paper's own elements on tetrahedra (P1 and P2 on the Kuhn tetrahedra of the cube
+# grid), at about two million DOFs like the Q1 workload.
+TET_CONFIGS = {
+    "p1_3d_128_cheb": dict(dim=3, element=2, n_cells=128, n_levels=6, smoother=1, omega=0.8,
+                           cheb_degree=2, nu_pre=1, nu_post=1, tol=1e-10, rhs="manufactured",
+                           precision="fp64"),
+    "p2_3d_64_cheb": dict(dim=3, element=3, n_cells=64, n_levels=5, smoother=1, omega=0.8,
+                          cheb_degree=2, nu_pre=1, nu_post=1, tol=1e-10, rhs="manufactured",
+                          precision="fp64"),
 }
 
 

@@ -60,6 +60,10 @@ CASES = [
     (3, 1, 8, 3, None),
     (3, 0, 16, 4, "blocks4"),  # coefficient blocks of 4 cells: the 2-cell level is Galerkin
     (3, 1, 8, 3, "blocks2"),
+    (3, 2, 8, 3, None),        # P1 on Kuhn tetrahedra
+    (3, 2, 16, 4, "blocks4"),
+    (3, 3, 4, 2, None),        # P2
+    (3, 3, 8, 3, "blocks2"),
 ]
 
 
@@ -81,14 +85,15 @@ def test_host_operators_bitwise_equal_oracle(lib, orc, dim, elem, N, L, kind):
             assert _csr_equal(mg.mg_assemble_operator(dim, elem, N, L, l, 2, k), H.R(l)), ("R", l)
 
 
-@pytest.mark.parametrize("dim,N,L,kind", [(2, 16, 3, None), (3, 8, 3, None), (3, 16, 3, "blocks2"), (3, 16, 3, "blocks4")])
-def test_shifted_operators_bitwise_equal_oracle(lib, orc, dim, N, L, kind):
+@pytest.mark.parametrize("dim,elem,N,L,kind", [(2, 0, 16, 3, None), (3, 0, 8, 3, None), (3, 0, 16, 3, "blocks2"),
+                                               (3, 0, 16, 3, "blocks4"), (3, 2, 8, 3, None), (3, 3, 4, 2, None)])
+def test_shifted_operators_bitwise_equal_oracle(lib, orc, dim, elem, N, L, kind):
     """A + sigma M on every level (Crank-Nicolson with dt = 0.01), Galerkin levels included."""
     sigma = 200.0
     k = _k(dim, N, kind)
-    H = orc.Hierarchy(dim, 0, N, L, k_cell=k, mass=sigma)
+    H = orc.Hierarchy(dim, elem, N, L, k_cell=k, mass=sigma)
     for l in range(L):
-        assert _csr_equal(mg.mg_assemble_operator(dim, 0, N, L, l, 0, k, mass=sigma), H.A(l)), ("A", l)
+        assert _csr_equal(mg.mg_assemble_operator(dim, elem, N, L, l, 0, k, mass=sigma), H.A(l)), ("A", l)
 
 
 def test_mass_shift_is_rejected_for_rotated_q1_and_negative_sigma(lib):
@@ -98,7 +103,7 @@ def test_mass_shift_is_rejected_for_rotated_q1_and_negative_sigma(lib):
         mg.mg_assemble_operator(3, 0, 4, 2, 1, 0, mass=-1.0)
 
 
-@pytest.mark.parametrize("dim,elem,N", [(2, 0, 32), (3, 0, 12), (3, 1, 6)])
+@pytest.mark.parametrize("dim,elem,N", [(2, 0, 32), (3, 0, 12), (3, 1, 6), (3, 2, 8), (3, 3, 4)])
 def test_load_vector_bitwise_equal_oracle(lib, orc, dim, elem, N):
     for modes in (W.manufactured_modes(dim), W.random_modes(dim, seed=4), None):
         b1 = mg.mg_load_vector(dim, elem, N, modes=modes, f_const=1.0)
