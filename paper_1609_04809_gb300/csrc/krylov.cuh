@@ -71,8 +71,19 @@ __global__ void __launch_bounds__(256) k_pcg_rz(const double *__restrict__ r, co
 {
     pdl_enter();
     double part = 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        part = __fma_rn(r[i], (double)z[i], part);
+    const int st = gridDim.x * blockDim.x;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    // four rows' loads in flight per thread; the sum runs in the same row order as a
+    // plain grid-stride loop
+    for (; i + 3 * st < n; i += 4 * st) {
+        double r0 = r[i], r1 = r[i + st], r2 = r[i + 2 * st], r3 = r[i + 3 * st];
+        double z0 = (double)z[i], z1 = (double)z[i + st], z2 = (double)z[i + 2 * st], z3 = (double)z[i + 3 * st];
+        part = __fma_rn(r0, z0, part);
+        part = __fma_rn(r1, z1, part);
+        part = __fma_rn(r2, z2, part);
+        part = __fma_rn(r3, z3, part);
+    }
+    for (; i < n; i += st) part = __fma_rn(r[i], (double)z[i], part);
     if (finish_norm(part, partial, ticket, scal + PCG_RZ)) {
         double ro = scal[PCG_RZ_OLD];
         scal[PCG_BETA] = ro == 0.0 ? 0.0 : __ddiv_rn(scal[PCG_RZ], ro);
@@ -113,7 +124,29 @@ __global__ void __launch_bounds__(256) k_pcg_update(double *__restrict__ x, doub
     pdl_enter();
     double alpha = scal[PCG_ALPHA];
     double sq = 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int st = gridDim.x * blockDim.x;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i + 3 * st < n; i += 4 * st) {  // four rows' loads in flight, rows in order
+        double xv[4], pv[4], rv[4], qv[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            int j = i + u * st;
+            xv[u] = x[j];
+            pv[u] = p[j];
+            rv[u] = r[j];
+            qv[u] = q[j];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            int j = i + u * st;
+            x[j] = __dadd_rn(xv[u], __dmul_rn(alpha, pv[u]));
+            double ri = __dsub_rn(rv[u], __dmul_rn(alpha, qv[u]));
+            r[j] = ri;
+            rin[j] = (Tin)ri;
+            sq = __fma_rn(ri, ri, sq);
+        }
+    }
+    for (; i < n; i += st) {
         x[i] = __dadd_rn(x[i], __dmul_rn(alpha, p[i]));
         double ri = __dsub_rn(r[i], __dmul_rn(alpha, q[i]));
         r[i] = ri;

@@ -100,7 +100,16 @@ __global__ void __launch_bounds__(256) k_norm2(const double *__restrict__ v, int
                                                double *norm2)
 {
     double sq = 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) sq = __fma_rn(v[i], v[i], sq);
+    const int st = gridDim.x * blockDim.x;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i + 3 * st < n; i += 4 * st) {  // four loads in flight, rows in order
+        double v0 = v[i], v1 = v[i + st], v2 = v[i + 2 * st], v3 = v[i + 3 * st];
+        sq = __fma_rn(v0, v0, sq);
+        sq = __fma_rn(v1, v1, sq);
+        sq = __fma_rn(v2, v2, sq);
+        sq = __fma_rn(v3, v3, sq);
+    }
+    for (; i < n; i += st) sq = __fma_rn(v[i], v[i], sq);
     finish_norm(sq, partial, ticket, norm2);
 }
 }  // namespace mgk
