@@ -915,3 +915,22 @@ def test_tet_nodal_error_has_the_element_order(orc, elem, Ns, order):
         errs.append(np.max(np.abs(x - u)))
     rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
     assert np.all(rates > order - 0.1), (errs, rates)
+
+
+def test_tet_dof_counts_match_the_paper(orc):
+    """The paper's Sec. 6 counts: its six-level P1 hierarchy (512 -> 16 cells per axis) has
+    6 N^3 tetrahedra and (N+1)^3 nodes per level, and P2 on N cells has the (2N+1)^3 nodes of
+    the grid of 2N cells; the oracle's interior numbering plus the boundary nodes gives them."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "paper_sec6_dof_counts.txt")
+    rows = [l.split(None, 5) for l in open(path) if l.strip() and not l.startswith("#")]
+    assert len(rows) == 4
+    for elem_name, n_cells, cells, dofs, kind, _src in rows:
+        N, cells, dofs = int(n_cells), int(cells), int(dofs)
+        elem = orc.P1 if elem_name == "P1" else orc.P2
+        M = N if elem == orc.P1 else 2 * N  # node grid
+        boundary = (M + 1) ** 3 - (M - 1) ** 3
+        assert orc.ndofs(3, elem, N) + boundary == dofs
+        assert cells == (6 * N ** 3 if kind == "tet" else N ** 3)
+    # the hierarchy: 512 and 16 cells per axis are six levels apart
+    assert 512 >> 5 == 16
