@@ -79,7 +79,9 @@ typedef int mg_status;
 #define MG_STORAGE_AUTO 0 /* chosen by timing the candidates on the device at setup */
 #define MG_STORAGE_CSR 1  /* compressed sparse rows, one thread per row */
 #define MG_STORAGE_ELL 2  /* column-major ELLPACK with explicit 32-bit column indices */
-#define MG_STORAGE_DIA 3  /* column-major ELLPACK whose columns are row + fixed offsets (Q1 only) */
+#define MG_STORAGE_DIA 3  /* column-major ELLPACK whose columns are row + fixed offsets (Q1, P1) */
+#define MG_STORAGE_SELL 4 /* sliced ELLPACK: rows sorted by length, slices of 32 rows stored
+                             column-major with their own width, 32-bit columns */
 
 #define MG_MAX_LEVELS 16
 

@@ -16,9 +16,10 @@ __global__ void __launch_bounds__(256) k_heat_rhs(MatView<double> B, int n, cons
                                                   const double *__restrict__ bF, double t, double *__restrict__ rhs)
 {
     pdl_enter();
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    rhs[i] = __dadd_rn(pcg_row<FMT, K>(B, i, u), __dmul_rn(t, bF[i]));
+    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    int i = fp64_dof<FMT>(B, q);
+    rhs[i] = __dadd_rn(fp64_row<FMT, K>(B, q, i, u), __dmul_rn(t, bF[i]));
 }
 
 }  // namespace mgk

@@ -464,6 +464,43 @@ __device__ __forceinline__ bool finish_norm(double part, double *partial, unsign
     return false;
 }
 
+// Row i (at storage position r) of an FP64 operator applied to the padded vector v:
+// column-ascending fused multiply-adds. FMT: 3 DIA (K slots), 2 ELL, 1 CSR, 4 SELL-32.
+template <int FMT, int K>
+__device__ __forceinline__ double fp64_row(const MatView<double> &A, int r, int i, const double *__restrict__ v)
+{
+    double s = 0.0;
+    if (FMT == 3) {  // DIA
+        double a[K], xv[K];
+#pragma unroll
+        for (int k = 0; k < K; k++) a[k] = __ldcs(A.val + (int64_t)k * A.ld + i);
+#pragma unroll
+        for (int k = 0; k < K; k++) xv[k] = __ldg(v + i + A.offs.o[k]);
+#pragma unroll
+        for (int k = 0; k < K; k++) s = __fma_rn(a[k], xv[k], s);
+    } else if (FMT == 2) {  // ELL
+        for (int k = 0; k < A.K; k++) {
+            int c = __ldcs(A.col + (int64_t)k * A.ld + i);
+            s = __fma_rn(__ldcs(A.val + (int64_t)k * A.ld + i), __ldg(v + c), s);
+        }
+    } else if (FMT == 4) {  // SELL-32
+        int64_t base = A.rowptr[r >> 5];
+        int Ks = (int)((A.rowptr[(r >> 5) + 1] - base) >> 5);
+        int64_t e = base + (r & 31);
+        for (int k = 0; k < Ks; k++, e += 32) s = __fma_rn(__ldcs(A.val + e), __ldg(v + __ldcs(A.col + e)), s);
+    } else {  // CSR
+        for (int64_t k = A.rowptr[i]; k < A.rowptr[i + 1]; k++) s = __fma_rn(A.val[k], __ldg(v + A.col[k]), s);
+    }
+    return s;
+}
+
+// the DOF at storage position r (SELL permutes rows; the other formats do not)
+template <int FMT>
+__device__ __forceinline__ int fp64_dof(const MatView<double> &A, int r)
+{
+    return FMT == 4 ? __ldg(A.perm + r) : r;
+}
+
 template <typename Tin, int FMT, int K>
 __global__ void __launch_bounds__(256) k_outer_resid(MatView<double> A, int n, const double *__restrict__ x,
                                                      const double *__restrict__ b, Tin *__restrict__ r,
@@ -471,25 +508,9 @@ __global__ void __launch_bounds__(256) k_outer_resid(MatView<double> A, int n, c
 {
     pdl_enter();
     double sq = 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        double s = 0.0;
-        if (FMT == 3) {  // DIA
-            double a[K], xv[K];
-#pragma unroll
-            for (int k = 0; k < K; k++) a[k] = __ldcs(A.val + (int64_t)k * A.ld + i);
-#pragma unroll
-            for (int k = 0; k < K; k++) xv[k] = __ldg(x + i + A.offs.o[k]);
-#pragma unroll
-            for (int k = 0; k < K; k++) s = __fma_rn(a[k], xv[k], s);
-        } else if (FMT == 2) {  // ELL
-            for (int k = 0; k < A.K; k++) {
-                int c = __ldcs(A.col + (int64_t)k * A.ld + i);
-                s = __fma_rn(__ldcs(A.val + (int64_t)k * A.ld + i), __ldg(x + c), s);
-            }
-        } else {  // CSR
-            for (int64_t k = A.rowptr[i]; k < A.rowptr[i + 1]; k++) s = __fma_rn(A.val[k], __ldg(x + A.col[k]), s);
-        }
-        double ri = __dsub_rn(b[i], s);
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+        int i = fp64_dof<FMT>(A, q);
+        double ri = __dsub_rn(b[i], fp64_row<FMT, K>(A, q, i, x));
         r[i] = (Tin)ri;
         sq = __fma_rn(ri, ri, sq);
     }

@@ -20,30 +20,6 @@ namespace mgk {
 
 enum PcgScalar { PCG_RZ = 0, PCG_RZ_OLD = 1, PCG_PQ = 2, PCG_ALPHA = 3, PCG_BETA = 4, PCG_NSCAL = 8 };
 
-// row i of the FP64 operator applied to the padded vector v
-template <int FMT, int K>
-__device__ __forceinline__ double pcg_row(const MatView<double> &A, int i, const double *__restrict__ v)
-{
-    double s = 0.0;
-    if (FMT == 3) {  // DIA
-        double a[K], xv[K];
-#pragma unroll
-        for (int k = 0; k < K; k++) a[k] = __ldcs(A.val + (int64_t)k * A.ld + i);
-#pragma unroll
-        for (int k = 0; k < K; k++) xv[k] = __ldg(v + i + A.offs.o[k]);
-#pragma unroll
-        for (int k = 0; k < K; k++) s = __fma_rn(a[k], xv[k], s);
-    } else if (FMT == 2) {  // ELL
-        for (int k = 0; k < A.K; k++) {
-            int c = __ldcs(A.col + (int64_t)k * A.ld + i);
-            s = __fma_rn(__ldcs(A.val + (int64_t)k * A.ld + i), __ldg(v + c), s);
-        }
-    } else {  // CSR
-        for (int64_t k = A.rowptr[i]; k < A.rowptr[i + 1]; k++) s = __fma_rn(A.val[k], __ldg(v + A.col[k]), s);
-    }
-    return s;
-}
-
 // r = b - A x in FP64 (kept in r64 and, in the inner precision, in rin: the V-cycle's
 // right-hand side); p = 0, rz_old = 0; ||r||^2 -> norm2
 template <typename Tin, int FMT, int K>
@@ -54,8 +30,9 @@ __global__ void __launch_bounds__(256) k_pcg_init(MatView<double> A, int n, cons
 {
     pdl_enter();
     double sq = 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        double ri = __dsub_rn(b[i], pcg_row<FMT, K>(A, i, x));
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+        int i = fp64_dof<FMT>(A, q);
+        double ri = __dsub_rn(b[i], fp64_row<FMT, K>(A, q, i, x));
         r64[i] = ri;
         rin[i] = (Tin)ri;
         p[i] = 0.0;
@@ -107,8 +84,9 @@ __global__ void __launch_bounds__(256) k_pcg_apply(MatView<double> A, int n, con
 {
     pdl_enter();
     double part = 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        double s = pcg_row<FMT, K>(A, i, p);
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        int i = fp64_dof<FMT>(A, t);
+        double s = fp64_row<FMT, K>(A, t, i, p);
         q[i] = s;
         part = __fma_rn(p[i], s, part);
     }

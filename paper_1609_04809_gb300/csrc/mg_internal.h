@@ -41,6 +41,9 @@ struct DevMat {
     int full_of[27] = {};// DIA: stencil position (dx+1) + 3(dy+1) + 9(dz+1) of each stored slot
     void *val = nullptr;
     int32_t *col = nullptr;
+    int32_t *perm = nullptr;  // SELL: DOF of each storage position
+    int64_t nslices = 0;      // SELL: slices of 32 rows
+    int64_t padded = 0;       // SELL: stored slots (entries incl. padding)
     int64_t *rowptr = nullptr;
     void *dinv = nullptr;  // 1 / a_ii, FP64 inner levels only
 };

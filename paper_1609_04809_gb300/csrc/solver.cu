@@ -161,6 +161,7 @@ static MatView<T> view(const DevMat &m)
     v.val = (const T *)m.val;
     v.col = m.col;
     v.rowptr = m.rowptr;
+    v.perm = m.perm;
     v.dinv = (const T *)m.dinv;
     v.ld = m.ld;
     v.K = m.K;
@@ -276,7 +277,18 @@ static double mat_bytes(const DevMat &m, int sv)
     switch (m.fmt) {
     case MG_STORAGE_DIA: return (double)m.K * (double)m.n * sv;
     case MG_STORAGE_ELL: return (double)m.K * (double)m.n * (sv + 4);
+    case MG_STORAGE_SELL: return (double)m.padded * (sv + 4) + 8.0 * (double)(m.nslices + 1) + 4.0 * (double)m.n;
     default: return (double)m.nnz * (sv + 4) + 8.0 * (double)(m.n + 1);
+    }
+}
+
+// stored entries one pass over the matrix multiplies (padding included)
+static double mat_entries(const DevMat &m)
+{
+    switch (m.fmt) {
+    case MG_STORAGE_CSR: return (double)m.nnz;
+    case MG_STORAGE_SELL: return (double)m.padded;
+    default: return (double)m.K * (double)m.n;
     }
 }
 
@@ -315,6 +327,8 @@ static void sweep_fmt(const DevMat &A, int n, const T *x, const T *b, T *out, T 
         });
     } else if (A.fmt == MG_STORAGE_ELL) {
         klaunch(pdl, k_ell_sweep<T, MODE>, g, blk, 0, s, v, n, x, b, out, d, c1, c2);
+    } else if (A.fmt == MG_STORAGE_SELL) {
+        klaunch(pdl, k_sell_sweep<T, MODE>, g, blk, 0, s, v, n, x, b, out, d, c1, c2);
     } else {
         klaunch(pdl, k_csr_sweep<T, MODE>, g, blk, 0, s, v, n, x, b, out, d, c1, c2);
     }
@@ -355,7 +369,7 @@ static void sweep(mg_hierarchy *h, int l, int mode, const T *x, const T *b, T *o
     }
     // algorithmic flops: two per stored entry (a multiply-add) plus the update's operations
     static const int kUpdateOps[6] = {1, 4, 4, 6, 2, 2};
-    double entries = L.A.fmt == MG_STORAGE_CSR ? (double)L.A.nnz : (double)L.A.K * n;
+    double entries = mat_entries(L.A);
     double flops = (zero ? 0.0 : 2.0 * entries) + kUpdateOps[mode] * n;
     LaunchScope ls(h, s, kclass, l, bytes, flops);
     int nn = (int)L.n;
@@ -628,7 +642,7 @@ static void enqueue_outer(mg_hierarchy *h, cudaStream_t s)
     const DevMat &A = h->A64;
     int n = (int)F.n;
     double bytes = mat_bytes(A, 8) + 16.0 * n + (double)n * sizeof(T);
-    double entries = A.fmt == MG_STORAGE_CSR ? (double)A.nnz : (double)A.K * n;
+    double entries = mat_entries(A);
     LaunchScope ls(h, s, MG_K_OUTER, h->Lf, bytes, 2.0 * entries + 3.0 * n);
     MatView<double> v = view<double>(A);
     dim3 g(reduce_grid(n)), blk(256);
@@ -642,6 +656,8 @@ static void enqueue_outer(mg_hierarchy *h, cudaStream_t s)
         });
     } else if (A.fmt == MG_STORAGE_ELL) {
         klaunch(pdl, k_outer_resid<T, 2, 1>, g, blk, 0, s, v, n, x, b, r, h->partial, h->ticket, h->norm2);
+    } else if (A.fmt == MG_STORAGE_SELL) {
+        klaunch(pdl, k_outer_resid<T, 4, 1>, g, blk, 0, s, v, n, x, b, r, h->partial, h->ticket, h->norm2);
     } else {
         klaunch(pdl, k_outer_resid<T, 1, 1>, g, blk, 0, s, v, n, x, b, r, h->partial, h->ticket, h->norm2);
     }
@@ -683,6 +699,8 @@ static void launch_fp64_rows(mg_hierarchy *h, const DevMat &A, MK &&mk)
         with_dia_k(A.K, [&](auto k) { mk(std::integral_constant<int, 3>(), k); });
     } else if (A.fmt == MG_STORAGE_ELL) {
         mk(std::integral_constant<int, 2>(), std::integral_constant<int, 1>());
+    } else if (A.fmt == MG_STORAGE_SELL) {
+        mk(std::integral_constant<int, 4>(), std::integral_constant<int, 1>());
     } else {
         mk(std::integral_constant<int, 1>(), std::integral_constant<int, 1>());
     }
@@ -695,7 +713,7 @@ static void enqueue_pcg_init(mg_hierarchy *h, cudaStream_t s)
     LevelD &F = h->lev[h->Lf];
     const DevMat &A = h->A64;
     int n = (int)F.n;
-    double entries = A.fmt == MG_STORAGE_CSR ? (double)A.nnz : (double)A.K * n;
+    double entries = mat_entries(A);
     LaunchScope ls(h, s, MG_K_OUTER, h->Lf, mat_bytes(A, 8) + 32.0 * n + (double)n * sizeof(T),
                    2.0 * entries + 3.0 * n);
     MatView<double> v = view<double>(A);
@@ -730,7 +748,7 @@ static void enqueue_pcg_iter(mg_hierarchy *h, cudaStream_t s)
         klaunch(pdl, k_pcg_dir<T>, g, blk, 0, s, z, h->pcg_p, n, (const double *)h->pcg_scal);
     }
     {
-        double entries = A.fmt == MG_STORAGE_CSR ? (double)A.nnz : (double)A.K * n;
+        double entries = mat_entries(A);
         LaunchScope ls(h, s, MG_K_KRYLOV, h->Lf, mat_bytes(A, 8) + 16.0 * n, 2.0 * entries + 2.0 * n);
         MatView<double> v = view<double>(A);
         launch_fp64_rows(h, A, [&](auto fmt, auto k) {
@@ -975,6 +993,25 @@ extern "C" mg_status mg_load_vector_separable(const mg_problem *p, const mg_rhs 
 }
 
 // device format of a level operator
+// SELL-32 layout: rows sorted by length, longest first (ties by row index), slices of 32
+// positions; slice s holds 32 * K_s slots from sptr[s] (K_s = its longest row).
+static void sell_layout(const mgh::Csr &A, std::vector<int32_t> &perm, std::vector<int64_t> &sptr)
+{
+    int64_t n = A.nrows;
+    perm.resize((size_t)n);
+    for (int64_t i = 0; i < n; i++) perm[i] = (int32_t)i;
+    std::stable_sort(perm.begin(), perm.end(), [&](int32_t a, int32_t b) {
+        return A.rowptr[a + 1] - A.rowptr[a] > A.rowptr[b + 1] - A.rowptr[b];
+    });
+    int64_t ns = (n + 31) / 32;
+    sptr.assign((size_t)ns + 1, 0);
+    for (int64_t s = 0; s < ns; s++) {
+        int32_t first = perm[(size_t)s * 32];
+        int64_t Ks = std::max<int64_t>(A.rowptr[first + 1] - A.rowptr[first], 1);
+        sptr[s + 1] = sptr[s] + 32 * Ks;
+    }
+}
+
 static void plan_matrix(DevMat &m, const mgh::Csr &A, int fmt, int dim, int N, int sv, mgi::Slab &slab, bool take)
 {
     m.fmt = fmt;
@@ -1028,6 +1065,26 @@ static void plan_matrix(DevMat &m, const mgh::Csr &A, int fmt, int dim, int N, i
             m.val = slab.take(bytes);
         else
             slab.reserve(bytes);
+    } else if (fmt == MG_STORAGE_SELL) {
+        std::vector<int32_t> perm;
+        std::vector<int64_t> sptr;
+        sell_layout(A, perm, sptr);
+        m.nslices = (int64_t)sptr.size() - 1;
+        m.padded = sptr.back();
+        m.K = (int)(m.nslices ? (sptr[1] - sptr[0]) / 32 : 1);  // the widest slice
+        size_t vb = (size_t)std::max<int64_t>(m.padded, 1) * sv, cb = (size_t)std::max<int64_t>(m.padded, 1) * 4,
+               sb = (size_t)(m.nslices + 1) * 8, pb = (size_t)std::max<int64_t>(m.n, 1) * 4;
+        if (take) {
+            m.val = slab.take(vb);
+            m.col = (int32_t *)slab.take(cb);
+            m.rowptr = (int64_t *)slab.take(sb);
+            m.perm = (int32_t *)slab.take(pb);
+        } else {
+            slab.reserve(vb);
+            slab.reserve(cb);
+            slab.reserve(sb);
+            slab.reserve(pb);
+        }
     } else if (fmt == MG_STORAGE_ELL) {
         int K = 0;
         for (int64_t i = 0; i < A.nrows; i++) K = std::max<int>(K, (int)(A.rowptr[i + 1] - A.rowptr[i]));
@@ -1077,6 +1134,33 @@ static void upload_matrix(const DevMat &m, const mgh::Csr &A, const std::vector<
             }
         }
         CK(cudaMemcpyAsync(m.val, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+        CK(cudaStreamSynchronize(s));
+    } else if (m.fmt == MG_STORAGE_SELL) {
+        std::vector<int32_t> perm;
+        std::vector<int64_t> sptr;
+        sell_layout(A, perm, sptr);
+        std::vector<T> v((size_t)std::max<int64_t>(m.padded, 1), T(0));
+        std::vector<int32_t> c((size_t)std::max<int64_t>(m.padded, 1), 0);
+#pragma omp parallel for schedule(static)
+        for (int64_t r = 0; r < m.nslices * 32; r++) {
+            int64_t sl = r / 32, lane = r % 32, Ks = (sptr[sl + 1] - sptr[sl]) / 32;
+            int64_t i = r < A.nrows ? perm[r] : -1;
+            int64_t len = i >= 0 ? A.rowptr[i + 1] - A.rowptr[i] : 0;
+            int32_t pad = (int32_t)(i >= 0 ? i : perm[(size_t)sl * 32]);  // lanes past n: any valid column
+            for (int64_t k = 0; k < Ks; k++) {
+                size_t e = (size_t)(sptr[sl] + 32 * k + lane);
+                if (k < len) {
+                    c[e] = A.col[A.rowptr[i] + k];
+                    v[e] = vals[A.rowptr[i] + k];
+                } else {
+                    c[e] = pad;
+                }
+            }
+        }
+        CK(cudaMemcpyAsync(m.val, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(m.col, c.data(), c.size() * 4, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(m.rowptr, sptr.data(), sptr.size() * 8, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(m.perm, perm.data(), perm.size() * 4, cudaMemcpyHostToDevice, s));
         CK(cudaStreamSynchronize(s));
     } else if (m.fmt == MG_STORAGE_ELL) {
         std::vector<T> v((size_t)m.K * m.ld, T(0));
@@ -1265,6 +1349,7 @@ static int tune_storage(mg_hierarchy *h, const mgh::Csr &A, int dim, int elem, i
     if (elem == MG_Q1 || elem == MG_P1) cands.push_back(MG_STORAGE_DIA);
     cands.push_back(MG_STORAGE_ELL);
     cands.push_back(MG_STORAGE_CSR);
+    if (elem == MG_RQ1 || elem == MG_P2) cands.push_back(MG_STORAGE_SELL);  // uneven rows (P2) or no DIA
     int best = cands[0];
     double best_ms = 1e300;
     for (int f : cands) {
@@ -1290,7 +1375,7 @@ void mgi::build_hierarchy(mg_hierarchy *h, const mg_problem *p, const mg_options
         throw Error(MG_EINVAL, "bad Chebyshev parameters");
     if (o->nu_pre < 0 || o->nu_post < 0 || o->max_iters < 0) throw Error(MG_EINVAL, "negative counts");
     if (o->precision != MG_FP64 && o->precision != MG_MIXED) throw Error(MG_EINVAL, "bad precision");
-    if (o->storage < MG_STORAGE_AUTO || o->storage > MG_STORAGE_DIA) throw Error(MG_EINVAL, "bad storage");
+    if (o->storage < MG_STORAGE_AUTO || o->storage > MG_STORAGE_SELL) throw Error(MG_EINVAL, "bad storage");
     h->prob = *p;
     h->prob.k_cell = nullptr;
     h->opt = *o;
@@ -1392,8 +1477,8 @@ void mgi::build_hierarchy(mg_hierarchy *h, const mg_problem *p, const mg_options
             L.fmt = lf;
             plan_matrix(L.A, A[l], lf, dim, L.N, sv, S, take);
             if (!h->mixed && l >= 1) L.A.dinv = vec((size_t)L.A.ld * 8);  // FP64 smoothers read D^-1
-            if (gs && l >= 1) {  // the colour-major copy of A for the Gauss-Seidel sweeps
-                plan_matrix(L.G, A[l], lf, dim, L.N, sv, S, take);
+            if (gs && l >= 1) {  // the colour-major copy of A for the Gauss-Seidel sweeps (CSR for SELL levels)
+                plan_matrix(L.G, A[l], lf == MG_STORAGE_SELL ? MG_STORAGE_CSR : lf, dim, L.N, sv, S, take);
                 if (!h->mixed) L.G.dinv = vec((size_t)L.G.ld * 8);
                 L.perm = (int32_t *)vec((size_t)std::max<int64_t>(L.G.n, 1) * 4);
             }
@@ -1792,7 +1877,7 @@ static mg_status heat_internal(mg_hierarchy *h, const double *g, int n_steps, do
         double t = g[k] + g[k + 1];
         {
             const DevMat &B = h->B64;
-            double entries = B.fmt == MG_STORAGE_CSR ? (double)B.nnz : (double)B.K * n;
+            double entries = mat_entries(B);
             LaunchScope ls(h, h->s, MG_K_OUTER, h->Lf, mat_bytes(B, 8) + 24.0 * n, 2.0 * entries + 2.0 * n);
             launch_fp64_rows(h, B, [&](auto fmt, auto kk) {
                 klaunch(pdl, k_heat_rhs<decltype(fmt)::value, decltype(kk)::value>, dim3(grid_for(n)), dim3(256), 0,
@@ -1932,6 +2017,33 @@ static void export_dev(const DevMat &m, int dim, int N, int sv, mgh::Csr &out)
         out.col.resize((size_t)m.nnz);
         CK(cudaMemcpy(out.col.data(), m.col, m.nnz * 4, cudaMemcpyDeviceToHost));
         out.val = sv == 8 ? download_vals<double>(m, (size_t)m.nnz) : download_vals<float>(m, (size_t)m.nnz);
+        return;
+    }
+    if (m.fmt == MG_STORAGE_SELL) {  // back to rows in DOF order, padding dropped
+        std::vector<double> v = sv == 8 ? download_vals<double>(m, (size_t)m.padded) : download_vals<float>(m, (size_t)m.padded);
+        std::vector<int32_t> c((size_t)m.padded), perm((size_t)m.n);
+        std::vector<int64_t> sptr((size_t)m.nslices + 1);
+        CK(cudaMemcpy(c.data(), m.col, c.size() * 4, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(perm.data(), m.perm, perm.size() * 4, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(sptr.data(), m.rowptr, sptr.size() * 8, cudaMemcpyDeviceToHost));
+        std::vector<std::vector<std::pair<int32_t, double>>> rows((size_t)m.n);
+        for (int64_t r = 0; r < m.n; r++) {
+            int64_t sl = r / 32, Ks = (sptr[sl + 1] - sptr[sl]) / 32;
+            int32_t prev = -1;
+            for (int64_t k = 0; k < Ks; k++) {
+                size_t e = (size_t)(sptr[sl] + 32 * k + r % 32);
+                if (c[e] <= prev) break;  // padding (column i after larger columns)
+                prev = c[e];
+                rows[perm[r]].push_back({c[e], v[e]});
+            }
+        }
+        for (int64_t i = 0; i < m.n; i++) {
+            for (auto &e : rows[i]) {
+                out.col.push_back(e.first);
+                out.val.push_back(e.second);
+            }
+            out.rowptr[i + 1] = (int64_t)out.col.size();
+        }
         return;
     }
     size_t cnt = (size_t)m.K * m.ld;
@@ -2074,9 +2186,10 @@ __global__ void __launch_bounds__(256) k_residual_noalloc(MatView<double> A, int
                                                           const double *__restrict__ b, double *__restrict__ r,
                                                           NoallocScratch *sc)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int q = blockIdx.x * blockDim.x + threadIdx.x;  // storage position (the DOF but for SELL)
     double sq = 0.0;
-    if (i < n) {
+    if (q < n) {
+        int i = FMT == MG_STORAGE_SELL ? __ldg(A.perm + q) : q;
         double s = 0.0;
         if (FMT == MG_STORAGE_DIA) {
 #pragma unroll
@@ -2090,6 +2203,11 @@ __global__ void __launch_bounds__(256) k_residual_noalloc(MatView<double> A, int
                 int c = __ldcs(A.col + (int64_t)k * A.ld + i);
                 s = __fma_rn(__ldcs(A.val + (int64_t)k * A.ld + i), __ldg(x + c), s);
             }
+        } else if (FMT == MG_STORAGE_SELL) {
+            int64_t base = A.rowptr[q >> 5];
+            int Ks = (int)((A.rowptr[(q >> 5) + 1] - base) >> 5);
+            int64_t e = base + (q & 31);
+            for (int k = 0; k < Ks; k++, e += 32) s = __fma_rn(__ldcs(A.val + e), __ldg(x + __ldcs(A.col + e)), s);
         } else {
             for (int64_t k = A.rowptr[i]; k < A.rowptr[i + 1]; k++) s = __fma_rn(A.val[k], __ldg(x + A.col[k]), s);
         }
@@ -2141,6 +2259,8 @@ extern "C" mg_status mg_residual_norm_noalloc(mg_hierarchy *h, const double *b_d
             });
         } else if (A.fmt == MG_STORAGE_ELL) {
             k_residual_noalloc<MG_STORAGE_ELL, 1><<<g, 256, 0, s>>>(v, nn, x_dev, b_dev, r_dev, sc);
+        } else if (A.fmt == MG_STORAGE_SELL) {
+            k_residual_noalloc<MG_STORAGE_SELL, 1><<<g, 256, 0, s>>>(v, nn, x_dev, b_dev, r_dev, sc);
         } else {
             k_residual_noalloc<MG_STORAGE_CSR, 1><<<g, 256, 0, s>>>(v, nn, x_dev, b_dev, r_dev, sc);
         }

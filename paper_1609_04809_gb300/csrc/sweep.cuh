@@ -62,10 +62,11 @@ struct DiaOffs {
 // Matrix view for the kernels (values of type T).
 template <typename T>
 struct MatView {
-    const T *val;          // DIA/ELL: K*ld (slot-major); CSR: nnz
-    const int32_t *col;    // ELL: K*ld; CSR: nnz
-    const int64_t *rowptr; // CSR
-    const T *dinv;         // 1 / a_ii (FP64 levels)
+    const T *val;          // DIA/ELL: K*ld (slot-major); CSR: nnz; SELL: padded slices
+    const int32_t *col;    // ELL: K*ld; CSR: nnz; SELL: padded slices
+    const int64_t *rowptr; // CSR: row starts; SELL: slice starts (entries)
+    const int32_t *perm;   // SELL: DOF of storage position r
+    const T *dinv;         // 1 / a_ii (FP64 levels), by DOF
     int64_t ld;
     int K;
     int center;            // DIA: slot of the diagonal
@@ -172,6 +173,35 @@ __global__ void __launch_bounds__(256) k_csr_sweep(MatView<T> A, int n, const T 
         }
     }
     T dinv = Ar<T>::kStoredDinv ? A.dinv[i] : Ar<T>::rcp(diag);
+    sweep_out<T, MODE>(i, s, dinv, IsZero<MODE>::value ? T(0) : x[i], b, out, d, c1, c2);
+}
+
+// SELL-32: storage position r (rows sorted by length, slices of 32 rows) holds DOF
+// perm[r]; slice s stores its rows column-major with K_s slots, K_s = its longest row,
+// so slot k of position r is entry rowptr[s] + 32 k + (r mod 32). Each row keeps its CSR
+// order (columns ascending); padded slots hold column perm[r] and value 0.
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256) k_sell_sweep(MatView<T> A, int n, const T *__restrict__ x,
+                                                    const T *__restrict__ b, T *__restrict__ out,
+                                                    T *__restrict__ d, T c1, T c2)
+{
+    pdl_enter();
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    int i = __ldg(A.perm + r);
+    T s = T(0), diag = T(0);
+    if (!IsZero<MODE>::value || !Ar<T>::kStoredDinv) {
+        int64_t base = A.rowptr[r >> 5];
+        int Ks = (int)((A.rowptr[(r >> 5) + 1] - base) >> 5);
+        int64_t e = base + (r & 31);
+        for (int k = 0; k < Ks; k++, e += 32) {
+            int c = __ldcs(A.col + e);
+            T v = __ldcs(A.val + e);
+            if (c == i && diag == T(0)) diag = v;
+            if (!IsZero<MODE>::value) s = Ar<T>::mac(s, v, __ldg(x + c));
+        }
+    }
+    T dinv = Ar<T>::kStoredDinv ? __ldcs(A.dinv + i) : Ar<T>::rcp(diag);
     sweep_out<T, MODE>(i, s, dinv, IsZero<MODE>::value ? T(0) : x[i], b, out, d, c1, c2);
 }
 

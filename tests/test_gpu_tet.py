@@ -136,3 +136,30 @@ def test_tet_full_size_workloads(orc, name):
     X = orc.node_coords(elem, N)
     err = np.max(np.abs(x.cpu().numpy() - np.prod(np.sin(np.pi * X), axis=1)))
     assert err < (4e-4 if elem == mg.MG_P1 else 2e-6), err  # about 2.5e-4 and 2e-7 extrapolated
+
+
+@pytest.mark.parametrize("elem,N,L", [(3, 8, 3), (1, 8, 3), (0, 16, 3), (2, 16, 3)])
+@pytest.mark.parametrize("precision", [mg.MG_FP64, mg.MG_MIXED])
+def test_sell_storage(orc, elem, N, L, precision):
+    """SELL-32 (rows sorted by length, slices of 32) on every element: FP64 bitwise; mixed
+    converged; exported operator equal to the host one; CG and the no-allocation residual
+    read it too."""
+    b = W.random_vector(mg.mg_ndofs(3, elem, N), seed=91)
+    H, O, g, o = _both(orc, elem, N, L, b, storage=mg.MG_STORAGE_SELL, precision=precision, omega=0.7)
+    assert H.info()["storage"][L - 1] == mg.MG_STORAGE_SELL
+    assert g[0] == mg.MG_OK
+    if precision == mg.MG_FP64:
+        assert g[1] == o[1] and np.array_equal(g[3], o[3])
+        rp, col, val, _ = mg.mg_export_operator(H.h, L - 1, 0, mg.MG_FP64)
+        A = O.A(L - 1)
+        assert np.array_equal(rp, A.rowptr) and np.array_equal(col, A.col) and np.array_equal(val, A.val)
+        bd = torch.from_numpy(b).cuda()
+        x = torch.zeros_like(bd)
+        st, it, hist = H.pcg(bd, x, 1e-10)
+        xo, ho, ito, conv = O.pcg(b, 1e-10)
+        assert st == mg.MG_OK and np.linalg.norm(x.cpu().numpy() - xo) <= 1e-9 * np.linalg.norm(xo)
+        r = torch.empty_like(bd)
+        nr = mg.mg_residual_norm_noalloc(H.h, bd, x, r)
+        assert abs(nr - np.linalg.norm(b - orc.spmv(A, x.cpu().numpy()))) <= 1e-12 * np.linalg.norm(b)
+    else:
+        assert np.linalg.norm(b - orc.spmv(O.A(L - 1), g[3])) <= 1e-10 * np.linalg.norm(b)
