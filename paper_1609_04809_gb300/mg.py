@@ -365,7 +365,7 @@ def mg_cycle(h, b_dev, x_dev, n_cycles):
 
 
 def mg_export_operator(h, level, which, precision=MG_FP64):
-    """Level operator as (rowptr, col, val, shape): which 0 = A, 1 = P, 2 = R."""
+    """Level operator as (rowptr, col, val): which 0 = A, 1 = P, 2 = R."""
     L = lib()
     nrows, nnz = ctypes.c_int64(0), ctypes.c_int64(0)
     _check(L.mg_export_operator(h, level, which, precision, ctypes.byref(nrows), ctypes.byref(nnz),

@@ -150,7 +150,7 @@ def test_sell_storage(orc, elem, N, L, precision):
     assert g[0] == mg.MG_OK
     if precision == mg.MG_FP64:
         assert g[1] == o[1] and np.array_equal(g[3], o[3])
-        rp, col, val, _ = mg.mg_export_operator(H.h, L - 1, 0, mg.MG_FP64)
+        rp, col, val = mg.mg_export_operator(H.h, L - 1, 0, mg.MG_FP64)
         A = O.A(L - 1)
         assert np.array_equal(rp, A.rowptr) and np.array_equal(col, A.col) and np.array_equal(val, A.val)
         bd = torch.from_numpy(b).cuda()
