@@ -422,11 +422,13 @@ __device__ __forceinline__ double block_sum(double v, double *sh)
     return s;  // valid in thread 0
 }
 
-// Grid of the kernels that end in a reduction: a fixed number of blocks (8 per SM of
-// GB300's 152) stepping through the rows, so that the per-block ticket of finish_norm
-// is taken 1216 times instead of once per 256 rows; a constant keeps the summation
-// order, hence the bits, independent of the device.
-constexpr int kReduceBlocks = 1216;
+// Grid of the kernels that end in a reduction: a fixed number of blocks stepping through
+// the rows, so that the per-block ticket of finish_norm is taken 912 times instead of
+// once per 256 rows. 912 = 6 blocks on each of GB300's 152 SMs, the residency those
+// kernels are compiled for (__launch_bounds__(256, 6): up to 42 registers, no spills), so
+// the grid is exactly one wave; a constant keeps the summation order, hence the bits,
+// independent of the device.
+constexpr int kReduceBlocks = 912;
 
 // Sum of `part` over the grid in a fixed order: block sums to partial[], the last block
 // to finish (ticket) adds them up. Returns true in the thread that wrote *out.
@@ -502,7 +504,7 @@ __device__ __forceinline__ int fp64_dof(const MatView<double> &A, int r)
 }
 
 template <typename Tin, int FMT, int K>
-__global__ void __launch_bounds__(256) k_outer_resid(MatView<double> A, int n, const double *__restrict__ x,
+__global__ void __launch_bounds__(256, 6) k_outer_resid(MatView<double> A, int n, const double *__restrict__ x,
                                                      const double *__restrict__ b, Tin *__restrict__ r,
                                                      double *partial, unsigned *ticket, double *norm2)
 {

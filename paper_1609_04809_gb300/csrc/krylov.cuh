@@ -23,7 +23,7 @@ enum PcgScalar { PCG_RZ = 0, PCG_RZ_OLD = 1, PCG_PQ = 2, PCG_ALPHA = 3, PCG_BETA
 // r = b - A x in FP64 (kept in r64 and, in the inner precision, in rin: the V-cycle's
 // right-hand side); p = 0, rz_old = 0; ||r||^2 -> norm2
 template <typename Tin, int FMT, int K>
-__global__ void __launch_bounds__(256) k_pcg_init(MatView<double> A, int n, const double *__restrict__ x,
+__global__ void __launch_bounds__(256, 6) k_pcg_init(MatView<double> A, int n, const double *__restrict__ x,
                                                   const double *__restrict__ b, double *__restrict__ r64,
                                                   Tin *__restrict__ rin, double *__restrict__ p, double *scal,
                                                   double *partial, unsigned *ticket, double *norm2)
@@ -43,7 +43,7 @@ __global__ void __launch_bounds__(256) k_pcg_init(MatView<double> A, int n, cons
 }
 
 template <typename Tin>
-__global__ void __launch_bounds__(256) k_pcg_rz(const double *__restrict__ r, const Tin *__restrict__ z, int n,
+__global__ void __launch_bounds__(256, 6) k_pcg_rz(const double *__restrict__ r, const Tin *__restrict__ z, int n,
                                                 double *partial, unsigned *ticket, double *scal)
 {
     pdl_enter();
@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(256) k_pcg_dir(const Tin *__restrict__ z, doub
 }
 
 template <int FMT, int K>
-__global__ void __launch_bounds__(256) k_pcg_apply(MatView<double> A, int n, const double *__restrict__ p,
+__global__ void __launch_bounds__(256, 6) k_pcg_apply(MatView<double> A, int n, const double *__restrict__ p,
                                                    double *__restrict__ q, double *partial, unsigned *ticket,
                                                    double *scal)
 {
@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(256) k_pcg_apply(MatView<double> A, int n, con
 }
 
 template <typename Tin>
-__global__ void __launch_bounds__(256) k_pcg_update(double *__restrict__ x, double *__restrict__ r,
+__global__ void __launch_bounds__(256, 6) k_pcg_update(double *__restrict__ x, double *__restrict__ r,
                                                     Tin *__restrict__ rin, const double *__restrict__ p,
                                                     const double *__restrict__ q, int n, double *scal,
                                                     double *partial, unsigned *ticket, double *norm2)
@@ -104,10 +104,10 @@ __global__ void __launch_bounds__(256) k_pcg_update(double *__restrict__ x, doub
     double sq = 0.0;
     const int st = gridDim.x * blockDim.x;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    for (; i + 3 * st < n; i += 4 * st) {  // four rows' loads in flight, rows in order
-        double xv[4], pv[4], rv[4], qv[4];
+    for (; i + st < n; i += 2 * st) {  // two rows' loads in flight (eight loads), rows in order
+        double xv[2], pv[2], rv[2], qv[2];
 #pragma unroll
-        for (int u = 0; u < 4; u++) {
+        for (int u = 0; u < 2; u++) {
             int j = i + u * st;
             xv[u] = x[j];
             pv[u] = p[j];
@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(256) k_pcg_update(double *__restrict__ x, doub
             qv[u] = q[j];
         }
 #pragma unroll
-        for (int u = 0; u < 4; u++) {
+        for (int u = 0; u < 2; u++) {
             int j = i + u * st;
             x[j] = __dadd_rn(xv[u], __dmul_rn(alpha, pv[u]));
             double ri = __dsub_rn(rv[u], __dmul_rn(alpha, qv[u]));

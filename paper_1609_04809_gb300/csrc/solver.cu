@@ -96,7 +96,7 @@ __global__ void k_lu_factor(double *a, int n, int *piv, int *info)
     }
 }
 
-__global__ void __launch_bounds__(256) k_norm2(const double *__restrict__ v, int n, double *partial, unsigned *ticket,
+__global__ void __launch_bounds__(256, 6) k_norm2(const double *__restrict__ v, int n, double *partial, unsigned *ticket,
                                                double *norm2)
 {
     double sq = 0.0;
