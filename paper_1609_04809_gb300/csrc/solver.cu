@@ -126,6 +126,14 @@ static inline unsigned grid_for(int64_t n) { return (unsigned)((n + 255) / 256);
 // grid of a kernel that ends in a block-partial reduction (finish_norm)
 static inline unsigned reduce_grid(int64_t n) { return std::min<unsigned>(std::max<unsigned>(grid_for(n), 1u), kReduceBlocks); }
 
+// threads per block of a row sweep: 256, or 64 below two blocks of 256 per SM of the 152,
+// so that the few rows of a small level spread over every SM (rows are independent)
+static inline unsigned sweep_block(int64_t n) { return n < 152 * 256 * 2 ? 64u : 256u; }
+
+// threads per block of a transfer over grid lines of l1 points: the line rounded up to
+// whole warps, at most 128 (a 128-thread block over a 63-point line idles half its threads)
+static inline unsigned line_block(unsigned l1) { return std::min(128u, std::max(32u, (l1 + 31) / 32 * 32)); }
+
 // f(std::integral_constant<int, K>()) for the stored slot count K of a DIA matrix: the
 // instantiated counts are 7 and 15 (P1, P1 + mass), 9 (2D Q1), 21 and 27 (3D Q1).
 template <typename F>
@@ -320,7 +328,8 @@ static void sweep_fmt(const DevMat &A, int n, const T *x, const T *b, T *out, T 
                       bool pdl = false)
 {
     MatView<T> v = view<T>(A);
-    dim3 g(grid_for(n)), blk(256);
+    unsigned bs = sweep_block(n);
+    dim3 g((unsigned)((n + bs - 1) / bs)), blk(bs);
     if (A.fmt == MG_STORAGE_DIA) {
         with_dia_k(A.K, [&](auto k) {
             klaunch(pdl, k_dia_sweep<T, decltype(k)::value, MODE>, g, blk, 0, s, v, n, x, b, out, d, c1, c2);
@@ -411,7 +420,8 @@ static void gs_sweep(mg_hierarchy *h, int l, T *x, bool post, cudaStream_t s)
         double bytes = slice + nr * (4.0 + 3.0 * sv + (G.dinv ? sv : 0));
         double entries = G.fmt == MG_STORAGE_CSR ? (double)L.nnz * nr / std::max<int64_t>(L.n, 1) : (double)G.K * nr;
         LaunchScope ls(h, s, MG_K_SMOOTH, l, bytes, 2.0 * entries + 4.0 * nr);
-        dim3 g((unsigned)((nr + 255) / 256)), blk(256);
+        unsigned bs = sweep_block(nr);
+        dim3 g((unsigned)((nr + bs - 1) / bs)), blk(bs);
         if (G.fmt == MG_STORAGE_DIA) {
             with_dia_k(G.K, [&](auto k) {
                 klaunch(pdl, k_gs_dia<T, decltype(k)::value>, g, blk, 0, s, v, (const int32_t *)L.perm, r0, nr, x, b);
@@ -476,13 +486,13 @@ static void restrict_to(mg_hierarchy *h, int l, const T *r, cudaStream_t s)
     if (!F.structured) bytes += mat_bytes(F.R, sv);
     LaunchScope ls(h, s, MG_K_RESTRICT, l, bytes);
     if (F.structured) {
-        unsigned l1 = (unsigned)(C.N - 1);
-        dim3 g((l1 + 127) / 128, l1, h->dim == 3 ? l1 : 1);
+        unsigned l1 = (unsigned)(C.N - 1), bx = line_block(l1);
+        dim3 g((l1 + bx - 1) / bx, l1, h->dim == 3 ? l1 : 1);
         bool pdl = h->opt.use_pdl != 0;
         if (h->dim == 3)
-            klaunch(pdl, k_restrict_q1<T, 3>, g, dim3(128), 0, s, r, (T *)C.b, C.N);
+            klaunch(pdl, k_restrict_q1<T, 3>, g, dim3(bx), 0, s, r, (T *)C.b, C.N);
         else
-            klaunch(pdl, k_restrict_q1<T, 2>, g, dim3(128), 0, s, r, (T *)C.b, C.N);
+            klaunch(pdl, k_restrict_q1<T, 2>, g, dim3(bx), 0, s, r, (T *)C.b, C.N);
     } else {
         klaunch(h->opt.use_pdl != 0, k_csr_apply<T, false>, dim3(grid_for(C.n)), dim3(256), 0, s,
                 (const int64_t *)F.R.rowptr, (const int32_t *)F.R.col, (const T *)F.R.val, (int)C.n, r, (T *)C.b);
@@ -507,13 +517,13 @@ static void prolong_add(mg_hierarchy *h, int l, const T *xc, T *xf, cudaStream_t
     if (!F.structured) bytes += mat_bytes(F.P, sv);
     LaunchScope ls(h, s, MG_K_PROLONG, l, bytes);
     if (F.structured) {
-        unsigned l1 = (unsigned)(F.N - 1);
-        dim3 g((l1 + 127) / 128, l1, h->dim == 3 ? l1 : 1);
+        unsigned l1 = (unsigned)(F.N - 1), bx = line_block(l1);
+        dim3 g((l1 + bx - 1) / bx, l1, h->dim == 3 ? l1 : 1);
         bool pdl = h->opt.use_pdl != 0;
         if (h->dim == 3)
-            klaunch(pdl, k_prolong_q1<T, 3>, g, dim3(128), 0, s, xc, xf, C.N);
+            klaunch(pdl, k_prolong_q1<T, 3>, g, dim3(bx), 0, s, xc, xf, C.N);
         else
-            klaunch(pdl, k_prolong_q1<T, 2>, g, dim3(128), 0, s, xc, xf, C.N);
+            klaunch(pdl, k_prolong_q1<T, 2>, g, dim3(bx), 0, s, xc, xf, C.N);
     } else {
         klaunch(h->opt.use_pdl != 0, k_csr_apply<T, true>, dim3(grid_for(F.n)), dim3(256), 0, s,
                 (const int64_t *)F.P.rowptr, (const int32_t *)F.P.col, (const T *)F.P.val, (int)F.n, xc, xf);
