@@ -61,28 +61,38 @@ __global__ void __launch_bounds__(128) k_restrict_q1(const T *__restrict__ r, T 
 // with |v - 2V| <= 1 per axis (boundary ones are zero and skipped), ascending coarse index.
 // Every such V carries the same weight prod_d (1 or 1/2) = 2^-(number of odd coordinates
 // of v), taken from a table: no floating-point work beyond one multiply-add per term.
-// Launch: x-lines of the fine grid, grid (ceil(nf1/blockDim), nf1, DIM == 3 ? nf1 : 1).
+// Thread m of a fine x-line computes the pair v0 = 2m (coarse X = m) and v0 = 2m + 1
+// (X = m, m + 1) from the same coarse loads: every lane runs the same loop, where one
+// thread per fine point would alternate one and two X terms within a warp.
+// Launch: grid (ceil(Nc/blockDim), nf1, DIM == 3 ? nf1 : 1), m = 0..Nc-1.
 template <typename T, int DIM>
 __global__ void __launch_bounds__(128) k_prolong_q1(const T *__restrict__ xc, T *__restrict__ xf, int Nc)
 {
     pdl_enter();
     int Nf = 2 * Nc, nf1 = Nf - 1, nc1 = Nc - 1;
-    int v0 = blockIdx.x * blockDim.x + threadIdx.x + 1;
-    if (v0 > nf1) return;
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= Nc) return;
     int v1 = blockIdx.y + 1, v2 = DIM == 3 ? blockIdx.z + 1 : 2;
-    int64_t i = (v0 - 1) + (int64_t)nf1 * ((v1 - 1) + (DIM == 3 ? (int64_t)nf1 * (v2 - 1) : 0));
-    int odd = (v0 & 1) + (v1 & 1) + (DIM == 3 ? (v2 & 1) : 0);
-    const T w = odd == 0 ? T(1) : (odd == 1 ? T(0.5) : (odd == 2 ? T(0.25) : T(0.125)));
-    int x0 = max(v0 >> 1, 1), x1 = min((v0 + 1) >> 1, Nc - 1);
+    int64_t line = (int64_t)nf1 * ((v1 - 1) + (DIM == 3 ? (int64_t)nf1 * (v2 - 1) : 0));
+    int oddyz = (v1 & 1) + (DIM == 3 ? (v2 & 1) : 0);
+    const T we = oddyz == 0 ? T(1) : (oddyz == 1 ? T(0.5) : T(0.25));               // v0 even
+    const T wo = oddyz == 0 ? T(0.5) : (oddyz == 1 ? T(0.25) : T(0.125));            // v0 odd
+    const bool lo = m >= 1, hi = m + 1 <= nc1;  // coarse X = m and X = m + 1 are interior
     int y0 = max(v1 >> 1, 1), y1 = min((v1 + 1) >> 1, Nc - 1);
     int z0 = DIM == 3 ? max(v2 >> 1, 1) : 1, z1 = DIM == 3 ? min((v2 + 1) >> 1, Nc - 1) : 1;
-    T t = T(0);
+    T te = T(0), to = T(0);
     for (int Z = z0; Z <= z1; Z++)
         for (int Y = y0; Y <= y1; Y++) {
             int64_t row = (int64_t)nc1 * ((Y - 1) + (DIM == 3 ? (int64_t)nc1 * (Z - 1) : 0)) - 1;
-            for (int X = x0; X <= x1; X++) t = Ar<T>::mac(t, w, __ldg(xc + row + X));
+            T cm = lo ? __ldg(xc + row + m) : T(0), cp = hi ? __ldg(xc + row + m + 1) : T(0);
+            if (lo) {
+                te = Ar<T>::mac(te, we, cm);
+                to = Ar<T>::mac(to, wo, cm);
+            }
+            if (hi) to = Ar<T>::mac(to, wo, cp);
         }
-    xf[i] = Ar<T>::add(xf[i], t);
+    if (m >= 1) xf[line + 2 * m - 1] = Ar<T>::add(xf[line + 2 * m - 1], te);  // v0 = 2m
+    xf[line + 2 * m] = Ar<T>::add(xf[line + 2 * m], to);                      // v0 = 2m + 1
 }
 
 // Explicit CSR transfer (rotated Q1): y_i = sum_k v_k x_col  (ADD: y_i += that sum).

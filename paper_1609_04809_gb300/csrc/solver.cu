@@ -517,8 +517,8 @@ static void prolong_add(mg_hierarchy *h, int l, const T *xc, T *xf, cudaStream_t
     if (!F.structured) bytes += mat_bytes(F.P, sv);
     LaunchScope ls(h, s, MG_K_PROLONG, l, bytes);
     if (F.structured) {
-        unsigned l1 = (unsigned)(F.N - 1), bx = line_block(l1);
-        dim3 g((l1 + bx - 1) / bx, l1, h->dim == 3 ? l1 : 1);
+        unsigned l1 = (unsigned)(F.N - 1), nx = (unsigned)C.N, bx = line_block(nx);  // pairs of fine points
+        dim3 g((nx + bx - 1) / bx, l1, h->dim == 3 ? l1 : 1);
         bool pdl = h->opt.use_pdl != 0;
         if (h->dim == 3)
             klaunch(pdl, k_prolong_q1<T, 3>, g, dim3(bx), 0, s, xc, xf, C.N);
