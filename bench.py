@@ -285,24 +285,26 @@ def serve_bench(args):
 
 
 def heat_report(n_cells=128, n_levels=6, dt=0.01, t_end=5.0, smoother=1, nu=1, tol=1e-10, methods=("dc", "pcg"),
-                precisions=("fp64", "mixed")):
-    """The heat-equation workload (Crank-Nicolson, the paper's model problem on Q1
-    hexahedra): the whole time loop with u resident on the device (mg_heat), per method
-    and precision, and once through the host API (mg_heat_host, host arrays in and out)."""
+                precisions=("fp64", "mixed"), element=0):
+    """The heat-equation workload (Crank-Nicolson, the paper's model problem; element 0:
+    Q1 hexahedra, 2: P1 on the Kuhn tetrahedra): the whole time loop with u resident on
+    the device (mg_heat), per method and precision, and once through the host API
+    (mg_heat_host, host arrays in and out)."""
     import torch
 
     from paper_1609_04809_gb300 import mg, workloads as W
     wl = W.heat_workload(dim=3, n_cells=n_cells, n_levels=n_levels, dt=dt, t_end=t_end)
-    bF = mg.mg_load_vector(3, 0, n_cells, modes=wl["source_modes"])
+    bF = mg.mg_load_vector(3, element, n_cells, modes=wl["source_modes"])
     bFd = torch.from_numpy(bF).cuda()
-    exact = W.q1_nodal_sine(3, n_cells, amp=wl["exact_amp"])
+    exact = W.q1_nodal_sine(3, n_cells, amp=wl["exact_amp"])  # Q1 and P1 share the vertex DOFs
     n = bF.size
-    out = {"workload": "heat_q1_3d_%d" % n_cells, "n_dofs": int(n), "dt": dt, "t_end": t_end,
+    out = {"workload": "heat_%s_3d_%d" % ("p1" if element == 2 else "q1", n_cells), "n_dofs": int(n), "dt": dt,
+           "t_end": t_end,
            "n_steps": wl["n_steps"], "tol_per_step": tol,
            "smoother": [k for k, v in SMOOTHERS.items() if v == smoother][0], "nu": nu}
     meth = {"dc": mg.MG_METHOD_DC, "pcg": mg.MG_METHOD_PCG}
     for prec in precisions:
-        H = mg.Hierarchy(3, 0, n_cells, n_levels, mass=wl["sigma"], smoother=smoother, nu_pre=nu, nu_post=nu,
+        H = mg.Hierarchy(3, element, n_cells, n_levels, mass=wl["sigma"], smoother=smoother, nu_pre=nu, nu_post=nu,
                          precision=mg.MG_MIXED if prec == "mixed" else mg.MG_FP64)
         for m in methods:
             u = torch.from_numpy(wl["u0"].copy()).cuda()
@@ -649,6 +651,9 @@ def main():
             print(json.dumps(config_report(name, smoother=args.smoother)), flush=True)
         if not args.no_heat:
             print(json.dumps(heat_report()), flush=True)
+            # the paper's own configuration: P1 tetrahedra, Gauss-Seidel with three sweeps
+            # before and after the coarse correction, six levels, dt = 0.01 to t = 5
+            print(json.dumps(heat_report(element=2, smoother=2, nu=3, methods=("dc", "pcg"))), flush=True)
         return 0
     return run_ours(args)
 
