@@ -97,17 +97,19 @@ def test_tet_mixed_precision(orc, elem, N, L):
     assert np.linalg.norm(g[3] - o[3]) <= 1e-8 * np.linalg.norm(o[3])
 
 
-def test_tet_heat_steps_bitwise(orc):
-    """Crank-Nicolson on P1 (the paper's model problem with its own element family)."""
+@pytest.mark.parametrize("sm,nu", [(1, 1), (2, 3)])
+def test_tet_heat_steps_bitwise(orc, sm, nu):
+    """Crank-Nicolson on P1 (the paper's model problem with its own element family; with
+    Gauss-Seidel 3+3, the paper's smoother)."""
     N, L = 16, 3
     wl = W.heat_workload(dim=3, n_cells=N, n_levels=L, dt=0.01, t_end=0.05)
     sigma = wl["sigma"]
-    H = mg.Hierarchy(3, mg.MG_P1, N, L, mass=sigma, smoother=1, nu_pre=1, nu_post=1)
+    H = mg.Hierarchy(3, mg.MG_P1, N, L, mass=sigma, smoother=sm, nu_pre=nu, nu_post=nu)
     assert H.info()["storage"][L - 1] == mg.MG_STORAGE_DIA
     bF = mg.mg_load_vector(3, mg.MG_P1, N, modes=wl["source_modes"])
     u = torch.from_numpy(wl["u0"].copy()).cuda()
     st, its = H.heat(torch.from_numpy(bF).cuda(), wl["g"], u, 1e-10)
-    O = orc.Hierarchy(3, mg.MG_P1, N, L, mass=sigma, opts=orc.Options(smoother=1, nu_pre=1, nu_post=1))
+    O = orc.Hierarchy(3, mg.MG_P1, N, L, mass=sigma, opts=orc.Options(smoother=sm, nu_pre=nu, nu_post=nu))
     uo, ito = orc.heat(O, orc.heat_B(3, mg.MG_P1, N, sigma), bF, wl["g"], wl["u0"], 1e-10)
     assert st == mg.MG_OK and list(its) == list(ito) and np.array_equal(u.cpu().numpy(), uo)
 
