@@ -1290,24 +1290,39 @@ orc_hier *orc_setup(int dim, int elem, int N_finest, int n_levels, const double 
 /*
  * Colour of DOF i for the multicolour Gauss-Seidel smoother. The paper colours the DOFs
  * of its hybrid computations and numbers them colour-wise (Sec. 4, "DOF Reordering");
- * the colouring is the natural one of each element, such that two DOFs of one colour
- * never share a cell, hence are never coupled by A:
+ * the colouring is chosen per element such that two DOFs of one colour never share a
+ * cell (or tetrahedron), hence are never coupled by A:
  *   Q1:  parity of each vertex coordinate, colour = (vx&1) + 2(vy&1) [+ 4(vz&1)]
  *        (two vertices of one cell differ by 1 in some coordinate);
  *   RQ1: face family and parity of the normal position, colour = 2f + (p&1)
- *        (the two faces of one family in a cell sit at p and p+1).
+ *        (the two faces of one family in a cell sit at p and p+1);
+ *   P1:  colour = (vx + vy + vz) mod 4: two vertices of a Kuhn tetrahedron differ by
+ *        an offset whose coordinates sum to 1, 2 or 3 in absolute value; four colours
+ *        are the fewest possible (every tetrahedron is a 4-clique);
+ *   P2:  colour = (wx + 2 wy + 4 wz) mod 15 on the grid of 2N cells: none of the 64
+ *        offsets between two nodes of a Kuhn tetrahedron maps to 0 mod 15 (the
+ *        smallest modulus of such a lattice colouring; a tetrahedron's 10 nodes need
+ *        at least 10 colours).
  */
 int orc_n_colours(int dim, int elem)
 {
-    if (elem == ORC_Q1 || elem == ORC_P1) /* P1: Kuhn edges change the parity of a coordinate */
+    if (elem == ORC_Q1)
         return 1 << dim;
-    return elem == ORC_RQ1 ? 6 : 0;       /* P2: no colouring */
+    if (elem == ORC_P1)
+        return 4;
+    return elem == ORC_RQ1 ? 6 : 15;
 }
 
 int orc_colour(int dim, int elem, int N, int64_t i)
 {
     int64_t n1 = N - 1, NN = N;
-    if (elem == ORC_Q1 || elem == ORC_P1) {
+    if (elem == ORC_P1 || elem == ORC_P2) {
+        int M = elem == ORC_P1 ? N : 2 * N; /* node grid */
+        int64_t m1 = M - 1;
+        int wx = (int)(i % m1) + 1, wy = (int)((i / m1) % m1) + 1, wz = (int)(i / (m1 * m1)) + 1;
+        return elem == ORC_P1 ? (wx + wy + wz) % 4 : (wx + 2 * wy + 4 * wz) % 15;
+    }
+    if (elem == ORC_Q1) {
         int vx = (int)(i % n1) + 1;
         int vy = (int)((i / n1) % n1) + 1;
         int c = (vx & 1) + 2 * (vy & 1);

@@ -451,7 +451,8 @@ def _vcycle_operator(H, opts, l):
 
 @pytest.mark.parametrize("dim,elem,N,L,smoother", [(2, 0, 16, 3, 0), (2, 0, 16, 3, 1),
                                                     (3, 1, 4, 2, 0), (3, 1, 4, 2, 1),
-                                                    (2, 0, 16, 3, 2), (3, 0, 8, 3, 2), (3, 1, 4, 2, 2)])
+                                                    (2, 0, 16, 3, 2), (3, 0, 8, 3, 2), (3, 1, 4, 2, 2),
+                                                    (3, 2, 8, 3, 2), (3, 3, 4, 2, 2)])
 def test_vcycle_equals_closed_form_operator(orc, dim, elem, N, L, smoother):
     opts = orc.Options(smoother=smoother, omega=0.7, nu_pre=2 if not smoother else 1,
                        nu_post=1 if not smoother else 2, cheb_degree=3 if smoother else 2)
@@ -554,7 +555,7 @@ def test_gs_colouring_valid_on_galerkin_levels(orc):
         assert not np.any(col[A.row[off]] == col[A.col[off]])
 
 
-@pytest.mark.parametrize("dim,elem,N", [(2, 0, 12), (3, 0, 6), (3, 1, 4)])
+@pytest.mark.parametrize("dim,elem,N", [(2, 0, 12), (3, 0, 6), (3, 1, 4), (3, 2, 6), (3, 3, 3)])
 @pytest.mark.parametrize("backward", [False, True])
 def test_gs_sweep_is_a_triangular_solve(orc, dim, elem, N, backward):
     """x' = x + (D + L)^-1 (b - A x), L the couplings to earlier colours (later ones backward)."""
@@ -594,7 +595,7 @@ def test_gs_sweep_contracts_the_energy_error(orc, dim, elem, N):
     assert np.linalg.norm(x2 - xs) <= 1e-12 * np.linalg.norm(xs)
 
 
-@pytest.mark.parametrize("dim,elem,N,L", [(2, 0, 16, 3), (3, 0, 8, 3), (3, 1, 4, 2)])
+@pytest.mark.parametrize("dim,elem,N,L", [(2, 0, 16, 3), (3, 0, 8, 3), (3, 1, 4, 2), (3, 2, 8, 3), (3, 3, 4, 2)])
 def test_gs_vcycle_is_symmetric(orc, dim, elem, N, L):
     """Forward sweeps before and backward sweeps after the correction: V = V^T."""
     H = orc.Hierarchy(dim, elem, N, L, opts=orc.Options(smoother=orc.GAUSS_SEIDEL, nu_pre=2, nu_post=2))
@@ -883,7 +884,7 @@ def test_tet_prolongation_interpolates_the_element_exactly(orc, elem, Nc):
     assert np.allclose(P[inner].sum(axis=1), 1.0, rtol=0, atol=1e-15)
 
 
-@pytest.mark.parametrize("elem,N,L,sm", [(2, 8, 3, 0), (2, 8, 3, 2), (3, 4, 2, 0), (3, 4, 2, 1)])
+@pytest.mark.parametrize("elem,N,L,sm", [(2, 8, 3, 0), (2, 8, 3, 2), (3, 4, 2, 0), (3, 4, 2, 1), (3, 4, 2, 2)])
 def test_tet_mg_matches_dense_solve(orc, elem, N, L, sm):
     H = orc.Hierarchy(3, elem, N, L, opts=orc.Options(smoother=sm, omega=0.7, nu_pre=2, nu_post=2))
     b = W.random_vector(H.n, seed=61)
@@ -893,11 +894,17 @@ def test_tet_mg_matches_dense_solve(orc, elem, N, L, sm):
     assert np.linalg.norm(x - xd) <= 1e-9 * np.linalg.norm(xd)
 
 
-def test_p1_gs_colouring_is_valid(orc):
-    A = orc.assemble(3, orc.P1, 6).to_scipy().tocoo()
-    col = orc.colours(3, orc.P1, 6)
-    off = A.row != A.col
-    assert not np.any(col[A.row[off]] == col[A.col[off]])
+@pytest.mark.parametrize("elem,N,ncol", [(2, 6, 4), (2, 9, 4), (3, 3, 15), (3, 5, 15)])
+def test_tet_gs_colouring_is_valid(orc, elem, N, ncol):
+    """P1: (vx+vy+vz) mod 4; P2: (wx+2wy+4wz) mod 15 on the 2N grid; with and without a mass shift."""
+    assert orc.n_colours(3, elem) == ncol
+    col = orc.colours(3, elem, N)
+    assert set(np.unique(col)) == set(range(ncol))
+    for mass in (0.0, 200.0):
+        A = orc.assemble(3, elem, N).to_scipy() + mass * orc.assemble_mass(3, elem, N).to_scipy()
+        A = A.tocoo()
+        off = A.row != A.col
+        assert not np.any(col[A.row[off]] == col[A.col[off]])
 
 
 @pytest.mark.slow
