@@ -58,7 +58,8 @@ typedef int mg_status;
  * interpolation. P1 DOFs: the interior vertices (numbered like Q1; storage DIA, ELL or
  * CSR). P2 DOFs: vertices and edge midpoints, i.e. the interior points of the grid of
  * 2 n_cells cells, numbered like Q1 there (ELL or CSR). Load vector: b = M f_I (the mass
- * matrix times f at the nodes). Gauss-Seidel: P1 only (vertex parity colours). */
+ * matrix times f at the nodes). Gauss-Seidel colours: P1 (vx + vy + vz) mod 4, P2
+ * (wx + 2wy + 4wz) mod 15 on the grid of 2 n_cells cells. */
 #define MG_P1 2
 #define MG_P2 3
 /* smoother */
@@ -70,7 +71,8 @@ typedef int mg_status;
                              DOFs of a colour at once; colours ascending before the coarse
                              correction, descending after it, so the V-cycle is symmetric.
                              Q1 colours: parity classes of the vertex coordinates (2^dim);
-                             rotated Q1: face family x parity of the normal position (6).
+                             rotated Q1: face family x parity of the normal position (6);
+                             P1, P2: see MG_P1.
                              Not available to the serving API. */
 /* precision */
 #define MG_FP64 0  /* every step in FP64 */

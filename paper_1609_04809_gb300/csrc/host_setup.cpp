@@ -1022,13 +1022,23 @@ void round_fp32(const Csr &A, std::vector<float> &val32)
 // ------------------------------------------------------------------------------------
 int n_colours(int dim, int elem)
 {
-    if (elem == MG_Q1 || elem == MG_P1) return 1 << dim;  // P1: Kuhn edges change a coordinate's parity
-    return elem == MG_RQ1 ? 6 : 0;                        // P2: no colouring
+    if (elem == MG_Q1) return 1 << dim;
+    if (elem == MG_P1) return 4;
+    return elem == MG_RQ1 ? 6 : 15;
 }
 
 int dof_colour(int dim, int elem, int N, int64_t i)
 {
-    if (elem == MG_Q1 || elem == MG_P1) {
+    if (elem == MG_P1 || elem == MG_P2) {
+        // P1: vertex coordinate sum mod 4 (Kuhn-edge offsets sum to 1..3 in absolute value);
+        // P2: (wx + 2 wy + 4 wz) mod 15 on the grid of 2N cells (no offset between two
+        // nodes of a Kuhn tetrahedron is 0 mod 15)
+        int M = elem == MG_P1 ? N : 2 * N;
+        int64_t m1 = M - 1;
+        int w[3] = {(int)(i % m1) + 1, (int)((i / m1) % m1) + 1, (int)(i / (m1 * m1)) + 1};
+        return elem == MG_P1 ? (w[0] + w[1] + w[2]) % 4 : (w[0] + 2 * w[1] + 4 * w[2]) % 15;
+    }
+    if (elem == MG_Q1) {
         int v[3];
         q1_coords(dim, N, i, v);
         return (v[0] & 1) | (v[1] & 1) << 1 | (dim == 3 ? (v[2] & 1) << 2 : 0);

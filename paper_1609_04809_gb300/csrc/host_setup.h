@@ -71,7 +71,8 @@ void build_hierarchy(int dim, int elem, int N_finest, int n_levels, const double
 
 // Multicolour Gauss-Seidel ordering. Q1: the parity class of the vertex coordinates,
 // colour (vx&1) + 2(vy&1) [+ 4(vz&1)]; rotated Q1: face family f and parity of the normal
-// position p, colour 2f + (p&1). DOFs of one colour never share a cell.
+// position p, colour 2f + (p&1); P1: (vx + vy + vz) mod 4; P2: (wx + 2wy + 4wz) mod 15 on
+// the grid of 2N cells. DOFs of one colour never share a cell (tetrahedron).
 int n_colours(int dim, int elem);
 int dof_colour(int dim, int elem, int N, int64_t i);
 // DOFs sorted by colour (index order within a colour): perm[coff[c] .. coff[c+1]) are

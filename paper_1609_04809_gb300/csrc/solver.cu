@@ -1448,8 +1448,6 @@ void mgi::build_hierarchy(mg_hierarchy *h, const mg_problem *p, const mg_options
     // ---- multicolour Gauss-Seidel: colour order of every smoothed level ----
     const bool gs = o->smoother == MG_GAUSS_SEIDEL;
     std::vector<std::vector<int32_t>> gs_perm((size_t)nlev);
-    if (gs && mgh::n_colours(dim, elem) == 0)
-        throw Error(MG_EINVAL, "the Gauss-Seidel smoother needs a colouring of the DOFs; P2 has none");
     if (gs)
         for (int l = 1; l <= Lf; l++) {
             if (!mgh::colouring_valid(A[l], dim, elem, h->lev[l].N))

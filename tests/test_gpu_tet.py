@@ -114,10 +114,13 @@ def test_tet_heat_steps_bitwise(orc, sm, nu):
     assert st == mg.MG_OK and list(its) == list(ito) and np.array_equal(u.cpu().numpy(), uo)
 
 
-def test_gs_is_rejected_for_p2():
-    with pytest.raises(mg.MgError) as e:
-        mg.Hierarchy(3, mg.MG_P2, 8, 3, smoother=mg.MG_GAUSS_SEIDEL)
-    assert e.value.status == mg.MG_EINVAL
+@pytest.mark.parametrize("elem,N,L,nu,storage", [(2, 32, 4, 2, mg.MG_STORAGE_DIA), (2, 16, 3, 3, mg.MG_STORAGE_CSR),
+                                                 (3, 16, 4, 2, mg.MG_STORAGE_AUTO), (3, 8, 3, 1, mg.MG_STORAGE_ELL)])
+def test_tet_gauss_seidel_bitwise(orc, elem, N, L, nu, storage):
+    """P1 (four colours) and P2 (fifteen colours) Gauss-Seidel, every storage of the copy."""
+    b = mg.mg_load_vector(3, elem, N, modes=W.manufactured_modes(3))
+    H, O, g, o = _both(orc, elem, N, L, b, smoother=mg.MG_GAUSS_SEIDEL, nu=nu, storage=storage)
+    assert g[0] == mg.MG_OK and g[1] == o[1] and np.array_equal(g[3], o[3])
 
 
 @pytest.mark.parametrize("name", ["p1_3d_128_cheb", "p2_3d_64_cheb"])
