@@ -407,7 +407,7 @@ def config_report(name, steps=20, warmup=5, smoother="workload"):
                     "time_to_tol_ms": 1e3 * float(np.median(ts[1:])), "iterations": its,
                     "final_rel_residual": rel, "true_fp64_rel_residual": true_rel,
                     "storage": ["csr", "ell", "dia", "sell"][info["storage"][Lf] - 1], "setup_s": setup_s,
-                    "device_gb": info["device_bytes"] / 1e9, "pcg": pcg}
+                    "device_gb": info["device_bytes"] / 1e9, "tail_levels": info["tail_levels"], "pcg": pcg}
         H.close()
         del H
         torch.cuda.empty_cache()
