@@ -111,3 +111,16 @@ def test_gs_rejected_by_serving():
     with pytest.raises(mg.MgError) as e:
         mg.Server(1 << 30, smoother=GS)
     assert e.value.status == mg.MG_EINVAL and "Gauss-Seidel" in str(e.value)
+
+
+def test_gs_full_size_128(orc):
+    """The 128^3 Q1 workload with Gauss-Seidel V(1,1) at full size, as bench --smoother
+    gauss-seidel runs it (DIA, colour pairs): bit for bit the oracle's iterates."""
+    c = W.CONFIGS["q1_3d_128_cheb"]
+    b = mg.mg_load_vector(3, 0, c["n_cells"], modes=W.manufactured_modes(3))
+    H, O, g, o = _both(orc, 3, 0, c["n_cells"], c["n_levels"], b, nu=(1, 1))
+    assert H.info()["storage"][c["n_levels"] - 1] == mg.MG_STORAGE_DIA
+    st, it, hist, x = g
+    conv, ito, ho, xo = o
+    assert st == mg.MG_OK and conv and it == ito
+    assert np.array_equal(x, xo)
