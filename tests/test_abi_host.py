@@ -22,7 +22,8 @@ def lib():
 
 
 def _declared(header):
-    src = open(os.path.join(ROOT, "include", header)).read()
+    with open(os.path.join(ROOT, "include", header)) as f:
+        src = f.read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"\b(mg_[a-z0-9_]+)\s*\(", src)))
 

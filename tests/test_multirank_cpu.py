@@ -34,7 +34,7 @@ def _rank_main(rank, world, port, out):
 def test_replica_throughput_two_gloo_ranks():
     world = 2
     port = _free_port()
-    mgr = tmp.Manager()
+    mgr = tmp.get_context("spawn").Manager()  # no fork of this (threaded) process
     out = mgr.dict()
     tmp.spawn(_rank_main, args=(world, port, out), nprocs=world, join=True)
     for r in range(world):
