@@ -29,7 +29,8 @@
  *   restriction b_c = R r with R = P^T stored by rows (fine index ascending)
  *   prolongation x_i <- x_i + t_i,  t_i = sum_J p_iJ c_J   (coarse index ascending, fused)
  *   coarsest solve: LU with partial pivoting; forward substitution sums column-
- *   ascending, back substitution sums column-descending.
+ *   ascending, back substitution sums column-descending, both fused like the row sums;
+ *   back substitution multiplies by the pivot's reciprocal, 1.0/u_ii.
  */
 #include <math.h>
 #include <stdint.h>
@@ -796,15 +797,17 @@ void orc_lu_solve(const double *lu, int n, const int *piv, const double *b, doub
     for (int i = 0; i < n; i++) { /* L y = Pb, unit diagonal */
         double s = 0.0;
         for (int j = 0; j < i; j++)
-            s = s + lu[(size_t)i * n + j] * x[j];
+            s = fma(lu[(size_t)i * n + j], x[j], s);
         x[i] = x[i] - s;
     }
     for (int i = n - 1; i >= 0; i--) { /* U x = y; the sum runs from j = n-1 down to i+1,
-                                          * the order in which the x_j become known */
+                                          * the order in which the x_j become known; the
+                                          * result is multiplied by the pivot's reciprocal */
         double s = 0.0;
         for (int j = n - 1; j > i; j--)
-            s = s + lu[(size_t)i * n + j] * x[j];
-        x[i] = (x[i] - s) / lu[(size_t)i * n + i];
+            s = fma(lu[(size_t)i * n + j], x[j], s);
+        double inv = 1.0 / lu[(size_t)i * n + i];
+        x[i] = (x[i] - s) * inv;
     }
 }
 
