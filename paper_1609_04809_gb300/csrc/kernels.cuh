@@ -116,8 +116,9 @@ __global__ void __launch_bounds__(256) k_csr_apply(const int64_t *__restrict__ r
 __global__ void k_lu_factor(double *a, int n, int *piv, int *info);
 
 // Solve with the factors: row swaps in factorisation order, then column-oriented
-// substitutions so every thread owns one row and its running sum: forward in ascending
-// column order, backward in descending column order. Input and output in T.
+// substitutions so every thread owns one row and its running sum (fused multiply-adds):
+// forward in ascending column order, backward in descending column order, each unknown
+// of the backward pass multiplied by its pivot's reciprocal. Input and output in T.
 template <typename T>
 __global__ void k_coarse_solve(const double *__restrict__ lu, const int *__restrict__ piv, int n,
                                const T *__restrict__ b, T *__restrict__ x)
@@ -138,20 +139,54 @@ __global__ void k_coarse_solve(const double *__restrict__ lu, const int *__restr
         }
     __syncthreads();
     double s = 0.0;
+    double inv = t < n ? __ddiv_rn(1.0, lu[(int64_t)t * n + t]) : 0.0;  // off the dependency chain
     for (int j = 0; j < n; j++) {
         if (t == j) xs[j] = __dsub_rn(xs[j], s);
         __syncthreads();
-        if (t > j && t < n) s = __dadd_rn(s, __dmul_rn(lu[(int64_t)t * n + j], xs[j]));
+        if (t > j && t < n) s = __fma_rn(lu[(int64_t)t * n + j], xs[j], s);
     }
     __syncthreads();
     s = 0.0;
     for (int j = n - 1; j >= 0; j--) {
-        if (t == j) xs[j] = __ddiv_rn(__dsub_rn(xs[j], s), lu[(int64_t)j * n + j]);
+        if (t == j) xs[j] = __dmul_rn(__dsub_rn(xs[j], s), inv);
         __syncthreads();
-        if (t < j) s = __dadd_rn(s, __dmul_rn(lu[(int64_t)t * n + j], xs[j]));
+        if (t < j) s = __fma_rn(lu[(int64_t)t * n + j], xs[j], s);
     }
     __syncthreads();
     if (t < n) x[t] = (T)xs[t];
+}
+
+// Substitutions of the pivoted right-hand side xs (shared memory, n <= 64) with the LU
+// factors L (shared memory, row-major) by one warp: lane l owns rows l and l + 32 and
+// their running sums, one __syncwarp per column. Forward: x_i -= sum_{j<i} l_ij x_j,
+// ascending j; backward: x_i = (x_i - sum_{j>i} u_ij x_j) * (1 / u_ii), descending j; sums
+// by fused multiply-adds. The reciprocals are formed before the loops, so the dependent
+// chain per column is one fused multiply-add, one subtraction (and one multiplication).
+__device__ __forceinline__ void lu_substitute_warp(const double *L, double *xs, int n, int l)
+{
+    int r0 = l, r1 = l + 32;
+    double inv0 = r0 < n ? __ddiv_rn(1.0, L[r0 * n + r0]) : 0.0;
+    double inv1 = r1 < n ? __ddiv_rn(1.0, L[r1 * n + r1]) : 0.0;
+    double s0 = 0.0, s1 = 0.0;
+    for (int j = 0; j < n; j++) {
+        if (j == r0) xs[j] = __dsub_rn(xs[j], s0);
+        if (j == r1) xs[j] = __dsub_rn(xs[j], s1);
+        __syncwarp();
+        double xj = xs[j];
+        if (r0 > j && r0 < n) s0 = __fma_rn(L[r0 * n + j], xj, s0);
+        if (r1 > j && r1 < n) s1 = __fma_rn(L[r1 * n + j], xj, s1);
+        __syncwarp();
+    }
+    s0 = s1 = 0.0;
+    for (int j = n - 1; j >= 0; j--) {
+        if (j == r0) xs[j] = __dmul_rn(__dsub_rn(xs[j], s0), inv0);
+        if (j == r1) xs[j] = __dmul_rn(__dsub_rn(xs[j], s1), inv1);
+        __syncwarp();
+        double xj = xs[j];
+        if (r0 < j) s0 = __fma_rn(L[r0 * n + j], xj, s0);
+        if (r1 < j) s1 = __fma_rn(L[r1 * n + j], xj, s1);
+        __syncwarp();
+    }
 }
 
 // The same solve for n <= 64 by one warp with the factors in shared memory: lane l owns
@@ -186,27 +221,7 @@ __global__ void __launch_bounds__(256) k_coarse_solve_warp(const double *__restr
             }
         }
     __syncwarp();
-    int r0 = l, r1 = l + 32;
-    double s0 = 0.0, s1 = 0.0;
-    for (int j = 0; j < n; j++) {  // forward: x_i -= sum_{j<i} l_ij x_j, ascending j
-        if (j == r0) xs[j] = __dsub_rn(xs[j], s0);
-        if (j == r1) xs[j] = __dsub_rn(xs[j], s1);
-        __syncwarp();
-        double xj = xs[j];
-        if (r0 > j && r0 < n) s0 = __dadd_rn(s0, __dmul_rn(L[r0 * n + j], xj));
-        if (r1 > j && r1 < n) s1 = __dadd_rn(s1, __dmul_rn(L[r1 * n + j], xj));
-        __syncwarp();
-    }
-    s0 = s1 = 0.0;
-    for (int j = n - 1; j >= 0; j--) {  // backward: descending j
-        if (j == r0) xs[j] = __ddiv_rn(__dsub_rn(xs[j], s0), L[j * n + j]);
-        if (j == r1) xs[j] = __ddiv_rn(__dsub_rn(xs[j], s1), L[j * n + j]);
-        __syncwarp();
-        double xj = xs[j];
-        if (r0 < j) s0 = __dadd_rn(s0, __dmul_rn(L[r0 * n + j], xj));
-        if (r1 < j) s1 = __dadd_rn(s1, __dmul_rn(L[r1 * n + j], xj));
-        __syncwarp();
-    }
+    lu_substitute_warp(L, xs, n, l);
     for (int k = l; k < n; k += 32) x[k] = (T)xs[k];
 }
 
@@ -382,27 +397,7 @@ __global__ void __launch_bounds__(512) k_tail(TailProg<T> P)
                         }
                     }
                 __syncwarp();
-                int r0 = tid, r1 = tid + 32;
-                double s0 = 0.0, s1 = 0.0;
-                for (int j = 0; j < n; j++) {
-                    if (j == r0) xs[j] = __dsub_rn(xs[j], s0);
-                    if (j == r1) xs[j] = __dsub_rn(xs[j], s1);
-                    __syncwarp();
-                    double xj = xs[j];
-                    if (r0 > j && r0 < n) s0 = __dadd_rn(s0, __dmul_rn(Ls[r0 * n + j], xj));
-                    if (r1 > j && r1 < n) s1 = __dadd_rn(s1, __dmul_rn(Ls[r1 * n + j], xj));
-                    __syncwarp();
-                }
-                s0 = s1 = 0.0;
-                for (int j = n - 1; j >= 0; j--) {
-                    if (j == r0) xs[j] = __ddiv_rn(__dsub_rn(xs[j], s0), Ls[j * n + j]);
-                    if (j == r1) xs[j] = __ddiv_rn(__dsub_rn(xs[j], s1), Ls[j * n + j]);
-                    __syncwarp();
-                    double xj = xs[j];
-                    if (r0 < j) s0 = __dadd_rn(s0, __dmul_rn(Ls[r0 * n + j], xj));
-                    if (r1 < j) s1 = __dadd_rn(s1, __dmul_rn(Ls[r1 * n + j], xj));
-                    __syncwarp();
-                }
+                lu_substitute_warp(Ls, xs, n, tid);
                 for (int k = tid; k < n; k += 32) L.x[0][k] = (T)xs[k];
             }
         }

@@ -353,27 +353,7 @@ __global__ void __launch_bounds__(32) k_sv_coarse(Plan P, int p)
                 }
             }
         __syncwarp();
-        int r0 = l, r1 = l + 32;
-        double s0 = 0.0, s1 = 0.0;
-        for (int j = 0; j < n; j++) {
-            if (j == r0) xs[j] = __dsub_rn(xs[j], s0);
-            if (j == r1) xs[j] = __dsub_rn(xs[j], s1);
-            __syncwarp();
-            double xj = xs[j];
-            if (r0 > j && r0 < n) s0 = __dadd_rn(s0, __dmul_rn(Ls[r0 * n + j], xj));
-            if (r1 > j && r1 < n) s1 = __dadd_rn(s1, __dmul_rn(Ls[r1 * n + j], xj));
-            __syncwarp();
-        }
-        s0 = s1 = 0.0;
-        for (int j = n - 1; j >= 0; j--) {
-            if (j == r0) xs[j] = __ddiv_rn(__dsub_rn(xs[j], s0), Ls[j * n + j]);
-            if (j == r1) xs[j] = __ddiv_rn(__dsub_rn(xs[j], s1), Ls[j * n + j]);
-            __syncwarp();
-            double xj = xs[j];
-            if (r0 < j) s0 = __dadd_rn(s0, __dmul_rn(Ls[r0 * n + j], xj));
-            if (r1 < j) s1 = __dadd_rn(s1, __dmul_rn(Ls[r1 * n + j], xj));
-            __syncwarp();
-        }
+        lu_substitute_warp(Ls, xs, n, l);
         for (int k = l; k < n; k += 32) C.x[0][k] = (float)xs[k];
     }
 }
