@@ -109,6 +109,25 @@ __global__ void __launch_bounds__(256) k_csr_apply(const int64_t *__restrict__ r
     y[i] = ADD ? Ar<T>::add(y[i], s) : s;
 }
 
+// The same transfer with the operator in SELL-32 (see k_sell_sweep): storage position r
+// computes row perm[r]; each row keeps its CSR order, so the sums equal k_csr_apply's.
+template <typename T, bool ADD>
+__global__ void __launch_bounds__(256) k_sell_apply(const int64_t *__restrict__ sptr, const int32_t *__restrict__ col,
+                                                    const T *__restrict__ val, const int32_t *__restrict__ perm,
+                                                    int n, const T *__restrict__ x, T *__restrict__ y)
+{
+    pdl_enter();
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    int i = __ldg(perm + r);
+    int64_t base = sptr[r >> 5];
+    int Ks = (int)((sptr[(r >> 5) + 1] - base) >> 5);
+    int64_t e = base + (r & 31);
+    T s = T(0);
+    for (int k = 0; k < Ks; k++, e += 32) s = Ar<T>::mac(s, __ldcs(val + e), __ldg(x + __ldcs(col + e)));
+    y[i] = ADD ? Ar<T>::add(y[i], s) : s;
+}
+
 // ------------------------------------------------------------------------------------
 // Coarsest level: dense LU in FP64 (one CTA, n <= 1024)
 // ------------------------------------------------------------------------------------

@@ -10,6 +10,7 @@
 
 #include "kernels.cuh"
 #include "mg.h"
+#include "transfer.cuh"
 
 namespace mgi {
 
@@ -48,6 +49,15 @@ struct DevMat {
     void *dinv = nullptr;  // 1 / a_ii, FP64 inner levels only
 };
 
+// A transfer generated from per-class tables (transfer.cuh); on = false: not used.
+struct XferD {
+    bool on = false;
+    mgk::XferGeom geo;
+    int32_t *cls = nullptr, *ent = nullptr;
+    void *w = nullptr;  // weights in the inner precision
+    int nent = 0;
+};
+
 struct LevelD {
     int N = 0;        // cells per axis
     int64_t n = 0;    // DOFs
@@ -59,7 +69,8 @@ struct LevelD {
     void *x[2] = {nullptr, nullptr};
     void *b = nullptr, *t = nullptr, *d = nullptr;
     bool structured = false;  // Q1 transfers computed from the grid
-    DevMat P, R;              // explicit transfers to level-1 (CSR)
+    DevMat P, R;              // explicit transfers to level-1 (SELL-32), when no tables
+    XferD Pt, Rt;             // table-driven transfers (rotated Q1, P1, P2)
     // multicolour Gauss-Seidel: a copy of A with its rows stored colour by colour (row r
     // of G is DOF perm[r]; colour c owns rows coff[c] .. coff[c+1]); D^-1 in G.dinv
     DevMat G;

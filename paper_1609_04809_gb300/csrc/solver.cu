@@ -120,6 +120,7 @@ __global__ void __launch_bounds__(256, 6) k_norm2(const double *__restrict__ v, 
 using mgi::DevMat;
 using mgi::Error;
 using mgi::LevelD;
+using mgi::XferD;
 
 static inline int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 static inline unsigned grid_for(int64_t n) { return (unsigned)((n + 255) / 256); }
@@ -372,7 +373,7 @@ static void sweep(mg_hierarchy *h, int l, int mode, const T *x, const T *b, T *o
     } else {  // the matrix, x, b, out [, D^-1] [, d read and/or write]
         kclass = mode == SW_RESID ? MG_K_RESID : MG_K_SMOOTH;
         bytes = mat_bytes(L.A, sv) + 3 * n * sv;
-        if (mode != SW_RESID && L.A.dinv) bytes += n * sv;
+        if (mode != SW_RESID && L.A.dinv && sv == 8) bytes += n * sv;  // FP32 sweeps use rcp(a_ii)
         if (mode == SW_CHEBF) bytes += n * sv;
         if (mode == SW_CHEB) bytes += 2 * n * sv;
     }
@@ -483,7 +484,7 @@ static void restrict_to(mg_hierarchy *h, int l, const T *r, cudaStream_t s)
     }
     int sv = sizeof(T);
     double bytes = (double)F.n * sv + (double)C.n * sv;
-    if (!F.structured) bytes += mat_bytes(F.R, sv);
+    if (!F.structured && !F.Rt.on) bytes += mat_bytes(F.R, sv);
     LaunchScope ls(h, s, MG_K_RESTRICT, l, bytes);
     if (F.structured) {
         unsigned l1 = (unsigned)(C.N - 1), bx = line_block(l1);
@@ -493,6 +494,14 @@ static void restrict_to(mg_hierarchy *h, int l, const T *r, cudaStream_t s)
             klaunch(pdl, k_restrict_q1<T, 3>, g, dim3(bx), 0, s, r, (T *)C.b, C.N);
         else
             klaunch(pdl, k_restrict_q1<T, 2>, g, dim3(bx), 0, s, r, (T *)C.b, C.N);
+    } else if (F.Rt.on) {
+        XferView<T> v{F.Rt.geo, F.Rt.cls, F.Rt.ent, (const T *)F.Rt.w};
+        klaunch(h->opt.use_pdl != 0, k_xfer_apply<T, false>, dim3(grid_for(C.n)), dim3(256), 0, s, v, (int)C.n, r,
+                (T *)C.b);
+    } else if (F.R.fmt == MG_STORAGE_SELL) {
+        klaunch(h->opt.use_pdl != 0, k_sell_apply<T, false>, dim3(grid_for(C.n)), dim3(256), 0, s,
+                (const int64_t *)F.R.rowptr, (const int32_t *)F.R.col, (const T *)F.R.val, (const int32_t *)F.R.perm,
+                (int)C.n, r, (T *)C.b);
     } else {
         klaunch(h->opt.use_pdl != 0, k_csr_apply<T, false>, dim3(grid_for(C.n)), dim3(256), 0, s,
                 (const int64_t *)F.R.rowptr, (const int32_t *)F.R.col, (const T *)F.R.val, (int)C.n, r, (T *)C.b);
@@ -514,7 +523,7 @@ static void prolong_add(mg_hierarchy *h, int l, const T *xc, T *xf, cudaStream_t
     }
     int sv = sizeof(T);
     double bytes = 2.0 * F.n * sv + (double)C.n * sv;
-    if (!F.structured) bytes += mat_bytes(F.P, sv);
+    if (!F.structured && !F.Pt.on) bytes += mat_bytes(F.P, sv);
     LaunchScope ls(h, s, MG_K_PROLONG, l, bytes);
     if (F.structured) {
         unsigned l1 = (unsigned)(F.N - 1), nx = (unsigned)C.N, bx = line_block(nx);  // pairs of fine points
@@ -524,6 +533,13 @@ static void prolong_add(mg_hierarchy *h, int l, const T *xc, T *xf, cudaStream_t
             klaunch(pdl, k_prolong_q1<T, 3>, g, dim3(bx), 0, s, xc, xf, C.N);
         else
             klaunch(pdl, k_prolong_q1<T, 2>, g, dim3(bx), 0, s, xc, xf, C.N);
+    } else if (F.Pt.on) {
+        XferView<T> v{F.Pt.geo, F.Pt.cls, F.Pt.ent, (const T *)F.Pt.w};
+        klaunch(h->opt.use_pdl != 0, k_xfer_apply<T, true>, dim3(grid_for(F.n)), dim3(256), 0, s, v, (int)F.n, xc, xf);
+    } else if (F.P.fmt == MG_STORAGE_SELL) {
+        klaunch(h->opt.use_pdl != 0, k_sell_apply<T, true>, dim3(grid_for(F.n)), dim3(256), 0, s,
+                (const int64_t *)F.P.rowptr, (const int32_t *)F.P.col, (const T *)F.P.val, (const int32_t *)F.P.perm,
+                (int)F.n, xc, xf);
     } else {
         klaunch(h->opt.use_pdl != 0, k_csr_apply<T, true>, dim3(grid_for(F.n)), dim3(256), 0, s,
                 (const int64_t *)F.P.rowptr, (const int32_t *)F.P.col, (const T *)F.P.val, (int)F.n, xc, xf);
@@ -1002,6 +1018,117 @@ extern "C" mg_status mg_load_vector_separable(const mg_problem *p, const mg_rhs 
     }
 }
 
+// ------------------------------------------------------------------------------------
+// Table-driven transfers (rotated Q1, P1, P2; transfer.cuh)
+// ------------------------------------------------------------------------------------
+// The DOF lattice of a level in its DOF frame; false where the transfers are computed
+// from the grid (Q1) or the element has no lattice description here (2D).
+static bool lattice_of(int dim, int elem, int N, mgk::LatGeom &G)
+{
+    G = mgk::LatGeom{};
+    if (dim != 3) return false;
+    if (elem == MG_RQ1) {  // face centres in half cells: family g = the normal axis
+        G.ng = 3;
+        G.s = 2;
+        int64_t fam = (int64_t)(N - 1) * N * N;
+        for (int g = 0; g < 3; g++) {
+            for (int d = 0; d < 3; d++) {
+                G.o[g][d] = d == g ? 2 : 1;
+                G.n[g][d] = d == g ? N - 1 : N;
+            }
+            G.base[g] = g * fam;
+        }
+        G.base[3] = 3 * fam;
+        return true;
+    }
+    if (elem == MG_P1 || elem == MG_P2) {  // interior points of the N (P1) or 2N (P2) grid
+        int M = elem == MG_P1 ? N : 2 * N;
+        G.ng = 1;
+        G.s = 1;
+        for (int d = 0; d < 3; d++) {
+            G.o[0][d] = 1;
+            G.n[0][d] = M - 1;
+        }
+        G.base[1] = (int64_t)(M - 1) * (M - 1) * (M - 1);
+        return true;
+    }
+    return false;
+}
+
+struct XferTables {
+    bool ok = false;
+    mgk::XferGeom geo;
+    std::vector<int32_t> cls, ent;
+    std::vector<double> w;
+};
+
+// Learn the class tables of transfer M (rows and columns on the lattices of geo): each
+// class takes the entries of its longest row, as offsets from the row's position. Then
+// every row is generated from its class and compared with the stored row; ok only if
+// all agree in columns, order and weights.
+static XferTables learn_xfer(const mgh::Csr &M, const mgk::XferGeom &geo)
+{
+    XferTables T;
+    T.geo = geo;
+    const int64_t n = M.nrows;
+    std::vector<int64_t> rep(mgk::XF_CLASSES, -1);
+    for (int64_t r = 0; r < n; r++) {
+        int X[3];
+        int key = mgk::xf_row(geo, r, X);
+        int64_t len = M.rowptr[r + 1] - M.rowptr[r];
+        if (rep[key] < 0 || len > M.rowptr[rep[key] + 1] - M.rowptr[rep[key]]) rep[key] = r;
+    }
+    T.cls.assign(mgk::XF_CLASSES + 1, 0);
+    for (int key = 0; key < mgk::XF_CLASSES; key++) {
+        T.cls[key] = (int32_t)T.ent.size();
+        int64_t r = rep[key];
+        if (r < 0) continue;
+        int X[3];
+        mgk::xf_row(geo, r, X);
+        for (int64_t k = M.rowptr[r]; k < M.rowptr[r + 1]; k++) {
+            int g, Y[3], D[3];
+            mgk::lat_decode(geo.col, M.col[k], g, Y);
+            for (int d = 0; d < 3; d++) {
+                D[d] = (geo.row_coarse ? Y[d] : 2 * Y[d]) - X[d];
+                if (D[d] < -128 || D[d] > 127) return T;
+            }
+            T.ent.push_back(mgk::xf_pack(D[0], D[1], D[2], g));
+            T.w.push_back(M.val[k]);
+        }
+    }
+    T.cls[mgk::XF_CLASSES] = (int32_t)T.ent.size();
+    int64_t bad = 0;
+#pragma omp parallel for schedule(static) reduction(+ : bad)
+    for (int64_t r = 0; r < n; r++) {
+        int X[3];
+        int key = mgk::xf_row(geo, r, X);
+        int64_t k = M.rowptr[r], k1 = M.rowptr[r + 1];
+        bool good = true;
+        for (int e = T.cls[key]; e < T.cls[key + 1] && good; e++) {
+            int64_t c = mgk::xf_col(geo, X, T.ent[e]);
+            if (c < 0) continue;  // a boundary DOF: not in the row
+            if (k >= k1 || M.col[k] != c || M.val[k] != T.w[e]) good = false;
+            k++;
+        }
+        if (!good || k != k1) bad++;
+    }
+    T.ok = bad == 0;
+    return T;
+}
+
+template <typename T>
+static void upload_xfer(const XferD &X, const XferTables &Tb, cudaStream_t s)
+{
+    std::vector<T> w(Tb.w.size());
+    for (size_t e = 0; e < w.size(); e++) w[e] = (T)Tb.w[e];  // FP32: rounded once, like the CSR copy
+    CK(cudaMemcpyAsync(X.cls, Tb.cls.data(), Tb.cls.size() * 4, cudaMemcpyHostToDevice, s));
+    if (!w.empty()) {
+        CK(cudaMemcpyAsync(X.ent, Tb.ent.data(), Tb.ent.size() * 4, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(X.w, w.data(), w.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+    }
+    CK(cudaStreamSynchronize(s));
+}
+
 // device format of a level operator
 // SELL-32 layout: rows sorted by length, longest first (ties by row index), slices of 32
 // positions; slice s holds 32 * K_s slots from sptr[s] (K_s = its longest row).
@@ -1156,7 +1283,11 @@ static void upload_matrix(const DevMat &m, const mgh::Csr &A, const std::vector<
             int64_t sl = r / 32, lane = r % 32, Ks = (sptr[sl + 1] - sptr[sl]) / 32;
             int64_t i = r < A.nrows ? perm[r] : -1;
             int64_t len = i >= 0 ? A.rowptr[i + 1] - A.rowptr[i] : 0;
-            int32_t pad = (int32_t)(i >= 0 ? i : perm[(size_t)sl * 32]);  // lanes past n: any valid column
+            // padding: column i (square operators), else the row's first column, so that a
+            // padded slot repeats a column of the row (lanes past n: any valid column)
+            int64_t ir = i >= 0 ? i : perm[(size_t)sl * 32];
+            int64_t lr = A.rowptr[ir + 1] - A.rowptr[ir];
+            int32_t pad = (int32_t)(A.ncols == A.nrows ? ir : (lr > 0 ? A.col[A.rowptr[ir]] : 0));
             for (int64_t k = 0; k < Ks; k++) {
                 size_t e = (size_t)(sptr[sl] + 32 * k + lane);
                 if (k < len) {
@@ -1455,6 +1586,17 @@ void mgi::build_hierarchy(mg_hierarchy *h, const mg_problem *p, const mg_options
             mgh::colour_order(dim, elem, h->lev[l].N, gs_perm[l], h->lev[l].coff);
             h->lev[l].gs_groups = mgh::colour_launch_groups(A[l], dim, elem, h->lev[l].N, h->lev[l].coff);
         }
+    // ---- transfer tables of the lattice elements (checked against every row) ----
+    std::vector<XferTables> xP((size_t)nlev), xR((size_t)nlev);
+    for (int l = 1; l <= Lf; l++) {
+        mgk::XferGeom gp, gr;
+        if (!lattice_of(dim, elem, h->lev[l].N, gp.row) || !lattice_of(dim, elem, h->lev[l - 1].N, gp.col)) continue;
+        gr.row = gp.col;
+        gr.col = gp.row;
+        gr.row_coarse = 1;
+        xP[l] = learn_xfer(P[l], gp);
+        xR[l] = learn_xfer(R[l], gr);
+    }
     for (int pass = 0; pass < 2; pass++) {
         bool take = pass == 1;
         mgi::Slab &S = h->slab;
@@ -1485,6 +1627,9 @@ void mgi::build_hierarchy(mg_hierarchy *h, const mg_problem *p, const mg_options
             L.fmt = lf;
             plan_matrix(L.A, A[l], lf, dim, L.N, sv, S, take);
             if (!h->mixed && l >= 1) L.A.dinv = vec((size_t)L.A.ld * 8);  // FP64 smoothers read D^-1
+            // FP32 sweeps from x = 0 on formats whose diagonal has no fixed slot read D^-1
+            // instead of scanning the row (the same value: 1/a_ii rounded once)
+            if (h->mixed && l >= 1 && lf != MG_STORAGE_DIA) L.A.dinv = vec((size_t)L.A.ld * 4);
             if (gs && l >= 1) {  // the colour-major copy of A for the Gauss-Seidel sweeps (CSR for SELL levels)
                 plan_matrix(L.G, A[l], lf == MG_STORAGE_SELL ? MG_STORAGE_CSR : lf, dim, L.N, sv, S, take);
                 if (!h->mixed) L.G.dinv = vec((size_t)L.G.ld * 8);
@@ -1504,9 +1649,20 @@ void mgi::build_hierarchy(mg_hierarchy *h, const mg_problem *p, const mg_options
             }
             if (l >= 1) {
                 L.structured = elem == MG_Q1;
-                if (!L.structured) {
-                    plan_matrix(L.P, P[l], MG_STORAGE_CSR, dim, L.N, sv, S, take);
-                    plan_matrix(L.R, R[l], MG_STORAGE_CSR, dim, L.N, sv, S, take);
+                if (!L.structured && xP[l].ok && xR[l].ok) {
+                    for (int t = 0; t < 2; t++) {
+                        XferD &X = t == 0 ? L.Pt : L.Rt;
+                        const XferTables &Tb = t == 0 ? xP[l] : xR[l];
+                        X.on = true;
+                        X.geo = Tb.geo;
+                        X.nent = (int)Tb.ent.size();
+                        X.cls = (int32_t *)vec((size_t)(mgk::XF_CLASSES + 1) * 4);
+                        X.ent = (int32_t *)vec((size_t)std::max(X.nent, 1) * 4);
+                        X.w = vec((size_t)std::max(X.nent, 1) * sv);
+                    }
+                } else if (!L.structured) {
+                    plan_matrix(L.P, P[l], MG_STORAGE_SELL, dim, L.N, sv, S, take);
+                    plan_matrix(L.R, R[l], MG_STORAGE_SELL, dim, L.N, sv, S, take);
                 }
             }
         }
@@ -1546,7 +1702,21 @@ void mgi::build_hierarchy(mg_hierarchy *h, const mg_problem *p, const mg_options
             std::vector<float> v32;
             mgh::round_fp32(A[l], v32);
             upload_matrix<float>(L.A, A[l], v32, dim, L.N, h->s);
-            if (l >= 1 && !L.structured) {
+            if (L.A.dinv) {
+                std::vector<float> dv((size_t)L.A.ld, 0.0f);
+                for (int64_t i = 0; i < A[l].nrows; i++)
+                    for (int64_t k = A[l].rowptr[i]; k < A[l].rowptr[i + 1]; k++)
+                        if (A[l].col[k] == i) {
+                            dv[i] = 1.0f / v32[k];
+                            break;
+                        }
+                CK(cudaMemcpyAsync(L.A.dinv, dv.data(), dv.size() * 4, cudaMemcpyHostToDevice, h->s));
+                CK(cudaStreamSynchronize(h->s));
+            }
+            if (l >= 1 && L.Pt.on) {
+                upload_xfer<float>(L.Pt, xP[l], h->s);
+                upload_xfer<float>(L.Rt, xR[l], h->s);
+            } else if (l >= 1 && !L.structured) {
                 upload_matrix<float>(L.P, P[l], to_f32(P[l].val), dim, L.N, h->s);
                 upload_matrix<float>(L.R, R[l], to_f32(R[l].val), dim, L.N, h->s);
             }
@@ -1560,7 +1730,10 @@ void mgi::build_hierarchy(mg_hierarchy *h, const mg_problem *p, const mg_options
                 CK(cudaMemcpyAsync(L.A.dinv, dv.data(), dv.size() * 8, cudaMemcpyHostToDevice, h->s));
                 CK(cudaStreamSynchronize(h->s));
             }
-            if (l >= 1 && !L.structured) {
+            if (l >= 1 && L.Pt.on) {
+                upload_xfer<double>(L.Pt, xP[l], h->s);
+                upload_xfer<double>(L.Rt, xR[l], h->s);
+            } else if (l >= 1 && !L.structured) {
                 upload_matrix<double>(L.P, P[l], P[l].val, dim, L.N, h->s);
                 upload_matrix<double>(L.R, R[l], R[l].val, dim, L.N, h->s);
             }
@@ -1702,6 +1875,9 @@ extern "C" mg_status mg_get_info(const mg_hierarchy *h, mg_info *info)
         info->storage[l] = h->lev[l].fmt;
         info->galerkin[l] = h->lev[l].galerkin;
         info->lambda[l] = h->lev[l].lambda;
+        const LevelD &L = h->lev[l];
+        info->transfer[l] = l == 0 ? MG_TRANSFER_NONE
+                                   : (L.structured ? MG_TRANSFER_GRID : (L.Pt.on ? MG_TRANSFER_TABLE : MG_TRANSFER_SELL));
     }
     info->device_bytes = h->slab.size;
     info->kernels_per_cycle = h->kernels_per_cycle;
@@ -2002,6 +2178,37 @@ extern "C" mg_status mg_assemble_operator(const mg_problem *p, int level, int wh
     }
 }
 
+extern "C" mg_status mg_transfer_tables(const mg_problem *p, int level, int *ok, int *n_entries)
+{
+    try {
+        validate_problem(p);
+        if (!ok || !n_entries) throw Error(MG_EINVAL, "NULL argument");
+        if (level < 1 || level > p->n_levels - 1) throw Error(MG_EINVAL, "bad level");
+        ok[0] = ok[1] = n_entries[0] = n_entries[1] = 0;
+        mgh::HostHierarchy HH;
+        mgh::build_hierarchy(p->dim, p->element, p->n_cells, p->n_levels, p->k_cell, level - 1, HH, p->mass);
+        mgk::XferGeom gp, gr;
+        if (!lattice_of(p->dim, p->element, HH.N[level], gp.row) ||
+            !lattice_of(p->dim, p->element, HH.N[level - 1], gp.col))
+            return MG_OK;
+        gr.row = gp.col;
+        gr.col = gp.row;
+        gr.row_coarse = 1;
+        XferTables tp = learn_xfer(HH.P[level], gp), tr = learn_xfer(HH.R[level], gr);
+        ok[0] = tp.ok;
+        ok[1] = tr.ok;
+        n_entries[0] = tp.ok ? (int)tp.ent.size() : 0;
+        n_entries[1] = tr.ok ? (int)tr.ent.size() : 0;
+        return MG_OK;
+    } catch (const Error &e) {
+        g_err = e.msg;
+        return e.st;
+    } catch (const std::bad_alloc &) {
+        g_err = "host allocation failed";
+        return MG_ENOMEM;
+    }
+}
+
 // ------------------------------------------------------------------------------------
 // Export and profiling
 // ------------------------------------------------------------------------------------
@@ -2013,7 +2220,42 @@ static std::vector<double> download_vals(const DevMat &m, size_t count)
     return std::vector<double>(v.begin(), v.end());
 }
 
-static void export_dev(const DevMat &m, int dim, int N, int sv, mgh::Csr &out)
+// a table-driven transfer as CSR: the device tables, each row generated as the kernel does
+static void export_xfer(const XferD &X, int64_t nrows, int sv, mgh::Csr &out)
+{
+    std::vector<int32_t> cls(mgk::XF_CLASSES + 1), ent((size_t)X.nent);
+    std::vector<double> w((size_t)X.nent);
+    CK(cudaMemcpy(cls.data(), X.cls, cls.size() * 4, cudaMemcpyDeviceToHost));
+    if (X.nent) {
+        CK(cudaMemcpy(ent.data(), X.ent, ent.size() * 4, cudaMemcpyDeviceToHost));
+        if (sv == 8) {
+            CK(cudaMemcpy(w.data(), X.w, w.size() * 8, cudaMemcpyDeviceToHost));
+        } else {
+            std::vector<float> wf(w.size());
+            CK(cudaMemcpy(wf.data(), X.w, wf.size() * 4, cudaMemcpyDeviceToHost));
+            for (size_t e = 0; e < w.size(); e++) w[e] = wf[e];
+        }
+    }
+    out.nrows = nrows;
+    out.rowptr.assign((size_t)nrows + 1, 0);
+    out.col.clear();
+    out.val.clear();
+    for (int64_t r = 0; r < nrows; r++) {
+        int X3[3];
+        int key = mgk::xf_row(X.geo, r, X3);
+        for (int e = cls[key]; e < cls[key + 1]; e++) {
+            int64_t c = mgk::xf_col(X.geo, X3, ent[e]);
+            if (c < 0) continue;
+            out.col.push_back((int32_t)c);
+            out.val.push_back(w[e]);
+        }
+        out.rowptr[r + 1] = (int64_t)out.col.size();
+    }
+}
+
+// transfers: the padding of a row without entries is a zero in column 0; transfer
+// operators hold no stored zeros, so drop_zero removes exactly the padding
+static void export_dev(const DevMat &m, int dim, int N, int sv, mgh::Csr &out, bool drop_zero = false)
 {
     out.nrows = m.n;
     out.rowptr.assign((size_t)m.n + 1, 0);
@@ -2041,6 +2283,7 @@ static void export_dev(const DevMat &m, int dim, int N, int sv, mgh::Csr &out)
             for (int64_t k = 0; k < Ks; k++) {
                 size_t e = (size_t)(sptr[sl] + 32 * k + r % 32);
                 if (c[e] <= prev) break;  // padding (column i after larger columns)
+                if (drop_zero && v[e] == 0.0) continue;
                 prev = c[e];
                 rows[perm[r]].push_back({c[e], v[e]});
             }
@@ -2119,8 +2362,10 @@ extern "C" mg_status mg_export_operator(const mg_hierarchy *hc, int level, int w
                 m = P;
             else
                 mgh::transpose(P, m);
+        } else if (L.Pt.on) {
+            export_xfer(which == 1 ? L.Pt : L.Rt, which == 1 ? L.n : h->lev[level - 1].n, h->inner_size, m);
         } else {
-            export_dev(which == 1 ? L.P : L.R, h->dim, L.N, h->inner_size, m);
+            export_dev(which == 1 ? L.P : L.R, h->dim, L.N, h->inner_size, m, true);
             if (which == 2) m.nrows = h->lev[level - 1].n;
         }
         if (which == 2 && L.structured) m.nrows = h->lev[level - 1].n;

@@ -66,7 +66,8 @@ struct MatView {
     const int32_t *col;    // ELL: K*ld; CSR: nnz; SELL: padded slices
     const int64_t *rowptr; // CSR: row starts; SELL: slice starts (entries)
     const int32_t *perm;   // SELL: DOF of storage position r
-    const T *dinv;         // 1 / a_ii (FP64 levels), by DOF
+    const T *dinv;         // 1 / a_ii by DOF: FP64 levels; FP32 ELL/CSR/SELL levels (read
+                           // only by sweeps from x = 0, which then skip the row scan)
     int64_t ld;
     int K;
     int center;            // DIA: slot of the diagonal
@@ -142,7 +143,8 @@ __global__ void __launch_bounds__(256) k_ell_sweep(MatView<T> A, int n, const T 
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     T s = T(0), diag = T(0);
-    if (!IsZero<MODE>::value || !Ar<T>::kStoredDinv) {
+    const bool zd = IsZero<MODE>::value && (Ar<T>::kStoredDinv || A.dinv != nullptr);
+    if (!zd) {
         for (int k = 0; k < A.K; k++) {
             int c = __ldcs(A.col + (int64_t)k * A.ld + i);
             T v = __ldcs(A.val + (int64_t)k * A.ld + i);
@@ -150,7 +152,7 @@ __global__ void __launch_bounds__(256) k_ell_sweep(MatView<T> A, int n, const T 
             if (!IsZero<MODE>::value) s = Ar<T>::mac(s, v, __ldg(x + c));
         }
     }
-    T dinv = Ar<T>::kStoredDinv ? __ldcs(A.dinv + i) : Ar<T>::rcp(diag);
+    T dinv = Ar<T>::kStoredDinv || zd ? __ldcs(A.dinv + i) : Ar<T>::rcp(diag);
     sweep_out<T, MODE>(i, s, dinv, IsZero<MODE>::value ? T(0) : x[i], b, out, d, c1, c2);
 }
 
@@ -163,7 +165,8 @@ __global__ void __launch_bounds__(256) k_csr_sweep(MatView<T> A, int n, const T 
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     T s = T(0), diag = T(0);
-    if (!IsZero<MODE>::value || !Ar<T>::kStoredDinv) {
+    const bool zd = IsZero<MODE>::value && (Ar<T>::kStoredDinv || A.dinv != nullptr);
+    if (!zd) {
         int64_t k0 = A.rowptr[i], k1 = A.rowptr[i + 1];
         for (int64_t k = k0; k < k1; k++) {
             int c = A.col[k];
@@ -172,7 +175,7 @@ __global__ void __launch_bounds__(256) k_csr_sweep(MatView<T> A, int n, const T 
             if (!IsZero<MODE>::value) s = Ar<T>::mac(s, v, __ldg(x + c));
         }
     }
-    T dinv = Ar<T>::kStoredDinv ? A.dinv[i] : Ar<T>::rcp(diag);
+    T dinv = Ar<T>::kStoredDinv || zd ? A.dinv[i] : Ar<T>::rcp(diag);
     sweep_out<T, MODE>(i, s, dinv, IsZero<MODE>::value ? T(0) : x[i], b, out, d, c1, c2);
 }
 
@@ -190,7 +193,8 @@ __global__ void __launch_bounds__(256) k_sell_sweep(MatView<T> A, int n, const T
     if (r >= n) return;
     int i = __ldg(A.perm + r);
     T s = T(0), diag = T(0);
-    if (!IsZero<MODE>::value || !Ar<T>::kStoredDinv) {
+    const bool zd = IsZero<MODE>::value && (Ar<T>::kStoredDinv || A.dinv != nullptr);
+    if (!zd) {
         int64_t base = A.rowptr[r >> 5];
         int Ks = (int)((A.rowptr[(r >> 5) + 1] - base) >> 5);
         int64_t e = base + (r & 31);
@@ -201,7 +205,7 @@ __global__ void __launch_bounds__(256) k_sell_sweep(MatView<T> A, int n, const T
             if (!IsZero<MODE>::value) s = Ar<T>::mac(s, v, __ldg(x + c));
         }
     }
-    T dinv = Ar<T>::kStoredDinv ? __ldcs(A.dinv + i) : Ar<T>::rcp(diag);
+    T dinv = Ar<T>::kStoredDinv || zd ? __ldcs(A.dinv + i) : Ar<T>::rcp(diag);
     sweep_out<T, MODE>(i, s, dinv, IsZero<MODE>::value ? T(0) : x[i], b, out, d, c1, c2);
 }
 
