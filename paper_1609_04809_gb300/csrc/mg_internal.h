@@ -52,8 +52,8 @@ struct DevMat {
 // A transfer generated from per-class tables (transfer.cuh); on = false: not used.
 struct XferD {
     bool on = false;
-    mgk::XferGeom geo;
-    int32_t *cls = nullptr, *ent = nullptr;
+    mgk::XferDev geo;
+    int32_t *cls = nullptr, *ent = nullptr, *dlt = nullptr;
     void *w = nullptr;  // weights in the inner precision
     int nent = 0;
 };

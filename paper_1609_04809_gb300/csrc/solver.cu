@@ -470,6 +470,20 @@ static int smooth(mg_hierarchy *h, int l, int c, bool post, cudaStream_t s)
     return c;
 }
 
+// launch shape of a table-driven transfer: x over t_0, y over t_1, z over the t_2 planes
+static void xfer_shape(const mgk::XferDev &G, dim3 &grid, dim3 &block)
+{
+    int n0 = 0, n1 = 0, nz = 0;
+    for (int g = 0; g < G.ng; g++) {
+        n0 = std::max(n0, G.n[g][0]);
+        n1 = std::max(n1, G.n[g][1]);
+        nz += G.n[g][2];
+    }
+    unsigned bx = line_block((unsigned)n0), by = std::max(1u, std::min(256u / bx, (unsigned)n1));
+    block = dim3(bx, by, 1);
+    grid = dim3(((unsigned)n0 + bx - 1) / bx, ((unsigned)n1 + by - 1) / by, (unsigned)nz);
+}
+
 template <typename T>
 static void restrict_to(mg_hierarchy *h, int l, const T *r, cudaStream_t s)
 {
@@ -495,9 +509,10 @@ static void restrict_to(mg_hierarchy *h, int l, const T *r, cudaStream_t s)
         else
             klaunch(pdl, k_restrict_q1<T, 2>, g, dim3(bx), 0, s, r, (T *)C.b, C.N);
     } else if (F.Rt.on) {
-        XferView<T> v{F.Rt.geo, F.Rt.cls, F.Rt.ent, (const T *)F.Rt.w};
-        klaunch(h->opt.use_pdl != 0, k_xfer_apply<T, false>, dim3(grid_for(C.n)), dim3(256), 0, s, v, (int)C.n, r,
-                (T *)C.b);
+        dim3 g, b;
+        xfer_shape(F.Rt.geo, g, b);
+        klaunch(h->opt.use_pdl != 0, k_xfer_apply<T, false>, g, b, 0, s, F.Rt.geo, (const int32_t *)F.Rt.cls,
+                (const int32_t *)F.Rt.ent, (const int32_t *)F.Rt.dlt, (const T *)F.Rt.w, r, (T *)C.b);
     } else if (F.R.fmt == MG_STORAGE_SELL) {
         klaunch(h->opt.use_pdl != 0, k_sell_apply<T, false>, dim3(grid_for(C.n)), dim3(256), 0, s,
                 (const int64_t *)F.R.rowptr, (const int32_t *)F.R.col, (const T *)F.R.val, (const int32_t *)F.R.perm,
@@ -534,8 +549,10 @@ static void prolong_add(mg_hierarchy *h, int l, const T *xc, T *xf, cudaStream_t
         else
             klaunch(pdl, k_prolong_q1<T, 2>, g, dim3(bx), 0, s, xc, xf, C.N);
     } else if (F.Pt.on) {
-        XferView<T> v{F.Pt.geo, F.Pt.cls, F.Pt.ent, (const T *)F.Pt.w};
-        klaunch(h->opt.use_pdl != 0, k_xfer_apply<T, true>, dim3(grid_for(F.n)), dim3(256), 0, s, v, (int)F.n, xc, xf);
+        dim3 g, b;
+        xfer_shape(F.Pt.geo, g, b);
+        klaunch(h->opt.use_pdl != 0, k_xfer_apply<T, true>, g, b, 0, s, F.Pt.geo, (const int32_t *)F.Pt.cls,
+                (const int32_t *)F.Pt.ent, (const int32_t *)F.Pt.dlt, (const T *)F.Pt.w, xc, xf);
     } else if (F.P.fmt == MG_STORAGE_SELL) {
         klaunch(h->opt.use_pdl != 0, k_sell_apply<T, true>, dim3(grid_for(F.n)), dim3(256), 0, s,
                 (const int64_t *)F.P.rowptr, (const int32_t *)F.P.col, (const T *)F.P.val, (const int32_t *)F.P.perm,
@@ -1057,60 +1074,115 @@ static bool lattice_of(int dim, int elem, int N, mgk::LatGeom &G)
 
 struct XferTables {
     bool ok = false;
-    mgk::XferGeom geo;
-    std::vector<int32_t> cls, ent;
+    mgk::XferDev dev;
+    std::vector<int32_t> cls, ent, dlt;
     std::vector<double> w;
 };
 
-// Learn the class tables of transfer M (rows and columns on the lattices of geo): each
-// class takes the entries of its longest row, as offsets from the row's position. Then
-// every row is generated from its class and compared with the stored row; ok only if
-// all agree in columns, order and weights.
-static XferTables learn_xfer(const mgh::Csr &M, const mgk::XferGeom &geo)
+// DOF r of lattice G: its family and position in the level's frame
+static void lat_decode(const mgk::LatGeom &G, int64_t r, int &g, int X[3])
+{
+    g = 0;
+    while (g + 1 < G.ng && r >= G.base[g + 1]) g++;
+    int64_t t = r - G.base[g];
+    int64_t n0 = G.n[g][0], n1 = G.n[g][1];
+    X[0] = G.o[g][0] + G.s * (int)(t % n0);
+    X[1] = G.o[g][1] + G.s * (int)((t / n0) % n1);
+    X[2] = G.o[g][2] + G.s * (int)(t / (n0 * n1));
+}
+
+// Learn the class tables of transfer M, rows on lattice rowG and columns on colG
+// (coarse_rows: R, rows on the coarse level; else P): each class takes the entries of its
+// longest row. Then every row is generated with the kernel's column arithmetic
+// (transfer.cuh), by the fast and the range-tested path where both apply, and compared
+// with the stored row; ok only if all agree in columns, order and weights.
+static XferTables learn_xfer(const mgh::Csr &M, const mgk::LatGeom &rowG, const mgk::LatGeom &colG, bool coarse_rows)
 {
     XferTables T;
-    T.geo = geo;
+    mgk::XferDev &G = T.dev;
+    if (rowG.base[rowG.ng] >= INT32_MAX || colG.base[colG.ng] >= INT32_MAX) return T;
+    G.ng = rowG.ng;
+    G.s = rowG.s;
+    G.rm = coarse_rows ? 2 : 1;
+    G.c = coarse_rows ? 1 : 2;
+    int q = G.c * colG.s;
+    G.qs = q == 1 ? 0 : (q == 2 ? 1 : 2);
+    G.cng = colG.ng;
+    int z = 0;
+    for (int g = 0; g < 3; g++)
+        for (int d = 0; d < 3; d++) {
+            G.o[g][d] = rowG.o[g][d];
+            G.n[g][d] = rowG.n[g][d];
+            G.co[g][d] = colG.o[g][d];
+            G.cn[g][d] = colG.n[g][d];
+        }
+    for (int g = 0; g < G.ng; g++) {
+        G.base[g] = (int)rowG.base[g];
+        G.zb[g] = z;
+        z += G.n[g][2];
+    }
+    for (int h = 0; h < G.cng; h++) G.cbase[h] = (int)colG.base[h];
     const int64_t n = M.nrows;
     std::vector<int64_t> rep(mgk::XF_CLASSES, -1);
     for (int64_t r = 0; r < n; r++) {
-        int X[3];
-        int key = mgk::xf_row(geo, r, X);
+        int g, X[3];
+        lat_decode(rowG, r, g, X);
+        int key = g * 64 + ((X[0] * G.rm) & 3) + 4 * ((X[1] * G.rm) & 3) + 16 * ((X[2] * G.rm) & 3);
         int64_t len = M.rowptr[r + 1] - M.rowptr[r];
         if (rep[key] < 0 || len > M.rowptr[rep[key] + 1] - M.rowptr[rep[key]]) rep[key] = r;
+    }
+    for (int h = 0; h < 3; h++) {
+        G.lo[h] = 0;
+        G.hi[h] = 0;
     }
     T.cls.assign(mgk::XF_CLASSES + 1, 0);
     for (int key = 0; key < mgk::XF_CLASSES; key++) {
         T.cls[key] = (int32_t)T.ent.size();
         int64_t r = rep[key];
         if (r < 0) continue;
-        int X[3];
-        mgk::xf_row(geo, r, X);
+        int g, X[3];
+        lat_decode(rowG, r, g, X);
+        for (int d = 0; d < 3; d++) X[d] *= G.rm;  // fine frame
         for (int64_t k = M.rowptr[r]; k < M.rowptr[r + 1]; k++) {
-            int g, Y[3], D[3];
-            mgk::lat_decode(geo.col, M.col[k], g, Y);
+            int h, Z[3], dl[3];
+            lat_decode(colG, M.col[k], h, Z);
             for (int d = 0; d < 3; d++) {
-                D[d] = (geo.row_coarse ? Y[d] : 2 * Y[d]) - X[d];
-                if (D[d] < -128 || D[d] > 127) return T;
+                // target lattice coordinate t' = (Z - o') / s'; the anchor a = floor((X - c o') / q)
+                int tt = (Z[d] - colG.o[h][d]) / colG.s;
+                int v = X[d] - G.c * colG.o[h][d];
+                int a = v >= 0 ? v / q : -((-v + q - 1) / q);
+                dl[d] = tt - a;
+                if (dl[d] < -128 || dl[d] > 127) return T;
+                G.lo[h] = std::min(G.lo[h], dl[d]);
+                G.hi[h] = std::max(G.hi[h], dl[d]);
             }
-            T.ent.push_back(mgk::xf_pack(D[0], D[1], D[2], g));
+            T.ent.push_back(mgk::xf_pack(dl[0], dl[1], dl[2], h));
+            T.dlt.push_back(dl[0] + colG.n[h][0] * (dl[1] + colG.n[h][1] * dl[2]));
             T.w.push_back(M.val[k]);
         }
     }
     T.cls[mgk::XF_CLASSES] = (int32_t)T.ent.size();
     int64_t bad = 0;
+    for (int g = 0; g < G.ng; g++) {
 #pragma omp parallel for schedule(static) reduction(+ : bad)
-    for (int64_t r = 0; r < n; r++) {
-        int X[3];
-        int key = mgk::xf_row(geo, r, X);
-        int64_t k = M.rowptr[r], k1 = M.rowptr[r + 1];
-        bool good = true;
-        for (int e = T.cls[key]; e < T.cls[key + 1] && good; e++) {
-            int64_t c = mgk::xf_col(geo, X, T.ent[e]);
-            if (c < 0) continue;  // a boundary DOF: not in the row
-            if (k >= k1 || M.col[k] != c || M.val[k] != T.w[e]) good = false;
-            k++;
-        }
-        if (!good || k != k1) bad++;
+        for (int t2 = 0; t2 < G.n[g][2]; t2++)
+            for (int t1 = 0; t1 < G.n[g][1]; t1++)
+                for (int t0 = 0; t0 < G.n[g][0]; t0++) {
+                    mgk::XferRow R;
+                    mgk::xf_row_setup(G, g, t0, t1, t2, R);
+                    mgk::XferRow Rs = R;
+                    Rs.inside = false;  // the range-tested path
+                    int64_t k = M.rowptr[R.r], k1 = M.rowptr[R.r + 1];
+                    bool good = true;
+                    for (int e = T.cls[R.key]; e < T.cls[R.key + 1] && good; e++) {
+                        int c = mgk::xf_entry_col(G, R, T.ent[e], T.dlt[e]);
+                        if (mgk::xf_entry_col(G, Rs, T.ent[e], T.dlt[e]) != c) good = false;
+                        if (c < 0) continue;  // a boundary DOF: not in the row
+                        if (k >= k1 || M.col[k] != c || M.val[k] != T.w[e]) good = false;
+                        k++;
+                    }
+                    if (!good || k != k1) bad++;
+                }
     }
     T.ok = bad == 0;
     return T;
@@ -1124,6 +1196,7 @@ static void upload_xfer(const XferD &X, const XferTables &Tb, cudaStream_t s)
     CK(cudaMemcpyAsync(X.cls, Tb.cls.data(), Tb.cls.size() * 4, cudaMemcpyHostToDevice, s));
     if (!w.empty()) {
         CK(cudaMemcpyAsync(X.ent, Tb.ent.data(), Tb.ent.size() * 4, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(X.dlt, Tb.dlt.data(), Tb.dlt.size() * 4, cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(X.w, w.data(), w.size() * sizeof(T), cudaMemcpyHostToDevice, s));
     }
     CK(cudaStreamSynchronize(s));
@@ -1589,13 +1662,10 @@ void mgi::build_hierarchy(mg_hierarchy *h, const mg_problem *p, const mg_options
     // ---- transfer tables of the lattice elements (checked against every row) ----
     std::vector<XferTables> xP((size_t)nlev), xR((size_t)nlev);
     for (int l = 1; l <= Lf; l++) {
-        mgk::XferGeom gp, gr;
-        if (!lattice_of(dim, elem, h->lev[l].N, gp.row) || !lattice_of(dim, elem, h->lev[l - 1].N, gp.col)) continue;
-        gr.row = gp.col;
-        gr.col = gp.row;
-        gr.row_coarse = 1;
-        xP[l] = learn_xfer(P[l], gp);
-        xR[l] = learn_xfer(R[l], gr);
+        mgk::LatGeom gf, gc;
+        if (!lattice_of(dim, elem, h->lev[l].N, gf) || !lattice_of(dim, elem, h->lev[l - 1].N, gc)) continue;
+        xP[l] = learn_xfer(P[l], gf, gc, false);
+        xR[l] = learn_xfer(R[l], gc, gf, true);
     }
     for (int pass = 0; pass < 2; pass++) {
         bool take = pass == 1;
@@ -1654,10 +1724,11 @@ void mgi::build_hierarchy(mg_hierarchy *h, const mg_problem *p, const mg_options
                         XferD &X = t == 0 ? L.Pt : L.Rt;
                         const XferTables &Tb = t == 0 ? xP[l] : xR[l];
                         X.on = true;
-                        X.geo = Tb.geo;
+                        X.geo = Tb.dev;
                         X.nent = (int)Tb.ent.size();
                         X.cls = (int32_t *)vec((size_t)(mgk::XF_CLASSES + 1) * 4);
                         X.ent = (int32_t *)vec((size_t)std::max(X.nent, 1) * 4);
+                        X.dlt = (int32_t *)vec((size_t)std::max(X.nent, 1) * 4);
                         X.w = vec((size_t)std::max(X.nent, 1) * sv);
                     }
                 } else if (!L.structured) {
@@ -2187,14 +2258,10 @@ extern "C" mg_status mg_transfer_tables(const mg_problem *p, int level, int *ok,
         ok[0] = ok[1] = n_entries[0] = n_entries[1] = 0;
         mgh::HostHierarchy HH;
         mgh::build_hierarchy(p->dim, p->element, p->n_cells, p->n_levels, p->k_cell, level - 1, HH, p->mass);
-        mgk::XferGeom gp, gr;
-        if (!lattice_of(p->dim, p->element, HH.N[level], gp.row) ||
-            !lattice_of(p->dim, p->element, HH.N[level - 1], gp.col))
+        mgk::LatGeom gf, gc;
+        if (!lattice_of(p->dim, p->element, HH.N[level], gf) || !lattice_of(p->dim, p->element, HH.N[level - 1], gc))
             return MG_OK;
-        gr.row = gp.col;
-        gr.col = gp.row;
-        gr.row_coarse = 1;
-        XferTables tp = learn_xfer(HH.P[level], gp), tr = learn_xfer(HH.R[level], gr);
+        XferTables tp = learn_xfer(HH.P[level], gf, gc, false), tr = learn_xfer(HH.R[level], gc, gf, true);
         ok[0] = tp.ok;
         ok[1] = tr.ok;
         n_entries[0] = tp.ok ? (int)tp.ent.size() : 0;
@@ -2223,11 +2290,12 @@ static std::vector<double> download_vals(const DevMat &m, size_t count)
 // a table-driven transfer as CSR: the device tables, each row generated as the kernel does
 static void export_xfer(const XferD &X, int64_t nrows, int sv, mgh::Csr &out)
 {
-    std::vector<int32_t> cls(mgk::XF_CLASSES + 1), ent((size_t)X.nent);
+    std::vector<int32_t> cls(mgk::XF_CLASSES + 1), ent((size_t)X.nent), dlt((size_t)X.nent);
     std::vector<double> w((size_t)X.nent);
     CK(cudaMemcpy(cls.data(), X.cls, cls.size() * 4, cudaMemcpyDeviceToHost));
     if (X.nent) {
         CK(cudaMemcpy(ent.data(), X.ent, ent.size() * 4, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(dlt.data(), X.dlt, dlt.size() * 4, cudaMemcpyDeviceToHost));
         if (sv == 8) {
             CK(cudaMemcpy(w.data(), X.w, w.size() * 8, cudaMemcpyDeviceToHost));
         } else {
@@ -2236,18 +2304,27 @@ static void export_xfer(const XferD &X, int64_t nrows, int sv, mgh::Csr &out)
             for (size_t e = 0; e < w.size(); e++) w[e] = wf[e];
         }
     }
+    const mgk::XferDev &G = X.geo;
+    std::vector<std::vector<std::pair<int32_t, double>>> rows((size_t)nrows);
+    for (int g = 0; g < G.ng; g++)
+        for (int t2 = 0; t2 < G.n[g][2]; t2++)
+            for (int t1 = 0; t1 < G.n[g][1]; t1++)
+                for (int t0 = 0; t0 < G.n[g][0]; t0++) {
+                    mgk::XferRow R;
+                    mgk::xf_row_setup(G, g, t0, t1, t2, R);
+                    for (int e = cls[R.key]; e < cls[R.key + 1]; e++) {
+                        int c = mgk::xf_entry_col(G, R, ent[e], dlt[e]);
+                        if (c >= 0) rows[R.r].push_back({c, w[e]});
+                    }
+                }
     out.nrows = nrows;
     out.rowptr.assign((size_t)nrows + 1, 0);
     out.col.clear();
     out.val.clear();
     for (int64_t r = 0; r < nrows; r++) {
-        int X3[3];
-        int key = mgk::xf_row(X.geo, r, X3);
-        for (int e = cls[key]; e < cls[key + 1]; e++) {
-            int64_t c = mgk::xf_col(X.geo, X3, ent[e]);
-            if (c < 0) continue;
-            out.col.push_back((int32_t)c);
-            out.val.push_back(w[e]);
+        for (auto &e : rows[r]) {
+            out.col.push_back(e.first);
+            out.val.push_back(e.second);
         }
         out.rowptr[r + 1] = (int64_t)out.col.size();
     }
