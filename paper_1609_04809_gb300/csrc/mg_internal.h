@@ -49,13 +49,15 @@ struct DevMat {
     void *dinv = nullptr;  // 1 / a_ii, FP64 inner levels only
 };
 
-// A transfer generated from per-class tables (transfer.cuh); on = false: not used.
+// A transfer generated from per-class tables on the interior boxes (transfer.cuh) and
+// stored explicitly (SELL-32, B) on the other rows; on = false: not used.
 struct XferD {
     bool on = false;
     mgk::XferDev geo;
-    int32_t *cls = nullptr, *ent = nullptr, *dlt = nullptr;
+    int32_t *cls = nullptr, *ent = nullptr;
     void *w = nullptr;  // weights in the inner precision
     int nent = 0;
+    DevMat B;           // the rows outside the boxes; B.perm holds their row indices
 };
 
 struct LevelD {

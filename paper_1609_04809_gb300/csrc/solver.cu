@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -470,18 +471,21 @@ static int smooth(mg_hierarchy *h, int l, int c, bool post, cudaStream_t s)
     return c;
 }
 
-// launch shape of a table-driven transfer: x over t_0, y over t_1, z over the t_2 planes
-static void xfer_shape(const mgk::XferDev &G, dim3 &grid, dim3 &block)
+// a table-driven transfer: the interior boxes from the tables, the other rows explicit
+// (the launch scope counts one launch; the second one is counted here)
+template <typename T, bool ADD>
+static void xfer_launch(mg_hierarchy *h, const XferD &X, const T *x, T *y, cudaStream_t s)
 {
-    int n0 = 0, n1 = 0, nz = 0;
-    for (int g = 0; g < G.ng; g++) {
-        n0 = std::max(n0, G.n[g][0]);
-        n1 = std::max(n1, G.n[g][1]);
-        nz += G.n[g][2];
+    const mgk::XferDev &G = X.geo;
+    bool pdl = h->opt.use_pdl != 0;
+    dim3 grid((unsigned)((G.bmax01 + 255) / 256), 1, (unsigned)G.bz[G.ng]);
+    klaunch(pdl, k_xfer_apply<T, ADD>, grid, dim3(256), 0, s, G, (const int32_t *)X.cls, (const int32_t *)X.ent,
+            (const T *)X.w, x, y);
+    if (X.B.n > 0) {
+        if (h->counting) h->kernels_per_cycle++;
+        klaunch(pdl, k_sell_apply<T, ADD>, dim3(grid_for(X.B.n)), dim3(256), 0, s, (const int64_t *)X.B.rowptr,
+                (const int32_t *)X.B.col, (const T *)X.B.val, (const int32_t *)X.B.perm, (int)X.B.n, x, y);
     }
-    unsigned bx = line_block((unsigned)n0), by = std::max(1u, std::min(256u / bx, (unsigned)n1));
-    block = dim3(bx, by, 1);
-    grid = dim3(((unsigned)n0 + bx - 1) / bx, ((unsigned)n1 + by - 1) / by, (unsigned)nz);
 }
 
 template <typename T>
@@ -498,7 +502,10 @@ static void restrict_to(mg_hierarchy *h, int l, const T *r, cudaStream_t s)
     }
     int sv = sizeof(T);
     double bytes = (double)F.n * sv + (double)C.n * sv;
-    if (!F.structured && !F.Rt.on) bytes += mat_bytes(F.R, sv);
+    if (F.Rt.on)
+        bytes += F.Rt.B.n > 0 ? mat_bytes(F.Rt.B, sv) : 0.0;
+    else if (!F.structured)
+        bytes += mat_bytes(F.R, sv);
     LaunchScope ls(h, s, MG_K_RESTRICT, l, bytes);
     if (F.structured) {
         unsigned l1 = (unsigned)(C.N - 1), bx = line_block(l1);
@@ -509,10 +516,7 @@ static void restrict_to(mg_hierarchy *h, int l, const T *r, cudaStream_t s)
         else
             klaunch(pdl, k_restrict_q1<T, 2>, g, dim3(bx), 0, s, r, (T *)C.b, C.N);
     } else if (F.Rt.on) {
-        dim3 g, b;
-        xfer_shape(F.Rt.geo, g, b);
-        klaunch(h->opt.use_pdl != 0, k_xfer_apply<T, false>, g, b, 0, s, F.Rt.geo, (const int32_t *)F.Rt.cls,
-                (const int32_t *)F.Rt.ent, (const int32_t *)F.Rt.dlt, (const T *)F.Rt.w, r, (T *)C.b);
+        xfer_launch<T, false>(h, F.Rt, r, (T *)C.b, s);
     } else if (F.R.fmt == MG_STORAGE_SELL) {
         klaunch(h->opt.use_pdl != 0, k_sell_apply<T, false>, dim3(grid_for(C.n)), dim3(256), 0, s,
                 (const int64_t *)F.R.rowptr, (const int32_t *)F.R.col, (const T *)F.R.val, (const int32_t *)F.R.perm,
@@ -538,7 +542,10 @@ static void prolong_add(mg_hierarchy *h, int l, const T *xc, T *xf, cudaStream_t
     }
     int sv = sizeof(T);
     double bytes = 2.0 * F.n * sv + (double)C.n * sv;
-    if (!F.structured && !F.Pt.on) bytes += mat_bytes(F.P, sv);
+    if (F.Pt.on)
+        bytes += F.Pt.B.n > 0 ? mat_bytes(F.Pt.B, sv) : 0.0;
+    else if (!F.structured)
+        bytes += mat_bytes(F.P, sv);
     LaunchScope ls(h, s, MG_K_PROLONG, l, bytes);
     if (F.structured) {
         unsigned l1 = (unsigned)(F.N - 1), nx = (unsigned)C.N, bx = line_block(nx);  // pairs of fine points
@@ -549,10 +556,7 @@ static void prolong_add(mg_hierarchy *h, int l, const T *xc, T *xf, cudaStream_t
         else
             klaunch(pdl, k_prolong_q1<T, 2>, g, dim3(bx), 0, s, xc, xf, C.N);
     } else if (F.Pt.on) {
-        dim3 g, b;
-        xfer_shape(F.Pt.geo, g, b);
-        klaunch(h->opt.use_pdl != 0, k_xfer_apply<T, true>, g, b, 0, s, F.Pt.geo, (const int32_t *)F.Pt.cls,
-                (const int32_t *)F.Pt.ent, (const int32_t *)F.Pt.dlt, (const T *)F.Pt.w, xc, xf);
+        xfer_launch<T, true>(h, F.Pt, xc, xf, s);
     } else if (F.P.fmt == MG_STORAGE_SELL) {
         klaunch(h->opt.use_pdl != 0, k_sell_apply<T, true>, dim3(grid_for(F.n)), dim3(256), 0, s,
                 (const int64_t *)F.P.rowptr, (const int32_t *)F.P.col, (const T *)F.P.val, (const int32_t *)F.P.perm,
@@ -1075,27 +1079,33 @@ static bool lattice_of(int dim, int elem, int N, mgk::LatGeom &G)
 struct XferTables {
     bool ok = false;
     mgk::XferDev dev;
-    std::vector<int32_t> cls, ent, dlt;
+    std::vector<int32_t> cls, ent;
     std::vector<double> w;
+    mgh::Csr bnd;                   // the rows outside the interior boxes, explicit
+    std::vector<int32_t> bnd_rows;  // their indices
 };
 
-// DOF r of lattice G: its family and position in the level's frame
-static void lat_decode(const mgk::LatGeom &G, int64_t r, int &g, int X[3])
+// DOF r of lattice G: its family and lattice point
+static void lat_decode(const mgk::LatGeom &G, int64_t r, int &g, int t[3])
 {
     g = 0;
     while (g + 1 < G.ng && r >= G.base[g + 1]) g++;
-    int64_t t = r - G.base[g];
+    int64_t u = r - G.base[g];
     int64_t n0 = G.n[g][0], n1 = G.n[g][1];
-    X[0] = G.o[g][0] + G.s * (int)(t % n0);
-    X[1] = G.o[g][1] + G.s * (int)((t / n0) % n1);
-    X[2] = G.o[g][2] + G.s * (int)(t / (n0 * n1));
+    t[0] = (int)(u % n0);
+    t[1] = (int)((u / n0) % n1);
+    t[2] = (int)(u / (n0 * n1));
 }
+
+static inline int floor_div(int v, int q) { return v >= 0 ? v / q : -((-v + q - 1) / q); }
 
 // Learn the class tables of transfer M, rows on lattice rowG and columns on colG
 // (coarse_rows: R, rows on the coarse level; else P): each class takes the entries of its
-// longest row. Then every row is generated with the kernel's column arithmetic
-// (transfer.cuh), by the fast and the range-tested path where both apply, and compared
-// with the stored row; ok only if all agree in columns, order and weights.
+// longest row. The interior box of each family is the longest run of lattice points per
+// axis on which every entry of every class lands inside its target lattice. Every box row
+// is generated with the kernel's arithmetic (transfer.cuh) and compared with the stored
+// row; ok only if all agree in columns, order and weights. The other rows are copied to
+// an explicit operator.
 static XferTables learn_xfer(const mgh::Csr &M, const mgk::LatGeom &rowG, const mgk::LatGeom &colG, bool coarse_rows)
 {
     XferTables T;
@@ -1105,10 +1115,9 @@ static XferTables learn_xfer(const mgh::Csr &M, const mgk::LatGeom &rowG, const 
     G.s = rowG.s;
     G.rm = coarse_rows ? 2 : 1;
     G.c = coarse_rows ? 1 : 2;
-    int q = G.c * colG.s;
+    const int q = G.c * colG.s;
     G.qs = q == 1 ? 0 : (q == 2 ? 1 : 2);
     G.cng = colG.ng;
-    int z = 0;
     for (int g = 0; g < 3; g++)
         for (int d = 0; d < 3; d++) {
             G.o[g][d] = rowG.o[g][d];
@@ -1116,90 +1125,118 @@ static XferTables learn_xfer(const mgh::Csr &M, const mgk::LatGeom &rowG, const 
             G.co[g][d] = colG.o[g][d];
             G.cn[g][d] = colG.n[g][d];
         }
-    for (int g = 0; g < G.ng; g++) {
-        G.base[g] = (int)rowG.base[g];
-        G.zb[g] = z;
-        z += G.n[g][2];
-    }
+    for (int g = 0; g < G.ng; g++) G.base[g] = (int)rowG.base[g];
     for (int h = 0; h < G.cng; h++) G.cbase[h] = (int)colG.base[h];
+    auto pos = [&](int g, int d, int t) { return (G.o[g][d] + G.s * t) * G.rm; };  // fine frame
+    auto key_of = [&](int g, const int t[3]) {
+        return g * 64 + (pos(g, 0, t[0]) & 3) + 4 * (pos(g, 1, t[1]) & 3) + 16 * (pos(g, 2, t[2]) & 3);
+    };
     const int64_t n = M.nrows;
     std::vector<int64_t> rep(mgk::XF_CLASSES, -1);
     for (int64_t r = 0; r < n; r++) {
-        int g, X[3];
-        lat_decode(rowG, r, g, X);
-        int key = g * 64 + ((X[0] * G.rm) & 3) + 4 * ((X[1] * G.rm) & 3) + 16 * ((X[2] * G.rm) & 3);
+        int g, t[3];
+        lat_decode(rowG, r, g, t);
+        int key = key_of(g, t);
         int64_t len = M.rowptr[r + 1] - M.rowptr[r];
         if (rep[key] < 0 || len > M.rowptr[rep[key] + 1] - M.rowptr[rep[key]]) rep[key] = r;
     }
-    for (int h = 0; h < 3; h++) {
-        G.lo[h] = 0;
-        G.hi[h] = 0;
-    }
+    // entries: target family, delta per axis, Delta, weight
+    std::vector<int> eh;
+    std::vector<std::array<int, 3>> edl;
     T.cls.assign(mgk::XF_CLASSES + 1, 0);
     for (int key = 0; key < mgk::XF_CLASSES; key++) {
         T.cls[key] = (int32_t)T.ent.size();
         int64_t r = rep[key];
         if (r < 0) continue;
-        int g, X[3];
-        lat_decode(rowG, r, g, X);
-        for (int d = 0; d < 3; d++) X[d] *= G.rm;  // fine frame
+        int g, t[3];
+        lat_decode(rowG, r, g, t);
         for (int64_t k = M.rowptr[r]; k < M.rowptr[r + 1]; k++) {
-            int h, Z[3], dl[3];
-            lat_decode(colG, M.col[k], h, Z);
-            for (int d = 0; d < 3; d++) {
-                // target lattice coordinate t' = (Z - o') / s'; the anchor a = floor((X - c o') / q)
-                int tt = (Z[d] - colG.o[h][d]) / colG.s;
-                int v = X[d] - G.c * colG.o[h][d];
-                int a = v >= 0 ? v / q : -((-v + q - 1) / q);
-                dl[d] = tt - a;
-                if (dl[d] < -128 || dl[d] > 127) return T;
-                G.lo[h] = std::min(G.lo[h], dl[d]);
-                G.hi[h] = std::max(G.hi[h], dl[d]);
-            }
-            T.ent.push_back(mgk::xf_pack(dl[0], dl[1], dl[2], h));
-            T.dlt.push_back(dl[0] + colG.n[h][0] * (dl[1] + colG.n[h][1] * dl[2]));
+            int h, tc[3];
+            lat_decode(colG, M.col[k], h, tc);
+            std::array<int, 3> dl;
+            for (int d = 0; d < 3; d++) dl[d] = tc[d] - floor_div(pos(g, d, t[d]) - G.c * colG.o[h][d], q);
+            int64_t D = dl[0] + (int64_t)colG.n[h][0] * (dl[1] + (int64_t)colG.n[h][1] * dl[2]);
+            if (D <= -(1 << 23) || D >= (1 << 23)) return T;
+            T.ent.push_back(mgk::xf_pack(h, (int)D));
             T.w.push_back(M.val[k]);
+            eh.push_back(h);
+            edl.push_back(dl);
         }
     }
     T.cls[mgk::XF_CLASSES] = (int32_t)T.ent.size();
-    int64_t bad = 0;
+    // interior boxes
+    int z = 0;
     for (int g = 0; g < G.ng; g++) {
-#pragma omp parallel for schedule(static) reduction(+ : bad)
-        for (int t2 = 0; t2 < G.n[g][2]; t2++)
-            for (int t1 = 0; t1 < G.n[g][1]; t1++)
-                for (int t0 = 0; t0 < G.n[g][0]; t0++) {
-                    mgk::XferRow R;
-                    mgk::xf_row_setup(G, g, t0, t1, t2, R);
-                    mgk::XferRow Rs = R;
-                    Rs.inside = false;  // the range-tested path
-                    int64_t k = M.rowptr[R.r], k1 = M.rowptr[R.r + 1];
-                    bool good = true;
-                    for (int e = T.cls[R.key]; e < T.cls[R.key + 1] && good; e++) {
-                        int c = mgk::xf_entry_col(G, R, T.ent[e], T.dlt[e]);
-                        if (mgk::xf_entry_col(G, Rs, T.ent[e], T.dlt[e]) != c) good = false;
-                        if (c < 0) continue;  // a boundary DOF: not in the row
-                        if (k >= k1 || M.col[k] != c || M.val[k] != T.w[e]) good = false;
-                        k++;
+        for (int d = 0; d < 3; d++) {
+            int best0 = 0, bestn = 0, run0 = 0, runn = 0;
+            for (int t = 0; t < G.n[g][d]; t++) {
+                int md = pos(g, d, t) & 3;
+                bool ok = true;
+                for (int key = g * 64; key < g * 64 + 64 && ok; key++) {
+                    if (((key - g * 64) >> (2 * d) & 3) != md) continue;
+                    for (int e = T.cls[key]; e < T.cls[key + 1]; e++) {
+                        int h = eh[e];
+                        int tt = floor_div(pos(g, d, t) - G.c * colG.o[h][d], q) + edl[e][d];
+                        if (tt < 0 || tt >= colG.n[h][d]) {
+                            ok = false;
+                            break;
+                        }
                     }
-                    if (!good || k != k1) bad++;
                 }
+                if (ok) {
+                    if (runn == 0) run0 = t;
+                    if (++runn > bestn) {
+                        bestn = runn;
+                        best0 = run0;
+                    }
+                } else {
+                    runn = 0;
+                }
+            }
+            G.bo[g][d] = best0;
+            G.bn[g][d] = bestn;
+        }
+        G.bz[g] = z;
+        z += G.bn[g][0] && G.bn[g][1] ? G.bn[g][2] : 0;
+        G.bmax01 = std::max(G.bmax01, G.bn[g][0] * G.bn[g][1]);
     }
-    T.ok = bad == 0;
+    G.bz[G.ng] = z;
+    if (z == 0) return T;
+    // every box row from the tables equals the stored row
+    std::vector<char> inbox((size_t)n, 0);
+    int64_t bad = 0;
+#pragma omp parallel for schedule(static) reduction(+ : bad)
+    for (int64_t r = 0; r < n; r++) {
+        int g, t[3];
+        lat_decode(rowG, r, g, t);
+        bool in = true;
+        for (int d = 0; d < 3; d++) in = in && t[d] >= G.bo[g][d] && t[d] < G.bo[g][d] + G.bn[g][d];
+        if (!in) continue;
+        inbox[r] = 1;
+        int key, anchor[3];
+        int rr = mgk::xf_row(G, g, t[0], t[1], t[2], key, anchor);
+        int64_t k = M.rowptr[r], k1 = M.rowptr[r + 1];
+        bool good = rr == r && k1 - k == T.cls[key + 1] - T.cls[key];
+        for (int e = T.cls[key]; e < T.cls[key + 1] && good; e++, k++)
+            good = M.col[k] == mgk::xf_col(anchor, T.ent[e]) && M.val[k] == T.w[e];
+        if (!good) bad++;
+    }
+    if (bad) return T;
+    T.bnd.nrows = 0;
+    T.bnd.ncols = M.ncols;
+    T.bnd.rowptr.assign(1, 0);
+    for (int64_t r = 0; r < n; r++) {
+        if (inbox[r]) continue;
+        T.bnd_rows.push_back((int32_t)r);
+        for (int64_t k = M.rowptr[r]; k < M.rowptr[r + 1]; k++) {
+            T.bnd.col.push_back(M.col[k]);
+            T.bnd.val.push_back(M.val[k]);
+        }
+        T.bnd.rowptr.push_back((int64_t)T.bnd.col.size());
+        T.bnd.nrows++;
+    }
+    T.ok = true;
     return T;
-}
-
-template <typename T>
-static void upload_xfer(const XferD &X, const XferTables &Tb, cudaStream_t s)
-{
-    std::vector<T> w(Tb.w.size());
-    for (size_t e = 0; e < w.size(); e++) w[e] = (T)Tb.w[e];  // FP32: rounded once, like the CSR copy
-    CK(cudaMemcpyAsync(X.cls, Tb.cls.data(), Tb.cls.size() * 4, cudaMemcpyHostToDevice, s));
-    if (!w.empty()) {
-        CK(cudaMemcpyAsync(X.ent, Tb.ent.data(), Tb.ent.size() * 4, cudaMemcpyHostToDevice, s));
-        CK(cudaMemcpyAsync(X.dlt, Tb.dlt.data(), Tb.dlt.size() * 4, cudaMemcpyHostToDevice, s));
-        CK(cudaMemcpyAsync(X.w, w.data(), w.size() * sizeof(T), cudaMemcpyHostToDevice, s));
-    }
-    CK(cudaStreamSynchronize(s));
 }
 
 // device format of a level operator
@@ -1323,9 +1360,11 @@ static void plan_matrix(DevMat &m, const mgh::Csr &A, int fmt, int dim, int N, i
     }
 }
 
+// rowmap (SELL only): the stored rows are rows (*rowmap)[i] of the full operator, and perm
+// holds those indices
 template <typename T>
 static void upload_matrix(const DevMat &m, const mgh::Csr &A, const std::vector<T> &vals, int dim, int N,
-                          cudaStream_t s)
+                          cudaStream_t s, const std::vector<int32_t> *rowmap = nullptr)
 {
     if (m.fmt == MG_STORAGE_DIA) {
         std::vector<T> v((size_t)m.K * m.ld, T(0));
@@ -1374,6 +1413,8 @@ static void upload_matrix(const DevMat &m, const mgh::Csr &A, const std::vector<
         CK(cudaMemcpyAsync(m.val, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(m.col, c.data(), c.size() * 4, cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(m.rowptr, sptr.data(), sptr.size() * 8, cudaMemcpyHostToDevice, s));
+        if (rowmap)
+            for (auto &p : perm) p = (*rowmap)[(size_t)p];
         CK(cudaMemcpyAsync(m.perm, perm.data(), perm.size() * 4, cudaMemcpyHostToDevice, s));
         CK(cudaStreamSynchronize(s));
     } else if (m.fmt == MG_STORAGE_ELL) {
@@ -1460,6 +1501,24 @@ static std::vector<float> to_f32(const std::vector<double> &v)
     std::vector<float> o(v.size());
     for (size_t i = 0; i < v.size(); i++) o[i] = (float)v[i];
     return o;
+}
+
+template <typename T>
+static void upload_xfer(const XferD &X, const XferTables &Tb, int dim, int N, cudaStream_t s)
+{
+    std::vector<T> w(Tb.w.size());
+    for (size_t e = 0; e < w.size(); e++) w[e] = (T)Tb.w[e];  // FP32: rounded once, like the CSR copy
+    CK(cudaMemcpyAsync(X.cls, Tb.cls.data(), Tb.cls.size() * 4, cudaMemcpyHostToDevice, s));
+    if (!w.empty()) {
+        CK(cudaMemcpyAsync(X.ent, Tb.ent.data(), Tb.ent.size() * 4, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(X.w, w.data(), w.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+    }
+    CK(cudaStreamSynchronize(s));
+    if (X.B.n > 0) {
+        std::vector<T> bv(Tb.bnd.val.size());
+        for (size_t e = 0; e < bv.size(); e++) bv[e] = (T)Tb.bnd.val[e];
+        upload_matrix<T>(X.B, Tb.bnd, bv, dim, N, s, &Tb.bnd_rows);
+    }
 }
 
 // Chebyshev coefficients of level l (the same recurrence as the smoother's definition)
@@ -1728,8 +1787,8 @@ void mgi::build_hierarchy(mg_hierarchy *h, const mg_problem *p, const mg_options
                         X.nent = (int)Tb.ent.size();
                         X.cls = (int32_t *)vec((size_t)(mgk::XF_CLASSES + 1) * 4);
                         X.ent = (int32_t *)vec((size_t)std::max(X.nent, 1) * 4);
-                        X.dlt = (int32_t *)vec((size_t)std::max(X.nent, 1) * 4);
                         X.w = vec((size_t)std::max(X.nent, 1) * sv);
+                        if (Tb.bnd.nrows > 0) plan_matrix(X.B, Tb.bnd, MG_STORAGE_SELL, dim, L.N, sv, S, take);
                     }
                 } else if (!L.structured) {
                     plan_matrix(L.P, P[l], MG_STORAGE_SELL, dim, L.N, sv, S, take);
@@ -1785,8 +1844,8 @@ void mgi::build_hierarchy(mg_hierarchy *h, const mg_problem *p, const mg_options
                 CK(cudaStreamSynchronize(h->s));
             }
             if (l >= 1 && L.Pt.on) {
-                upload_xfer<float>(L.Pt, xP[l], h->s);
-                upload_xfer<float>(L.Rt, xR[l], h->s);
+                upload_xfer<float>(L.Pt, xP[l], dim, L.N, h->s);
+                upload_xfer<float>(L.Rt, xR[l], dim, L.N, h->s);
             } else if (l >= 1 && !L.structured) {
                 upload_matrix<float>(L.P, P[l], to_f32(P[l].val), dim, L.N, h->s);
                 upload_matrix<float>(L.R, R[l], to_f32(R[l].val), dim, L.N, h->s);
@@ -1802,8 +1861,8 @@ void mgi::build_hierarchy(mg_hierarchy *h, const mg_problem *p, const mg_options
                 CK(cudaStreamSynchronize(h->s));
             }
             if (l >= 1 && L.Pt.on) {
-                upload_xfer<double>(L.Pt, xP[l], h->s);
-                upload_xfer<double>(L.Rt, xR[l], h->s);
+                upload_xfer<double>(L.Pt, xP[l], dim, L.N, h->s);
+                upload_xfer<double>(L.Rt, xR[l], dim, L.N, h->s);
             } else if (l >= 1 && !L.structured) {
                 upload_matrix<double>(L.P, P[l], P[l].val, dim, L.N, h->s);
                 upload_matrix<double>(L.R, R[l], R[l].val, dim, L.N, h->s);
@@ -2290,12 +2349,11 @@ static std::vector<double> download_vals(const DevMat &m, size_t count)
 // a table-driven transfer as CSR: the device tables, each row generated as the kernel does
 static void export_xfer(const XferD &X, int64_t nrows, int sv, mgh::Csr &out)
 {
-    std::vector<int32_t> cls(mgk::XF_CLASSES + 1), ent((size_t)X.nent), dlt((size_t)X.nent);
+    std::vector<int32_t> cls(mgk::XF_CLASSES + 1), ent((size_t)X.nent);
     std::vector<double> w((size_t)X.nent);
     CK(cudaMemcpy(cls.data(), X.cls, cls.size() * 4, cudaMemcpyDeviceToHost));
     if (X.nent) {
         CK(cudaMemcpy(ent.data(), X.ent, ent.size() * 4, cudaMemcpyDeviceToHost));
-        CK(cudaMemcpy(dlt.data(), X.dlt, dlt.size() * 4, cudaMemcpyDeviceToHost));
         if (sv == 8) {
             CK(cudaMemcpy(w.data(), X.w, w.size() * 8, cudaMemcpyDeviceToHost));
         } else {
@@ -2304,19 +2362,36 @@ static void export_xfer(const XferD &X, int64_t nrows, int sv, mgh::Csr &out)
             for (size_t e = 0; e < w.size(); e++) w[e] = wf[e];
         }
     }
-    const mgk::XferDev &G = X.geo;
     std::vector<std::vector<std::pair<int32_t, double>>> rows((size_t)nrows);
+    const mgk::XferDev &G = X.geo;
     for (int g = 0; g < G.ng; g++)
-        for (int t2 = 0; t2 < G.n[g][2]; t2++)
-            for (int t1 = 0; t1 < G.n[g][1]; t1++)
-                for (int t0 = 0; t0 < G.n[g][0]; t0++) {
-                    mgk::XferRow R;
-                    mgk::xf_row_setup(G, g, t0, t1, t2, R);
-                    for (int e = cls[R.key]; e < cls[R.key + 1]; e++) {
-                        int c = mgk::xf_entry_col(G, R, ent[e], dlt[e]);
-                        if (c >= 0) rows[R.r].push_back({c, w[e]});
-                    }
+        for (int t2 = G.bo[g][2]; t2 < G.bo[g][2] + G.bn[g][2]; t2++)
+            for (int t1 = G.bo[g][1]; t1 < G.bo[g][1] + G.bn[g][1]; t1++)
+                for (int t0 = G.bo[g][0]; t0 < G.bo[g][0] + G.bn[g][0]; t0++) {
+                    int key, anchor[3];
+                    int r = mgk::xf_row(G, g, t0, t1, t2, key, anchor);
+                    for (int e = cls[key]; e < cls[key + 1]; e++) rows[r].push_back({mgk::xf_col(anchor, ent[e]), w[e]});
                 }
+    if (X.B.n > 0) {  // the explicit rows: SELL slots in row order up to the first padding
+        const DevMat &m = X.B;
+        std::vector<double> v = sv == 8 ? download_vals<double>(m, (size_t)m.padded) : download_vals<float>(m, (size_t)m.padded);
+        std::vector<int32_t> c((size_t)m.padded), perm((size_t)m.n);
+        std::vector<int64_t> sptr((size_t)m.nslices + 1);
+        CK(cudaMemcpy(c.data(), m.col, c.size() * 4, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(perm.data(), m.perm, perm.size() * 4, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(sptr.data(), m.rowptr, sptr.size() * 8, cudaMemcpyDeviceToHost));
+        for (int64_t p = 0; p < m.n; p++) {
+            int64_t sl = p / 32, Ks = (sptr[sl + 1] - sptr[sl]) / 32;
+            int32_t prev = -1;
+            for (int64_t k = 0; k < Ks; k++) {
+                size_t e = (size_t)(sptr[sl] + 32 * k + p % 32);
+                if (c[e] <= prev) break;
+                if (v[e] == 0.0) continue;  // the padding of a row without entries
+                prev = c[e];
+                rows[perm[p]].push_back({c[e], v[e]});
+            }
+        }
+    }
     out.nrows = nrows;
     out.rowptr.assign((size_t)nrows + 1, 0);
     out.col.clear();

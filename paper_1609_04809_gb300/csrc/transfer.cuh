@@ -4,9 +4,9 @@
 // The prolongation P of Sec. 5.1 (interpolation into the refined space) and the
 // restriction R = P^T are translation invariant on a uniformly refined grid: the entries
 // of a row depend only on where its DOF sits within a coarse cell, up to the entries that
-// fall on the Dirichlet boundary. Each row is therefore generated from a small table, one
-// list of (offset, target family, weight) per row class, instead of being read from a
-// stored matrix: the kernel reads x and writes y, and no column indices.
+// fall on the Dirichlet boundary. Away from the boundary each row is therefore generated
+// from a small table, one list of (target family, offset, weight) per row class, instead
+// of being read from a stored matrix; the rows near the boundary stay explicit (SELL-32).
 //
 // DOF positions are integers in the level's DOF frame (rotated Q1: half cells, the face
 // centres; P1: cells, the vertices; P2: half cells, vertices and edge midpoints). One unit
@@ -16,18 +16,19 @@
 // size in fine units is 2 or 4).
 //
 // Column arithmetic. A row at fine-frame position X and an entry with fine-frame offset D
-// on target family g' reach the target lattice point t'_d = (X_d + D_d - c o'_d) / q with
+// on target family h reach the target lattice point t'_d = (X_d + D_d - c o'_d) / q with
 // c = 2 for P (coarse columns), 1 for R, and q = c s' (1, 2 or 4). Writing
 // X_d - c o'_d = q a_d + r_d (0 <= r_d < q), r_d is fixed by the class, so
 // t'_d = a_d + delta_d with delta_d = (D_d + r_d) / q a constant of the entry, and the
-// column is anchor(g') + Delta with anchor(g') = base'(g') + a_0 + n'_0 (a_1 + n'_1 a_2)
-// per row and Delta = delta_0 + n'_0 (delta_1 + n'_1 delta_2) per entry. Rows whose
-// anchors lie far enough inside every target lattice skip the range test.
+// column is anchor(h) + Delta with anchor(h) = base'(h) + a_0 + n'_0 (a_1 + n'_1 a_2) per
+// row and Delta = delta_0 + n'_0 (delta_1 + n'_1 delta_2) per entry.
 //
-// The tables are learned on the host from the exact CSR operator and checked there
-// against every row with the functions below, the kernel's own column arithmetic
-// (entries in the same order, with the same weights), so the kernel's sums equal the
-// CSR sums term by term.
+// The interior box of a family is the set of rows whose every entry lands inside its
+// target lattice; its rows take the table with no range test. The tables are learned on
+// the host from the exact CSR operator and every box row is checked there with the
+// functions below, the kernel's own arithmetic, against the stored row (entries in the
+// same order, with the same weights), so the kernel's sums equal the CSR sums term by
+// term.
 #pragma once
 
 #include <cstdint>
@@ -49,103 +50,79 @@ struct LatGeom {
 
 // everything the kernel needs about the row and column lattices of one transfer
 struct XferDev {
-    int ng = 0, s = 1;          // row lattice: families, spacing
+    int ng = 0, s = 1;           // row lattice: families, spacing
     int o[3][3] = {}, n[3][3] = {};
     int base[3] = {};
-    int zb[3] = {};             // launch z of each family's first t_2 plane
-    int rm = 1;                 // row frame -> fine frame factor (2: rows on the coarse level)
-    int c = 1, qs = 0;          // fine frame -> column frame factor (2: coarse columns); log2 q
-    int cng = 0;                // column lattice
+    int rm = 1;                  // row frame -> fine frame factor (2: rows on the coarse level)
+    int c = 1, qs = 0;           // fine frame -> column frame factor (2: coarse columns); log2 q
+    int cng = 0;                 // column lattice
     int co[3][3] = {}, cn[3][3] = {};
     int cbase[3] = {};
-    int lo[3] = {}, hi[3] = {}; // per target family: min and max delta_d over the entries
+    int bo[3][3] = {}, bn[3][3] = {};  // interior box of each family: first t_d, extent
+    int bz[4] = {};              // launch z of each family's first box plane; bz[ng] = total
+    int bmax01 = 0;              // largest bn[g][0] * bn[g][1]
 };
 
-// one row: its index, class and the anchors of the target families
-struct XferRow {
-    int r, key;
-    int a[3][3];
-    int anchor[3];
-    bool inside;  // every entry's target lies in its lattice: no range test needed
-};
-
-__host__ __device__ __forceinline__ void xf_row_setup(const XferDev &G, int g, int t0, int t1, int t2, XferRow &R)
+// the row at lattice point t of family g: index, class, fine-frame position and the
+// anchors of the target families
+__host__ __device__ __forceinline__ int xf_row(const XferDev &G, int g, int t0, int t1, int t2, int &key,
+                                               int anchor[3])
 {
-    R.r = G.base[g] + t0 + G.n[g][0] * (t1 + G.n[g][1] * t2);
     int t[3] = {t0, t1, t2}, X[3];
     for (int d = 0; d < 3; d++) X[d] = (G.o[g][d] + G.s * t[d]) * G.rm;
-    R.key = g * 64 + (X[0] & 3) + 4 * (X[1] & 3) + 16 * (X[2] & 3);
-    R.inside = true;
+    key = g * 64 + (X[0] & 3) + 4 * (X[1] & 3) + 16 * (X[2] & 3);
     for (int h = 0; h < 3; h++) {
-        if (h >= G.cng) {
-            R.anchor[h] = 0;
-            for (int d = 0; d < 3; d++) R.a[h][d] = 0;
-            continue;
-        }
-        for (int d = 0; d < 3; d++) {
-            R.a[h][d] = (X[d] - G.c * G.co[h][d]) >> G.qs;  // floor division by q
-            if (R.a[h][d] + G.lo[h] < 0 || R.a[h][d] + G.hi[h] >= G.cn[h][d]) R.inside = false;
-        }
-        R.anchor[h] = G.cbase[h] + R.a[h][0] + G.cn[h][0] * (R.a[h][1] + G.cn[h][1] * R.a[h][2]);
+        int a[3];
+        for (int d = 0; d < 3; d++) a[d] = (X[d] - G.c * G.co[h][d]) >> G.qs;  // floor division by q
+        anchor[h] = h < G.cng ? G.cbase[h] + a[0] + G.cn[h][0] * (a[1] + G.cn[h][1] * a[2]) : 0;
     }
+    return G.base[g] + t0 + G.n[g][0] * (t1 + G.n[g][1] * t2);
 }
 
-// entry packing: delta_d as three signed bytes and the target family
-__host__ __device__ __forceinline__ int32_t xf_pack(int d0, int d1, int d2, int g)
+// an entry: target family (top byte) and Delta (24-bit signed)
+__host__ __device__ __forceinline__ int32_t xf_pack(int h, int delta)
 {
-    return (int32_t)((uint32_t)(d0 & 0xff) | ((uint32_t)(d1 & 0xff) << 8) | ((uint32_t)(d2 & 0xff) << 16) |
-                     ((uint32_t)g << 24));
+    return (int32_t)(((uint32_t)h << 24) | ((uint32_t)delta & 0xffffffu));
 }
 
-__host__ __device__ __forceinline__ int xf_sel(const int *v, int h) { return h == 0 ? v[0] : (h == 1 ? v[1] : v[2]); }
-
-// column of an entry (packed p, linear offset D) for row R, or -1 (a boundary DOF)
-__host__ __device__ __forceinline__ int xf_entry_col(const XferDev &G, const XferRow &R, int32_t p, int32_t D)
+__host__ __device__ __forceinline__ int xf_col(const int anchor[3], int32_t p)
 {
     int h = (p >> 24) & 0xff;
-    int col = xf_sel(R.anchor, h) + D;
-    if (R.inside) return col;
-    int dl[3] = {(int)(int8_t)(p & 0xff), (int)(int8_t)((p >> 8) & 0xff), (int)(int8_t)((p >> 16) & 0xff)};
-    for (int d = 0; d < 3; d++) {
-        int av = h == 0 ? R.a[0][d] : (h == 1 ? R.a[1][d] : R.a[2][d]);
-        int cn = h == 0 ? G.cn[0][d] : (h == 1 ? G.cn[1][d] : G.cn[2][d]);
-        int tt = av + dl[d];
-        if (tt < 0 || tt >= cn) return -1;
-    }
-    return col;
+    int delta = (int)((uint32_t)p << 8) >> 8;  // sign-extend the low 24 bits
+    return (h == 0 ? anchor[0] : (h == 1 ? anchor[1] : anchor[2])) + delta;
 }
 
-// y_r = sum over the row's entries e (table order) of w_e x_col(e)  (ADD: y_r += that sum).
-// Launch: x over t_0, y over t_1, z over the families' t_2 planes (G.zb). Entries are
-// processed eight at a time: columns first, then the gathers, then the multiply-adds in
-// order, so eight loads are in flight per thread.
+// y_r = sum over the row's entries e (table order) of w_e x_col(e)  (ADD: y_r += that sum),
+// for the rows of the interior boxes. Launch: z over the families' box planes (G.bz), x
+// over the points of a plane. Entries are processed eight at a time: columns first, then
+// the gathers, then the multiply-adds in order, so eight loads are in flight per thread.
 template <typename T, bool ADD>
 __global__ void __launch_bounds__(256) k_xfer_apply(XferDev G, const int32_t *__restrict__ cls,
-                                                    const int32_t *__restrict__ ent, const int32_t *__restrict__ dlt,
-                                                    const T *__restrict__ wt, const T *__restrict__ x,
-                                                    T *__restrict__ y)
+                                                    const int32_t *__restrict__ ent, const T *__restrict__ wt,
+                                                    const T *__restrict__ x, T *__restrict__ y)
 {
     pdl_enter();
     int z = blockIdx.z;
-    int g = (G.ng > 1 && z >= G.zb[1]) + (G.ng > 2 && z >= G.zb[2]);
-    int t0 = blockIdx.x * blockDim.x + threadIdx.x, t1 = blockIdx.y * blockDim.y + threadIdx.y, t2 = z - G.zb[g];
-    if (t0 >= G.n[g][0] || t1 >= G.n[g][1]) return;
-    XferRow R;
-    xf_row_setup(G, g, t0, t1, t2, R);
-    int lo = __ldg(cls + R.key), hi = __ldg(cls + R.key + 1);
+    int g = (G.ng > 1 && z >= G.bz[1]) + (G.ng > 2 && z >= G.bz[2]);
+    int w0 = G.bn[g][0], i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= w0 * G.bn[g][1]) return;
+    int t1 = i / w0, t0 = i - t1 * w0;
+    int key, anchor[3];
+    int r = xf_row(G, g, t0 + G.bo[g][0], t1 + G.bo[g][1], z - G.bz[g] + G.bo[g][2], key, anchor);
+    int lo = __ldg(cls + key), hi = __ldg(cls + key + 1);
     T s = T(0);
     for (int e0 = lo; e0 < hi; e0 += 8) {
         int c[8];
 #pragma unroll
-        for (int j = 0; j < 8; j++) c[j] = e0 + j < hi ? xf_entry_col(G, R, __ldg(ent + e0 + j), __ldg(dlt + e0 + j)) : -1;
+        for (int j = 0; j < 8; j++) c[j] = e0 + j < hi ? xf_col(anchor, __ldg(ent + e0 + j)) : 0;
         T v[8];
 #pragma unroll
-        for (int j = 0; j < 8; j++) v[j] = c[j] >= 0 ? __ldg(x + c[j]) : T(0);
+        for (int j = 0; j < 8; j++) v[j] = e0 + j < hi ? __ldg(x + c[j]) : T(0);
 #pragma unroll
         for (int j = 0; j < 8; j++)
-            if (c[j] >= 0) s = Ar<T>::mac(s, __ldg(wt + e0 + j), v[j]);
+            if (e0 + j < hi) s = Ar<T>::mac(s, __ldg(wt + e0 + j), v[j]);
     }
-    y[R.r] = ADD ? Ar<T>::add(y[R.r], s) : s;
+    y[r] = ADD ? Ar<T>::add(y[r], s) : s;
 }
 
 }  // namespace mgk

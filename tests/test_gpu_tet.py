@@ -173,20 +173,15 @@ def test_sell_storage(orc, elem, N, L, precision):
 @pytest.mark.parametrize("elem,N,L", [(1, 16, 3), (2, 16, 3), (3, 16, 3), (3, 8, 3)])
 @pytest.mark.parametrize("precision", [mg.MG_FP64, mg.MG_MIXED])
 def test_table_transfers(orc, elem, N, L, precision):
-    """Rotated Q1, P1, P2: P and R generated from per-class tables on every level whose
-    coarse grid has at least 4 cells per axis, explicit (SELL-32) below that; the device
-    transfers exported as CSR equal the host operators; FP64 solves bitwise, mixed
-    converged to the FP64 residual."""
+    """Rotated Q1, P1, P2: P and R generated from per-class tables on the interior rows of
+    every level, the rows near the boundary explicit (SELL-32); the device transfers
+    exported as CSR equal the host operators; FP64 solves bitwise, mixed converged to the
+    FP64 residual."""
     b = W.random_vector(mg.mg_ndofs(3, elem, N), seed=93)
     H, O, g, o = _both(orc, elem, N, L, b, precision=precision)
     tr = H.info()["transfer"]
     assert tr[0] == mg.MG_TRANSFER_NONE
-    for l in range(1, L):
-        Nc = (N >> (L - 1 - l)) // 2
-        if Nc >= 4:
-            assert tr[l] == mg.MG_TRANSFER_TABLE, (l, tr)
-        else:
-            assert tr[l] in (mg.MG_TRANSFER_TABLE, mg.MG_TRANSFER_SELL)
+    assert all(t == mg.MG_TRANSFER_TABLE for t in tr[1:]), tr
     assert g[0] == mg.MG_OK
     if precision == mg.MG_FP64:
         assert g[1] == o[1] and np.array_equal(g[3], o[3])
