@@ -54,8 +54,8 @@ struct DevMat {
 struct XferD {
     bool on = false;
     mgk::XferDev geo;
-    int32_t *cls = nullptr, *ent = nullptr;
-    void *w = nullptr;  // weights in the inner precision
+    int32_t *cls = nullptr;
+    void *ent = nullptr;  // XferEnt<T>, T the inner precision
     int nent = 0;
     DevMat B;           // the rows outside the boxes; B.perm holds their row indices
 };

@@ -479,8 +479,8 @@ static void xfer_launch(mg_hierarchy *h, const XferD &X, const T *x, T *y, cudaS
     const mgk::XferDev &G = X.geo;
     bool pdl = h->opt.use_pdl != 0;
     dim3 grid((unsigned)((G.bmax01 + 255) / 256), 1, (unsigned)G.bz[G.ng]);
-    klaunch(pdl, k_xfer_apply<T, ADD>, grid, dim3(256), 0, s, G, (const int32_t *)X.cls, (const int32_t *)X.ent,
-            (const T *)X.w, x, y);
+    klaunch(pdl, k_xfer_apply<T, ADD>, grid, dim3(256), 0, s, G, (const int32_t *)X.cls,
+            (const mgk::XferEnt<T> *)X.ent, x, y);
     if (X.B.n > 0) {
         if (h->counting) h->kernels_per_cycle++;
         klaunch(pdl, k_sell_apply<T, ADD>, dim3(grid_for(X.B.n)), dim3(256), 0, s, (const int64_t *)X.B.rowptr,
@@ -1198,7 +1198,7 @@ static XferTables learn_xfer(const mgh::Csr &M, const mgk::LatGeom &rowG, const 
         }
         G.bz[g] = z;
         z += G.bn[g][0] && G.bn[g][1] ? G.bn[g][2] : 0;
-        G.bmax01 = std::max(G.bmax01, G.bn[g][0] * G.bn[g][1]);
+        G.bmax01 = std::max(G.bmax01, (G.bn[g][0] + 1) / 2 * G.bn[g][1]);  // pairs along t_0
     }
     G.bz[G.ng] = z;
     if (z == 0) return T;
@@ -1506,13 +1506,14 @@ static std::vector<float> to_f32(const std::vector<double> &v)
 template <typename T>
 static void upload_xfer(const XferD &X, const XferTables &Tb, int dim, int N, cudaStream_t s)
 {
-    std::vector<T> w(Tb.w.size());
-    for (size_t e = 0; e < w.size(); e++) w[e] = (T)Tb.w[e];  // FP32: rounded once, like the CSR copy
-    CK(cudaMemcpyAsync(X.cls, Tb.cls.data(), Tb.cls.size() * 4, cudaMemcpyHostToDevice, s));
-    if (!w.empty()) {
-        CK(cudaMemcpyAsync(X.ent, Tb.ent.data(), Tb.ent.size() * 4, cudaMemcpyHostToDevice, s));
-        CK(cudaMemcpyAsync(X.w, w.data(), w.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+    std::vector<mgk::XferEnt<T>> ent(Tb.ent.size());
+    for (size_t e = 0; e < ent.size(); e++) {
+        ent[e].p = Tb.ent[e];
+        ent[e].pad = 0;
+        ent[e].w = (T)Tb.w[e];  // FP32: rounded once, like the CSR copy
     }
+    CK(cudaMemcpyAsync(X.cls, Tb.cls.data(), Tb.cls.size() * 4, cudaMemcpyHostToDevice, s));
+    if (!ent.empty()) CK(cudaMemcpyAsync(X.ent, ent.data(), ent.size() * sizeof(ent[0]), cudaMemcpyHostToDevice, s));
     CK(cudaStreamSynchronize(s));
     if (X.B.n > 0) {
         std::vector<T> bv(Tb.bnd.val.size());
@@ -1786,8 +1787,7 @@ void mgi::build_hierarchy(mg_hierarchy *h, const mg_problem *p, const mg_options
                         X.geo = Tb.dev;
                         X.nent = (int)Tb.ent.size();
                         X.cls = (int32_t *)vec((size_t)(mgk::XF_CLASSES + 1) * 4);
-                        X.ent = (int32_t *)vec((size_t)std::max(X.nent, 1) * 4);
-                        X.w = vec((size_t)std::max(X.nent, 1) * sv);
+                        X.ent = vec((size_t)std::max(X.nent, 1) * 16);  // XferEnt<T>
                         if (Tb.bnd.nrows > 0) plan_matrix(X.B, Tb.bnd, MG_STORAGE_SELL, dim, L.N, sv, S, take);
                     }
                 } else if (!L.structured) {
@@ -2352,14 +2352,19 @@ static void export_xfer(const XferD &X, int64_t nrows, int sv, mgh::Csr &out)
     std::vector<int32_t> cls(mgk::XF_CLASSES + 1), ent((size_t)X.nent);
     std::vector<double> w((size_t)X.nent);
     CK(cudaMemcpy(cls.data(), X.cls, cls.size() * 4, cudaMemcpyDeviceToHost));
-    if (X.nent) {
-        CK(cudaMemcpy(ent.data(), X.ent, ent.size() * 4, cudaMemcpyDeviceToHost));
-        if (sv == 8) {
-            CK(cudaMemcpy(w.data(), X.w, w.size() * 8, cudaMemcpyDeviceToHost));
-        } else {
-            std::vector<float> wf(w.size());
-            CK(cudaMemcpy(wf.data(), X.w, wf.size() * 4, cudaMemcpyDeviceToHost));
-            for (size_t e = 0; e < w.size(); e++) w[e] = wf[e];
+    if (X.nent && sv == 8) {
+        std::vector<mgk::XferEnt<double>> q((size_t)X.nent);
+        CK(cudaMemcpy(q.data(), X.ent, q.size() * sizeof(q[0]), cudaMemcpyDeviceToHost));
+        for (size_t e = 0; e < q.size(); e++) {
+            ent[e] = q[e].p;
+            w[e] = q[e].w;
+        }
+    } else if (X.nent) {
+        std::vector<mgk::XferEnt<float>> q((size_t)X.nent);
+        CK(cudaMemcpy(q.data(), X.ent, q.size() * sizeof(q[0]), cudaMemcpyDeviceToHost));
+        for (size_t e = 0; e < q.size(); e++) {
+            ent[e] = q[e].p;
+            w[e] = q[e].w;
         }
     }
     std::vector<std::vector<std::pair<int32_t, double>>> rows((size_t)nrows);

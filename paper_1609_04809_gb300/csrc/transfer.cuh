@@ -60,7 +60,7 @@ struct XferDev {
     int cbase[3] = {};
     int bo[3][3] = {}, bn[3][3] = {};  // interior box of each family: first t_d, extent
     int bz[4] = {};              // launch z of each family's first box plane; bz[ng] = total
-    int bmax01 = 0;              // largest bn[g][0] * bn[g][1]
+    int bmax01 = 0;              // largest number of t_0 pairs in a box plane
 };
 
 // the row at lattice point t of family g: index, class, fine-frame position and the
@@ -92,37 +92,66 @@ __host__ __device__ __forceinline__ int xf_col(const int anchor[3], int32_t p)
     return (h == 0 ? anchor[0] : (h == 1 ? anchor[1] : anchor[2])) + delta;
 }
 
+// one table entry as the kernel reads it: packed target and offset, weight (16 bytes)
+template <typename T>
+struct alignas(16) XferEnt {
+    int32_t p, pad;
+    T w;
+};
+
+// s += the entries [lo, hi) of a row with the given anchors, in table order; four at a
+// time (columns, then the gathers, then the multiply-adds), the rest one by one
+template <typename T>
+__device__ __forceinline__ T xf_row_sum(const XferEnt<T> *__restrict__ ent, int lo, int hi, const int anchor[3],
+                                        const T *__restrict__ x)
+{
+    T s = T(0);
+    int e = lo;
+    for (; e + 4 <= hi; e += 4) {
+        XferEnt<T> q[4];
+        T v[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) q[j] = ent[e + j];
+#pragma unroll
+        for (int j = 0; j < 4; j++) v[j] = __ldg(x + xf_col(anchor, q[j].p));
+#pragma unroll
+        for (int j = 0; j < 4; j++) s = Ar<T>::mac(s, q[j].w, v[j]);
+    }
+    for (; e < hi; e++) {
+        XferEnt<T> q = ent[e];
+        s = Ar<T>::mac(s, q.w, __ldg(x + xf_col(anchor, q.p)));
+    }
+    return s;
+}
+
 // y_r = sum over the row's entries e (table order) of w_e x_col(e)  (ADD: y_r += that sum),
-// for the rows of the interior boxes. Launch: z over the families' box planes (G.bz), x
-// over the points of a plane. Entries are processed eight at a time: columns first, then
-// the gathers, then the multiply-adds in order, so eight loads are in flight per thread.
+// for the rows of the interior boxes. Each thread takes two neighbouring points along
+// t_0 (t_0 = bo_0 + 2k, 2k + 1), so that a warp's first rows, and its second rows, share
+// one class wherever the class changes with the parity of t_0. Launch: z over the
+// families' box planes (G.bz), x over the pairs of a plane.
 template <typename T, bool ADD>
 __global__ void __launch_bounds__(256) k_xfer_apply(XferDev G, const int32_t *__restrict__ cls,
-                                                    const int32_t *__restrict__ ent, const T *__restrict__ wt,
-                                                    const T *__restrict__ x, T *__restrict__ y)
+                                                    const XferEnt<T> *__restrict__ ent, const T *__restrict__ x,
+                                                    T *__restrict__ y)
 {
     pdl_enter();
     int z = blockIdx.z;
     int g = (G.ng > 1 && z >= G.bz[1]) + (G.ng > 2 && z >= G.bz[2]);
-    int w0 = G.bn[g][0], i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= w0 * G.bn[g][1]) return;
-    int t1 = i / w0, t0 = i - t1 * w0;
+    int w0 = G.bn[g][0], np = (w0 + 1) >> 1, i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= np * G.bn[g][1]) return;
+    int t1 = i / np, k = i - t1 * np;
+    int t2 = z - G.bz[g] + G.bo[g][2];
+    t1 += G.bo[g][1];
+    int t0 = G.bo[g][0] + 2 * k;
     int key, anchor[3];
-    int r = xf_row(G, g, t0 + G.bo[g][0], t1 + G.bo[g][1], z - G.bz[g] + G.bo[g][2], key, anchor);
-    int lo = __ldg(cls + key), hi = __ldg(cls + key + 1);
-    T s = T(0);
-    for (int e0 = lo; e0 < hi; e0 += 8) {
-        int c[8];
-#pragma unroll
-        for (int j = 0; j < 8; j++) c[j] = e0 + j < hi ? xf_col(anchor, __ldg(ent + e0 + j)) : 0;
-        T v[8];
-#pragma unroll
-        for (int j = 0; j < 8; j++) v[j] = e0 + j < hi ? __ldg(x + c[j]) : T(0);
-#pragma unroll
-        for (int j = 0; j < 8; j++)
-            if (e0 + j < hi) s = Ar<T>::mac(s, __ldg(wt + e0 + j), v[j]);
-    }
+    int r = xf_row(G, g, t0, t1, t2, key, anchor);
+    T s = xf_row_sum(ent, __ldg(cls + key), __ldg(cls + key + 1), anchor, x);
     y[r] = ADD ? Ar<T>::add(y[r], s) : s;
+    if (2 * k + 1 < w0) {
+        r = xf_row(G, g, t0 + 1, t1, t2, key, anchor);
+        s = xf_row_sum(ent, __ldg(cls + key), __ldg(cls + key + 1), anchor, x);
+        y[r] = ADD ? Ar<T>::add(y[r], s) : s;
+    }
 }
 
 }  // namespace mgk
