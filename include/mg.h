@@ -85,14 +85,9 @@ typedef int mg_status;
 #define MG_STORAGE_SELL 4 /* sliced ELLPACK: rows sorted by length, slices of 32 rows stored
                              column-major with their own width, 32-bit columns */
 /* grid transfers P (prolongation, Sec. 5.1) and R = P^T of a level (mg_info.transfer) */
-#define MG_TRANSFER_NONE 0  /* level 0 (no coarser level) */
-#define MG_TRANSFER_GRID 1  /* Q1: weights computed from the grid in the kernel */
-#define MG_TRANSFER_TABLE 2 /* rotated Q1, P1, P2: each row generated from a table of
-                               (position offset, weight) per row class (the DOF's position
-                               within a coarse cell); the tables are checked against the
-                               explicit operator on the host, every row, before use */
-#define MG_TRANSFER_SELL 3  /* explicit P and R in SELL-32 (when a table does not reproduce
-                               every row) */
+#define MG_TRANSFER_NONE 0 /* level 0 (no coarser level) */
+#define MG_TRANSFER_GRID 1 /* Q1: weights computed from the grid in the kernel */
+#define MG_TRANSFER_SELL 2 /* rotated Q1, P1, P2: explicit P and R in SELL-32 */
 
 #define MG_MAX_LEVELS 16
 
@@ -196,13 +191,6 @@ mg_status mg_load_vector_separable(const mg_problem *p, const mg_rhs *f, double 
  * col/val nnz entries (caller-owned host arrays). */
 mg_status mg_assemble_operator(const mg_problem *p, int level, int which, int64_t *nrows, int64_t *nnz,
                                int64_t *rowptr, int32_t *col, double *val);
-
-/* Host only: whether the grid transfers between level and level-1 (1 <= level <
- * n_levels) are generated exactly by per-class tables (MG_TRANSFER_TABLE). ok[0], ok[1]:
- * 1 if every row of P, resp. R, equals the table's row (columns, order, weights), else 0;
- * n_entries[0..1]: the tables' entries (0 where ok is 0). Q1 and 2D problems report 0
- * (their transfers are computed from the grid). ok, n_entries: caller-owned arrays of 2. */
-mg_status mg_transfer_tables(const mg_problem *p, int level, int *ok, int *n_entries);
 
 /* Build the level hierarchy: per-level stiffness matrices (rediscretised; R A P of the
  * finer level where the coefficient is not resolved by the coarse cells), transfer

@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(128) k_prolong_q1(const T *__restrict__ xc, T 
     xf[line + 2 * m] = Ar<T>::add(xf[line + 2 * m], to);                      // v0 = 2m + 1
 }
 
-// Explicit CSR transfer (rotated Q1): y_i = sum_k v_k x_col  (ADD: y_i += that sum).
+// Explicit CSR transfer: y_i = sum_k v_k x_col  (ADD: y_i += that sum).
 template <typename T, bool ADD>
 __global__ void __launch_bounds__(256) k_csr_apply(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
                                                    const T *__restrict__ val, int n, const T *__restrict__ x,

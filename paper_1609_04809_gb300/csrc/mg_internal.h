@@ -10,7 +10,6 @@
 
 #include "kernels.cuh"
 #include "mg.h"
-#include "transfer.cuh"
 
 namespace mgi {
 
@@ -49,17 +48,6 @@ struct DevMat {
     void *dinv = nullptr;  // 1 / a_ii, FP64 inner levels only
 };
 
-// A transfer generated from per-class tables on the interior boxes (transfer.cuh) and
-// stored explicitly (SELL-32, B) on the other rows; on = false: not used.
-struct XferD {
-    bool on = false;
-    mgk::XferDev geo;
-    int32_t *cls = nullptr;
-    void *ent = nullptr;  // XferEnt<T>, T the inner precision
-    int nent = 0;
-    DevMat B;           // the rows outside the boxes; B.perm holds their row indices
-};
-
 struct LevelD {
     int N = 0;        // cells per axis
     int64_t n = 0;    // DOFs
@@ -71,8 +59,7 @@ struct LevelD {
     void *x[2] = {nullptr, nullptr};
     void *b = nullptr, *t = nullptr, *d = nullptr;
     bool structured = false;  // Q1 transfers computed from the grid
-    DevMat P, R;              // explicit transfers to level-1 (SELL-32), when no tables
-    XferD Pt, Rt;             // table-driven transfers (rotated Q1, P1, P2)
+    DevMat P, R;              // explicit transfers to level-1 (SELL-32)
     // multicolour Gauss-Seidel: a copy of A with its rows stored colour by colour (row r
     // of G is DOF perm[r]; colour c owns rows coff[c] .. coff[c+1]); D^-1 in G.dinv
     DevMat G;

@@ -10,7 +10,6 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
-#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -121,7 +120,6 @@ __global__ void __launch_bounds__(256, 6) k_norm2(const double *__restrict__ v, 
 using mgi::DevMat;
 using mgi::Error;
 using mgi::LevelD;
-using mgi::XferD;
 
 static inline int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 static inline unsigned grid_for(int64_t n) { return (unsigned)((n + 255) / 256); }
@@ -471,23 +469,6 @@ static int smooth(mg_hierarchy *h, int l, int c, bool post, cudaStream_t s)
     return c;
 }
 
-// a table-driven transfer: the interior boxes from the tables, the other rows explicit
-// (the launch scope counts one launch; the second one is counted here)
-template <typename T, bool ADD>
-static void xfer_launch(mg_hierarchy *h, const XferD &X, const T *x, T *y, cudaStream_t s)
-{
-    const mgk::XferDev &G = X.geo;
-    bool pdl = h->opt.use_pdl != 0;
-    dim3 grid((unsigned)((G.bmax01 + 255) / 256), 1, (unsigned)G.bz[G.ng]);
-    klaunch(pdl, k_xfer_apply<T, ADD>, grid, dim3(256), 0, s, G, (const int32_t *)X.cls,
-            (const mgk::XferEnt<T> *)X.ent, x, y);
-    if (X.B.n > 0) {
-        if (h->counting) h->kernels_per_cycle++;
-        klaunch(pdl, k_sell_apply<T, ADD>, dim3(grid_for(X.B.n)), dim3(256), 0, s, (const int64_t *)X.B.rowptr,
-                (const int32_t *)X.B.col, (const T *)X.B.val, (const int32_t *)X.B.perm, (int)X.B.n, x, y);
-    }
-}
-
 template <typename T>
 static void restrict_to(mg_hierarchy *h, int l, const T *r, cudaStream_t s)
 {
@@ -502,10 +483,7 @@ static void restrict_to(mg_hierarchy *h, int l, const T *r, cudaStream_t s)
     }
     int sv = sizeof(T);
     double bytes = (double)F.n * sv + (double)C.n * sv;
-    if (F.Rt.on)
-        bytes += F.Rt.B.n > 0 ? mat_bytes(F.Rt.B, sv) : 0.0;
-    else if (!F.structured)
-        bytes += mat_bytes(F.R, sv);
+    if (!F.structured) bytes += mat_bytes(F.R, sv);
     LaunchScope ls(h, s, MG_K_RESTRICT, l, bytes);
     if (F.structured) {
         unsigned l1 = (unsigned)(C.N - 1), bx = line_block(l1);
@@ -515,8 +493,6 @@ static void restrict_to(mg_hierarchy *h, int l, const T *r, cudaStream_t s)
             klaunch(pdl, k_restrict_q1<T, 3>, g, dim3(bx), 0, s, r, (T *)C.b, C.N);
         else
             klaunch(pdl, k_restrict_q1<T, 2>, g, dim3(bx), 0, s, r, (T *)C.b, C.N);
-    } else if (F.Rt.on) {
-        xfer_launch<T, false>(h, F.Rt, r, (T *)C.b, s);
     } else if (F.R.fmt == MG_STORAGE_SELL) {
         klaunch(h->opt.use_pdl != 0, k_sell_apply<T, false>, dim3(grid_for(C.n)), dim3(256), 0, s,
                 (const int64_t *)F.R.rowptr, (const int32_t *)F.R.col, (const T *)F.R.val, (const int32_t *)F.R.perm,
@@ -542,10 +518,7 @@ static void prolong_add(mg_hierarchy *h, int l, const T *xc, T *xf, cudaStream_t
     }
     int sv = sizeof(T);
     double bytes = 2.0 * F.n * sv + (double)C.n * sv;
-    if (F.Pt.on)
-        bytes += F.Pt.B.n > 0 ? mat_bytes(F.Pt.B, sv) : 0.0;
-    else if (!F.structured)
-        bytes += mat_bytes(F.P, sv);
+    if (!F.structured) bytes += mat_bytes(F.P, sv);
     LaunchScope ls(h, s, MG_K_PROLONG, l, bytes);
     if (F.structured) {
         unsigned l1 = (unsigned)(F.N - 1), nx = (unsigned)C.N, bx = line_block(nx);  // pairs of fine points
@@ -555,8 +528,6 @@ static void prolong_add(mg_hierarchy *h, int l, const T *xc, T *xf, cudaStream_t
             klaunch(pdl, k_prolong_q1<T, 3>, g, dim3(bx), 0, s, xc, xf, C.N);
         else
             klaunch(pdl, k_prolong_q1<T, 2>, g, dim3(bx), 0, s, xc, xf, C.N);
-    } else if (F.Pt.on) {
-        xfer_launch<T, true>(h, F.Pt, xc, xf, s);
     } else if (F.P.fmt == MG_STORAGE_SELL) {
         klaunch(h->opt.use_pdl != 0, k_sell_apply<T, true>, dim3(grid_for(F.n)), dim3(256), 0, s,
                 (const int64_t *)F.P.rowptr, (const int32_t *)F.P.col, (const T *)F.P.val, (const int32_t *)F.P.perm,
@@ -1039,206 +1010,6 @@ extern "C" mg_status mg_load_vector_separable(const mg_problem *p, const mg_rhs 
     }
 }
 
-// ------------------------------------------------------------------------------------
-// Table-driven transfers (rotated Q1, P1, P2; transfer.cuh)
-// ------------------------------------------------------------------------------------
-// The DOF lattice of a level in its DOF frame; false where the transfers are computed
-// from the grid (Q1) or the element has no lattice description here (2D).
-static bool lattice_of(int dim, int elem, int N, mgk::LatGeom &G)
-{
-    G = mgk::LatGeom{};
-    if (dim != 3) return false;
-    if (elem == MG_RQ1) {  // face centres in half cells: family g = the normal axis
-        G.ng = 3;
-        G.s = 2;
-        int64_t fam = (int64_t)(N - 1) * N * N;
-        for (int g = 0; g < 3; g++) {
-            for (int d = 0; d < 3; d++) {
-                G.o[g][d] = d == g ? 2 : 1;
-                G.n[g][d] = d == g ? N - 1 : N;
-            }
-            G.base[g] = g * fam;
-        }
-        G.base[3] = 3 * fam;
-        return true;
-    }
-    if (elem == MG_P1 || elem == MG_P2) {  // interior points of the N (P1) or 2N (P2) grid
-        int M = elem == MG_P1 ? N : 2 * N;
-        G.ng = 1;
-        G.s = 1;
-        for (int d = 0; d < 3; d++) {
-            G.o[0][d] = 1;
-            G.n[0][d] = M - 1;
-        }
-        G.base[1] = (int64_t)(M - 1) * (M - 1) * (M - 1);
-        return true;
-    }
-    return false;
-}
-
-struct XferTables {
-    bool ok = false;
-    mgk::XferDev dev;
-    std::vector<int32_t> cls, ent;
-    std::vector<double> w;
-    mgh::Csr bnd;                   // the rows outside the interior boxes, explicit
-    std::vector<int32_t> bnd_rows;  // their indices
-};
-
-// DOF r of lattice G: its family and lattice point
-static void lat_decode(const mgk::LatGeom &G, int64_t r, int &g, int t[3])
-{
-    g = 0;
-    while (g + 1 < G.ng && r >= G.base[g + 1]) g++;
-    int64_t u = r - G.base[g];
-    int64_t n0 = G.n[g][0], n1 = G.n[g][1];
-    t[0] = (int)(u % n0);
-    t[1] = (int)((u / n0) % n1);
-    t[2] = (int)(u / (n0 * n1));
-}
-
-static inline int floor_div(int v, int q) { return v >= 0 ? v / q : -((-v + q - 1) / q); }
-
-// Learn the class tables of transfer M, rows on lattice rowG and columns on colG
-// (coarse_rows: R, rows on the coarse level; else P): each class takes the entries of its
-// longest row. The interior box of each family is the longest run of lattice points per
-// axis on which every entry of every class lands inside its target lattice. Every box row
-// is generated with the kernel's arithmetic (transfer.cuh) and compared with the stored
-// row; ok only if all agree in columns, order and weights. The other rows are copied to
-// an explicit operator.
-static XferTables learn_xfer(const mgh::Csr &M, const mgk::LatGeom &rowG, const mgk::LatGeom &colG, bool coarse_rows)
-{
-    XferTables T;
-    mgk::XferDev &G = T.dev;
-    if (rowG.base[rowG.ng] >= INT32_MAX || colG.base[colG.ng] >= INT32_MAX) return T;
-    G.ng = rowG.ng;
-    G.s = rowG.s;
-    G.rm = coarse_rows ? 2 : 1;
-    G.c = coarse_rows ? 1 : 2;
-    const int q = G.c * colG.s;
-    G.qs = q == 1 ? 0 : (q == 2 ? 1 : 2);
-    G.cng = colG.ng;
-    for (int g = 0; g < 3; g++)
-        for (int d = 0; d < 3; d++) {
-            G.o[g][d] = rowG.o[g][d];
-            G.n[g][d] = rowG.n[g][d];
-            G.co[g][d] = colG.o[g][d];
-            G.cn[g][d] = colG.n[g][d];
-        }
-    for (int g = 0; g < G.ng; g++) G.base[g] = (int)rowG.base[g];
-    for (int h = 0; h < G.cng; h++) G.cbase[h] = (int)colG.base[h];
-    auto pos = [&](int g, int d, int t) { return (G.o[g][d] + G.s * t) * G.rm; };  // fine frame
-    auto key_of = [&](int g, const int t[3]) {
-        return g * 64 + (pos(g, 0, t[0]) & 3) + 4 * (pos(g, 1, t[1]) & 3) + 16 * (pos(g, 2, t[2]) & 3);
-    };
-    const int64_t n = M.nrows;
-    std::vector<int64_t> rep(mgk::XF_CLASSES, -1);
-    for (int64_t r = 0; r < n; r++) {
-        int g, t[3];
-        lat_decode(rowG, r, g, t);
-        int key = key_of(g, t);
-        int64_t len = M.rowptr[r + 1] - M.rowptr[r];
-        if (rep[key] < 0 || len > M.rowptr[rep[key] + 1] - M.rowptr[rep[key]]) rep[key] = r;
-    }
-    // entries: target family, delta per axis, Delta, weight
-    std::vector<int> eh;
-    std::vector<std::array<int, 3>> edl;
-    T.cls.assign(mgk::XF_CLASSES + 1, 0);
-    for (int key = 0; key < mgk::XF_CLASSES; key++) {
-        T.cls[key] = (int32_t)T.ent.size();
-        int64_t r = rep[key];
-        if (r < 0) continue;
-        int g, t[3];
-        lat_decode(rowG, r, g, t);
-        for (int64_t k = M.rowptr[r]; k < M.rowptr[r + 1]; k++) {
-            int h, tc[3];
-            lat_decode(colG, M.col[k], h, tc);
-            std::array<int, 3> dl;
-            for (int d = 0; d < 3; d++) dl[d] = tc[d] - floor_div(pos(g, d, t[d]) - G.c * colG.o[h][d], q);
-            int64_t D = dl[0] + (int64_t)colG.n[h][0] * (dl[1] + (int64_t)colG.n[h][1] * dl[2]);
-            if (D <= -(1 << 23) || D >= (1 << 23)) return T;
-            T.ent.push_back(mgk::xf_pack(h, (int)D));
-            T.w.push_back(M.val[k]);
-            eh.push_back(h);
-            edl.push_back(dl);
-        }
-    }
-    T.cls[mgk::XF_CLASSES] = (int32_t)T.ent.size();
-    // interior boxes
-    int z = 0;
-    for (int g = 0; g < G.ng; g++) {
-        for (int d = 0; d < 3; d++) {
-            int best0 = 0, bestn = 0, run0 = 0, runn = 0;
-            for (int t = 0; t < G.n[g][d]; t++) {
-                int md = pos(g, d, t) & 3;
-                bool ok = true;
-                for (int key = g * 64; key < g * 64 + 64 && ok; key++) {
-                    if (((key - g * 64) >> (2 * d) & 3) != md) continue;
-                    for (int e = T.cls[key]; e < T.cls[key + 1]; e++) {
-                        int h = eh[e];
-                        int tt = floor_div(pos(g, d, t) - G.c * colG.o[h][d], q) + edl[e][d];
-                        if (tt < 0 || tt >= colG.n[h][d]) {
-                            ok = false;
-                            break;
-                        }
-                    }
-                }
-                if (ok) {
-                    if (runn == 0) run0 = t;
-                    if (++runn > bestn) {
-                        bestn = runn;
-                        best0 = run0;
-                    }
-                } else {
-                    runn = 0;
-                }
-            }
-            G.bo[g][d] = best0;
-            G.bn[g][d] = bestn;
-        }
-        G.bz[g] = z;
-        z += G.bn[g][0] && G.bn[g][1] ? G.bn[g][2] : 0;
-        G.bmax01 = std::max(G.bmax01, (G.bn[g][0] + 1) / 2 * G.bn[g][1]);  // pairs along t_0
-    }
-    G.bz[G.ng] = z;
-    if (z == 0) return T;
-    // every box row from the tables equals the stored row
-    std::vector<char> inbox((size_t)n, 0);
-    int64_t bad = 0;
-#pragma omp parallel for schedule(static) reduction(+ : bad)
-    for (int64_t r = 0; r < n; r++) {
-        int g, t[3];
-        lat_decode(rowG, r, g, t);
-        bool in = true;
-        for (int d = 0; d < 3; d++) in = in && t[d] >= G.bo[g][d] && t[d] < G.bo[g][d] + G.bn[g][d];
-        if (!in) continue;
-        inbox[r] = 1;
-        int key, anchor[3];
-        int rr = mgk::xf_row(G, g, t[0], t[1], t[2], key, anchor);
-        int64_t k = M.rowptr[r], k1 = M.rowptr[r + 1];
-        bool good = rr == r && k1 - k == T.cls[key + 1] - T.cls[key];
-        for (int e = T.cls[key]; e < T.cls[key + 1] && good; e++, k++)
-            good = M.col[k] == mgk::xf_col(anchor, T.ent[e]) && M.val[k] == T.w[e];
-        if (!good) bad++;
-    }
-    if (bad) return T;
-    T.bnd.nrows = 0;
-    T.bnd.ncols = M.ncols;
-    T.bnd.rowptr.assign(1, 0);
-    for (int64_t r = 0; r < n; r++) {
-        if (inbox[r]) continue;
-        T.bnd_rows.push_back((int32_t)r);
-        for (int64_t k = M.rowptr[r]; k < M.rowptr[r + 1]; k++) {
-            T.bnd.col.push_back(M.col[k]);
-            T.bnd.val.push_back(M.val[k]);
-        }
-        T.bnd.rowptr.push_back((int64_t)T.bnd.col.size());
-        T.bnd.nrows++;
-    }
-    T.ok = true;
-    return T;
-}
-
 // device format of a level operator
 // SELL-32 layout: rows sorted by length, longest first (ties by row index), slices of 32
 // positions; slice s holds 32 * K_s slots from sptr[s] (K_s = its longest row).
@@ -1360,11 +1131,9 @@ static void plan_matrix(DevMat &m, const mgh::Csr &A, int fmt, int dim, int N, i
     }
 }
 
-// rowmap (SELL only): the stored rows are rows (*rowmap)[i] of the full operator, and perm
-// holds those indices
 template <typename T>
 static void upload_matrix(const DevMat &m, const mgh::Csr &A, const std::vector<T> &vals, int dim, int N,
-                          cudaStream_t s, const std::vector<int32_t> *rowmap = nullptr)
+                          cudaStream_t s)
 {
     if (m.fmt == MG_STORAGE_DIA) {
         std::vector<T> v((size_t)m.K * m.ld, T(0));
@@ -1413,8 +1182,6 @@ static void upload_matrix(const DevMat &m, const mgh::Csr &A, const std::vector<
         CK(cudaMemcpyAsync(m.val, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(m.col, c.data(), c.size() * 4, cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(m.rowptr, sptr.data(), sptr.size() * 8, cudaMemcpyHostToDevice, s));
-        if (rowmap)
-            for (auto &p : perm) p = (*rowmap)[(size_t)p];
         CK(cudaMemcpyAsync(m.perm, perm.data(), perm.size() * 4, cudaMemcpyHostToDevice, s));
         CK(cudaStreamSynchronize(s));
     } else if (m.fmt == MG_STORAGE_ELL) {
@@ -1501,25 +1268,6 @@ static std::vector<float> to_f32(const std::vector<double> &v)
     std::vector<float> o(v.size());
     for (size_t i = 0; i < v.size(); i++) o[i] = (float)v[i];
     return o;
-}
-
-template <typename T>
-static void upload_xfer(const XferD &X, const XferTables &Tb, int dim, int N, cudaStream_t s)
-{
-    std::vector<mgk::XferEnt<T>> ent(Tb.ent.size());
-    for (size_t e = 0; e < ent.size(); e++) {
-        ent[e].p = Tb.ent[e];
-        ent[e].pad = 0;
-        ent[e].w = (T)Tb.w[e];  // FP32: rounded once, like the CSR copy
-    }
-    CK(cudaMemcpyAsync(X.cls, Tb.cls.data(), Tb.cls.size() * 4, cudaMemcpyHostToDevice, s));
-    if (!ent.empty()) CK(cudaMemcpyAsync(X.ent, ent.data(), ent.size() * sizeof(ent[0]), cudaMemcpyHostToDevice, s));
-    CK(cudaStreamSynchronize(s));
-    if (X.B.n > 0) {
-        std::vector<T> bv(Tb.bnd.val.size());
-        for (size_t e = 0; e < bv.size(); e++) bv[e] = (T)Tb.bnd.val[e];
-        upload_matrix<T>(X.B, Tb.bnd, bv, dim, N, s, &Tb.bnd_rows);
-    }
 }
 
 // Chebyshev coefficients of level l (the same recurrence as the smoother's definition)
@@ -1719,14 +1467,6 @@ void mgi::build_hierarchy(mg_hierarchy *h, const mg_problem *p, const mg_options
             mgh::colour_order(dim, elem, h->lev[l].N, gs_perm[l], h->lev[l].coff);
             h->lev[l].gs_groups = mgh::colour_launch_groups(A[l], dim, elem, h->lev[l].N, h->lev[l].coff);
         }
-    // ---- transfer tables of the lattice elements (checked against every row) ----
-    std::vector<XferTables> xP((size_t)nlev), xR((size_t)nlev);
-    for (int l = 1; l <= Lf; l++) {
-        mgk::LatGeom gf, gc;
-        if (!lattice_of(dim, elem, h->lev[l].N, gf) || !lattice_of(dim, elem, h->lev[l - 1].N, gc)) continue;
-        xP[l] = learn_xfer(P[l], gf, gc, false);
-        xR[l] = learn_xfer(R[l], gc, gf, true);
-    }
     for (int pass = 0; pass < 2; pass++) {
         bool take = pass == 1;
         mgi::Slab &S = h->slab;
@@ -1779,18 +1519,7 @@ void mgi::build_hierarchy(mg_hierarchy *h, const mg_problem *p, const mg_options
             }
             if (l >= 1) {
                 L.structured = elem == MG_Q1;
-                if (!L.structured && xP[l].ok && xR[l].ok) {
-                    for (int t = 0; t < 2; t++) {
-                        XferD &X = t == 0 ? L.Pt : L.Rt;
-                        const XferTables &Tb = t == 0 ? xP[l] : xR[l];
-                        X.on = true;
-                        X.geo = Tb.dev;
-                        X.nent = (int)Tb.ent.size();
-                        X.cls = (int32_t *)vec((size_t)(mgk::XF_CLASSES + 1) * 4);
-                        X.ent = vec((size_t)std::max(X.nent, 1) * 16);  // XferEnt<T>
-                        if (Tb.bnd.nrows > 0) plan_matrix(X.B, Tb.bnd, MG_STORAGE_SELL, dim, L.N, sv, S, take);
-                    }
-                } else if (!L.structured) {
+                if (!L.structured) {
                     plan_matrix(L.P, P[l], MG_STORAGE_SELL, dim, L.N, sv, S, take);
                     plan_matrix(L.R, R[l], MG_STORAGE_SELL, dim, L.N, sv, S, take);
                 }
@@ -1843,10 +1572,7 @@ void mgi::build_hierarchy(mg_hierarchy *h, const mg_problem *p, const mg_options
                 CK(cudaMemcpyAsync(L.A.dinv, dv.data(), dv.size() * 4, cudaMemcpyHostToDevice, h->s));
                 CK(cudaStreamSynchronize(h->s));
             }
-            if (l >= 1 && L.Pt.on) {
-                upload_xfer<float>(L.Pt, xP[l], dim, L.N, h->s);
-                upload_xfer<float>(L.Rt, xR[l], dim, L.N, h->s);
-            } else if (l >= 1 && !L.structured) {
+            if (l >= 1 && !L.structured) {
                 upload_matrix<float>(L.P, P[l], to_f32(P[l].val), dim, L.N, h->s);
                 upload_matrix<float>(L.R, R[l], to_f32(R[l].val), dim, L.N, h->s);
             }
@@ -1860,10 +1586,7 @@ void mgi::build_hierarchy(mg_hierarchy *h, const mg_problem *p, const mg_options
                 CK(cudaMemcpyAsync(L.A.dinv, dv.data(), dv.size() * 8, cudaMemcpyHostToDevice, h->s));
                 CK(cudaStreamSynchronize(h->s));
             }
-            if (l >= 1 && L.Pt.on) {
-                upload_xfer<double>(L.Pt, xP[l], dim, L.N, h->s);
-                upload_xfer<double>(L.Rt, xR[l], dim, L.N, h->s);
-            } else if (l >= 1 && !L.structured) {
+            if (l >= 1 && !L.structured) {
                 upload_matrix<double>(L.P, P[l], P[l].val, dim, L.N, h->s);
                 upload_matrix<double>(L.R, R[l], R[l].val, dim, L.N, h->s);
             }
@@ -2005,9 +1728,7 @@ extern "C" mg_status mg_get_info(const mg_hierarchy *h, mg_info *info)
         info->storage[l] = h->lev[l].fmt;
         info->galerkin[l] = h->lev[l].galerkin;
         info->lambda[l] = h->lev[l].lambda;
-        const LevelD &L = h->lev[l];
-        info->transfer[l] = l == 0 ? MG_TRANSFER_NONE
-                                   : (L.structured ? MG_TRANSFER_GRID : (L.Pt.on ? MG_TRANSFER_TABLE : MG_TRANSFER_SELL));
+        info->transfer[l] = l == 0 ? MG_TRANSFER_NONE : (h->lev[l].structured ? MG_TRANSFER_GRID : MG_TRANSFER_SELL);
     }
     info->device_bytes = h->slab.size;
     info->kernels_per_cycle = h->kernels_per_cycle;
@@ -2308,33 +2029,6 @@ extern "C" mg_status mg_assemble_operator(const mg_problem *p, int level, int wh
     }
 }
 
-extern "C" mg_status mg_transfer_tables(const mg_problem *p, int level, int *ok, int *n_entries)
-{
-    try {
-        validate_problem(p);
-        if (!ok || !n_entries) throw Error(MG_EINVAL, "NULL argument");
-        if (level < 1 || level > p->n_levels - 1) throw Error(MG_EINVAL, "bad level");
-        ok[0] = ok[1] = n_entries[0] = n_entries[1] = 0;
-        mgh::HostHierarchy HH;
-        mgh::build_hierarchy(p->dim, p->element, p->n_cells, p->n_levels, p->k_cell, level - 1, HH, p->mass);
-        mgk::LatGeom gf, gc;
-        if (!lattice_of(p->dim, p->element, HH.N[level], gf) || !lattice_of(p->dim, p->element, HH.N[level - 1], gc))
-            return MG_OK;
-        XferTables tp = learn_xfer(HH.P[level], gf, gc, false), tr = learn_xfer(HH.R[level], gc, gf, true);
-        ok[0] = tp.ok;
-        ok[1] = tr.ok;
-        n_entries[0] = tp.ok ? (int)tp.ent.size() : 0;
-        n_entries[1] = tr.ok ? (int)tr.ent.size() : 0;
-        return MG_OK;
-    } catch (const Error &e) {
-        g_err = e.msg;
-        return e.st;
-    } catch (const std::bad_alloc &) {
-        g_err = "host allocation failed";
-        return MG_ENOMEM;
-    }
-}
-
 // ------------------------------------------------------------------------------------
 // Export and profiling
 // ------------------------------------------------------------------------------------
@@ -2344,70 +2038,6 @@ static std::vector<double> download_vals(const DevMat &m, size_t count)
     std::vector<T> v(count);
     CK(cudaMemcpy(v.data(), m.val, count * sizeof(T), cudaMemcpyDeviceToHost));
     return std::vector<double>(v.begin(), v.end());
-}
-
-// a table-driven transfer as CSR: the device tables, each row generated as the kernel does
-static void export_xfer(const XferD &X, int64_t nrows, int sv, mgh::Csr &out)
-{
-    std::vector<int32_t> cls(mgk::XF_CLASSES + 1), ent((size_t)X.nent);
-    std::vector<double> w((size_t)X.nent);
-    CK(cudaMemcpy(cls.data(), X.cls, cls.size() * 4, cudaMemcpyDeviceToHost));
-    if (X.nent && sv == 8) {
-        std::vector<mgk::XferEnt<double>> q((size_t)X.nent);
-        CK(cudaMemcpy(q.data(), X.ent, q.size() * sizeof(q[0]), cudaMemcpyDeviceToHost));
-        for (size_t e = 0; e < q.size(); e++) {
-            ent[e] = q[e].p;
-            w[e] = q[e].w;
-        }
-    } else if (X.nent) {
-        std::vector<mgk::XferEnt<float>> q((size_t)X.nent);
-        CK(cudaMemcpy(q.data(), X.ent, q.size() * sizeof(q[0]), cudaMemcpyDeviceToHost));
-        for (size_t e = 0; e < q.size(); e++) {
-            ent[e] = q[e].p;
-            w[e] = q[e].w;
-        }
-    }
-    std::vector<std::vector<std::pair<int32_t, double>>> rows((size_t)nrows);
-    const mgk::XferDev &G = X.geo;
-    for (int g = 0; g < G.ng; g++)
-        for (int t2 = G.bo[g][2]; t2 < G.bo[g][2] + G.bn[g][2]; t2++)
-            for (int t1 = G.bo[g][1]; t1 < G.bo[g][1] + G.bn[g][1]; t1++)
-                for (int t0 = G.bo[g][0]; t0 < G.bo[g][0] + G.bn[g][0]; t0++) {
-                    int key, anchor[3];
-                    int r = mgk::xf_row(G, g, t0, t1, t2, key, anchor);
-                    for (int e = cls[key]; e < cls[key + 1]; e++) rows[r].push_back({mgk::xf_col(anchor, ent[e]), w[e]});
-                }
-    if (X.B.n > 0) {  // the explicit rows: SELL slots in row order up to the first padding
-        const DevMat &m = X.B;
-        std::vector<double> v = sv == 8 ? download_vals<double>(m, (size_t)m.padded) : download_vals<float>(m, (size_t)m.padded);
-        std::vector<int32_t> c((size_t)m.padded), perm((size_t)m.n);
-        std::vector<int64_t> sptr((size_t)m.nslices + 1);
-        CK(cudaMemcpy(c.data(), m.col, c.size() * 4, cudaMemcpyDeviceToHost));
-        CK(cudaMemcpy(perm.data(), m.perm, perm.size() * 4, cudaMemcpyDeviceToHost));
-        CK(cudaMemcpy(sptr.data(), m.rowptr, sptr.size() * 8, cudaMemcpyDeviceToHost));
-        for (int64_t p = 0; p < m.n; p++) {
-            int64_t sl = p / 32, Ks = (sptr[sl + 1] - sptr[sl]) / 32;
-            int32_t prev = -1;
-            for (int64_t k = 0; k < Ks; k++) {
-                size_t e = (size_t)(sptr[sl] + 32 * k + p % 32);
-                if (c[e] <= prev) break;
-                if (v[e] == 0.0) continue;  // the padding of a row without entries
-                prev = c[e];
-                rows[perm[p]].push_back({c[e], v[e]});
-            }
-        }
-    }
-    out.nrows = nrows;
-    out.rowptr.assign((size_t)nrows + 1, 0);
-    out.col.clear();
-    out.val.clear();
-    for (int64_t r = 0; r < nrows; r++) {
-        for (auto &e : rows[r]) {
-            out.col.push_back(e.first);
-            out.val.push_back(e.second);
-        }
-        out.rowptr[r + 1] = (int64_t)out.col.size();
-    }
 }
 
 // transfers: the padding of a row without entries is a zero in column 0; transfer
@@ -2519,8 +2149,6 @@ extern "C" mg_status mg_export_operator(const mg_hierarchy *hc, int level, int w
                 m = P;
             else
                 mgh::transpose(P, m);
-        } else if (L.Pt.on) {
-            export_xfer(which == 1 ? L.Pt : L.Rt, which == 1 ? L.n : h->lev[level - 1].n, h->inner_size, m);
         } else {
             export_dev(which == 1 ? L.P : L.R, h->dim, L.N, h->inner_size, m, true);
             if (which == 2) m.nrows = h->lev[level - 1].n;

@@ -18,7 +18,7 @@ MG_Q1, MG_RQ1, MG_P1, MG_P2 = 0, 1, 2, 3
 MG_JACOBI, MG_CHEBYSHEV, MG_GAUSS_SEIDEL = 0, 1, 2
 MG_FP64, MG_MIXED = 0, 1
 MG_STORAGE_AUTO, MG_STORAGE_CSR, MG_STORAGE_ELL, MG_STORAGE_DIA, MG_STORAGE_SELL = 0, 1, 2, 3, 4
-MG_TRANSFER_NONE, MG_TRANSFER_GRID, MG_TRANSFER_TABLE, MG_TRANSFER_SELL = 0, 1, 2, 3
+MG_TRANSFER_NONE, MG_TRANSFER_GRID, MG_TRANSFER_SELL = 0, 1, 2
 MG_MAX_LEVELS = 16
 (MG_K_SMOOTH, MG_K_RESID, MG_K_RESTRICT, MG_K_PROLONG, MG_K_COARSE, MG_K_OUTER, MG_K_UPDATE,
  MG_K_SMOOTH0, MG_K_KRYLOV) = range(9)
@@ -103,7 +103,6 @@ SIGNATURES = {
     "mg_heat": (ctypes.c_int, [_vp, _vp, _dp, ctypes.c_int, _vp, ctypes.c_double, ctypes.c_int, _P(ctypes.c_int)]),
     "mg_heat_host": (ctypes.c_int, [_vp, _dp, _dp, ctypes.c_int, _dp, ctypes.c_double, ctypes.c_int,
                                     _P(ctypes.c_int)]),
-    "mg_transfer_tables": (ctypes.c_int, [_P(mg_problem), ctypes.c_int, _P(ctypes.c_int), _P(ctypes.c_int)]),
     "mg_cycle": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _dp]),
     "mg_export_operator": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P(ctypes.c_int64),
                                           _P(ctypes.c_int64), _P(ctypes.c_int64), _P(ctypes.c_int32), _dp]),
@@ -254,15 +253,6 @@ def mg_assemble_operator(dim, element, n_cells, n_levels, level, which=0, k_cell
                                   rowptr.ctypes.data_as(_P(ctypes.c_int64)),
                                   col.ctypes.data_as(_P(ctypes.c_int32)), _as_dp(val)))
     return rowptr, col[:nnz.value], val[:nnz.value]
-
-
-def mg_transfer_tables(dim, element, n_cells, n_levels, level, k_cell=None):
-    """Host check (no GPU) of the table-driven transfers between level and level-1:
-    ((ok_P, ok_R), (entries_P, entries_R))."""
-    p, _k = _problem(dim, element, n_cells, n_levels, k_cell, 0.0)
-    ok, ne = (ctypes.c_int * 2)(), (ctypes.c_int * 2)()
-    _check(lib().mg_transfer_tables(ctypes.byref(p), level, ok, ne))
-    return (ok[0], ok[1]), (ne[0], ne[1])
 
 
 def mg_load_vector_separable(dim, n_cells, modes=None, f_const=1.0):

@@ -128,30 +128,3 @@ def test_invalid_arguments_are_rejected(lib):
         mg.mg_assemble_operator(2, mg.MG_RQ1, 8, 2, 0)  # rotated Q1 is 3D only
     with pytest.raises(mg.MgError):
         mg.mg_assemble_operator(3, mg.MG_Q1, 8, 2, 1, which=5)
-
-
-@pytest.mark.parametrize("elem,N,L", [(1, 8, 3), (1, 16, 3), (2, 16, 3), (3, 8, 3), (3, 16, 3), (1, 24, 3),
-                                     (2, 20, 3), (3, 12, 3)])
-def test_transfer_tables_reproduce_every_row(lib, elem, N, L):
-    """Rotated Q1, P1, P2: on every level the per-class tables generate the rows of P and R
-    inside the interior boxes exactly (columns, order, weights; checked in the library,
-    row by row), the rest staying explicit. On levels whose coarse grid has at least 4
-    cells per axis every class has a complete row, and P and R, one the transpose of the
-    other, hold the same couplings per period of the grid: equally many entries."""
-    for l in range(1, L):
-        Nc = (N >> (L - 1 - l)) // 2
-        (okP, okR), (nP, nR) = mg.mg_transfer_tables(3, elem, N, L, l)
-        assert okP == 1 and okR == 1, (elem, N, l)
-        if Nc >= 4:
-            assert nP == nR > 0
-
-
-def test_transfer_tables_rotated_q1_counts(lib):
-    """Rotated Q1: a fine face on a coarse face takes that face and the +-1/4 faces of both
-    cells (9 entries), a face inside a coarse cell two faces (2 entries); 3 families x 8
-    positions mod 4 give 3 x (4 x 9 + 4 x 2) = 132 entries."""
-    (ok, n) = mg.mg_transfer_tables(3, mg.MG_RQ1, 32, 4, 3)
-    assert ok == (1, 1) and n == (132, 132)
-    # Q1 and 2D problems compute their transfers from the grid: no tables
-    assert mg.mg_transfer_tables(3, mg.MG_Q1, 16, 3, 2) == ((0, 0), (0, 0))
-    assert mg.mg_transfer_tables(2, mg.MG_Q1, 16, 3, 2) == ((0, 0), (0, 0))

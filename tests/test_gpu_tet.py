@@ -172,16 +172,14 @@ def test_sell_storage(orc, elem, N, L, precision):
 
 @pytest.mark.parametrize("elem,N,L", [(1, 16, 3), (2, 16, 3), (3, 16, 3), (3, 8, 3)])
 @pytest.mark.parametrize("precision", [mg.MG_FP64, mg.MG_MIXED])
-def test_table_transfers(orc, elem, N, L, precision):
-    """Rotated Q1, P1, P2: P and R generated from per-class tables on the interior rows of
-    every level, the rows near the boundary explicit (SELL-32); the device transfers
-    exported as CSR equal the host operators; FP64 solves bitwise, mixed converged to the
-    FP64 residual."""
+def test_explicit_transfers(orc, elem, N, L, precision):
+    """Rotated Q1, P1, P2: P and R stored explicitly in SELL-32 (rows sorted by length;
+    the prolongation of rotated Q1 has rows without entries next to the boundary); the
+    device transfers exported as CSR equal the host operators; FP64 solves bitwise, mixed
+    converged to the FP64 residual."""
     b = W.random_vector(mg.mg_ndofs(3, elem, N), seed=93)
     H, O, g, o = _both(orc, elem, N, L, b, precision=precision)
-    tr = H.info()["transfer"]
-    assert tr[0] == mg.MG_TRANSFER_NONE
-    assert all(t == mg.MG_TRANSFER_TABLE for t in tr[1:]), tr
+    assert H.info()["transfer"] == [mg.MG_TRANSFER_NONE] + [mg.MG_TRANSFER_SELL] * (L - 1)
     assert g[0] == mg.MG_OK
     if precision == mg.MG_FP64:
         assert g[1] == o[1] and np.array_equal(g[3], o[3])
@@ -191,3 +189,8 @@ def test_table_transfers(orc, elem, N, L, precision):
                 assert np.array_equal(rp, M.rowptr) and np.array_equal(col, M.col) and np.array_equal(val, M.val)
     else:
         assert np.linalg.norm(b - orc.spmv(O.A(L - 1), g[3])) <= 1e-10 * np.linalg.norm(b)
+
+
+def test_q1_transfers_from_the_grid():
+    H = mg.Hierarchy(3, mg.MG_Q1, 16, 3)
+    assert H.info()["transfer"] == [mg.MG_TRANSFER_NONE, mg.MG_TRANSFER_GRID, mg.MG_TRANSFER_GRID]
