@@ -169,6 +169,12 @@ SWEEP_TEXT = {0: "fused residual + damped Jacobi update", 1: "fused residual + C
               2: "one colour of a multicolour Gauss-Seidel sweep, in place"}
 
 
+def _tail_mode(args):
+    if args.no_tail or args.tail == "off":
+        return 0
+    return 1 if args.tail == "on" else 2
+
+
 def _config_args(name, smoother="workload"):
     """The workload's parameters; `smoother` other than "workload" replaces its smoother."""
     from paper_1609_04809_gb300 import workloads as W
@@ -471,7 +477,7 @@ def run_ours(args):
     H = mg.Hierarchy(c["dim"], c["element"], c["n_cells"], c["n_levels"], smoother=c["smoother"],
                      omega=c["omega"], cheb_degree=c["cheb_degree"], nu_pre=c["nu_pre"], nu_post=c["nu_post"],
                      precision=mg.MG_MIXED if args.precision == "mixed" else mg.MG_FP64,
-                     use_pdl=0 if args.no_pdl else 1, coarse_tail=0 if args.no_tail else 2,
+                     use_pdl=0 if args.no_pdl else 1, coarse_tail=_tail_mode(args),
                      storage=STORAGES[args.storage])
     info = H.info()
     Lf = c["n_levels"] - 1
@@ -553,7 +559,8 @@ def run_ours(args):
             p64, pit64, _ = solve_time(H, mg.mg_pcg)
             Hm = mg.Hierarchy(c["dim"], c["element"], c["n_cells"], c["n_levels"], smoother=c["smoother"],
                               omega=c["omega"], cheb_degree=c["cheb_degree"], nu_pre=c["nu_pre"],
-                              nu_post=c["nu_post"], precision=mg.MG_MIXED)
+                              nu_post=c["nu_post"], precision=mg.MG_MIXED, use_pdl=0 if args.no_pdl else 1,
+                              coarse_tail=_tail_mode(args), storage=STORAGES[args.storage])
             t32, it32, r32 = solve_time(Hm)
             p32, pit32, _ = solve_time(Hm, mg.mg_pcg)
             tts = {"tol": tol, "fp64_ms": 1e3 * t64, "fp64_iters": it64, "mixed_ms": 1e3 * t32, "mixed_iters": it32,
@@ -626,6 +633,9 @@ def main():
     ap.add_argument("--serve-slots", type=int, default=256)
     ap.add_argument("--no-pdl", action="store_true", help="launch without programmatic dependent launch")
     ap.add_argument("--no-tail", action="store_true", help="run the small levels as separate kernels")
+    ap.add_argument("--tail", default="auto", choices=["auto", "on", "off"],
+                    help="coarse-level tail launch: auto times the V-cycle with and without it at setup "
+                         "(pin it under a profiler); --no-tail is --tail off")
     ap.add_argument("--storage", default="auto", choices=sorted(STORAGES),
                     help="level-matrix storage; auto times the candidates at setup (pin it under a profiler, "
                          "whose serialisation would skew that timing)")
