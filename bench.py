@@ -164,7 +164,8 @@ def replica_throughput(ms_local, n_dofs, steps, world, dist=None, device="cpu"):
 
 
 SMOOTHERS = {"jacobi": 0, "chebyshev": 1, "gauss-seidel": 2}
-STORAGES = {"auto": 0, "csr": 1, "ell": 2, "dia": 3, "sell": 4}
+STORAGES = {"auto": 0, "csr": 1, "ell": 2, "dia": 3, "sell": 4, "stencil": 5}
+STORAGE_NAMES = {v: k for k, v in STORAGES.items()}
 SWEEP_TEXT = {0: "fused residual + damped Jacobi update", 1: "fused residual + Chebyshev update",
               2: "one colour of a multicolour Gauss-Seidel sweep, in place"}
 
@@ -412,7 +413,7 @@ def config_report(name, steps=20, warmup=5, smoother="workload"):
                     "finest_sweep_fp64_tflops": k_flops / ks / 1e12 if (ks and tag == "fp64") else None,
                     "time_to_tol_ms": 1e3 * float(np.median(ts[1:])), "iterations": its,
                     "final_rel_residual": rel, "true_fp64_rel_residual": true_rel,
-                    "storage": ["csr", "ell", "dia", "sell"][info["storage"][Lf] - 1], "setup_s": setup_s,
+                    "storage": STORAGE_NAMES[info["storage"][Lf]], "setup_s": setup_s,
                     "device_gb": info["device_bytes"] / 1e9, "tail_levels": info["tail_levels"], "pcg": pcg}
         H.close()
         del H
@@ -597,7 +598,7 @@ def run_ours(args):
                           "parallelism": "replicas" if world > 1 else "single-gpu",
                           "l2": "inputs larger than L2 (finest FP64 matrix %.0f MB > 129 MB L2)"
                                 % (info["nnz"][Lf] * 8 / 1e6),
-                          "storage": ["csr", "ell", "dia", "sell"][info["storage"][Lf] - 1],
+                          "storage": STORAGE_NAMES[info["storage"][Lf]],
                           "smoother": [k for k, v in SMOOTHERS.items() if v == c["smoother"]][0]},
                "roofline": roofline_block(args.precision, name, fp64_tflops, achieved, peak, peak_kind, k_flops,
                                           k_bytes, k_cnt, k_s, c["smoother"]),

@@ -84,6 +84,13 @@ typedef int mg_status;
 #define MG_STORAGE_DIA 3  /* column-major ELLPACK whose columns are row + fixed offsets (Q1, P1) */
 #define MG_STORAGE_SELL 4 /* sliced ELLPACK: rows sorted by length, slices of 32 rows stored
                              column-major with their own width, 32-bit columns */
+#define MG_STORAGE_STENCIL 5 /* constant stencil (Q1, P1; FP32 levels of a mixed hierarchy):
+                                one value per stencil position, used where every row of the
+                                level matrix is the same stencil (constant coefficient,
+                                rediscretised), boundary neighbours masked from the grid
+                                coordinates; no matrix is stored or streamed. Checked exactly
+                                on the host; levels that fail the check, Galerkin levels and
+                                levels of at most 32768 rows keep DIA. Not with Gauss-Seidel. */
 /* grid transfers P (prolongation, Sec. 5.1) and R = P^T of a level (mg_info.transfer) */
 #define MG_TRANSFER_NONE 0 /* level 0 (no coarser level) */
 #define MG_TRANSFER_GRID 1 /* Q1: weights computed from the grid in the kernel */

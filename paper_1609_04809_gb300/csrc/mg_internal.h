@@ -45,7 +45,12 @@ struct DevMat {
     int64_t nslices = 0;      // SELL: slices of 32 rows
     int64_t padded = 0;       // SELL: stored slots (entries incl. padding)
     int64_t *rowptr = nullptr;
-    void *dinv = nullptr;  // 1 / a_ii, FP64 inner levels only
+    void *dinv = nullptr;  // 1 / a_ii: FP64 levels; FP32 ELL/CSR/SELL levels
+    // STENCIL (slots as DIA): the value of each slot and 1 / a_ii in the inner precision
+    // (held as double), the grid (interior points per axis, dimension)
+    double sval[27] = {};
+    double sdinv = 0.0;
+    int n1 = 0, dim = 3;
 };
 
 struct LevelD {

@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -284,6 +285,7 @@ static double mat_bytes(const DevMat &m, int sv)
 {
     switch (m.fmt) {
     case MG_STORAGE_DIA: return (double)m.K * (double)m.n * sv;
+    case MG_STORAGE_STENCIL: return 0.0;  // the values are launch parameters
     case MG_STORAGE_ELL: return (double)m.K * (double)m.n * (sv + 4);
     case MG_STORAGE_SELL: return (double)m.padded * (sv + 4) + 8.0 * (double)(m.nslices + 1) + 4.0 * (double)m.n;
     default: return (double)m.nnz * (sv + 4) + 8.0 * (double)(m.n + 1);
@@ -327,6 +329,25 @@ template <typename T, int MODE>
 static void sweep_fmt(const DevMat &A, int n, const T *x, const T *b, T *out, T *d, T c1, T c2, cudaStream_t s,
                       bool pdl = false)
 {
+    if (A.fmt == MG_STORAGE_STENCIL) {
+        StencilView<T> S{};
+        for (int k = 0; k < A.K; k++) {
+            S.a[k] = (T)A.sval[k];
+            S.off[k] = A.offs.o[k];
+            S.pos[k] = A.full_of[k];
+        }
+        S.dinv = (T)A.sdinv;
+        S.n1 = A.n1;
+        unsigned bx = line_block((unsigned)A.n1);
+        dim3 g(((unsigned)A.n1 + bx - 1) / bx, (unsigned)A.n1, A.dim == 3 ? (unsigned)A.n1 : 1u);
+        with_dia_k(A.K, [&](auto k) {
+            if (A.dim == 3)
+                klaunch(pdl, k_stencil_sweep<T, decltype(k)::value, MODE, 3>, g, dim3(bx), 0, s, S, x, b, out, d, c1, c2);
+            else
+                klaunch(pdl, k_stencil_sweep<T, decltype(k)::value, MODE, 2>, g, dim3(bx), 0, s, S, x, b, out, d, c1, c2);
+        });
+        return;
+    }
     MatView<T> v = view<T>(A);
     unsigned bs = sweep_block(n);
     dim3 g((unsigned)((n + bs - 1) / bs)), blk(bs);
@@ -367,7 +388,9 @@ static void sweep(mg_hierarchy *h, int l, int mode, const T *x, const T *b, T *o
     bool zero = mode == SW_JACOBI_Z || mode == SW_CHEBF_Z;
     if (zero) {  // the diagonal (stored D^-1, the DIA diagonal slot, or a row scan), b, out [, d]
         kclass = MG_K_SMOOTH0;
-        double diag = L.A.dinv ? n * sv : (L.A.fmt == MG_STORAGE_DIA ? n * sv : mat_bytes(L.A, sv));
+        double diag = L.A.fmt == MG_STORAGE_STENCIL
+                          ? 0.0
+                          : (L.A.dinv ? n * sv : (L.A.fmt == MG_STORAGE_DIA ? n * sv : mat_bytes(L.A, sv)));
         bytes = diag + 2 * n * sv + (mode == SW_CHEBF_Z ? n * sv : 0);
     } else {  // the matrix, x, b, out [, D^-1] [, d read and/or write]
         kclass = mode == SW_RESID ? MG_K_RESID : MG_K_SMOOTH;
@@ -1030,14 +1053,91 @@ static void sell_layout(const mgh::Csr &A, std::vector<int32_t> &perm, std::vect
     }
 }
 
-static void plan_matrix(DevMat &m, const mgh::Csr &A, int fmt, int dim, int N, int sv, mgi::Slab &slab, bool take)
+// Constant stencil (Q1, P1 on the grid vertices): by_pos[p] receives the values of the
+// row of grid point (2, 2[, 2]) by stencil position p = (dx+1) + 3(dy+1) [+ 9(dz+1)], in the
+// inner precision (FP32: that row's row-sum-preserving rounding, as round_fp32 forms it).
+// True only if every row of A holds exactly these FP64 values at its in-grid neighbours:
+// no entry outside the 3^d box, the stencil's nonzero positions all present where the
+// neighbour is in the grid, any other entry zero.
+static bool constant_stencil(const mgh::Csr &A, int dim, int N, int sv, double by_pos[27])
+{
+    if (N < 4) return false;
+    const int npos = dim == 3 ? 27 : 9;
+    const int64_t n1 = N - 1;
+    const int64_t i0 = 1 + n1 * (1 + (dim == 3 ? n1 : 0));
+    double st[27] = {};
+    bool has[27] = {};
+    auto pos_of = [&](const int *ci, const int *cj, int &p) {
+        int q[3] = {0, 0, 0};
+        for (int a = 0; a < dim; a++) {
+            q[a] = cj[a] - ci[a];
+            if (q[a] < -1 || q[a] > 1) return false;
+        }
+        p = (q[0] + 1) + 3 * (q[1] + 1) + (dim == 3 ? 9 * (q[2] + 1) : 0);
+        return true;
+    };
+    int ci[3], cj[3], p;
+    mgh::q1_coords(dim, N, i0, ci);
+    for (int64_t k = A.rowptr[i0]; k < A.rowptr[i0 + 1]; k++) {
+        mgh::q1_coords(dim, N, A.col[k], cj);
+        if (!pos_of(ci, cj, p)) return false;
+        st[p] = A.val[k];
+        has[p] = true;
+    }
+    int64_t bad = 0;
+#pragma omp parallel for schedule(static) reduction(+ : bad)
+    for (int64_t i = 0; i < A.nrows; i++) {
+        int vi[3], vj[3], q;
+        mgh::q1_coords(dim, N, i, vi);
+        unsigned seen = 0;
+        bool ok = true;
+        for (int64_t k = A.rowptr[i]; k < A.rowptr[i + 1] && ok; k++) {
+            mgh::q1_coords(dim, N, A.col[k], vj);
+            ok = pos_of(vi, vj, q) && A.val[k] == (has[q] ? st[q] : 0.0);
+            if (ok) seen |= 1u << q;
+        }
+        for (int pp = 0; pp < npos && ok; pp++) {
+            if (!has[pp] || st[pp] == 0.0 || ((seen >> pp) & 1u)) continue;
+            int dd[3] = {pp % 3 - 1, (pp / 3) % 3 - 1, pp / 9 - 1};
+            bool in = true;
+            for (int a = 0; a < dim; a++) in = in && vi[a] + dd[a] >= 1 && vi[a] + dd[a] <= N - 1;
+            ok = !in;  // a stencil neighbour inside the grid is missing from the row
+        }
+        if (!ok) bad++;
+    }
+    if (bad) return false;
+    for (int pp = 0; pp < 27; pp++) by_pos[pp] = st[pp];
+    if (sv == 4) {  // the row-sum-preserving FP32 rounding of row i0
+        double rowsum = 0.0, off32 = 0.0;
+        int pc = -1;
+        for (int64_t k = A.rowptr[i0]; k < A.rowptr[i0 + 1]; k++) {
+            mgh::q1_coords(dim, N, A.col[k], cj);
+            pos_of(ci, cj, p);
+            rowsum = rowsum + A.val[k];
+            if (A.col[k] == i0) {
+                pc = p;
+            } else {
+                by_pos[p] = (double)(float)A.val[k];
+                off32 = off32 + by_pos[p];
+            }
+        }
+        if (pc >= 0) by_pos[pc] = (double)(float)(rowsum - off32);
+    }
+    return true;
+}
+
+// stencil_vals: STENCIL only, the values by stencil position (constant_stencil)
+static void plan_matrix(DevMat &m, const mgh::Csr &A, int fmt, int dim, int N, int sv, mgi::Slab &slab, bool take,
+                        const double *stencil_vals = nullptr)
 {
     m.fmt = fmt;
     m.n = A.nrows;
     m.nnz = A.nnz();
     m.ld = round_up(std::max<int64_t>(m.n, 1), 64);
     m.elem_size = sv;
-    if (fmt == MG_STORAGE_DIA) {
+    m.n1 = N - 1;
+    m.dim = dim;
+    if (fmt == MG_STORAGE_DIA || fmt == MG_STORAGE_STENCIL) {
         // keep the stencil positions that hold a nonzero anywhere (ascending offset),
         // padded with unused positions up to an instantiated slot count (9, 21 or 27).
         // A symmetric matrix uses position p iff it uses npos-1-p, and padding adds such
@@ -1078,6 +1178,13 @@ static void plan_matrix(DevMat &m, const mgh::Csr &A, int fmt, int dim, int N, i
             k++;
         }
         if (k != K || m.center != K / 2) throw Error(MG_EINVAL, "DIA slot selection is not symmetric");
+        if (fmt == MG_STORAGE_STENCIL) {  // values as launch parameters; nothing stored
+            if (!stencil_vals) throw Error(MG_EINVAL, "stencil storage without stencil values");
+            for (int q = 0; q < K; q++) m.sval[q] = stencil_vals[m.full_of[q]];
+            double ac = m.sval[m.center];
+            m.sdinv = sv == 8 ? 1.0 / ac : (double)(1.0f / (float)ac);
+            return;
+        }
         size_t bytes = (size_t)m.K * m.ld * sv;
         if (take)
             m.val = slab.take(bytes);
@@ -1135,6 +1242,7 @@ template <typename T>
 static void upload_matrix(const DevMat &m, const mgh::Csr &A, const std::vector<T> &vals, int dim, int N,
                           cudaStream_t s)
 {
+    if (m.fmt == MG_STORAGE_STENCIL) return;  // nothing stored
     if (m.fmt == MG_STORAGE_DIA) {
         std::vector<T> v((size_t)m.K * m.ld, T(0));
         int k3 = dim == 3 ? 9 : 0;
@@ -1294,6 +1402,9 @@ static int pick_storage(const mg_options &o, int elem)
     bool vertex_grid = elem == MG_Q1 || elem == MG_P1;  // DOFs on the grid vertices, stencil in the 27-point box
     if (o.storage == MG_STORAGE_DIA && !vertex_grid)
         throw Error(MG_EINVAL, "DIA storage needs Q1 or P1 (fixed stencil offsets)");
+    if (o.storage == MG_STORAGE_STENCIL &&
+        (!vertex_grid || o.precision != MG_MIXED || o.smoother == MG_GAUSS_SEIDEL))
+        throw Error(MG_EINVAL, "stencil storage needs Q1 or P1, mixed precision and no Gauss-Seidel");
     if (o.storage != MG_STORAGE_AUTO) return o.storage;
     return vertex_grid ? MG_STORAGE_DIA : MG_STORAGE_ELL;
 }
@@ -1302,13 +1413,15 @@ static int pick_storage(const mg_options &o, int elem)
 // in temporary device memory and timed on residual sweeps; the fastest wins. Choices are
 // cached per (dim, element, cells, value size) for the life of the process.
 template <typename T>
-static double time_format(mg_hierarchy *h, const mgh::Csr &A, int fmt, int dim, int N)
+static double time_format(mg_hierarchy *h, const mgh::Csr &A, int fmt, int dim, int N, const double *svals)
 {
     mgi::Slab S;
     DevMat m;
-    plan_matrix(m, A, fmt, dim, N, sizeof(T), S, false);
+    plan_matrix(m, A, fmt, dim, N, sizeof(T), S, false, svals);
     int64_t n1 = N - 1;
-    int64_t pad = fmt == MG_STORAGE_DIA ? round_up(dim == 3 ? n1 * n1 + n1 + 1 : n1 + 1, 64) : 0;
+    int64_t pad = fmt == MG_STORAGE_DIA || fmt == MG_STORAGE_STENCIL
+                      ? round_up(dim == 3 ? n1 * n1 + n1 + 1 : n1 + 1, 64)
+                      : 0;
     int64_t ld = round_up(std::max<int64_t>(A.nrows, 1), 64);
     S.reserve((size_t)(ld + 2 * pad) * sizeof(T));
     S.reserve((size_t)ld * sizeof(T) * 2);
@@ -1323,7 +1436,7 @@ static double time_format(mg_hierarchy *h, const mgh::Csr &A, int fmt, int dim, 
     if (!S.base) return 1e300;  // no room to try it: never chosen
     double ms_best = 1e300;
     try {
-        plan_matrix(m, A, fmt, dim, N, sizeof(T), S, true);
+        plan_matrix(m, A, fmt, dim, N, sizeof(T), S, true, svals);
         char *xb = (char *)S.take((size_t)(ld + 2 * pad) * sizeof(T));
         T *x = (T *)(xb + pad * sizeof(T));
         T *b = (T *)S.take((size_t)ld * sizeof(T)), *r = (T *)S.take((size_t)ld * sizeof(T));
@@ -1357,11 +1470,12 @@ static double time_format(mg_hierarchy *h, const mgh::Csr &A, int fmt, int dim, 
     return ms_best;
 }
 
-static int tune_storage(mg_hierarchy *h, const mgh::Csr &A, int dim, int elem, int N)
+// svals: the level's constant stencil (constant_stencil) when it may be stored as one
+static int tune_storage(mg_hierarchy *h, const mgh::Csr &A, int dim, int elem, int N, const double *svals)
 {
     static std::mutex mu;
-    static std::map<std::tuple<int, int, int, int, bool>, int> cache;
-    auto key = std::make_tuple(dim, elem, N, h->inner_size, h->mass != 0.0);
+    static std::map<std::tuple<int, int, int, int, bool, bool>, int> cache;
+    auto key = std::make_tuple(dim, elem, N, h->inner_size, h->mass != 0.0, svals != nullptr);
     {
         std::lock_guard<std::mutex> lk(mu);
         auto it = cache.find(key);
@@ -1372,10 +1486,11 @@ static int tune_storage(mg_hierarchy *h, const mgh::Csr &A, int dim, int elem, i
     cands.push_back(MG_STORAGE_ELL);
     cands.push_back(MG_STORAGE_CSR);
     if (elem == MG_RQ1 || elem == MG_P2) cands.push_back(MG_STORAGE_SELL);  // uneven rows (P2) or no DIA
+    if (svals) cands.push_back(MG_STORAGE_STENCIL);
     int best = cands[0];
     double best_ms = 1e300;
     for (int f : cands) {
-        double ms = h->mixed ? time_format<float>(h, A, f, dim, N) : time_format<double>(h, A, f, dim, N);
+        double ms = h->mixed ? time_format<float>(h, A, f, dim, N, svals) : time_format<double>(h, A, f, dim, N, svals);
         if (ms < best_ms) {
             best_ms = ms;
             best = f;
@@ -1397,7 +1512,7 @@ void mgi::build_hierarchy(mg_hierarchy *h, const mg_problem *p, const mg_options
         throw Error(MG_EINVAL, "bad Chebyshev parameters");
     if (o->nu_pre < 0 || o->nu_post < 0 || o->max_iters < 0) throw Error(MG_EINVAL, "negative counts");
     if (o->precision != MG_FP64 && o->precision != MG_MIXED) throw Error(MG_EINVAL, "bad precision");
-    if (o->storage < MG_STORAGE_AUTO || o->storage > MG_STORAGE_SELL) throw Error(MG_EINVAL, "bad storage");
+    if (o->storage < MG_STORAGE_AUTO || o->storage > MG_STORAGE_STENCIL) throw Error(MG_EINVAL, "bad storage");
     h->prob = *p;
     h->prob.k_cell = nullptr;
     h->opt = *o;
@@ -1453,9 +1568,21 @@ void mgi::build_hierarchy(mg_hierarchy *h, const mg_problem *p, const mg_options
     // ---- device memory plan (pass 0: count, pass 1: assign) ----
     int fmt = pick_storage(*o, elem);
     std::vector<int> lfmt((size_t)nlev, fmt);
-    if (o->storage == MG_STORAGE_AUTO)  // measured on the levels large enough to be bandwidth-bound
+    // constant-stencil storage: FP32 levels above the coarse-level tail whose every row is
+    // the same stencil (checked exactly)
+    std::vector<std::array<double, 27>> svals((size_t)nlev);
+    std::vector<char> scan((size_t)nlev, 0);
+    if (h->mixed && (elem == MG_Q1 || elem == MG_P1) && o->smoother != MG_GAUSS_SEIDEL)
         for (int l = 1; l <= Lf; l++)
-            if (h->lev[l].n >= 32768) lfmt[l] = tune_storage(h, A[l], dim, elem, h->lev[l].N);
+            if (h->lev[l].n >= 32768) scan[l] = constant_stencil(A[l], dim, h->lev[l].N, 4, svals[l].data());
+    if (o->storage == MG_STORAGE_AUTO) {  // measured on the levels large enough to be bandwidth-bound
+        for (int l = 1; l <= Lf; l++)
+            if (h->lev[l].n >= 32768)
+                lfmt[l] = tune_storage(h, A[l], dim, elem, h->lev[l].N, scan[l] ? svals[l].data() : nullptr);
+    } else if (fmt == MG_STORAGE_STENCIL) {
+        for (int l = 0; l <= Lf; l++)
+            if (!scan[l]) lfmt[l] = MG_STORAGE_DIA;
+    }
     int sv = h->inner_size;
     // ---- multicolour Gauss-Seidel: colour order of every smoothed level ----
     const bool gs = o->smoother == MG_GAUSS_SEIDEL;
@@ -1495,18 +1622,20 @@ void mgi::build_hierarchy(mg_hierarchy *h, const mg_problem *p, const mg_options
             LevelD &L = h->lev[l];
             int lf = lfmt[l];
             L.fmt = lf;
-            plan_matrix(L.A, A[l], lf, dim, L.N, sv, S, take);
+            plan_matrix(L.A, A[l], lf, dim, L.N, sv, S, take, lf == MG_STORAGE_STENCIL ? svals[l].data() : nullptr);
             if (!h->mixed && l >= 1) L.A.dinv = vec((size_t)L.A.ld * 8);  // FP64 smoothers read D^-1
             // FP32 sweeps from x = 0 on formats whose diagonal has no fixed slot read D^-1
             // instead of scanning the row (the same value: 1/a_ii rounded once)
-            if (h->mixed && l >= 1 && lf != MG_STORAGE_DIA) L.A.dinv = vec((size_t)L.A.ld * 4);
+            if (h->mixed && l >= 1 && lf != MG_STORAGE_DIA && lf != MG_STORAGE_STENCIL)
+                L.A.dinv = vec((size_t)L.A.ld * 4);
             if (gs && l >= 1) {  // the colour-major copy of A for the Gauss-Seidel sweeps (CSR for SELL levels)
                 plan_matrix(L.G, A[l], lf == MG_STORAGE_SELL ? MG_STORAGE_CSR : lf, dim, L.N, sv, S, take);
                 if (!h->mixed) L.G.dinv = vec((size_t)L.G.ld * 8);
                 L.perm = (int32_t *)vec((size_t)std::max<int64_t>(L.G.n, 1) * 4);
             }
             int64_t n1 = L.N - 1;
-            L.pad = lf == MG_STORAGE_DIA ? round_up(dim == 3 ? n1 * n1 + n1 + 1 : n1 + 1, 64) : 0;
+            L.pad = lf == MG_STORAGE_DIA || lf == MG_STORAGE_STENCIL ? round_up(dim == 3 ? n1 * n1 + n1 + 1 : n1 + 1, 64)
+                                                                     : 0;
             int64_t ld = L.A.ld;
             if (with_vectors) {
                 for (int c = 0; c < 2; c++) {
@@ -1527,7 +1656,8 @@ void mgi::build_hierarchy(mg_hierarchy *h, const mg_problem *p, const mg_options
         }
         LevelD &F = h->lev[Lf];
         if (h->mixed) {
-            plan_matrix(h->A64, A[Lf], F.fmt, dim, F.N, 8, S, take);
+            // the FP64 operator of the outer residual is stored (a stencil level stores DIA)
+            plan_matrix(h->A64, A[Lf], F.fmt == MG_STORAGE_STENCIL ? MG_STORAGE_DIA : F.fmt, dim, F.N, 8, S, take);
         } else if (take) {
             h->A64 = F.A;
         }
@@ -1542,7 +1672,7 @@ void mgi::build_hierarchy(mg_hierarchy *h, const mg_problem *p, const mg_options
             h->pcg_q = (double *)vec((size_t)F.A.ld * 8);
             h->pcg_scal = (double *)vec(PCG_NSCAL * 8);
             if (h->mass != 0.0) {
-                plan_matrix(h->B64, Bh, F.fmt, dim, F.N, 8, S, take);
+                plan_matrix(h->B64, Bh, F.fmt == MG_STORAGE_STENCIL ? MG_STORAGE_DIA : F.fmt, dim, F.N, 8, S, take);
                 h->bF64 = (double *)vec((size_t)F.A.ld * 8);
             }
         }
@@ -2079,6 +2209,27 @@ static void export_dev(const DevMat &m, int dim, int N, int sv, mgh::Csr &out, b
             for (auto &e : rows[i]) {
                 out.col.push_back(e.first);
                 out.val.push_back(e.second);
+            }
+            out.rowptr[i + 1] = (int64_t)out.col.size();
+        }
+        return;
+    }
+    if (m.fmt == MG_STORAGE_STENCIL) {  // every in-grid neighbour with the stencil's value
+        int slot_of[27];
+        for (int p = 0; p < 27; p++) slot_of[p] = -1;
+        for (int k = 0; k < m.K; k++) slot_of[m.full_of[k]] = k;
+        int64_t n1 = N - 1;
+        for (int64_t i = 0; i < m.n; i++) {
+            int ci[3] = {0, 0, 0};
+            mgh::q1_coords(dim, N, i, ci);
+            for (int p = 0; p < (dim == 3 ? 27 : 9); p++) {
+                int d[3] = {p % 3 - 1, (p / 3) % 3 - 1, dim == 3 ? p / 9 - 1 : 0};
+                bool inside = true;
+                for (int a = 0; a < dim; a++)
+                    if (ci[a] + d[a] < 1 || ci[a] + d[a] > N - 1) inside = false;
+                if (!inside) continue;
+                out.col.push_back((int32_t)(i + d[0] + n1 * d[1] + n1 * n1 * d[2]));
+                out.val.push_back(slot_of[p] >= 0 ? m.sval[slot_of[p]] : 0.0);
             }
             out.rowptr[i + 1] = (int64_t)out.col.size();
         }

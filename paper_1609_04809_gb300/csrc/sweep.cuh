@@ -133,6 +133,51 @@ __global__ void __launch_bounds__(256) k_dia_sweep(MatView<T> A, int n, const T 
     sweep_out<T, MODE>(i, s, dinv, xv[C], b, out, d, c1, c2);
 }
 
+// Constant stencil: every row holds the same value a[k] at stencil position pos[k]
+// ((dx+1) + 3(dy+1) + 9(dz+1), ascending, so the slots are in ascending column order),
+// minus the neighbours outside the grid, which the row does not hold. One thread per
+// grid point (launch: x along the grid line, y and z the other two axes); the neighbour
+// masks come from the point's coordinates, and x is padded like DIA, so every load is in
+// bounds and only the multiply-adds are predicated.
+template <typename T>
+struct StencilView {
+    T a[27];
+    int32_t off[27];
+    int32_t pos[27];
+    T dinv;  // 1 / a_ii of the stencil
+    int n1;  // interior points per axis
+};
+
+template <typename T, int K, int MODE, int DIM>
+__global__ void __launch_bounds__(128) k_stencil_sweep(StencilView<T> S, const T *__restrict__ x,
+                                                       const T *__restrict__ b, T *__restrict__ out,
+                                                       T *__restrict__ d, T c1, T c2)
+{
+    pdl_enter();
+    int vx = blockIdx.x * blockDim.x + threadIdx.x, vy = blockIdx.y, vz = DIM == 3 ? blockIdx.z : 0;
+    if (vx >= S.n1) return;
+    int i = vx + S.n1 * (vy + S.n1 * vz);
+    if (IsZero<MODE>::value) {
+        sweep_out<T, MODE>(i, T(0), S.dinv, T(0), b, out, d, c1, c2);
+        return;
+    }
+    constexpr int C = K / 2;
+    // per axis, bit j: the neighbour at offset j - 1 exists (2D: the z index is 0)
+    unsigned mx = 2u | (vx > 0 ? 1u : 0u) | (vx < S.n1 - 1 ? 4u : 0u);
+    unsigned my = 2u | (vy > 0 ? 1u : 0u) | (vy < S.n1 - 1 ? 4u : 0u);
+    unsigned mz = DIM == 3 ? (2u | (vz > 0 ? 1u : 0u) | (vz < S.n1 - 1 ? 4u : 0u)) : 1u;
+    T xv[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) xv[k] = __ldg(x + i + S.off[k]);
+    T s = T(0);
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        int p = S.pos[k];
+        if ((mx >> (p % 3)) & (my >> ((p / 3) % 3)) & (mz >> (p / 9)) & 1u) s = Ar<T>::mac(s, S.a[k], xv[k]);
+    }
+    sweep_out<T, MODE>(i, s, S.dinv, xv[C], b, out, d, c1, c2);
+}
+
 // ELL with explicit columns; padded slots hold column i and value 0.
 template <typename T, int MODE>
 __global__ void __launch_bounds__(256) k_ell_sweep(MatView<T> A, int n, const T *__restrict__ x,
