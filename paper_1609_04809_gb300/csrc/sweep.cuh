@@ -162,19 +162,22 @@ __global__ void __launch_bounds__(128) k_stencil_sweep(StencilView<T> S, const T
         return;
     }
     constexpr int C = K / 2;
-    // per axis, bit j: the neighbour at offset j - 1 exists (2D: the z index is 0)
+    // bit p of m: the neighbour at stencil position p lies in the grid (per axis, bit j of
+    // mx, my, mz: the neighbour at offset j - 1 exists)
     unsigned mx = 2u | (vx > 0 ? 1u : 0u) | (vx < S.n1 - 1 ? 4u : 0u);
     unsigned my = 2u | (vy > 0 ? 1u : 0u) | (vy < S.n1 - 1 ? 4u : 0u);
-    unsigned mz = DIM == 3 ? (2u | (vz > 0 ? 1u : 0u) | (vz < S.n1 - 1 ? 4u : 0u)) : 1u;
+    unsigned m = ((my & 1u) ? mx : 0u) | ((my & 2u) ? mx << 3 : 0u) | ((my & 4u) ? mx << 6 : 0u);
+    if (DIM == 3) {
+        unsigned mz = 2u | (vz > 0 ? 1u : 0u) | (vz < S.n1 - 1 ? 4u : 0u);
+        m = ((mz & 1u) ? m : 0u) | ((mz & 2u) ? m << 9 : 0u) | ((mz & 4u) ? m << 18 : 0u);
+    }
     T xv[K];
 #pragma unroll
     for (int k = 0; k < K; k++) xv[k] = __ldg(x + i + S.off[k]);
     T s = T(0);
 #pragma unroll
-    for (int k = 0; k < K; k++) {
-        int p = S.pos[k];
-        if ((mx >> (p % 3)) & (my >> ((p / 3) % 3)) & (mz >> (p / 9)) & 1u) s = Ar<T>::mac(s, S.a[k], xv[k]);
-    }
+    for (int k = 0; k < K; k++)
+        if ((m >> S.pos[k]) & 1u) s = Ar<T>::mac(s, S.a[k], xv[k]);
     sweep_out<T, MODE>(i, s, S.dinv, xv[C], b, out, d, c1, c2);
 }
 
