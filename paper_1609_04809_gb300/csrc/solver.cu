@@ -338,13 +338,13 @@ static void sweep_fmt(const DevMat &A, int n, const T *x, const T *b, T *out, T 
         }
         S.dinv = (T)A.sdinv;
         S.n1 = A.n1;
-        unsigned bx = line_block((unsigned)A.n1);
-        dim3 g(((unsigned)A.n1 + bx - 1) / bx, (unsigned)A.n1, A.dim == 3 ? (unsigned)A.n1 : 1u);
+        unsigned n1 = (unsigned)A.n1, bx = line_block(n1), by = std::min(256u / bx, n1);
+        dim3 g((n1 + bx - 1) / bx, (n1 + by - 1) / by, A.dim == 3 ? n1 : 1u), blk(bx, by);
         with_dia_k(A.K, [&](auto k) {
             if (A.dim == 3)
-                klaunch(pdl, k_stencil_sweep<T, decltype(k)::value, MODE, 3>, g, dim3(bx), 0, s, S, x, b, out, d, c1, c2);
+                klaunch(pdl, k_stencil_sweep<T, decltype(k)::value, MODE, 3>, g, blk, 0, s, S, x, b, out, d, c1, c2);
             else
-                klaunch(pdl, k_stencil_sweep<T, decltype(k)::value, MODE, 2>, g, dim3(bx), 0, s, S, x, b, out, d, c1, c2);
+                klaunch(pdl, k_stencil_sweep<T, decltype(k)::value, MODE, 2>, g, blk, 0, s, S, x, b, out, d, c1, c2);
         });
         return;
     }

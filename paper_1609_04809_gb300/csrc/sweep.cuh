@@ -138,7 +138,8 @@ __global__ void __launch_bounds__(256) k_dia_sweep(MatView<T> A, int n, const T 
 // minus the neighbours outside the grid, which the row does not hold. One thread per
 // grid point (launch: x along the grid line, y and z the other two axes); the neighbour
 // masks come from the point's coordinates, and x is padded like DIA, so every load is in
-// bounds and only the multiply-adds are predicated.
+// bounds and only the multiply-adds are predicated. Blocks of up to 256 threads cover
+// 256 / blockDim.x neighbouring grid lines.
 template <typename T>
 struct StencilView {
     T a[27];
@@ -149,13 +150,14 @@ struct StencilView {
 };
 
 template <typename T, int K, int MODE, int DIM>
-__global__ void __launch_bounds__(128) k_stencil_sweep(StencilView<T> S, const T *__restrict__ x,
+__global__ void __launch_bounds__(256) k_stencil_sweep(StencilView<T> S, const T *__restrict__ x,
                                                        const T *__restrict__ b, T *__restrict__ out,
                                                        T *__restrict__ d, T c1, T c2)
 {
     pdl_enter();
-    int vx = blockIdx.x * blockDim.x + threadIdx.x, vy = blockIdx.y, vz = DIM == 3 ? blockIdx.z : 0;
-    if (vx >= S.n1) return;
+    int vx = blockIdx.x * blockDim.x + threadIdx.x, vy = blockIdx.y * blockDim.y + threadIdx.y;
+    int vz = DIM == 3 ? blockIdx.z : 0;
+    if (vx >= S.n1 || vy >= S.n1) return;
     int i = vx + S.n1 * (vy + S.n1 * vz);
     if (IsZero<MODE>::value) {
         sweep_out<T, MODE>(i, T(0), S.dinv, T(0), b, out, d, c1, c2);
