@@ -115,10 +115,27 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def _traffic_from_profile(kernel_tag):
-    """DRAM bytes per launch from the committed ncu summary, if it matches the current kernels."""
-    src = os.path.join(ROOT, "paper_1609_04809_gb300", "csrc", "sweep.cuh")
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+SWEEP_KERNELS = {"dia": "k_dia_sweep", "ell": "k_ell_sweep", "csr": "k_csr_sweep", "sell": "k_sell_sweep",
+                 "stencil": "k_stencil_sweep"}
+
+
+def _kernel_sha(storage):
+    """sha256[:16] of the sweep kernel of this storage as the compiler sees it: sweep.cuh up
+    to the end of that kernel (its helpers come first), comments and blank lines dropped."""
+    src = open(os.path.join(ROOT, "paper_1609_04809_gb300", "csrc", "sweep.cuh")).read()
+    start = src.index(SWEEP_KERNELS[storage] + "(")
+    end = src.index("\n}\n", start) + 3
+    lines = [ln.split("//")[0].rstrip() for ln in src[:end].splitlines()]
+    return hashlib.sha256("\n".join(ln for ln in lines if ln.strip()).encode()).hexdigest()[:16]
+
+
+def _traffic_from_profile(kernel_tag, storage):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the sweep
+    kernel of this storage as it is now."""
+    if storage not in SWEEP_KERNELS:
+        return None
+    sha = _kernel_sha(storage)
+    kernel_tag = "%s_%s" % (kernel_tag, storage)
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
@@ -129,7 +146,8 @@ def _traffic_from_profile(kernel_tag):
     return None
 
 
-def roofline_block(precision, name, tflops, gbs, peak_gbs, peak_kind, flops, nbytes, launches, sec, smoother=1):
+def roofline_block(precision, name, tflops, gbs, peak_gbs, peak_kind, flops, nbytes, launches, sec, smoother=1,
+                   storage="dia"):
     """The dominant kernel against the roofline that binds it: the FP64 pipe for the FP64
     sweep (GB300 issues about 2 DFMA per clock per SM), HBM bandwidth for the FP32 one."""
     hbm = {"achieved": gbs, "peak": peak_gbs, "unit": "GB/s", "frac": gbs / peak_gbs if gbs else None,
@@ -139,14 +157,14 @@ def roofline_block(precision, name, tflops, gbs, peak_gbs, peak_kind, flops, nby
     if precision == "fp64":
         out = {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                "frac": tflops / FP64_PEAK_TFLOPS if tflops else None,
-               "traffic": _traffic_from_profile("smooth_fp64_%s" % name) if smoother != 2 else None,
+               "traffic": _traffic_from_profile("smooth_fp64_%s" % name, storage) if smoother != 2 else None,
                "kernel": "finest-level smoother sweep (%s), FP64" % SWEEP_TEXT[smoother],
                "peak_kind": "FP64 pipe: 152 SMs x 2.07 GHz x 2 DFMA/clk/SM x 2 flop (recipe nominal)",
                "hbm": hbm}
     else:
         out = dict(hbm)
         out.update({"bound": "hbm",
-                    "traffic": _traffic_from_profile("smooth_fp32_%s" % name) if smoother != 2 else None,
+                    "traffic": _traffic_from_profile("smooth_fp32_%s" % name, storage) if smoother != 2 else None,
                     "kernel": "finest-level smoother sweep (%s), FP32" % SWEEP_TEXT[smoother]})
     out.update(common)
     return out
@@ -601,7 +619,7 @@ def run_ours(args):
                           "storage": STORAGE_NAMES[info["storage"][Lf]],
                           "smoother": [k for k, v in SMOOTHERS.items() if v == c["smoother"]][0]},
                "roofline": roofline_block(args.precision, name, fp64_tflops, achieved, peak, peak_kind, k_flops,
-                                          k_bytes, k_cnt, k_s, c["smoother"]),
+                                          k_bytes, k_cnt, k_s, c["smoother"], STORAGE_NAMES[info["storage"][Lf]]),
                "kernel_ms_per_step": per_kernel,
                "e2e": e2e, "time_to_solution": tts, "cpu_baseline": cpu,
                "gpu_launches": info["kernels_per_cycle"] * args.steps + 1,
