@@ -119,10 +119,12 @@ SWEEP_KERNELS = {"dia": "k_dia_sweep", "ell": "k_ell_sweep", "csr": "k_csr_sweep
                  "stencil": "k_stencil_sweep"}
 
 
-def _kernel_sha(storage):
+def _kernel_sha(storage, src=None):
     """sha256[:16] of the sweep kernel of this storage as the compiler sees it: sweep.cuh up
-    to the end of that kernel (its helpers come first), comments and blank lines dropped."""
-    src = open(os.path.join(ROOT, "paper_1609_04809_gb300", "csrc", "sweep.cuh")).read()
+    to the end of that kernel (its helpers come first), comments and blank lines dropped.
+    src: the header's text (default: the file)."""
+    if src is None:
+        src = open(os.path.join(ROOT, "paper_1609_04809_gb300", "csrc", "sweep.cuh")).read()
     start = src.index(SWEEP_KERNELS[storage] + "(")
     end = src.index("\n}\n", start) + 3
     lines = [ln.split("//")[0].rstrip() for ln in src[:end].splitlines()]
