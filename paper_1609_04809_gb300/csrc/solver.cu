@@ -325,6 +325,13 @@ static void klaunch(bool pdl, void (*kernel)(KArgs...), dim3 grid, dim3 block, s
     if (e != cudaSuccess) throw Error(MG_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
 }
 
+// stencil position sets with fixed-position kernels: bit (dx+1) + 3(dy+1) + 9(dz+1)
+constexpr unsigned kStencil27 = 0x7FFFFFFu;  // every position (Q1 + mass shift)
+constexpr unsigned kFaces = (1u << 4) | (1u << 10) | (1u << 12) | (1u << 14) | (1u << 16) | (1u << 22);
+constexpr unsigned kStencilQ1 = kStencil27 & ~kFaces;   // 3D Q1: face couplings are zero
+constexpr unsigned kStencilP1 = kFaces | (1u << 13);    // P1 on the Kuhn mesh: seven points
+constexpr unsigned kStencil9 = 0x1FFu;                  // 2D Q1
+
 template <typename T, int MODE>
 static void sweep_fmt(const DevMat &A, int n, const T *x, const T *b, T *out, T *d, T c1, T c2, cudaStream_t s,
                       bool pdl = false)
@@ -340,6 +347,24 @@ static void sweep_fmt(const DevMat &A, int n, const T *x, const T *b, T *out, T 
         S.n1 = A.n1;
         unsigned n1 = (unsigned)A.n1, bx = line_block(n1), by = std::min(256u / bx, n1);
         dim3 g((n1 + bx - 1) / bx, (n1 + by - 1) / by, A.dim == 3 ? n1 : 1u), blk(bx, by);
+        unsigned pm = 0;  // the stored positions; the common sets have fixed-position kernels
+        for (int k = 0; k < A.K; k++) pm |= 1u << A.full_of[k];
+        if (A.dim == 3 && pm == kStencilQ1) {
+            klaunch(pdl, k_stencil_fixed<T, kStencilQ1, MODE, 3>, g, blk, 0, s, S, x, b, out, d, c1, c2);
+            return;
+        }
+        if (A.dim == 3 && pm == kStencil27) {
+            klaunch(pdl, k_stencil_fixed<T, kStencil27, MODE, 3>, g, blk, 0, s, S, x, b, out, d, c1, c2);
+            return;
+        }
+        if (A.dim == 3 && pm == kStencilP1) {
+            klaunch(pdl, k_stencil_fixed<T, kStencilP1, MODE, 3>, g, blk, 0, s, S, x, b, out, d, c1, c2);
+            return;
+        }
+        if (A.dim == 2 && pm == kStencil9) {
+            klaunch(pdl, k_stencil_fixed<T, kStencil9, MODE, 2>, g, blk, 0, s, S, x, b, out, d, c1, c2);
+            return;
+        }
         with_dia_k(A.K, [&](auto k) {
             if (A.dim == 3)
                 klaunch(pdl, k_stencil_sweep<T, decltype(k)::value, MODE, 3>, g, blk, 0, s, S, x, b, out, d, c1, c2);

@@ -183,6 +183,47 @@ __global__ void __launch_bounds__(256) k_stencil_sweep(StencilView<T> S, const T
     sweep_out<T, MODE>(i, s, S.dinv, xv[C], b, out, d, c1, c2);
 }
 
+// The same sweep with the stencil's positions fixed at compile time (PM: bit p set for
+// each stored position, ascending p = slot order): the offsets of a grid line become
+// immediates on one row pointer per (dy, dz), and each slot's mask test a constant bit.
+template <typename T, unsigned PM, int MODE, int DIM>
+__global__ void __launch_bounds__(256) k_stencil_fixed(StencilView<T> S, const T *__restrict__ x,
+                                                       const T *__restrict__ b, T *__restrict__ out,
+                                                       T *__restrict__ d, T c1, T c2)
+{
+    pdl_enter();
+    int vx = blockIdx.x * blockDim.x + threadIdx.x, vy = blockIdx.y * blockDim.y + threadIdx.y;
+    int vz = DIM == 3 ? blockIdx.z : 0;
+    if (vx >= S.n1 || vy >= S.n1) return;
+    const int n1 = S.n1;
+    int i = vx + n1 * (vy + n1 * vz);
+    if (IsZero<MODE>::value) {
+        sweep_out<T, MODE>(i, T(0), S.dinv, T(0), b, out, d, c1, c2);
+        return;
+    }
+    unsigned mx = 2u | (vx > 0 ? 1u : 0u) | (vx < n1 - 1 ? 4u : 0u);
+    unsigned my = 2u | (vy > 0 ? 1u : 0u) | (vy < n1 - 1 ? 4u : 0u);
+    unsigned m = ((my & 1u) ? mx : 0u) | ((my & 2u) ? mx << 3 : 0u) | ((my & 4u) ? mx << 6 : 0u);
+    if (DIM == 3) {
+        unsigned mz = 2u | (vz > 0 ? 1u : 0u) | (vz < n1 - 1 ? 4u : 0u);
+        m = ((mz & 1u) ? m : 0u) | ((mz & 2u) ? m << 9 : 0u) | ((mz & 4u) ? m << 18 : 0u);
+    }
+    constexpr int CP = DIM == 3 ? 13 : 4;  // the centre position
+    const T *xi = x + i;
+    T s = T(0), xc = T(0);
+    int k = 0;
+#pragma unroll
+    for (int p = 0; p < (DIM == 3 ? 27 : 9); p++) {
+        if (!((PM >> p) & 1u)) continue;
+        const int dx = p % 3 - 1, dy = (p / 3) % 3 - 1, dz = DIM == 3 ? p / 9 - 1 : 0;
+        T v = __ldg(xi + (dy * n1 + dz * n1 * n1) + dx);
+        if (p == CP) xc = v;
+        if (p == CP || ((m >> p) & 1u)) s = Ar<T>::mac(s, S.a[k], v);
+        k++;
+    }
+    sweep_out<T, MODE>(i, s, S.dinv, xc, b, out, d, c1, c2);
+}
+
 // ELL with explicit columns; padded slots hold column i and value 0.
 template <typename T, int MODE>
 __global__ void __launch_bounds__(256) k_ell_sweep(MatView<T> A, int n, const T *__restrict__ x,
