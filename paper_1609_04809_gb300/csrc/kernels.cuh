@@ -95,22 +95,9 @@ __global__ void __launch_bounds__(128) k_prolong_q1(const T *__restrict__ xc, T 
     xf[line + 2 * m] = Ar<T>::add(xf[line + 2 * m], to);                      // v0 = 2m + 1
 }
 
-// Explicit CSR transfer: y_i = sum_k v_k x_col  (ADD: y_i += that sum).
-template <typename T, bool ADD>
-__global__ void __launch_bounds__(256) k_csr_apply(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
-                                                   const T *__restrict__ val, int n, const T *__restrict__ x,
-                                                   T *__restrict__ y)
-{
-    pdl_enter();
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    T s = T(0);
-    for (int64_t k = rowptr[i]; k < rowptr[i + 1]; k++) s = Ar<T>::mac(s, val[k], __ldg(x + col[k]));
-    y[i] = ADD ? Ar<T>::add(y[i], s) : s;
-}
-
-// The same transfer with the operator in SELL-32 (see k_sell_sweep): storage position r
-// computes row perm[r]; each row keeps its CSR order, so the sums equal k_csr_apply's.
+// Explicit transfer (rotated Q1, P1, P2) with the operator in SELL-32 (see k_sell_sweep):
+// y_i = sum_k v_k x_col(k) in the row's CSR order (ADD: y_i += that sum); storage position
+// r computes row perm[r].
 template <typename T, bool ADD>
 __global__ void __launch_bounds__(256) k_sell_apply(const int64_t *__restrict__ sptr, const int32_t *__restrict__ col,
                                                     const T *__restrict__ val, const int32_t *__restrict__ perm,

@@ -541,13 +541,10 @@ static void restrict_to(mg_hierarchy *h, int l, const T *r, cudaStream_t s)
             klaunch(pdl, k_restrict_q1<T, 3>, g, dim3(bx), 0, s, r, (T *)C.b, C.N);
         else
             klaunch(pdl, k_restrict_q1<T, 2>, g, dim3(bx), 0, s, r, (T *)C.b, C.N);
-    } else if (F.R.fmt == MG_STORAGE_SELL) {
+    } else {  // explicit R in SELL-32
         klaunch(h->opt.use_pdl != 0, k_sell_apply<T, false>, dim3(grid_for(C.n)), dim3(256), 0, s,
                 (const int64_t *)F.R.rowptr, (const int32_t *)F.R.col, (const T *)F.R.val, (const int32_t *)F.R.perm,
                 (int)C.n, r, (T *)C.b);
-    } else {
-        klaunch(h->opt.use_pdl != 0, k_csr_apply<T, false>, dim3(grid_for(C.n)), dim3(256), 0, s,
-                (const int64_t *)F.R.rowptr, (const int32_t *)F.R.col, (const T *)F.R.val, (int)C.n, r, (T *)C.b);
     }
 }
 
@@ -576,13 +573,10 @@ static void prolong_add(mg_hierarchy *h, int l, const T *xc, T *xf, cudaStream_t
             klaunch(pdl, k_prolong_q1<T, 3>, g, dim3(bx), 0, s, xc, xf, C.N);
         else
             klaunch(pdl, k_prolong_q1<T, 2>, g, dim3(bx), 0, s, xc, xf, C.N);
-    } else if (F.P.fmt == MG_STORAGE_SELL) {
+    } else {  // explicit P in SELL-32
         klaunch(h->opt.use_pdl != 0, k_sell_apply<T, true>, dim3(grid_for(F.n)), dim3(256), 0, s,
                 (const int64_t *)F.P.rowptr, (const int32_t *)F.P.col, (const T *)F.P.val, (const int32_t *)F.P.perm,
                 (int)F.n, xc, xf);
-    } else {
-        klaunch(h->opt.use_pdl != 0, k_csr_apply<T, true>, dim3(grid_for(F.n)), dim3(256), 0, s,
-                (const int64_t *)F.P.rowptr, (const int32_t *)F.P.col, (const T *)F.P.val, (int)F.n, xc, xf);
     }
 }
 
