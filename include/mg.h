@@ -199,6 +199,13 @@ mg_status mg_load_vector_separable(const mg_problem *p, const mg_rhs *f, double 
 mg_status mg_assemble_operator(const mg_problem *p, int level, int which, int64_t *nrows, int64_t *nnz,
                                int64_t *rowptr, int32_t *col, double *val);
 
+/* Host only: *is_stencil = 1 if every row of the level-`level` matrix (as mg_setup
+ * assembles it, mass shift included) is the same stencil: no entry outside the 3^d box
+ * of the grid point, the interior row's FP64 values at every in-grid neighbour, zero
+ * elsewhere; the condition for MG_STORAGE_STENCIL on an FP32 level. Q1 and P1 only (0
+ * for the other elements and for grids of fewer than 4 cells per axis). */
+mg_status mg_constant_stencil(const mg_problem *p, int level, int *is_stencil);
+
 /* Build the level hierarchy: per-level stiffness matrices (rediscretised; R A P of the
  * finer level where the coefficient is not resolved by the coarse cells), transfer
  * operators P (Q1 nodal interpolation, rotated-Q1 face averaging) and R = P^T, device

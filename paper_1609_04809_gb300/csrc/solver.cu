@@ -2178,6 +2178,28 @@ extern "C" mg_status mg_assemble_operator(const mg_problem *p, int level, int wh
     }
 }
 
+extern "C" mg_status mg_constant_stencil(const mg_problem *p, int level, int *is_stencil)
+{
+    try {
+        validate_problem(p);
+        if (!is_stencil) throw Error(MG_EINVAL, "NULL argument");
+        if (level < 0 || level > p->n_levels - 1) throw Error(MG_EINVAL, "bad level");
+        *is_stencil = 0;
+        if (p->element != MG_Q1 && p->element != MG_P1) return MG_OK;
+        mgh::HostHierarchy HH;
+        mgh::build_hierarchy(p->dim, p->element, p->n_cells, p->n_levels, p->k_cell, level, HH, p->mass);
+        double vals[27];
+        *is_stencil = constant_stencil(HH.A[level], p->dim, HH.N[level], 8, vals) ? 1 : 0;
+        return MG_OK;
+    } catch (const Error &e) {
+        g_err = e.msg;
+        return e.st;
+    } catch (const std::bad_alloc &) {
+        g_err = "host allocation failed";
+        return MG_ENOMEM;
+    }
+}
+
 // ------------------------------------------------------------------------------------
 // Export and profiling
 // ------------------------------------------------------------------------------------

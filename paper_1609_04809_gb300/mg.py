@@ -103,6 +103,7 @@ SIGNATURES = {
     "mg_heat": (ctypes.c_int, [_vp, _vp, _dp, ctypes.c_int, _vp, ctypes.c_double, ctypes.c_int, _P(ctypes.c_int)]),
     "mg_heat_host": (ctypes.c_int, [_vp, _dp, _dp, ctypes.c_int, _dp, ctypes.c_double, ctypes.c_int,
                                     _P(ctypes.c_int)]),
+    "mg_constant_stencil": (ctypes.c_int, [_P(mg_problem), ctypes.c_int, _P(ctypes.c_int)]),
     "mg_cycle": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _dp]),
     "mg_export_operator": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P(ctypes.c_int64),
                                           _P(ctypes.c_int64), _P(ctypes.c_int64), _P(ctypes.c_int32), _dp]),
@@ -253,6 +254,14 @@ def mg_assemble_operator(dim, element, n_cells, n_levels, level, which=0, k_cell
                                   rowptr.ctypes.data_as(_P(ctypes.c_int64)),
                                   col.ctypes.data_as(_P(ctypes.c_int32)), _as_dp(val)))
     return rowptr, col[:nnz.value], val[:nnz.value]
+
+
+def mg_constant_stencil(dim, element, n_cells, n_levels, level, k_cell=None, mass=0.0):
+    """Host check (no GPU): is every row of the level matrix the same stencil? (bool)"""
+    p, _k = _problem(dim, element, n_cells, n_levels, k_cell, mass)
+    out = ctypes.c_int(0)
+    _check(lib().mg_constant_stencil(ctypes.byref(p), level, ctypes.byref(out)))
+    return bool(out.value)
 
 
 def mg_load_vector_separable(dim, n_cells, modes=None, f_const=1.0):

@@ -128,3 +128,69 @@ def test_invalid_arguments_are_rejected(lib):
         mg.mg_assemble_operator(2, mg.MG_RQ1, 8, 2, 0)  # rotated Q1 is 3D only
     with pytest.raises(mg.MgError):
         mg.mg_assemble_operator(3, mg.MG_Q1, 8, 2, 1, which=5)
+
+
+def _constant_stencil_ref(A, dim, N):
+    """The constant-stencil condition written out on an oracle matrix: every entry within
+    the 3^d box of its grid point, equal to the interior row's value at its position (zero
+    where that row has none), and every in-grid neighbour with a nonzero stencil value
+    present."""
+    n1 = N - 1
+    n = A.rowptr.size - 1
+    rows = np.repeat(np.arange(n), np.diff(A.rowptr))
+
+    def coords(idx):
+        c = [idx % n1, (idx // n1) % n1] + ([idx // (n1 * n1)] if dim == 3 else [])
+        return np.stack(c, axis=1)
+
+    ci, cj = coords(rows), coords(A.col.astype(np.int64))
+    d = cj - ci
+    if np.any(np.abs(d) > 1):
+        return False
+    pos = (d[:, 0] + 1) + 3 * (d[:, 1] + 1) + (9 * (d[:, 2] + 1) if dim == 3 else 0)
+    i0 = 1 + n1 * (1 + (n1 if dim == 3 else 0))
+    sel = rows == i0
+    st, has = np.zeros(27), np.zeros(27, bool)
+    st[pos[sel]], has[pos[sel]] = A.val[sel], True
+    if not np.array_equal(A.val, np.where(has[pos], st[pos], 0.0)):
+        return False
+    present = np.zeros((n, 27), bool)
+    present[rows, pos] = True
+    allc = coords(np.arange(n))
+    for p in range(27 if dim == 3 else 9):
+        if not has[p] or st[p] == 0.0:
+            continue
+        dd = np.array([p % 3 - 1, (p // 3) % 3 - 1] + ([p // 9 - 1] if dim == 3 else []))
+        inside = np.all((allc + dd >= 0) & (allc + dd <= n1 - 1), axis=1)
+        if np.any(inside & ~present[:, p]):
+            return False
+    return True
+
+
+@pytest.mark.parametrize("dim,elem,N,L,kind,mass", [
+    (3, 0, 16, 3, None, 0.0), (2, 0, 32, 3, None, 0.0), (3, 0, 16, 3, "blocks4", 0.0),
+    (3, 0, 16, 3, None, 200.0), (3, 2, 16, 3, None, 0.0), (3, 2, 16, 3, None, 200.0),
+    (3, 2, 16, 4, "blocks4", 0.0)])
+def test_constant_stencil_check_agrees_with_the_oracle_operator(lib, orc, dim, elem, N, L, kind, mass):
+    """The library's host check behind MG_STORAGE_STENCIL against the condition written out
+    on the oracle's matrices: constant coefficients (with or without the mass shift) give
+    one stencil per level; per-cell coefficients and Galerkin levels do not."""
+    k = _k(dim, N, kind)
+    H = orc.Hierarchy(dim, elem, N, L, k_cell=k, mass=mass)
+    for l in range(L):
+        Nl = N >> (L - 1 - l)
+        got = mg.mg_constant_stencil(dim, elem, N, L, l, k, mass=mass)
+        want = Nl >= 4 and _constant_stencil_ref(H.A(l), dim, Nl)
+        assert got == want, (l, got, want)
+        if kind is None and Nl >= 4:
+            assert got
+    if kind is not None:
+        assert not mg.mg_constant_stencil(dim, elem, N, L, L - 1, k, mass=mass)
+
+
+def test_constant_stencil_only_for_vertex_elements(lib):
+    assert not mg.mg_constant_stencil(3, mg.MG_RQ1, 16, 3, 2)
+    assert not mg.mg_constant_stencil(3, mg.MG_P2, 8, 3, 2)
+    # a grid of 2 cells per axis has no interior row with all neighbours inside
+    assert not mg.mg_constant_stencil(3, mg.MG_Q1, 8, 3, 0)
+    assert mg.mg_constant_stencil(3, mg.MG_Q1, 16, 3, 0)
