@@ -89,7 +89,8 @@ def test_heat_edge_cases(orc):
     # one step equals the oracle's
     st, its = H.heat(torch.from_numpy(bF).cuda(), wl["g"], u, 1e-10)
     O = orc.Hierarchy(3, 0, 8, 2, mass=wl["sigma"], opts=orc.Options())
-    uo, ito = orc.heat(O, orc.heat_B(3, 0, 8, wl["sigma"]), bF, wl["g"], wl["u0"], 1e-10)
+    bFo = orc.load_vector(3, orc.Q1, 8, modes=wl["source_modes"])
+    uo, ito = orc.heat(O, orc.heat_B(3, orc.Q1, 8, wl["sigma"]), bFo, wl["g"], wl["u0"], 1e-10)
     assert np.array_equal(u.cpu().numpy(), uo) and list(its) == list(ito)
 
 

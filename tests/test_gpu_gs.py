@@ -54,7 +54,7 @@ CASES = [
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
 def test_gs_fp64_bitwise(orc, case):
     _, dim, elem, N, L, nu = case
-    b = mg.mg_load_vector(dim, elem, N, modes=W.manufactured_modes(dim))
+    b = orc.load_vector(dim, elem, N, modes=W.manufactured_modes(dim))
     H, O, g, o = _both(orc, dim, elem, N, L, b, nu=nu)
     st, it, hist, x = g
     conv, ito, ho, xo = o
@@ -77,7 +77,7 @@ def test_gs_every_storage_and_graph_mode(orc, dim, elem, N, L, storage, graph):
 def test_gs_galerkin_levels(orc):
     dim, N, L = 3, 32, 4
     k = W.k_blocks(N, dim=3, blocks_per_axis=8, seed=20260101)
-    b = mg.mg_load_vector(dim, 0, N, modes=None, f_const=1.0)
+    b = orc.load_vector(dim, 0, N)
     H, O, g, o = _both(orc, dim, 0, N, L, b, k=k)
     assert H.info()["galerkin"] == [1, 0, 0, 0]
     assert g[0] == mg.MG_OK and g[1] == o[1] and np.array_equal(g[3], o[3])
@@ -97,7 +97,7 @@ def test_gs_vcycle_alone_bitwise(orc):
 
 @pytest.mark.parametrize("dim,elem,N,L", [(3, 0, 32, 4), (3, 1, 16, 4), (2, 0, 128, 6)])
 def test_gs_mixed_precision_reaches_fp64_tolerance(orc, dim, elem, N, L):
-    b = mg.mg_load_vector(dim, elem, N, modes=W.manufactured_modes(dim))
+    b = orc.load_vector(dim, elem, N, modes=W.manufactured_modes(dim))
     H, O, g, o = _both(orc, dim, elem, N, L, b, precision=mg.MG_MIXED)
     st, it, hist, x = g
     assert st == mg.MG_OK
@@ -117,7 +117,7 @@ def test_gs_full_size_128(orc):
     """The 128^3 Q1 workload with Gauss-Seidel V(1,1) at full size, as bench --smoother
     gauss-seidel runs it (DIA, colour pairs): bit for bit the oracle's iterates."""
     c = W.CONFIGS["q1_3d_128_cheb"]
-    b = mg.mg_load_vector(3, 0, c["n_cells"], modes=W.manufactured_modes(3))
+    b = orc.load_vector(3, 0, c["n_cells"], modes=W.manufactured_modes(3))
     H, O, g, o = _both(orc, 3, 0, c["n_cells"], c["n_levels"], b, nu=(1, 1))
     assert H.info()["storage"][c["n_levels"] - 1] == mg.MG_STORAGE_DIA
     st, it, hist, x = g

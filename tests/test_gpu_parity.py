@@ -79,7 +79,7 @@ SMALL = [
 @pytest.mark.parametrize("case", SMALL, ids=[c[0] for c in SMALL])
 def test_fp64_matches_oracle_manufactured(orc, case):
     _, dim, elem, N, L, sm, om, n1, n2 = case
-    b = mg.mg_load_vector(dim, elem, N, modes=W.manufactured_modes(dim))
+    b = orc.load_vector(dim, elem, N, modes=W.manufactured_modes(dim))
     H, O, g, o = _run_both(orc, dim, elem, N, L, b, smoother=sm, omega=om, nu_pre=n1, nu_post=n2)
     _assert_fp64_parity(g, o)
     if sm == 1:
@@ -165,7 +165,7 @@ def test_rq1_storage(orc, storage):
 def test_variable_coefficient_with_galerkin_levels(orc):
     dim, elem, N, L = 3, 0, 32, 4  # blocks of 4 cells: the 4^3-cell level straddles blocks
     k = W.k_blocks(N, dim=3, blocks_per_axis=8, seed=20260101)
-    b = mg.mg_load_vector(dim, elem, N, modes=None, f_const=1.0)
+    b = orc.load_vector(dim, elem, N)
     H, O, g, o = _run_both(orc, dim, elem, N, L, b, smoother=1, nu_pre=1, nu_post=1, k=k)
     assert H.info()["galerkin"] == [1, 0, 0, 0]
     _assert_fp64_parity(g, o)
@@ -175,11 +175,12 @@ def test_device_operators_equal_host_operators(orc):
     for dim, elem, N, L, fmt in [(3, 0, 8, 3, mg.MG_STORAGE_DIA), (2, 0, 16, 3, mg.MG_STORAGE_DIA),
                                  (3, 1, 8, 3, mg.MG_STORAGE_ELL), (3, 0, 8, 2, mg.MG_STORAGE_CSR)]:
         H = mg.Hierarchy(dim, elem, N, L, storage=fmt)
+        O = orc.Hierarchy(dim, elem, N, L)
         for l in range(L):
             for which in ((0, 1, 2) if l else (0,)):
                 a = H.export(l, which)
-                b = mg.mg_assemble_operator(dim, elem, N, L, l, which)
-                for u, v in zip(a, b):
+                m = (O.A, O.P, O.R)[which](l)
+                for u, v in zip(a, (m.rowptr, m.col, m.val)):
                     assert np.array_equal(u, v), (dim, elem, l, which)
 
 
@@ -257,7 +258,7 @@ def test_profiled_launch_counts(orc):
 
 @pytest.mark.parametrize("dim,elem,N,L,sm", [(3, 0, 32, 4, 1), (3, 1, 16, 4, 0), (2, 0, 128, 6, 0)])
 def test_mixed_precision_reaches_fp64_tolerance(orc, dim, elem, N, L, sm):
-    b = mg.mg_load_vector(dim, elem, N, modes=W.manufactured_modes(dim))
+    b = orc.load_vector(dim, elem, N, modes=W.manufactured_modes(dim))
     H, O, g, o = _run_both(orc, dim, elem, N, L, b, smoother=sm, omega=0.7 if elem else 0.8,
                            nu_pre=1 if sm else 2, nu_post=1 if sm else 2, precision=mg.MG_MIXED)
     st, it, hist, x = g

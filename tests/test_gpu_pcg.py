@@ -70,7 +70,7 @@ CASES = [
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
 def test_pcg_fp64_matches_oracle(orc, case):
     _, dim, elem, N, L, sm, om, nu = case
-    b = mg.mg_load_vector(dim, elem, N, modes=W.manufactured_modes(dim))
+    b = orc.load_vector(dim, elem, N, modes=W.manufactured_modes(dim))
     H, O, g, o = _pcg_both(orc, dim, elem, N, L, b, smoother=sm, omega=om, nu=nu)
     _assert_parity(g, o, 1e-10)
 
@@ -87,7 +87,7 @@ def test_pcg_every_storage_and_graph_mode(orc, storage, graph):
 def test_pcg_variable_coefficient(orc):
     N, L = 32, 4
     k = W.k_blocks(N, dim=3, blocks_per_axis=8, seed=20260101)
-    b = mg.mg_load_vector(3, 0, N, modes=None, f_const=1.0)
+    b = orc.load_vector(3, 0, N)
     H, O, g, o = _pcg_both(orc, 3, 0, N, L, b, smoother=1, nu=1, k=k)
     _assert_parity(g, o, 1e-10)
     # and CG needs fewer V-cycles than the defect correction on the jumping coefficient
@@ -99,7 +99,7 @@ def test_pcg_variable_coefficient(orc):
 @pytest.mark.parametrize("smoother", [0, 1, 2])
 def test_pcg_mixed_precision_reaches_fp64_tolerance(orc, smoother):
     dim, elem, N, L = 3, 0, 32, 4
-    b = mg.mg_load_vector(dim, elem, N, modes=W.manufactured_modes(dim))
+    b = orc.load_vector(dim, elem, N, modes=W.manufactured_modes(dim))
     H, O, g, o = _pcg_both(orc, dim, elem, N, L, b, smoother=smoother, nu=1 if smoother else 2,
                            precision=mg.MG_MIXED)
     st, it, hist, x = g
@@ -133,7 +133,7 @@ def test_pcg_rejects_an_unsymmetric_vcycle():
 def test_pcg_full_size_128(orc):
     """The 128^3 Chebyshev workload at full size, as the bench runs it."""
     c = W.CONFIGS["q1_3d_128_cheb"]
-    b = mg.mg_load_vector(3, 0, c["n_cells"], modes=W.manufactured_modes(3))
+    b = orc.load_vector(3, 0, c["n_cells"], modes=W.manufactured_modes(3))
     H, O, g, o = _pcg_both(orc, 3, 0, c["n_cells"], c["n_levels"], b, smoother=c["smoother"], omega=c["omega"],
                            nu=c["nu_pre"])
     _assert_parity(g, o, 1e-10)

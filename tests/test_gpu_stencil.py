@@ -2,8 +2,8 @@
 every row of a rediscretised constant-coefficient level is the same stencil, so the
 level keeps one value per stencil position and masks the boundary neighbours from the
 grid coordinates. The FP32 V-cycle is a preconditioner inside the FP64 defect
-correction; the bar is the FP64 residual, checked here against the stored-matrix (DIA)
-solve and the host operator."""
+correction; the bar is the FP64 residual, recomputed by the oracle from its own matrix,
+and the distance to the stored-matrix (DIA) solve."""
 import numpy as np
 import pytest
 
@@ -23,23 +23,24 @@ def _lib():
     torch.cuda.set_device(0)
 
 
-def _solve(dim, elem, N, L, b, storage, sm=1, nu=1, omega=0.8, k=None, mass=0.0):
+def _solve(orc, dim, elem, N, L, b, storage, sm=1, nu=1, omega=0.8, k=None):
+    """Mixed solve to 1e-10; nr is ||b - A x|| with A assembled and applied by the oracle."""
     H = mg.Hierarchy(dim, elem, N, L, k_cell=k, smoother=sm, omega=omega, nu_pre=nu, nu_post=nu,
-                     precision=mg.MG_MIXED, storage=storage, mass=mass)
+                     precision=mg.MG_MIXED, storage=storage)
     bd = torch.from_numpy(b).cuda()
     x = torch.zeros_like(bd)
     st, it, hist = H.solve(bd, x, 1e-10)
-    r = torch.empty_like(bd)
-    nr = mg.mg_residual_norm_noalloc(H.h, bd, x, r)  # FP64, the stored FP64 operator
-    return H, st, it, nr, x.cpu().numpy()
+    x = x.cpu().numpy()
+    nr = np.linalg.norm(b - orc.spmv(orc.assemble(dim, elem, N, k_cell=k), x))
+    return H, st, it, nr, x
 
 
 @pytest.mark.parametrize("dim,elem,N,L,sm", [(3, mg.MG_Q1, 96, 5, 1), (2, mg.MG_Q1, 256, 5, 0),
                                              (3, mg.MG_P1, 64, 4, 1)])
-def test_stencil_levels_solve_like_stored_ones(dim, elem, N, L, sm):
+def test_stencil_levels_solve_like_stored_ones(orc, dim, elem, N, L, sm):
     b = W.random_vector(mg.mg_ndofs(dim, elem, N), seed=97)
-    Hs, st, it, nr, xs = _solve(dim, elem, N, L, b, mg.MG_STORAGE_STENCIL, sm=sm)
-    Hd, st_d, it_d, nr_d, xd = _solve(dim, elem, N, L, b, mg.MG_STORAGE_DIA, sm=sm)
+    Hs, st, it, nr, xs = _solve(orc, dim, elem, N, L, b, mg.MG_STORAGE_STENCIL, sm=sm)
+    Hd, st_d, it_d, nr_d, xd = _solve(orc, dim, elem, N, L, b, mg.MG_STORAGE_DIA, sm=sm)
     info = Hs.info()
     for l in range(L):
         want = mg.MG_STORAGE_STENCIL if l >= 1 and info["n"][l] >= 32768 else mg.MG_STORAGE_DIA
@@ -51,15 +52,16 @@ def test_stencil_levels_solve_like_stored_ones(dim, elem, N, L, sm):
     assert np.linalg.norm(xs - xd) <= 1e-6 * np.linalg.norm(xd)  # both within cond(A) x 1e-10
 
 
-def test_stencil_export_is_the_host_operator_rounded():
-    """The exported FP32 stencil level has the host operator's structure; off-diagonal
+def test_stencil_export_is_the_host_operator_rounded(orc):
+    """The exported FP32 stencil level has the oracle's operator structure; off-diagonal
     values are the FP64 ones rounded to FP32, the diagonal the row-sum-preserving rounding
     of an interior row (equal on interior rows, within FP32 rounding on the others)."""
     dim, elem, N, L = 3, mg.MG_Q1, 64, 4
     H = mg.Hierarchy(dim, elem, N, L, precision=mg.MG_MIXED, storage=mg.MG_STORAGE_STENCIL)
     assert H.info()["storage"][L - 1] == mg.MG_STORAGE_STENCIL
     rp, col, val = mg.mg_export_operator(H.h, L - 1, 0, mg.MG_MIXED)
-    hp, hc, hv = mg.mg_assemble_operator(dim, elem, N, L, L - 1, 0)
+    Ao = orc.assemble(dim, elem, N)
+    hp, hc, hv = Ao.rowptr, Ao.col, Ao.val
     assert np.array_equal(rp, hp) and np.array_equal(col, hc)
     rows = np.repeat(np.arange(len(rp) - 1), np.diff(rp))
     off = col != rows
@@ -70,13 +72,13 @@ def test_stencil_export_is_the_host_operator_rounded():
     assert np.array_equal(rp64, hp) and np.array_equal(col64, hc) and np.array_equal(val64, hv)
 
 
-def test_stencil_needs_a_constant_stencil_and_falls_back_to_dia():
+def test_stencil_needs_a_constant_stencil_and_falls_back_to_dia(orc):
     """A per-cell coefficient makes the rows differ: every level keeps DIA. Requests the
     storage cannot serve are rejected."""
     dim, elem, N, L = 3, mg.MG_Q1, 64, 4
     k = W.k_blocks(N, dim=3, blocks_per_axis=8, seed=5)
-    b = mg.mg_load_vector(dim, elem, N, modes=None, f_const=1.0)
-    H, st, it, nr, x = _solve(dim, elem, N, L, b, mg.MG_STORAGE_STENCIL, k=k)
+    b = orc.load_vector(dim, elem, N)
+    H, st, it, nr, x = _solve(orc, dim, elem, N, L, b, mg.MG_STORAGE_STENCIL, k=k)
     assert H.info()["storage"] == [mg.MG_STORAGE_DIA] * L
     assert st == mg.MG_OK and nr <= 1e-10 * np.linalg.norm(b)
     for kw in (dict(precision=mg.MG_FP64), dict(precision=mg.MG_MIXED, smoother=mg.MG_GAUSS_SEIDEL)):

@@ -49,8 +49,8 @@ CASES = [
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
 def test_tet_fp64_bitwise(orc, case):
     _, elem, N, L, sm, nu = case
-    b = mg.mg_load_vector(3, elem, N, modes=W.manufactured_modes(3))
-    assert np.array_equal(b, orc.load_vector(3, elem, N, modes=W.manufactured_modes(3)))
+    b = orc.load_vector(3, elem, N, modes=W.manufactured_modes(3))
+    assert np.array_equal(b, mg.mg_load_vector(3, elem, N, modes=W.manufactured_modes(3)))
     H, O, g, o = _both(orc, elem, N, L, b, smoother=sm, nu=nu)
     assert g[0] == mg.MG_OK and o[0] and g[1] == o[1]
     assert np.array_equal(g[3], o[3])
@@ -72,7 +72,7 @@ def test_tet_every_storage_and_graph_mode(orc, elem, N, L, storage, graph):
 def test_tet_variable_coefficient_galerkin_levels(orc):
     N, L = 32, 4
     k = W.k_blocks(N, dim=3, blocks_per_axis=8, seed=20260101)
-    b = mg.mg_load_vector(3, mg.MG_P1, N, modes=None, f_const=1.0)
+    b = orc.load_vector(3, mg.MG_P1, N)
     H, O, g, o = _both(orc, mg.MG_P1, N, L, b, smoother=1, nu=1, k=k)
     assert H.info()["galerkin"] == [1, 0, 0, 0]
     assert g[1] == o[1] and np.array_equal(g[3], o[3])
@@ -80,7 +80,7 @@ def test_tet_variable_coefficient_galerkin_levels(orc):
 
 @pytest.mark.parametrize("elem,N,L", [(2, 32, 4), (3, 16, 4)])
 def test_tet_pcg(orc, elem, N, L):
-    b = mg.mg_load_vector(3, elem, N, modes=W.manufactured_modes(3))
+    b = orc.load_vector(3, elem, N, modes=W.manufactured_modes(3))
     H, O, g, o = _both(orc, elem, N, L, b, smoother=1, nu=1, method="pcg")
     assert g[0] == mg.MG_OK and abs(g[1] - o[1]) <= 1
     m = min(len(g[2]), len(o[2]))
@@ -90,7 +90,7 @@ def test_tet_pcg(orc, elem, N, L):
 
 @pytest.mark.parametrize("elem,N,L", [(2, 32, 4), (3, 16, 4)])
 def test_tet_mixed_precision(orc, elem, N, L):
-    b = mg.mg_load_vector(3, elem, N, modes=W.manufactured_modes(3))
+    b = orc.load_vector(3, elem, N, modes=W.manufactured_modes(3))
     H, O, g, o = _both(orc, elem, N, L, b, smoother=1, nu=1, precision=mg.MG_MIXED)
     assert g[0] == mg.MG_OK
     assert np.linalg.norm(b - orc.spmv(O.A(L - 1), g[3])) <= 1e-10 * np.linalg.norm(b)
@@ -110,7 +110,8 @@ def test_tet_heat_steps_bitwise(orc, sm, nu):
     u = torch.from_numpy(wl["u0"].copy()).cuda()
     st, its = H.heat(torch.from_numpy(bF).cuda(), wl["g"], u, 1e-10)
     O = orc.Hierarchy(3, mg.MG_P1, N, L, mass=sigma, opts=orc.Options(smoother=sm, nu_pre=nu, nu_post=nu))
-    uo, ito = orc.heat(O, orc.heat_B(3, mg.MG_P1, N, sigma), bF, wl["g"], wl["u0"], 1e-10)
+    bFo = orc.load_vector(3, orc.P1, N, modes=wl["source_modes"])
+    uo, ito = orc.heat(O, orc.heat_B(3, orc.P1, N, sigma), bFo, wl["g"], wl["u0"], 1e-10)
     assert st == mg.MG_OK and list(its) == list(ito) and np.array_equal(u.cpu().numpy(), uo)
 
 
@@ -118,7 +119,7 @@ def test_tet_heat_steps_bitwise(orc, sm, nu):
                                                  (3, 16, 4, 2, mg.MG_STORAGE_AUTO), (3, 8, 3, 1, mg.MG_STORAGE_ELL)])
 def test_tet_gauss_seidel_bitwise(orc, elem, N, L, nu, storage):
     """P1 (four colours) and P2 (fifteen colours) Gauss-Seidel, every storage of the copy."""
-    b = mg.mg_load_vector(3, elem, N, modes=W.manufactured_modes(3))
+    b = orc.load_vector(3, elem, N, modes=W.manufactured_modes(3))
     H, O, g, o = _both(orc, elem, N, L, b, smoother=mg.MG_GAUSS_SEIDEL, nu=nu, storage=storage)
     assert g[0] == mg.MG_OK and g[1] == o[1] and np.array_equal(g[3], o[3])
 
@@ -130,7 +131,7 @@ def test_tet_full_size_workloads(orc, name):
     level of the element's order."""
     c = W.TET_CONFIGS[name]
     elem, N, L = c["element"], c["n_cells"], c["n_levels"]
-    b = mg.mg_load_vector(3, elem, N, modes=W.manufactured_modes(3))
+    b = orc.load_vector(3, elem, N, modes=W.manufactured_modes(3))
     H = mg.Hierarchy(3, elem, N, L, smoother=c["smoother"], omega=c["omega"], nu_pre=c["nu_pre"], nu_post=c["nu_post"])
     bd = torch.from_numpy(b).cuda()
     x = torch.zeros_like(bd)

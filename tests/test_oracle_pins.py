@@ -491,6 +491,36 @@ def test_power_iteration_bounds(orc):
     assert H2.lam(2) == lam  # reproducible bit for bit
 
 
+def _power_lambda_numpy(A, steps, seed):
+    """lambda_hat of the stated reading, written out in numpy: start v = 1 + 0.2 (u - 1/2)
+    with u_i the i-th SplitMix64(seed) draw, v /= ||v||; then `steps` times w = D^-1 A v,
+    lambda = ||w||, v = w / lambda."""
+    n = A.shape[0]
+    dinv = 1.0 / A.diagonal()
+    v = 1.0 + 0.2 * (W.uniform01(seed, n) - 0.5)
+    v = v / np.linalg.norm(v)
+    lam = 0.0
+    for _ in range(steps):
+        w = dinv * (A @ v)
+        lam = np.linalg.norm(w)
+        v = w / lam
+    return lam
+
+
+@pytest.mark.parametrize("dim,N,L", [(2, 32, 3), (3, 16, 3)])
+def test_power_iteration_follows_the_stated_reading(orc, dim, N, L):
+    """The Chebyshev bound: 20 power steps on D^-1 A from the seeded start vector (seed
+    1609), on the Kronecker-form matrix of every smoothed level. A different step count,
+    seed, start vector or normalisation moves lambda_hat far beyond the rounding bound."""
+    H = orc.Hierarchy(dim, orc.Q1, N, L, opts=orc.Options(smoother=orc.CHEBYSHEV))
+    for l in range(1, L):
+        A = sp.csr_matrix(_kron_q1(dim, H.level_N(l)))
+        want = _power_lambda_numpy(A, 20, 1609)
+        assert abs(H.lam(l) - want) <= 1e-13 * want, (l, H.lam(l), want)
+        for other in (_power_lambda_numpy(A, 19, 1609), _power_lambda_numpy(A, 20, 1608)):
+            assert abs(H.lam(l) - other) > 1e-11 * want
+
+
 @pytest.mark.slow
 @pytest.mark.parametrize("dim,elem,Ns", [(2, 0, (16, 32, 64)), (3, 0, (8, 16, 32)),
                                          (3, 1, (4, 8, 16))])
