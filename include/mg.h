@@ -179,19 +179,23 @@ typedef struct {
 
 void mg_options_default(mg_options *o);
 
-/* Number of interior DOFs; -1 for an invalid combination. */
+/* Number of interior DOFs; -1 for an invalid combination. The DOF sets are those of the
+ * paper's elements on the uniformly refined grid (Sec. 5.1; P1/P2 counts of Sec. 6.4). */
 int64_t mg_ndofs(int dim, int element, int n_cells);
 
 /* Load vector b_i = integral of f phi_i over the finest grid, 3-point Gauss rule per
- * axis per cell (host computation). b_host: n DOFs, caller-owned. */
+ * axis per cell (host computation): the right-hand side of the sparse FE system A x = b
+ * of Sec. 2 ("FEM and iterative methods"). b_host: n DOFs, caller-owned. MG_EINVAL for
+ * an invalid problem. */
 mg_status mg_load_vector(const mg_problem *p, const mg_rhs *f, double *b_host);
 
-/* The same Q1 load vector with the tensor Gauss rule factorised per sine mode and axis
+/* (Sec. 2, as mg_load_vector.) The same Q1 load vector with the tensor Gauss rule factorised per sine mode and axis
  * (b = sum_m c_m X_m (x) Y_m [(x) Z_m]): O(modes * n) instead of O(modes * 3^d * n) sine
  * evaluations, equal to mg_load_vector up to rounding. Q1 only. */
 mg_status mg_load_vector_separable(const mg_problem *p, const mg_rhs *f, double *b_host);
 
-/* The hierarchy's level operators as assembled on the host, without a GPU: which = 0:
+/* The level operators of Sec. 5.1 (system matrix per level) and Sec. 5.4 (transfers), as
+ * assembled on the host, without a GPU: which = 0:
  * A_level, 1: P_level (rows: level, columns: level-1), 2: R_level = P_level^T, in CSR
  * with ascending columns and FP64 values (the same matrices mg_setup stores). Call with
  * rowptr = NULL to get *nrows and *nnz only; then rowptr holds nrows+1 entries and
@@ -202,20 +206,36 @@ mg_status mg_assemble_operator(const mg_problem *p, int level, int which, int64_
 /* Host only: *is_stencil = 1 if every row of the level-`level` matrix (as mg_setup
  * assembles it, mass shift included) is the same stencil: no entry outside the 3^d box
  * of the grid point, the interior row's FP64 values at every in-grid neighbour, zero
- * elsewhere; the condition for MG_STORAGE_STENCIL on an FP32 level. Q1 and P1 only (0
- * for the other elements and for grids of fewer than 4 cells per axis). */
+ * elsewhere. The paper stores every level matrix (Sec. 5.1); this is the per-level
+ * condition under which a stored FP32 level can be replaced by its stencil. It is
+ * necessary, not sufficient: mg_setup uses MG_STORAGE_STENCIL only on levels l >= 1 of
+ * at least 32768 rows of a mixed-precision hierarchy without Gauss-Seidel, requested
+ * by MG_STORAGE_STENCIL or chosen by the MG_STORAGE_AUTO timing, and keeps DIA
+ * elsewhere even where this check returns 1. Q1 and P1 only (0 for the other elements
+ * and for grids of fewer than 4 cells per axis). */
 mg_status mg_constant_stencil(const mg_problem *p, int level, int *is_stencil);
 
-/* Build the level hierarchy: per-level stiffness matrices (rediscretised; R A P of the
+/* Build the level hierarchy of Sec. 5.1 (uniform refinement of the coarsest grid, the
+ * system matrix assembled on every level) with the transfers of Sec. 5.4: per-level
+ * stiffness matrices (rediscretised; R A P of the
  * finer level where the coefficient is not resolved by the coarse cells), transfer
  * operators P (Q1 nodal interpolation, rotated-Q1 face averaging) and R = P^T, device
- * storage, the coarsest-level LU factorisation (FP64, on the device), smoother
- * parameters and the CUDA graphs of one iteration. dev may be NULL. */
+ * storage, the coarsest-level LU factorisation for the exact coarse solve of the V-cycle
+ * (Sec. 5.3; FP64, on the device), smoother parameters and the CUDA graphs of one
+ * iteration. p, o: host structs (read only, not kept); dev may be NULL (cudaMalloc);
+ * *out receives a hierarchy owned by the library until mg_hierarchy_free. MG_EINVAL for
+ * invalid sizes or options, MG_ENOMEM when dev->alloc fails, MG_ECUDA on a CUDA error;
+ * nothing is left allocated on failure. */
 mg_status mg_setup(const mg_problem *p, const mg_options *o, const mg_device *dev, mg_hierarchy **out);
+/* Release everything mg_setup allocated (through dev->free). NULL is MG_EINVAL. */
 mg_status mg_hierarchy_free(mg_hierarchy *h);
+/* Describe a built hierarchy (sizes, storage per level, Sec. 5.1 levels); info: host. */
 mg_status mg_get_info(const mg_hierarchy *h, mg_info *info);
 
-/* Defect correction with V-cycles until ||b - A x||_2 <= rel_tol * ||b||_2:
+/* The solve of the paper: the V-cycle of Sec. 5.3 (Algorithm "Parallel Multigrid Solver
+ * (V-Cycle)": pre-smoothing, restriction of the defect, exact coarsest solve,
+ * prolongation and correction, post-smoothing) applied in a defect-correction loop
+ * until ||b - A x||_2 <= rel_tol * ||b||_2 (the paper gives no stopping rule):
  *   r_k = b - A x_k (FP64), stop test, c = V(r_k), x_{k+1} = x_k + c.
  * b_dev, x_dev: device pointers to n doubles; x_dev holds the initial guess on entry
  * and the result on exit. iters (may be NULL): V-cycles performed. res_hist (host, may
@@ -225,8 +245,8 @@ mg_status mg_get_info(const mg_hierarchy *h, mg_info *info);
 mg_status mg_solve(mg_hierarchy *h, const double *b_dev, double *x_dev, double rel_tol, int *iters,
                    double *res_hist);
 
-/* mg_solve with host arrays: copies b to the device, solves, copies x back (x_host
- * also supplies the initial guess). */
+/* mg_solve (Sec. 5.3) with host arrays: copies b to the device, solves, copies x back
+ * (x_host also supplies the initial guess). Errors as mg_solve. */
 mg_status mg_solve_host(mg_hierarchy *h, const double *b_host, double *x_host, double rel_tol, int *iters,
                         double *res_hist);
 
@@ -244,7 +264,8 @@ mg_status mg_solve_host(mg_hierarchy *h, const double *b_host, double *x_host, d
 mg_status mg_pcg(mg_hierarchy *h, const double *b_dev, double *x_dev, double rel_tol, int *iters,
                  double *res_hist);
 
-/* mg_pcg with host arrays (x_host also supplies the initial guess). */
+/* mg_pcg (Sec. 1, Saad Alg. 9.1) with host arrays (x_host also supplies the initial
+ * guess). Errors as mg_pcg. */
 mg_status mg_pcg_host(mg_hierarchy *h, const double *b_host, double *x_host, double rel_tol, int *iters,
                       double *res_hist);
 
@@ -266,24 +287,28 @@ mg_status mg_pcg_host(mg_hierarchy *h, const double *b_host, double *x_host, dou
 mg_status mg_heat(mg_hierarchy *h, const double *bF_dev, const double *g_host, int n_steps, double *u_dev,
                   double rel_tol, int method, int *iters);
 
-/* mg_heat with host arrays bF_host, u_host (copied in, u copied back). */
+/* mg_heat (Sec. 6.2) with host arrays bF_host, u_host (copied in, u copied back). */
 mg_status mg_heat_host(mg_hierarchy *h, const double *bF_host, const double *g_host, int n_steps, double *u_host,
                        double rel_tol, int method, int *iters);
 
-/* Exactly n_cycles defect-correction iterations without a stop test (no host
- * synchronisation between them). rel_res (may be NULL): ||r|| / ||b|| of the last
- * residual computed, i.e. before the last correction. */
+/* Exactly n_cycles defect-correction iterations with the V-cycle of Sec. 5.3, without a
+ * stop test (no host synchronisation between them). b_dev, x_dev as mg_solve. rel_res
+ * (host, may be NULL): ||r|| / ||b|| of the last residual computed, i.e. before the last
+ * correction. MG_EINVAL for NULL vectors or n_cycles < 0. */
 mg_status mg_cycle(mg_hierarchy *h, const double *b_dev, double *x_dev, int n_cycles, double *rel_res);
 
-/* Copy a level operator to the host as CSR (FP64 values, structural pattern):
+/* The device copy of a level operator of Sec. 5.1 / 5.4, to the host as CSR (FP64
+ * values, structural pattern):
  * which = 0: A_level (precision MG_FP64 or MG_MIXED selects the stored copy),
  * 1: P_level (rows: level, columns: level-1), 2: R_level = P_level^T.
  * Call with rowptr = NULL to get *nnz only; otherwise rowptr holds nrows+1, col/val nnz. */
 mg_status mg_export_operator(const mg_hierarchy *h, int level, int which, int precision, int64_t *nrows,
                              int64_t *nnz, int64_t *rowptr, int32_t *col, double *val);
 
-/* Per-kernel timing with CUDA events recorded around every launch (kernel classes
- * below); off by default. mg_profile_read returns the accumulated device time and
+/* Measurement, not part of the method: the paper reports the solve's cost per step
+ * class (Sec. 5.5 "Computational complexity": every step O(N)); these time each kernel
+ * class per level. Per-kernel timing with CUDA events recorded around every launch
+ * (kernel classes below); off by default. mg_profile_read returns the accumulated device time and
  * launch count of one (class, level) since the last enable, and the algorithmic
  * bytes one such launch moves. */
 #define MG_K_SMOOTH 0   /* smoother sweep (fused residual + update) */
@@ -369,12 +394,21 @@ typedef struct {
 /* Defaults: 4 GiB budget, 256 slots, 4 rows per thread, 4 blocks per SM, Chebyshev
  * degree 2 with one application before and after the coarse correction. */
 void mg_serve_config_default(mg_serve_config *cfg);
+/* Serving has no counterpart in the paper: it runs the solve of mg_solve (Sec. 5.3) for
+ * many independent problems at once. cfg, dev: host structs (read only); *out is owned by
+ * the library until mg_serve_destroy. MG_EINVAL for invalid options (Gauss-Seidel is not
+ * served), MG_ENOMEM if the budget cannot be reserved, MG_ECUDA on a CUDA error. */
 mg_status mg_serve_create(const mg_serve_config *cfg, const mg_device *dev, mg_server **out);
-/* Submit A x = b with b copied from b_host (n doubles, host) before returning; the
- * ticket identifies the request. Relative tolerance on ||b - A x||_2 / ||b||_2. */
+/* Submit A x = b (the system of Sec. 2, solved as mg_solve does) with b copied from
+ * b_host (n doubles, host) before returning; the ticket identifies the request.
+ * Relative tolerance on ||b - A x||_2 / ||b||_2. The request takes the server's options
+ * (mg_serve_config.options): the phase launches of one iteration share one smoother.
+ * MG_EINVAL for an unsupported problem, a tolerance <= 0, or a right-hand side holding a
+ * NaN or an infinity. */
 mg_status mg_serve_submit(mg_server *s, const mg_problem *p, const double *b_host, double rel_tol, uint64_t *ticket);
-/* Submit with the right-hand side given by f; the load vector is assembled on the
- * server's setup thread. */
+/* Submit with the right-hand side given by f (as mg_load_vector_separable); the load
+ * vector is assembled on the server's setup thread. MG_EINVAL as mg_serve_submit, also
+ * for a non-finite amplitude or f_const. */
 mg_status mg_serve_submit_rhs(mg_server *s, const mg_problem *p, const mg_rhs *f, double rel_tol, uint64_t *ticket);
 /* MG_PENDING while the request runs; otherwise its final status (MG_OK, MG_ENOCONV,
  * MG_EBUDGET, ...), with x copied to x_host (n doubles, may be NULL) and the V-cycle

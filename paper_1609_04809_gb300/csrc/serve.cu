@@ -1249,10 +1249,21 @@ static mg_status submit_common(mg_server *S, const mg_problem *p, const double *
     r->tol = tol;
     int64_t n = mgh::ndofs(p->dim, MG_Q1, p->n_cells);
     if (b_host) {
+        for (int64_t i = 0; i < n; i++)
+            if (!std::isfinite(b_host[i])) {
+                mgi::set_error("the right-hand side holds a NaN or an infinity");
+                return MG_EINVAL;
+            }
         r->b.assign(b_host, b_host + n);
     } else {
         if (!f || f->n_modes < 0 || (f->n_modes > 0 && (!f->amp || !f->freq))) {
             mgi::set_error("bad right-hand side");
+            return MG_EINVAL;
+        }
+        bool finite = std::isfinite(f->f_const);
+        for (int m = 0; m < f->n_modes; m++) finite = finite && std::isfinite(f->amp[m]);
+        if (!finite) {
+            mgi::set_error("the right-hand side holds a NaN or an infinity");
             return MG_EINVAL;
         }
         r->has_rhs = true;

@@ -1901,20 +1901,35 @@ static void join_out(mg_hierarchy *h)
     CK(cudaStreamSynchronize(h->s));
 }
 
+// A right-hand side or initial guess holding a NaN or an infinity is rejected before the
+// first cycle; a residual that stops being finite ends the iteration at once.
+static void check_finite_start(double nb, double nr)
+{
+    if (!std::isfinite(nb)) throw Error(MG_EINVAL, "the right-hand side holds a NaN or an infinity");
+    if (!std::isfinite(nr)) throw Error(MG_EINVAL, "the initial guess holds a NaN or an infinity");
+}
+
 static mg_status solve_internal(mg_hierarchy *h, double tol, int *iters, double *hist)
 {
     ensure_graphs(h);
     double nb = norm_b(h);
+    if (!std::isfinite(nb)) check_finite_start(nb, 0.0);
     int k = 0;
     mg_status st = MG_ENOCONV;
     run_r(h);
     double nr = std::sqrt(read_norm2(h));
     prof_collect(h, true, false);
+    check_finite_start(nb, nr);
+    bool diverged = false;
     for (;;) {
         double rel = nb > 0.0 ? nr / nb : nr;
         if (hist) hist[k] = rel;
-        if (rel <= tol) {  // a NaN residual runs on to max_iters
+        if (rel <= tol) {
             st = MG_OK;
+            break;
+        }
+        if (!std::isfinite(rel)) {
+            diverged = true;
             break;
         }
         if (k == h->opt.max_iters) break;
@@ -1925,7 +1940,7 @@ static mg_status solve_internal(mg_hierarchy *h, double tol, int *iters, double 
         k++;
     }
     if (iters) *iters = k;
-    if (st == MG_ENOCONV) g_err = "max_iters reached before the tolerance";
+    if (st == MG_ENOCONV) g_err = diverged ? "the residual is no longer finite" : "max_iters reached before the tolerance";
     return st;
 }
 
@@ -1937,16 +1952,23 @@ static mg_status pcg_internal(mg_hierarchy *h, double tol, int *iters, double *h
         throw Error(MG_EINVAL, "conjugate gradients need a symmetric V-cycle (nu_pre == nu_post)");
     ensure_pcg_graphs(h);
     double nb = norm_b(h);
+    if (!std::isfinite(nb)) check_finite_start(nb, 0.0);
     int k = 0;
     mg_status st = MG_ENOCONV;
     run_graph_or_eager(h, h->g_pi, enqueue_pi);
     double nr = std::sqrt(read_norm2(h));
     prof_collect_pcg(h, true, false);
+    check_finite_start(nb, nr);
+    bool diverged = false;
     for (;;) {
         double rel = nb > 0.0 ? nr / nb : nr;
         if (hist) hist[k] = rel;
         if (rel <= tol) {
             st = MG_OK;
+            break;
+        }
+        if (!std::isfinite(rel)) {
+            diverged = true;
             break;
         }
         if (k == h->opt.max_iters) break;
@@ -1956,7 +1978,7 @@ static mg_status pcg_internal(mg_hierarchy *h, double tol, int *iters, double *h
         k++;
     }
     if (iters) *iters = k;
-    if (st == MG_ENOCONV) g_err = "max_iters reached before the tolerance";
+    if (st == MG_ENOCONV) g_err = diverged ? "the residual is no longer finite" : "max_iters reached before the tolerance";
     return st;
 }
 
