@@ -116,7 +116,7 @@ class ClockSampler:
 
 
 SWEEP_KERNELS = {"dia": "k_dia_sweep", "ell": "k_ell_sweep", "csr": "k_csr_sweep", "sell": "k_sell_sweep",
-                 "stencil": "k_stencil_sweep"}
+                 "stencil": "k_stencil_sweep", "coef": "k_coef_sweep"}
 
 
 def _kernel_sha(storage, src=None):
@@ -184,7 +184,7 @@ def replica_throughput(ms_local, n_dofs, steps, world, dist=None, device="cpu"):
 
 
 SMOOTHERS = {"jacobi": 0, "chebyshev": 1, "gauss-seidel": 2}
-STORAGES = {"auto": 0, "csr": 1, "ell": 2, "dia": 3, "sell": 4, "stencil": 5}
+STORAGES = {"auto": 0, "csr": 1, "ell": 2, "dia": 3, "sell": 4, "stencil": 5, "coef": 6}
 STORAGE_NAMES = {v: k for k, v in STORAGES.items()}
 SWEEP_TEXT = {0: "fused residual + damped Jacobi update", 1: "fused residual + Chebyshev update",
               2: "one colour of a multicolour Gauss-Seidel sweep, in place"}

@@ -84,13 +84,26 @@ typedef int mg_status;
 #define MG_STORAGE_DIA 3  /* column-major ELLPACK whose columns are row + fixed offsets (Q1, P1) */
 #define MG_STORAGE_SELL 4 /* sliced ELLPACK: rows sorted by length, slices of 32 rows stored
                              column-major with their own width, 32-bit columns */
-#define MG_STORAGE_STENCIL 5 /* constant stencil (Q1, P1; FP32 levels of a mixed hierarchy):
-                                one value per stencil position, used where every row of the
+#define MG_STORAGE_STENCIL 5 /* constant stencil (Q1, P1, rotated Q1; FP32 levels of a mixed
+                                hierarchy): one value per stencil position (rotated Q1: the
+                                three values of a face's row: itself, the opposite faces of its
+                                two cells, their other faces), used where every row of the
                                 level matrix is the same stencil (constant coefficient,
                                 rediscretised), boundary neighbours masked from the grid
                                 coordinates; no matrix is stored or streamed. Checked exactly
                                 on the host; levels that fail the check, Galerkin levels and
-                                levels of at most 32768 rows keep DIA. Not with Gauss-Seidel. */
+                                levels of at most 32768 rows keep DIA (rotated Q1: ELL). Not
+                                with Gauss-Seidel. */
+#define MG_STORAGE_COEF 6 /* per-cell coefficient (3D Q1; FP32 levels of a mixed hierarchy):
+                             where the level matrix is the rediscretisation of a per-cell
+                             coefficient k_e (every level above the Galerkin ones, no mass
+                             shift), one FP32 value k_e h / 12 per cell is stored and the
+                             sweep forms each row from the 8 cells around its vertex and the
+                             Q1 element stiffness; 4 bytes per cell instead of 21 values per
+                             row. Checked on the host against the assembled FP64 matrix
+                             (every entry within 1e-12 of the row's diagonal); levels that
+                             fail the check and levels of at most 32768 rows keep DIA. Not
+                             with Gauss-Seidel. */
 /* grid transfers P (prolongation, Sec. 5.1) and R = P^T of a level (mg_info.transfer) */
 #define MG_TRANSFER_NONE 0 /* level 0 (no coarser level) */
 #define MG_TRANSFER_GRID 1 /* Q1: weights computed from the grid in the kernel */

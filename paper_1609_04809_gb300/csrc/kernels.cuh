@@ -80,19 +80,35 @@ __global__ void __launch_bounds__(128) k_prolong_q1(const T *__restrict__ xc, T 
     const bool lo = m >= 1, hi = m + 1 <= nc1;  // coarse X = m and X = m + 1 are interior
     int y0 = max(v1 >> 1, 1), y1 = min((v1 + 1) >> 1, Nc - 1);
     int z0 = DIM == 3 ? max(v2 >> 1, 1) : 1, z1 = DIM == 3 ? min((v2 + 1) >> 1, Nc - 1) : 1;
-    T te = T(0), to = T(0);
-    for (int Z = z0; Z <= z1; Z++)
-        for (int Y = y0; Y <= y1; Y++) {
+    // every load first (the fine pair, then up to 2 x 2 coarse rows), then the sums in the
+    // order Z ascending, Y ascending: the same terms in the same order as a loop over them
+    const T f0 = m >= 1 ? xf[line + 2 * m - 1] : T(0), f1 = xf[line + 2 * m];
+    T cm[2][2], cp[2][2];
+    bool on[2][2];
+#pragma unroll
+    for (int zz = 0; zz < 2; zz++)
+#pragma unroll
+        for (int yy = 0; yy < 2; yy++) {
+            const int Z = z0 + zz, Y = y0 + yy;
+            on[zz][yy] = Y <= y1 && Z <= z1 && (DIM == 3 || zz == 0);
             int64_t row = (int64_t)nc1 * ((Y - 1) + (DIM == 3 ? (int64_t)nc1 * (Z - 1) : 0)) - 1;
-            T cm = lo ? __ldg(xc + row + m) : T(0), cp = hi ? __ldg(xc + row + m + 1) : T(0);
-            if (lo) {
-                te = Ar<T>::mac(te, we, cm);
-                to = Ar<T>::mac(to, wo, cm);
-            }
-            if (hi) to = Ar<T>::mac(to, wo, cp);
+            cm[zz][yy] = on[zz][yy] && lo ? __ldg(xc + row + m) : T(0);
+            cp[zz][yy] = on[zz][yy] && hi ? __ldg(xc + row + m + 1) : T(0);
         }
-    if (m >= 1) xf[line + 2 * m - 1] = Ar<T>::add(xf[line + 2 * m - 1], te);  // v0 = 2m
-    xf[line + 2 * m] = Ar<T>::add(xf[line + 2 * m], to);                      // v0 = 2m + 1
+    T te = T(0), to = T(0);
+#pragma unroll
+    for (int zz = 0; zz < 2; zz++)
+#pragma unroll
+        for (int yy = 0; yy < 2; yy++) {
+            if (!on[zz][yy]) continue;
+            if (lo) {
+                te = Ar<T>::mac(te, we, cm[zz][yy]);
+                to = Ar<T>::mac(to, wo, cm[zz][yy]);
+            }
+            if (hi) to = Ar<T>::mac(to, wo, cp[zz][yy]);
+        }
+    if (m >= 1) xf[line + 2 * m - 1] = Ar<T>::add(f0, te);  // v0 = 2m
+    xf[line + 2 * m] = Ar<T>::add(f1, to);                  // v0 = 2m + 1
 }
 
 // Explicit transfer (rotated Q1, P1, P2) with the operator in SELL-32 (see k_sell_sweep):

@@ -51,6 +51,7 @@ struct DevMat {
     double sval[27] = {};
     double sdinv = 0.0;
     int n1 = 0, dim = 3;
+    int elem = MG_Q1;  // STENCIL: MG_RQ1 for the face stencil (sval[0..2]: diagonal, opposite, other)
 };
 
 struct LevelD {

@@ -286,6 +286,7 @@ static double mat_bytes(const DevMat &m, int sv)
     switch (m.fmt) {
     case MG_STORAGE_DIA: return (double)m.K * (double)m.n * sv;
     case MG_STORAGE_STENCIL: return 0.0;  // the values are launch parameters
+    case MG_STORAGE_COEF: return 4.0 * (double)(m.n1 + 1) * (m.n1 + 1) * (m.n1 + 1);  // one FP32 value per cell
     case MG_STORAGE_ELL: return (double)m.K * (double)m.n * (sv + 4);
     case MG_STORAGE_SELL: return (double)m.padded * (sv + 4) + 8.0 * (double)(m.nslices + 1) + 4.0 * (double)m.n;
     default: return (double)m.nnz * (sv + 4) + 8.0 * (double)(m.n + 1);
@@ -336,6 +337,33 @@ template <typename T, int MODE>
 static void sweep_fmt(const DevMat &A, int n, const T *x, const T *b, T *out, T *d, T c1, T c2, cudaStream_t s,
                       bool pdl = false)
 {
+    if (A.fmt == MG_STORAGE_COEF) {
+        if constexpr (std::is_same<T, float>::value) {
+            // planes per thread: up to 16, fewer where the columns alone would not give about
+            // two waves of 2048 threads on each of the 152 SMs
+            int n1 = A.n1;
+            int zc = (int)std::max<int64_t>(1, std::min<int64_t>(16, (int64_t)n1 * n1 * n1 / (2 * 2048 * 152)));
+            CoefView S{(const float *)A.val, n1, zc};
+            unsigned bx = line_block((unsigned)n1), by = std::min(256u / bx, (unsigned)n1);
+            dim3 g((unsigned)((n1 + bx - 1) / bx), (unsigned)((n1 + by - 1) / by), (unsigned)((n1 + zc - 1) / zc)),
+                blk(bx, by);
+            klaunch(pdl, k_coef_sweep<MODE>, g, blk, 0, s, S, x, b, out, d, c1, c2);
+            return;
+        } else {
+            throw Error(MG_EINVAL, "coefficient storage holds FP32 levels only");
+        }
+    }
+    if (A.fmt == MG_STORAGE_STENCIL && A.elem == MG_RQ1) {
+        if constexpr (std::is_same<T, float>::value) {
+            Rq1View S{A.n1 + 1, (float)A.sval[1], (float)A.sdinv};
+            unsigned N = (unsigned)(A.n1 + 1), bx = line_block(N), by = std::min(256u / bx, N);
+            dim3 g((N + bx - 1) / bx, (N + by - 1) / by, 3 * N), blk(bx, by);
+            klaunch(pdl, k_stencil_rq1<MODE>, g, blk, 0, s, S, x, b, out, d, c1, c2);
+            return;
+        } else {
+            throw Error(MG_EINVAL, "the face stencil holds FP32 levels only");
+        }
+    }
     if (A.fmt == MG_STORAGE_STENCIL) {
         StencilView<T> S{};
         for (int k = 0; k < A.K; k++) {
@@ -1145,9 +1173,166 @@ static bool constant_stencil(const mgh::Csr &A, int dim, int N, int sv, double b
     return true;
 }
 
+// The in-grid neighbours of rotated-Q1 face r on N cells per axis (the same enumeration
+// as k_stencil_rq1): col[], role[] (0 the face itself, 1 a face opposite it in one of its
+// two cells, 2 one of the other faces of those cells). Returns the count.
+static int rq1_neighbours(int N, int64_t r, int64_t *col, int *role)
+{
+    const int64_t M = N - 1, ny0 = M * N * N, nz0 = 2 * M * N * N;
+    int f = r < ny0 ? 0 : (r < nz0 ? 1 : 2);
+    int64_t loc = r - (f == 0 ? 0 : (f == 1 ? ny0 : nz0));
+    int p, q, c;  // the kernel's thread coordinates (fast, line, slab) of the face
+    if (f == 0) {
+        p = (int)(loc % M);
+        q = (int)((loc / M) % N);
+        c = (int)(loc / (M * N));
+    } else if (f == 1) {
+        p = (int)(loc % N);
+        q = (int)((loc / N) % M);
+        c = (int)(loc / (N * M));
+    } else {
+        p = (int)(loc % N);
+        q = (int)((loc / N) % N);
+        c = (int)(loc / ((int64_t)N * N));
+    }
+    int cnt = 0;
+    auto add = [&](bool in, int64_t j, int ro) {
+        if (!in) return;
+        col[cnt] = j;
+        role[cnt] = ro;
+        cnt++;
+    };
+    add(true, r, 0);
+    int t0 = f == 0 ? p : (f == 1 ? q : c);  // position along the normal minus 1
+    int64_t step = f == 0 ? 1 : (f == 1 ? N : (int64_t)N * N);
+    add(t0 >= 1, r - step, 1);
+    add(t0 + 1 <= M - 1, r + step, 1);
+    for (int s2 = 0; s2 < 2; s2++)
+        for (int t = 0; t < 2; t++) {
+            if (f == 0) {
+                int cx = p + s2, jy = q + t, kz = c + t;
+                add(jy >= 1 && jy <= M, ny0 + cx + N * ((jy - 1) + M * c), 2);
+                add(kz >= 1 && kz <= M, nz0 + cx + N * (q + (int64_t)N * (kz - 1)), 2);
+            } else if (f == 1) {
+                int cy = q + s2, ix = p + t, kz = c + t;
+                add(ix >= 1 && ix <= M, (ix - 1) + M * (cy + (int64_t)N * c), 2);
+                add(kz >= 1 && kz <= M, nz0 + p + N * (cy + (int64_t)N * (kz - 1)), 2);
+            } else {
+                int cz = c + s2, ix = p + t, jy = q + t;
+                add(ix >= 1 && ix <= M, (ix - 1) + M * (q + (int64_t)N * cz), 2);
+                add(jy >= 1 && jy <= M, ny0 + p + N * ((jy - 1) + M * cz), 2);
+            }
+        }
+    return cnt;
+}
+
+// Constant face stencil of a rotated-Q1 level (MG_STORAGE_STENCIL): true if every row of
+// A holds exactly its in-grid neighbours of rq1_neighbours, with one FP64 value per role
+// taken from an interior row: the diagonal 6 v, the opposite faces v, the other faces -v
+// (each within 1e-13 of the diagonal, the values of a constant coefficient). vals
+// receives (diagonal, opposite, other).
+static bool rq1_constant_stencil(const mgh::Csr &A, int N, double vals[3])
+{
+    if (N < 4 || A.nrows != mgh::ndofs(3, MG_RQ1, N)) return false;
+    const int64_t M = N - 1;
+    const int64_t r0 = 1 + M * (1 + (int64_t)N * 1);  // x-face at position 2 over cell (1, 1)
+    double ref[3] = {0.0, 0.0, 0.0};
+    {
+        int64_t col[11];
+        int role[11];
+        int cnt = rq1_neighbours(N, r0, col, role);
+        if (cnt != 11 || A.rowptr[r0 + 1] - A.rowptr[r0] != 11) return false;
+        for (int64_t q = A.rowptr[r0]; q < A.rowptr[r0 + 1]; q++)
+            for (int k = 0; k < cnt; k++)
+                if (col[k] == A.col[q]) ref[role[k]] = A.val[q];
+    }
+    const double tol = 1e-13 * std::fabs(ref[0]);
+    if (!(ref[0] > 0.0) || std::fabs(ref[0] - 6.0 * ref[1]) > tol || std::fabs(ref[2] + ref[1]) > tol) return false;
+    int64_t bad = 0;
+#pragma omp parallel for schedule(static) reduction(+ : bad)
+    for (int64_t r = 0; r < A.nrows; r++) {
+        int64_t col[11];
+        int role[11];
+        int cnt = rq1_neighbours(N, r, col, role);
+        bool ok = A.rowptr[r + 1] - A.rowptr[r] == cnt;
+        for (int64_t q = A.rowptr[r]; q < A.rowptr[r + 1] && ok; q++) {
+            bool hit = false;
+            for (int k = 0; k < cnt && !hit; k++)
+                if (col[k] == A.col[q]) hit = A.val[q] == ref[role[k]];
+            ok = hit;
+        }
+        if (!ok) bad++;
+    }
+    if (bad) return false;
+    for (int k = 0; k < 3; k++) vals[k] = ref[k];
+    return true;
+}
+
+// Per-cell coefficient form of a 3D Q1 level (MG_STORAGE_COEF): true if every row of A is
+// the rediscretisation of the per-cell coefficient k of this level's N^3 cells (x fastest)
+// with the unit-cube Q1 stiffness: a_ii = (h/3) sum of the 8 k_e around vertex i, a_ij =
+// -(h/12) sum of k_e over the cells holding both corners for a corner across a face (2
+// cells) or the body (1 cell), 0 across an edge; every entry within 1e-12 of the row's
+// diagonal, every in-grid corner across a face or the body present. kap receives the
+// stored values k_e h / 12 in FP32.
+static bool coef_form(const mgh::Csr &A, int N, const std::vector<double> &k, std::vector<float> &kap)
+{
+    if (N < 4 || (int64_t)k.size() != (int64_t)N * N * N) return false;
+    const double h = 1.0 / N;
+    const int64_t nc = N;
+    int64_t bad = 0;
+#pragma omp parallel for schedule(static) reduction(+ : bad)
+    for (int64_t i = 0; i < A.nrows; i++) {
+        int vi[3], vj[3];
+        mgh::q1_coords(3, N, i, vi);
+        // k of the cell on side (a, b, c) of the vertex: cell (X - 1 + a, Y - 1 + b, Z - 1 + c)
+        auto kc = [&](int a, int b, int c) { return k[(size_t)((vi[0] - 1 + a) + nc * ((vi[1] - 1 + b) + nc * (vi[2] - 1 + c)))]; };
+        double ks = 0.0;
+        for (int e = 0; e < 8; e++) ks += kc(e & 1, (e >> 1) & 1, e >> 2);
+        const double diag = ks * h / 3.0, tol = 1e-12 * std::fabs(diag);
+        int found = 0, want = 1;
+        for (int p = 0; p < 27; p++) {  // the in-grid corners across a face or the body
+            int d[3] = {p % 3 - 1, (p / 3) % 3 - 1, p / 9 - 1};
+            int nz = (d[0] != 0) + (d[1] != 0) + (d[2] != 0);
+            bool in = true;
+            for (int a = 0; a < 3; a++) in = in && vi[a] + d[a] >= 1 && vi[a] + d[a] <= N - 1;
+            if (in && nz >= 2) want++;
+        }
+        bool ok = true;
+        for (int64_t q = A.rowptr[i]; q < A.rowptr[i + 1] && ok; q++) {
+            mgh::q1_coords(3, N, A.col[q], vj);
+            int d[3] = {vj[0] - vi[0], vj[1] - vi[1], vj[2] - vi[2]};
+            for (int a = 0; a < 3; a++) ok = ok && d[a] >= -1 && d[a] <= 1;
+            if (!ok) break;
+            int nz = (d[0] != 0) + (d[1] != 0) + (d[2] != 0);
+            double expect = 0.0;
+            if (nz == 0) {
+                expect = diag;
+            } else if (nz >= 2) {
+                double sk = 0.0;
+                for (int e = 0; e < 8; e++) {
+                    int side[3] = {e & 1, (e >> 1) & 1, e >> 2};
+                    bool both = true;
+                    for (int a = 0; a < 3; a++)
+                        if (d[a] != 0 && side[a] != (d[a] > 0 ? 1 : 0)) both = false;
+                    if (both) sk += kc(side[0], side[1], side[2]);
+                }
+                expect = -sk * h / 12.0;
+            }
+            ok = std::fabs(A.val[q] - expect) <= tol;
+            if (ok && nz != 1) found++;
+        }
+        if (!ok || found != want) bad++;
+    }
+    if (bad) return false;
+    kap.resize(k.size());
+    for (size_t e = 0; e < k.size(); e++) kap[e] = (float)(k[e] * h / 12.0);
+    return true;
+}
+
 // stencil_vals: STENCIL only, the values by stencil position (constant_stencil)
 static void plan_matrix(DevMat &m, const mgh::Csr &A, int fmt, int dim, int N, int sv, mgi::Slab &slab, bool take,
-                        const double *stencil_vals = nullptr)
+                        const double *stencil_vals = nullptr, int elem = MG_Q1)
 {
     m.fmt = fmt;
     m.n = A.nrows;
@@ -1156,6 +1341,36 @@ static void plan_matrix(DevMat &m, const mgh::Csr &A, int fmt, int dim, int N, i
     m.elem_size = sv;
     m.n1 = N - 1;
     m.dim = dim;
+    m.elem = elem;
+    if (fmt == MG_STORAGE_STENCIL && elem == MG_RQ1) {  // face stencil: three values, nothing stored
+        if (!stencil_vals) throw Error(MG_EINVAL, "stencil storage without stencil values");
+        m.K = 11;
+        for (int q = 0; q < 3; q++) m.sval[q] = stencil_vals[q];
+        // the FP32 sweep forms hv * (6 x_i - ...): a_ii = 6 hv in FP32
+        float hv = (float)m.sval[1];
+        m.sdinv = sv == 8 ? 1.0 / m.sval[0] : (double)(1.0f / (6.0f * hv));
+        return;
+    }
+    if (fmt == MG_STORAGE_COEF) {  // 3D Q1: the 21 positions of the stencil, one value per cell
+        if (dim != 3) throw Error(MG_EINVAL, "coefficient storage is 3D Q1 only");
+        int64_t n1 = N - 1;
+        int k = 0;
+        for (int p = 0; p < 27; p++) {
+            int dx = p % 3 - 1, dy = (p / 3) % 3 - 1, dz = p / 9 - 1;
+            if ((dx != 0) + (dy != 0) + (dz != 0) == 1) continue;  // edge-adjacent: coupling 0
+            m.offs.o[k] = (int32_t)(dx + n1 * dy + n1 * n1 * dz);
+            m.full_of[k] = p;
+            if (p == 13) m.center = k;
+            k++;
+        }
+        m.K = k;
+        size_t bytes = (size_t)N * N * N * 4;
+        if (take)
+            m.val = slab.take(bytes);
+        else
+            slab.reserve(bytes);
+        return;
+    }
     if (fmt == MG_STORAGE_DIA || fmt == MG_STORAGE_STENCIL) {
         // keep the stencil positions that hold a nonzero anywhere (ascending offset),
         // padded with unused positions up to an instantiated slot count (9, 21 or 27).
@@ -1261,7 +1476,7 @@ template <typename T>
 static void upload_matrix(const DevMat &m, const mgh::Csr &A, const std::vector<T> &vals, int dim, int N,
                           cudaStream_t s)
 {
-    if (m.fmt == MG_STORAGE_STENCIL) return;  // nothing stored
+    if (m.fmt == MG_STORAGE_STENCIL || m.fmt == MG_STORAGE_COEF) return;  // no matrix values stored
     if (m.fmt == MG_STORAGE_DIA) {
         std::vector<T> v((size_t)m.K * m.ld, T(0));
         int k3 = dim == 3 ? 9 : 0;
@@ -1422,9 +1637,12 @@ static int pick_storage(const mg_options &o, int elem)
     if (o.storage == MG_STORAGE_DIA && !vertex_grid)
         throw Error(MG_EINVAL, "DIA storage needs Q1 or P1 (fixed stencil offsets)");
     if (o.storage == MG_STORAGE_STENCIL &&
-        (!vertex_grid || o.precision != MG_MIXED || o.smoother == MG_GAUSS_SEIDEL))
-        throw Error(MG_EINVAL, "stencil storage needs Q1 or P1, mixed precision and no Gauss-Seidel");
-    if (o.storage != MG_STORAGE_AUTO) return o.storage;
+        ((!vertex_grid && elem != MG_RQ1) || o.precision != MG_MIXED || o.smoother == MG_GAUSS_SEIDEL))
+        throw Error(MG_EINVAL, "stencil storage needs Q1, P1 or rotated Q1, mixed precision and no Gauss-Seidel");
+    if (o.storage == MG_STORAGE_COEF && (elem != MG_Q1 || o.precision != MG_MIXED || o.smoother == MG_GAUSS_SEIDEL))
+        throw Error(MG_EINVAL, "coefficient storage needs 3D Q1, mixed precision and no Gauss-Seidel");
+    if (o.storage != MG_STORAGE_AUTO) return o.storage == MG_STORAGE_STENCIL && elem == MG_RQ1 ? MG_STORAGE_STENCIL
+                                                                                             : o.storage;
     return vertex_grid ? MG_STORAGE_DIA : MG_STORAGE_ELL;
 }
 
@@ -1432,13 +1650,14 @@ static int pick_storage(const mg_options &o, int elem)
 // in temporary device memory and timed on residual sweeps; the fastest wins. Choices are
 // cached per (dim, element, cells, value size) for the life of the process.
 template <typename T>
-static double time_format(mg_hierarchy *h, const mgh::Csr &A, int fmt, int dim, int N, const double *svals)
+static double time_format(mg_hierarchy *h, const mgh::Csr &A, int fmt, int dim, int N, const double *svals,
+                          const std::vector<float> *kap)
 {
     mgi::Slab S;
     DevMat m;
-    plan_matrix(m, A, fmt, dim, N, sizeof(T), S, false, svals);
+    plan_matrix(m, A, fmt, dim, N, sizeof(T), S, false, svals, h->elem);
     int64_t n1 = N - 1;
-    int64_t pad = fmt == MG_STORAGE_DIA || fmt == MG_STORAGE_STENCIL
+    int64_t pad = (fmt == MG_STORAGE_DIA || fmt == MG_STORAGE_STENCIL || fmt == MG_STORAGE_COEF) && h->elem != MG_RQ1
                       ? round_up(dim == 3 ? n1 * n1 + n1 + 1 : n1 + 1, 64)
                       : 0;
     int64_t ld = round_up(std::max<int64_t>(A.nrows, 1), 64);
@@ -1455,13 +1674,17 @@ static double time_format(mg_hierarchy *h, const mgh::Csr &A, int fmt, int dim, 
     if (!S.base) return 1e300;  // no room to try it: never chosen
     double ms_best = 1e300;
     try {
-        plan_matrix(m, A, fmt, dim, N, sizeof(T), S, true, svals);
+        plan_matrix(m, A, fmt, dim, N, sizeof(T), S, true, svals, h->elem);
         char *xb = (char *)S.take((size_t)(ld + 2 * pad) * sizeof(T));
         T *x = (T *)(xb + pad * sizeof(T));
         T *b = (T *)S.take((size_t)ld * sizeof(T)), *r = (T *)S.take((size_t)ld * sizeof(T));
         CK(cudaMemsetAsync(S.base, 0, S.size, h->s));
         std::vector<T> vals(A.val.begin(), A.val.end());
         upload_matrix<T>(m, A, vals, dim, N, h->s);
+        if (fmt == MG_STORAGE_COEF) {
+            if (!kap) throw Error(MG_EINVAL, "coefficient storage without coefficients");
+            CK(cudaMemcpyAsync(m.val, kap->data(), kap->size() * 4, cudaMemcpyHostToDevice, h->s));
+        }
         cudaEvent_t e0, e1;
         CK(cudaEventCreate(&e0));
         CK(cudaEventCreate(&e1));
@@ -1490,11 +1713,13 @@ static double time_format(mg_hierarchy *h, const mgh::Csr &A, int fmt, int dim, 
 }
 
 // svals: the level's constant stencil (constant_stencil) when it may be stored as one
-static int tune_storage(mg_hierarchy *h, const mgh::Csr &A, int dim, int elem, int N, const double *svals)
+// kap: the level's per-cell coefficients (coef_form) when it may be stored in that form
+static int tune_storage(mg_hierarchy *h, const mgh::Csr &A, int dim, int elem, int N, const double *svals,
+                        const std::vector<float> *kap)
 {
     static std::mutex mu;
-    static std::map<std::tuple<int, int, int, int, bool, bool>, int> cache;
-    auto key = std::make_tuple(dim, elem, N, h->inner_size, h->mass != 0.0, svals != nullptr);
+    static std::map<std::tuple<int, int, int, int, bool, bool, bool>, int> cache;
+    auto key = std::make_tuple(dim, elem, N, h->inner_size, h->mass != 0.0, svals != nullptr, kap != nullptr);
     {
         std::lock_guard<std::mutex> lk(mu);
         auto it = cache.find(key);
@@ -1506,10 +1731,12 @@ static int tune_storage(mg_hierarchy *h, const mgh::Csr &A, int dim, int elem, i
     cands.push_back(MG_STORAGE_CSR);
     if (elem == MG_RQ1 || elem == MG_P2) cands.push_back(MG_STORAGE_SELL);  // uneven rows (P2) or no DIA
     if (svals) cands.push_back(MG_STORAGE_STENCIL);
+    if (kap && h->mixed) cands.push_back(MG_STORAGE_COEF);
     int best = cands[0];
     double best_ms = 1e300;
     for (int f : cands) {
-        double ms = h->mixed ? time_format<float>(h, A, f, dim, N, svals) : time_format<double>(h, A, f, dim, N, svals);
+        double ms = h->mixed ? time_format<float>(h, A, f, dim, N, svals, kap)
+                             : time_format<double>(h, A, f, dim, N, svals, kap);
         if (ms < best_ms) {
             best_ms = ms;
             best = f;
@@ -1531,7 +1758,9 @@ void mgi::build_hierarchy(mg_hierarchy *h, const mg_problem *p, const mg_options
         throw Error(MG_EINVAL, "bad Chebyshev parameters");
     if (o->nu_pre < 0 || o->nu_post < 0 || o->max_iters < 0) throw Error(MG_EINVAL, "negative counts");
     if (o->precision != MG_FP64 && o->precision != MG_MIXED) throw Error(MG_EINVAL, "bad precision");
-    if (o->storage < MG_STORAGE_AUTO || o->storage > MG_STORAGE_STENCIL) throw Error(MG_EINVAL, "bad storage");
+    if (o->storage < MG_STORAGE_AUTO || o->storage > MG_STORAGE_COEF) throw Error(MG_EINVAL, "bad storage");
+    if (o->storage == MG_STORAGE_COEF && (p->dim != 3 || p->mass != 0.0))
+        throw Error(MG_EINVAL, "coefficient storage needs 3D Q1 without a mass shift");
     h->prob = *p;
     h->prob.k_cell = nullptr;
     h->opt = *o;
@@ -1594,13 +1823,38 @@ void mgi::build_hierarchy(mg_hierarchy *h, const mg_problem *p, const mg_options
     if (h->mixed && (elem == MG_Q1 || elem == MG_P1) && o->smoother != MG_GAUSS_SEIDEL)
         for (int l = 1; l <= Lf; l++)
             if (h->lev[l].n >= 32768) scan[l] = constant_stencil(A[l], dim, h->lev[l].N, 4, svals[l].data());
+    if (h->mixed && elem == MG_RQ1 && o->smoother != MG_GAUSS_SEIDEL)
+        for (int l = 1; l <= Lf; l++)
+            if (h->lev[l].n >= 32768 && !h->lev[l].galerkin)
+                scan[l] = rq1_constant_stencil(A[l], h->lev[l].N, svals[l].data());
+    // per-cell coefficient storage: FP32 levels of 3D Q1 rediscretised with a per-cell
+    // coefficient (checked against the assembled matrix)
+    std::vector<std::vector<float>> kap((size_t)nlev);
+    std::vector<char> coef((size_t)nlev, 0);
+    if (h->mixed && elem == MG_Q1 && dim == 3 && p->mass == 0.0 && o->smoother != MG_GAUSS_SEIDEL &&
+        (o->storage == MG_STORAGE_AUTO || o->storage == MG_STORAGE_COEF))
+        for (int l = 1; l <= Lf; l++) {
+            const LevelD &L = h->lev[l];
+            if (L.n < 32768 || L.galerkin) continue;
+            std::vector<double> kl;
+            bool have = true;
+            if (p->k_cell)
+                have = mgh::coarse_coefficient(dim, p->n_cells, p->k_cell, L.N, kl);
+            else
+                kl.assign((size_t)L.N * L.N * L.N, 1.0);
+            coef[l] = have && coef_form(A[l], L.N, kl, kap[l]);
+        }
     if (o->storage == MG_STORAGE_AUTO) {  // measured on the levels large enough to be bandwidth-bound
         for (int l = 1; l <= Lf; l++)
             if (h->lev[l].n >= 32768)
-                lfmt[l] = tune_storage(h, A[l], dim, elem, h->lev[l].N, scan[l] ? svals[l].data() : nullptr);
+                lfmt[l] = tune_storage(h, A[l], dim, elem, h->lev[l].N, scan[l] ? svals[l].data() : nullptr,
+                                       coef[l] ? &kap[l] : nullptr);
     } else if (fmt == MG_STORAGE_STENCIL) {
         for (int l = 0; l <= Lf; l++)
-            if (!scan[l]) lfmt[l] = MG_STORAGE_DIA;
+            if (!scan[l]) lfmt[l] = elem == MG_RQ1 ? MG_STORAGE_ELL : MG_STORAGE_DIA;
+    } else if (fmt == MG_STORAGE_COEF) {
+        for (int l = 0; l <= Lf; l++)
+            if (!coef[l]) lfmt[l] = MG_STORAGE_DIA;
     }
     int sv = h->inner_size;
     // ---- multicolour Gauss-Seidel: colour order of every smoothed level ----
@@ -1641,11 +1895,11 @@ void mgi::build_hierarchy(mg_hierarchy *h, const mg_problem *p, const mg_options
             LevelD &L = h->lev[l];
             int lf = lfmt[l];
             L.fmt = lf;
-            plan_matrix(L.A, A[l], lf, dim, L.N, sv, S, take, lf == MG_STORAGE_STENCIL ? svals[l].data() : nullptr);
+            plan_matrix(L.A, A[l], lf, dim, L.N, sv, S, take, lf == MG_STORAGE_STENCIL ? svals[l].data() : nullptr, elem);
             if (!h->mixed && l >= 1) L.A.dinv = vec((size_t)L.A.ld * 8);  // FP64 smoothers read D^-1
             // FP32 sweeps from x = 0 on formats whose diagonal has no fixed slot read D^-1
             // instead of scanning the row (the same value: 1/a_ii rounded once)
-            if (h->mixed && l >= 1 && lf != MG_STORAGE_DIA && lf != MG_STORAGE_STENCIL)
+            if (h->mixed && l >= 1 && lf != MG_STORAGE_DIA && lf != MG_STORAGE_STENCIL && lf != MG_STORAGE_COEF)
                 L.A.dinv = vec((size_t)L.A.ld * 4);
             if (gs && l >= 1) {  // the colour-major copy of A for the Gauss-Seidel sweeps (CSR for SELL levels)
                 plan_matrix(L.G, A[l], lf == MG_STORAGE_SELL ? MG_STORAGE_CSR : lf, dim, L.N, sv, S, take);
@@ -1653,8 +1907,9 @@ void mgi::build_hierarchy(mg_hierarchy *h, const mg_problem *p, const mg_options
                 L.perm = (int32_t *)vec((size_t)std::max<int64_t>(L.G.n, 1) * 4);
             }
             int64_t n1 = L.N - 1;
-            L.pad = lf == MG_STORAGE_DIA || lf == MG_STORAGE_STENCIL ? round_up(dim == 3 ? n1 * n1 + n1 + 1 : n1 + 1, 64)
-                                                                     : 0;
+            L.pad = (lf == MG_STORAGE_DIA || lf == MG_STORAGE_STENCIL || lf == MG_STORAGE_COEF) && elem != MG_RQ1
+                        ? round_up(dim == 3 ? n1 * n1 + n1 + 1 : n1 + 1, 64)
+                        : 0;
             int64_t ld = L.A.ld;
             if (with_vectors) {
                 for (int c = 0; c < 2; c++) {
@@ -1675,8 +1930,10 @@ void mgi::build_hierarchy(mg_hierarchy *h, const mg_problem *p, const mg_options
         }
         LevelD &F = h->lev[Lf];
         if (h->mixed) {
-            // the FP64 operator of the outer residual is stored (a stencil level stores DIA)
-            plan_matrix(h->A64, A[Lf], F.fmt == MG_STORAGE_STENCIL ? MG_STORAGE_DIA : F.fmt, dim, F.N, 8, S, take);
+            // the FP64 operator of the outer residual is stored (a stencil or coefficient level stores DIA)
+            bool formed = F.fmt == MG_STORAGE_STENCIL || F.fmt == MG_STORAGE_COEF;
+            int f64 = formed ? (elem == MG_RQ1 ? MG_STORAGE_SELL : MG_STORAGE_DIA) : F.fmt;
+            plan_matrix(h->A64, A[Lf], f64, dim, F.N, 8, S, take);
         } else if (take) {
             h->A64 = F.A;
         }
@@ -1691,7 +1948,9 @@ void mgi::build_hierarchy(mg_hierarchy *h, const mg_problem *p, const mg_options
             h->pcg_q = (double *)vec((size_t)F.A.ld * 8);
             h->pcg_scal = (double *)vec(PCG_NSCAL * 8);
             if (h->mass != 0.0) {
-                plan_matrix(h->B64, Bh, F.fmt == MG_STORAGE_STENCIL ? MG_STORAGE_DIA : F.fmt, dim, F.N, 8, S, take);
+                bool formed = F.fmt == MG_STORAGE_STENCIL || F.fmt == MG_STORAGE_COEF;
+                int f64 = formed ? (elem == MG_RQ1 ? MG_STORAGE_SELL : MG_STORAGE_DIA) : F.fmt;
+                plan_matrix(h->B64, Bh, f64, dim, F.N, 8, S, take);
                 h->bF64 = (double *)vec((size_t)F.A.ld * 8);
             }
         }
@@ -1708,8 +1967,13 @@ void mgi::build_hierarchy(mg_hierarchy *h, const mg_problem *p, const mg_options
         LevelD &L = h->lev[l];
         if (h->mixed) {
             std::vector<float> v32;
-            mgh::round_fp32(A[l], v32);
-            upload_matrix<float>(L.A, A[l], v32, dim, L.N, h->s);
+            if (L.A.fmt == MG_STORAGE_COEF) {
+                CK(cudaMemcpyAsync(L.A.val, kap[l].data(), kap[l].size() * 4, cudaMemcpyHostToDevice, h->s));
+                CK(cudaStreamSynchronize(h->s));
+            } else {
+                mgh::round_fp32(A[l], v32);
+                upload_matrix<float>(L.A, A[l], v32, dim, L.N, h->s);
+            }
             if (L.A.dinv) {
                 std::vector<float> dv((size_t)L.A.ld, 0.0f);
                 for (int64_t i = 0; i < A[l].nrows; i++)
@@ -2271,6 +2535,62 @@ static void export_dev(const DevMat &m, int dim, int N, int sv, mgh::Csr &out, b
         for (int64_t i = 0; i < m.n; i++) {
             for (auto &e : rows[i]) {
                 out.col.push_back(e.first);
+                out.val.push_back(e.second);
+            }
+            out.rowptr[i + 1] = (int64_t)out.col.size();
+        }
+        return;
+    }
+    if (m.fmt == MG_STORAGE_COEF) {  // the operator the sweep applies: sums of -kap_e, 4 sum kap_e
+        int64_t n1 = N - 1, nc = N;
+        std::vector<float> kap((size_t)(nc * nc * nc));
+        CK(cudaMemcpy(kap.data(), m.val, kap.size() * 4, cudaMemcpyDeviceToHost));
+        for (int64_t i = 0; i < m.n; i++) {
+            int ci[3] = {0, 0, 0};
+            mgh::q1_coords(3, N, i, ci);
+            auto K = [&](int a, int b, int c) { return kap[(size_t)((ci[0] - 1 + a) + nc * ((ci[1] - 1 + b) + nc * (ci[2] - 1 + c)))]; };
+            for (int p = 0; p < 27; p++) {
+                int d[3] = {p % 3 - 1, (p / 3) % 3 - 1, p / 9 - 1};
+                int nz = (d[0] != 0) + (d[1] != 0) + (d[2] != 0);
+                bool inside = true;
+                for (int a = 0; a < 3; a++)
+                    if (ci[a] + d[a] < 1 || ci[a] + d[a] > N - 1) inside = false;
+                if (!inside) continue;
+                float v = 0.0f;
+                if (nz == 0) {
+                    float ks = ((K(0, 0, 0) + K(1, 0, 0)) + (K(0, 1, 0) + K(1, 1, 0))) +
+                               ((K(0, 0, 1) + K(1, 0, 1)) + (K(0, 1, 1) + K(1, 1, 1)));
+                    v = 4.0f * ks;
+                } else if (nz >= 2) {  // the cells holding both corners: one per nonzero offset side
+                    for (int a = 0; a < 2; a++)
+                        for (int b = 0; b < 2; b++)
+                            for (int c = 0; c < 2; c++) {
+                                int side[3] = {a, b, c};
+                                bool both = true;
+                                for (int q = 0; q < 3; q++)
+                                    if (d[q] != 0 && side[q] != (d[q] > 0 ? 1 : 0)) both = false;
+                                if (both) v -= K(a, b, c);
+                            }
+                }
+                out.col.push_back((int32_t)(i + d[0] + n1 * d[1] + n1 * n1 * d[2]));
+                out.val.push_back((double)v);
+            }
+            out.rowptr[i + 1] = (int64_t)out.col.size();
+        }
+        return;
+    }
+    if (m.fmt == MG_STORAGE_STENCIL && m.elem == MG_RQ1) {  // the face stencil, columns ascending
+        float hv = (float)m.sval[1];
+        const double rv[3] = {(double)(6.0f * hv), (double)hv, -(double)hv};
+        for (int64_t i = 0; i < m.n; i++) {
+            int64_t col[11];
+            int role[11];
+            int cnt = rq1_neighbours(N, i, col, role);
+            std::vector<std::pair<int64_t, double>> row;
+            for (int k = 0; k < cnt; k++) row.push_back({col[k], rv[role[k]]});
+            std::sort(row.begin(), row.end());
+            for (auto &e : row) {
+                out.col.push_back((int32_t)e.first);
                 out.val.push_back(e.second);
             }
             out.rowptr[i + 1] = (int64_t)out.col.size();

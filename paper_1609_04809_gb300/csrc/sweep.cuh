@@ -37,7 +37,7 @@ struct Ar<float> {
     static __device__ __forceinline__ float add(float a, float b) { return a + b; }
     static __device__ __forceinline__ float sub(float a, float b) { return a - b; }
     static __device__ __forceinline__ float mac(float s, float a, float b) { return fmaf(a, b, s); }
-    static __device__ __forceinline__ float rcp(float a) { return __fdiv_rn(1.0f, a); }
+    static __device__ __forceinline__ float rcp(float a) { return __frcp_rn(a); }  // 1/a correctly rounded
 };
 
 // Sweep modes: what a pass does with s = (A x)_i and dinv = 1 / a_ii.
@@ -93,6 +93,36 @@ __device__ __forceinline__ void sweep_out(int i, T s, T dinv, T xi, const T *__r
     } else if (MODE == SW_CHEB) {
         T r = A::sub(bi, s);
         T dd = A::add(A::mul(c1, d[i]), A::mul(c2, A::mul(dinv, r)));
+        d[i] = dd;
+        out[i] = A::add(xi, dd);
+    } else if (MODE == SW_JACOBI_Z) {
+        out[i] = A::mul(c1, A::mul(dinv, bi));
+    } else {  // SW_CHEBF_Z
+        T dd = A::mul(c1, A::mul(dinv, bi));
+        d[i] = dd;
+        out[i] = dd;
+    }
+}
+
+// sweep_out with b_i and (SW_CHEB) d_i already loaded
+template <typename T, int MODE>
+__device__ __forceinline__ void sweep_out_v(int i, T s, T dinv, T xi, T bi, T di, T *__restrict__ out,
+                                            T *__restrict__ d, T c1, T c2)
+{
+    using A = Ar<T>;
+    if (MODE == SW_RESID) {
+        out[i] = A::sub(bi, s);
+    } else if (MODE == SW_JACOBI) {
+        T r = A::sub(bi, s);
+        out[i] = A::add(xi, A::mul(c1, A::mul(dinv, r)));
+    } else if (MODE == SW_CHEBF) {
+        T r = A::sub(bi, s);
+        T dd = A::mul(c1, A::mul(dinv, r));
+        d[i] = dd;
+        out[i] = A::add(xi, dd);
+    } else if (MODE == SW_CHEB) {
+        T r = A::sub(bi, s);
+        T dd = A::add(A::mul(c1, di), A::mul(c2, A::mul(dinv, r)));
         d[i] = dd;
         out[i] = A::add(xi, dd);
     } else if (MODE == SW_JACOBI_Z) {
@@ -222,6 +252,275 @@ __global__ void __launch_bounds__(256) k_stencil_fixed(StencilView<T> S, const T
         k++;
     }
     sweep_out<T, MODE>(i, s, S.dinv, xc, b, out, d, c1, c2);
+}
+
+// Per-cell coefficient (3D Q1, FP32): the level matrix of -div(k grad u) rediscretised
+// with a coefficient k_e per cell is sum_e k_e h K_ref, and the unit-cube Q1 stiffness
+// K_ref has 1/3 on the diagonal, 0 between edge-adjacent corners and -1/12 between the
+// other corner pairs. With kap_e = k_e h / 12 row i is therefore
+//     (A x)_i = sum over the 8 cells e around vertex i of kap_e (4 x_i - s_e),
+// s_e the sum of x at the four corners of e that share no edge with i (three across a
+// face, one across the body): the matrix is formed from one value per cell and never
+// stored. s_e is summed in pairs, (x_f1 + x_f2) + (x_f3 + x_b), so that a constant x gives
+// exactly 4 x_i - s_e = 0 (the interior row sums vanish in FP32 as they do in the
+// assembled matrix); a_ii = 4 sum_e kap_e. Corners on the Dirichlet boundary hold 0.
+// kap: (n1 + 1)^3 cells, x fastest.
+//
+// A thread owns the grid column (vx, vy) over `zc` consecutive planes and marches along
+// z: the x values of the 3 x 3 neighbouring columns on planes z - 1, z, z + 1 and the kap
+// values of the 2 x 2 neighbouring cell columns on cell planes z, z + 1 stay in
+// registers, so each step loads only the new plane (9 x and 4 kap values, gathered
+// through L1 where neighbouring threads share them) instead of all 29. The three planes
+// rotate by renaming (the loop is unrolled three times), loads use one row pointer per
+// dy with immediate dx offsets. Columns off the grid in x or y are selected to the
+// Dirichlet value 0; planes z = -1 and z = n1 fall in the zero halo of the x buffer (x is
+// padded by n1^2 + n1 + 1 zeros on both sides, written at setup and never again).
+struct CoefView {
+    const float *kap;
+    int n1;  // interior points per axis (cells per axis - 1)
+    int zc;  // planes per thread
+};
+
+#ifndef MG_COEF_MIN_BLOCKS
+#define MG_COEF_MIN_BLOCKS 4  // 64 registers: four 256-thread blocks per SM (measured best of 1, 4, 6)
+#endif
+template <int MODE>
+__global__ void __launch_bounds__(256, MG_COEF_MIN_BLOCKS) k_coef_sweep(CoefView S, const float *__restrict__ x,
+                                                    const float *__restrict__ b, float *__restrict__ out,
+                                                    float *__restrict__ d, float c1, float c2)
+{
+    constexpr bool Z = IsZero<MODE>::value;
+    pdl_enter();
+    const int n1 = S.n1, nc = n1 + 1;
+    const int vx = blockIdx.x * blockDim.x + threadIdx.x, vy = blockIdx.y * blockDim.y + threadIdx.y;
+    if (vx >= n1 || vy >= n1) return;
+    const int z0 = blockIdx.z * S.zc, z1 = min(z0 + S.zc, n1);
+    const int64_t plane = (int64_t)n1 * n1, cplane = (int64_t)nc * nc;
+    // column c = (dx + 1) + 3 (dy + 1) of the point's 3 x 3 neighbourhood lies in the grid
+    const bool xlo = vx > 0, xhi = vx < n1 - 1, ylo = vy > 0, yhi = vy < n1 - 1;
+    bool cin[9];
+#pragma unroll
+    for (int c = 0; c < 9; c++) {
+        const int dx = c % 3 - 1, dy = c / 3 - 1;
+        cin[c] = (dx >= 0 || xlo) && (dx <= 0 || xhi) && (dy >= 0 || ylo) && (dy <= 0 || yhi);
+    }
+    const float *xr = x + vx + (int64_t)n1 * vy + plane * (z0 - 1);  // column (vx, vy), plane z0 - 1
+    const float *kr = S.kap + vx + (int64_t)nc * vy + cplane * z0;   // cell column (vx, vy), plane z0
+    auto load_plane = [&](float P[9]) {  // the 9 columns at plane xr, then advance xr
+        const float *rm = xr - n1, *rp = xr + n1;
+#pragma unroll
+        for (int c = 0; c < 9; c++) {
+            const int dx = c % 3 - 1, dy = c / 3 - 1;
+            const float v = __ldg((dy < 0 ? rm : (dy > 0 ? rp : xr)) + dx);
+            P[c] = cin[c] ? v : 0.0f;
+        }
+        xr += plane;
+    };
+    auto load_cells = [&](float K[4]) {  // the 2 x 2 cells at plane kr, then advance kr
+        K[0] = __ldg(kr);
+        K[1] = __ldg(kr + 1);
+        K[2] = __ldg(kr + nc);
+        K[3] = __ldg(kr + nc + 1);
+        kr += cplane;
+    };
+    // b_i (and d_i for the later Chebyshev steps) of the point on plane z, loaded with the
+    // plane so that all of a step's loads are in flight together
+    auto load_bd = [&](int z, float &bi, float &di) {
+        const int i = vx + n1 * vy + (int)(plane * z);
+        bi = __ldg(b + i);
+        di = MODE == SW_CHEB ? d[i] : 0.0f;
+    };
+    // one point: planes Pm, P0, Pp (z - 1, z, z + 1), cell planes Kc, Kn (z, z + 1)
+    auto point = [&](const float Pm[9], const float P0[9], const float Pp[9], const float Kc[4], const float Kn[4],
+                     int z, float bi, float di) {
+        const int i = vx + n1 * vy + (int)(plane * z);
+        // the 8 cells around the point: cell (vx + a, vy + b, z + c), e = a + 2 b + 4 c
+        float kap[8];
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            kap[e] = Kc[e];
+            kap[e + 4] = Kn[e];
+        }
+        const float ksum = ((kap[0] + kap[1]) + (kap[2] + kap[3])) + ((kap[4] + kap[5]) + (kap[6] + kap[7]));
+        const float dinv = Ar<float>::rcp(4.0f * ksum);
+        if (Z) {
+            sweep_out_v<float, MODE>(i, 0.0f, dinv, 0.0f, bi, di, out, d, c1, c2);
+            return;
+        }
+        // x at stencil position p = (dx+1) + 3(dy+1) + 9(dz+1): column p % 9 of plane p / 9
+        auto xv = [&](int p) { return p < 9 ? Pm[p] : (p < 18 ? P0[p - 9] : Pp[p - 18]); };
+        const float xc = xv(13);
+        float acc = 0.0f;
+#pragma unroll
+        for (int e = 0; e < 8; e++) {
+            // cell e lies on the side (sx, sy, sz) of the point; its corners that share no
+            // edge with the point sit at (sx, sy, 0), (sx, 0, sz), (0, sy, sz), (sx, sy, sz)
+            const int sx = (e & 1) ? 1 : -1, sy = ((e >> 1) & 1) ? 1 : -1, sz = (e >> 2) ? 1 : -1;
+            const float fxy = xv((sx + 1) + 3 * (sy + 1) + 9);
+            const float fxz = xv((sx + 1) + 3 + 9 * (sz + 1));
+            const float fyz = xv(1 + 3 * (sy + 1) + 9 * (sz + 1));
+            const float fb = xv((sx + 1) + 3 * (sy + 1) + 9 * (sz + 1));
+            const float se = (fxy + fxz) + (fyz + fb);
+            acc = fmaf(kap[e], fmaf(4.0f, xc, -se), acc);
+        }
+        sweep_out_v<float, MODE>(i, acc, dinv, xc, bi, di, out, d, c1, c2);
+    };
+    float A[9] = {}, B[9] = {}, C[9] = {}, KA[4], KB[4];
+    if (!Z) {
+        load_plane(A);  // z0 - 1
+        load_plane(B);  // z0
+    }
+    load_cells(KA);  // cell plane z0
+    int z = z0;
+    float bi, di;
+    // roles rotate A -> B -> C (planes) and KA -> KB (cell planes) from step to step
+    for (; z + 3 <= z1; z += 3) {
+        if (!Z) load_plane(C);
+        load_cells(KB);
+        load_bd(z, bi, di);
+        point(A, B, C, KA, KB, z, bi, di);
+        if (!Z) load_plane(A);
+        load_cells(KA);
+        load_bd(z + 1, bi, di);
+        point(B, C, A, KB, KA, z + 1, bi, di);
+        if (!Z) load_plane(B);
+        load_cells(KB);
+        load_bd(z + 2, bi, di);
+        point(C, A, B, KA, KB, z + 2, bi, di);
+        // after three steps the planes are back in their roles (A = z + 2, B = z + 3); the
+        // cell planes are swapped (KA = z + 2, KB = z + 3)
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            const float t = KA[e];
+            KA[e] = KB[e];
+            KB[e] = t;
+        }
+    }
+    if (z < z1) {
+        if (!Z) load_plane(C);
+        load_cells(KB);
+        load_bd(z, bi, di);
+        point(A, B, C, KA, KB, z, bi, di);
+        z++;
+        if (z < z1) {
+            if (!Z) load_plane(A);
+            load_cells(KA);
+            load_bd(z, bi, di);
+            point(B, C, A, KB, KA, z, bi, di);
+        }
+    }
+}
+
+// Constant stencil of the rotated-Q1 face space (FP32 levels of a mixed hierarchy with a
+// constant coefficient). The element couples each face of a cell to itself by 3h, to the
+// opposite face by h and to the four other faces by -h, so the row of an interior face
+// (two cells) is 6h on the diagonal, +h at the two faces opposite it and -h at the eight
+// other faces of its two cells; faces on the Dirichlet boundary are absent. With hv = h
+//     (A x)_i = hv ((8 x_i - S_8) - (2 x_i - (x_o1 + x_o2))),
+// S_8 the sum of the eight (pairwise, so that a constant x gives exactly 0 in FP32 as the
+// interior row sums do). DOF numbering as in mg.h: faces normal to x (i, j, k), i the
+// face position 1..N-1 along x and (j, k) the cell, index (i-1) + (N-1)(j + N k); normal
+// to y: (N-1)N^2 + i + N((j-1) + (N-1) k); normal to z: 2(N-1)N^2 + i + N(j + N(k-1)).
+// Launch: grid (ceil(N / bx), ceil(N / by), 3 N), blockIdx.z = family * N + slab; a
+// thread owns the face at (fast, line, slab) of its family. Neighbours off the grid are
+// not loaded (predicated), so no padding is needed.
+struct Rq1View {
+    int N;       // cells per axis
+    float hv;    // the coupling to an opposite face (h times the coefficient)
+    float dinv;  // 1 / (6 hv)
+};
+
+template <int MODE>
+__global__ void __launch_bounds__(256) k_stencil_rq1(Rq1View S, const float *__restrict__ x,
+                                                     const float *__restrict__ b, float *__restrict__ out,
+                                                     float *__restrict__ d, float c1, float c2)
+{
+    pdl_enter();
+    const int N = S.N, M = N - 1;
+    const int f = blockIdx.z / N, c = blockIdx.z - f * N;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x, q = blockIdx.y * blockDim.y + threadIdx.y;
+    if (p >= N || q >= N) return;
+    const int64_t nx0 = 0, ny0 = (int64_t)M * N * N, nz0 = 2 * (int64_t)M * N * N;
+    // the face's own index, its two opposite faces (o1 below, o2 above along the normal)
+    // and the eight other faces of its two cells, with their in-grid masks
+    int64_t i;
+    int64_t o1, o2, e[8];
+    bool mo1, mo2, me[8];
+    if (f == 0) {  // normal to x: position p + 1 (p < N - 1), cell (j, k) = (q, c)
+        if (p >= M) return;
+        i = nx0 + p + (int64_t)M * (q + (int64_t)N * c);
+        o1 = i - 1;
+        o2 = i + 1;
+        mo1 = p >= 1;
+        mo2 = p + 1 <= M - 1;
+        // the cells on either side: x-index p (below) and p + 1 (above)
+#pragma unroll
+        for (int s2 = 0; s2 < 2; s2++) {
+            const int cx = p + s2;
+#pragma unroll
+            for (int t = 0; t < 2; t++) {
+                const int jy = q + t;  // y-face position j' in 1..N-1
+                e[4 * s2 + t] = ny0 + cx + (int64_t)N * ((jy - 1) + (int64_t)M * c);
+                me[4 * s2 + t] = jy >= 1 && jy <= M;
+                const int kz = c + t;  // z-face position k' in 1..N-1
+                e[4 * s2 + 2 + t] = nz0 + cx + (int64_t)N * (q + (int64_t)N * (kz - 1));
+                me[4 * s2 + 2 + t] = kz >= 1 && kz <= M;
+            }
+        }
+    } else if (f == 1) {  // normal to y: position q + 1 (q < N - 1), cell (i, k) = (p, c)
+        if (q >= M) return;
+        i = ny0 + p + (int64_t)N * (q + (int64_t)M * c);
+        o1 = i - N;
+        o2 = i + N;
+        mo1 = q >= 1;
+        mo2 = q + 1 <= M - 1;
+#pragma unroll
+        for (int s2 = 0; s2 < 2; s2++) {
+            const int cy = q + s2;
+#pragma unroll
+            for (int t = 0; t < 2; t++) {
+                const int ix = p + t;  // x-face position i' in 1..N-1
+                e[4 * s2 + t] = nx0 + (ix - 1) + (int64_t)M * (cy + (int64_t)N * c);
+                me[4 * s2 + t] = ix >= 1 && ix <= M;
+                const int kz = c + t;
+                e[4 * s2 + 2 + t] = nz0 + p + (int64_t)N * (cy + (int64_t)N * (kz - 1));
+                me[4 * s2 + 2 + t] = kz >= 1 && kz <= M;
+            }
+        }
+    } else {  // normal to z: position c + 1 (c < N - 1), cell (i, j) = (p, q)
+        if (c >= M) return;
+        i = nz0 + p + (int64_t)N * (q + (int64_t)N * c);
+        o1 = i - (int64_t)N * N;
+        o2 = i + (int64_t)N * N;
+        mo1 = c >= 1;
+        mo2 = c + 1 <= M - 1;
+#pragma unroll
+        for (int s2 = 0; s2 < 2; s2++) {
+            const int cz = c + s2;
+#pragma unroll
+            for (int t = 0; t < 2; t++) {
+                const int ix = p + t;
+                e[4 * s2 + t] = nx0 + (ix - 1) + (int64_t)M * (q + (int64_t)N * cz);
+                me[4 * s2 + t] = ix >= 1 && ix <= M;
+                const int jy = q + t;
+                e[4 * s2 + 2 + t] = ny0 + p + (int64_t)N * ((jy - 1) + (int64_t)M * cz);
+                me[4 * s2 + 2 + t] = jy >= 1 && jy <= M;
+            }
+        }
+    }
+    const int ii = (int)i;
+    if (IsZero<MODE>::value) {
+        sweep_out<float, MODE>(ii, 0.0f, S.dinv, 0.0f, b, out, d, c1, c2);
+        return;
+    }
+    const float xc = __ldg(x + i);
+    const float xo1 = mo1 ? __ldg(x + o1) : 0.0f, xo2 = mo2 ? __ldg(x + o2) : 0.0f;
+    float xe[8];
+#pragma unroll
+    for (int k = 0; k < 8; k++) xe[k] = me[k] ? __ldg(x + e[k]) : 0.0f;
+    const float s8 = ((xe[0] + xe[1]) + (xe[2] + xe[3])) + ((xe[4] + xe[5]) + (xe[6] + xe[7]));
+    const float s = (8.0f * xc - s8) - (2.0f * xc - (xo1 + xo2));
+    sweep_out<float, MODE>(ii, S.hv * s, S.dinv, xc, b, out, d, c1, c2);
 }
 
 // ELL with explicit columns; padded slots hold column i and value 0.

@@ -18,6 +18,7 @@ MG_Q1, MG_RQ1, MG_P1, MG_P2 = 0, 1, 2, 3
 MG_JACOBI, MG_CHEBYSHEV, MG_GAUSS_SEIDEL = 0, 1, 2
 MG_FP64, MG_MIXED = 0, 1
 MG_STORAGE_AUTO, MG_STORAGE_CSR, MG_STORAGE_ELL, MG_STORAGE_DIA, MG_STORAGE_SELL, MG_STORAGE_STENCIL = 0, 1, 2, 3, 4, 5
+MG_STORAGE_COEF = 6
 MG_TRANSFER_NONE, MG_TRANSFER_GRID, MG_TRANSFER_SELL = 0, 1, 2
 MG_MAX_LEVELS = 16
 (MG_K_SMOOTH, MG_K_RESID, MG_K_RESTRICT, MG_K_PROLONG, MG_K_COARSE, MG_K_OUTER, MG_K_UPDATE,

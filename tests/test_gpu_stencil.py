@@ -85,7 +85,45 @@ def test_stencil_needs_a_constant_stencil_and_falls_back_to_dia(orc):
         with pytest.raises(mg.MgError):
             mg.Hierarchy(dim, elem, 16, 3, storage=mg.MG_STORAGE_STENCIL, **kw)
     with pytest.raises(mg.MgError):
-        mg.Hierarchy(3, mg.MG_RQ1, 16, 3, storage=mg.MG_STORAGE_STENCIL, precision=mg.MG_MIXED)
+        mg.Hierarchy(3, mg.MG_P2, 8, 2, storage=mg.MG_STORAGE_STENCIL, precision=mg.MG_MIXED)
+
+
+def _solve_rq1(orc, N, L, b, storage):
+    H = mg.Hierarchy(3, mg.MG_RQ1, N, L, smoother=mg.MG_JACOBI, omega=0.7, nu_pre=2, nu_post=2,
+                     precision=mg.MG_MIXED, storage=storage)
+    bd = torch.from_numpy(b).cuda()
+    x = torch.zeros_like(bd)
+    st, it, hist = H.solve(bd, x, 1e-10)
+    x = x.cpu().numpy()
+    return H, st, it, np.linalg.norm(b - orc.spmv(orc.assemble(3, orc.RQ1, N), x)), x
+
+
+def test_rq1_face_stencil_levels_solve_like_stored_ones(orc):
+    """Rotated Q1 with a constant coefficient: every face row is 6h, +h at the two
+    opposite faces, -h at the eight other faces of its cells. 48^3 and 24^3 cells are
+    stencil levels (n >= 32768), the smaller ones keep ELL."""
+    N, L = 48, 4
+    b = W.random_vector(mg.mg_ndofs(3, mg.MG_RQ1, N), seed=41)
+    Hs, st, it, nr, xs = _solve_rq1(orc, N, L, b, mg.MG_STORAGE_STENCIL)
+    He, st_e, it_e, nr_e, xe = _solve_rq1(orc, N, L, b, mg.MG_STORAGE_ELL)
+    assert Hs.info()["storage"] == [mg.MG_STORAGE_ELL] * 2 + [mg.MG_STORAGE_STENCIL] * 2
+    assert Hs.info()["device_bytes"] < He.info()["device_bytes"]
+    assert st == st_e == mg.MG_OK
+    assert nr <= 1e-10 * np.linalg.norm(b) and abs(it - it_e) <= 1
+    assert np.linalg.norm(xs - xe) <= 1e-6 * np.linalg.norm(xe)
+
+
+def test_rq1_face_stencil_export_is_the_oracle_operator(orc):
+    N, L = 48, 4
+    H = mg.Hierarchy(3, mg.MG_RQ1, N, L, precision=mg.MG_MIXED, storage=mg.MG_STORAGE_STENCIL, omega=0.7)
+    assert H.info()["storage"][L - 1] == mg.MG_STORAGE_STENCIL
+    rp, col, val = mg.mg_export_operator(H.h, L - 1, 0, mg.MG_MIXED)
+    Ao = orc.assemble(3, orc.RQ1, N)
+    assert np.array_equal(rp, Ao.rowptr) and np.array_equal(col, Ao.col)
+    assert np.all(np.abs(val - Ao.val) <= 1e-6 * (6.0 / N))
+    # the FP64 operator of the outer residual stays stored and exact
+    rp64, col64, val64 = mg.mg_export_operator(H.h, L - 1, 0, mg.MG_FP64)
+    assert np.array_equal(rp64, Ao.rowptr) and np.array_equal(col64, Ao.col) and np.array_equal(val64, Ao.val)
 
 
 def test_stencil_with_mass_shift_heat_steps():
