@@ -1,19 +1,24 @@
 """Benchmark: V-cycle throughput of the GB300 multigrid solve (DOFs per second per V-cycle).
 
-Workload (default): 3D Poisson on the unit cube, conforming Q1 on a 128^3 hex mesh
-(2,048,383 interior DOFs, 27-point stencil), f from u = sin(pi x) sin(pi y) sin(pi z),
-FP64, 6 levels (coarsest 4^3 cells, dense LU), V(2,2) with one degree-2 Chebyshev
-polynomial per smoothing phase. A step is one defect-correction iteration: FP64 outer
-residual and its norm, one V-cycle, x += c.
+Workload (default): the largest single-GPU workload, 3D diffusion -div(k grad u) = 1 on
+the unit cube, conforming Q1 on a 256^3 hex mesh (16,581,375 interior DOFs), k piecewise
+constant on 16^3 blocks with log10 k ~ U[-2, 2] (SplitMix64 seed 20260101), 7 levels
+(coarsest 4^3 cells, dense LU; Galerkin levels where the cells straddle the blocks),
+V(2,2) with one degree-2 Chebyshev polynomial per smoothing phase, in the precision the
+workload specifies: FP32 V-cycle inside FP64 defect correction. A step is one
+defect-correction iteration: FP64 outer residual and its norm, one FP32 V-cycle, x += c.
 
 Prints one JSON line (rank 0). Besides the throughput it reports
-  * roofline: the dominant kernel (finest-level smoother sweep) timed with CUDA events
-    around each launch inside the timed region, its algorithmic bytes per launch, and
-    the fraction of the measured HBM copy bandwidth;
+  * roofline: the dominant kernel of the step (events around each of its launches inside
+    the timed region), against the roofline that binds it, with the HBM fraction beside
+    it; roofline_kernels: the other finest-level kernels the same way;
+  * whole_cycle: algorithmic bytes of every launch of one step over the step time;
   * e2e: full solves to 1e-10 through mg_solve_host from pinned host memory;
-  * time_to_solution: FP64 and mixed (FP32 V-cycle in FP64 defect correction) solves;
-  * cpu_baseline: the FP64 CPU oracle on a bounded sample of the same workload.
---impl reference times the oracle alone (the reference arm) on host cores.
+  * time_to_solution: mixed vs plain FP64 to 1e-10 on the same inputs (and CG);
+  * configs: the 128^3 constant-coefficient Q1 workload in both precisions;
+  * cpu_baseline: the FP64 CPU oracle on a bounded sample of the same workload, on all
+    host cores and on one.
+--impl reference times the oracle alone (the reference arm) on the host cores.
 """
 import argparse
 import hashlib
@@ -30,10 +35,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "V-cycle DOFs/s"
-# FP64 issue rate of GB300: 2 DFMA per clock per SM (the recipe's nominal 1.25 TFLOP/s)
-FP64_PEAK_TFLOPS = 152 * 2.07e9 * 2 * 2 / 1e12
 UNIT = "DOF/s"
+DEFAULT_CONFIG = "q1_3d_256_vark"
 WORKLOADS = {
+    "q1_3d_256_vark": "3D diffusion, Q1, 256^3 cells (16,581,375 DOFs), k on 16^3 blocks (log10 k ~ U[-2,2]), "
+                      "7 levels, V(2,2) Chebyshev deg 2, FP32 V-cycle in FP64 defect correction",
     "q1_3d_128_cheb": "3D Poisson, Q1, 128^3 cells (2,048,383 DOFs), 6 levels, V(2,2) Chebyshev deg 2, FP64",
     "q1_2d_64": "2D Poisson, Q1, 64^2 cells (3,969 DOFs), 5 levels, V(2,2) Jacobi 0.8, FP64",
     "rq1_3d_96": "3D Poisson, rotated Q1, 96^3 cells (2,626,560 DOFs), 6 levels, V(2,2) Jacobi 0.7, FP64",
@@ -56,6 +62,28 @@ def _peaks():
         return float(d["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
 
+
+def _max_sm_mhz():
+    """Maximum SM clock: nvidia-smi, else MEASURED_PEAKS.json, else the nominal 2070 MHz."""
+    try:
+        out = subprocess.run(["nvidia-smi", "-i", "0", "--query-gpu=clocks.max.sm", "--format=csv,noheader,nounits"],
+                             capture_output=True, text=True, timeout=20).stdout.strip().splitlines()
+        return float(out[0]), "nvidia-smi clocks.max.sm"
+    except (OSError, ValueError, IndexError, subprocess.SubprocessError):
+        pass
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return float(json.load(open(p)).get("sm_max_mhz", 2070.0)), "MEASURED_PEAKS.json sm_max_mhz"
+    return 2070.0, "nominal"
+
+
+def fp64_peak():
+    """FP64 pipe peak of this device: SMs x maximum SM clock x 2 FP64 FMA per clock per SM
+    x 2 flop (GB300's unit count; the nominal 1.25 TFLOP/s at 152 SMs and 2.07 GHz)."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    mhz, src = _max_sm_mhz()
+    return sms * mhz * 1e6 * 2 * 2 / 1e12, "FP64 pipe: %d SMs x %.0f MHz (%s) x 2 DFMA/clk/SM x 2 flop" % (sms, mhz, src)
 
 class ClockSampler:
     """nvidia-smi clock / throttle samples every 25 ms while running."""
@@ -115,59 +143,87 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+CSRC = os.path.join(ROOT, "paper_1609_04809_gb300", "csrc")
+# the source a kernel's code consists of: (file, function or struct) in order
+KERNEL_PARTS = {
+    "k_dia_sweep": [("sweep.cuh", "pdl_enter"), ("sweep.cuh", "struct Ar<double>"), ("sweep.cuh", "struct Ar<float>"),
+                    ("sweep.cuh", "sweep_out"), ("sweep.cuh", "k_dia_sweep")],
+    "k_coef_sweep": [("sweep.cuh", "pdl_enter"), ("sweep.cuh", "struct Ar<float>"), ("sweep.cuh", "sweep_out"),
+                     ("sweep.cuh", "sweep_out_v"), ("sweep.cuh", "struct CoefView"), ("sweep.cuh", "k_coef_sweep")],
+    "k_outer_resid": [("sweep.cuh", "pdl_enter"), ("kernels.cuh", "block_sum"), ("kernels.cuh", "finish_norm"),
+                      ("kernels.cuh", "fp64_row"), ("kernels.cuh", "fp64_dof"), ("kernels.cuh", "k_outer_resid")],
+}
 SWEEP_KERNELS = {"dia": "k_dia_sweep", "ell": "k_ell_sweep", "csr": "k_csr_sweep", "sell": "k_sell_sweep",
                  "stencil": "k_stencil_sweep", "coef": "k_coef_sweep"}
 
 
-def _kernel_sha(storage, src=None):
-    """sha256[:16] of the sweep kernel of this storage as the compiler sees it: sweep.cuh up
-    to the end of that kernel (its helpers come first), comments and blank lines dropped.
-    src: the header's text (default: the file)."""
-    if src is None:
-        src = open(os.path.join(ROOT, "paper_1609_04809_gb300", "csrc", "sweep.cuh")).read()
-    start = src.index(SWEEP_KERNELS[storage] + "(")
-    end = src.index("\n}\n", start) + 3
-    lines = [ln.split("//")[0].rstrip() for ln in src[:end].splitlines()]
+def _source_part(src, name):
+    """The text of one function (its template line included) or struct of a source file."""
+    if name.startswith("struct "):
+        start = src.index(name + " {")
+        return src[start:src.index("\n};\n", start) + 4]
+    import re
+    m = re.search(r"(^template <[^\n]*\n)?^\S[^\n]*?\b" + re.escape(name) + r"\(", src, re.M)
+    if m is None:
+        raise KeyError(name)
+    return src[m.start():src.index("\n}\n", m.start()) + 3]
+
+
+def _kernel_sha(kernel, sources=None):
+    """sha256[:16] of the code a kernel consists of (KERNEL_PARTS), comments and blank lines
+    dropped. sources: {file: text} (default: the files in csrc/)."""
+    text = []
+    for f, name in KERNEL_PARTS[kernel]:
+        src = sources[f] if sources else open(os.path.join(CSRC, f)).read()
+        text.append(_source_part(src, name))
+    lines = [ln.split("//")[0].rstrip() for ln in "\n".join(text).splitlines()]
     return hashlib.sha256("\n".join(ln for ln in lines if ln.strip()).encode()).hexdigest()[:16]
 
 
-def _traffic_from_profile(kernel_tag, storage):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on the sweep
-    kernel of this storage as it is now."""
-    if storage not in SWEEP_KERNELS:
+def _traffic(tag, kernel, n_dofs):
+    """DRAM bytes per launch of `kernel` from the committed ncu record `tag`, if the record
+    was taken on the kernel's code as it is now; records taken on a smaller case of the
+    workload are scaled to n_dofs rows (the traffic of these passes grows with the rows)."""
+    if kernel not in KERNEL_PARTS:
         return None
-    sha = _kernel_sha(storage)
-    kernel_tag = "%s_%s" % (kernel_tag, storage)
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
+    sha = _kernel_sha(kernel)
     for line in open(path):
         parts = line.split()
-        if len(parts) >= 3 and parts[0] == kernel_tag and parts[1] == sha:
-            return float(parts[2])
+        if len(parts) >= 4 and parts[0] == tag and parts[1] == sha:
+            return float(parts[2]) * n_dofs / float(parts[3])
     return None
 
 
-def roofline_block(precision, name, tflops, gbs, peak_gbs, peak_kind, flops, nbytes, launches, sec, smoother=1,
-                   storage="dia"):
-    """The dominant kernel against the roofline that binds it: the FP64 pipe for the FP64
-    sweep (GB300 issues about 2 DFMA per clock per SM), HBM bandwidth for the FP32 one."""
-    hbm = {"achieved": gbs, "peak": peak_gbs, "unit": "GB/s", "frac": gbs / peak_gbs if gbs else None,
+def kernel_roofline(kclass, precision, storage, workload, n_dofs, ms, cnt, nbytes, flops, peak_gbs, peak_kind,
+                    fp64_tf, fp64_kind):
+    """One kernel class of the finest level against the roofline that binds it: the FP64
+    pipe for FP64 passes (GB300 issues about 2 DFMA per clock per SM, below HBM speed for
+    these passes), HBM bandwidth for the FP32 ones; the HBM fraction is reported beside
+    the FP64 one. ms, cnt: event-timed total and launches; nbytes, flops: algorithmic per
+    launch (mg_profile_read)."""
+    if not cnt:
+        return None
+    sec = ms / cnt * 1e-3
+    gbs = nbytes / sec / 1e9
+    kernel = {"outer": "k_outer_resid", "smooth": SWEEP_KERNELS.get(storage)}.get(kclass)
+    tag = "%s_%s_%s_%s" % (kclass, precision, workload, "dia" if kclass == "outer" else storage)
+    hbm = {"achieved": gbs, "peak": peak_gbs, "unit": "GB/s", "frac": gbs / peak_gbs,
            "peak_kind": "%s HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" % peak_kind}
-    common = {"flops_per_launch": flops, "bytes_per_launch": nbytes, "launches": launches,
-              "us_per_launch": 1e6 * sec if launches else None}
-    if precision == "fp64":
-        out = {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-               "frac": tflops / FP64_PEAK_TFLOPS if tflops else None,
-               "traffic": _traffic_from_profile("smooth_fp64_%s" % name, storage) if smoother != 2 else None,
-               "kernel": "finest-level smoother sweep (%s), FP64" % SWEEP_TEXT[smoother],
-               "peak_kind": "FP64 pipe: 152 SMs x 2.07 GHz x 2 DFMA/clk/SM x 2 flop (recipe nominal)",
-               "hbm": hbm}
+    what = {"outer": "FP64 outer residual r = b - A x and ||r||^2 (defect correction)",
+            "smooth": "finest-level smoother sweep (%s storage, %s)" % (storage, precision)}[kclass]
+    common = {"kernel": what, "bytes_per_launch": nbytes, "flops_per_launch": flops, "launches": cnt,
+              "us_per_launch": 1e6 * sec, "traffic": _traffic(tag, kernel, n_dofs) if kernel else None,
+              "traffic_record": tag}
+    if precision == "fp64" or kclass == "outer":
+        tf = flops / sec / 1e12
+        out = {"bound": "alu", "achieved": tf, "peak": fp64_tf, "unit": "TFLOP/s", "frac": tf / fp64_tf,
+               "peak_kind": fp64_kind, "hbm": hbm}
     else:
         out = dict(hbm)
-        out.update({"bound": "hbm",
-                    "traffic": _traffic_from_profile("smooth_fp32_%s" % name, storage) if smoother != 2 else None,
-                    "kernel": "finest-level smoother sweep (%s), FP32" % SWEEP_TEXT[smoother]})
+        out["bound"] = "hbm"
     out.update(common)
     return out
 
@@ -196,30 +252,55 @@ def _tail_mode(args):
     return 1 if args.tail == "on" else 2
 
 
-def _config_args(name, smoother="workload"):
-    """The workload's parameters; `smoother` other than "workload" replaces its smoother."""
+def _config_args(name, smoother="workload", cells=None):
+    """The workload's parameters; `smoother` other than "workload" replaces its smoother;
+    `cells` runs the same workload on another grid (levels adjusted so that the coarsest
+    grid keeps its size; used for profiling a smaller case)."""
     from paper_1609_04809_gb300 import workloads as W
     c = dict({**W.CONFIGS, **W.TET_CONFIGS}[name])
     if smoother != "workload":
         c["smoother"] = SMOOTHERS[smoother]
+    if cells and cells != c["n_cells"]:
+        coarse = c["n_cells"] >> (c["n_levels"] - 1)
+        c["n_levels"] = int(round(np.log2(cells / coarse))) + 1
+        c["n_cells"] = cells
     return c
 
 
-def _problem_rhs(c):
-    from paper_1609_04809_gb300 import mg, workloads as W
-    modes = W.manufactured_modes(c["dim"]) if c["rhs"] == "manufactured" else None
-    return mg.mg_load_vector(c["dim"], c["element"], c["n_cells"], modes=modes, f_const=1.0), modes
-
-
-def _oracle_workload(name, smoother="workload"):
-    import oracle
+def _k_field(c):
     from paper_1609_04809_gb300 import workloads as W
-    c = _config_args(name, smoother)
-    O = oracle.Hierarchy(c["dim"], c["element"], c["n_cells"], c["n_levels"],
+    if c.get("k") == "blocks16":
+        return W.k_blocks(c["n_cells"], dim=3, blocks_per_axis=16, seed=20260101)
+    return None
+
+
+def _modes(c):
+    from paper_1609_04809_gb300 import workloads as W
+    return W.manufactured_modes(c["dim"]) if c["rhs"] == "manufactured" else None
+
+
+def _problem_rhs(c):
+    from paper_1609_04809_gb300 import mg
+    return mg.mg_load_vector(c["dim"], c["element"], c["n_cells"], modes=_modes(c), f_const=1.0)
+
+
+def _hierarchy(c, precision, args=None):
+    from paper_1609_04809_gb300 import mg
+    kw = {}
+    if args is not None:
+        kw = dict(use_pdl=0 if args.no_pdl else 1, coarse_tail=_tail_mode(args), storage=STORAGES[args.storage])
+    return mg.Hierarchy(c["dim"], c["element"], c["n_cells"], c["n_levels"], k_cell=_k_field(c),
+                        smoother=c["smoother"], omega=c["omega"], cheb_degree=c["cheb_degree"], nu_pre=c["nu_pre"],
+                        nu_post=c["nu_post"], precision=mg.MG_MIXED if precision == "mixed" else mg.MG_FP64, **kw)
+
+
+def _oracle_workload(name, smoother="workload", cells=None):
+    import oracle
+    c = _config_args(name, smoother, cells)
+    O = oracle.Hierarchy(c["dim"], c["element"], c["n_cells"], c["n_levels"], k_cell=_k_field(c),
                          opts=oracle.Options(smoother=c["smoother"], omega=c["omega"], cheb_degree=c["cheb_degree"],
                                              nu_pre=c["nu_pre"], nu_post=c["nu_post"]))
-    modes = W.manufactured_modes(c["dim"]) if c["rhs"] == "manufactured" else None
-    b = oracle.load_vector(c["dim"], c["element"], c["n_cells"], modes=modes)
+    b = oracle.load_vector(c["dim"], c["element"], c["n_cells"], modes=_modes(c))
     return O, O.A(c["n_levels"] - 1), b
 
 
@@ -230,15 +311,47 @@ def _oracle_step(O, A, b, x):
     return x + O.vcycle(r)
 
 
-def cpu_baseline(name, cycles, smoother="workload"):
-    """The oracle (single-threaded C, FP64) on the same workload: setup, then `cycles` timed iterations."""
-    O, A, b = _oracle_workload(name, smoother)
-    x = np.zeros(O.n)
+def _host_cpu():
+    model = None
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith(("model name", "cpu model")):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    if model is None:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for ln in out.splitlines():
+                if ln.startswith("Model name"):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+        except (OSError, subprocess.SubprocessError):
+            pass
+    return {"nproc": os.cpu_count(), "model": model}
+
+
+def cpu_baseline(name, cycles_all=3, cycles_one=1, smoother="workload"):
+    """The oracle (plain FP64 C; row loops on OpenMP threads) on the same workload: setup
+    (not timed), then `cycles_all` defect-correction iterations on all host cores and
+    `cycles_one` on one core."""
+    import oracle
     t0 = time.perf_counter()
-    for _ in range(cycles):
-        x = _oracle_step(O, A, b, x)
-    dt = time.perf_counter() - t0
-    return O.n * cycles / dt, dt
+    O, A, b = _oracle_workload(name, smoother)
+    setup = time.perf_counter() - t0
+    cores = os.cpu_count() or 1
+    out = {}
+    for tag, th, cyc in (("all", cores, cycles_all), ("one", 1, cycles_one)):
+        oracle.set_threads(th)
+        x = np.zeros(O.n)
+        t0 = time.perf_counter()
+        for _ in range(cyc):
+            x = _oracle_step(O, A, b, x)
+        dt = time.perf_counter() - t0
+        out[tag] = (O.n * cyc / dt, dt, th, cyc)
+    oracle.set_threads(cores)
+    return out, setup
 
 
 def serve_bench(args):
@@ -362,25 +475,30 @@ def heat_report(n_cells=128, n_levels=6, dt=0.01, t_end=5.0, smoother=1, nu=1, t
     return out
 
 
-def config_report(name, steps=20, warmup=5, smoother="workload"):
+def oracle_solution_error(name, x_gpu, tol):
+    """||x - x_oracle|| / ||x_oracle|| for a GPU solution of workload `name`, the oracle
+    solving the same problem (its own matrix and right-hand side) to `tol` in FP64."""
+    O, A, b = _oracle_workload(name)
+    xo, ho, ito, conv = O.solve(b, tol)
+    return float(np.linalg.norm(x_gpu - xo) / np.linalg.norm(xo)), int(ito), bool(conv)
+
+
+def config_report(name, steps=20, warmup=5, smoother="workload", oracle_error=False):
     """One workload in both precisions: V-cycle throughput, the finest sweep against its
-    roofline, and time to 1e-10 (median of 3 solves)."""
+    roofline, and time to 1e-10 (median of 3 solves); with oracle_error, the distance of
+    each precision's solution to the oracle's."""
     import torch
 
-    from paper_1609_04809_gb300 import mg, workloads as W
+    from paper_1609_04809_gb300 import mg
     c = _config_args(name, smoother)
-    k = W.k_blocks(c["n_cells"], dim=3, blocks_per_axis=16, seed=20260101) if c.get("k") == "blocks16" else None
-    modes = W.manufactured_modes(c["dim"]) if c["rhs"] == "manufactured" else None
-    b = mg.mg_load_vector(c["dim"], c["element"], c["n_cells"], modes=modes, f_const=1.0)
+    b = _problem_rhs(c)
     bd = torch.from_numpy(b).cuda()
     out = {"workload": name, "smoother": [k for k, v in SMOOTHERS.items() if v == c["smoother"]][0],
            "n_dofs": int(b.size)}
     peak, _ = _peaks()
     for prec, tag in ((mg.MG_FP64, "fp64"), (mg.MG_MIXED, "mixed")):
         t0 = time.perf_counter()
-        H = mg.Hierarchy(c["dim"], c["element"], c["n_cells"], c["n_levels"], k_cell=k, smoother=c["smoother"],
-                         omega=c["omega"], cheb_degree=c["cheb_degree"], nu_pre=c["nu_pre"], nu_post=c["nu_post"],
-                         precision=prec)
+        H = _hierarchy(c, tag)
         setup_s = time.perf_counter() - t0
         info = H.info()
         Lf = c["n_levels"] - 1
@@ -407,6 +525,7 @@ def config_report(name, steps=20, warmup=5, smoother="workload"):
             its, rel = it, hist[-1]
         rd = torch.empty_like(bd)
         true_rel = mg.mg_residual_norm_noalloc(H.h, bd, x, rd) / float(np.linalg.norm(b))
+        err = oracle_solution_error(name, x.cpu().numpy(), c["tol"]) if oracle_error else None
         pcg = None
         if c["nu_pre"] == c["nu_post"]:
             pts, pits = [], 0
@@ -433,8 +552,11 @@ def config_report(name, steps=20, warmup=5, smoother="workload"):
                     "finest_sweep_fp64_tflops": k_flops / ks / 1e12 if (ks and tag == "fp64") else None,
                     "time_to_tol_ms": 1e3 * float(np.median(ts[1:])), "iterations": its,
                     "final_rel_residual": rel, "true_fp64_rel_residual": true_rel,
-                    "storage": STORAGE_NAMES[info["storage"][Lf]], "setup_s": setup_s,
+                    "storage": [STORAGE_NAMES[v] for v in info["storage"]], "setup_s": setup_s,
                     "device_gb": info["device_bytes"] / 1e9, "tail_levels": info["tail_levels"], "pcg": pcg}
+        if err is not None:
+            out[tag]["rel_error_vs_oracle"] = err[0]
+            out[tag]["oracle_iterations"] = err[1]
         H.close()
         del H
         torch.cuda.empty_cache()
@@ -443,16 +565,19 @@ def config_report(name, steps=20, warmup=5, smoother="workload"):
 
 
 def run_reference(args):
+    """The reference arm: the oracle, as it stands, on all host cores, on the bench's
+    workload: setup (not timed), W warm-up and K timed defect-correction iterations."""
     rank = _env_int("RANK", 0)
     if rank != 0:
         return 0
     import oracle
     oracle.build()
     name = args.config
-    O, A, b = _oracle_workload(name, args.smoother)
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    O, A, b = _oracle_workload(name, args.smoother, args.cells)
     x = np.zeros(O.n)
-    # a bounded sample: at most 32 timed iterations (about 8 s on one Grace core at 128^3)
-    steps, warm = min(args.steps, 32), min(args.warmup, 2)
+    steps, warm = args.steps, min(args.warmup, 3)
     for _ in range(warm):
         x = _oracle_step(O, A, b, x)
     t0 = time.perf_counter()
@@ -460,22 +585,43 @@ def run_reference(args):
         x = _oracle_step(O, A, b, x)
     dt = time.perf_counter() - t0
     val = O.n * steps / dt
-    sample = ("%d defect-correction iterations (FP64 residual + V-cycle + update) of the %s workload "
-              "(%d requested; at most 32 are timed), oracle setup excluded" % (steps, name, args.steps))
+    cpu = _host_cpu()
+    sample = ("%d defect-correction iterations (FP64 residual + V-cycle + update) of the %s workload after %d "
+              "warm-up iterations, oracle setup excluded; plain FP64 C with its row loops on %d OpenMP threads (%s)"
+              % (steps, name, warm, cores, cpu["model"]))
+    c = _config_args(name, args.smoother, args.cells)
     out = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic", "config": {"workload": name, "description": WORKLOADS.get(name, name)},
-           "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "data": "synthetic", "config": {"workload": name, "description": WORKLOADS.get(name, name),
+                                           "n_dofs": int(O.n), "n_cells": c["n_cells"]},
+           "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                            "host": cpu},
            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
     return 0
 
 
+def _class_totals(h, kclasses, levels):
+    """(ms, launches, bytes per launch, flops per launch) summed over the given levels."""
+    from paper_1609_04809_gb300 import mg
+    out = {}
+    for kc in kclasses:
+        tot = [0.0, 0, 0.0, 0.0]
+        for l in levels:
+            ms, cnt, by, fl = mg.mg_profile_read(h, kc, l)
+            tot[0] += ms
+            tot[1] += cnt
+            if cnt:
+                tot[2], tot[3] = by, fl
+        out[kc] = tot
+    return out
+
+
 def run_ours(args):
     import torch
 
-    from paper_1609_04809_gb300 import mg, workloads as W
+    from paper_1609_04809_gb300 import mg
     import __graft_entry__
 
     world = _env_int("WORLD_SIZE", 1)
@@ -492,16 +638,16 @@ def run_ours(args):
         dist.barrier()
 
     name = args.config
-    c = _config_args(name, args.smoother)
-    b_host, modes = _problem_rhs(c)
+    c = _config_args(name, args.smoother, args.cells)
+    precision = c["precision"] if args.precision == "workload" else args.precision
+    b_host = _problem_rhs(c)
     n = b_host.size
-    H = mg.Hierarchy(c["dim"], c["element"], c["n_cells"], c["n_levels"], smoother=c["smoother"],
-                     omega=c["omega"], cheb_degree=c["cheb_degree"], nu_pre=c["nu_pre"], nu_post=c["nu_post"],
-                     precision=mg.MG_MIXED if args.precision == "mixed" else mg.MG_FP64,
-                     use_pdl=0 if args.no_pdl else 1, coarse_tail=_tail_mode(args),
-                     storage=STORAGES[args.storage])
+    t0 = time.perf_counter()
+    H = _hierarchy(c, precision, args)
+    setup_s = time.perf_counter() - t0
     info = H.info()
     Lf = c["n_levels"] - 1
+    storage = STORAGE_NAMES[info["storage"][Lf]]
     bd = torch.from_numpy(b_host).cuda()
     xd = torch.zeros_like(bd)
     stream = torch.cuda.current_stream()
@@ -509,7 +655,9 @@ def run_ours(args):
     # warm-up steps
     H.cycle(bd, xd, args.warmup)
     torch.cuda.synchronize()
-    mg.mg_profile_enable(H.h, True, classes=[mg.MG_K_SMOOTH], levels=[Lf])  # the dominant kernel only
+    # the finest level's dominant kernels, timed by events around each of their launches
+    timed_classes = [mg.MG_K_OUTER, mg.MG_K_SMOOTH]
+    mg.mg_profile_enable(H.h, True, classes=timed_classes, levels=[Lf])
     xd.zero_()
     torch.cuda.synchronize()
     if dist:
@@ -525,111 +673,165 @@ def run_ours(args):
         dist.barrier()
     ms = e0.elapsed_time(e1)
     value, ms_max = replica_throughput(ms, n, args.steps, world, dist, device="cuda")
-
-    # dominant kernel: finest-level smoother sweep
-    k_ms, k_cnt, k_bytes, k_flops = mg.mg_profile_read(H.h, mg.MG_K_SMOOTH, Lf)
+    ms_step = ms_max / args.steps
+    timed = _class_totals(H.h, timed_classes, [Lf])
     mg.mg_profile_enable(H.h, False)
-    # per-class device time of one step, from a separate profiled pass over every launch
+
+    # a separate instrumented pass over every launch of 5 steps: per-class device time and
+    # the algorithmic bytes of every launch (events around each launch serialise the graph,
+    # so these times add up to more than the step; they are reported as shares too)
     mg.mg_profile_enable(H.h, True)
     xk = torch.zeros_like(bd)
     H.cycle(bd, xk, 5)
-    per_kernel = {}
+    inst = _class_totals(H.h, range(mg.MG_K_COUNT), range(c["n_levels"]))
+    step_bytes = 0.0
     for kc in range(mg.MG_K_COUNT):
-        tot = sum(mg.mg_profile_read(H.h, kc, l)[0] for l in range(c["n_levels"]))
-        per_kernel[mg.KCLASS_NAMES[kc]] = round(tot / 5, 4)
+        for l in range(c["n_levels"]):
+            ms_l, cnt_l, by_l, _ = mg.mg_profile_read(H.h, kc, l)
+            step_bytes += by_l * cnt_l / 5.0
     mg.mg_profile_enable(H.h, False)
+    inst_ms = {mg.KCLASS_NAMES[kc]: inst[kc][0] / 5.0 for kc in inst}
+    inst_total = sum(inst_ms.values())
+    kernel_ms = {"instrumented": {k: round(v, 4) for k, v in inst_ms.items()},
+                 "share": {k: round(v / inst_total, 4) for k, v in inst_ms.items()} if inst_total else None,
+                 "scaled_to_step": {k: round(v / inst_total * ms_step, 4) for k, v in inst_ms.items()}
+                 if inst_total else None,
+                 "note": "instrumented: events around every launch of 5 steps (serialised, so the sum exceeds "
+                         "ms_per_step); scaled_to_step: the shares applied to ms_per_step"}
     peak, peak_kind = _peaks()
-    k_s = k_ms / k_cnt * 1e-3 if k_cnt else None
-    achieved = k_bytes / k_s / 1e9 if k_cnt else None
-    fp64_tflops = k_flops / k_s / 1e12 if k_cnt else None
+    fp64_tf, fp64_kind = fp64_peak()
+    roofs = {}
+    for kc, key in ((mg.MG_K_OUTER, "outer"), (mg.MG_K_SMOOTH, "smooth")):
+        t_ms, cnt, by, fl = timed[kc]
+        r = kernel_roofline(key, precision, storage, name if not args.cells else "%s_cells%d" % (name, c["n_cells"]),
+                            n, t_ms, cnt, by, fl, peak, peak_kind, fp64_tf, fp64_kind)
+        if r:
+            r["ms_per_step"] = t_ms / args.steps
+            roofs[key] = r
+    dominant = max(roofs, key=lambda k: roofs[k]["ms_per_step"]) if roofs else None
+    whole = {"bytes_per_step": step_bytes, "achieved": step_bytes / (ms_step * 1e-3) / 1e9, "peak": peak,
+             "unit": "GB/s", "frac": step_bytes / (ms_step * 1e-3) / 1e9 / peak,
+             "note": "algorithmic bytes of every launch of one step (all levels, the FP64 outer residual and "
+                     "the update included) over the timed ms_per_step"}
 
     out = None
     if rank == 0:
+        tol = c["tol"]
         # end to end through the public host API: full solves from pinned host memory
         bh = torch.from_numpy(b_host).pin_memory()
         xh = torch.zeros(n, dtype=torch.float64).pin_memory()
-        tol = c["tol"]
-        mg.mg_solve_host(H.h, bh.numpy(), xh.numpy(), tol)  # warm
-        e2e_runs, e2e_iters = [], 0
         e2e = None
-        for _ in range(args.e2e_solves):
-            xh.zero_()
-            t0 = time.perf_counter()
-            st, it, hist = mg.mg_solve_host(H.h, bh.numpy(), xh.numpy(), tol)
-            e2e_runs.append(time.perf_counter() - t0)
-            e2e_iters = it
-        e2e_t = float(np.median(e2e_runs)) if e2e_runs else None
-        e2e = None if not e2e_runs else {"value": n * e2e_iters / e2e_t, "unit": UNIT, "h2d_bytes_per_step": 16 * n, "d2h_bytes_per_step": 8 * n,
-               "step": "one mg_solve_host call to rel. residual %g (%d V-cycles, %.3f ms)" % (tol, e2e_iters, 1e3 * e2e_t)}
+        if args.e2e_solves > 0:
+            mg.mg_solve_host(H.h, bh.numpy(), xh.numpy(), tol)  # warm
+            e2e_runs, e2e_iters = [], 0
+            for _ in range(args.e2e_solves):
+                xh.zero_()
+                t0 = time.perf_counter()
+                st, it, hist = mg.mg_solve_host(H.h, bh.numpy(), xh.numpy(), tol)
+                e2e_runs.append(time.perf_counter() - t0)
+                e2e_iters = it
+            e2e_t = float(np.median(e2e_runs))
+            e2e = {"value": n * e2e_iters / e2e_t, "unit": UNIT, "h2d_bytes_per_step": 16 * n,
+                   "d2h_bytes_per_step": 8 * n,
+                   "step": "one mg_solve_host call to rel. residual %g (%d V-cycles, %.3f ms)"
+                           % (tol, e2e_iters, 1e3 * e2e_t)}
 
-        # time to solution, FP64 vs mixed
+        # time to solution on the same inputs: this precision and the other one, defect
+        # correction and CG
         tts = None
-        if not args.no_mixed:
+        if not args.no_tts:
             def solve_time(h, fn=mg.mg_solve):
                 x = torch.zeros_like(bd)
-                fn(h.h, bd, x, tol, 100)
+                fn(h.h, bd, x, tol, 200)
                 ts = []
                 for _ in range(3):
                     x.zero_()
                     torch.cuda.synchronize()
                     s0 = time.perf_counter()
-                    st, it, hist = fn(h.h, bd, x, tol, 100)
+                    st, it, hist = fn(h.h, bd, x, tol, 200)
                     ts.append(time.perf_counter() - s0)
-                return float(np.median(ts)), it, hist[-1]
-            t64, it64, r64 = solve_time(H)
-            p64, pit64, _ = solve_time(H, mg.mg_pcg)
-            Hm = mg.Hierarchy(c["dim"], c["element"], c["n_cells"], c["n_levels"], smoother=c["smoother"],
-                              omega=c["omega"], cheb_degree=c["cheb_degree"], nu_pre=c["nu_pre"],
-                              nu_post=c["nu_post"], precision=mg.MG_MIXED, use_pdl=0 if args.no_pdl else 1,
-                              coarse_tail=_tail_mode(args), storage=STORAGES[args.storage])
-            t32, it32, r32 = solve_time(Hm)
-            p32, pit32, _ = solve_time(Hm, mg.mg_pcg)
-            tts = {"tol": tol, "fp64_ms": 1e3 * t64, "fp64_iters": it64, "mixed_ms": 1e3 * t32, "mixed_iters": it32,
-                   "mixed_final_rel_residual": r32, "speedup_mixed_vs_fp64": t64 / t32,
-                   "pcg": {"fp64_ms": 1e3 * p64, "fp64_iters": pit64, "mixed_ms": 1e3 * p32, "mixed_iters": pit32,
-                           "method": "CG preconditioned by one V-cycle (mg_pcg)"}}
-            Hm.close()
+                rd = torch.empty_like(bd)
+                true_rel = mg.mg_residual_norm_noalloc(h.h, bd, x, rd) / float(np.linalg.norm(b_host))
+                return float(np.median(ts)), it, true_rel
+            other = "fp64" if precision == "mixed" else "mixed"
+            Ho = _hierarchy(c, other, args)
+            res = {}
+            for tag, h in ((precision, H), (other, Ho)):
+                t_dc, it_dc, r_dc = solve_time(h)
+                t_cg, it_cg, r_cg = solve_time(h, mg.mg_pcg) if c["nu_pre"] == c["nu_post"] else (None, None, None)
+                res[tag] = {"ms": 1e3 * t_dc, "iters": it_dc, "true_fp64_rel_residual": r_dc,
+                            "pcg_ms": 1e3 * t_cg if t_cg else None, "pcg_iters": it_cg,
+                            "pcg_true_fp64_rel_residual": r_cg}
+            Ho.close()
+            del Ho
+            torch.cuda.empty_cache()
+            tts = {"tol": tol, "fp64": res["fp64"], "mixed": res["mixed"],
+                   "speedup_mixed_vs_fp64": res["fp64"]["ms"] / res["mixed"]["ms"],
+                   "speedup_mixed_vs_fp64_pcg": (res["fp64"]["pcg_ms"] / res["mixed"]["pcg_ms"]
+                                                 if res["mixed"]["pcg_ms"] else None),
+                   "method": "defect correction with V-cycles (mg_solve); pcg: CG preconditioned by one V-cycle "
+                             "(mg_pcg); true_fp64_rel_residual recomputed in FP64 after the solve"}
+
+        H.close()
+        torch.cuda.empty_cache()
+        configs = None
+        if world == 1 and not args.no_configs:
+            configs = {}
+            for other_name in ("q1_3d_128_cheb",):
+                if other_name != name:
+                    configs[other_name] = config_report(other_name)
+                    torch.cuda.empty_cache()
 
         heat = None
         if world == 1 and not args.no_heat:
-            H.close()
-            torch.cuda.empty_cache()
             heat = heat_report(methods=("dc", "pcg"), precisions=("fp64", "mixed"))
 
         serving = None
         if world == 1 and args.serve_requests > 0:
-            H.close()
-            torch.cuda.empty_cache()
             serving = serve_bench(args)
 
         cpu = None
         if world == 1 and not args.no_cpu:
-            cv, cdt = cpu_baseline(name, args.cpu_cycles, args.smoother)
-            cpu = {"value": cv, "unit": UNIT, "cores": 1, "kind": "oracle",
-                   "sample": "%d defect-correction iterations of the %s workload by the single-threaded FP64 "
-                             "C oracle (setup excluded, %.1f s)" % (args.cpu_cycles, name, cdt)}
+            res, osetup = cpu_baseline(name, args.cpu_cycles, 1, args.smoother)
+            host = _host_cpu()
+            va, dta, tha, cya = res["all"]
+            v1, dt1, _, cy1 = res["one"]
+            cpu = {"value": va, "unit": UNIT, "cores": tha, "kind": "oracle",
+                   "sample": "%d defect-correction iterations of the %s workload by the FP64 C oracle with its row "
+                             "loops on %d OpenMP threads (%.1f s; oracle setup %.1f s, not timed)"
+                             % (cya, name, tha, dta, osetup),
+                   "single_core": {"value": v1, "unit": UNIT, "cores": 1,
+                                   "sample": "%d iteration on one thread (%.1f s)" % (cy1, dt1)},
+                   "host": host}
 
         clocks = clk.summary()
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-               "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+               "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None,
-               "dtype": "f64" if args.precision == "fp64" else "f32 V-cycle / f64 outer", "data": "synthetic",
+               "dtype": "f64" if precision == "fp64" else "f32 V-cycle / f64 outer", "data": "synthetic",
                "config": {"workload": name, "description": WORKLOADS.get(name, name), "n_dofs": n,
+                          "n_cells": c["n_cells"], "precision": precision,
                           "parallelism": "replicas" if world > 1 else "single-gpu",
                           "l2": "inputs larger than L2 (finest FP64 matrix %.0f MB > 129 MB L2)"
                                 % (info["nnz"][Lf] * 8 / 1e6),
-                          "storage": STORAGE_NAMES[info["storage"][Lf]],
-                          "smoother": [k for k, v in SMOOTHERS.items() if v == c["smoother"]][0]},
-               "roofline": roofline_block(args.precision, name, fp64_tflops, achieved, peak, peak_kind, k_flops,
-                                          k_bytes, k_cnt, k_s, c["smoother"], STORAGE_NAMES[info["storage"][Lf]]),
-               "kernel_ms_per_step": per_kernel,
+                          "storage": [STORAGE_NAMES[v] for v in info["storage"]],
+                          "smoother": [k for k, v in SMOOTHERS.items() if v == c["smoother"]][0],
+                          "setup_s": setup_s,
+                          "headline": "the largest single-GPU workload, in the precision it specifies"
+                                      if name == DEFAULT_CONFIG else "chosen by --config"},
+               "roofline": roofs.get(dominant),
+               "roofline_kernels": roofs,
+               "whole_cycle": whole,
+               "kernel_ms_per_step": kernel_ms,
                "e2e": e2e, "time_to_solution": tts, "cpu_baseline": cpu,
                "gpu_launches": info["kernels_per_cycle"] * args.steps + 1,
+               "configs": configs,
                "heat": heat,
                "serving": serving,
                "clocks": clocks}
         print(json.dumps(out))
-    H.close()
+    else:
+        H.close()
     if dist:
         dist.barrier()
         dist.destroy_process_group()
@@ -642,11 +844,14 @@ def main():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="q1_3d_128_cheb", choices=sorted(WORKLOADS))
+    ap.add_argument("--config", default=DEFAULT_CONFIG, choices=sorted(WORKLOADS))
+    ap.add_argument("--cells", type=int, default=None,
+                    help="run the workload on another grid (profiling a smaller case; not a bench line)")
     ap.add_argument("--e2e-solves", type=int, default=3)
-    ap.add_argument("--cpu-cycles", type=int, default=8)
+    ap.add_argument("--cpu-cycles", type=int, default=3)
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-tts", action="store_true", help="skip the time-to-solution comparison")
+    ap.add_argument("--no-configs", action="store_true", help="skip the nested 128^3 workload")
     ap.add_argument("--no-heat", action="store_true", help="skip the Crank-Nicolson heat workload")
     ap.add_argument("--serve-requests", type=int, default=4096)
     ap.add_argument("--serve-capacity-requests", type=int, default=1024)
@@ -663,9 +868,10 @@ def main():
     ap.add_argument("--smoother", default="workload", choices=["workload"] + sorted(SMOOTHERS),
                     help="replace the workload's smoother (the headline uses the workload's own)")
     ap.add_argument("--all-configs", action="store_true",
-                    help="report every solve workload (FP64 and mixed) instead of the bench line")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
-                    help="fp64: the workload as specified (headline); mixed: FP32 V-cycle, for analysis")
+                    help="report every solve workload (FP64 and mixed, with the distance to the oracle's "
+                         "solution) instead of the bench line")
+    ap.add_argument("--precision", default="workload", choices=["workload", "fp64", "mixed"],
+                    help="workload: the precision the workload specifies (headline); fp64 / mixed for analysis")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -679,7 +885,7 @@ def main():
         torch.cuda.set_device(0)
         from paper_1609_04809_gb300 import workloads as W
         for name in list(W.CONFIGS) + list(W.TET_CONFIGS):
-            print(json.dumps(config_report(name, smoother=args.smoother)), flush=True)
+            print(json.dumps(config_report(name, smoother=args.smoother, oracle_error=not args.no_cpu)), flush=True)
         if not args.no_heat:
             print(json.dumps(heat_report()), flush=True)
             # the paper's own configuration: P1 tetrahedra, Gauss-Seidel with three sweeps

@@ -49,7 +49,7 @@ def build(force=False):
             and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
         return _LIB
     tmp = _LIB + ".tmp%d" % os.getpid()
-    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC",
            "-shared", "-o", tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB)
@@ -113,6 +113,8 @@ def lib():
         L.orc_colour.restype = ctypes.c_int
         L.orc_colour.argtypes = [ctypes.c_int] * 3 + [ctypes.c_int64]
         L.orc_gs_sweep.argtypes = [P(_CSR), dp, ip, ctypes.c_int, ctypes.c_int, dp, dp]
+        L.orc_set_threads.argtypes = [ctypes.c_int]
+        L.orc_get_threads.restype = ctypes.c_int
         L.orc_power_lambda.restype = ctypes.c_double
         L.orc_power_lambda.argtypes = [P(_CSR), dp, ctypes.c_int, ctypes.c_uint64]
         _lib = L
@@ -151,6 +153,15 @@ class CSR:
 
     def dense(self):
         return self.to_scipy().toarray()
+
+
+def set_threads(n):
+    """Threads of the oracle's row loops (the results do not depend on it)."""
+    lib().orc_set_threads(int(n))
+
+
+def get_threads():
+    return int(lib().orc_get_threads())
 
 
 def ndofs(dim, elem, N):

@@ -13,9 +13,14 @@
  * (V-Cycle)"): pre-smoothing, restriction of the residual, recursion down to an exact
  * coarsest solve, prolongation and correction, post-smoothing.
  *
- * Build: gcc -O2 -std=c11 -ffp-contract=off -fPIC -shared mg_oracle.c -lm
+ * Build: gcc -O2 -std=c11 -ffp-contract=off -fopenmp -fPIC -shared mg_oracle.c -lm
  * (-ffp-contract=off keeps every a*b+c as a rounded product followed by a rounded
  * sum, on x86 and on Arm alike.)
+ *
+ * Threads: the row loops of the sparse products, the residual, the smoother updates and
+ * the prolongation may run on several OpenMP threads (orc_set_threads). Each row is
+ * still one sequential sum computed by one thread, so the results do not depend on the
+ * thread count; norms, inner products and everything else stay sequential.
  *
  * Floating-point conventions (the reading of every step, in the order evaluated):
  *   y_i = sum_j a_ij x_j           column-ascending, starting from 0.0, each term
@@ -33,6 +38,7 @@
  *   back substitution multiplies by the pivot's reciprocal, 1.0/u_ii.
  */
 #include <math.h>
+#include <omp.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -245,9 +251,10 @@ static int assemble_ref(int dim, int elem, int N, const double *kref, const doub
         return -1;
 
     /* pattern: row i couples to every interior DOF of every cell that contains i */
-    int64_t cells[8], g[8], cand[64];
     for (int pass = 0; pass < 2; pass++) {
+#pragma omp parallel for schedule(static)
         for (int64_t i = 0; i < n; i++) {
+            int64_t cells[8], g[8], cand[64];
             int mc = dof_cells(dim, elem, N, i, cells);
             int m = 0;
             for (int c = 0; c < mc; c++) {
@@ -282,20 +289,29 @@ static int assemble_ref(int dim, int elem, int N, const double *kref, const doub
         }
     }
 
-    /* values: plain element loop, cells in lexicographic order */
+    /* values: a_ij = sum over the cells e that contain DOFs i and j, in lexicographic
+     * (ascending) cell order, of (k_e * hfac) * kref[a][b], a and b the local numbers of i
+     * and j in e. Row i is filled by visiting its cells in ascending order, so every entry
+     * receives its terms in the order of a loop over all cells; rows are independent. */
+    (void)ncells;
     int nloc = elem == ORC_Q1 ? (1 << dim) : 6;
-    for (int64_t e = 0; e < ncells; e++) {
-        int cx = (int)(e % NN), cy = (int)((e / NN) % NN), cz = dim == 3 ? (int)(e / (NN * NN)) : 0;
-        double ke = k_cell ? k_cell[e] : 1.0;
-        double s = ke * hfac;
-        cell_dofs(dim, elem, N, cx, cy, cz, g);
-        for (int a = 0; a < nloc; a++) {
-            if (g[a] < 0)
-                continue;
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; i++) {
+        int64_t cells[8], g[8];
+        int mc = dof_cells(dim, elem, N, i, cells);
+        for (int c = 0; c < mc; c++) {
+            int64_t e = cells[c];
+            int cx = (int)(e % NN), cy = (int)((e / NN) % NN), cz = dim == 3 ? (int)(e / (NN * NN)) : 0;
+            double ke = k_cell ? k_cell[e] : 1.0;
+            double s = ke * hfac;
+            cell_dofs(dim, elem, N, cx, cy, cz, g);
+            int a = 0;
+            while (g[a] != i)
+                a++;
             for (int b = 0; b < nloc; b++) {
                 if (g[b] < 0)
                     continue;
-                int64_t p = find_col(A, g[a], g[b]);
+                int64_t p = find_col(A, i, g[b]);
                 A->val[p] = A->val[p] + s * kref[a * nloc + b];
             }
         }
@@ -632,9 +648,13 @@ int orc_load_vector(int dim, int elem, int N, int nmodes, const double *amp, con
     gauss3(gx, gw);
     int nloc = elem == ORC_Q1 ? (1 << dim) : 6;
     int nqz = dim == 3 ? 3 : 1;
-    for (int64_t i = 0; i < n; i++)
-        b[i] = 0.0;
-    int64_t g[8];
+    /* cell contributions be[e][a] (cells independent), then b_i = the sum of its cells'
+     * contributions in ascending cell order from 0.0 (rows independent): the order of a
+     * loop over the cells adding into b */
+    double *bec = (double *)malloc((size_t)ncells * nloc * sizeof(double));
+    if (!bec)
+        return -1;
+#pragma omp parallel for schedule(static)
     for (int64_t e = 0; e < ncells; e++) {
         int c[3] = {(int)(e % NN), (int)((e / NN) % NN), dim == 3 ? (int)(e / (NN * NN)) : 0};
         double be[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -652,11 +672,25 @@ int orc_load_vector(int dim, int elem, int N, int nmodes, const double *amp, con
                     for (int a = 0; a < nloc; a++)
                         be[a] = be[a] + fw * basis_at(dim, elem, a, xi, rq1_basis);
                 }
-        cell_dofs(dim, elem, N, c[0], c[1], c[2], g);
         for (int a = 0; a < nloc; a++)
-            if (g[a] >= 0)
-                b[g[a]] = b[g[a]] + be[a];
+            bec[e * nloc + a] = be[a];
     }
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; i++) {
+        int64_t cells[8], g[8];
+        int mc = dof_cells(dim, elem, N, i, cells);
+        double bi = 0.0;
+        for (int c = 0; c < mc; c++) {
+            int64_t e = cells[c];
+            cell_dofs(dim, elem, N, (int)(e % NN), (int)((e / NN) % NN), dim == 3 ? (int)(e / (NN * NN)) : 0, g);
+            int a = 0;
+            while (g[a] != i)
+                a++;
+            bi = bi + bec[e * nloc + a];
+        }
+        b[i] = bi;
+    }
+    free(bec);
     return 0;
 }
 
@@ -698,8 +732,13 @@ double orc_l2_error(int dim, int elem, int N, int nmodes, const double *amp, con
 /* Sparse kernels                                                                    */
 /* ------------------------------------------------------------------------------ */
 
+/* threads for the row loops below (results are the same for every count) */
+void orc_set_threads(int n) { omp_set_num_threads(n > 0 ? n : 1); }
+int orc_get_threads(void) { return omp_get_max_threads(); }
+
 void orc_spmv(const orc_csr *A, const double *x, double *y)
 {
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < A->nrows; i++) {
         double s = 0.0;
         for (int64_t k = A->rowptr[i]; k < A->rowptr[i + 1]; k++)
@@ -710,6 +749,7 @@ void orc_spmv(const orc_csr *A, const double *x, double *y)
 
 static void residual(const orc_csr *A, const double *b, const double *x, double *r)
 {
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < A->nrows; i++) {
         double s = 0.0;
         for (int64_t k = A->rowptr[i]; k < A->rowptr[i + 1]; k++)
@@ -1143,6 +1183,7 @@ double orc_power_lambda(const orc_csr *A, const double *dinv, int iters, uint64_
     double lam = 0.0;
     for (int it = 0; it < iters; it++) {
         orc_spmv(A, v, w);
+#pragma omp parallel for schedule(static)
         for (int64_t i = 0; i < n; i++)
             w[i] = dinv[i] * w[i];
         lam = norm2(w, n);
@@ -1381,6 +1422,7 @@ static void smooth(orc_hier *H, const orc_opts *o, int l, const double *b, doubl
     }
     if (o->smoother == 0) {
         residual(A, b, x, r);
+#pragma omp parallel for schedule(static)
         for (int64_t i = 0; i < n; i++)
             t[i] = x[i] + o->omega * (dinv[i] * r[i]);
         memcpy(x, t, (size_t)n * sizeof(double));
@@ -1394,6 +1436,7 @@ static void smooth(orc_hier *H, const orc_opts *o, int l, const double *b, doubl
     double rho0 = 1.0 / sigma;
     residual(A, b, x, r);
     double c0 = 1.0 / theta;
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; i++) {
         d[i] = c0 * (dinv[i] * r[i]);
         x[i] = x[i] + d[i];
@@ -1402,6 +1445,7 @@ static void smooth(orc_hier *H, const orc_opts *o, int l, const double *b, doubl
         residual(A, b, x, r);
         double rho1 = 1.0 / (2.0 * sigma - rho0);
         double c1 = rho1 * rho0, c2 = (2.0 * rho1) / delta;
+#pragma omp parallel for schedule(static)
         for (int64_t i = 0; i < n; i++) {
             d[i] = c1 * d[i] + c2 * (dinv[i] * r[i]);
             x[i] = x[i] + d[i];
@@ -1426,6 +1470,7 @@ static void vcycle(orc_hier *H, const orc_opts *o, int l, const double *b, doubl
     orc_spmv(&H->R[l], H->r[l], bc);
     memset(xc, 0, (size_t)H->A[l - 1].nrows * sizeof(double));
     vcycle(H, o, l - 1, bc, xc);         /* coarse-grid correction */
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; i++) {    /* prolongation and correction */
         double t = 0.0;
         for (int64_t k = H->P[l].rowptr[i]; k < H->P[l].rowptr[i + 1]; k++)
@@ -1474,6 +1519,7 @@ int orc_solve(orc_hier *H, const orc_opts *o, const double *b, double *x, double
         if (k == o->max_iters)
             break;
         orc_vcycle(H, o, r, c);
+#pragma omp parallel for schedule(static)
         for (int64_t i = 0; i < n; i++)
             x[i] = x[i] + c[i];
     }

@@ -1,11 +1,16 @@
-"""Host-side logic of bench.py: the coarse-tail flag and the key that ties a recorded
-DRAM traffic figure to the code of the kernel it was measured on."""
+"""Host-side logic of bench.py: the coarse-tail flag, workload scaling for profiling, and
+the key that ties a recorded DRAM traffic figure to the code of the kernel it was
+measured on."""
 import argparse
 import os
 
 import bench
 
-SWEEP = os.path.join(os.path.dirname(__file__), "..", "paper_1609_04809_gb300", "csrc", "sweep.cuh")
+CSRC = os.path.join(os.path.dirname(__file__), "..", "paper_1609_04809_gb300", "csrc")
+
+
+def _sources():
+    return {f: open(os.path.join(CSRC, f)).read() for f in ("sweep.cuh", "kernels.cuh")}
 
 
 def test_tail_mode():
@@ -21,20 +26,39 @@ def test_storage_names_round_trip():
         assert bench.STORAGE_NAMES[code] == name
 
 
+def test_smaller_case_keeps_the_coarsest_grid():
+    c = bench._config_args("q1_3d_256_vark", cells=128)
+    assert c["n_cells"] == 128 and c["n_levels"] == 6 and c["precision"] == "mixed"
+    assert bench._config_args("q1_3d_256_vark")["n_levels"] == 7
+
+
 def test_kernel_key_follows_the_kernel_code_only():
-    src = open(SWEEP).read()
-    key = bench._kernel_sha("dia", src)
-    assert key == bench._kernel_sha("dia")
+    src = _sources()
+    for kernel in bench.KERNEL_PARTS:
+        key = bench._kernel_sha(kernel, src)
+        assert key == bench._kernel_sha(kernel)
+    key = bench._kernel_sha("k_dia_sweep", src)
+    sweep = src["sweep.cuh"]
     # comments and blank lines do not change it
-    commented = src.replace("__global__ void __launch_bounds__(256) k_dia_sweep",
-                            "// a remark\n\n__global__ void __launch_bounds__(256) k_dia_sweep", 1)
-    assert commented != src and bench._kernel_sha("dia", commented) == key
-    # code after the kernel (another kernel) does not change it
-    later = src.replace("struct StencilView {", "struct StencilView {\n    int unused;", 1)
-    assert later != src and bench._kernel_sha("dia", later) == key
-    # a change inside the kernel does
-    changed = src.replace("if (i >= n) return;\n    constexpr int C = K / 2;",
-                          "if (i >= n) return;\n    constexpr int C = K / 2 + 0;", 1)
-    assert changed != src and bench._kernel_sha("dia", changed) != key
-    # every storage with a sweep kernel has a key
-    assert len({bench._kernel_sha(st, src) for st in bench.SWEEP_KERNELS}) == len(bench.SWEEP_KERNELS)
+    commented = sweep.replace("template <typename T, int K, int MODE>\n__global__ void __launch_bounds__(256) k_dia_sweep",
+                              "// a remark\n\ntemplate <typename T, int K, int MODE>\n"
+                              "__global__ void __launch_bounds__(256) k_dia_sweep", 1)
+    commented = commented.replace("    if (i >= n) return;\n    constexpr int C = K / 2;",
+                                  "    if (i >= n) return;  // past the end\n\n    constexpr int C = K / 2;", 1)
+    assert commented != sweep and bench._kernel_sha("k_dia_sweep", {**src, "sweep.cuh": commented}) == key
+    # code outside the kernel's parts (another kernel) does not change it
+    later = sweep.replace("struct StencilView {", "struct StencilView {\n    int unused;", 1)
+    assert later != sweep and bench._kernel_sha("k_dia_sweep", {**src, "sweep.cuh": later}) == key
+    # a change inside the kernel, or in a helper it calls, does
+    changed = sweep.replace("if (i >= n) return;\n    constexpr int C = K / 2;",
+                            "if (i >= n) return;\n    constexpr int C = K / 2 + 0;", 1)
+    assert changed != sweep and bench._kernel_sha("k_dia_sweep", {**src, "sweep.cuh": changed}) != key
+    helper = sweep.replace("out[i] = A::sub(bi, s);", "out[i] = A::sub(bi, s) + T(0);", 1)
+    assert helper != sweep and bench._kernel_sha("k_dia_sweep", {**src, "sweep.cuh": helper}) != key
+    # the outer residual's key follows kernels.cuh's reduction helpers
+    k = src["kernels.cuh"]
+    red = k.replace("constexpr int kReduceBlocks = 912;", "constexpr int kReduceBlocks = 912; // same", 1)
+    assert bench._kernel_sha("k_outer_resid", {**src, "kernels.cuh": red}) == bench._kernel_sha("k_outer_resid", src)
+    fin = k.replace("*ticket = 0u;", "*ticket = 0u + 0u;", 1)
+    assert fin != k and bench._kernel_sha("k_outer_resid", {**src, "kernels.cuh": fin}) != bench._kernel_sha(
+        "k_outer_resid", src)
