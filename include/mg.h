@@ -355,9 +355,12 @@ mg_status mg_profile_read(const mg_hierarchy *h, int kclass, int level, double *
  *   synchronises it before returning.
  * Limit: n <= 16,777,216 rows (MG_EINVAL with a message beyond it).
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress);
- * make that first call before any stream capture. Every call shares the one array and
- * it keeps the last call's contents: calls that overlap on the GPU (other streams or
- * threads) race on it and must be serialised by the caller. */
+ * make that first call before any stream capture. The address is then kept per device
+ * for the life of the process: after a cudaDeviceReset (or any other end of the device's
+ * primary context) the kept address is stale, so this entry point must not be called on
+ * that device again. Every call shares the one array and it keeps the last call's
+ * contents: calls that overlap on the GPU (other streams or threads) race on it and must
+ * be serialised by the caller. */
 mg_status mg_residual_norm_noalloc(mg_hierarchy *h, const double *b_dev, const double *x_dev, double *r_dev,
                                    double *rnorm);
 

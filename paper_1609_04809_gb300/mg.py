@@ -175,7 +175,10 @@ class TorchDevice:
         self._torch = torch
         self._live = {}
 
+        self.allocations = 0  # calls of the alloc callback
+
         def _alloc(nbytes, ctx):
+            self.allocations += 1
             try:
                 t = torch.empty(int(nbytes), dtype=torch.uint8, device="cuda")
             except Exception:
@@ -393,7 +396,19 @@ def mg_export_operator(h, level, which, precision=MG_FP64):
 
 
 def mg_residual_norm_noalloc(h, b_dev, x_dev, r_dev):
-    """r_dev = b - A x on the finest level and ||r||_2, with no device allocation (see mg.h)."""
+    """r_dev = b - A x on the finest level and ||r||_2, with no device allocation (see mg.h).
+
+    The C entry point cannot check sizes or devices, so the tensors are checked here: each
+    must be a contiguous float64 CUDA tensor of the hierarchy's finest DOF count on the
+    current device (ValueError otherwise, before anything is launched)."""
+    import torch
+    n = mg_get_info(h)["n"][-1]
+    dev = torch.cuda.current_device()
+    for name, t in (("b", b_dev), ("x", x_dev), ("r", r_dev)):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.device.index == dev and t.dtype == torch.float64
+                and t.is_contiguous() and t.numel() == n):
+            raise ValueError("mg_residual_norm_noalloc: %s must be a contiguous float64 CUDA tensor of %d "
+                             "elements on device %d" % (name, n, dev))
     nr = ctypes.c_double(0.0)
     _check(lib().mg_residual_norm_noalloc(h, ctypes.c_void_p(b_dev.data_ptr()), ctypes.c_void_p(x_dev.data_ptr()),
                                           ctypes.c_void_p(r_dev.data_ptr()), ctypes.byref(nr)))

@@ -7,8 +7,9 @@
   * The same 3D workloads in mixed precision: the true FP64 residual, recomputed by the
     oracle from its own matrix, is <= 1e-10 relative; the distance to the oracle's FP64
     solution is checked against the bound stated in the test.
-  * 3D Q1 256^3 with a 16^3-block coefficient field (log10 k ~ U[-2,2]): mixed and
-    plain FP64 GPU solves both reach 1e-10 in the oracle's FP64 residual and agree.
+  * 3D Q1 256^3 with a 16^3-block coefficient field (log10 k ~ U[-2,2]): the FP64 GPU
+    solve against the oracle's as above; the mixed one reaches 1e-10 in the oracle's FP64
+    residual and lies within the stated bound of the oracle's solution.
 """
 import numpy as np
 import pytest
@@ -90,26 +91,39 @@ def test_mixed_workload_reaches_fp64_tolerance(orc, name):
     assert np.linalg.norm(x - xo) <= 1e-9 * np.linalg.norm(xo)
 
 
-def test_variable_coefficient_256_mixed_and_fp64(orc):
+def test_variable_coefficient_256_fp64_and_mixed_against_the_oracle(orc):
+    """The 256^3 workload (k on 16^3-cell blocks, Galerkin levels where the cells straddle
+    the blocks) solved by the oracle and on the GPU. FP64: residual history within 1e-12
+    relative per entry, equal iteration counts, solution within 1e-9 relative (bit for bit
+    expected). Mixed: the oracle's FP64 residual of the GPU solution <= 1e-10 relative and
+    the distance to the oracle's solution within 1e-8 relative (both solutions satisfy the
+    1e-10 residual test; the coefficient jumps of 10^4 make the system far worse
+    conditioned than the constant-coefficient ones, hence the wider bound)."""
     c = W.CONFIGS["q1_3d_256_vark"]
     N = c["n_cells"]
     k = W.k_blocks(N, dim=3, blocks_per_axis=16, seed=20260101)
-    b = orc.load_vector(3, 0, N)
-    res = {}
-    for prec in (mg.MG_MIXED, mg.MG_FP64):
-        H = _setup(c, prec, k=k)
-        info = H.info()
-        st, it, hist, x = _gpu_solve(H, b, c["tol"])
-        assert st == mg.MG_OK, (prec, it, hist[-3:])
-        res[prec] = (x, it)
-        H.close()
-        del H
-        torch.cuda.empty_cache()
+    b = orc.load_vector(3, orc.Q1, N)
+    O = orc.Hierarchy(3, orc.Q1, N, c["n_levels"], k_cell=k,
+                      opts=orc.Options(smoother=c["smoother"], omega=c["omega"], cheb_degree=c["cheb_degree"],
+                                       nu_pre=c["nu_pre"], nu_post=c["nu_post"]))
+    xo, ho, ito, conv = O.solve(b, c["tol"])
+    assert conv
+    H = _setup(c, mg.MG_FP64, k=k)
+    info = H.info()
     assert info["galerkin"][:3] == [1, 1, 0]  # 4^3 and 8^3 cells straddle the 16^3 blocks
-    A = orc.assemble(3, 0, N, k_cell=k)
+    st, it, hist, x = _gpu_solve(H, b, c["tol"])
+    H.close()
+    del H
+    torch.cuda.empty_cache()
+    assert st == mg.MG_OK and it == ito, (it, ito)
+    assert np.all(np.abs(hist - ho) <= 1e-12 * ho), np.max(np.abs(hist - ho) / ho)
+    assert np.linalg.norm(x - xo) <= 1e-9 * np.linalg.norm(xo)
+    assert np.array_equal(x, xo), np.max(np.abs(x - xo))
+    H = _setup(c, mg.MG_MIXED, k=k)
+    st, it, hist, x32 = _gpu_solve(H, b, c["tol"])
+    H.close()
+    assert st == mg.MG_OK
+    A = O.A(c["n_levels"] - 1)
     nb = np.linalg.norm(b)
-    for prec, (x, it) in res.items():
-        r = b - orc.spmv(A, x)
-        assert np.linalg.norm(r) <= c["tol"] * nb, (prec, np.linalg.norm(r) / nb)
-    x32, x64 = res[mg.MG_MIXED][0], res[mg.MG_FP64][0]
-    assert np.linalg.norm(x32 - x64) <= 1e-8 * np.linalg.norm(x64)
+    assert np.linalg.norm(b - orc.spmv(A, x32)) <= c["tol"] * nb
+    assert np.linalg.norm(x32 - xo) <= 1e-8 * np.linalg.norm(xo)
