@@ -406,16 +406,23 @@ def serve_bench(args):
             return time.perf_counter() - start, S.stats(), iters
 
         cap_n = min(args.serve_capacity_requests, len(trace))
-        cap_wall, cap_stats, _ = run(trace[:cap_n], None)
+        cap_wall, cap_stats, cap_iters = run(trace[:cap_n], None)
         capacity = cap_n / cap_wall
+        cap_work = sum(mg.mg_ndofs(r["dim"], 0, r["n_cells"]) * it for r, it in zip(trace[:cap_n], cap_iters))
         rate = 0.7 * capacity
         trace = W.serving_trace(n_requests=args.serve_requests, seed=4096, rate=rate)
         wall, st, iters = run(trace, rate)
         dofs = sum(mg.mg_ndofs(r["dim"], 0, r["n_cells"]) for r in trace)
         return {"requests": len(trace), "tol": tol, "precision": "FP32 V-cycle in FP64 defect correction",
                 "arrival_rate_per_s": rate, "capacity_solves_per_s": capacity,
-                "capacity_sample": cap_n, "solves_per_s": st["solves_per_s"], "p50_ms": st["p50_ms"],
+                "capacity_sample": cap_n,
+                "capacity_dof_vcycles_per_s": cap_work / cap_wall,
+                "capacity_gpu_busy_frac": cap_stats["gpu_ms"] / max(cap_stats["span_ms"], 1e-9),
+                "capacity_mean_batch": cap_stats["mean_batch"],
+                "solves_per_s": st["solves_per_s"], "p50_ms": st["p50_ms"],
                 "p99_ms": st["p99_ms"], "max_ms": st["max_ms"], "mean_batch": st["mean_batch"],
+                "gpu_busy_frac": st["gpu_ms"] / max(st["span_ms"], 1e-9),
+                "setup_busy_frac": st["setup_ms"] / max(st["span_ms"], 1e-9),
                 "iterations_mean": float(np.mean(iters)), "iterations_max": int(np.max(iters)),
                 "dofs_total": int(dofs), "wall_s": wall, "budget_gb": args.serve_budget_gb,
                 "device_bytes_peak": int(st["device_bytes_peak"]), "operator_sets": st["operator_sets"],

@@ -405,6 +405,9 @@ typedef struct {
     double p50_ms, p99_ms, max_ms; /* latency submit -> completion of finished requests */
     double solves_per_s;         /* completed / (last completion - first submission) */
     size_t device_bytes_in_use, device_bytes_peak;
+    double gpu_ms;               /* device time of the batched iterations (CUDA events) */
+    double setup_ms;             /* busy time of the setup thread (operator sets, right-hand sides) */
+    double span_ms;              /* first submission to last completion */
 } mg_serve_stats;
 
 /* Defaults: 4 GiB budget, 256 slots, 4 rows per thread, 4 blocks per SM, Chebyshev

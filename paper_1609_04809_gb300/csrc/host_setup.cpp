@@ -853,17 +853,17 @@ void load_vector(int dim, int elem, int N, const mg_rhs *f, double *b)
 // products of sines (or a constant) the rule splits into one-dimensional sums per mode
 // and axis, b = sum_m c_m X_m (x) Y_m [(x) Z_m], at O(modes * n) cost. Equal to
 // load_vector up to rounding (the sums are grouped differently).
-void load_vector_separable(int dim, int N, const mg_rhs *f, double *b)
+void load_vector_factors(int dim, int N, const mg_rhs *f, std::vector<double> &v, std::vector<double> &c)
 {
-    int64_t n1 = N - 1, n = dim == 2 ? n1 * n1 : n1 * n1 * n1;
+    int64_t n1 = N - 1;
     double h = 1.0 / (double)N;
     double sq = std::sqrt(0.6);
     const double gx[3] = {0.5 - 0.5 * sq, 0.5, 0.5 + 0.5 * sq};
     const double gw[3] = {5.0 / 18.0, 8.0 / 18.0, 5.0 / 18.0};
     int nm = f->n_modes == 0 ? 1 : f->n_modes;
     // v[m][d][i-1]: integral of (sin or 1) times the hat of node i along axis d
-    std::vector<double> v((size_t)nm * 3 * n1);
-    std::vector<double> c(nm);
+    v.assign((size_t)nm * 3 * n1, 0.0);
+    c.assign(nm, 0.0);
     for (int m = 0; m < nm; m++) {
         int ksq = 0;
         if (f->n_modes)
@@ -887,6 +887,14 @@ void load_vector_separable(int dim, int N, const mg_rhs *f, double *b)
             }
         }
     }
+}
+
+void load_vector_separable(int dim, int N, const mg_rhs *f, double *b)
+{
+    int64_t n1 = N - 1, n = dim == 2 ? n1 * n1 : n1 * n1 * n1;
+    std::vector<double> v, c;
+    load_vector_factors(dim, N, f, v, c);
+    int nm = (int)c.size();
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; i++) {
         int64_t ix = i % n1, iy = (i / n1) % n1, iz = dim == 3 ? i / (n1 * n1) : 0;

@@ -46,8 +46,11 @@ bool coarse_coefficient(int dim, int NL, const double *kL, int Nl, std::vector<d
 void load_vector(int dim, int elem, int N, const mg_rhs *f, double *b);
 
 // The Q1 load vector of the same rule, factorised per mode and axis (O(modes * n));
-// equal to load_vector up to rounding.
+// equal to load_vector up to rounding: b_i = sum_m c[m] * ((v[m][0][ix] * v[m][1][iy])
+// [* v[m][2][iz]]) in mode order, each product and sum rounded once.
 void load_vector_separable(int dim, int N, const mg_rhs *f, double *b);
+// Its factors: v (modes x 3 x (N-1), axis-major per mode) and c (modes).
+void load_vector_factors(int dim, int N, const mg_rhs *f, std::vector<double> &v, std::vector<double> &c);
 
 double power_lambda(const Csr &A, const std::vector<double> &dinv, int iters, uint64_t seed);
 

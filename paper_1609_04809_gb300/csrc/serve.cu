@@ -121,11 +121,14 @@ constexpr int SV_MAXK = 21;   // DIA slots of the Q1 stiffness (9 in 2D, 21 in 3
 constexpr int SV_MAXDEG = 4;  // Chebyshev degree supported by the server
 
 struct SvLevel {  // one level of one request, FP32
-    const float *val;
+    const float *val;  // DIA values (nullptr: a constant stencil, values in sv)
     int64_t ld;
     int K, n, N, dim;
     int slot;
     int32_t offs[SV_MAXK];
+    int32_t pos[SV_MAXK];  // stencil: position (dx+1) + 3(dy+1) + 9(dz+1) of each slot
+    float sv[SV_MAXK];     // stencil: the value of each slot
+    float sdinv;           // stencil: 1 / a_ii
     float *x[2];
     float *b, *t, *d;
     float omega, c0;
@@ -198,6 +201,42 @@ __device__ __forceinline__ void sv_sweep_tile(const SvLevel &L, int row0, int in
     for (int r = 0; r < RPT; r++) {
         int i = row0 + r * 256 + threadIdx.x;
         if (i >= L.n) return;
+        if (!L.val) {  // constant stencil: the row's neighbours masked from its coordinates
+            if (IsZero<MODE>::value) {
+                sweep_out<float, MODE>(i, 0.f, L.sdinv, 0.f, L.b, o, L.d, c1, c2);
+                continue;
+            }
+            const int n1 = L.N - 1;
+            const int vx = i % n1, vy = (i / n1) % n1, vz = L.dim == 3 ? i / (n1 * n1) : 0;
+            unsigned mx = 2u | (vx > 0 ? 1u : 0u) | (vx < n1 - 1 ? 4u : 0u);
+            unsigned my = 2u | (vy > 0 ? 1u : 0u) | (vy < n1 - 1 ? 4u : 0u);
+            unsigned m = ((my & 1u) ? mx : 0u) | ((my & 2u) ? mx << 3 : 0u) | ((my & 4u) ? mx << 6 : 0u);
+            if (L.dim == 3) {
+                unsigned mz = 2u | (vz > 0 ? 1u : 0u) | (vz < n1 - 1 ? 4u : 0u);
+                m = ((mz & 1u) ? m : 0u) | ((mz & 2u) ? m << 9 : 0u) | ((mz & 4u) ? m << 18 : 0u);
+            }
+            const int cp = L.dim == 3 ? 13 : 4;  // the centre position
+            float s = 0.f, xi = 0.f;
+            if (L.K == 21) {
+                float xv[21];
+#pragma unroll
+                for (int k = 0; k < 21; k++) xv[k] = __ldg(x + i + L.offs[k]);
+#pragma unroll
+                for (int k = 0; k < 21; k++)
+                    if (L.pos[k] == cp || ((m >> L.pos[k]) & 1u)) s = fmaf(L.sv[k], xv[k], s);
+                xi = xv[10];
+            } else {
+                float xv[9];
+#pragma unroll
+                for (int k = 0; k < 9; k++) xv[k] = __ldg(x + i + L.offs[k]);
+#pragma unroll
+                for (int k = 0; k < 9; k++)
+                    if (L.pos[k] == cp || ((m >> L.pos[k]) & 1u)) s = fmaf(L.sv[k], xv[k], s);
+                xi = xv[4];
+            }
+            sweep_out<float, MODE>(i, s, L.sdinv, xi, L.b, o, L.d, c1, c2);
+            continue;
+        }
         if (IsZero<MODE>::value) {
             float dg = __ldcs(L.val + (int64_t)(L.K / 2) * L.ld + i);
             sweep_out<float, MODE>(i, 0.f, Ar<float>::rcp(dg), 0.f, L.b, o, L.d, c1, c2);
@@ -443,6 +482,28 @@ __global__ void __launch_bounds__(256) k_sv_update(Plan P, int p)
     }
 }
 
+// Right-hand side of a request given by sine modes (mg_serve_submit_rhs), formed on the
+// device from its per-mode, per-axis factors: b_i = sum_m c[m] * ((v[m][0][ix] *
+// v[m][1][iy]) [* v[m][2][iz]]), mode order, every product and sum rounded once (the
+// evaluation of the host's mg_load_vector_separable, so both give the same bits).
+// rv: nm x 3 x n1 factors then nm coefficients.
+__global__ void __launch_bounds__(256) k_sv_rhs(double *__restrict__ b, const double *__restrict__ rv, int nm, int n1,
+                                                int dim, int64_t n)
+{
+    const double *c = rv + (int64_t)nm * 3 * n1;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t ix = i % n1, iy = (i / n1) % n1, iz = dim == 3 ? i / ((int64_t)n1 * n1) : 0;
+        double s = 0.0;
+        for (int m = 0; m < nm; m++) {
+            const double *vm = rv + (int64_t)m * 3 * n1;
+            double t = __dmul_rn(vm[ix], vm[n1 + iy]);
+            if (dim == 3) t = __dmul_rn(t, vm[2 * n1 + iz]);
+            s = __dadd_rn(s, __dmul_rn(c[m], t));
+        }
+        b[i] = s;
+    }
+}
+
 // ------------------------------------------------------------------------------------
 // Host side
 // ------------------------------------------------------------------------------------
@@ -458,6 +519,7 @@ struct Work {  // per-request device workspace (from the arena)
     std::vector<std::pair<void *, size_t>> blocks;
     std::vector<float *> x0, x1, b, t, d;  // per level
     double *x64 = nullptr, *b64 = nullptr;
+    double *rv = nullptr;  // right-hand-side factors (requests given by sine modes)
 };
 
 struct Request {
@@ -478,6 +540,9 @@ struct Request {
     std::vector<double> amp;
     std::vector<int> freq;
     double f_const = 0.0;
+    std::vector<double> rv;  // factors of the right-hand side (load_vector_factors), then c
+    int nm = 0;
+    int outcome = 0;  // after retirement: 1 converged, 2 max_iters reached
 };
 
 }  // namespace
@@ -526,6 +591,12 @@ struct mg_server {
     // statistics
     std::vector<double> latencies_ms;
     uint64_t completed = 0, cycles = 0, batch_sum = 0;
+    double gpu_ms = 0.0, setup_ms = 0.0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // finished requests whose solutions are still on the device: copied back on the copy
+    // stream while the next batched iteration runs
+    cudaStream_t cs = nullptr;
+    std::vector<Request *> draining;
     Clock::time_point t_first_submit, t_last_done;
     bool any_submit = false;
     std::string fatal;
@@ -622,6 +693,10 @@ bool alloc_workspace(mg_server *S, Request *r)
         w.b64 = (double *)take(F.A.ld * 8);
         ok = x && w.b64;
         if (ok) w.x64 = (double *)(x + pad * 8);
+        if (ok && r->has_rhs) {
+            w.rv = (double *)take(r->rv.size() * 8);
+            ok = w.rv != nullptr;
+        }
     }
     if (!ok) {
         for (auto &bl : w.blocks) S->arena.release(bl.first, bl.second);
@@ -676,14 +751,19 @@ void build_plan(mg_server *S, std::vector<SvPhase> &phases, std::vector<int4> &i
         for (int l = 0; l < ops.nlev; l++) {
             const mgi::LevelD &L = h->lev[l];
             SvLevel v{};
-            v.val = (const float *)L.A.val;
+            v.val = L.A.fmt == MG_STORAGE_STENCIL ? nullptr : (const float *)L.A.val;
             v.ld = L.A.ld;
             v.K = L.A.K;
             v.n = (int)L.n;
             v.N = L.N;
             v.dim = ops.dim;
             v.slot = r->slot;
-            for (int k = 0; k < L.A.K && k < SV_MAXK; k++) v.offs[k] = L.A.offs.o[k];
+            for (int k = 0; k < L.A.K && k < SV_MAXK; k++) {
+                v.offs[k] = L.A.offs.o[k];
+                v.pos[k] = L.A.full_of[k];
+                v.sv[k] = (float)L.A.sval[k];
+            }
+            v.sdinv = (float)L.A.sdinv;
             v.x[0] = r->ws.x0[l];
             v.x[1] = r->ws.x1[l];
             v.b = r->ws.b[l];
@@ -896,6 +976,8 @@ void finish_request(mg_server *S, Request *r, mg_status st, const std::string &e
     }
     r->b.clear();
     r->b.shrink_to_fit();
+    r->rv.clear();
+    r->rv.shrink_to_fit();
 }
 
 // device bytes of a Q1 operator set (FP32 level matrices, FP64 finest matrix, LU and
@@ -930,7 +1012,9 @@ OpSet *get_opset(mg_server *S, int dim, int N, int nlev, std::unique_lock<std::m
     mg_problem p{dim, MG_Q1, N, nlev, nullptr};
     mg_options o = S->opt;
     o.precision = MG_MIXED;
-    o.storage = MG_STORAGE_DIA;
+    // FP32 levels of at least 32768 rows as the constant stencil (every request has k = 1),
+    // the smaller ones in DIA: the same storage mg_setup gives MG_STORAGE_STENCIL
+    o.storage = MG_STORAGE_STENCIL;
     o.use_graph = 0;
     mg_device dev{arena_alloc_cb, arena_free_cb, &S->arena, nullptr};
     std::unique_ptr<OpSet> ops(new OpSet());
@@ -979,16 +1063,18 @@ void setup_loop(mg_server *S)
         }
         Request *r = S->setup_q.front();
         S->setup_q.pop_front();
-        if (r->has_rhs) {
+        auto t0 = Clock::now();
+        if (r->has_rhs) {  // the per-mode, per-axis factors; the device forms b at admission
             lk.unlock();
-            mg_problem p{r->dim, MG_Q1, r->N, r->nlev, nullptr};
             mg_rhs f{(int)r->amp.size(), r->amp.data(), r->freq.data(), r->f_const};
-            r->b.resize((size_t)mgh::ndofs(r->dim, MG_Q1, r->N));
-            mgh::load_vector_separable(r->dim, r->N, &f, r->b.data());
-            (void)p;
+            std::vector<double> c;
+            mgh::load_vector_factors(r->dim, r->N, &f, r->rv, c);
+            r->nm = (int)c.size();
+            r->rv.insert(r->rv.end(), c.begin(), c.end());
             lk.lock();
         }
         OpSet *ops = get_opset(S, r->dim, r->N, r->nlev, lk);
+        S->setup_ms += std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
         if (!ops) {
             finish_request(S, r, MG_EBUDGET, "operators do not fit the device budget: " + g_setup_err);
             S->cv_done.notify_all();
@@ -1030,7 +1116,14 @@ void admit(mg_server *S)
             SCK(cudaMemsetAsync((char *)r->ws.x0[l] - pl * 4, 0, (size_t)(L.A.ld + 2 * pl) * 4, S->s));
             SCK(cudaMemsetAsync((char *)r->ws.x1[l] - pl * 4, 0, (size_t)(L.A.ld + 2 * pl) * 4, S->s));
         }
-        SCK(cudaMemcpyAsync(r->ws.b64, r->b.data(), (size_t)n * 8, cudaMemcpyHostToDevice, S->s));
+        if (r->has_rhs) {
+            SCK(cudaMemcpyAsync(r->ws.rv, r->rv.data(), r->rv.size() * 8, cudaMemcpyHostToDevice, S->s));
+            int grid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)S->nsm * 8);
+            k_sv_rhs<<<grid, 256, 0, S->s>>>(r->ws.b64, r->ws.rv, r->nm, F.N - 1, r->dim, n);
+            SCK(cudaGetLastError());
+        } else {
+            SCK(cudaMemcpyAsync(r->ws.b64, r->b.data(), (size_t)n * 8, cudaMemcpyHostToDevice, S->s));
+        }
         SvState init{};
         init.first = 1;
         SCK(cudaMemcpyAsync(&S->d_state[r->slot], &init, sizeof(SvState), cudaMemcpyHostToDevice, S->s));
@@ -1040,6 +1133,8 @@ void admit(mg_server *S)
     if (changed) S->plan_dirty = true;
 }
 
+// requests that met their tolerance (or max_iters) leave the batch: their slots are free
+// at once, their workspaces once their solutions have been copied back (drain)
 void retire(mg_server *S)
 {
     std::vector<Request *> keep;
@@ -1053,27 +1148,46 @@ void retire(mg_server *S)
             keep.push_back(r);
             continue;
         }
-        bool done = st.converged == 1;
-        int64_t n = r->ops->h->A64.n;
-        if ((size_t)n > S->xstage_elems) {
-            if (S->h_xstage) cudaFreeHost(S->h_xstage);
-            SCK(cudaMallocHost(&S->h_xstage, (size_t)n * 8));
-            S->xstage_elems = (size_t)n;
-        }
-        SCK(cudaMemcpyAsync(S->h_xstage, r->ws.x64, (size_t)n * 8, cudaMemcpyDeviceToHost, S->s));
-        SCK(cudaStreamSynchronize(S->s));
-        r->x.assign(S->h_xstage, S->h_xstage + n);
-        free_workspace(S, r);
         S->free_slots.push_back(r->slot);
         r->slot = -1;
-        r->ops->refs--;
-        r->ops->last_use = ++S->clock;
-        finish_request(S, r, done ? MG_OK : MG_ENOCONV, done ? "" : "max_iters reached");
+        r->outcome = st.converged;
+        S->draining.push_back(r);
         changed = true;
     }
     S->active.swap(keep);
-    if (changed) {
-        S->plan_dirty = true;
+    if (changed) S->plan_dirty = true;
+}
+
+// copy the solutions of the retired requests to the host (copy stream, pinned staging),
+// called without the lock while the next iteration runs on the compute stream; the
+// requests' workspaces are not in that iteration's plan
+void drain_copy(mg_server *S, const std::vector<Request *> &batch)
+{
+    for (Request *r : batch) {
+        int64_t n = r->ops->h->A64.n;
+        if ((size_t)n > S->xstage_elems) {
+            if (S->h_xstage) cudaFreeHost(S->h_xstage);
+            S->h_xstage = nullptr;
+            SCK(cudaMallocHost(&S->h_xstage, (size_t)n * 8));
+            S->xstage_elems = (size_t)n;
+        }
+        SCK(cudaMemcpyAsync(S->h_xstage, r->ws.x64, (size_t)n * 8, cudaMemcpyDeviceToHost, S->cs));
+        SCK(cudaStreamSynchronize(S->cs));
+        r->x.assign(S->h_xstage, S->h_xstage + n);
+    }
+}
+
+// with the lock: release the drained requests' workspaces and finish them
+void drain_finish(mg_server *S, const std::vector<Request *> &batch)
+{
+    for (Request *r : batch) {
+        bool done = r->outcome == 1;
+        free_workspace(S, r);
+        r->ops->refs--;
+        r->ops->last_use = ++S->clock;
+        finish_request(S, r, done ? MG_OK : MG_ENOCONV, done ? "" : "max_iters reached");
+    }
+    if (!batch.empty()) {
         S->cv_done.notify_all();
         S->cv_setup.notify_all();
     }
@@ -1086,7 +1200,16 @@ void sched_loop(mg_server *S)
     try {
         while (!S->stop) {
             admit(S);
+            std::vector<Request *> batch;
+            batch.swap(S->draining);
             if (S->active.empty()) {
+                if (!batch.empty()) {  // nothing to overlap with: copy back now
+                    lk.unlock();
+                    drain_copy(S, batch);
+                    lk.lock();
+                    drain_finish(S, batch);
+                    continue;
+                }
                 S->cv_sched.wait_for(lk, std::chrono::milliseconds(50));
                 continue;
             }
@@ -1097,10 +1220,17 @@ void sched_loop(mg_server *S)
             cudaGraphExec_t g = graph_for(S, S->cur_depth);
             // the graph's phase count depends only on the depth; contents come from the plan
             lk.unlock();
+            SCK(cudaEventRecord(S->ev0, S->s));
             SCK(cudaGraphLaunch(g, S->s));
+            SCK(cudaEventRecord(S->ev1, S->s));
             SCK(cudaMemcpyAsync(S->h_state, S->d_state, sizeof(SvState) * S->max_active, cudaMemcpyDeviceToHost, S->s));
+            drain_copy(S, batch);  // overlaps the iteration just launched
             SCK(cudaStreamSynchronize(S->s));
+            float gms = 0.f;
+            SCK(cudaEventElapsedTime(&gms, S->ev0, S->ev1));
             lk.lock();
+            drain_finish(S, batch);
+            S->gpu_ms += gms;
             S->cycles++;
             S->batch_sum += S->active.size();
             retire(S);
@@ -1108,7 +1238,9 @@ void sched_loop(mg_server *S)
     } catch (const Error &e) {
         S->fatal = e.msg;
         for (Request *r : S->active) finish_request(S, r, e.st, e.msg);
+        for (Request *r : S->draining) finish_request(S, r, e.st, e.msg);
         S->active.clear();
+        S->draining.clear();
         S->cv_done.notify_all();
     }
 }
@@ -1163,6 +1295,9 @@ extern "C" mg_status mg_serve_create(const mg_serve_config *cfg, const mg_device
         SCK(cudaGetDevice(&S->device));
         SCK(cudaDeviceGetAttribute(&S->nsm, cudaDevAttrMultiProcessorCount, S->device));
         SCK(cudaStreamCreateWithFlags(&S->s, cudaStreamNonBlocking));
+        SCK(cudaStreamCreateWithFlags(&S->cs, cudaStreamNonBlocking));
+        SCK(cudaEventCreate(&S->ev0));
+        SCK(cudaEventCreate(&S->ev1));
         size_t budget = (size_t)rup((int64_t)cfg->hbm_budget_bytes, 256);
         void *base = nullptr;
         if (S->own_alloc) {
@@ -1379,6 +1514,8 @@ extern "C" mg_status mg_serve_get_stats(mg_server *S, mg_serve_stats *out)
     out->device_bytes_in_use = S->arena.in_use;
     out->device_bytes_peak = S->arena.peak;
     out->operator_sets = (int)S->opsets.size();
+    out->gpu_ms = S->gpu_ms;
+    out->setup_ms = S->setup_ms;
     if (!S->latencies_ms.empty()) {
         std::vector<double> v = S->latencies_ms;
         std::sort(v.begin(), v.end());
@@ -1388,6 +1525,7 @@ extern "C" mg_status mg_serve_get_stats(mg_server *S, mg_serve_stats *out)
         out->max_ms = v.back();
         double span = std::chrono::duration<double>(S->t_last_done - S->t_first_submit).count();
         out->solves_per_s = span > 0 ? (double)S->completed / span : 0.0;
+        out->span_ms = 1e3 * span;
     }
     return MG_OK;
 }
@@ -1401,6 +1539,7 @@ extern "C" mg_status mg_serve_reset_stats(mg_server *S)
     std::lock_guard<std::mutex> lk(S->mu);
     S->latencies_ms.clear();
     S->completed = S->cycles = S->batch_sum = 0;
+    S->gpu_ms = S->setup_ms = 0.0;
     S->any_submit = false;
     S->arena.peak = S->arena.in_use;
     return MG_OK;
@@ -1497,6 +1636,12 @@ extern "C" mg_status mg_serve_destroy(mg_server *S)
         else if (S->dev.free)
             S->dev.free(S->arena.base, S->arena.size, S->dev.ctx);
     }
+    if (S->cs) {
+        cudaStreamSynchronize(S->cs);
+        cudaStreamDestroy(S->cs);
+    }
+    if (S->ev0) cudaEventDestroy(S->ev0);
+    if (S->ev1) cudaEventDestroy(S->ev1);
     if (S->s) cudaStreamDestroy(S->s);
     delete S;
     return MG_OK;

@@ -80,7 +80,8 @@ class mg_serve_stats(ctypes.Structure):
                 ("queued", ctypes.c_int), ("operator_sets", ctypes.c_int), ("mean_batch", ctypes.c_double),
                 ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
                 ("solves_per_s", ctypes.c_double), ("device_bytes_in_use", ctypes.c_size_t),
-                ("device_bytes_peak", ctypes.c_size_t)]
+                ("device_bytes_peak", ctypes.c_size_t), ("gpu_ms", ctypes.c_double), ("setup_ms", ctypes.c_double),
+                ("span_ms", ctypes.c_double)]
 
 
 # every entry point declared in include/mg.h, with its ctypes signature

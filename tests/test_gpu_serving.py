@@ -49,15 +49,19 @@ def _true_rel_residual(dim, N, L, b, x):
 
 
 def test_served_request_equals_single_solve():
+    """Served requests keep the levels of at least 32768 rows as the constant stencil and
+    the smaller ones in DIA, the storage mg_setup gives MG_STORAGE_STENCIL: the same bits
+    as mg_solve with it (2D 256^2 and 3D 64^3 have stencil levels, the others none)."""
     S = mg.Server(2 * GB)
     try:
-        for dim, N, seed in [(3, 32, 1), (2, 128, 2)]:
+        for dim, N, seed in [(3, 32, 1), (2, 128, 2), (2, 256, 3), (3, 64, 4)]:
             L = _levels(dim, N)
             b = _rhs(dim, N, seed)
             st, x, it, hist = S.wait(S.submit(dim, N, L, b, TOL), b.size, hist_len=100)
             assert st == mg.MG_OK
             H = mg.Hierarchy(dim, mg.MG_Q1, N, L, smoother=mg.MG_CHEBYSHEV, nu_pre=1, nu_post=1,
-                             precision=mg.MG_MIXED)
+                             precision=mg.MG_MIXED, storage=mg.MG_STORAGE_STENCIL)
+            assert (mg.MG_STORAGE_STENCIL in H.info()["storage"]) == (b.size >= 32768)
             bd = torch.from_numpy(b).cuda()
             xd = torch.zeros_like(bd)
             st2, it2, hist2 = H.solve(bd, xd, TOL)
