@@ -355,9 +355,12 @@ static void sweep_fmt(const DevMat &A, int n, const T *x, const T *b, T *out, T 
     }
     if (A.fmt == MG_STORAGE_STENCIL && A.elem == MG_RQ1) {
         if constexpr (std::is_same<T, float>::value) {
-            Rq1View S{A.n1 + 1, (float)A.sval[1], (float)A.sdinv};
+            // slabs per thread: up to 8, fewer where the blocks would not give about two
+            // waves of 2048 threads on each of the 152 SMs
             unsigned N = (unsigned)(A.n1 + 1), bx = line_block(N), by = std::min(256u / bx, N);
-            dim3 g((N + bx - 1) / bx, (N + by - 1) / by, 3 * N), blk(bx, by);
+            int cz = (int)std::max<int64_t>(1, std::min<int64_t>(8, 3 * (int64_t)N * N * N / (2 * 2048 * 152)));
+            Rq1View S{A.n1 + 1, (float)A.sval[1], (float)A.sdinv, cz};
+            dim3 g((N + bx - 1) / bx, (N + by - 1) / by, 3 * ((N + cz - 1) / cz)), blk(bx, by);
             klaunch(pdl, k_stencil_rq1<MODE>, g, blk, 0, s, S, x, b, out, d, c1, c2);
             return;
         } else {
@@ -377,16 +380,17 @@ static void sweep_fmt(const DevMat &A, int n, const T *x, const T *b, T *out, T 
         dim3 g((n1 + bx - 1) / bx, (n1 + by - 1) / by, A.dim == 3 ? n1 : 1u), blk(bx, by);
         unsigned pm = 0;  // the stored positions; the common sets have fixed-position kernels
         for (int k = 0; k < A.K; k++) pm |= 1u << A.full_of[k];
-        if (A.dim == 3 && pm == kStencilQ1) {
-            klaunch(pdl, k_stencil_fixed<T, kStencilQ1, MODE, 3>, g, blk, 0, s, S, x, b, out, d, c1, c2);
-            return;
-        }
-        if (A.dim == 3 && pm == kStencil27) {
-            klaunch(pdl, k_stencil_fixed<T, kStencil27, MODE, 3>, g, blk, 0, s, S, x, b, out, d, c1, c2);
-            return;
-        }
-        if (A.dim == 3 && pm == kStencilP1) {
-            klaunch(pdl, k_stencil_fixed<T, kStencilP1, MODE, 3>, g, blk, 0, s, S, x, b, out, d, c1, c2);
+        if (A.dim == 3 && (pm == kStencilQ1 || pm == kStencil27 || pm == kStencilP1)) {
+            // 3D: each thread marches along z through up to 16 planes of its column (fewer where
+            // the columns alone would not give about two waves of 2048 threads per SM)
+            int zc = (int)std::max<int64_t>(1, std::min<int64_t>(16, (int64_t)n1 * n1 * n1 / (2 * 2048 * 152)));
+            dim3 gz(g.x, g.y, (n1 + zc - 1) / zc);
+            if (pm == kStencilQ1)
+                klaunch(pdl, k_stencil_march<T, kStencilQ1, MODE>, gz, blk, 0, s, S, zc, x, b, out, d, c1, c2);
+            else if (pm == kStencil27)
+                klaunch(pdl, k_stencil_march<T, kStencil27, MODE>, gz, blk, 0, s, S, zc, x, b, out, d, c1, c2);
+            else
+                klaunch(pdl, k_stencil_march<T, kStencilP1, MODE>, gz, blk, 0, s, S, zc, x, b, out, d, c1, c2);
             return;
         }
         if (A.dim == 2 && pm == kStencil9) {
@@ -1233,7 +1237,8 @@ static int rq1_neighbours(int N, int64_t r, int64_t *col, int *role)
 // receives (diagonal, opposite, other).
 static bool rq1_constant_stencil(const mgh::Csr &A, int N, double vals[3])
 {
-    if (N < 4 || A.nrows != mgh::ndofs(3, MG_RQ1, N)) return false;
+    // the face-stencil kernel indexes faces in 32 bits
+    if (N < 4 || A.nrows != mgh::ndofs(3, MG_RQ1, N) || A.nrows >= ((int64_t)1 << 31)) return false;
     const int64_t M = N - 1;
     const int64_t r0 = 1 + M * (1 + (int64_t)N * 1);  // x-face at position 2 over cell (1, 1)
     double ref[3] = {0.0, 0.0, 0.0};
