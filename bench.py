@@ -149,7 +149,8 @@ KERNEL_PARTS = {
     "k_dia_sweep": [("sweep.cuh", "pdl_enter"), ("sweep.cuh", "struct Ar<double>"), ("sweep.cuh", "struct Ar<float>"),
                     ("sweep.cuh", "sweep_out"), ("sweep.cuh", "k_dia_sweep")],
     "k_coef_sweep": [("sweep.cuh", "pdl_enter"), ("sweep.cuh", "struct Ar<float>"), ("sweep.cuh", "sweep_out"),
-                     ("sweep.cuh", "sweep_out_v"), ("sweep.cuh", "struct CoefView"), ("sweep.cuh", "k_coef_sweep")],
+                     ("sweep.cuh", "sweep_out_v"), ("sweep.cuh", "fused_update"), ("sweep.cuh", "struct CoefView"),
+                     ("sweep.cuh", "k_coef_sweep")],
     "k_outer_resid": [("sweep.cuh", "pdl_enter"), ("kernels.cuh", "block_sum"), ("kernels.cuh", "finish_norm"),
                       ("kernels.cuh", "fp64_row"), ("kernels.cuh", "fp64_dof"), ("kernels.cuh", "k_outer_resid")],
 }

@@ -154,6 +154,9 @@ struct mg_hierarchy {
     int tail_level = -1;
     int tail_cluster = 8;
     bool tail_rec = false;
+    // the V-cycle being enqueued is followed by x64 += c (enqueue_v); the finest level's last
+    // post-smoothing sweep applied it (update_fused)
+    bool fuse_update = false, update_fused = false;
     std::vector<mgk::TailOp> tail_ops;
     std::mutex mu;
 

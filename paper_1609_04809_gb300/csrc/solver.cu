@@ -333,10 +333,25 @@ constexpr unsigned kStencilQ1 = kStencil27 & ~kFaces;   // 3D Q1: face couplings
 constexpr unsigned kStencilP1 = kFaces | (1u << 13);    // P1 on the Kuhn mesh: seven points
 constexpr unsigned kStencil9 = 0x1FFu;                  // 2D Q1
 
+// whether a sweep of this level can also apply the finest correction to x64 (fused_update)
+template <typename T>
+static bool can_fuse_update(const DevMat &A)
+{
+    if (!std::is_same<T, float>::value) return false;
+    if (A.fmt == MG_STORAGE_COEF) return true;
+    if (A.fmt != MG_STORAGE_STENCIL) return false;
+    if (A.elem == MG_RQ1) return true;
+    unsigned pm = 0;
+    for (int k = 0; k < A.K; k++) pm |= 1u << A.full_of[k];
+    return A.dim == 3 && (pm == kStencilQ1 || pm == kStencil27 || pm == kStencilP1);
+}
+
+// upd: x64 for the sweep that also applies the correction (only where can_fuse_update)
 template <typename T, int MODE>
 static void sweep_fmt(const DevMat &A, int n, const T *x, const T *b, T *out, T *d, T c1, T c2, cudaStream_t s,
-                      bool pdl = false)
+                      bool pdl = false, double *upd = nullptr)
 {
+    if (upd && !can_fuse_update<T>(A)) throw Error(MG_EINVAL, "this storage does not apply the update");
     if (A.fmt == MG_STORAGE_COEF) {
         if constexpr (std::is_same<T, float>::value) {
             // planes per thread: up to 16, fewer where the columns alone would not give about
@@ -347,7 +362,7 @@ static void sweep_fmt(const DevMat &A, int n, const T *x, const T *b, T *out, T 
             unsigned bx = line_block((unsigned)n1), by = std::min(256u / bx, (unsigned)n1);
             dim3 g((unsigned)((n1 + bx - 1) / bx), (unsigned)((n1 + by - 1) / by), (unsigned)((n1 + zc - 1) / zc)),
                 blk(bx, by);
-            klaunch(pdl, k_coef_sweep<MODE>, g, blk, 0, s, S, x, b, out, d, c1, c2);
+            klaunch(pdl, k_coef_sweep<MODE>, g, blk, 0, s, S, x, b, out, d, c1, c2, upd);
             return;
         } else {
             throw Error(MG_EINVAL, "coefficient storage holds FP32 levels only");
@@ -361,7 +376,7 @@ static void sweep_fmt(const DevMat &A, int n, const T *x, const T *b, T *out, T 
             int cz = (int)std::max<int64_t>(1, std::min<int64_t>(8, 3 * (int64_t)N * N * N / (2 * 2048 * 152)));
             Rq1View S{A.n1 + 1, (float)A.sval[1], (float)A.sdinv, cz};
             dim3 g((N + bx - 1) / bx, (N + by - 1) / by, 3 * ((N + cz - 1) / cz)), blk(bx, by);
-            klaunch(pdl, k_stencil_rq1<MODE>, g, blk, 0, s, S, x, b, out, d, c1, c2);
+            klaunch(pdl, k_stencil_rq1<MODE>, g, blk, 0, s, S, x, b, out, d, c1, c2, upd);
             return;
         } else {
             throw Error(MG_EINVAL, "the face stencil holds FP32 levels only");
@@ -386,11 +401,11 @@ static void sweep_fmt(const DevMat &A, int n, const T *x, const T *b, T *out, T 
             int zc = (int)std::max<int64_t>(1, std::min<int64_t>(16, (int64_t)n1 * n1 * n1 / (2 * 2048 * 152)));
             dim3 gz(g.x, g.y, (n1 + zc - 1) / zc);
             if (pm == kStencilQ1)
-                klaunch(pdl, k_stencil_march<T, kStencilQ1, MODE>, gz, blk, 0, s, S, zc, x, b, out, d, c1, c2);
+                klaunch(pdl, k_stencil_march<T, kStencilQ1, MODE>, gz, blk, 0, s, S, zc, x, b, out, d, c1, c2, upd);
             else if (pm == kStencil27)
-                klaunch(pdl, k_stencil_march<T, kStencil27, MODE>, gz, blk, 0, s, S, zc, x, b, out, d, c1, c2);
+                klaunch(pdl, k_stencil_march<T, kStencil27, MODE>, gz, blk, 0, s, S, zc, x, b, out, d, c1, c2, upd);
             else
-                klaunch(pdl, k_stencil_march<T, kStencilP1, MODE>, gz, blk, 0, s, S, zc, x, b, out, d, c1, c2);
+                klaunch(pdl, k_stencil_march<T, kStencilP1, MODE>, gz, blk, 0, s, S, zc, x, b, out, d, c1, c2, upd);
             return;
         }
         if (A.dim == 2 && pm == kStencil9) {
@@ -423,9 +438,14 @@ static void sweep_fmt(const DevMat &A, int n, const T *x, const T *b, T *out, T 
 
 template <typename T>
 static void sweep(mg_hierarchy *h, int l, int mode, const T *x, const T *b, T *out, T *d, double c1, double c2,
-                  cudaStream_t s)
+                  cudaStream_t s, bool fuse = false)
 {
     LevelD &L = h->lev[l];
+    // the iteration's update x64 += c in this sweep (the finest level's last one), where the
+    // level's storage has a kernel that applies it
+    double *upd = fuse && l == h->Lf && !(h->tail_rec && l <= h->tail_level) && can_fuse_update<T>(L.A) ? h->x64
+                                                                                                       : nullptr;
+    if (upd) h->update_fused = true;
     if (h->tail_rec && l <= h->tail_level) {  // part of the coarse-level tail launch
         TailOp op{};
         op.kind = TAIL_SWEEP;
@@ -456,6 +476,7 @@ static void sweep(mg_hierarchy *h, int l, int mode, const T *x, const T *b, T *o
         if (mode == SW_CHEBF) bytes += n * sv;
         if (mode == SW_CHEB) bytes += 2 * n * sv;
     }
+    if (upd) bytes += 16 * n;  // x64 read and written
     // algorithmic flops: two per stored entry (a multiply-add) plus the update's operations
     static const int kUpdateOps[6] = {1, 4, 4, 6, 2, 2};
     double entries = mat_entries(L.A);
@@ -463,13 +484,14 @@ static void sweep(mg_hierarchy *h, int l, int mode, const T *x, const T *b, T *o
     LaunchScope ls(h, s, kclass, l, bytes, flops);
     int nn = (int)L.n;
     T a = (T)c1, bb = (T)c2;
+    bool pdl = h->opt.use_pdl != 0;
     switch (mode) {
-    case SW_RESID: sweep_fmt<T, SW_RESID>(L.A, nn, x, b, out, d, a, bb, s, h->opt.use_pdl != 0); break;
-    case SW_JACOBI: sweep_fmt<T, SW_JACOBI>(L.A, nn, x, b, out, d, a, bb, s, h->opt.use_pdl != 0); break;
-    case SW_CHEBF: sweep_fmt<T, SW_CHEBF>(L.A, nn, x, b, out, d, a, bb, s, h->opt.use_pdl != 0); break;
-    case SW_CHEB: sweep_fmt<T, SW_CHEB>(L.A, nn, x, b, out, d, a, bb, s, h->opt.use_pdl != 0); break;
-    case SW_JACOBI_Z: sweep_fmt<T, SW_JACOBI_Z>(L.A, nn, x, b, out, d, a, bb, s, h->opt.use_pdl != 0); break;
-    default: sweep_fmt<T, SW_CHEBF_Z>(L.A, nn, x, b, out, d, a, bb, s, h->opt.use_pdl != 0); break;
+    case SW_RESID: sweep_fmt<T, SW_RESID>(L.A, nn, x, b, out, d, a, bb, s, pdl, upd); break;
+    case SW_JACOBI: sweep_fmt<T, SW_JACOBI>(L.A, nn, x, b, out, d, a, bb, s, pdl, upd); break;
+    case SW_CHEBF: sweep_fmt<T, SW_CHEBF>(L.A, nn, x, b, out, d, a, bb, s, pdl, upd); break;
+    case SW_CHEB: sweep_fmt<T, SW_CHEB>(L.A, nn, x, b, out, d, a, bb, s, pdl, upd); break;
+    case SW_JACOBI_Z: sweep_fmt<T, SW_JACOBI_Z>(L.A, nn, x, b, out, d, a, bb, s, pdl, upd); break;
+    default: sweep_fmt<T, SW_CHEBF_Z>(L.A, nn, x, b, out, d, a, bb, s, pdl, upd); break;
     }
 }
 
@@ -515,10 +537,11 @@ static void gs_sweep(mg_hierarchy *h, int l, T *x, bool post, cudaStream_t s)
 }
 
 template <typename T>
-static int smooth(mg_hierarchy *h, int l, int c, bool post, cudaStream_t s)
+static int smooth(mg_hierarchy *h, int l, int c, bool post, cudaStream_t s, bool fuse_last = false)
 {
     LevelD &L = h->lev[l];
     T *b = (T *)L.b, *d = (T *)L.d;
+    const int last = h->opt.smoother == MG_JACOBI ? 0 : h->opt.cheb_degree - 1;  // the last step of this application
     if (h->opt.smoother == MG_GAUSS_SEIDEL) {  // in place: the buffer does not change
         if (c < 0) {
             CK(cudaMemsetAsync(L.x[0], 0, (size_t)L.n * sizeof(T), s));
@@ -529,21 +552,22 @@ static int smooth(mg_hierarchy *h, int l, int c, bool post, cudaStream_t s)
     }
     if (h->opt.smoother == MG_JACOBI) {
         if (c < 0) {
-            sweep<T>(h, l, SW_JACOBI_Z, nullptr, b, (T *)L.x[0], d, L.omega, 0.0, s);
+            sweep<T>(h, l, SW_JACOBI_Z, nullptr, b, (T *)L.x[0], d, L.omega, 0.0, s, fuse_last);
             return 0;
         }
-        sweep<T>(h, l, SW_JACOBI, (T *)L.x[c], b, (T *)L.x[1 - c], d, L.omega, 0.0, s);
+        sweep<T>(h, l, SW_JACOBI, (T *)L.x[c], b, (T *)L.x[1 - c], d, L.omega, 0.0, s, fuse_last);
         return 1 - c;
     }
     if (c < 0) {
-        sweep<T>(h, l, SW_CHEBF_Z, nullptr, b, (T *)L.x[0], d, L.cheb_c0, 0.0, s);
+        sweep<T>(h, l, SW_CHEBF_Z, nullptr, b, (T *)L.x[0], d, L.cheb_c0, 0.0, s, fuse_last && last == 0);
         c = 0;
     } else {
-        sweep<T>(h, l, SW_CHEBF, (T *)L.x[c], b, (T *)L.x[1 - c], d, L.cheb_c0, 0.0, s);
+        sweep<T>(h, l, SW_CHEBF, (T *)L.x[c], b, (T *)L.x[1 - c], d, L.cheb_c0, 0.0, s, fuse_last && last == 0);
         c = 1 - c;
     }
     for (int j = 1; j < h->opt.cheb_degree; j++) {
-        sweep<T>(h, l, SW_CHEB, (T *)L.x[c], b, (T *)L.x[1 - c], d, L.cheb_c1[j], L.cheb_c2[j], s);
+        sweep<T>(h, l, SW_CHEB, (T *)L.x[c], b, (T *)L.x[1 - c], d, L.cheb_c1[j], L.cheb_c2[j], s,
+                 fuse_last && j == last);
         c = 1 - c;
     }
     return c;
@@ -718,7 +742,8 @@ static int enqueue_vcycle(mg_hierarchy *h, cudaStream_t s)
             cur[l] = 0;
         }
         prolong_add<T>(h, l, (const T *)h->lev[l - 1].x[cur[l - 1]], (T *)L.x[cur[l]], s);
-        for (int a = 0; a < h->opt.nu_post; a++) cur[l] = smooth<T>(h, l, cur[l], true, s);
+        for (int a = 0; a < h->opt.nu_post; a++)
+            cur[l] = smooth<T>(h, l, cur[l], true, s, h->fuse_update && l == Lf && a == h->opt.nu_post - 1);
     }
     if (h->tail_rec) {  // the whole hierarchy was the tail
         launch_tail<T>(h, s);
@@ -772,14 +797,20 @@ static void enqueue_r(mg_hierarchy *h, cudaStream_t s)
         enqueue_outer<double>(h, s);
 }
 
+// one V-cycle and x64 += c; the update rides on the finest level's last post-smoothing
+// sweep where its storage has a kernel for that, else it is a launch of its own
 static void enqueue_v(mg_hierarchy *h, cudaStream_t s)
 {
+    h->update_fused = false;
+    h->fuse_update = true;
     if (h->mixed) {
         int c = enqueue_vcycle<float>(h, s);
-        enqueue_update<float>(h, c, s);
+        h->fuse_update = false;
+        if (!h->update_fused) enqueue_update<float>(h, c, s);
     } else {
         int c = enqueue_vcycle<double>(h, s);
-        enqueue_update<double>(h, c, s);
+        h->fuse_update = false;
+        if (!h->update_fused) enqueue_update<double>(h, c, s);
     }
 }
 

@@ -75,63 +75,77 @@ struct MatView {
 };
 
 template <typename T, int MODE>
-__device__ __forceinline__ void sweep_out(int i, T s, T dinv, T xi, const T *__restrict__ b, T *__restrict__ out,
-                                          T *__restrict__ d, T c1, T c2)
+__device__ __forceinline__ T sweep_out(int i, T s, T dinv, T xi, const T *__restrict__ b, T *__restrict__ out,
+                                       T *__restrict__ d, T c1, T c2)
 {
     using A = Ar<T>;
-    T bi = b[i];
+    T bi = b[i], o;
     if (MODE == SW_RESID) {
-        out[i] = A::sub(bi, s);
+        o = A::sub(bi, s);
     } else if (MODE == SW_JACOBI) {
         T r = A::sub(bi, s);
-        out[i] = A::add(xi, A::mul(c1, A::mul(dinv, r)));
+        o = A::add(xi, A::mul(c1, A::mul(dinv, r)));
     } else if (MODE == SW_CHEBF) {
         T r = A::sub(bi, s);
         T dd = A::mul(c1, A::mul(dinv, r));
         d[i] = dd;
-        out[i] = A::add(xi, dd);
+        o = A::add(xi, dd);
     } else if (MODE == SW_CHEB) {
         T r = A::sub(bi, s);
         T dd = A::add(A::mul(c1, d[i]), A::mul(c2, A::mul(dinv, r)));
         d[i] = dd;
-        out[i] = A::add(xi, dd);
+        o = A::add(xi, dd);
     } else if (MODE == SW_JACOBI_Z) {
-        out[i] = A::mul(c1, A::mul(dinv, bi));
+        o = A::mul(c1, A::mul(dinv, bi));
     } else {  // SW_CHEBF_Z
         T dd = A::mul(c1, A::mul(dinv, bi));
         d[i] = dd;
-        out[i] = dd;
+        o = dd;
     }
+    out[i] = o;
+    return o;
+}
+
+// The finest level's last post-smoothing sweep of a defect-correction iteration can also
+// apply the correction to the FP64 iterate, x64_i <- x64_i + c_i (upd = x64; nullptr: no
+// update): the operation of k_update, one launch and one pass over c fewer.
+template <typename T, int MODE>
+__device__ __forceinline__ void fused_update(double *__restrict__ upd, int i, T c)
+{
+    if (MODE != SW_RESID && upd) upd[i] = __dadd_rn(upd[i], (double)c);
 }
 
 // sweep_out with b_i and (SW_CHEB) d_i already loaded
 template <typename T, int MODE>
-__device__ __forceinline__ void sweep_out_v(int i, T s, T dinv, T xi, T bi, T di, T *__restrict__ out,
-                                            T *__restrict__ d, T c1, T c2)
+__device__ __forceinline__ T sweep_out_v(int i, T s, T dinv, T xi, T bi, T di, T *__restrict__ out,
+                                         T *__restrict__ d, T c1, T c2)
 {
     using A = Ar<T>;
+    T o;
     if (MODE == SW_RESID) {
-        out[i] = A::sub(bi, s);
+        o = A::sub(bi, s);
     } else if (MODE == SW_JACOBI) {
         T r = A::sub(bi, s);
-        out[i] = A::add(xi, A::mul(c1, A::mul(dinv, r)));
+        o = A::add(xi, A::mul(c1, A::mul(dinv, r)));
     } else if (MODE == SW_CHEBF) {
         T r = A::sub(bi, s);
         T dd = A::mul(c1, A::mul(dinv, r));
         d[i] = dd;
-        out[i] = A::add(xi, dd);
+        o = A::add(xi, dd);
     } else if (MODE == SW_CHEB) {
         T r = A::sub(bi, s);
         T dd = A::add(A::mul(c1, di), A::mul(c2, A::mul(dinv, r)));
         d[i] = dd;
-        out[i] = A::add(xi, dd);
+        o = A::add(xi, dd);
     } else if (MODE == SW_JACOBI_Z) {
-        out[i] = A::mul(c1, A::mul(dinv, bi));
+        o = A::mul(c1, A::mul(dinv, bi));
     } else {  // SW_CHEBF_Z
         T dd = A::mul(c1, A::mul(dinv, bi));
         d[i] = dd;
-        out[i] = dd;
+        o = dd;
     }
+    out[i] = o;
+    return o;
 }
 
 // DIA: column of slot k is i + offs.o[k]. x points at element 0 of a buffer padded on
@@ -265,7 +279,7 @@ __global__ void __launch_bounds__(256) k_stencil_fixed(StencilView<T> S, const T
 template <typename T, unsigned PM, int MODE>
 __global__ void __launch_bounds__(256) k_stencil_march(StencilView<T> S, int zc, const T *__restrict__ x,
                                                        const T *__restrict__ b, T *__restrict__ out,
-                                                       T *__restrict__ d, T c1, T c2)
+                                                       T *__restrict__ d, T c1, T c2, double *__restrict__ upd)
 {
     pdl_enter();
     const int n1 = S.n1;
@@ -308,7 +322,7 @@ __global__ void __launch_bounds__(256) k_stencil_march(StencilView<T> S, int zc,
             if (p == 13 || ((m >> p) & 1u)) s = Ar<T>::mac(s, S.a[k], v);
             k++;
         }
-        sweep_out<T, MODE>(i, s, S.dinv, P0[4], b, out, d, c1, c2);
+        fused_update<T, MODE>(upd, i, sweep_out<T, MODE>(i, s, S.dinv, P0[4], b, out, d, c1, c2));
     };
     if (!IsZero<MODE>::value) {
         load_plane(A);  // z0 - 1
@@ -367,7 +381,8 @@ struct CoefView {
 template <int MODE>
 __global__ void __launch_bounds__(256, MG_COEF_MIN_BLOCKS) k_coef_sweep(CoefView S, const float *__restrict__ x,
                                                     const float *__restrict__ b, float *__restrict__ out,
-                                                    float *__restrict__ d, float c1, float c2)
+                                                    float *__restrict__ d, float c1, float c2,
+                                                    double *__restrict__ upd)
 {
     constexpr bool Z = IsZero<MODE>::value;
     pdl_enter();
@@ -443,7 +458,7 @@ __global__ void __launch_bounds__(256, MG_COEF_MIN_BLOCKS) k_coef_sweep(CoefView
             const float se = (fxy + fxz) + (fyz + fb);
             acc = fmaf(kap[e], fmaf(4.0f, xc, -se), acc);
         }
-        sweep_out_v<float, MODE>(i, acc, dinv, xc, bi, di, out, d, c1, c2);
+        fused_update<float, MODE>(upd, i, sweep_out_v<float, MODE>(i, acc, dinv, xc, bi, di, out, d, c1, c2));
     };
     float A[9] = {}, B[9] = {}, C[9] = {}, KA[4], KB[4];
     if (!Z) {
@@ -515,7 +530,8 @@ struct Rq1View {
 template <int MODE>
 __global__ void __launch_bounds__(256) k_stencil_rq1(Rq1View S, const float *__restrict__ x,
                                                      const float *__restrict__ b, float *__restrict__ out,
-                                                     float *__restrict__ d, float c1, float c2)
+                                                     float *__restrict__ d, float c1, float c2,
+                                                     double *__restrict__ upd)
 {
     pdl_enter();
     // 32-bit indices: setup keeps this storage for levels of fewer than 2^31 faces
@@ -598,7 +614,7 @@ __global__ void __launch_bounds__(256) k_stencil_rq1(Rq1View S, const float *__r
     for (int k = 0; k < 8; k++) xe[k] = me[k] ? __ldg(x + e[k]) : 0.0f;
     const float s8 = ((xe[0] + xe[1]) + (xe[2] + xe[3])) + ((xe[4] + xe[5]) + (xe[6] + xe[7]));
     const float s = (8.0f * xc - s8) - (2.0f * xc - (xo1 + xo2));
-    sweep_out<float, MODE>(i, S.hv * s, S.dinv, xc, b, out, d, c1, c2);
+    fused_update<float, MODE>(upd, i, sweep_out<float, MODE>(i, S.hv * s, S.dinv, xc, b, out, d, c1, c2));
     }
 }
 
