@@ -333,6 +333,12 @@ def _host_cpu():
     return {"nproc": os.cpu_count(), "model": model}
 
 
+def _workload_config(name, c, n, nnz_finest):
+    """The bench line's `config`: the workload alone, the same for both arms."""
+    return {"workload": name, "description": WORKLOADS.get(name, name), "n_dofs": int(n), "n_cells": c["n_cells"],
+            "l2": "inputs larger than L2 (finest FP64 matrix %.0f MB > 129 MB L2)" % (int(nnz_finest) * 8 / 1e6)}
+
+
 def cpu_baseline(name, cycles_all=3, cycles_one=1, smoother="workload"):
     """The oracle (plain FP64 C; row loops on OpenMP threads) on the same workload: setup
     (not timed), then `cycles_all` defect-correction iterations on all host cores and
@@ -609,8 +615,8 @@ def run_reference(args):
     out = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic", "config": {"workload": name, "description": WORKLOADS.get(name, name),
-                                           "n_dofs": int(O.n), "n_cells": c["n_cells"]},
+           "data": "synthetic", "config": _workload_config(name, c, int(O.n), A.nnz if hasattr(A, "nnz")
+                                                            else len(A.val)),
            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
                             "host": cpu},
            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -825,16 +831,13 @@ def run_ours(args):
                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None,
                "dtype": "f64" if precision == "fp64" else "f32 V-cycle / f64 outer", "data": "synthetic",
-               "config": {"workload": name, "description": WORKLOADS.get(name, name), "n_dofs": n,
-                          "n_cells": c["n_cells"], "precision": precision,
-                          "parallelism": "replicas" if world > 1 else "single-gpu",
-                          "l2": "inputs larger than L2 (finest FP64 matrix %.0f MB > 129 MB L2)"
-                                % (info["nnz"][Lf] * 8 / 1e6),
-                          "storage": [STORAGE_NAMES[v] for v in info["storage"]],
-                          "smoother": [k for k, v in SMOOTHERS.items() if v == c["smoother"]][0],
-                          "setup_s": setup_s,
-                          "headline": "the largest single-GPU workload, in the precision it specifies"
-                                      if name == DEFAULT_CONFIG else "chosen by --config"},
+               "config": _workload_config(name, c, n, info["nnz"][Lf]),
+               "run": {"precision": precision, "parallelism": "replicas" if world > 1 else "single-gpu",
+                       "storage": [STORAGE_NAMES[v] for v in info["storage"]],
+                       "smoother": [k for k, v in SMOOTHERS.items() if v == c["smoother"]][0],
+                       "setup_s": setup_s,
+                       "headline": "the largest single-GPU workload, in the precision it specifies"
+                                   if name == DEFAULT_CONFIG else "chosen by --config"},
                "roofline": roofs.get(dominant),
                "roofline_kernels": roofs,
                "whole_cycle": whole,
