@@ -53,7 +53,7 @@ def test_kernel_key_follows_the_kernel_code_only():
     changed = sweep.replace("if (i >= n) return;\n    constexpr int C = K / 2;",
                             "if (i >= n) return;\n    constexpr int C = K / 2 + 0;", 1)
     assert changed != sweep and bench._kernel_sha("k_dia_sweep", {**src, "sweep.cuh": changed}) != key
-    helper = sweep.replace("out[i] = A::sub(bi, s);", "out[i] = A::sub(bi, s) + T(0);", 1)
+    helper = sweep.replace("o = A::sub(bi, s);", "o = A::sub(bi, s) + T(0);", 1)
     assert helper != sweep and bench._kernel_sha("k_dia_sweep", {**src, "sweep.cuh": helper}) != key
     # the outer residual's key follows kernels.cuh's reduction helpers
     k = src["kernels.cuh"]
