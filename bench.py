@@ -150,9 +150,12 @@ KERNEL_PARTS = {
                     ("sweep.cuh", "sweep_out"), ("sweep.cuh", "k_dia_sweep")],
     "k_coef_sweep": [("sweep.cuh", "pdl_enter"), ("sweep.cuh", "struct Ar<float>"), ("sweep.cuh", "sweep_out"),
                      ("sweep.cuh", "sweep_out_v"), ("sweep.cuh", "fused_update"), ("sweep.cuh", "struct CoefView"),
-                     ("sweep.cuh", "k_coef_sweep")],
-    "k_outer_resid": [("sweep.cuh", "pdl_enter"), ("kernels.cuh", "block_sum"), ("kernels.cuh", "finish_norm"),
-                      ("kernels.cuh", "fp64_row"), ("kernels.cuh", "fp64_dof"), ("kernels.cuh", "k_outer_resid")],
+                     ("sweep.cuh", "coef_corner"), ("sweep.cuh", "coef_edge_x"), ("sweep.cuh", "coef_edge_y"),
+                     ("sweep.cuh", "coef_march"), ("sweep.cuh", "k_coef_sweep")],
+    "k_outer_resid": [("sweep.cuh", "pdl_enter"), ("sweep.cuh", "struct Ar<float>"), ("sweep.cuh", "sweep_out_v"),
+                      ("kernels.cuh", "block_sum"), ("kernels.cuh", "finish_norm"), ("kernels.cuh", "fp64_row"),
+                      ("kernels.cuh", "fp64_dof"), ("kernels.cuh", "struct ZStep"), ("kernels.cuh", "zstep_dinv"),
+                      ("kernels.cuh", "k_outer_resid")],
 }
 SWEEP_KERNELS = {"dia": "k_dia_sweep", "ell": "k_ell_sweep", "csr": "k_csr_sweep", "sell": "k_sell_sweep",
                  "stencil": "k_stencil_sweep", "coef": "k_coef_sweep"}
@@ -167,6 +170,9 @@ def _source_part(src, name):
     m = re.search(r"(^template <[^\n]*\n)?^\S[^\n]*?\b" + re.escape(name) + r"\(", src, re.M)
     if m is None:
         raise KeyError(name)
+    line_end = src.index("\n", m.end())
+    if src[m.end():line_end].rstrip().endswith("}"):  # a one-line function
+        return src[m.start():line_end + 1]
     return src[m.start():src.index("\n}\n", m.start()) + 3]
 
 

@@ -150,6 +150,12 @@ typedef struct {
                         0 never, 1 whenever it applies, 2 (default) where setup measures the
                         captured V-cycle faster with it than without (always when use_graph
                         is 0); every choice computes the same bits */
+    int fuse_first; /* the first pre-smoothing step of a level starts from x = 0 and needs
+                       only the level's right-hand side and D^-1 (Sec. 5.3, the smoothing
+                       steps of the V-cycle): 1 (default) takes it in the kernel that makes
+                       that right-hand side (the restriction from the finer level; on the
+                       finest level of a mixed hierarchy the FP64 outer residual), 0 as a
+                       sweep of its own; the same bits either way (Jacobi and Chebyshev) */
 } mg_options;
 
 /* Right-hand side f of -div(k grad u) = f: the constant f_const if n_modes == 0, else

@@ -27,14 +27,42 @@
 
 namespace mgk {
 
+// The first pre-smoothing step on a level starts from x = 0, so it needs only the level's
+// right-hand side and D^-1: the kernel that produces the right-hand side (the restriction
+// from the finer level; on the finest FP32 level the outer residual) can take it
+// (ZM = SW_JACOBI_Z or SW_CHEBF_Z) while it holds b_i, with the arithmetic and the stored
+// values of the separate sweep (sweep_out_v). D^-1 is a stored array, 1 / a_ii of the DIA
+// diagonal slot, or the constant of a constant stencil.
+template <typename T>
+struct ZStep {
+    const T *dinv = nullptr;         // stored 1 / a_ii, or nullptr
+    const T *diag = nullptr;         // a_ii (the DIA diagonal slot), or nullptr
+    T cdinv = T(0);                  // 1 / a_ii of a constant stencil (dinv and diag null)
+    T *out = nullptr, *d = nullptr;  // the step's x and (SW_CHEBF_Z) Chebyshev direction
+    T c1 = T(0);
+};
+
+template <typename T>
+__device__ __forceinline__ T zstep_dinv(const ZStep<T> &Z, int i)
+{
+    return Z.dinv ? __ldcs(Z.dinv + i) : (Z.diag ? Ar<T>::rcp(__ldcs(Z.diag + i)) : Z.cdinv);
+}
+
+template <typename T, int ZM>
+__device__ __forceinline__ void zstep(const ZStep<T> &Z, int i, T bi)
+{
+    if constexpr (ZM != 0) sweep_out_v<T, ZM>(i, T(0), zstep_dinv(Z, i), T(0), bi, T(0), Z.out, Z.d, Z.c1, T(0));
+}
+
 // ------------------------------------------------------------------------------------
 // Q1 grid transfers on the structured grid (no stored matrix)
 // ------------------------------------------------------------------------------------
 // Restriction b_c = P^T r: coarse vertex (X,Y[,Z]) gathers the 3^d fine vertices around
 // (2X,2Y[,2Z]) in ascending fine index, weight prod_d (1 if on the line, 1/2 otherwise).
+// ZM: the coarse level's first smoothing step as well (ZStep).
 // Launch: x-lines of the coarse grid, grid (ceil(nc1/blockDim), nc1, DIM == 3 ? nc1 : 1).
-template <typename T, int DIM>
-__global__ void __launch_bounds__(128) k_restrict_q1(const T *__restrict__ r, T *__restrict__ bc, int Nc)
+template <typename T, int DIM, int ZM = 0>
+__global__ void __launch_bounds__(128) k_restrict_q1(const T *__restrict__ r, T *__restrict__ bc, int Nc, ZStep<T> Zs)
 {
     pdl_enter();
     int nc1 = Nc - 1, nf1 = 2 * Nc - 1;
@@ -55,69 +83,75 @@ __global__ void __launch_bounds__(128) k_restrict_q1(const T *__restrict__ r, T 
                 s = Ar<T>::mac(s, w, __ldg(r + j));
             }
     bc[I] = s;
+    zstep<T, ZM>(Zs, (int)I, s);
 }
 
 // Prolongation and correction x_f += P x_c: fine vertex v takes the coarse vertices V
-// with |v - 2V| <= 1 per axis (boundary ones are zero and skipped), ascending coarse index.
-// Every such V carries the same weight prod_d (1 or 1/2) = 2^-(number of odd coordinates
-// of v), taken from a table: no floating-point work beyond one multiply-add per term.
-// Thread m of a fine x-line computes the pair v0 = 2m (coarse X = m) and v0 = 2m + 1
-// (X = m, m + 1) from the same coarse loads: every lane runs the same loop, where one
-// thread per fine point would alternate one and two X terms within a warp.
-// Launch: grid (ceil(Nc/blockDim), nf1, DIM == 3 ? nf1 : 1), m = 0..Nc-1.
+// with |v - 2V| <= 1 per axis (boundary ones are zero), ascending coarse index. Every
+// such V carries the same weight prod_d (1 or 1/2) = 2^-(number of odd coordinates of v),
+// so the sum is one multiply-add per term from s = 0 in the order Z, Y, X ascending.
+// Thread (X, Y[, Z]), X, Y, Z = 0 .. Nc - 1, owns the 2^d fine vertices (2X + ex, 2Y + ey
+// [, 2Z + ez]), e in {0, 1}, that are interior, and the 2^d coarse corners (X + dx,
+// Y + dy[, Z + dz]) they draw on: all of its fine and coarse values are loaded before
+// any sum, so each thread has 2^d fine values in flight instead of two. A vertex with
+// e = 0 on an axis takes d = 0 only, one with e = 1 takes d = 0, 1; corners off the
+// interior are read as +0, whose terms leave the sum's bits unchanged (s starts at +0,
+// and s + (+0) = s), so the result is the same as summing over the interior corners only.
+// Launch: grid (ceil(Nc/blockDim), Nc, DIM == 3 ? Nc : 1).
 template <typename T, int DIM>
 __global__ void __launch_bounds__(128) k_prolong_q1(const T *__restrict__ xc, T *__restrict__ xf, int Nc)
 {
     pdl_enter();
-    int Nf = 2 * Nc, nf1 = Nf - 1, nc1 = Nc - 1;
-    int m = blockIdx.x * blockDim.x + threadIdx.x;
-    if (m >= Nc) return;
-    int v1 = blockIdx.y + 1, v2 = DIM == 3 ? blockIdx.z + 1 : 2;
-    int64_t line = (int64_t)nf1 * ((v1 - 1) + (DIM == 3 ? (int64_t)nf1 * (v2 - 1) : 0));
-    int oddyz = (v1 & 1) + (DIM == 3 ? (v2 & 1) : 0);
-    const T we = oddyz == 0 ? T(1) : (oddyz == 1 ? T(0.5) : T(0.25));               // v0 even
-    const T wo = oddyz == 0 ? T(0.5) : (oddyz == 1 ? T(0.25) : T(0.125));            // v0 odd
-    const bool lo = m >= 1, hi = m + 1 <= nc1;  // coarse X = m and X = m + 1 are interior
-    int y0 = max(v1 >> 1, 1), y1 = min((v1 + 1) >> 1, Nc - 1);
-    int z0 = DIM == 3 ? max(v2 >> 1, 1) : 1, z1 = DIM == 3 ? min((v2 + 1) >> 1, Nc - 1) : 1;
-    // every load first (the fine pair, then up to 2 x 2 coarse rows), then the sums in the
-    // order Z ascending, Y ascending: the same terms in the same order as a loop over them
-    const T f0 = m >= 1 ? xf[line + 2 * m - 1] : T(0), f1 = xf[line + 2 * m];
-    T cm[2][2], cp[2][2];
-    bool on[2][2];
+    constexpr int NZ = DIM == 3 ? 2 : 1;
+    const int nf1 = 2 * Nc - 1, nc1 = Nc - 1;
+    const int X = blockIdx.x * blockDim.x + threadIdx.x;
+    if (X >= Nc) return;
+    const int Y = blockIdx.y, Z = DIM == 3 ? blockIdx.z : 1;
+    T c[NZ][2][2], f[NZ][2][2];
+    bool fin[NZ][2][2];
+    // fine vertex (2X + ex, 2Y + ey, 2Z + ez) at base + ex + nf1 ey + nf1^2 ez
+    const int64_t base = (2 * X - 1) + (int64_t)nf1 * ((2 * Y - 1) + (DIM == 3 ? (int64_t)nf1 * (2 * Z - 1) : 0));
 #pragma unroll
-    for (int zz = 0; zz < 2; zz++)
+    for (int dz = 0; dz < NZ; dz++)
 #pragma unroll
-        for (int yy = 0; yy < 2; yy++) {
-            const int Z = z0 + zz, Y = y0 + yy;
-            on[zz][yy] = Y <= y1 && Z <= z1 && (DIM == 3 || zz == 0);
-            int64_t row = (int64_t)nc1 * ((Y - 1) + (DIM == 3 ? (int64_t)nc1 * (Z - 1) : 0)) - 1;
-            cm[zz][yy] = on[zz][yy] && lo ? __ldg(xc + row + m) : T(0);
-            cp[zz][yy] = on[zz][yy] && hi ? __ldg(xc + row + m + 1) : T(0);
-        }
-    T te = T(0), to = T(0);
+        for (int dy = 0; dy < 2; dy++)
 #pragma unroll
-    for (int zz = 0; zz < 2; zz++)
-#pragma unroll
-        for (int yy = 0; yy < 2; yy++) {
-            if (!on[zz][yy]) continue;
-            if (lo) {
-                te = Ar<T>::mac(te, we, cm[zz][yy]);
-                to = Ar<T>::mac(to, wo, cm[zz][yy]);
+            for (int dx = 0; dx < 2; dx++) {
+                const int cx = X + dx, cy = Y + dy, cz = Z + dz;
+                const bool in = cx >= 1 && cx <= nc1 && cy >= 1 && cy <= nc1 && (DIM == 2 || (cz >= 1 && cz <= nc1));
+                c[dz][dy][dx] = in ? __ldg(xc + (cx - 1) + (int64_t)nc1 * ((cy - 1) + (DIM == 3 ? (int64_t)nc1 * (cz - 1) : 0)))
+                                   : T(0);
+                const bool v = (2 * X + dx >= 1) && (2 * Y + dy >= 1) && (DIM == 2 || 2 * Z + dz >= 1);
+                fin[dz][dy][dx] = v;
+                f[dz][dy][dx] = v ? xf[base + dx + (int64_t)nf1 * (dy + (int64_t)nf1 * dz)] : T(0);
             }
-            if (hi) to = Ar<T>::mac(to, wo, cp[zz][yy]);
-        }
-    if (m >= 1) xf[line + 2 * m - 1] = Ar<T>::add(f0, te);  // v0 = 2m
-    xf[line + 2 * m] = Ar<T>::add(f1, to);                  // v0 = 2m + 1
+#pragma unroll
+    for (int ez = 0; ez < NZ; ez++)
+#pragma unroll
+        for (int ey = 0; ey < 2; ey++)
+#pragma unroll
+            for (int ex = 0; ex < 2; ex++) {
+                const int odd = ex + ey + ez;
+                const T w = odd == 0 ? T(1) : (odd == 1 ? T(0.5) : (odd == 2 ? T(0.25) : T(0.125)));
+                T s = T(0);
+#pragma unroll
+                for (int dz = 0; dz <= ez; dz++)
+#pragma unroll
+                    for (int dy = 0; dy <= ey; dy++)
+#pragma unroll
+                        for (int dx = 0; dx <= ex; dx++) s = Ar<T>::mac(s, w, c[dz][dy][dx]);
+                if (fin[ez][ey][ex])
+                    xf[base + ex + (int64_t)nf1 * (ey + (int64_t)nf1 * ez)] = Ar<T>::add(f[ez][ey][ex], s);
+            }
 }
 
 // Explicit transfer (rotated Q1, P1, P2) with the operator in SELL-32 (see k_sell_sweep):
 // y_i = sum_k v_k x_col(k) in the row's CSR order (ADD: y_i += that sum); storage position
 // r computes row perm[r].
-template <typename T, bool ADD>
+template <typename T, bool ADD, int ZM = 0>
 __global__ void __launch_bounds__(256) k_sell_apply(const int64_t *__restrict__ sptr, const int32_t *__restrict__ col,
                                                     const T *__restrict__ val, const int32_t *__restrict__ perm,
-                                                    int n, const T *__restrict__ x, T *__restrict__ y)
+                                                    int n, const T *__restrict__ x, T *__restrict__ y, ZStep<T> Zs)
 {
     pdl_enter();
     int r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -129,6 +163,7 @@ __global__ void __launch_bounds__(256) k_sell_apply(const int64_t *__restrict__ 
     T s = T(0);
     for (int k = 0; k < Ks; k++, e += 32) s = Ar<T>::mac(s, __ldcs(val + e), __ldg(x + __ldcs(col + e)));
     y[i] = ADD ? Ar<T>::add(y[i], s) : s;
+    if (!ADD) zstep<T, ZM>(Zs, i, s);
 }
 
 // ------------------------------------------------------------------------------------
@@ -530,21 +565,35 @@ __device__ __forceinline__ int fp64_dof(const MatView<double> &A, int r)
     return FMT == 4 ? __ldg(A.perm + r) : r;
 }
 
-template <typename Tin, int FMT, int K>
+// ZM: the finest FP32 level's first smoothing step as well (ZStep), on the defect as the
+// FP32 value stored in r; its D^-1 is loaded before the row so that its latency hides
+// behind the row's.
+template <typename Tin, int FMT, int K, int ZM = 0>
 __global__ void __launch_bounds__(256, 6) k_outer_resid(MatView<double> A, int n, const double *__restrict__ x,
                                                      const double *__restrict__ b, Tin *__restrict__ r,
-                                                     double *partial, unsigned *ticket, double *norm2)
+                                                     double *partial, unsigned *ticket, double *norm2,
+                                                     ZStep<float> Zs)
 {
     pdl_enter();
     double sq = 0.0;
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
         int i = fp64_dof<FMT>(A, q);
+        float dv = 0.0f;
+        if constexpr (ZM != 0) dv = zstep_dinv(Zs, i);
         double ri = __dsub_rn(b[i], fp64_row<FMT, K>(A, q, i, x));
-        r[i] = (Tin)ri;
+        const Tin rt = (Tin)ri;
+        r[i] = rt;
         sq = __fma_rn(ri, ri, sq);
+        if constexpr (ZM != 0)
+            sweep_out_v<float, ZM>(i, 0.0f, dv, 0.0f, (float)rt, 0.0f, Zs.out, Zs.d, Zs.c1, 0.0f);
     }
     finish_norm(sq, partial, ticket, norm2);
 }
+
+// 1 / a_ii of a per-cell-coefficient level, as its sweep forms it: 4 times the sum of the
+// eight cells around the vertex, the cells summed per cell plane ((k0 + k1) + (k2 + k3)),
+// lower plane first. Launch: grid (ceil(n1/blockDim.x), n1, n1).
+__global__ void k_coef_dinv(const float *__restrict__ kap, int n1, float *__restrict__ dinv);
 
 __global__ void k_norm2(const double *__restrict__ v, int n, double *partial, unsigned *ticket, double *norm2);
 

@@ -63,6 +63,9 @@ struct LevelD {
     int galerkin = 0;
     DevMat A;         // inner precision
     void *x[2] = {nullptr, nullptr};
+    // 1 / a_ii of a per-cell-coefficient level, read by the kernel that takes the level's
+    // first smoothing step with its right-hand side (zfuse)
+    void *zdinv = nullptr;
     void *b = nullptr, *t = nullptr, *d = nullptr;
     bool structured = false;  // Q1 transfers computed from the grid
     DevMat P, R;              // explicit transfers to level-1 (SELL-32)
@@ -157,6 +160,10 @@ struct mg_hierarchy {
     // the V-cycle being enqueued is followed by x64 += c (enqueue_v); the finest level's last
     // post-smoothing sweep applied it (update_fused)
     bool fuse_update = false, update_fused = false;
+    // zfuse: the restriction to level l - 1 >= 1 also takes that level's first smoothing
+    // step (from x = 0); outer_z: the outer residual kernel takes the finest level's, and
+    // the V-cycle that follows it (enqueue_v) starts after that step
+    bool zfuse = false, outer_z = false;
     std::vector<mgk::TailOp> tail_ops;
     std::mutex mu;
 

@@ -113,6 +113,16 @@ __global__ void __launch_bounds__(256, 6) k_norm2(const double *__restrict__ v, 
     for (; i < n; i += st) sq = __fma_rn(v[i], v[i], sq);
     finish_norm(sq, partial, ticket, norm2);
 }
+
+__global__ void k_coef_dinv(const float *__restrict__ kap, int n1, float *__restrict__ dinv)
+{
+    const int vx = blockIdx.x * blockDim.x + threadIdx.x, vy = blockIdx.y, vz = blockIdx.z;
+    if (vx >= n1) return;
+    const int64_t nc = n1 + 1;
+    const float *k0 = kap + vx + nc * (vy + nc * (int64_t)vz), *k1 = k0 + nc * nc;
+    const float kc = (k0[0] + k0[1]) + (k0[nc] + k0[nc + 1]), kn = (k1[0] + k1[1]) + (k1[nc] + k1[nc + 1]);
+    dinv[vx + (int64_t)n1 * (vy + (int64_t)n1 * vz)] = Ar<float>::rcp(4.0f * (kc + kn));
+}
 }  // namespace mgk
 
 // ------------------------------------------------------------------------------------
@@ -355,9 +365,9 @@ static void sweep_fmt(const DevMat &A, int n, const T *x, const T *b, T *out, T 
     if (A.fmt == MG_STORAGE_COEF) {
         if constexpr (std::is_same<T, float>::value) {
             // planes per thread: up to 16, fewer where the columns alone would not give about
-            // two waves of 2048 threads on each of the 152 SMs
+            // MG_COEF_THREADS threads on each of the 152 SMs (two waves of 2048)
             int n1 = A.n1;
-            int zc = (int)std::max<int64_t>(1, std::min<int64_t>(16, (int64_t)n1 * n1 * n1 / (2 * 2048 * 152)));
+            int zc = (int)std::max<int64_t>(1, std::min<int64_t>(16, (int64_t)n1 * n1 * n1 / ((int64_t)MG_COEF_THREADS * 152)));
             CoefView S{(const float *)A.val, n1, zc};
             unsigned bx = line_block((unsigned)n1), by = std::min(256u / bx, (unsigned)n1);
             dim3 g((unsigned)((n1 + bx - 1) / bx), (unsigned)((n1 + by - 1) / by), (unsigned)((n1 + zc - 1) / zc)),
@@ -537,8 +547,11 @@ static void gs_sweep(mg_hierarchy *h, int l, T *x, bool post, cudaStream_t s)
 }
 
 template <typename T>
-static int smooth(mg_hierarchy *h, int l, int c, bool post, cudaStream_t s, bool fuse_last = false)
+static int smooth(mg_hierarchy *h, int l, int c, bool post, cudaStream_t s, bool fuse_last = false,
+                  bool first_done = false)
 {
+    // first_done: the step from x = 0 was taken by the kernel that made the level's
+    // right-hand side (zfuse, outer_z)
     LevelD &L = h->lev[l];
     T *b = (T *)L.b, *d = (T *)L.d;
     const int last = h->opt.smoother == MG_JACOBI ? 0 : h->opt.cheb_degree - 1;  // the last step of this application
@@ -552,14 +565,15 @@ static int smooth(mg_hierarchy *h, int l, int c, bool post, cudaStream_t s, bool
     }
     if (h->opt.smoother == MG_JACOBI) {
         if (c < 0) {
-            sweep<T>(h, l, SW_JACOBI_Z, nullptr, b, (T *)L.x[0], d, L.omega, 0.0, s, fuse_last);
+            if (!first_done) sweep<T>(h, l, SW_JACOBI_Z, nullptr, b, (T *)L.x[0], d, L.omega, 0.0, s, fuse_last);
             return 0;
         }
         sweep<T>(h, l, SW_JACOBI, (T *)L.x[c], b, (T *)L.x[1 - c], d, L.omega, 0.0, s, fuse_last);
         return 1 - c;
     }
     if (c < 0) {
-        sweep<T>(h, l, SW_CHEBF_Z, nullptr, b, (T *)L.x[0], d, L.cheb_c0, 0.0, s, fuse_last && last == 0);
+        if (!first_done)
+            sweep<T>(h, l, SW_CHEBF_Z, nullptr, b, (T *)L.x[0], d, L.cheb_c0, 0.0, s, fuse_last && last == 0);
         c = 0;
     } else {
         sweep<T>(h, l, SW_CHEBF, (T *)L.x[c], b, (T *)L.x[1 - c], d, L.cheb_c0, 0.0, s, fuse_last && last == 0);
@@ -573,8 +587,37 @@ static int smooth(mg_hierarchy *h, int l, int c, bool post, cudaStream_t s, bool
     return c;
 }
 
+// The first pre-smoothing step of level l (from x = 0) as a ZStep for the kernel that
+// produces the level's right-hand side; bytes: what that step adds to the kernel's traffic
 template <typename T>
-static void restrict_to(mg_hierarchy *h, int l, const T *r, cudaStream_t s)
+static mgk::ZStep<T> zstep_of(mg_hierarchy *h, int l, double *bytes)
+{
+    LevelD &L = h->lev[l];
+    const DevMat &M = L.A;
+    const int sv = sizeof(T);
+    mgk::ZStep<T> Z{};
+    if (M.fmt == MG_STORAGE_COEF)
+        Z.dinv = (const T *)L.zdinv;
+    else if (M.fmt == MG_STORAGE_STENCIL)
+        Z.cdinv = (T)M.sdinv;
+    else if (M.dinv)  // FP64 levels; FP32 ELL, CSR and SELL levels
+        Z.dinv = (const T *)M.dinv;
+    else if (M.fmt == MG_STORAGE_DIA)
+        Z.diag = (const T *)M.val + (int64_t)M.center * M.ld;
+    else
+        throw Error(MG_EINVAL, "level has no diagonal for the fused first smoothing step");
+    if (M.fmt == MG_STORAGE_COEF && !L.zdinv) throw Error(MG_EINVAL, "coefficient level without D^-1");
+    const bool cheb = h->opt.smoother == MG_CHEBYSHEV;
+    Z.out = (T *)L.x[0];
+    Z.d = (T *)L.d;
+    Z.c1 = (T)(cheb ? L.cheb_c0 : L.omega);
+    *bytes += (M.fmt == MG_STORAGE_STENCIL ? 0.0 : (double)L.n * sv) + (cheb ? 2.0 : 1.0) * L.n * sv;
+    return Z;
+}
+
+// zf: level l - 1's first smoothing step rides on the restriction (zfuse)
+template <typename T>
+static void restrict_to(mg_hierarchy *h, int l, const T *r, cudaStream_t s, bool zf = false)
 {
     LevelD &F = h->lev[l], &C = h->lev[l - 1];
     if (h->tail_rec && l <= h->tail_level) {
@@ -588,20 +631,31 @@ static void restrict_to(mg_hierarchy *h, int l, const T *r, cudaStream_t s)
     int sv = sizeof(T);
     double bytes = (double)F.n * sv + (double)C.n * sv;
     if (!F.structured) bytes += mat_bytes(F.R, sv);
+    mgk::ZStep<T> Z{};
+    if (zf) Z = zstep_of<T>(h, l - 1, &bytes);
     LaunchScope ls(h, s, MG_K_RESTRICT, l, bytes);
-    if (F.structured) {
-        unsigned l1 = (unsigned)(C.N - 1), bx = line_block(l1);
-        dim3 g((l1 + bx - 1) / bx, l1, h->dim == 3 ? l1 : 1);
-        bool pdl = h->opt.use_pdl != 0;
-        if (h->dim == 3)
-            klaunch(pdl, k_restrict_q1<T, 3>, g, dim3(bx), 0, s, r, (T *)C.b, C.N);
-        else
-            klaunch(pdl, k_restrict_q1<T, 2>, g, dim3(bx), 0, s, r, (T *)C.b, C.N);
-    } else {  // explicit R in SELL-32
-        klaunch(h->opt.use_pdl != 0, k_sell_apply<T, false>, dim3(grid_for(C.n)), dim3(256), 0, s,
-                (const int64_t *)F.R.rowptr, (const int32_t *)F.R.col, (const T *)F.R.val, (const int32_t *)F.R.perm,
-                (int)C.n, r, (T *)C.b);
-    }
+    const bool pdl = h->opt.use_pdl != 0;
+    auto go = [&](auto zm) {
+        constexpr int ZM = decltype(zm)::value;
+        if (F.structured) {
+            unsigned l1 = (unsigned)(C.N - 1), bx = line_block(l1);
+            dim3 g((l1 + bx - 1) / bx, l1, h->dim == 3 ? l1 : 1);
+            if (h->dim == 3)
+                klaunch(pdl, k_restrict_q1<T, 3, ZM>, g, dim3(bx), 0, s, r, (T *)C.b, C.N, Z);
+            else
+                klaunch(pdl, k_restrict_q1<T, 2, ZM>, g, dim3(bx), 0, s, r, (T *)C.b, C.N, Z);
+        } else {  // explicit R in SELL-32
+            klaunch(pdl, k_sell_apply<T, false, ZM>, dim3(grid_for(C.n)), dim3(256), 0, s,
+                    (const int64_t *)F.R.rowptr, (const int32_t *)F.R.col, (const T *)F.R.val,
+                    (const int32_t *)F.R.perm, (int)C.n, r, (T *)C.b, Z);
+        }
+    };
+    if (!zf)
+        go(std::integral_constant<int, 0>());
+    else if (h->opt.smoother == MG_CHEBYSHEV)
+        go(std::integral_constant<int, SW_CHEBF_Z>());
+    else
+        go(std::integral_constant<int, SW_JACOBI_Z>());
 }
 
 template <typename T>
@@ -622,8 +676,8 @@ static void prolong_add(mg_hierarchy *h, int l, const T *xc, T *xf, cudaStream_t
     if (!F.structured) bytes += mat_bytes(F.P, sv);
     LaunchScope ls(h, s, MG_K_PROLONG, l, bytes);
     if (F.structured) {
-        unsigned l1 = (unsigned)(F.N - 1), nx = (unsigned)C.N, bx = line_block(nx);  // pairs of fine points
-        dim3 g((nx + bx - 1) / bx, l1, h->dim == 3 ? l1 : 1);
+        unsigned nx = (unsigned)C.N, bx = line_block(nx);  // one thread per coarse cell corner (X, Y[, Z])
+        dim3 g((nx + bx - 1) / bx, nx, h->dim == 3 ? nx : 1);
         bool pdl = h->opt.use_pdl != 0;
         if (h->dim == 3)
             klaunch(pdl, k_prolong_q1<T, 3>, g, dim3(bx), 0, s, xc, xf, C.N);
@@ -632,7 +686,7 @@ static void prolong_add(mg_hierarchy *h, int l, const T *xc, T *xf, cudaStream_t
     } else {  // explicit P in SELL-32
         klaunch(h->opt.use_pdl != 0, k_sell_apply<T, true>, dim3(grid_for(F.n)), dim3(256), 0, s,
                 (const int64_t *)F.P.rowptr, (const int32_t *)F.P.col, (const T *)F.P.val, (const int32_t *)F.P.perm,
-                (int)F.n, xc, xf);
+                (int)F.n, xc, xf, mgk::ZStep<T>{});
     }
 }
 
@@ -680,17 +734,23 @@ static void launch_tail(mg_hierarchy *h, cudaStream_t s)
     h->tail_ops.clear();
 }
 
+// first_done: the finest level's first smoothing step was taken by the outer residual
 template <typename T>
-static int enqueue_vcycle(mg_hierarchy *h, cudaStream_t s)
+static int enqueue_vcycle(mg_hierarchy *h, cudaStream_t s, bool first_done = false)
 {
     int Lf = h->Lf;
     std::vector<int> cur((size_t)h->nlev, -1);
     h->tail_ops.clear();
     h->tail_rec = h->tail_level >= 1;
+    // fz[l]: level l's first smoothing step was taken by the kernel that produced its
+    // right-hand side (the outer residual on the finest level, the restriction below it)
+    std::vector<char> fz((size_t)h->nlev, 0);
+    fz[Lf] = first_done;
+    for (int l = 1; l < Lf; l++) fz[l] = h->zfuse && !(h->tail_rec && l <= h->tail_level);
     for (int l = Lf; l >= 1; l--) {  // pre-smoothing and restriction of the residual
         LevelD &L = h->lev[l];
         int c = -1;
-        for (int a = 0; a < h->opt.nu_pre; a++) c = smooth<T>(h, l, c, false, s);
+        for (int a = 0; a < h->opt.nu_pre; a++) c = smooth<T>(h, l, c, false, s, false, fz[l] && a == 0);
         const T *r;
         if (c < 0) {
             r = (const T *)L.b;  // b - A 0 = b
@@ -698,7 +758,7 @@ static int enqueue_vcycle(mg_hierarchy *h, cudaStream_t s)
             sweep<T>(h, l, SW_RESID, (T *)L.x[c], (T *)L.b, (T *)L.t, nullptr, 0.0, 0.0, s);
             r = (const T *)L.t;
         }
-        restrict_to<T>(h, l, r, s);
+        restrict_to<T>(h, l, r, s, l - 1 >= 1 && fz[l - 1]);
         cur[l] = c;
     }
     if (h->tail_rec) {  // the coarsest solve belongs to the tail launch
@@ -752,6 +812,20 @@ static int enqueue_vcycle(mg_hierarchy *h, cudaStream_t s)
     return cur[Lf];
 }
 
+template <typename MK>
+static void launch_fp64_rows(mg_hierarchy *h, const DevMat &A, MK &&mk)
+{
+    if (A.fmt == MG_STORAGE_DIA) {
+        with_dia_k(A.K, [&](auto k) { mk(std::integral_constant<int, 3>(), k); });
+    } else if (A.fmt == MG_STORAGE_ELL) {
+        mk(std::integral_constant<int, 2>(), std::integral_constant<int, 1>());
+    } else if (A.fmt == MG_STORAGE_SELL) {
+        mk(std::integral_constant<int, 4>(), std::integral_constant<int, 1>());
+    } else {
+        mk(std::integral_constant<int, 1>(), std::integral_constant<int, 1>());
+    }
+}
+
 template <typename T>
 static void enqueue_outer(mg_hierarchy *h, cudaStream_t s)
 {
@@ -760,23 +834,43 @@ static void enqueue_outer(mg_hierarchy *h, cudaStream_t s)
     int n = (int)F.n;
     double bytes = mat_bytes(A, 8) + 16.0 * n + (double)n * sizeof(T);
     double entries = mat_entries(A);
-    LaunchScope ls(h, s, MG_K_OUTER, h->Lf, bytes, 2.0 * entries + 3.0 * n);
     MatView<double> v = view<double>(A);
     dim3 g(reduce_grid(n)), blk(256);
     T *r = (T *)F.b;
     bool pdl = h->opt.use_pdl != 0;
     const double *x = h->x64, *b = h->b64;
+    if constexpr (std::is_same<T, float>::value) {
+        if (h->outer_z) {  // and the finest level's first smoothing step (from x = 0)
+            const bool cheb = h->opt.smoother == MG_CHEBYSHEV;
+            mgk::ZStep<float> Z = zstep_of<float>(h, h->Lf, &bytes);
+            LaunchScope ls(h, s, MG_K_OUTER, h->Lf, bytes, 2.0 * entries + 5.0 * n);
+            launch_fp64_rows(h, A, [&](auto fmt, auto k) {
+                constexpr int FMT = decltype(fmt)::value, K = decltype(k)::value;
+                if (cheb)
+                    klaunch(pdl, k_outer_resid<float, FMT, K, SW_CHEBF_Z>, g, blk, 0, s, v, n, x, b, r, h->partial,
+                            h->ticket, h->norm2, Z);
+                else
+                    klaunch(pdl, k_outer_resid<float, FMT, K, SW_JACOBI_Z>, g, blk, 0, s, v, n, x, b, r, h->partial,
+                            h->ticket, h->norm2, Z);
+            });
+            return;
+        }
+    }
+    LaunchScope ls(h, s, MG_K_OUTER, h->Lf, bytes, 2.0 * entries + 3.0 * n);
     if (A.fmt == MG_STORAGE_DIA) {
         with_dia_k(A.K, [&](auto k) {
             klaunch(pdl, k_outer_resid<T, 3, decltype(k)::value>, g, blk, 0, s, v, n, x, b, r, h->partial, h->ticket,
-                    h->norm2);
+                    h->norm2, mgk::ZStep<float>{});
         });
     } else if (A.fmt == MG_STORAGE_ELL) {
-        klaunch(pdl, k_outer_resid<T, 2, 1>, g, blk, 0, s, v, n, x, b, r, h->partial, h->ticket, h->norm2);
+        klaunch(pdl, k_outer_resid<T, 2, 1>, g, blk, 0, s, v, n, x, b, r, h->partial, h->ticket, h->norm2,
+                mgk::ZStep<float>{});
     } else if (A.fmt == MG_STORAGE_SELL) {
-        klaunch(pdl, k_outer_resid<T, 4, 1>, g, blk, 0, s, v, n, x, b, r, h->partial, h->ticket, h->norm2);
+        klaunch(pdl, k_outer_resid<T, 4, 1>, g, blk, 0, s, v, n, x, b, r, h->partial, h->ticket, h->norm2,
+                mgk::ZStep<float>{});
     } else {
-        klaunch(pdl, k_outer_resid<T, 1, 1>, g, blk, 0, s, v, n, x, b, r, h->partial, h->ticket, h->norm2);
+        klaunch(pdl, k_outer_resid<T, 1, 1>, g, blk, 0, s, v, n, x, b, r, h->partial, h->ticket, h->norm2,
+                mgk::ZStep<float>{});
     }
 }
 
@@ -804,7 +898,7 @@ static void enqueue_v(mg_hierarchy *h, cudaStream_t s)
     h->update_fused = false;
     h->fuse_update = true;
     if (h->mixed) {
-        int c = enqueue_vcycle<float>(h, s);
+        int c = enqueue_vcycle<float>(h, s, h->outer_z);
         h->fuse_update = false;
         if (!h->update_fused) enqueue_update<float>(h, c, s);
     } else {
@@ -815,19 +909,6 @@ static void enqueue_v(mg_hierarchy *h, cudaStream_t s)
 }
 
 // ---- preconditioned CG ----
-template <typename MK>
-static void launch_fp64_rows(mg_hierarchy *h, const DevMat &A, MK &&mk)
-{
-    if (A.fmt == MG_STORAGE_DIA) {
-        with_dia_k(A.K, [&](auto k) { mk(std::integral_constant<int, 3>(), k); });
-    } else if (A.fmt == MG_STORAGE_ELL) {
-        mk(std::integral_constant<int, 2>(), std::integral_constant<int, 1>());
-    } else if (A.fmt == MG_STORAGE_SELL) {
-        mk(std::integral_constant<int, 4>(), std::integral_constant<int, 1>());
-    } else {
-        mk(std::integral_constant<int, 1>(), std::integral_constant<int, 1>());
-    }
-}
 
 // r_0 = b - A x_0 (FP64, and in the inner precision as the V-cycle's right-hand side)
 template <typename T>
@@ -1056,6 +1137,7 @@ extern "C" void mg_options_default(mg_options *o)
     o->use_graph = 1;
     o->use_pdl = 1;
     o->coarse_tail = 2;
+    o->fuse_first = 1;
 }
 
 extern "C" int64_t mg_ndofs(int dim, int element, int n_cells)
@@ -1805,6 +1887,12 @@ void mgi::build_hierarchy(mg_hierarchy *h, const mg_problem *p, const mg_options
     h->nlev = p->n_levels;
     h->Lf = p->n_levels - 1;
     h->mixed = o->precision == MG_MIXED;
+    // the first pre-smoothing step of a level (from x = 0) rides on the kernel that makes
+    // the level's right-hand side: the restriction on the levels below the finest, the
+    // outer residual on the finest level of a mixed hierarchy
+    h->zfuse = o->fuse_first != 0 && h->Lf >= 1 && o->nu_pre >= 1 &&
+               (o->smoother == MG_JACOBI || o->smoother == MG_CHEBYSHEV);
+    h->outer_z = h->zfuse && h->mixed;
     h->inner_size = h->mixed ? 4 : 8;
     if (dev) h->dev = *dev;
     h->own_alloc = !h->dev.alloc;
@@ -1937,6 +2025,7 @@ void mgi::build_hierarchy(mg_hierarchy *h, const mg_problem *p, const mg_options
             // instead of scanning the row (the same value: 1/a_ii rounded once)
             if (h->mixed && l >= 1 && lf != MG_STORAGE_DIA && lf != MG_STORAGE_STENCIL && lf != MG_STORAGE_COEF)
                 L.A.dinv = vec((size_t)L.A.ld * 4);
+            if (h->zfuse && l >= 1 && lf == MG_STORAGE_COEF) L.zdinv = vec((size_t)L.A.ld * 4);
             if (gs && l >= 1) {  // the colour-major copy of A for the Gauss-Seidel sweeps (CSR for SELL levels)
                 plan_matrix(L.G, A[l], lf == MG_STORAGE_SELL ? MG_STORAGE_CSR : lf, dim, L.N, sv, S, take);
                 if (!h->mixed) L.G.dinv = vec((size_t)L.G.ld * 8);
@@ -2005,6 +2094,12 @@ void mgi::build_hierarchy(mg_hierarchy *h, const mg_problem *p, const mg_options
             std::vector<float> v32;
             if (L.A.fmt == MG_STORAGE_COEF) {
                 CK(cudaMemcpyAsync(L.A.val, kap[l].data(), kap[l].size() * 4, cudaMemcpyHostToDevice, h->s));
+                if (L.zdinv) {
+                    const int n1 = L.A.n1;
+                    mgk::k_coef_dinv<<<dim3((unsigned)((n1 + 127) / 128), (unsigned)n1, (unsigned)n1), 128, 0, h->s>>>(
+                        (const float *)L.A.val, n1, (float *)L.zdinv);
+                    CK(cudaGetLastError());
+                }
                 CK(cudaStreamSynchronize(h->s));
             } else {
                 mgh::round_fp32(A[l], v32);

@@ -45,7 +45,7 @@ class mg_options(ctypes.Structure):
                 ("cheb_ratio", ctypes.c_double), ("power_iters", ctypes.c_int),
                 ("power_seed", ctypes.c_uint64), ("precision", ctypes.c_int), ("storage", ctypes.c_int),
                 ("max_iters", ctypes.c_int), ("use_graph", ctypes.c_int), ("use_pdl", ctypes.c_int),
-                ("coarse_tail", ctypes.c_int)]
+                ("coarse_tail", ctypes.c_int), ("fuse_first", ctypes.c_int)]
 
 
 class mg_rhs(ctypes.Structure):
