@@ -150,8 +150,7 @@ KERNEL_PARTS = {
                     ("sweep.cuh", "sweep_out"), ("sweep.cuh", "k_dia_sweep")],
     "k_coef_sweep": [("sweep.cuh", "pdl_enter"), ("sweep.cuh", "struct Ar<float>"), ("sweep.cuh", "sweep_out"),
                      ("sweep.cuh", "sweep_out_v"), ("sweep.cuh", "fused_update"), ("sweep.cuh", "struct CoefView"),
-                     ("sweep.cuh", "coef_corner"), ("sweep.cuh", "coef_edge_x"), ("sweep.cuh", "coef_edge_y"),
-                     ("sweep.cuh", "coef_march"), ("sweep.cuh", "k_coef_sweep")],
+                     ("sweep.cuh", "k_coef_sweep")],
     "k_outer_resid": [("sweep.cuh", "pdl_enter"), ("sweep.cuh", "struct Ar<float>"), ("sweep.cuh", "sweep_out_v"),
                       ("kernels.cuh", "block_sum"), ("kernels.cuh", "finish_norm"), ("kernels.cuh", "fp64_row"),
                       ("kernels.cuh", "fp64_dof"), ("kernels.cuh", "struct ZStep"), ("kernels.cuh", "zstep_dinv"),

@@ -353,72 +353,64 @@ __global__ void __launch_bounds__(256) k_stencil_march(StencilView<T> S, int zc,
 // K_ref has 1/3 on the diagonal, 0 between edge-adjacent corners and -1/12 between the
 // other corner pairs. With kap_e = k_e h / 12 row i is therefore
 //     (A x)_i = sum over the 8 cells e around vertex i of kap_e (4 x_i - s_e),
-// s_e the sum of x at the four corners of e that share no edge with i: for the cell on
-// the side (sx, sy, sz) of i these are the corner (sx, sy) of i's own plane, and the
-// corner (sx, sy) and the two edge columns (sx, 0), (0, sy) of plane z + sz. s_e is summed
-// in pairs, s_e = V + U with V = x(sx, sy) on the two planes (lower plane first) and
-// U = x(sx, 0) + x(0, sy) on plane z + sz, so that a constant x gives exactly
-// 4 x_i - s_e = 0 (the interior row sums vanish in FP32 as they do in the assembled
-// matrix); a_ii = 4 sum_e kap_e, the cells summed per cell plane ((k0 + k1) + (k2 + k3)),
-// lower plane first. Corners on the Dirichlet boundary hold 0. kap: (n1 + 1)^3 cells, x
-// fastest.
+// s_e the sum of x at the four corners of e that share no edge with i (three across a
+// face, one across the body): the matrix is formed from one value per cell and never
+// stored. s_e is summed in pairs, (x_f1 + x_f2) + (x_f3 + x_b), so that a constant x gives
+// exactly 4 x_i - s_e = 0 (the interior row sums vanish in FP32 as they do in the
+// assembled matrix); a_ii = 4 sum_e kap_e. Corners on the Dirichlet boundary hold 0.
+// kap: (n1 + 1)^3 cells, x fastest.
 //
 // A thread owns the grid column (vx, vy) over `zc` consecutive planes and marches along
-// z. Each step loads the new plane z + 1 (9 x values, gathered through L1 where
-// neighbouring threads share them) and the new cell plane (4 kap values). Every pair is
-// added once per column and carried in registers: V between planes z and z + 1 serves the
-// upper cells of point z and the lower cells of point z + 1; U of plane p serves the
-// upper cells of point p - 1 and the lower cells of point p + 1 (so U is kept for two
-// steps); the cell-plane sum serves two points. Per point: 8 pair additions, 8 s_e
-// additions and 16 fused multiply-adds. Columns off the grid in x or y are selected to the
-// Dirichlet value 0; that selection is compiled only for warps that touch the x or y
-// boundary (a warp is 32 consecutive columns of one grid line, so the test is
-// warp-uniform). Planes z = -1 and z = n1 fall in the zero halo of the x buffer (x is
-// padded by n1^2 + n1 + 1 zeros on both sides, written at setup and never again). Row
-// indices fit in 32 bits (n1^3 < 2^31 is checked at setup).
-
-#ifndef MG_COEF_MIN_BLOCKS
-#define MG_COEF_MIN_BLOCKS 4  // four 256-thread blocks per SM
-#endif
-#ifndef MG_COEF_THREADS
-#define MG_COEF_THREADS 4096  // threads per SM the split into plane chunks aims at
-#endif
+// z: the x values of the 3 x 3 neighbouring columns on planes z - 1, z, z + 1 and the kap
+// values of the 2 x 2 neighbouring cell columns on cell planes z, z + 1 stay in
+// registers, so each step loads only the new plane (9 x and 4 kap values, gathered
+// through L1 where neighbouring threads share them) instead of all 29. The three planes
+// rotate by renaming (the loop is unrolled three times), loads use one row pointer per
+// dy with immediate dx offsets. Columns off the grid in x or y are selected to the
+// Dirichlet value 0; planes z = -1 and z = n1 fall in the zero halo of the x buffer (x is
+// padded by n1^2 + n1 + 1 zeros on both sides, written at setup and never again).
 struct CoefView {
     const float *kap;
     int n1;  // interior points per axis (cells per axis - 1)
     int zc;  // planes per thread
 };
 
-// quadrant q = a + 2 b of the 3 x 3 column neighbourhood, (sx, sy) = (a ? 1 : -1, b ? 1 : -1);
-// column c = (dx + 1) + 3 (dy + 1)
-__device__ __forceinline__ constexpr int coef_corner(int q) { return ((q & 1) ? 2 : 0) + ((q & 2) ? 6 : 0); }
-__device__ __forceinline__ constexpr int coef_edge_x(int q) { return (q & 1) ? 5 : 3; }
-__device__ __forceinline__ constexpr int coef_edge_y(int q) { return (q & 2) ? 7 : 1; }
-
-template <int MODE, bool EDGE>
-__device__ __forceinline__ void coef_march(const CoefView &S, int vx, int vy, const float *__restrict__ x,
-                                           const float *__restrict__ b, float *__restrict__ out,
-                                           float *__restrict__ d, float c1, float c2, double *__restrict__ upd)
+#ifndef MG_COEF_MIN_BLOCKS
+#define MG_COEF_MIN_BLOCKS 4  // 64 registers: four 256-thread blocks per SM (measured best of 1, 4, 6)
+#endif
+#ifndef MG_COEF_THREADS
+#define MG_COEF_THREADS 4096  // threads per SM the split into plane chunks aims at
+#endif
+template <int MODE>
+__global__ void __launch_bounds__(256, MG_COEF_MIN_BLOCKS) k_coef_sweep(CoefView S, const float *__restrict__ x,
+                                                    const float *__restrict__ b, float *__restrict__ out,
+                                                    float *__restrict__ d, float c1, float c2,
+                                                    double *__restrict__ upd)
 {
     constexpr bool Z = IsZero<MODE>::value;
-    const int n1 = S.n1, nc = n1 + 1, plane = n1 * n1;
+    pdl_enter();
+    const int n1 = S.n1, nc = n1 + 1;
+    const int vx = blockIdx.x * blockDim.x + threadIdx.x, vy = blockIdx.y * blockDim.y + threadIdx.y;
+    if (vx >= n1 || vy >= n1) return;
     const int z0 = blockIdx.z * S.zc, z1 = min(z0 + S.zc, n1);
-    const int64_t cplane = (int64_t)nc * nc;
+    const int64_t plane = (int64_t)n1 * n1, cplane = (int64_t)nc * nc;
+    // column c = (dx + 1) + 3 (dy + 1) of the point's 3 x 3 neighbourhood lies in the grid
+    const bool xlo = vx > 0, xhi = vx < n1 - 1, ylo = vy > 0, yhi = vy < n1 - 1;
     bool cin[9];
 #pragma unroll
     for (int c = 0; c < 9; c++) {
         const int dx = c % 3 - 1, dy = c / 3 - 1;
-        cin[c] = (dx >= 0 || vx > 0) && (dx <= 0 || vx < n1 - 1) && (dy >= 0 || vy > 0) && (dy <= 0 || vy < n1 - 1);
+        cin[c] = (dx >= 0 || xlo) && (dx <= 0 || xhi) && (dy >= 0 || ylo) && (dy <= 0 || yhi);
     }
-    const float *xr = x + vx + (int64_t)n1 * vy + (int64_t)plane * (z0 - 1);  // column (vx, vy), plane z0 - 1
-    const float *kr = S.kap + vx + (int64_t)nc * vy + cplane * z0;            // cell column (vx, vy), plane z0
+    const float *xr = x + vx + (int64_t)n1 * vy + plane * (z0 - 1);  // column (vx, vy), plane z0 - 1
+    const float *kr = S.kap + vx + (int64_t)nc * vy + cplane * z0;   // cell column (vx, vy), plane z0
     auto load_plane = [&](float P[9]) {  // the 9 columns at plane xr, then advance xr
         const float *rm = xr - n1, *rp = xr + n1;
 #pragma unroll
         for (int c = 0; c < 9; c++) {
             const int dx = c % 3 - 1, dy = c / 3 - 1;
             const float v = __ldg((dy < 0 ? rm : (dy > 0 ? rp : xr)) + dx);
-            P[c] = !EDGE || cin[c] ? v : 0.0f;
+            P[c] = cin[c] ? v : 0.0f;
         }
         xr += plane;
     };
@@ -429,84 +421,92 @@ __device__ __forceinline__ void coef_march(const CoefView &S, int vx, int vy, co
         K[3] = __ldg(kr + nc + 1);
         kr += cplane;
     };
-    // carried state at the start of step z: the centre and corners of plane z, U of planes
-    // z - 1 (Um) and z (Uc), V between planes z - 1 and z (Vm), the cell plane z (the cells
-    // below) and its sum
-    float xc = 0.0f, Cc[4] = {}, Um[4] = {}, Uc[4] = {}, Vm[4] = {}, Kc[4];
-    if (!Z) {
-        float P[9];
-        load_plane(P);  // z0 - 1
+    // b_i (and d_i for the later Chebyshev steps) of the point on plane z, loaded with the
+    // plane so that all of a step's loads are in flight together
+    auto load_bd = [&](int z, float &bi, float &di) {
+        const int i = vx + n1 * vy + (int)(plane * z);
+        bi = __ldg(b + i);
+        di = MODE == SW_CHEB ? d[i] : 0.0f;
+    };
+    // one point: planes Pm, P0, Pp (z - 1, z, z + 1), cell planes Kc, Kn (z, z + 1)
+    auto point = [&](const float Pm[9], const float P0[9], const float Pp[9], const float Kc[4], const float Kn[4],
+                     int z, float bi, float di) {
+        const int i = vx + n1 * vy + (int)(plane * z);
+        // the 8 cells around the point: cell (vx + a, vy + b, z + c), e = a + 2 b + 4 c
+        float kap[8];
 #pragma unroll
-        for (int q = 0; q < 4; q++) {
-            Um[q] = P[coef_edge_x(q)] + P[coef_edge_y(q)];
-            Cc[q] = P[coef_corner(q)];
+        for (int e = 0; e < 4; e++) {
+            kap[e] = Kc[e];
+            kap[e + 4] = Kn[e];
         }
-        load_plane(P);  // z0
-#pragma unroll
-        for (int q = 0; q < 4; q++) {
-            Vm[q] = Cc[q] + P[coef_corner(q)];
-            Uc[q] = P[coef_edge_x(q)] + P[coef_edge_y(q)];
-            Cc[q] = P[coef_corner(q)];
-        }
-        xc = P[4];
-    }
-    load_cells(Kc);
-    float kc = (Kc[0] + Kc[1]) + (Kc[2] + Kc[3]);
-    int i = vx + n1 * vy + plane * z0;
-    for (int z = z0; z < z1; z++, i += plane) {
-        float P[9], Kn[4];
-        if (!Z) load_plane(P);  // z + 1
-        load_cells(Kn);         // cell plane z + 1
-        const float bi = __ldg(b + i), di = MODE == SW_CHEB ? d[i] : 0.0f;
-        const float kn = (Kn[0] + Kn[1]) + (Kn[2] + Kn[3]);
-        const float dinv = Ar<float>::rcp(4.0f * (kc + kn));
+        const float ksum = ((kap[0] + kap[1]) + (kap[2] + kap[3])) + ((kap[4] + kap[5]) + (kap[6] + kap[7]));
+        const float dinv = Ar<float>::rcp(4.0f * ksum);
         if (Z) {
             sweep_out_v<float, MODE>(i, 0.0f, dinv, 0.0f, bi, di, out, d, c1, c2);
-        } else {
-            float Up[4], Vp[4];
-#pragma unroll
-            for (int q = 0; q < 4; q++) {
-                Up[q] = P[coef_edge_x(q)] + P[coef_edge_y(q)];
-                Vp[q] = Cc[q] + P[coef_corner(q)];
-            }
-            // the cells in the order e = a + 2 b + 4 c: below (c = 0), then above
-            float acc = 0.0f;
-#pragma unroll
-            for (int q = 0; q < 4; q++) acc = fmaf(Kc[q], fmaf(4.0f, xc, -(Vm[q] + Um[q])), acc);
-#pragma unroll
-            for (int q = 0; q < 4; q++) acc = fmaf(Kn[q], fmaf(4.0f, xc, -(Vp[q] + Up[q])), acc);
-            fused_update<float, MODE>(upd, i, sweep_out_v<float, MODE>(i, acc, dinv, xc, bi, di, out, d, c1, c2));
-#pragma unroll
-            for (int q = 0; q < 4; q++) {
-                Um[q] = Uc[q];
-                Uc[q] = Up[q];
-                Vm[q] = Vp[q];
-                Cc[q] = P[coef_corner(q)];
-            }
-            xc = P[4];
+            return;
         }
+        // x at stencil position p = (dx+1) + 3(dy+1) + 9(dz+1): column p % 9 of plane p / 9
+        auto xv = [&](int p) { return p < 9 ? Pm[p] : (p < 18 ? P0[p - 9] : Pp[p - 18]); };
+        const float xc = xv(13);
+        float acc = 0.0f;
 #pragma unroll
-        for (int q = 0; q < 4; q++) Kc[q] = Kn[q];
-        kc = kn;
+        for (int e = 0; e < 8; e++) {
+            // cell e lies on the side (sx, sy, sz) of the point; its corners that share no
+            // edge with the point sit at (sx, sy, 0), (sx, 0, sz), (0, sy, sz), (sx, sy, sz)
+            const int sx = (e & 1) ? 1 : -1, sy = ((e >> 1) & 1) ? 1 : -1, sz = (e >> 2) ? 1 : -1;
+            const float fxy = xv((sx + 1) + 3 * (sy + 1) + 9);
+            const float fxz = xv((sx + 1) + 3 + 9 * (sz + 1));
+            const float fyz = xv(1 + 3 * (sy + 1) + 9 * (sz + 1));
+            const float fb = xv((sx + 1) + 3 * (sy + 1) + 9 * (sz + 1));
+            const float se = (fxy + fxz) + (fyz + fb);
+            acc = fmaf(kap[e], fmaf(4.0f, xc, -se), acc);
+        }
+        fused_update<float, MODE>(upd, i, sweep_out_v<float, MODE>(i, acc, dinv, xc, bi, di, out, d, c1, c2));
+    };
+    float A[9] = {}, B[9] = {}, C[9] = {}, KA[4], KB[4];
+    if (!Z) {
+        load_plane(A);  // z0 - 1
+        load_plane(B);  // z0
     }
-}
-
-template <int MODE>
-__global__ void __launch_bounds__(256, MG_COEF_MIN_BLOCKS) k_coef_sweep(CoefView S, const float *__restrict__ x,
-                                                    const float *__restrict__ b, float *__restrict__ out,
-                                                    float *__restrict__ d, float c1, float c2,
-                                                    double *__restrict__ upd)
-{
-    pdl_enter();
-    const int n1 = S.n1;
-    const int vx = blockIdx.x * blockDim.x + threadIdx.x, vy = blockIdx.y * blockDim.y + threadIdx.y;
-    if (vx >= n1 || vy >= n1) return;
-    // blockDim.x is a multiple of 32: a warp is 32 consecutive columns of one line vy
-    const int wx = vx - (threadIdx.x & 31);
-    if (wx >= 1 && wx + 31 <= n1 - 2 && vy >= 1 && vy <= n1 - 2)
-        coef_march<MODE, false>(S, vx, vy, x, b, out, d, c1, c2, upd);
-    else
-        coef_march<MODE, true>(S, vx, vy, x, b, out, d, c1, c2, upd);
+    load_cells(KA);  // cell plane z0
+    int z = z0;
+    float bi, di;
+    // roles rotate A -> B -> C (planes) and KA -> KB (cell planes) from step to step
+    for (; z + 3 <= z1; z += 3) {
+        if (!Z) load_plane(C);
+        load_cells(KB);
+        load_bd(z, bi, di);
+        point(A, B, C, KA, KB, z, bi, di);
+        if (!Z) load_plane(A);
+        load_cells(KA);
+        load_bd(z + 1, bi, di);
+        point(B, C, A, KB, KA, z + 1, bi, di);
+        if (!Z) load_plane(B);
+        load_cells(KB);
+        load_bd(z + 2, bi, di);
+        point(C, A, B, KA, KB, z + 2, bi, di);
+        // after three steps the planes are back in their roles (A = z + 2, B = z + 3); the
+        // cell planes are swapped (KA = z + 2, KB = z + 3)
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            const float t = KA[e];
+            KA[e] = KB[e];
+            KB[e] = t;
+        }
+    }
+    if (z < z1) {
+        if (!Z) load_plane(C);
+        load_cells(KB);
+        load_bd(z, bi, di);
+        point(A, B, C, KA, KB, z, bi, di);
+        z++;
+        if (z < z1) {
+            if (!Z) load_plane(A);
+            load_cells(KA);
+            load_bd(z, bi, di);
+            point(B, C, A, KB, KA, z, bi, di);
+        }
+    }
 }
 
 // Constant stencil of the rotated-Q1 face space (FP32 levels of a mixed hierarchy with a
