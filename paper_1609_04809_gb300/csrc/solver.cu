@@ -372,6 +372,10 @@ static void sweep_fmt(const DevMat &A, int n, const T *x, const T *b, T *out, T 
             unsigned bx = line_block((unsigned)n1), by = std::min(256u / bx, (unsigned)n1);
             dim3 g((unsigned)((n1 + bx - 1) / bx), (unsigned)((n1 + by - 1) / by), (unsigned)((n1 + zc - 1) / zc)),
                 blk(bx, by);
+            if constexpr (MODE == SW_RESID) {  // the pair-carrying march: faster for the residual
+                klaunch(pdl, k_coef_resid<SW_RESID>, g, blk, 0, s, S, x, b, out, d, c1, c2, upd);
+                return;
+            }
             klaunch(pdl, k_coef_sweep<MODE>, g, blk, 0, s, S, x, b, out, d, c1, c2, upd);
             return;
         } else {
@@ -835,7 +839,7 @@ static void enqueue_outer(mg_hierarchy *h, cudaStream_t s)
     double bytes = mat_bytes(A, 8) + 16.0 * n + (double)n * sizeof(T);
     double entries = mat_entries(A);
     MatView<double> v = view<double>(A);
-    dim3 g(reduce_grid(n)), blk(256);
+    dim3 g(std::min<unsigned>(reduce_grid(n), (unsigned)mgk::kOuterBlocks)), blk(256);
     T *r = (T *)F.b;
     bool pdl = h->opt.use_pdl != 0;
     const double *x = h->x64, *b = h->b64;
