@@ -21,20 +21,25 @@ namespace mgk {
 enum PcgScalar { PCG_RZ = 0, PCG_RZ_OLD = 1, PCG_PQ = 2, PCG_ALPHA = 3, PCG_BETA = 4, PCG_NSCAL = 8 };
 
 // r = b - A x in FP64 (kept in r64 and, in the inner precision, in rin: the V-cycle's
-// right-hand side); p = 0, rz_old = 0; ||r||^2 -> norm2
-template <typename Tin, int FMT, int K>
+// right-hand side); p = 0, rz_old = 0; ||r||^2 -> norm2. ZM: also the finest FP32 level's
+// first smoothing step on rin (ZStep, as in k_outer_resid).
+template <typename Tin, int FMT, int K, int ZM = 0>
 __global__ void __launch_bounds__(256, 6) k_pcg_init(MatView<double> A, int n, const double *__restrict__ x,
                                                   const double *__restrict__ b, double *__restrict__ r64,
                                                   Tin *__restrict__ rin, double *__restrict__ p, double *scal,
-                                                  double *partial, unsigned *ticket, double *norm2)
+                                                  double *partial, unsigned *ticket, double *norm2, ZStep<float> Zs)
 {
     pdl_enter();
     double sq = 0.0;
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
         int i = fp64_dof<FMT>(A, q);
+        float dv = 0.0f;
+        if constexpr (ZM != 0) dv = zstep_dinv(Zs, i);
         double ri = __dsub_rn(b[i], fp64_row<FMT, K>(A, q, i, x));
         r64[i] = ri;
         rin[i] = (Tin)ri;
+        if constexpr (ZM != 0)
+            sweep_out_v<float, ZM>(i, 0.0f, dv, 0.0f, (float)(Tin)ri, 0.0f, Zs.out, Zs.d, Zs.c1, 0.0f);
         p[i] = 0.0;
         sq = __fma_rn(ri, ri, sq);
     }
@@ -93,11 +98,13 @@ __global__ void __launch_bounds__(256, 6) k_pcg_apply(MatView<double> A, int n, 
     if (finish_norm(part, partial, ticket, scal + PCG_PQ)) scal[PCG_ALPHA] = __ddiv_rn(scal[PCG_RZ], scal[PCG_PQ]);
 }
 
-template <typename Tin>
+// ZM: also the finest FP32 level's first smoothing step on rin (ZStep, as in k_outer_resid)
+template <typename Tin, int ZM = 0>
 __global__ void __launch_bounds__(256, 6) k_pcg_update(double *__restrict__ x, double *__restrict__ r,
                                                     Tin *__restrict__ rin, const double *__restrict__ p,
                                                     const double *__restrict__ q, int n, double *scal,
-                                                    double *partial, unsigned *ticket, double *norm2)
+                                                    double *partial, unsigned *ticket, double *norm2,
+                                                    ZStep<float> Zs)
 {
     pdl_enter();
     double alpha = scal[PCG_ALPHA];
@@ -122,6 +129,7 @@ __global__ void __launch_bounds__(256, 6) k_pcg_update(double *__restrict__ x, d
             r[j] = ri;
             rin[j] = (Tin)ri;
             sq = __fma_rn(ri, ri, sq);
+            zstep<float, ZM>(Zs, j, (float)(Tin)ri);
         }
     }
     for (; i < n; i += st) {
@@ -130,6 +138,7 @@ __global__ void __launch_bounds__(256, 6) k_pcg_update(double *__restrict__ x, d
         r[i] = ri;
         rin[i] = (Tin)ri;
         sq = __fma_rn(ri, ri, sq);
+        zstep<float, ZM>(Zs, i, (float)(Tin)ri);
     }
     if (finish_norm(sq, partial, ticket, norm2)) scal[PCG_RZ_OLD] = scal[PCG_RZ];
 }

@@ -922,15 +922,26 @@ static void enqueue_pcg_init(mg_hierarchy *h, cudaStream_t s)
     const DevMat &A = h->A64;
     int n = (int)F.n;
     double entries = mat_entries(A);
-    LaunchScope ls(h, s, MG_K_OUTER, h->Lf, mat_bytes(A, 8) + 32.0 * n + (double)n * sizeof(T),
-                   2.0 * entries + 3.0 * n);
+    double bytes = mat_bytes(A, 8) + 32.0 * n + (double)n * sizeof(T);
+    mgk::ZStep<float> Z{};
+    const bool zf = std::is_same<T, float>::value && h->outer_z;  // and the finest level's first step
+    if (zf) Z = zstep_of<float>(h, h->Lf, &bytes);
+    LaunchScope ls(h, s, MG_K_OUTER, h->Lf, bytes, 2.0 * entries + (zf ? 5.0 : 3.0) * n);
     MatView<double> v = view<double>(A);
     bool pdl = h->opt.use_pdl != 0;
     dim3 g(reduce_grid(n)), blk(256);
+    const int zm = !zf ? 0 : (h->opt.smoother == MG_CHEBYSHEV ? (int)SW_CHEBF_Z : (int)SW_JACOBI_Z);
     launch_fp64_rows(h, A, [&](auto fmt, auto k) {
-        klaunch(pdl, k_pcg_init<T, decltype(fmt)::value, decltype(k)::value>, g, blk, 0, s, v, n,
-                (const double *)h->x64, (const double *)h->b64, h->pcg_r, (T *)F.b, h->pcg_p, h->pcg_scal,
-                h->partial, h->ticket, h->norm2);
+        constexpr int FMT = decltype(fmt)::value, K = decltype(k)::value;
+        auto go = [&](auto kern) {
+            klaunch(pdl, kern, g, blk, 0, s, v, n, (const double *)h->x64, (const double *)h->b64, h->pcg_r,
+                    (T *)F.b, h->pcg_p, h->pcg_scal, h->partial, h->ticket, h->norm2, Z);
+        };
+        if constexpr (std::is_same<T, float>::value) {
+            if (zm == SW_CHEBF_Z) return go(k_pcg_init<T, FMT, K, SW_CHEBF_Z>);
+            if (zm == SW_JACOBI_Z) return go(k_pcg_init<T, FMT, K, SW_JACOBI_Z>);
+        }
+        go(k_pcg_init<T, FMT, K, 0>);
     });
 }
 
@@ -943,7 +954,8 @@ static void enqueue_pcg_iter(mg_hierarchy *h, cudaStream_t s)
     int n = (int)F.n, sv = sizeof(T);
     bool pdl = h->opt.use_pdl != 0;
     dim3 g(grid_for(n)), blk(256);
-    int c = enqueue_vcycle<T>(h, s);
+    // the V-cycle's finest first step was taken by the kernel that wrote r (init or update)
+    int c = enqueue_vcycle<T>(h, s, std::is_same<T, float>::value && h->outer_z);
     const T *z = (const T *)F.x[c];
     dim3 gr(reduce_grid(n));  // the kernels that end in an inner product
     {
@@ -965,9 +977,25 @@ static void enqueue_pcg_iter(mg_hierarchy *h, cudaStream_t s)
         });
     }
     {
-        LaunchScope ls(h, s, MG_K_KRYLOV, h->Lf, 48.0 * n + (double)n * sv, 6.0 * n);
-        klaunch(pdl, k_pcg_update<T>, gr, blk, 0, s, h->x64, h->pcg_r, (T *)F.b, (const double *)h->pcg_p,
-                (const double *)h->pcg_q, n, h->pcg_scal, h->partial, h->ticket, h->norm2);
+        double bytes = 48.0 * n + (double)n * sv;
+        mgk::ZStep<float> Z{};
+        const bool zf = std::is_same<T, float>::value && h->outer_z;  // and the next V-cycle's first step
+        if (zf) Z = zstep_of<float>(h, h->Lf, &bytes);
+        LaunchScope ls(h, s, MG_K_KRYLOV, h->Lf, bytes, (zf ? 8.0 : 6.0) * n);
+        auto go = [&](auto kern) {
+            klaunch(pdl, kern, gr, blk, 0, s, h->x64, h->pcg_r, (T *)F.b, (const double *)h->pcg_p,
+                    (const double *)h->pcg_q, n, h->pcg_scal, h->partial, h->ticket, h->norm2, Z);
+        };
+        if constexpr (std::is_same<T, float>::value) {
+            if (zf && h->opt.smoother == MG_CHEBYSHEV)
+                go(k_pcg_update<T, SW_CHEBF_Z>);
+            else if (zf)
+                go(k_pcg_update<T, SW_JACOBI_Z>);
+            else
+                go(k_pcg_update<T, 0>);
+        } else {
+            go(k_pcg_update<T, 0>);
+        }
     }
 }
 

@@ -25,6 +25,7 @@ def _lib():
 
 
 def _run(dim, elem, N, L, fuse, k=None, **opts):
+    """Three V-cycles from x = 0, a solve to 1e-9 and (symmetric V-cycles) a CG solve."""
     H = mg.Hierarchy(dim, elem, N, L, k_cell=k, fuse_first=fuse, **opts)
     n = mg.mg_ndofs(dim, elem, N)
     rng = np.random.default_rng(7)
@@ -33,9 +34,14 @@ def _run(dim, elem, N, L, fuse, k=None, **opts):
     H.cycle(b, x, 3)
     xs = torch.zeros_like(b)
     st, it, hist = H.solve(b, xs, 1e-9)
+    pcg = None
+    if opts.get("nu_pre", 2) == opts.get("nu_post", 2) and opts.get("smoother") != mg.MG_GAUSS_SEIDEL:
+        xp = torch.zeros_like(b)
+        pst, pit, phist = H.pcg(b, xp, 1e-9)
+        pcg = (pst, pit, np.asarray(phist)[:pit + 1], xp.cpu().numpy())
     info = H.info()
     H.close()
-    return x.cpu().numpy(), st, it, np.asarray(hist), xs.cpu().numpy(), info
+    return x.cpu().numpy(), st, it, np.asarray(hist), xs.cpu().numpy(), info, pcg
 
 
 CASES = [
@@ -56,14 +62,18 @@ CASES = [
 def test_fused_first_step_equals_the_separate_sweep(dim, elem, N, L, prec, sm, nu, storage, kb):
     k = W.k_blocks(N, dim=3, blocks_per_axis=kb, seed=20260101) if kb else None
     opts = dict(smoother=sm, nu_pre=nu, nu_post=nu, omega=0.8, precision=prec, storage=storage, coarse_tail=0)
-    xf, stf, itf, hf, sf, info_f = _run(dim, elem, N, L, 1, k, **opts)
-    x0, st0, it0, h0, s0, info_0 = _run(dim, elem, N, L, 0, k, **opts)
+    xf, stf, itf, hf, sf, info_f, pf = _run(dim, elem, N, L, 1, k, **opts)
+    x0, st0, it0, h0, s0, info_0, p0 = _run(dim, elem, N, L, 0, k, **opts)
     assert info_f["storage"] == info_0["storage"]
     assert info_f["kernels_per_cycle"] < info_0["kernels_per_cycle"]
     assert np.array_equal(xf, x0), np.max(np.abs(xf - x0))
     assert stf == st0 == mg.MG_OK and itf == it0
     assert np.array_equal(hf[:itf + 1], h0[:it0 + 1])
     assert np.array_equal(sf, s0)
+    # CG preconditioned by the V-cycle: on a mixed hierarchy its residual kernels (init and
+    # update) take the finest first step too
+    assert pf[0] == p0[0] == mg.MG_OK and pf[1] == p0[1]
+    assert np.array_equal(pf[2], p0[2]) and np.array_equal(pf[3], p0[3])
 
 
 def test_nothing_to_fuse_for_gauss_seidel_or_no_presmoothing():
@@ -74,4 +84,5 @@ def test_nothing_to_fuse_for_gauss_seidel_or_no_presmoothing():
         a = _run(3, mg.MG_Q1, 32, 3, 1, None, coarse_tail=0, **opts)
         b = _run(3, mg.MG_Q1, 32, 3, 0, None, coarse_tail=0, **opts)
         assert a[5]["kernels_per_cycle"] == b[5]["kernels_per_cycle"]
+        assert a[2] == b[2] and np.array_equal(a[3][:a[2] + 1], b[3][:b[2] + 1])
         assert np.array_equal(a[0], b[0])
