@@ -491,7 +491,7 @@ __device__ __forceinline__ double block_sum(double v, double *sh)
 // the grid is exactly one wave; a constant keeps the summation order, hence the bits,
 // independent of the device.
 constexpr int kReduceBlocks = 912;
-constexpr int kOuterBlocks = 608;  // the outer residual's grid (<= kReduceBlocks partial sums)
+constexpr int kOuterBlocks = 456;  // the outer residual's grid (<= kReduceBlocks partial sums)
 
 // Sum of `part` over the grid in a fixed order: block sums to partial[], the last block
 // to finish (ticket) adds them up. Returns true in the thread that wrote *out.
@@ -569,10 +569,11 @@ __device__ __forceinline__ int fp64_dof(const MatView<double> &A, int r)
 // ZM: the finest FP32 level's first smoothing step as well (ZStep), on the defect as the
 // FP32 value stored in r; its D^-1 is loaded before the row so that its latency hides
 // behind the row's.
-// Launched on kOuterBlocks blocks (four per SM, 64 registers a thread: measured faster than
-// five or six per SM with 48 or 40 registers, whose rows spill their loads into the chain).
+// Launched on kOuterBlocks blocks (three per SM, 80 registers a thread: measured faster than
+// four, five or six per SM with 64, 48 or 40 registers, where the compiler interleaves more
+// of each row's 42 loads with its chain of fused multiply-adds).
 template <typename Tin, int FMT, int K, int ZM = 0>
-__global__ void __launch_bounds__(256, 4) k_outer_resid(MatView<double> A, int n, const double *__restrict__ x,
+__global__ void __launch_bounds__(256, 3) k_outer_resid(MatView<double> A, int n, const double *__restrict__ x,
                                                      const double *__restrict__ b, Tin *__restrict__ r,
                                                      double *partial, unsigned *ticket, double *norm2,
                                                      ZStep<float> Zs)
