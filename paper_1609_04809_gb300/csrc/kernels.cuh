@@ -489,9 +489,11 @@ __device__ __forceinline__ double block_sum(double v, double *sh)
 // once per 256 rows. 912 = 6 blocks on each of GB300's 152 SMs, the residency those
 // kernels are compiled for (__launch_bounds__(256, 6): up to 42 registers, no spills), so
 // the grid is exactly one wave; a constant keeps the summation order, hence the bits,
-// independent of the device.
+// independent of the device. The kernels that apply the FP64 operator row by row (the
+// outer residual, the CG residual and matrix product) run 3 blocks per SM with 80
+// registers instead (kOuterBlocks = 456 blocks, at most kReduceBlocks partial sums).
 constexpr int kReduceBlocks = 912;
-constexpr int kOuterBlocks = 456;  // the outer residual's grid (<= kReduceBlocks partial sums)
+constexpr int kOuterBlocks = 456;
 
 // Sum of `part` over the grid in a fixed order: block sums to partial[], the last block
 // to finish (ticket) adds them up. Returns true in the thread that wrote *out.

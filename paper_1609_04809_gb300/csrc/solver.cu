@@ -929,7 +929,7 @@ static void enqueue_pcg_init(mg_hierarchy *h, cudaStream_t s)
     LaunchScope ls(h, s, MG_K_OUTER, h->Lf, bytes, 2.0 * entries + (zf ? 5.0 : 3.0) * n);
     MatView<double> v = view<double>(A);
     bool pdl = h->opt.use_pdl != 0;
-    dim3 g(reduce_grid(n)), blk(256);
+    dim3 g(std::min<unsigned>(reduce_grid(n), (unsigned)mgk::kOuterBlocks)), blk(256);  // FP64 rows: 3 blocks per SM
     const int zm = !zf ? 0 : (h->opt.smoother == MG_CHEBYSHEV ? (int)SW_CHEBF_Z : (int)SW_JACOBI_Z);
     launch_fp64_rows(h, A, [&](auto fmt, auto k) {
         constexpr int FMT = decltype(fmt)::value, K = decltype(k)::value;
@@ -971,8 +971,9 @@ static void enqueue_pcg_iter(mg_hierarchy *h, cudaStream_t s)
         double entries = mat_entries(A);
         LaunchScope ls(h, s, MG_K_KRYLOV, h->Lf, mat_bytes(A, 8) + 16.0 * n, 2.0 * entries + 2.0 * n);
         MatView<double> v = view<double>(A);
+        dim3 ga(std::min<unsigned>(reduce_grid(n), (unsigned)mgk::kOuterBlocks));  // FP64 rows: 3 blocks per SM
         launch_fp64_rows(h, A, [&](auto fmt, auto k) {
-            klaunch(pdl, k_pcg_apply<decltype(fmt)::value, decltype(k)::value>, gr, blk, 0, s, v, n,
+            klaunch(pdl, k_pcg_apply<decltype(fmt)::value, decltype(k)::value>, ga, blk, 0, s, v, n,
                     (const double *)h->pcg_p, h->pcg_q, h->partial, h->ticket, h->pcg_scal);
         });
     }
