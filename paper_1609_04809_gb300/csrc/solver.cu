@@ -1839,11 +1839,24 @@ static double time_format(mg_hierarchy *h, const mgh::Csr &A, int fmt, int dim, 
         cudaEvent_t e0, e1;
         CK(cudaEventCreate(&e0));
         CK(cudaEventCreate(&e1));
-        // a busy GPU first (clocks leave their idle state), then the best of several runs
-        for (int rep = 0; rep < 200; rep++) sweep_fmt<T, SW_RESID>(m, (int)A.nrows, x, b, r, (T *)nullptr, T(0), T(0), h->s);
+        // a busy GPU first (clocks leave their idle state), then the best of several runs.
+        // An FP32 level is timed on what a V-cycle runs on it, three smoothing steps per
+        // residual (the per-cell form has a separate residual kernel); an FP64 level on
+        // residuals (its smoothing steps would read a D^-1 this trial does not build).
+        auto four = [&]() {
+            if constexpr (std::is_same<T, float>::value) {
+                for (int k = 0; k < 3; k++)
+                    sweep_fmt<T, SW_JACOBI>(m, (int)A.nrows, x, b, r, (T *)nullptr, T(0.8), T(0), h->s);
+                sweep_fmt<T, SW_RESID>(m, (int)A.nrows, x, b, r, (T *)nullptr, T(0), T(0), h->s);
+            } else {
+                for (int k = 0; k < 4; k++)
+                    sweep_fmt<T, SW_RESID>(m, (int)A.nrows, x, b, r, (T *)nullptr, T(0), T(0), h->s);
+            }
+        };
+        for (int rep = 0; rep < 50; rep++) four();
         for (int rep = 0; rep < 10; rep++) {
             CK(cudaEventRecord(e0, h->s));
-            for (int k = 0; k < 4; k++) sweep_fmt<T, SW_RESID>(m, (int)A.nrows, x, b, r, (T *)nullptr, T(0), T(0), h->s);
+            four();
             CK(cudaEventRecord(e1, h->s));
             CK(cudaEventSynchronize(e1));
             float ms = 0.f;
