@@ -489,11 +489,14 @@ __device__ __forceinline__ double block_sum(double v, double *sh)
 // once per 256 rows. 912 = 6 blocks on each of GB300's 152 SMs, the residency those
 // kernels are compiled for (__launch_bounds__(256, 6): up to 42 registers, no spills), so
 // the grid is exactly one wave; a constant keeps the summation order, hence the bits,
-// independent of the device. The kernels that apply the FP64 operator row by row (the
+// independent of the device. The kernels that apply a DIA FP64 operator row by row (the
 // outer residual, the CG residual and matrix product) run 3 blocks per SM with 80
-// registers instead (kOuterBlocks = 456 blocks, at most kReduceBlocks partial sums).
+// registers instead (kOuterBlocks = 456 blocks, at most kReduceBlocks partial sums); on
+// the gathered formats (ELL, CSR, SELL) they keep 6 blocks per SM, which hide the latency
+// of each column index's dependent load better.
 constexpr int kReduceBlocks = 912;
 constexpr int kOuterBlocks = 456;
+constexpr int fp64_rows_blocks_per_sm(int fmt) { return fmt == 3 ? 3 : 6; }
 
 // Sum of `part` over the grid in a fixed order: block sums to partial[], the last block
 // to finish (ticket) adds them up. Returns true in the thread that wrote *out.
@@ -571,11 +574,11 @@ __device__ __forceinline__ int fp64_dof(const MatView<double> &A, int r)
 // ZM: the finest FP32 level's first smoothing step as well (ZStep), on the defect as the
 // FP32 value stored in r; its D^-1 is loaded before the row so that its latency hides
 // behind the row's.
-// Launched on kOuterBlocks blocks (three per SM, 80 registers a thread: measured faster than
-// four, five or six per SM with 64, 48 or 40 registers, where the compiler interleaves more
-// of each row's 42 loads with its chain of fused multiply-adds).
+// DIA: launched on kOuterBlocks blocks (three per SM, 80 registers a thread: measured faster
+// than four, five or six per SM with 64, 48 or 40 registers, where the compiler interleaves
+// more of each row's 42 loads with its chain of fused multiply-adds).
 template <typename Tin, int FMT, int K, int ZM = 0>
-__global__ void __launch_bounds__(256, 3) k_outer_resid(MatView<double> A, int n, const double *__restrict__ x,
+__global__ void __launch_bounds__(256, fp64_rows_blocks_per_sm(FMT)) k_outer_resid(MatView<double> A, int n, const double *__restrict__ x,
                                                      const double *__restrict__ b, Tin *__restrict__ r,
                                                      double *partial, unsigned *ticket, double *norm2,
                                                      ZStep<float> Zs)

@@ -24,7 +24,7 @@ enum PcgScalar { PCG_RZ = 0, PCG_RZ_OLD = 1, PCG_PQ = 2, PCG_ALPHA = 3, PCG_BETA
 // right-hand side); p = 0, rz_old = 0; ||r||^2 -> norm2. ZM: also the finest FP32 level's
 // first smoothing step on rin (ZStep, as in k_outer_resid).
 template <typename Tin, int FMT, int K, int ZM = 0>
-__global__ void __launch_bounds__(256, 3) k_pcg_init(MatView<double> A, int n, const double *__restrict__ x,
+__global__ void __launch_bounds__(256, fp64_rows_blocks_per_sm(FMT)) k_pcg_init(MatView<double> A, int n, const double *__restrict__ x,
                                                   const double *__restrict__ b, double *__restrict__ r64,
                                                   Tin *__restrict__ rin, double *__restrict__ p, double *scal,
                                                   double *partial, unsigned *ticket, double *norm2, ZStep<float> Zs)
@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(256) k_pcg_dir(const Tin *__restrict__ z, doub
 }
 
 template <int FMT, int K>
-__global__ void __launch_bounds__(256, 3) k_pcg_apply(MatView<double> A, int n, const double *__restrict__ p,
+__global__ void __launch_bounds__(256, fp64_rows_blocks_per_sm(FMT)) k_pcg_apply(MatView<double> A, int n, const double *__restrict__ p,
                                                    double *__restrict__ q, double *partial, unsigned *ticket,
                                                    double *scal)
 {

@@ -136,6 +136,12 @@ static inline int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * 
 static inline unsigned grid_for(int64_t n) { return (unsigned)((n + 255) / 256); }
 // grid of a kernel that ends in a block-partial reduction (finish_norm)
 static inline unsigned reduce_grid(int64_t n) { return std::min<unsigned>(std::max<unsigned>(grid_for(n), 1u), kReduceBlocks); }
+// grid of a kernel that applies an FP64 operator row by row: one wave at the residency it
+// is compiled for (mgk::fp64_rows_blocks_per_sm; the storage codes equal its FMT codes)
+static inline unsigned fp64_rows_grid(const DevMat &A, int64_t n)
+{
+    return std::min<unsigned>(reduce_grid(n), 152u * (unsigned)mgk::fp64_rows_blocks_per_sm(A.fmt));
+}
 
 // threads per block of a row sweep: 256, or 64 below two blocks of 256 per SM of the 152,
 // so that the few rows of a small level spread over every SM (rows are independent)
@@ -839,7 +845,7 @@ static void enqueue_outer(mg_hierarchy *h, cudaStream_t s)
     double bytes = mat_bytes(A, 8) + 16.0 * n + (double)n * sizeof(T);
     double entries = mat_entries(A);
     MatView<double> v = view<double>(A);
-    dim3 g(std::min<unsigned>(reduce_grid(n), (unsigned)mgk::kOuterBlocks)), blk(256);
+    dim3 g(fp64_rows_grid(A, n)), blk(256);
     T *r = (T *)F.b;
     bool pdl = h->opt.use_pdl != 0;
     const double *x = h->x64, *b = h->b64;
@@ -929,7 +935,7 @@ static void enqueue_pcg_init(mg_hierarchy *h, cudaStream_t s)
     LaunchScope ls(h, s, MG_K_OUTER, h->Lf, bytes, 2.0 * entries + (zf ? 5.0 : 3.0) * n);
     MatView<double> v = view<double>(A);
     bool pdl = h->opt.use_pdl != 0;
-    dim3 g(std::min<unsigned>(reduce_grid(n), (unsigned)mgk::kOuterBlocks)), blk(256);  // FP64 rows: 3 blocks per SM
+    dim3 g(fp64_rows_grid(A, n)), blk(256);
     const int zm = !zf ? 0 : (h->opt.smoother == MG_CHEBYSHEV ? (int)SW_CHEBF_Z : (int)SW_JACOBI_Z);
     launch_fp64_rows(h, A, [&](auto fmt, auto k) {
         constexpr int FMT = decltype(fmt)::value, K = decltype(k)::value;
@@ -971,7 +977,7 @@ static void enqueue_pcg_iter(mg_hierarchy *h, cudaStream_t s)
         double entries = mat_entries(A);
         LaunchScope ls(h, s, MG_K_KRYLOV, h->Lf, mat_bytes(A, 8) + 16.0 * n, 2.0 * entries + 2.0 * n);
         MatView<double> v = view<double>(A);
-        dim3 ga(std::min<unsigned>(reduce_grid(n), (unsigned)mgk::kOuterBlocks));  // FP64 rows: 3 blocks per SM
+        dim3 ga(fp64_rows_grid(A, n));
         launch_fp64_rows(h, A, [&](auto fmt, auto k) {
             klaunch(pdl, k_pcg_apply<decltype(fmt)::value, decltype(k)::value>, ga, blk, 0, s, v, n,
                     (const double *)h->pcg_p, h->pcg_q, h->partial, h->ticket, h->pcg_scal);
