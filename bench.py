@@ -156,7 +156,7 @@ KERNEL_PARTS = {
     "k_outer_resid": [("sweep.cuh", "pdl_enter"), ("sweep.cuh", "struct Ar<float>"), ("sweep.cuh", "sweep_out_v"),
                       ("kernels.cuh", "block_sum"), ("kernels.cuh", "finish_norm"), ("kernels.cuh", "fp64_row"),
                       ("kernels.cuh", "fp64_dof"), ("kernels.cuh", "struct ZStep"), ("kernels.cuh", "zstep_dinv"),
-                      ("kernels.cuh", "k_outer_resid")],
+                      ("kernels.cuh", "fp64_rows_blocks_per_sm"), ("kernels.cuh", "k_outer_resid")],
 }
 SWEEP_KERNELS = {"dia": "k_dia_sweep", "ell": "k_ell_sweep", "csr": "k_csr_sweep", "sell": "k_sell_sweep",
                  "stencil": "k_stencil_sweep", "coef": "k_coef_sweep"}

@@ -62,3 +62,9 @@ def test_kernel_key_follows_the_kernel_code_only():
     fin = k.replace("*ticket = 0u;", "*ticket = 0u + 0u;", 1)
     assert fin != k and bench._kernel_sha("k_outer_resid", {**src, "kernels.cuh": fin}) != bench._kernel_sha(
         "k_outer_resid", src)
+    # and its residency (a one-line function in its launch bounds)
+    occ = k.replace("return fmt == 3 ? 3 : 6;", "return fmt == 3 ? 4 : 6;", 1)
+    assert occ != k and bench._kernel_sha("k_outer_resid", {**src, "kernels.cuh": occ}) != bench._kernel_sha(
+        "k_outer_resid", src)
+    one = bench._source_part(k, "fp64_rows_blocks_per_sm")
+    assert one.startswith("constexpr int fp64_rows_blocks_per_sm(") and one.count("\n") == 1
