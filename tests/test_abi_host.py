@@ -43,6 +43,9 @@ def test_every_declared_symbol_is_exported(lib):
 def test_defaults_and_ndofs(lib):
     o = mg.mg_options_default()
     assert (o.smoother, o.omega, o.nu_pre, o.nu_post, o.precision, o.max_iters) == (0, 0.8, 2, 2, 0, 100)
+    # the last fields of the struct: a layout mismatch between mg.h and the binding would
+    # shift them
+    assert (o.use_graph, o.use_pdl, o.coarse_tail, o.fuse_first) == (1, 1, 2, 1)
     assert mg.mg_ndofs(2, mg.MG_Q1, 64) == 63 ** 2
     assert mg.mg_ndofs(3, mg.MG_Q1, 128) == 127 ** 3
     assert mg.mg_ndofs(3, mg.MG_RQ1, 96) == 3 * 95 * 96 * 96 == 2626560
